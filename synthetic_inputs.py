@@ -1,0 +1,84 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the bench.
+
+This module holds workload definitions (ring degree, prime bit sizes, digit
+count, scale, batch size) and seeded message generators only: none of the
+scheme's arithmetic lives here.  Both the CPU oracle and the CUDA library get
+their messages and seeds from here; each side then draws its own secret,
+errors and masks from the seed with its own implementation of the
+counter-based SplitMix64 generator.
+
+The paper's datasets (MNIST and the other Table 2 sets) are not available;
+messages are uniform in [-1, 1] (real and imaginary parts), the distribution
+the scheme's error bounds are quoted on, and the MLP inputs are uniform in
+[0, 1] with 784 features per sample.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    log_n: int
+    q_bits: tuple
+    p_bits: tuple
+    dnum: int
+    log2_scale: float
+    h: int = 64
+    sigma: float = 3.2
+    batch: int = 1
+    rot_steps: tuple = field(default_factory=tuple)
+
+    @property
+    def n(self) -> int:
+        return 1 << self.log_n
+
+    @property
+    def slots(self) -> int:
+        return self.n // 2
+
+
+# Toy ring (not secure): N = 2^12, 2048 slots, scale 2^40.  q0 ~ 2^50 holds the
+# message after the last rescale; q1, q2 ~ 2^40 match the scale so that a
+# rescale returns it to ~2^40; one special prime of 51 bits (>= every q_i).
+TOY = Workload("toy_n4096_q50_40_40_p51", 12, (50, 40, 40), (51,), 3, 40.0,
+               batch=1, rot_steps=(1,))
+
+# N = 2^16, 24 ciphertext primes (q0 ~ 2^61, 23 x ~2^55), 8 special primes of
+# 61 bits, dnum = 3 (8 primes per digit), scale 2^55, 64 ciphertext pairs and
+# rotations by every power of two up to 2^14.
+PLAIN = Workload("n65536_L24_dnum3_b64", 16, (61,) + (55,) * 23, (61,) * 8, 3, 55.0,
+                 batch=64, rot_steps=tuple(1 << k for k in range(15)))
+
+# Small versions of the same shapes that the CPU oracle finishes in seconds
+# while still spanning several NTT tiles and more than one digit.
+SMALL = Workload("n4096_L6_dnum3", 12, (61,) + (55,) * 5, (61,) * 2, 3, 55.0,
+                 batch=3, rot_steps=(1, 2, 4, -1))
+MID = Workload("n8192_L8_dnum3", 13, (61,) + (55,) * 7, (61,) * 3, 3, 55.0,
+               batch=2, rot_steps=(1, 8))
+
+
+def rng(seed: int, stream: str) -> np.random.Generator:
+    """An independent numpy generator per (seed, stream name)."""
+    tag = int.from_bytes(stream.encode()[:8].ljust(8, b"\0"), "little")
+    return np.random.default_rng([seed, tag])
+
+
+def messages(seed: int, count: int, n_slots: int, real_only: bool = False) -> np.ndarray:
+    """`count` vectors of `n_slots` complex slots, real and imaginary parts
+    uniform in [-1, 1]."""
+    g = rng(seed, "msg")
+    re = g.uniform(-1.0, 1.0, size=(count, n_slots))
+    if real_only:
+        return re.astype(np.complex128)
+    im = g.uniform(-1.0, 1.0, size=(count, n_slots))
+    return re + 1j * im
+
+
+def enc_seeds(seed: int, count: int) -> list[int]:
+    """Per-ciphertext encryption seeds (64-bit)."""
+    g = rng(seed, "encseed")
+    return [int(x) for x in g.integers(0, 2 ** 63 - 1, size=count, dtype=np.int64)]
