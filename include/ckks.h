@@ -1,0 +1,198 @@
+/*
+ * ckks.h -- C ABI of the GB300 RNS-CKKS evaluation core.
+ *
+ * The operations follow the statement of CKKS in ReBoot (arXiv 2506.19693),
+ * Sec. 3: a parameter set {N, q, Delta} (N the ring degree, q the prime chain,
+ * Delta the scale); batching of up to N/2 complex values into one plaintext
+ * through the complex canonical embedding; secret-key encryption; slot-wise
+ * homomorphic +, -, x (Eq. add, sub, mult) and their plaintext variants;
+ * switching to the next prime after a multiplication; Rot(a, k), a cyclic left
+ * shift by k slots with one key per k; and bootstrapping.  The scheme's
+ * internals (prime chain, NTT order, hybrid key switching, rescale rounding)
+ * are the textbook RNS-CKKS readings listed in the design notes as C1..C12.
+ *
+ * Conventions for every entry point:
+ *  - Return value: CKKS_OK (0) or a negative CKKS_E_* status.  Nothing aborts,
+ *    nothing throws; ckks_status_str() names a status.
+ *  - Device pointers ("_dev") are CUDA global-memory addresses on the device
+ *    that was current when the context was created; the caller owns them and
+ *    keeps them alive until the work enqueued on the context's stream is done.
+ *    Host pointers ("_host" or plain host arrays) are read or written before
+ *    the call returns.
+ *  - All device work is enqueued on the context's stream (stream order); calls
+ *    that return host data synchronise that stream.
+ *  - Layout: a polynomial over limbs q_0..q_l is uint64[l+1][N], limb-major,
+ *    each limb contiguous, residues in [0, q_i).  A ciphertext buffer is
+ *    uint64[2][n_limbs][N]: poly 0 at data, poly 1 at data + n_limbs*N; only
+ *    limbs 0..level of each poly are meaningful (n_limbs >= level + 1 is the
+ *    capacity, so rescale can work in place).  Ciphertexts and plaintexts live
+ *    in the NTT domain, canonical order A[j] = a(psi^(2*brv(j)+1)) mod q_i.
+ *  - The context is not thread-safe; use one context per host thread.
+ */
+#ifndef CKKS_H
+#define CKKS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CKKS_OK 0
+#define CKKS_E_PARAM (-1)   /* invalid argument or parameter set               */
+#define CKKS_E_LEVEL (-2)   /* level mismatch, level out of range, level 0 rescale */
+#define CKKS_E_SCALE (-3)   /* scaled plaintext >= 2^62 or scale mismatch       */
+#define CKKS_E_NOKEY (-4)   /* secret, relinearisation or Galois key missing    */
+#define CKKS_E_OOM (-5)     /* device or host allocation failed                 */
+#define CKKS_E_CUDA (-6)    /* a CUDA runtime call failed                       */
+#define CKKS_E_TIMEOUT (-7) /* a bounded device-side wait ran out               */
+#define CKKS_E_STATE (-8)   /* call made in the wrong state                      */
+
+#define CKKS_MAX_Q 60
+#define CKKS_MAX_P 16
+
+typedef struct ckks_ctx ckks_ctx;
+
+/* Parameter set Theta = {N, q, Delta} (Sec. 3).  N = 2^log_n (2^12..2^16).
+ * The chain q_0..q_{n_q-1} and the special primes p_0..p_{n_p-1} are the
+ * largest primes = 1 mod 2^17 below 2^bits, taken in chain order per bit size
+ * (reading C1).  dnum = number of key-switching digits: alpha = ceil(n_q/dnum)
+ * q-primes per digit (reading C7).  h = Hamming weight of the ternary secret,
+ * sigma = standard deviation of the rounded Gaussian error (tail cut at
+ * floor(6 sigma)).  log2_scale is the default scale used by ckks_encode when
+ * it is passed scale <= 0. */
+typedef struct {
+  uint32_t log_n, n_q, n_p, dnum, h;
+  uint32_t q_bits[CKKS_MAX_Q], p_bits[CKKS_MAX_P];
+  double log2_scale, sigma;
+  uint64_t seed; /* unused by ckks_ctx_create; kept for presets */
+} ckks_params;
+
+/* A ciphertext handle.  data: device, uint64[2][n_limbs][N], NTT domain.
+ * level: index of the top active prime (level + 1 active limbs).
+ * scale: Delta of the encrypted message, tracked exactly as a double. */
+typedef struct {
+  uint64_t *data;
+  uint32_t log_n, level, n_limbs, is_ntt;
+  double scale;
+} ckks_ct;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context for `params` on the current CUDA device; all its work goes
+ * to `cuda_stream` (a cudaStream_t, or NULL for the legacy default stream).
+ * Derives primes, roots and all tables and uploads them.  *out owns them. */
+int ckks_ctx_create(const ckks_params *params, void *cuda_stream, ckks_ctx **out);
+int ckks_ctx_destroy(ckks_ctx *ctx);
+/* Change the stream later calls enqueue on. */
+int ckks_ctx_set_stream(ckks_ctx *ctx, void *cuda_stream);
+/* Host copy of the moduli q_0..q_{n_q-1}, p_0..p_{n_p-1} (cap entries max). */
+int ckks_ctx_moduli(const ckks_ctx *ctx, uint64_t *out_host, int cap);
+/* Host copy of the primitive 2N-th roots psi_i (reading C2). */
+int ckks_ctx_roots(const ckks_ctx *ctx, uint64_t *out_host, int cap);
+/* Digits actually used (ceil(n_q / alpha)) and alpha. */
+int ckks_ctx_digits(const ckks_ctx *ctx, int *n_digits, int *alpha);
+/* Bytes of device memory the context holds (tables, keys, scratch). */
+int ckks_ctx_device_bytes(const ckks_ctx *ctx, uint64_t *bytes);
+
+/* ---- keys (Sec. 3: "one key corresponding to each desired rotation index") */
+
+/* Draw the ternary secret from `seed` and build the relinearisation key
+ * (s^2 -> s) plus one Galois key per rotation step in rot_steps[0..n_rot)
+ * (left rotation by k, g = 5^(k mod N/2) mod 2N), the conjugation key when
+ * want_conj.  want_boot must be 0 (CKKS_E_STATE otherwise).  Randomness:
+ * counter-based SplitMix64 keyed by seed (reading C4).  Replaces earlier keys. */
+int ckks_keygen_from_seed(ckks_ctx *ctx, uint64_t seed, const int32_t *rot_steps, int n_rot,
+                          int want_conj, int want_boot);
+/* Add the Galois key for element g (odd, < 2N) to the current key set. */
+int ckks_keygen_galois(ckks_ctx *ctx, uint64_t galois_elt);
+/* Galois element of a left rotation by k. */
+uint64_t ckks_galois_elt(const ckks_ctx *ctx, int32_t k);
+/* TEST ONLY: host copy of the ternary secret (int8[N]). */
+int ckks_debug_secret(const ckks_ctx *ctx, int8_t *out_host);
+/* TEST ONLY: host copy of one switching key, uint64[n_digits][2][n_q+n_p][N]
+ * (b_j, a_j per digit, NTT domain); galois_elt 0 selects relinearisation. */
+int ckks_debug_key(const ckks_ctx *ctx, uint64_t galois_elt, uint64_t *out_host);
+
+/* ---- plaintexts (Sec. 3 batching) --------------------------------------- */
+
+/* Encode n_slots <= N/2 complex values (re/im host arrays; missing slots are 0)
+ * at `scale` (<= 0 selects the default) into an NTT-domain plaintext over
+ * q_0..q_level: pt_dev is uint64[level+1][N].  Coefficients are
+ * round-half-away(scale * tau^-1(z)) computed in FP64 on the GPU; CKKS_E_SCALE
+ * if any reaches 2^62. */
+int ckks_encode(ckks_ctx *ctx, const double *re, const double *im, int n_slots, uint32_t level,
+                double scale, uint64_t *pt_dev);
+/* Decode an NTT-domain plaintext over q_0..q_level: centred CRT to FP64, then
+ * the forward embedding, divided by `scale`.  Writes n_slots values to re/im. */
+int ckks_decode(ckks_ctx *ctx, const uint64_t *pt_dev, uint32_t level, double scale, double *re,
+                double *im, int n_slots);
+/* Signed integer coefficients (host int64[N], |m| < 2^62) -> NTT-domain
+ * residues over q_0..q_level in pt_dev. */
+int ckks_pt_from_int(ckks_ctx *ctx, const int64_t *m_host, uint32_t level, uint64_t *pt_dev);
+/* Forward (inverse != 0: inverse) negacyclic NTT, in place, of n_limbs limbs
+ * at data_dev; limb l uses modulus index first_mod + l (0..n_q-1 are q_i,
+ * n_q.. are p_j).  Residues in [0, modulus) in and out. */
+int ckks_ntt(ckks_ctx *ctx, uint64_t *data_dev, uint32_t n_limbs, uint32_t first_mod, int inverse);
+
+/* ---- encryption (Sec. 3, reading C5) ------------------------------------ */
+
+/* ct = ([-a s + m + e], a) over q_0..q_level; a uniform (drawn in the NTT
+ * domain), e rounded Gaussian, both from enc_seed.  out->data must hold
+ * out->n_limbs >= level + 1 limbs per poly; level/scale/is_ntt are set. */
+int ckks_encrypt(ckks_ctx *ctx, const uint64_t *pt_dev, uint32_t level, double scale,
+                 uint64_t enc_seed, ckks_ct *out);
+/* pt_dev (uint64[level+1][N]) = c0 + c1 s, NTT domain. */
+int ckks_decrypt(ckks_ctx *ctx, const ckks_ct *ct, uint64_t *pt_dev);
+
+/* ---- evaluation (Eq. add, sub, mult; Sec. 3) ----------------------------- */
+
+/* Slot-wise sum / difference; levels must match (CKKS_E_LEVEL).  out may alias. */
+int ckks_add(ckks_ctx *ctx, const ckks_ct *a, const ckks_ct *b, ckks_ct *out);
+int ckks_sub(ckks_ctx *ctx, const ckks_ct *a, const ckks_ct *b, ckks_ct *out);
+/* (c0 * pt, c1 * pt); out->scale = a->scale * pt_scale. */
+int ckks_mul_plain(ckks_ctx *ctx, const ckks_ct *a, const uint64_t *pt_dev, double pt_scale,
+                   ckks_ct *out);
+/* (c0 + pt, c1); the plaintext must be at a's scale. */
+int ckks_add_plain(ckks_ctx *ctx, const ckks_ct *a, const uint64_t *pt_dev, ckks_ct *out);
+/* Multiply by a signed integer constant; consumes no level (reading C14). */
+int ckks_mul_int(ckks_ctx *ctx, const ckks_ct *a, int64_t k, ckks_ct *out);
+/* Relinearised product (reading C6): (d0, d1) + KeySwitch_{s^2->s}(d2) with
+ * d0 = a0 b0, d1 = a0 b1 + a1 b0, d2 = a1 b1.  out->scale = a->scale*b->scale. */
+int ckks_mul_relin(ckks_ctx *ctx, const ckks_ct *a, const ckks_ct *b, ckks_ct *out);
+/* Drop the top prime q_l: c'_i = (c_i - [c_l]_centred) * q_l^-1 mod q_i
+ * (reading C10); level -1, scale / q_l.  In place; CKKS_E_LEVEL at level 0. */
+int ckks_rescale(ckks_ctx *ctx, ckks_ct *inout);
+/* Rot(a, k): left cyclic shift of the slots by k (Sec. 3), via
+ * X -> X^(5^k mod 2N) and key switching (reading C11). */
+int ckks_rotate(ckks_ctx *ctx, const ckks_ct *a, int32_t k, ckks_ct *out);
+/* Complex conjugation of every slot (X -> X^(2N-1)). */
+int ckks_conjugate(ckks_ctx *ctx, const ckks_ct *a, ckks_ct *out);
+/* Apply the automorphism X -> X^g (g odd, < 2N) and switch back to s. */
+int ckks_automorph(ckks_ctx *ctx, const ckks_ct *a, uint64_t galois_elt, ckks_ct *out);
+
+/* ---- batched variants: n independent ciphertexts in one set of launches -- */
+
+/* out[i] = mul_relin(a[i], b[i]) then, if do_rescale, rescale(out[i]).
+ * All a[i], b[i] at one level. */
+int ckks_mul_relin_batch(ckks_ctx *ctx, const ckks_ct *a, const ckks_ct *b, ckks_ct *out, int n,
+                         int do_rescale);
+/* out[i] = rotate(in[i], k[i]). */
+int ckks_rotate_batch(ckks_ctx *ctx, const ckks_ct *in, const int32_t *k, ckks_ct *out, int n);
+/* In-place rescale of n ciphertexts at one level. */
+int ckks_rescale_batch(ckks_ctx *ctx, ckks_ct *inout, int n);
+
+/* ---- checkpoint helpers ------------------------------------------------- */
+
+/* Copy a ciphertext's active limbs to/from host memory as
+ * uint64[2][level+1][N] (NTT domain). */
+int ckks_ct_export(ckks_ctx *ctx, const ckks_ct *ct, uint64_t *out_host);
+int ckks_ct_import(ckks_ctx *ctx, const uint64_t *in_host, ckks_ct *ct);
+
+const char *ckks_status_str(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CKKS_H */

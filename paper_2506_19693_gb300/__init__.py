@@ -1,0 +1,380 @@
+"""Python binding of the GB300 RNS-CKKS library (``include/ckks.h``).
+
+Argument marshalling only: every step of every operation runs in the CUDA
+library ``_build/libckks.so``.  PyTorch provides device memory (ciphertexts
+and plaintexts are torch tensors on the GPU) and the stream the library
+enqueues on.  Importing this package without the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+CKKS_OK = 0
+STATUS = {0: "CKKS_OK", -1: "CKKS_E_PARAM", -2: "CKKS_E_LEVEL", -3: "CKKS_E_SCALE", -4: "CKKS_E_NOKEY",
+          -5: "CKKS_E_OOM", -6: "CKKS_E_CUDA", -7: "CKKS_E_TIMEOUT", -8: "CKKS_E_STATE"}
+
+
+class CkksError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(status, status)}")
+        self.status = status
+
+
+class CkksParams(ctypes.Structure):
+    _fields_ = [("log_n", ctypes.c_uint32), ("n_q", ctypes.c_uint32), ("n_p", ctypes.c_uint32),
+                ("dnum", ctypes.c_uint32), ("h", ctypes.c_uint32),
+                ("q_bits", ctypes.c_uint32 * 60), ("p_bits", ctypes.c_uint32 * 16),
+                ("log2_scale", ctypes.c_double), ("sigma", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class CkksCt(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("log_n", ctypes.c_uint32), ("level", ctypes.c_uint32),
+                ("n_limbs", ctypes.c_uint32), ("is_ntt", ctypes.c_uint32), ("scale", ctypes.c_double)]
+
+
+# C-ABI symbols and signatures, in header order.
+_V, _I, _U64, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_double
+_CTP = ctypes.POINTER(CkksCt)
+SIGNATURES = {
+    "ckks_ctx_create": (_I, [ctypes.POINTER(CkksParams), _V, ctypes.POINTER(_V)]),
+    "ckks_ctx_destroy": (_I, [_V]),
+    "ckks_ctx_set_stream": (_I, [_V, _V]),
+    "ckks_ctx_moduli": (_I, [_V, _V, _I]),
+    "ckks_ctx_roots": (_I, [_V, _V, _I]),
+    "ckks_ctx_digits": (_I, [_V, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "ckks_ctx_device_bytes": (_I, [_V, ctypes.POINTER(_U64)]),
+    "ckks_keygen_from_seed": (_I, [_V, _U64, _V, _I, _I, _I]),
+    "ckks_keygen_galois": (_I, [_V, _U64]),
+    "ckks_galois_elt": (_U64, [_V, ctypes.c_int32]),
+    "ckks_debug_secret": (_I, [_V, _V]),
+    "ckks_debug_key": (_I, [_V, _U64, _V]),
+    "ckks_encode": (_I, [_V, _V, _V, _I, ctypes.c_uint32, _D, _V]),
+    "ckks_decode": (_I, [_V, _V, ctypes.c_uint32, _D, _V, _V, _I]),
+    "ckks_pt_from_int": (_I, [_V, _V, ctypes.c_uint32, _V]),
+    "ckks_ntt": (_I, [_V, _V, ctypes.c_uint32, ctypes.c_uint32, _I]),
+    "ckks_encrypt": (_I, [_V, _V, ctypes.c_uint32, _D, _U64, _CTP]),
+    "ckks_decrypt": (_I, [_V, _CTP, _V]),
+    "ckks_add": (_I, [_V, _CTP, _CTP, _CTP]),
+    "ckks_sub": (_I, [_V, _CTP, _CTP, _CTP]),
+    "ckks_mul_plain": (_I, [_V, _CTP, _V, _D, _CTP]),
+    "ckks_add_plain": (_I, [_V, _CTP, _V, _CTP]),
+    "ckks_mul_int": (_I, [_V, _CTP, ctypes.c_int64, _CTP]),
+    "ckks_mul_relin": (_I, [_V, _CTP, _CTP, _CTP]),
+    "ckks_rescale": (_I, [_V, _CTP]),
+    "ckks_rotate": (_I, [_V, _CTP, ctypes.c_int32, _CTP]),
+    "ckks_conjugate": (_I, [_V, _CTP, _CTP]),
+    "ckks_automorph": (_I, [_V, _CTP, _U64, _CTP]),
+    "ckks_mul_relin_batch": (_I, [_V, _CTP, _CTP, _CTP, _I, _I]),
+    "ckks_rotate_batch": (_I, [_V, _CTP, _V, _CTP, _I]),
+    "ckks_rescale_batch": (_I, [_V, _CTP, _I]),
+    "ckks_ct_export": (_I, [_V, _CTP, _V]),
+    "ckks_ct_import": (_I, [_V, _V, _CTP]),
+    "ckks_status_str": (ctypes.c_char_p, [_I]),
+}
+
+_lib = None
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load libckks.so (building it first if the sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.lib_path()
+    if not os.path.exists(path):
+        path = _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != CKKS_OK:
+        raise CkksError(rc, what)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+@dataclass
+class Ciphertext:
+    """A ciphertext in HBM: ``data`` is an int64 torch tensor of shape
+    [2, n_limbs, N] (bit pattern of uint64 residues, NTT domain)."""
+    data: "object"
+    level: int
+    scale: float
+
+    @property
+    def n_limbs(self) -> int:
+        return int(self.data.shape[1])
+
+    def handle(self, log_n: int) -> CkksCt:
+        return CkksCt(self.data.data_ptr(), log_n, self.level, self.n_limbs, 1, self.scale)
+
+
+class Context:
+    """One parameter set on the current CUDA device and stream."""
+
+    def __init__(self, log_n: int, q_bits, p_bits, dnum: int, h: int = 64, sigma: float = 3.2,
+                 log2_scale: float = 40.0, stream=None):
+        torch = _torch()
+        self.lib = load_library()
+        p = CkksParams()
+        p.log_n, p.n_q, p.n_p, p.dnum, p.h = log_n, len(q_bits), len(p_bits), dnum, h
+        for i, b in enumerate(q_bits):
+            p.q_bits[i] = b
+        for i, b in enumerate(p_bits):
+            p.p_bits[i] = b
+        p.log2_scale, p.sigma = log2_scale, sigma
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        h_ = ctypes.c_void_p()
+        _check(self.lib.ckks_ctx_create(ctypes.byref(p), ctypes.c_void_p(self.stream.cuda_stream),
+                                        ctypes.byref(h_)), "ckks_ctx_create")
+        self._h = h_
+        self.log_n, self.n = log_n, 1 << log_n
+        self.n_q, self.n_p, self.dnum = len(q_bits), len(p_bits), dnum
+        buf = (ctypes.c_uint64 * (self.n_q + self.n_p))()
+        self.lib.ckks_ctx_moduli(self._h, buf, self.n_q + self.n_p)
+        self.moduli = [int(x) for x in buf]
+        self.q = self.moduli[: self.n_q]
+        self.p = self.moduli[self.n_q:]
+        self.lib.ckks_ctx_roots(self._h, buf, self.n_q + self.n_p)
+        self.psi = [int(x) for x in buf]
+        nd, al = ctypes.c_int(), ctypes.c_int()
+        self.lib.ckks_ctx_digits(self._h, ctypes.byref(nd), ctypes.byref(al))
+        self.n_digits, self.alpha = nd.value, al.value
+        self.default_scale = 2.0 ** log2_scale
+
+    @classmethod
+    def from_workload(cls, w, stream=None) -> "Context":
+        return cls(w.log_n, w.q_bits, w.p_bits, w.dnum, w.h, w.sigma, w.log2_scale, stream)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self.lib.ckks_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- memory ----
+    def new_ct(self, n_limbs: int, level: int | None = None, scale: float = 1.0) -> Ciphertext:
+        torch = _torch()
+        t = torch.empty((2, n_limbs, self.n), dtype=torch.int64, device=self.device)
+        return Ciphertext(t, n_limbs - 1 if level is None else level, scale)
+
+    def new_pt(self, level: int):
+        torch = _torch()
+        return torch.empty((level + 1, self.n), dtype=torch.int64, device=self.device)
+
+    def device_bytes(self) -> int:
+        b = ctypes.c_uint64()
+        _check(self.lib.ckks_ctx_device_bytes(self._h, ctypes.byref(b)), "ckks_ctx_device_bytes")
+        return b.value
+
+    # ---- keys ----
+    def keygen(self, seed: int, rot_steps=(), conj: bool = False) -> None:
+        arr = (ctypes.c_int32 * max(1, len(rot_steps)))(*rot_steps)
+        _check(self.lib.ckks_keygen_from_seed(self._h, seed, arr, len(rot_steps), int(conj), 0),
+               "ckks_keygen_from_seed")
+
+    def keygen_galois(self, g: int) -> None:
+        _check(self.lib.ckks_keygen_galois(self._h, g), "ckks_keygen_galois")
+
+    def galois_elt(self, k: int) -> int:
+        return int(self.lib.ckks_galois_elt(self._h, k))
+
+    def debug_secret(self) -> np.ndarray:
+        s = np.zeros(self.n, dtype=np.int8)
+        _check(self.lib.ckks_debug_secret(self._h, s.ctypes.data), "ckks_debug_secret")
+        return s
+
+    def debug_key(self, g: int) -> np.ndarray:
+        out = np.zeros((self.n_digits, 2, self.n_q + self.n_p, self.n), dtype=np.uint64)
+        _check(self.lib.ckks_debug_key(self._h, g, out.ctypes.data), "ckks_debug_key")
+        return out
+
+    # ---- plaintexts ----
+    def encode(self, z, level: int, scale: float | None = None):
+        z = np.asarray(z, dtype=np.complex128)
+        re = np.ascontiguousarray(z.real)
+        im = np.ascontiguousarray(z.imag)
+        pt = self.new_pt(level)
+        _check(self.lib.ckks_encode(self._h, re.ctypes.data, im.ctypes.data, len(z), level,
+                                    scale or self.default_scale, pt.data_ptr()), "ckks_encode")
+        return pt
+
+    def decode(self, pt, level: int, scale: float, n_slots: int | None = None) -> np.ndarray:
+        n_slots = n_slots or self.n // 2
+        re = np.zeros(n_slots)
+        im = np.zeros(n_slots)
+        _check(self.lib.ckks_decode(self._h, pt.data_ptr(), level, scale, re.ctypes.data, im.ctypes.data,
+                                    n_slots), "ckks_decode")
+        return re + 1j * im
+
+    def pt_from_int(self, m: np.ndarray, level: int):
+        m = np.ascontiguousarray(m, dtype=np.int64)
+        pt = self.new_pt(level)
+        _check(self.lib.ckks_pt_from_int(self._h, m.ctypes.data, level, pt.data_ptr()), "ckks_pt_from_int")
+        return pt
+
+    def ntt(self, data, first_mod: int, inverse: bool = False) -> None:
+        """In-place transform of a [limbs, N] int64 device tensor."""
+        _check(self.lib.ckks_ntt(self._h, data.data_ptr(), int(data.shape[0]), first_mod, int(inverse)),
+               "ckks_ntt")
+
+    # ---- encryption ----
+    def encrypt(self, pt, level: int, scale: float, enc_seed: int, n_limbs: int | None = None) -> Ciphertext:
+        ct = self.new_ct(n_limbs or level + 1, level, scale)
+        h = ct.handle(self.log_n)
+        _check(self.lib.ckks_encrypt(self._h, pt.data_ptr(), level, scale, enc_seed, ctypes.byref(h)),
+               "ckks_encrypt")
+        return ct
+
+    def decrypt(self, ct: Ciphertext):
+        pt = self.new_pt(ct.level)
+        h = ct.handle(self.log_n)
+        _check(self.lib.ckks_decrypt(self._h, ctypes.byref(h), pt.data_ptr()), "ckks_decrypt")
+        return pt
+
+    def decrypt_decode(self, ct: Ciphertext, n_slots: int | None = None) -> np.ndarray:
+        return self.decode(self.decrypt(ct), ct.level, ct.scale, n_slots)
+
+    # ---- evaluation ----
+    def _out_like(self, a: Ciphertext, out: Ciphertext | None) -> Ciphertext:
+        return out if out is not None else self.new_ct(a.level + 1, a.level, a.scale)
+
+    def _binary(self, fn, a: Ciphertext, b: Ciphertext, out: Ciphertext | None, what: str) -> Ciphertext:
+        out = self._out_like(a, out)
+        ha, hb, ho = a.handle(self.log_n), b.handle(self.log_n), out.handle(self.log_n)
+        _check(fn(self._h, ctypes.byref(ha), ctypes.byref(hb), ctypes.byref(ho)), what)
+        out.level, out.scale = ho.level, ho.scale
+        return out
+
+    def add(self, a, b, out=None):
+        return self._binary(self.lib.ckks_add, a, b, out, "ckks_add")
+
+    def sub(self, a, b, out=None):
+        return self._binary(self.lib.ckks_sub, a, b, out, "ckks_sub")
+
+    def mul_relin(self, a, b, out=None):
+        return self._binary(self.lib.ckks_mul_relin, a, b, out, "ckks_mul_relin")
+
+    def mul_plain(self, a: Ciphertext, pt, pt_scale: float, out=None) -> Ciphertext:
+        out = self._out_like(a, out)
+        ha, ho = a.handle(self.log_n), out.handle(self.log_n)
+        _check(self.lib.ckks_mul_plain(self._h, ctypes.byref(ha), pt.data_ptr(), pt_scale, ctypes.byref(ho)),
+               "ckks_mul_plain")
+        out.level, out.scale = ho.level, ho.scale
+        return out
+
+    def add_plain(self, a: Ciphertext, pt, out=None) -> Ciphertext:
+        out = self._out_like(a, out)
+        ha, ho = a.handle(self.log_n), out.handle(self.log_n)
+        _check(self.lib.ckks_add_plain(self._h, ctypes.byref(ha), pt.data_ptr(), ctypes.byref(ho)),
+               "ckks_add_plain")
+        out.level, out.scale = ho.level, ho.scale
+        return out
+
+    def mul_int(self, a: Ciphertext, k: int, out=None) -> Ciphertext:
+        out = self._out_like(a, out)
+        ha, ho = a.handle(self.log_n), out.handle(self.log_n)
+        _check(self.lib.ckks_mul_int(self._h, ctypes.byref(ha), k, ctypes.byref(ho)), "ckks_mul_int")
+        out.level, out.scale = ho.level, ho.scale
+        return out
+
+    def rescale(self, a: Ciphertext) -> Ciphertext:
+        """In place: drops the top prime."""
+        h = a.handle(self.log_n)
+        _check(self.lib.ckks_rescale(self._h, ctypes.byref(h)), "ckks_rescale")
+        a.level, a.scale = h.level, h.scale
+        return a
+
+    def automorph(self, a: Ciphertext, g: int, out=None) -> Ciphertext:
+        out = self._out_like(a, out)
+        ha, ho = a.handle(self.log_n), out.handle(self.log_n)
+        _check(self.lib.ckks_automorph(self._h, ctypes.byref(ha), g, ctypes.byref(ho)), "ckks_automorph")
+        out.level, out.scale = ho.level, ho.scale
+        return out
+
+    def rotate(self, a: Ciphertext, k: int, out=None) -> Ciphertext:
+        out = self._out_like(a, out)
+        ha, ho = a.handle(self.log_n), out.handle(self.log_n)
+        _check(self.lib.ckks_rotate(self._h, ctypes.byref(ha), k, ctypes.byref(ho)), "ckks_rotate")
+        out.level, out.scale = ho.level, ho.scale
+        return out
+
+    def conjugate(self, a: Ciphertext, out=None) -> Ciphertext:
+        out = self._out_like(a, out)
+        ha, ho = a.handle(self.log_n), out.handle(self.log_n)
+        _check(self.lib.ckks_conjugate(self._h, ctypes.byref(ha), ctypes.byref(ho)), "ckks_conjugate")
+        out.level, out.scale = ho.level, ho.scale
+        return out
+
+    # ---- batched ----
+    def _handles(self, cts):
+        arr = (CkksCt * len(cts))()
+        for i, c in enumerate(cts):
+            arr[i] = c.handle(self.log_n)
+        return arr
+
+    def mul_relin_batch(self, a, b, out, rescale: bool = False) -> None:
+        ha, hb, ho = self._handles(a), self._handles(b), self._handles(out)
+        _check(self.lib.ckks_mul_relin_batch(self._h, ha, hb, ho, len(a), int(rescale)), "ckks_mul_relin_batch")
+        for i, c in enumerate(out):
+            c.level, c.scale = ho[i].level, ho[i].scale
+
+    def rotate_batch(self, cts, steps, out) -> None:
+        hi, ho = self._handles(cts), self._handles(out)
+        ks = (ctypes.c_int32 * len(steps))(*steps)
+        _check(self.lib.ckks_rotate_batch(self._h, hi, ks, ho, len(cts)), "ckks_rotate_batch")
+        for i, c in enumerate(out):
+            c.level, c.scale = ho[i].level, ho[i].scale
+
+    def rescale_batch(self, cts) -> None:
+        h = self._handles(cts)
+        _check(self.lib.ckks_rescale_batch(self._h, h, len(cts)), "ckks_rescale_batch")
+        for i, c in enumerate(cts):
+            c.level, c.scale = h[i].level, h[i].scale
+
+    # ---- host exchange ----
+    def export_ct(self, ct: Ciphertext) -> np.ndarray:
+        out = np.zeros((2, ct.level + 1, self.n), dtype=np.uint64)
+        h = ct.handle(self.log_n)
+        _check(self.lib.ckks_ct_export(self._h, ctypes.byref(h), out.ctypes.data), "ckks_ct_export")
+        return out
+
+    def import_ct(self, arr: np.ndarray, level: int, scale: float, n_limbs: int | None = None) -> Ciphertext:
+        arr = np.ascontiguousarray(arr, dtype=np.uint64)
+        ct = self.new_ct(n_limbs or level + 1, level, scale)
+        h = ct.handle(self.log_n)
+        _check(self.lib.ckks_ct_import(self._h, arr.ctypes.data, ctypes.byref(h)), "ckks_ct_import")
+        return ct
+
+
+def tensor_to_u64(t) -> np.ndarray:
+    """Copy a device int64 tensor to host as uint64 (same bits)."""
+    return t.detach().cpu().numpy().view(np.uint64)
+
+
+def u64_to_tensor(a: np.ndarray, device):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64)).to(device)

@@ -1,0 +1,710 @@
+// C ABI entry points (include/ckks.h): context, keys, encryption and the
+// homomorphic operations of ReBoot Sec. 3, orchestrated over the kernels in
+// ntt.cu, ops.cu, keyswitch.cu and encode.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ops.cuh"
+
+// ---------------------------------------------------------------- scratch
+int ensure_scratch(ckks_ctx *c, size_t words) {
+  if (words <= c->scratch_words) return CKKS_OK;
+  CK_CUDA(cudaStreamSynchronize(c->stream));
+  if (c->scratch) cudaFree(c->scratch);
+  c->scratch = nullptr;
+  c->scratch_words = 0;
+  if (cudaMalloc(&c->scratch, words * sizeof(u64)) != cudaSuccess) {
+    cudaGetLastError();
+    return CKKS_E_OOM;
+  }
+  c->scratch_words = words;
+  return CKKS_OK;
+}
+int ensure_fscratch(ckks_ctx *c, size_t words) {
+  if (words <= c->fscratch_words) return CKKS_OK;
+  CK_CUDA(cudaStreamSynchronize(c->stream));
+  if (c->fscratch) cudaFree(c->fscratch);
+  c->fscratch = nullptr;
+  c->fscratch_words = 0;
+  if (cudaMalloc(&c->fscratch, words * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return CKKS_E_OOM;
+  }
+  c->fscratch_words = words;
+  return CKKS_OK;
+}
+
+namespace {
+
+int last_err() { return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_CUDA; }
+u64 *poly1(const ckks_ct *ct, u32 n) { return ct->data + (size_t)ct->n_limbs * n; }
+
+bool ct_ok(const ckks_ctx *c, const ckks_ct *ct) {
+  return ct && ct->data && ct->log_n == (u32)c->log_n && (int)ct->level < c->n_q && ct->n_limbs >= ct->level + 1;
+}
+
+void free_keys(ckks_ctx *c) {
+  if (c->relin.data) cudaFree(c->relin.data);
+  c->relin.data = nullptr;
+  for (auto &kv : c->galois) cudaFree(kv.second.data);
+  c->galois.clear();
+}
+
+size_t key_words(const ckks_ctx *c) { return (size_t)c->n_digits * 2 * (c->n_q + c->n_p) * c->n; }
+
+// Build a switching key from s' (NTT domain over all n_q + n_p moduli) to s
+// (reading C7); key_id 0 = relinearisation, else the Galois element.
+int make_key(ckks_ctx *c, u64 key_id, const u64 *sp_ntt, DevKey *out) {
+  const int ext = c->n_q + c->n_p;
+  const u32 n = c->n;
+  u64 *data = nullptr;
+  if (cudaMalloc(&data, key_words(c) * sizeof(u64)) != cudaSuccess) {
+    cudaGetLastError();
+    return CKKS_E_OOM;
+  }
+  int rc = ensure_scratch(c, (size_t)ext * n + n);
+  if (rc) { cudaFree(data); return rc; }
+  u64 *e_res = c->scratch;
+  i64 *e_dev = reinterpret_cast<i64 *>(c->scratch + (size_t)ext * n);
+  std::vector<i64> e(n);
+  int mods[MAX_MODS];
+  for (int i = 0; i < ext; ++i) mods[i] = i;
+  KeyArgs ka;
+  ka.sp_ntt = sp_ntt;
+  ka.err = e_res;
+  for (int t = 0; t < c->n_q; ++t) {
+    u64 p = 1;
+    for (int k = 0; k < c->n_p; ++k) p = host_mulmod(p, c->mod[c->n_q + k] % c->mod[t], c->mod[t]);
+    ka.p_mod[t] = p;
+  }
+  for (int j = 0; j < c->n_digits; ++j) {
+    sample_gaussian(sm_stream(c->key_seed, TAG_KEY_E, key_id * 256 + j), n, c->sigma, c->e_bound, e.data());
+    CK_CUDA(cudaMemcpyAsync(e_dev, e.data(), sizeof(i64) * n, cudaMemcpyHostToDevice, c->stream));
+    rc = ew_signed_to_res(c, e_dev, e_res, 0, ext);
+    if (rc) break;
+    const u64 *s1[1] = {e_res};
+    u64 *d1[1] = {e_res};
+    rc = launch_ntt(c, s1, d1, 1, ext, mods, false);
+    if (rc) break;
+    ka.key_a = sm_stream(c->key_seed, TAG_KEY_A, key_id * 256 + j);
+    ka.lo = j * c->alpha;
+    ka.hi = std::min((j + 1) * c->alpha, c->n_q);
+    ka.b = data + (size_t)(2 * j) * ext * n;
+    ka.a = data + (size_t)(2 * j + 1) * ext * n;
+    rc = ew_keyrow(c, ka, ext);
+    if (rc) break;
+    // the host error buffer is reused next digit: finish the copy first
+    CK_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  if (rc) { cudaFree(data); return rc; }
+  out->data = data;
+  return CKKS_OK;
+}
+
+int galois_key(ckks_ctx *c, u64 g) {
+  if (!c->have_secret) return CKKS_E_STATE;
+  if ((g & 1) == 0 || g >= 2ULL * c->n) return CKKS_E_PARAM;
+  if (c->galois.count(g)) return CKKS_OK;
+  const int ext = c->n_q + c->n_p;
+  u64 *sp = nullptr;
+  if (cudaMalloc(&sp, (size_t)ext * c->n * sizeof(u64)) != cudaSuccess) {
+    cudaGetLastError();
+    return CKKS_E_OOM;
+  }
+  EwArgs a;
+  a.x0[0] = c->d_s_ntt;
+  a.o0[0] = sp;
+  int rc = ew_automorph(c, a, (u32)g, ext, 1, false);
+  DevKey k;
+  if (!rc) rc = make_key(c, g, sp, &k);
+  cudaStreamSynchronize(c->stream);
+  cudaFree(sp);
+  if (rc) return rc;
+  c->galois[g] = k;
+  return CKKS_OK;
+}
+
+const DevKey *find_galois(const ckks_ctx *c, u64 g) {
+  auto it = c->galois.find(g);
+  return it == c->galois.end() ? nullptr : &it->second;
+}
+
+// in-place rescale of n <= MAX_CTS ciphertexts at one level (reading C10)
+int rescale_chunk(ckks_ctx *c, ckks_ct *cts, int n) {
+  const int level = cts[0].level;
+  const u32 nn = c->n;
+  const size_t per = (size_t)2 * nn + (size_t)2 * level * nn;
+  int rc = ensure_scratch(c, per * n);
+  if (rc) return rc;
+  std::vector<const u64 *> src(2 * n);
+  std::vector<u64 *> dst(2 * n);
+  RescaleArgs r;
+  r.level = level;
+  r.qlinv = c->d_conv + c->conv.rescale_qlinv + 2 * (size_t)level * c->n_q;
+  for (int i = 0; i < n; ++i) {
+    u64 *last = c->scratch + per * i;
+    src[2 * i] = cts[i].data + (size_t)level * nn;
+    src[2 * i + 1] = poly1(&cts[i], nn) + (size_t)level * nn;
+    dst[2 * i] = last;
+    dst[2 * i + 1] = last + nn;
+    r.c0[i] = cts[i].data;
+    r.c1[i] = poly1(&cts[i], nn);
+    r.last[i] = last;
+    r.lift[i] = last + 2 * nn;
+  }
+  int m1[1] = {level};
+  rc = launch_ntt(c, src.data(), dst.data(), 2 * n, 1, m1, true);
+  if (rc) return rc;
+  rc = ew_rescale_lift(c, r, n);
+  if (rc) return rc;
+  std::vector<const u64 *> ls(2 * n);
+  std::vector<u64 *> ld(2 * n);
+  for (int i = 0; i < n; ++i)
+    for (int p = 0; p < 2; ++p) {
+      ld[2 * i + p] = r.lift[i] + (size_t)p * level * nn;
+      ls[2 * i + p] = ld[2 * i + p];
+    }
+  int mods[MAX_MODS];
+  for (int l = 0; l < level; ++l) mods[l] = l;
+  rc = launch_ntt(c, ls.data(), ld.data(), 2 * n, level, mods, false);
+  if (rc) return rc;
+  rc = ew_rescale_finish(c, r, n);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) {
+    cts[i].scale /= (double)c->mod[level];
+    cts[i].level = level - 1;
+  }
+  return CKKS_OK;
+}
+
+int mul_relin_chunk(ckks_ctx *c, const ckks_ct *a, const ckks_ct *b, ckks_ct *out, int n) {
+  const int level = a[0].level, nl = level + 1;
+  const u32 nn = c->n;
+  if (!c->relin.data) return CKKS_E_NOKEY;
+  const size_t d2w = (size_t)nl * nn * n;
+  int rc = ensure_scratch(c, d2w + ks_ws_words(c, level, n));
+  if (rc) return rc;
+  std::vector<u64 *> d2(n);
+  EwArgs e;
+  for (int i = 0; i < n; ++i) {
+    d2[i] = c->scratch + (size_t)nl * nn * i;
+    e.x0[i] = a[i].data;
+    e.x1[i] = poly1(&a[i], nn);
+    e.y0[i] = b[i].data;
+    e.y1[i] = poly1(&b[i], nn);
+    e.o0[i] = out[i].data;
+    e.o1[i] = poly1(&out[i], nn);
+  }
+  rc = ew_tensor(c, e, d2.data(), nl, n);
+  if (rc) return rc;
+  std::vector<const u64 *> dd(n), keys(n), b0(n), b1(n);
+  std::vector<u64 *> o0(n), o1(n);
+  for (int i = 0; i < n; ++i) {
+    dd[i] = d2[i];
+    keys[i] = c->relin.data;
+    b0[i] = e.o0[i];
+    b1[i] = e.o1[i];
+    o0[i] = e.o0[i];
+    o1[i] = e.o1[i];
+  }
+  const double sa = a[0].scale;
+  std::vector<double> scales(n);
+  for (int i = 0; i < n; ++i) scales[i] = a[i].scale * b[i].scale;
+  rc = ks_batch(c, level, n, dd.data(), keys.data(), b0.data(), b1.data(), o0.data(), o1.data(),
+                c->scratch + d2w);
+  if (rc) return rc;
+  (void)sa;
+  for (int i = 0; i < n; ++i) {
+    out[i].level = level;
+    out[i].scale = scales[i];
+    out[i].is_ntt = 1;
+    out[i].log_n = c->log_n;
+  }
+  return CKKS_OK;
+}
+
+// out[i] = sigma_{g[i]}(in[i]) followed by key switching (reading C11)
+int automorph_chunk(ckks_ctx *c, const ckks_ct *in, const u64 *g, ckks_ct *out, int n) {
+  const int level = in[0].level, nl = level + 1;
+  const u32 nn = c->n;
+  std::vector<const u64 *> keys(n);
+  for (int i = 0; i < n; ++i) {
+    const DevKey *k = find_galois(c, g[i]);
+    if (!k) return CKKS_E_NOKEY;
+    keys[i] = k->data;
+  }
+  const size_t tw = (size_t)2 * nl * nn * n;
+  int rc = ensure_scratch(c, tw + ks_ws_words(c, level, n));
+  if (rc) return rc;
+  std::vector<const u64 *> t1(n), t0(n);
+  std::vector<u64 *> o0(n), o1(n);
+  for (int i = 0; i < n; ++i) {
+    u64 *tmp = c->scratch + (size_t)2 * nl * nn * i;
+    EwArgs e;
+    e.x0[0] = in[i].data;
+    e.x1[0] = poly1(&in[i], nn);
+    e.o0[0] = tmp;
+    e.o1[0] = tmp + (size_t)nl * nn;
+    rc = ew_automorph(c, e, (u32)g[i], nl, 1, true);
+    if (rc) return rc;
+    t0[i] = tmp;
+    t1[i] = tmp + (size_t)nl * nn;
+    o0[i] = out[i].data;
+    o1[i] = poly1(&out[i], nn);
+  }
+  std::vector<double> scales(n);
+  for (int i = 0; i < n; ++i) scales[i] = in[i].scale;
+  rc = ks_batch(c, level, n, t1.data(), keys.data(), t0.data(), nullptr, o0.data(), o1.data(),
+                c->scratch + tw);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) {
+    out[i].level = level;
+    out[i].scale = scales[i];
+    out[i].is_ntt = 1;
+    out[i].log_n = c->log_n;
+  }
+  return CKKS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ckks_status_str(int s) {
+  switch (s) {
+    case CKKS_OK: return "ok";
+    case CKKS_E_PARAM: return "invalid argument or parameter set";
+    case CKKS_E_LEVEL: return "level mismatch or out of range";
+    case CKKS_E_SCALE: return "scale out of range";
+    case CKKS_E_NOKEY: return "required key missing";
+    case CKKS_E_OOM: return "out of memory";
+    case CKKS_E_CUDA: return "CUDA runtime error";
+    case CKKS_E_TIMEOUT: return "bounded device wait expired";
+    case CKKS_E_STATE: return "call made in the wrong state";
+    default: return "unknown status";
+  }
+}
+
+int ckks_ctx_create(const ckks_params *p, void *stream, ckks_ctx **out) {
+  if (!p || !out) return CKKS_E_PARAM;
+  *out = nullptr;
+  if (p->log_n < 12 || p->log_n > 16 || p->n_q < 1 || p->n_q > CKKS_MAX_Q || p->n_p < 1 ||
+      p->n_p > CKKS_MAX_P || p->dnum < 1 || p->n_q + p->n_p > MAX_MODS || p->h < 1 ||
+      p->h > (1u << p->log_n) || !(p->sigma > 0))
+    return CKKS_E_PARAM;
+  ckks_ctx *c = new (std::nothrow) ckks_ctx();
+  if (!c) return CKKS_E_OOM;
+  cudaGetDevice(&c->device);
+  c->stream = (cudaStream_t)stream;
+  c->log_n = p->log_n;
+  c->n = 1u << p->log_n;
+  c->n_q = p->n_q;
+  c->n_p = p->n_p;
+  c->dnum = p->dnum;
+  c->alpha = (c->n_q + c->dnum - 1) / c->dnum;
+  c->n_digits = (c->n_q + c->alpha - 1) / c->alpha;
+  c->h = p->h;
+  c->sigma = p->sigma;
+  c->e_bound = (i64)std::floor(6.0 * p->sigma);
+  c->default_scale = std::ldexp(1.0, 0) * std::pow(2.0, p->log2_scale);
+  if (c->alpha > 16 || c->n_p > 16 || c->n_digits > 8) { delete c; return CKKS_E_PARAM; }
+  unsigned bits[MAX_MODS];
+  for (int i = 0; i < c->n_q; ++i) bits[i] = p->q_bits[i];
+  for (int i = 0; i < c->n_p; ++i) bits[c->n_q + i] = p->p_bits[i];
+  if (host_gen_primes(c->n_q + c->n_p, bits, c->mod) != CKKS_OK) { delete c; return CKKS_E_PARAM; }
+  for (int i = 0; i < c->n_q + c->n_p; ++i) c->psi[i] = host_find_psi(c->mod[i], c->n);
+  int rc = build_tables(c);
+  if (rc) { ckks_ctx_destroy(c); return rc; }
+  *out = c;
+  return CKKS_OK;
+}
+
+int ckks_ctx_destroy(ckks_ctx *c) {
+  if (!c) return CKKS_E_PARAM;
+  cudaStreamSynchronize(c->stream);
+  free_keys(c);
+  cudaFree(c->d_mods);
+  cudaFree(c->d_tw_fwd);
+  cudaFree(c->d_tw_inv);
+  cudaFree(c->d_conv);
+  cudaFree(c->d_s_ntt);
+  cudaFree(c->scratch);
+  cudaFree(c->fscratch);
+  if (c->pinned) cudaFreeHost(c->pinned);
+  delete c;
+  return CKKS_OK;
+}
+
+int ckks_ctx_set_stream(ckks_ctx *c, void *stream) {
+  if (!c) return CKKS_E_PARAM;
+  c->stream = (cudaStream_t)stream;
+  return CKKS_OK;
+}
+
+int ckks_ctx_moduli(const ckks_ctx *c, uint64_t *out, int cap) {
+  if (!c || !out) return CKKS_E_PARAM;
+  const int m = std::min(cap, c->n_q + c->n_p);
+  for (int i = 0; i < m; ++i) out[i] = c->mod[i];
+  return m;
+}
+
+int ckks_ctx_roots(const ckks_ctx *c, uint64_t *out, int cap) {
+  if (!c || !out) return CKKS_E_PARAM;
+  const int m = std::min(cap, c->n_q + c->n_p);
+  for (int i = 0; i < m; ++i) out[i] = c->psi[i];
+  return m;
+}
+
+int ckks_ctx_digits(const ckks_ctx *c, int *n_digits, int *alpha) {
+  if (!c) return CKKS_E_PARAM;
+  if (n_digits) *n_digits = c->n_digits;
+  if (alpha) *alpha = c->alpha;
+  return CKKS_OK;
+}
+
+int ckks_ctx_device_bytes(const ckks_ctx *c, uint64_t *bytes) {
+  if (!c || !bytes) return CKKS_E_PARAM;
+  size_t b = c->table_bytes + c->scratch_words * 8 + c->fscratch_words * 8;
+  if (c->d_s_ntt) b += (size_t)(c->n_q + c->n_p) * c->n * 8;
+  if (c->relin.data) b += key_words(c) * 8;
+  b += c->galois.size() * key_words(c) * 8;
+  *bytes = b;
+  return CKKS_OK;
+}
+
+uint64_t ckks_galois_elt(const ckks_ctx *c, int32_t k) {
+  const i64 half = c->n / 2;
+  const i64 r = ((k % half) + half) % half;
+  return host_powmod(5, (u64)r, 2ULL * c->n);
+}
+
+int ckks_keygen_from_seed(ckks_ctx *c, uint64_t seed, const int32_t *rot, int n_rot, int want_conj,
+                          int want_boot) {
+  if (!c || n_rot < 0 || (n_rot > 0 && !rot)) return CKKS_E_PARAM;
+  if (want_boot) return CKKS_E_STATE;  // the bootstrapping key set is not part of this build
+  CK_CUDA(cudaStreamSynchronize(c->stream));
+  free_keys(c);
+  const int ext = c->n_q + c->n_p;
+  const u32 n = c->n;
+  c->key_seed = seed;
+  c->s_host.assign(n, 0);
+  sample_secret(seed, n, c->h, c->s_host.data());
+  if (!c->d_s_ntt && cudaMalloc(&c->d_s_ntt, (size_t)ext * n * sizeof(u64)) != cudaSuccess) {
+    cudaGetLastError();
+    return CKKS_E_OOM;
+  }
+  int rc = ensure_scratch(c, n);
+  if (rc) return rc;
+  std::vector<i64> s64(n);
+  for (u32 i = 0; i < n; ++i) s64[i] = c->s_host[i];
+  i64 *s_dev = reinterpret_cast<i64 *>(c->scratch);
+  CK_CUDA(cudaMemcpyAsync(s_dev, s64.data(), sizeof(i64) * n, cudaMemcpyHostToDevice, c->stream));
+  rc = ew_signed_to_res(c, s_dev, c->d_s_ntt, 0, ext);
+  if (rc) return rc;
+  int mods[MAX_MODS];
+  for (int i = 0; i < ext; ++i) mods[i] = i;
+  const u64 *s1[1] = {c->d_s_ntt};
+  u64 *d1[1] = {c->d_s_ntt};
+  rc = launch_ntt(c, s1, d1, 1, ext, mods, false);
+  if (rc) return rc;
+  CK_CUDA(cudaStreamSynchronize(c->stream));
+  c->have_secret = true;
+  // relinearisation key: s' = s^2
+  u64 *s2 = nullptr;
+  if (cudaMalloc(&s2, (size_t)ext * n * sizeof(u64)) != cudaSuccess) {
+    cudaGetLastError();
+    return CKKS_E_OOM;
+  }
+  rc = ew_square(c, s2, c->d_s_ntt, ext);
+  if (!rc) rc = make_key(c, 0, s2, &c->relin);
+  cudaStreamSynchronize(c->stream);
+  cudaFree(s2);
+  if (rc) return rc;
+  for (int i = 0; i < n_rot; ++i) {
+    rc = galois_key(c, ckks_galois_elt(c, rot[i]));
+    if (rc) return rc;
+  }
+  if (want_conj) {
+    rc = galois_key(c, 2ULL * n - 1);
+    if (rc) return rc;
+  }
+  CK_CUDA(cudaStreamSynchronize(c->stream));
+  return CKKS_OK;
+}
+
+int ckks_keygen_galois(ckks_ctx *c, uint64_t g) {
+  if (!c) return CKKS_E_PARAM;
+  int rc = galois_key(c, g);
+  if (rc) return rc;
+  CK_CUDA(cudaStreamSynchronize(c->stream));
+  return CKKS_OK;
+}
+
+int ckks_debug_secret(const ckks_ctx *c, int8_t *out) {
+  if (!c || !out) return CKKS_E_PARAM;
+  if (!c->have_secret) return CKKS_E_STATE;
+  std::memcpy(out, c->s_host.data(), c->n);
+  return CKKS_OK;
+}
+
+int ckks_debug_key(const ckks_ctx *c, uint64_t g, uint64_t *out) {
+  if (!c || !out) return CKKS_E_PARAM;
+  const DevKey *k = g == 0 ? (c->relin.data ? &c->relin : nullptr) : find_galois(c, g);
+  if (!k) return CKKS_E_NOKEY;
+  CK_CUDA(cudaStreamSynchronize(c->stream));
+  CK_CUDA(cudaMemcpy(out, k->data, key_words(c) * sizeof(u64), cudaMemcpyDeviceToHost));
+  return CKKS_OK;
+}
+
+int ckks_pt_from_int(ckks_ctx *c, const int64_t *m, uint32_t level, uint64_t *pt) {
+  if (!c || !m || !pt) return CKKS_E_PARAM;
+  if ((int)level >= c->n_q) return CKKS_E_LEVEL;
+  const u32 n = c->n;
+  int rc = ensure_scratch(c, n);
+  if (rc) return rc;
+  i64 *dv = reinterpret_cast<i64 *>(c->scratch);
+  CK_CUDA(cudaMemcpyAsync(dv, m, sizeof(i64) * n, cudaMemcpyHostToDevice, c->stream));
+  rc = ew_signed_to_res(c, dv, pt, 0, level + 1);
+  if (rc) return rc;
+  int mods[MAX_MODS];
+  for (u32 l = 0; l <= level; ++l) mods[l] = l;
+  const u64 *s1[1] = {pt};
+  u64 *d1[1] = {pt};
+  rc = launch_ntt(c, s1, d1, 1, level + 1, mods, false);
+  if (rc) return rc;
+  CK_CUDA(cudaStreamSynchronize(c->stream));
+  return CKKS_OK;
+}
+
+int ckks_ntt(ckks_ctx *c, uint64_t *data, uint32_t n_limbs, uint32_t first_mod, int inverse) {
+  if (!c || !data || n_limbs == 0 || first_mod + n_limbs > (u32)(c->n_q + c->n_p)) return CKKS_E_PARAM;
+  int mods[MAX_MODS];
+  for (u32 l = 0; l < n_limbs; ++l) mods[l] = first_mod + l;
+  const u64 *s1[1] = {data};
+  u64 *d1[1] = {data};
+  return launch_ntt(c, s1, d1, 1, n_limbs, mods, inverse != 0);
+}
+
+int ckks_encrypt(ckks_ctx *c, const uint64_t *pt, uint32_t level, double scale, uint64_t enc_seed,
+                 ckks_ct *out) {
+  if (!c || !pt || !out || !out->data) return CKKS_E_PARAM;
+  if (!c->have_secret) return CKKS_E_NOKEY;
+  if ((int)level >= c->n_q || out->n_limbs < level + 1) return CKKS_E_LEVEL;
+  const u32 n = c->n;
+  const int nl = level + 1;
+  int rc = ensure_scratch(c, (size_t)nl * n + n);
+  if (rc) return rc;
+  u64 *e_res = c->scratch;
+  i64 *e_dev = reinterpret_cast<i64 *>(c->scratch + (size_t)nl * n);
+  std::vector<i64> e(n);
+  sample_gaussian(sm_stream(enc_seed, TAG_ENC_E, 0), n, c->sigma, c->e_bound, e.data());
+  CK_CUDA(cudaMemcpyAsync(e_dev, e.data(), sizeof(i64) * n, cudaMemcpyHostToDevice, c->stream));
+  rc = ew_signed_to_res(c, e_dev, e_res, 0, nl);
+  if (rc) return rc;
+  int mods[MAX_MODS];
+  for (int l = 0; l < nl; ++l) mods[l] = l;
+  const u64 *s1[1] = {e_res};
+  u64 *d1[1] = {e_res};
+  rc = launch_ntt(c, s1, d1, 1, nl, mods, false);
+  if (rc) return rc;
+  EncArgs ea;
+  ea.key_a[0] = sm_stream(enc_seed, TAG_ENC_A, 0);
+  ea.pt[0] = pt;
+  ea.err[0] = e_res;
+  ea.c0[0] = out->data;
+  ea.c1[0] = poly1(out, n);
+  rc = ew_encrypt(c, ea, nl, 1);
+  if (rc) return rc;
+  out->level = level;
+  out->scale = scale;
+  out->is_ntt = 1;
+  out->log_n = c->log_n;
+  CK_CUDA(cudaStreamSynchronize(c->stream));
+  return CKKS_OK;
+}
+
+int ckks_decrypt(ckks_ctx *c, const ckks_ct *ct, uint64_t *pt) {
+  if (!c || !pt || !ct_ok(c, ct)) return CKKS_E_PARAM;
+  if (!c->have_secret) return CKKS_E_NOKEY;
+  EwArgs a;
+  a.x0[0] = ct->data;
+  a.x1[0] = poly1(ct, c->n);
+  a.o0[0] = pt;
+  return ew_decrypt(c, a, ct->level + 1, 1);
+}
+
+int ckks_add(ckks_ctx *c, const ckks_ct *a, const ckks_ct *b, ckks_ct *out) {
+  if (!c || !ct_ok(c, a) || !ct_ok(c, b) || !out || !out->data) return CKKS_E_PARAM;
+  if (a->level != b->level || out->n_limbs < a->level + 1) return CKKS_E_LEVEL;
+  EwArgs e;
+  e.x0[0] = a->data; e.x1[0] = poly1(a, c->n);
+  e.y0[0] = b->data; e.y1[0] = poly1(b, c->n);
+  e.o0[0] = out->data; e.o1[0] = poly1(out, c->n);
+  const double s = a->scale;
+  const u32 lv = a->level;
+  int rc = ew_addsub(c, e, lv + 1, 1, false);
+  if (rc) return rc;
+  out->level = lv; out->scale = s; out->is_ntt = 1; out->log_n = c->log_n;
+  return CKKS_OK;
+}
+
+int ckks_sub(ckks_ctx *c, const ckks_ct *a, const ckks_ct *b, ckks_ct *out) {
+  if (!c || !ct_ok(c, a) || !ct_ok(c, b) || !out || !out->data) return CKKS_E_PARAM;
+  if (a->level != b->level || out->n_limbs < a->level + 1) return CKKS_E_LEVEL;
+  EwArgs e;
+  e.x0[0] = a->data; e.x1[0] = poly1(a, c->n);
+  e.y0[0] = b->data; e.y1[0] = poly1(b, c->n);
+  e.o0[0] = out->data; e.o1[0] = poly1(out, c->n);
+  const double s = a->scale;
+  const u32 lv = a->level;
+  int rc = ew_addsub(c, e, lv + 1, 1, true);
+  if (rc) return rc;
+  out->level = lv; out->scale = s; out->is_ntt = 1; out->log_n = c->log_n;
+  return CKKS_OK;
+}
+
+int ckks_mul_plain(ckks_ctx *c, const ckks_ct *a, const uint64_t *pt, double pt_scale, ckks_ct *out) {
+  if (!c || !ct_ok(c, a) || !pt || !out || !out->data) return CKKS_E_PARAM;
+  if (out->n_limbs < a->level + 1) return CKKS_E_LEVEL;
+  EwArgs e;
+  e.x0[0] = a->data; e.x1[0] = poly1(a, c->n);
+  e.y0[0] = pt;
+  e.o0[0] = out->data; e.o1[0] = poly1(out, c->n);
+  const double s = a->scale * pt_scale;
+  const u32 lv = a->level;
+  int rc = ew_plain(c, e, lv + 1, 1, 0);
+  if (rc) return rc;
+  out->level = lv; out->scale = s; out->is_ntt = 1; out->log_n = c->log_n;
+  return CKKS_OK;
+}
+
+int ckks_add_plain(ckks_ctx *c, const ckks_ct *a, const uint64_t *pt, ckks_ct *out) {
+  if (!c || !ct_ok(c, a) || !pt || !out || !out->data) return CKKS_E_PARAM;
+  if (out->n_limbs < a->level + 1) return CKKS_E_LEVEL;
+  EwArgs e;
+  e.x0[0] = a->data; e.x1[0] = poly1(a, c->n);
+  e.y0[0] = pt;
+  e.o0[0] = out->data; e.o1[0] = poly1(out, c->n);
+  const double s = a->scale;
+  const u32 lv = a->level;
+  int rc = ew_plain(c, e, lv + 1, 1, 1);
+  if (rc) return rc;
+  out->level = lv; out->scale = s; out->is_ntt = 1; out->log_n = c->log_n;
+  return CKKS_OK;
+}
+
+int ckks_mul_int(ckks_ctx *c, const ckks_ct *a, int64_t k, ckks_ct *out) {
+  if (!c || !ct_ok(c, a) || !out || !out->data) return CKKS_E_PARAM;
+  if (out->n_limbs < a->level + 1) return CKKS_E_LEVEL;
+  EwArgs e;
+  e.x0[0] = a->data; e.x1[0] = poly1(a, c->n);
+  e.o0[0] = out->data; e.o1[0] = poly1(out, c->n);
+  const double s = a->scale;
+  const u32 lv = a->level;
+  int rc = ew_mul_int(c, e, lv + 1, 1, k);
+  if (rc) return rc;
+  out->level = lv; out->scale = s; out->is_ntt = 1; out->log_n = c->log_n;
+  return CKKS_OK;
+}
+
+int ckks_mul_relin_batch(ckks_ctx *c, const ckks_ct *a, const ckks_ct *b, ckks_ct *out, int n,
+                         int do_rescale) {
+  if (!c || !a || !b || !out || n < 0) return CKKS_E_PARAM;
+  if (n == 0) return CKKS_OK;
+  const u32 level = a[0].level;
+  for (int i = 0; i < n; ++i) {
+    if (!ct_ok(c, &a[i]) || !ct_ok(c, &b[i]) || !out[i].data) return CKKS_E_PARAM;
+    if (a[i].level != level || b[i].level != level || out[i].n_limbs < level + 1) return CKKS_E_LEVEL;
+  }
+  if (do_rescale && level == 0) return CKKS_E_LEVEL;
+  for (int i0 = 0; i0 < n; i0 += MAX_CTS) {
+    const int cnt = std::min(MAX_CTS, n - i0);
+    int rc = mul_relin_chunk(c, a + i0, b + i0, out + i0, cnt);
+    if (rc) return rc;
+    if (do_rescale) {
+      rc = rescale_chunk(c, out + i0, cnt);
+      if (rc) return rc;
+    }
+  }
+  return last_err();
+}
+
+int ckks_mul_relin(ckks_ctx *c, const ckks_ct *a, const ckks_ct *b, ckks_ct *out) {
+  return ckks_mul_relin_batch(c, a, b, out, 1, 0);
+}
+
+int ckks_rescale_batch(ckks_ctx *c, ckks_ct *cts, int n) {
+  if (!c || !cts || n < 0) return CKKS_E_PARAM;
+  if (n == 0) return CKKS_OK;
+  const u32 level = cts[0].level;
+  for (int i = 0; i < n; ++i) {
+    if (!ct_ok(c, &cts[i])) return CKKS_E_PARAM;
+    if (cts[i].level != level) return CKKS_E_LEVEL;
+  }
+  if (level == 0) return CKKS_E_LEVEL;
+  for (int i0 = 0; i0 < n; i0 += MAX_CTS) {
+    int rc = rescale_chunk(c, cts + i0, std::min(MAX_CTS, n - i0));
+    if (rc) return rc;
+  }
+  return CKKS_OK;
+}
+
+int ckks_rescale(ckks_ctx *c, ckks_ct *ct) { return ckks_rescale_batch(c, ct, 1); }
+
+int ckks_automorph(ckks_ctx *c, const ckks_ct *a, uint64_t g, ckks_ct *out) {
+  if (!c || !ct_ok(c, a) || !out || !out->data) return CKKS_E_PARAM;
+  if (out->n_limbs < a->level + 1) return CKKS_E_LEVEL;
+  u64 gg = g;
+  return automorph_chunk(c, a, &gg, out, 1);
+}
+
+int ckks_rotate(ckks_ctx *c, const ckks_ct *a, int32_t k, ckks_ct *out) {
+  if (!c) return CKKS_E_PARAM;
+  return ckks_automorph(c, a, ckks_galois_elt(c, k), out);
+}
+
+int ckks_conjugate(ckks_ctx *c, const ckks_ct *a, ckks_ct *out) {
+  if (!c) return CKKS_E_PARAM;
+  return ckks_automorph(c, a, 2ULL * c->n - 1, out);
+}
+
+int ckks_rotate_batch(ckks_ctx *c, const ckks_ct *in, const int32_t *k, ckks_ct *out, int n) {
+  if (!c || !in || !k || !out || n < 0) return CKKS_E_PARAM;
+  if (n == 0) return CKKS_OK;
+  const u32 level = in[0].level;
+  for (int i = 0; i < n; ++i) {
+    if (!ct_ok(c, &in[i]) || !out[i].data) return CKKS_E_PARAM;
+    if (in[i].level != level || out[i].n_limbs < level + 1) return CKKS_E_LEVEL;
+  }
+  for (int i0 = 0; i0 < n; i0 += MAX_CTS) {
+    const int cnt = std::min(MAX_CTS, n - i0);
+    std::vector<u64> g(cnt);
+    for (int i = 0; i < cnt; ++i) g[i] = ckks_galois_elt(c, k[i0 + i]);
+    int rc = automorph_chunk(c, in + i0, g.data(), out + i0, cnt);
+    if (rc) return rc;
+  }
+  return CKKS_OK;
+}
+
+int ckks_ct_export(ckks_ctx *c, const ckks_ct *ct, uint64_t *out) {
+  if (!c || !ct_ok(c, ct) || !out) return CKKS_E_PARAM;
+  const size_t w = (size_t)(ct->level + 1) * c->n;
+  CK_CUDA(cudaMemcpyAsync(out, ct->data, w * 8, cudaMemcpyDeviceToHost, c->stream));
+  CK_CUDA(cudaMemcpyAsync(out + w, poly1(ct, c->n), w * 8, cudaMemcpyDeviceToHost, c->stream));
+  CK_CUDA(cudaStreamSynchronize(c->stream));
+  return CKKS_OK;
+}
+
+int ckks_ct_import(ckks_ctx *c, const uint64_t *in, ckks_ct *ct) {
+  if (!c || !ct_ok(c, ct) || !in) return CKKS_E_PARAM;
+  const size_t w = (size_t)(ct->level + 1) * c->n;
+  CK_CUDA(cudaMemcpyAsync(ct->data, in, w * 8, cudaMemcpyHostToDevice, c->stream));
+  CK_CUDA(cudaMemcpyAsync(poly1(ct, c->n), in + w, w * 8, cudaMemcpyHostToDevice, c->stream));
+  CK_CUDA(cudaStreamSynchronize(c->stream));
+  return CKKS_OK;
+}
+
+}  // extern "C"

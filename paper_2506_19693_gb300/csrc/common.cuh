@@ -1,0 +1,75 @@
+// Shared device/host definitions of the GB300 RNS-CKKS core.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ckks.h"
+
+typedef uint64_t u64;
+typedef int64_t i64;
+typedef uint32_t u32;
+
+#define MAX_MODS 80            // q's + p's
+#define MAX_POLYS 256          // polynomials per launch (pointer arrays in kernel params)
+
+// Per-modulus constants, read by every kernel through a device pointer.
+struct ModInfo {
+  u64 q;          // the prime (< 2^62)
+  u64 twoq;       // 2q
+  u64 r64;        // 2^64 mod q
+  u64 r64_s;      // Shoup companion floor(r64 * 2^64 / q)
+  u64 one_s;      // floor(2^64 / q): Shoup companion of 1
+  u64 ninv;       // N^-1 mod q
+  u64 ninv_s;
+  u64 pad;
+};
+
+#if defined(__CUDACC__)
+// ---------------------------------------------------------------------------
+// Modular arithmetic (q < 2^62).
+// Shoup: for constant w < q with w_s = floor(w 2^64 / q), any x < 2^64:
+//   w x - floor(w_s x / 2^64) q  lies in [0, 2q).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ u64 shoup_lazy(u64 x, u64 w, u64 w_s, u64 q) {
+  return w * x - __umul64hi(w_s, x) * q;
+}
+__device__ __forceinline__ u64 csub(u64 x, u64 q) { return x >= q ? x - q : x; }
+__device__ __forceinline__ u64 shoup(u64 x, u64 w, u64 w_s, u64 q) {
+  return csub(shoup_lazy(x, w, w_s, q), q);
+}
+// Reduce the 128-bit value hi * 2^64 + lo mod q:
+// hi * (2^64 mod q) via Shoup and lo * 1 via Shoup, each in [0, 2q); sum < 4q.
+__device__ __forceinline__ u64 reduce128(u64 hi, u64 lo, const ModInfo &m) {
+  u64 a = shoup_lazy(hi, m.r64, m.r64_s, m.q);
+  u64 b = lo - __umul64hi(m.one_s, lo) * m.q;
+  u64 r = a + b;
+  r = csub(r, m.twoq);
+  return csub(r, m.q);
+}
+__device__ __forceinline__ u64 mulmod(u64 a, u64 b, const ModInfo &m) {
+  return reduce128(__umul64hi(a, b), a * b, m);
+}
+// 128-bit multiply-accumulate
+__device__ __forceinline__ void mac128(u64 &hi, u64 &lo, u64 a, u64 b) {
+  u64 pl = a * b, ph = __umul64hi(a, b);
+  lo += pl;
+  hi += ph + (lo < pl ? 1 : 0);
+}
+__device__ __forceinline__ u64 addmod(u64 a, u64 b, u64 q) { return csub(a + b, q); }
+__device__ __forceinline__ u64 submod(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
+#endif  // __CUDACC__
+
+// Host-side error helper
+#define CK_CUDA(call)                                 \
+  do {                                                \
+    cudaError_t _e = (call);                          \
+    if (_e != cudaSuccess) return CKKS_E_CUDA;        \
+  } while (0)
+
+struct PolyPtrs {
+  u64 *p[MAX_POLYS];
+};
+struct CPolyPtrs {
+  const u64 *p[MAX_POLYS];
+};

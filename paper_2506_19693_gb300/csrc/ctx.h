@@ -1,0 +1,115 @@
+// Internal (host-side) context of the GB300 RNS-CKKS core.
+#pragma once
+
+#include <map>
+#include <vector>
+
+#include "common.cuh"
+
+// A Galois or relinearisation key resident in HBM:
+// uint64[n_digits][2][n_q + n_p][N] (b_j, a_j), NTT domain.
+struct DevKey {
+  u64 *data = nullptr;
+};
+
+// Per-level basis-conversion constants for ModUp of digit j at level l and for
+// ModDown / rescale.  All live in one device buffer; these are host offsets.
+struct ConvTables {
+  // ModUp(level l, digit j): source limbs [lo, hi), hi <= l+1.
+  //   qhat_inv[i], qhat_inv_s[i]        (i < hi-lo)      : [Qhat_i^-1]_{q_i} and Shoup
+  //   qhat_mod[t * n_src + i]                             : Qhat_i mod target t
+  // targets t enumerate (q_0..q_l minus [lo,hi)) then p_0..p_{K-1}.
+  std::vector<size_t> modup_off;   // index l * n_digits + j -> offset (u64 words)
+  // ModDown to level l: phat_inv[k] (Shoup pair), phat_mod[i * K + k], pinv[i] (Shoup pair)
+  size_t moddown_phat_inv = 0;     // [K] pairs
+  size_t moddown_phat_mod = 0;     // [n_q][K]
+  size_t moddown_pinv = 0;         // [n_q] pairs
+  // rescale from level l: qlinv[l * n_q + i] (Shoup pair) = q_l^-1 mod q_i
+  size_t rescale_qlinv = 0;
+  // decode: Garner constants inv(q_j) mod q_i  [n_q][n_q] and half-Q digits per level
+  size_t garner_inv = 0;
+  size_t halfq_digits = 0;         // [n_q][n_q]: digits of (Q_l - 1)/2 for level l
+  size_t total = 0;
+};
+
+struct ckks_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int log_n = 0;
+  u32 n = 0;
+  int n_q = 0, n_p = 0, dnum = 0, alpha = 0, n_digits = 0, h = 0;
+  double sigma = 3.2, default_scale = 1.0;
+  i64 e_bound = 19;
+  u64 mod[MAX_MODS] = {0};
+  u64 psi[MAX_MODS] = {0};
+
+  // device tables
+  ModInfo *d_mods = nullptr;         // [n_q + n_p]
+  ulonglong2 *d_tw_fwd = nullptr;    // [n_q + n_p][N]: (psi^brv(k), Shoup)
+  ulonglong2 *d_tw_inv = nullptr;    // [n_q + n_p][N]: (psi^-brv(k), Shoup)
+  u64 *d_conv = nullptr;             // ConvTables payload
+  ConvTables conv;
+  std::vector<u64> h_conv;           // host copy of the payload
+
+  // secret
+  bool have_secret = false;
+  std::vector<int8_t> s_host;        // [N]
+  u64 *d_s_ntt = nullptr;            // [n_q + n_p][N]
+  u64 key_seed = 0;
+  DevKey relin;
+  std::map<u64, DevKey> galois;
+
+  // scratch (grown on demand, owned)
+  u64 *scratch = nullptr;
+  size_t scratch_words = 0;
+  double *fscratch = nullptr;
+  size_t fscratch_words = 0;
+  void *pinned = nullptr;            // pinned host staging
+  size_t pinned_bytes = 0;
+  size_t table_bytes = 0;
+
+  size_t limb_words() const { return (size_t)n; }
+  int ext_limbs(int level) const { return level + 1 + n_p; }
+  // index into the key's limb axis for extended-basis position t at level l
+  int key_limb(int level, int t) const { return t <= level ? t : n_q + (t - level - 1); }
+  // modulus index of extended-basis position t at level l
+  int ext_mod(int level, int t) const { return t <= level ? t : n_q + (t - level - 1); }
+};
+
+// ---- host parameter derivation (params_host.cpp) ----
+int host_gen_primes(int count, const unsigned *bits, u64 *out);
+u64 host_find_psi(u64 q, u64 n);
+u64 host_powmod(u64 b, u64 e, u64 q);
+u64 host_mulmod(u64 a, u64 b, u64 q);
+u64 host_invmod(u64 a, u64 q);
+u64 host_shoup(u64 w, u64 q);
+u64 host_bitrev(u64 x, int bits);
+int build_tables(ckks_ctx *c);
+
+// ---- host sampling (sampling_host.cpp) ----
+u64 sm_draw(u64 key, u64 ctr);
+u64 sm_stream(u64 seed, u64 tag, u64 idx);
+enum { TAG_SECRET = 1, TAG_KEY_A = 2, TAG_KEY_E = 3, TAG_ENC_A = 4, TAG_ENC_E = 5 };
+void sample_secret(u64 seed, u32 n, int h, int8_t *s);
+void sample_gaussian(u64 key, u32 n, double sigma, i64 bound, i64 *e);
+u64 sample_uniform(u64 key, u64 idx, u64 q);
+
+// ---- scratch ----
+int ensure_scratch(ckks_ctx *c, size_t words);
+int ensure_fscratch(ckks_ctx *c, size_t words);
+
+// ---- NTT launchers (ntt.cu) ----
+// Transform `npoly` polynomials of `nl` limbs each.  Limb l of poly p is at
+// src.p[p] + l*N (read) and dst.p[p] + l*N (written); its modulus index is
+// mods[l].  src may equal dst.
+int launch_ntt(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, int nl,
+               const int *mods, bool inverse);
+
+// ---- element-wise and key-switch launchers (ops.cu / keyswitch.cu) ----
+// Key switching of np <= 128 NTT-domain polynomials at `level`, one key per
+// polynomial: o_c = base_c + u_c (base may be null) with u0 + u1 s ~ d s'.
+// ws: device workspace of ks_ws_words(level, np) words.
+size_t ks_ws_words(const ckks_ctx *c, int level, int np);
+int ks_batch(ckks_ctx *c, int level, int np, const u64 *const *d, const u64 *const *keys,
+             const u64 *const *base0, const u64 *const *base1, u64 *const *o0, u64 *const *o1,
+             u64 *ws);

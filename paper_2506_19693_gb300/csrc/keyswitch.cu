@@ -1,0 +1,298 @@
+// Hybrid key switching (readings C7-C9): ModUp by fast basis conversion,
+// inner product with the switching key, ModDown.
+//
+// For np polynomials d (NTT domain, limbs q_0..q_l) and one key per
+// polynomial, computes (u0, u1) with u0 + u1 s ~ d s' and writes
+//   o0 = base0 + u0,   o1 = base1 + u1      (base may be null -> 0).
+//
+// Data flow (all buffers limb-major uint64, per polynomial):
+//   dc   = iNTT(d)                                   [l+1][N]
+//   for each active digit j (q-limbs [lo, hi) of the top-level digit j):
+//     ext_j[t] = BConv_{D_j -> t}(dc[lo:hi])  for t outside [lo, hi)   (C8)
+//     ext_j[t] = NTT(ext_j[t]); positions inside [lo, hi) reuse d itself
+//   acc_c[t] = sum_j ext_j[t] * key_j,c[t]          (c = 0 for b, 1 for a)
+//   acc_c[P] = iNTT(acc_c[P]);  z_c = NTT(BConv_{P -> Q_l}(acc_c[P]))  (C9)
+//   o_c      = base_c + (acc_c[Q] - z_c) * P^-1
+// The key is read once per launch for a batch that shares it: the inner
+// product loops over the batch with the key words held in registers.
+#include "ops.cuh"
+
+namespace {
+
+constexpr int TPB = 256;
+constexpr int MAXS = 16;   // source limbs of one basis conversion
+constexpr int MAXD = 8;    // digits
+
+struct BConvArgs {
+  const ModInfo *mods;
+  u32 n;
+  int nt;
+  const u64 *inv;                  // [ns] pairs: [Bhat_i^-1]_{b_i}, Shoup
+  const u64 *tab;                  // [nt][ns]: Bhat_i mod target
+  unsigned char src_mod[MAXS];
+  unsigned char dst_mod[MAX_MODS];
+  unsigned char dst_pos[MAX_MODS];
+  const u64 *src[MAX_CTS];         // first source limb (limbs contiguous)
+  u64 *dst[MAX_CTS];               // output polynomial base (limb positions dst_pos)
+};
+
+template <int NS>
+__global__ void __launch_bounds__(TPB) k_bconv(const BConvArgs a) {
+  const u32 k = blockIdx.x * TPB + threadIdx.x;
+  const int p = blockIdx.y;
+  if (k >= a.n) return;
+  const u64 *src = a.src[p];
+  u64 y[NS];
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    const u64 q = a.mods[a.src_mod[i]].q;
+    y[i] = shoup(src[(size_t)i * a.n + k], a.inv[2 * i], a.inv[2 * i + 1], q);
+  }
+  u64 *dst = a.dst[p];
+  for (int t = 0; t < a.nt; ++t) {
+    const u64 *row = a.tab + (size_t)t * NS;
+    u64 hi = 0, lo = 0;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) mac128(hi, lo, y[i], __ldg(&row[i]));
+    dst[(size_t)a.dst_pos[t] * a.n + k] = reduce128(hi, lo, a.mods[a.dst_mod[t]]);
+  }
+}
+
+struct IPArgs {
+  const ModInfo *mods;
+  u32 n;
+  int ext, ndig, key_ext, np;
+  unsigned char mod_of[MAX_MODS];
+  unsigned char keylimb_of[MAX_MODS];
+  int lo[MAXD], hi[MAXD];
+  const u64 *d[MAX_CTS];
+  const u64 *ext_buf[MAX_CTS];     // [ndig][ext][N]
+  const u64 *key[MAX_CTS];         // [n_digits][2][key_ext][N]
+  u64 *acc[MAX_CTS];               // [2][ext][N]
+};
+
+__global__ void __launch_bounds__(TPB) k_inner(const IPArgs a) {
+  const u32 k = blockIdx.x * TPB + threadIdx.x;
+  const int t = blockIdx.y;
+  if (k >= a.n) return;
+  const ModInfo &m = a.mods[a.mod_of[t]];
+  const int kl = a.keylimb_of[t];
+  u64 kb[MAXD], ka[MAXD];
+  const u64 *cur = nullptr;
+  for (int p = 0; p < a.np; ++p) {
+    if (a.key[p] != cur) {
+      cur = a.key[p];
+#pragma unroll
+      for (int j = 0; j < MAXD; ++j) {
+        if (j < a.ndig) {
+          kb[j] = cur[((size_t)(2 * j) * a.key_ext + kl) * a.n + k];
+          ka[j] = cur[((size_t)(2 * j + 1) * a.key_ext + kl) * a.n + k];
+        }
+      }
+    }
+    u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0;
+#pragma unroll
+    for (int j = 0; j < MAXD; ++j) {
+      if (j < a.ndig) {
+        const u64 v = (t >= a.lo[j] && t < a.hi[j]) ? a.d[p][(size_t)t * a.n + k]
+                                                     : a.ext_buf[p][((size_t)j * a.ext + t) * a.n + k];
+        mac128(h0, l0, v, kb[j]);
+        mac128(h1, l1, v, ka[j]);
+      }
+    }
+    a.acc[p][(size_t)t * a.n + k] = reduce128(h0, l0, m);
+    a.acc[p][((size_t)a.ext + t) * a.n + k] = reduce128(h1, l1, m);
+  }
+}
+
+struct CombineArgs {
+  const ModInfo *mods;
+  u32 n;
+  int ext;
+  const u64 *pinv;                 // [n_q] pairs
+  const u64 *acc[MAX_CTS];
+  const u64 *z[MAX_CTS];           // [2][l+1][N]
+  const u64 *base0[MAX_CTS], *base1[MAX_CTS];
+  u64 *o0[MAX_CTS], *o1[MAX_CTS];
+};
+
+__global__ void __launch_bounds__(TPB) k_combine(const CombineArgs a, int nl) {
+  const u32 k = blockIdx.x * TPB + threadIdx.x;
+  const int t = blockIdx.y, p = blockIdx.z;
+  if (k >= a.n) return;
+  const u64 q = a.mods[t].q, w = a.pinv[2 * t], ws = a.pinv[2 * t + 1];
+  const size_t off = (size_t)t * a.n + k;
+  const u64 x0 = a.acc[p][off], x1 = a.acc[p][(size_t)a.ext * a.n + off];
+  const u64 z0 = a.z[p][off], z1 = a.z[p][(size_t)nl * a.n + off];
+  u64 r0 = shoup(submod(x0, z0, q), w, ws, q);
+  u64 r1 = shoup(submod(x1, z1, q), w, ws, q);
+  if (a.base0[p]) r0 = addmod(r0, a.base0[p][off], q);
+  if (a.base1[p]) r1 = addmod(r1, a.base1[p][off], q);
+  a.o0[p][off] = r0;
+  a.o1[p][off] = r1;
+}
+
+int launch_bconv(ckks_ctx *c, BConvArgs &a, int ns, int np) {
+  a.mods = c->d_mods;
+  a.n = c->n;
+  dim3 g((c->n + TPB - 1) / TPB, np);
+  switch (ns) {
+#define CASE(S) case S: k_bconv<S><<<g, TPB, 0, c->stream>>>(a); break;
+    CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+    CASE(9) CASE(10) CASE(11) CASE(12) CASE(13) CASE(14) CASE(15) CASE(16)
+#undef CASE
+    default: return CKKS_E_PARAM;
+  }
+  return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_CUDA;
+}
+
+}  // namespace
+
+size_t ks_ws_words(const ckks_ctx *c, int level, int np) {
+  const int nl = level + 1, ext = nl + c->n_p;
+  const int ndig = (nl + c->alpha - 1) / c->alpha;
+  return (size_t)c->n * (nl + (size_t)ndig * ext + 2 * ext + 2 * nl) * np;
+}
+
+int ks_batch(ckks_ctx *c, int level, int np, const u64 *const *d, const u64 *const *keys,
+             const u64 *const *base0, const u64 *const *base1, u64 *const *o0, u64 *const *o1,
+             u64 *ws) {
+  if (np <= 0) return CKKS_OK;
+  if (np > MAX_CTS) return CKKS_E_PARAM;
+  const u32 n = c->n;
+  const int nl = level + 1, K = c->n_p, ext = nl + K;
+  const int ndig = (nl + c->alpha - 1) / c->alpha;
+  if (ndig > MAXD || c->alpha > MAXS || K > MAXS) return CKKS_E_PARAM;
+  // workspace per polynomial: dc [nl], ext [ndig][ext], acc [2][ext], z [2][nl]
+  const size_t per = ks_ws_words(c, level, 1);
+  int rc = CKKS_OK;
+  std::vector<u64 *> dc(np), eb(np), acc(np), z(np);
+  for (int i = 0; i < np; ++i) {
+    u64 *base = ws + per * i;
+    dc[i] = base;
+    eb[i] = dc[i] + (size_t)nl * n;
+    acc[i] = eb[i] + (size_t)ndig * ext * n;
+    z[i] = acc[i] + (size_t)2 * ext * n;
+  }
+  int mods[MAX_MODS];
+  for (int t = 0; t < ext; ++t) mods[t] = c->ext_mod(level, t);
+  // 1. dc = iNTT(d)
+  rc = launch_ntt(c, d, dc.data(), np, nl, mods, true);
+  if (rc) return rc;
+  // 2. ModUp per digit
+  std::vector<const u64 *> srcs(np);
+  std::vector<u64 *> dsts(np);
+  for (int j = 0; j < ndig; ++j) {
+    const int lo = j * c->alpha, hi = std::min((j + 1) * c->alpha, nl), ns = hi - lo;
+    BConvArgs a;
+    const u64 *tbl = c->d_conv + c->conv.modup_off[(size_t)level * c->n_digits + j];
+    a.inv = tbl;
+    a.tab = tbl + 2 * ns;
+    a.nt = ext - ns;
+    for (int i = 0; i < ns; ++i) a.src_mod[i] = (unsigned char)(lo + i);
+    int tt = 0;
+    for (int t = 0; t < ext; ++t) {
+      if (t >= lo && t < hi) continue;
+      a.dst_mod[tt] = (unsigned char)mods[t];
+      a.dst_pos[tt] = (unsigned char)t;
+      ++tt;
+    }
+    for (int i = 0; i < np; ++i) {
+      a.src[i] = dc[i] + (size_t)lo * n;
+      a.dst[i] = eb[i] + (size_t)j * ext * n;
+    }
+    rc = launch_bconv(c, a, ns, np);
+    if (rc) return rc;
+    // NTT of the converted limbs: positions [0, lo) and [hi, ext)
+    if (lo > 0) {
+      for (int i = 0; i < np; ++i) dsts[i] = eb[i] + (size_t)j * ext * n, srcs[i] = dsts[i];
+      rc = launch_ntt(c, srcs.data(), dsts.data(), np, lo, mods, false);
+      if (rc) return rc;
+    }
+    for (int i = 0; i < np; ++i) dsts[i] = eb[i] + ((size_t)j * ext + hi) * n, srcs[i] = dsts[i];
+    rc = launch_ntt(c, srcs.data(), dsts.data(), np, ext - hi, mods + hi, false);
+    if (rc) return rc;
+  }
+  // 3. inner product with the keys
+  {
+    IPArgs a;
+    a.mods = c->d_mods;
+    a.n = n;
+    a.ext = ext;
+    a.ndig = ndig;
+    a.key_ext = c->n_q + c->n_p;
+    a.np = np;
+    for (int t = 0; t < ext; ++t) {
+      a.mod_of[t] = (unsigned char)mods[t];
+      a.keylimb_of[t] = (unsigned char)c->key_limb(level, t);
+    }
+    for (int j = 0; j < ndig; ++j) {
+      a.lo[j] = j * c->alpha;
+      a.hi[j] = std::min((j + 1) * c->alpha, nl);
+    }
+    for (int i = 0; i < np; ++i) {
+      a.d[i] = d[i];
+      a.ext_buf[i] = eb[i];
+      a.key[i] = keys[i];
+      a.acc[i] = acc[i];
+    }
+    dim3 g((n + TPB - 1) / TPB, ext);
+    k_inner<<<g, TPB, 0, c->stream>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return CKKS_E_CUDA;
+  }
+  // 4. ModDown
+  {
+    std::vector<const u64 *> ps(2 * np);
+    std::vector<u64 *> pd(2 * np);
+    for (int i = 0; i < np; ++i)
+      for (int cc = 0; cc < 2; ++cc) {
+        pd[2 * i + cc] = acc[i] + ((size_t)cc * ext + nl) * n;
+        ps[2 * i + cc] = pd[2 * i + cc];
+      }
+    rc = launch_ntt(c, ps.data(), pd.data(), 2 * np, K, mods + nl, true);
+    if (rc) return rc;
+    for (int p0 = 0; p0 < 2 * np; p0 += MAX_CTS) {
+      const int cnt = std::min(MAX_CTS, 2 * np - p0);
+      BConvArgs a;
+      a.inv = c->d_conv + c->conv.moddown_phat_inv;
+      a.tab = c->d_conv + c->conv.moddown_phat_mod;
+      a.nt = nl;
+      for (int i = 0; i < K; ++i) a.src_mod[i] = (unsigned char)(c->n_q + i);
+      for (int t = 0; t < nl; ++t) {
+        a.dst_mod[t] = (unsigned char)t;
+        a.dst_pos[t] = (unsigned char)t;
+      }
+      for (int x = 0; x < cnt; ++x) {
+        const int pp = p0 + x, i = pp / 2, cc = pp % 2;
+        a.src[x] = pd[pp];
+        a.dst[x] = z[i] + (size_t)cc * nl * n;
+      }
+      rc = launch_bconv(c, a, K, cnt);
+      if (rc) return rc;
+    }
+    for (int i = 0; i < np; ++i)
+      for (int cc = 0; cc < 2; ++cc) {
+        pd[2 * i + cc] = z[i] + (size_t)cc * nl * n;
+        ps[2 * i + cc] = pd[2 * i + cc];
+      }
+    rc = launch_ntt(c, ps.data(), pd.data(), 2 * np, nl, mods, false);
+    if (rc) return rc;
+    CombineArgs a;
+    a.mods = c->d_mods;
+    a.n = n;
+    a.ext = ext;
+    a.pinv = c->d_conv + c->conv.moddown_pinv;
+    for (int i = 0; i < np; ++i) {
+      a.acc[i] = acc[i];
+      a.z[i] = z[i];
+      a.base0[i] = base0 ? base0[i] : nullptr;
+      a.base1[i] = base1 ? base1[i] : nullptr;
+      a.o0[i] = o0[i];
+      a.o1[i] = o1[i];
+    }
+    dim3 g((n + TPB - 1) / TPB, nl, np);
+    k_combine<<<g, TPB, 0, c->stream>>>(a, nl);
+    if (cudaGetLastError() != cudaSuccess) return CKKS_E_CUDA;
+  }
+  return CKKS_OK;
+}

@@ -1,0 +1,267 @@
+// Negacyclic NTT / inverse NTT over uint64 RNS limbs (reading C2).
+//
+// Forward transform: merged-psi Cooley-Tukey, stages m = 1, 2, ..., N/2; at
+// stage m the butterfly of group i pairs (j, j + N/2m) with twiddle
+// psi^brv(m + i).  The output is in the canonical order
+// A[j] = a(psi^(2 brv(j) + 1)).  The inverse runs the Gentleman-Sande mirror
+// (stages m = N/2 .. 1, twiddles psi^-brv(m + i)) and multiplies by N^-1.
+//
+// GB300 layout: a limb (N = 2^16 words, 512 KiB) does not fit in one CTA's
+// shared memory, so the transform is split in two passes over HBM.  View the
+// limb as H x B (B = 256 contiguous words per row, H = N / B rows):
+//   pass A -- the first log2 H stages pair words of the same column; a CTA
+//             takes 16 adjacent columns (each row segment is one 128-byte
+//             line), loads them straight into registers, runs radix-2^s
+//             sub-transforms in registers, exchanges once through shared
+//             memory and writes back coalesced;
+//   pass B -- the last 8 stages stay inside one row; a CTA takes 16 rows.
+// Each thread owns 2^s words and runs s butterfly stages in registers
+// (Harvey's lazy butterflies: values stay in [0, 4q) forward, [0, 2q)
+// inverse; q < 2^62).
+#include "ctx.h"
+
+namespace {
+
+constexpr int LB = 8;            // log2 of the row length handled by pass B
+constexpr int BROW = 1 << LB;    // 256
+constexpr int CA = 16;           // columns per pass-A tile
+constexpr int RB = 16;           // rows per pass-B tile
+constexpr int THREADS = 256;
+
+struct NttParams {
+  const ModInfo *mods;
+  const ulonglong2 *tw;          // [modulus][N]
+  u32 n;
+  int n_limbs;
+  unsigned char mod_of_limb[MAX_MODS];
+  CPolyPtrs src;
+  PolyPtrs dst;
+};
+
+// Pass-B shared-memory padding: one spare word per 16 keeps the 16-word
+// strided accesses of the row stages conflict-free.
+__device__ __forceinline__ int padb(int off) { return off + (off >> 4); }
+
+template <int K>
+__device__ __forceinline__ void fwd_step(u64 (&v)[1 << K], u32 mg, const ulonglong2 *__restrict__ tw,
+                                         u64 q, u64 twoq) {
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    const int half = 1 << (K - 1 - s);
+#pragma unroll
+    for (int e = 0; e < (1 << K); ++e) {
+      if (e & half) continue;
+      const ulonglong2 w = __ldg(&tw[(mg << s) + (e >> (K - s))]);
+      u64 x = v[e];
+      if (x >= twoq) x -= twoq;
+      const u64 t = shoup_lazy(v[e + half], w.x, w.y, q);
+      v[e] = x + t;
+      v[e + half] = x + twoq - t;
+    }
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void inv_step(u64 (&v)[1 << K], u32 mg, const ulonglong2 *__restrict__ tw,
+                                         u64 q, u64 twoq) {
+#pragma unroll
+  for (int s = K - 1; s >= 0; --s) {
+    const int half = 1 << (K - 1 - s);
+#pragma unroll
+    for (int e = 0; e < (1 << K); ++e) {
+      if (e & half) continue;
+      const ulonglong2 w = __ldg(&tw[(mg << s) + (e >> (K - s))]);
+      const u64 x = v[e], y = v[e + half];
+      u64 sum = x + y;
+      if (sum >= twoq) sum -= twoq;
+      v[e] = sum;
+      v[e + half] = shoup_lazy(x + twoq - y, w.x, w.y, q);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- forward
+template <int LH, int S1>
+__global__ void __launch_bounds__(THREADS) fwd_pass_a(const NttParams prm) {
+  constexpr int H = 1 << LH, S2 = LH - S1;
+  __shared__ u64 sm[H * CA];
+  const int limb = blockIdx.y, poly = blockIdx.z;
+  const int mi = prm.mod_of_limb[limb];
+  const u64 q = prm.mods[mi].q, twoq = 2 * q;
+  const ulonglong2 *tw = prm.tw + (size_t)mi * prm.n;
+  const u64 *src = prm.src.p[poly] + (size_t)limb * prm.n;
+  u64 *dst = prm.dst.p[poly] + (size_t)limb * prm.n;
+  const int c0 = blockIdx.x * CA;
+  for (int x = threadIdx.x; x < (H >> S1) * CA; x += THREADS) {
+    const int c = x % CA, r0 = x / CA;
+    u64 v[1 << S1];
+#pragma unroll
+    for (int e = 0; e < (1 << S1); ++e) v[e] = src[(size_t)(r0 + (e << S2)) * BROW + c0 + c];
+    fwd_step<S1>(v, 1u, tw, q, twoq);
+#pragma unroll
+    for (int e = 0; e < (1 << S1); ++e) sm[(r0 + (e << S2)) * CA + c] = v[e];
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < (1 << S1) * CA; x += THREADS) {
+    const int c = x % CA, g = x / CA;
+    u64 v[1 << S2];
+#pragma unroll
+    for (int e = 0; e < (1 << S2); ++e) v[e] = sm[((g << S2) + e) * CA + c];
+    fwd_step<S2>(v, (1u << S1) + g, tw, q, twoq);
+#pragma unroll
+    for (int e = 0; e < (1 << S2); ++e) dst[(size_t)((g << S2) + e) * BROW + c0 + c] = v[e];
+  }
+}
+
+template <int LH>
+__global__ void __launch_bounds__(THREADS) fwd_pass_b(const NttParams prm, int from_src) {
+  constexpr int H = 1 << LH, U1 = 4, U2 = LB - U1;
+  __shared__ u64 sm[RB * BROW + (RB * BROW >> 4)];
+  const int limb = blockIdx.y, poly = blockIdx.z;
+  const int mi = prm.mod_of_limb[limb];
+  const u64 q = prm.mods[mi].q, twoq = 2 * q;
+  const ulonglong2 *tw = prm.tw + (size_t)mi * prm.n;
+  const u64 *src = (from_src ? prm.src.p[poly] : prm.dst.p[poly]) + (size_t)limb * prm.n;
+  u64 *dst = prm.dst.p[poly] + (size_t)limb * prm.n;
+  const int row0 = blockIdx.x * RB;
+  for (int x = threadIdx.x; x < RB * (BROW >> U1); x += THREADS) {
+    const int l0 = x % (BROW >> U1), rr = x / (BROW >> U1), b = row0 + rr;
+    u64 v[1 << U1];
+#pragma unroll
+    for (int e = 0; e < (1 << U1); ++e) v[e] = src[(size_t)b * BROW + l0 + (e << U2)];
+    fwd_step<U1>(v, (u32)(H + b), tw, q, twoq);
+#pragma unroll
+    for (int e = 0; e < (1 << U1); ++e) sm[padb(rr * BROW + l0 + (e << U2))] = v[e];
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < (RB << U1); x += THREADS) {
+    const int g = x % (1 << U1), rr = x / (1 << U1), b = row0 + rr;
+    u64 v[1 << U2];
+#pragma unroll
+    for (int e = 0; e < (1 << U2); ++e) v[e] = sm[padb(rr * BROW + (g << U2) + e)];
+    fwd_step<U2>(v, ((u32)(H + b) << U1) + g, tw, q, twoq);
+#pragma unroll
+    for (int e = 0; e < (1 << U2); ++e) {
+      u64 r = v[e];
+      if (r >= twoq) r -= twoq;
+      if (r >= q) r -= q;
+      sm[padb(rr * BROW + (g << U2) + e)] = r;
+    }
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < RB * BROW; x += THREADS) dst[(size_t)row0 * BROW + x] = sm[padb(x)];
+}
+
+// ---------------------------------------------------------------- inverse
+template <int LH>
+__global__ void __launch_bounds__(THREADS) inv_pass_b(const NttParams prm) {
+  constexpr int H = 1 << LH, U1 = 4, U2 = LB - U1;
+  __shared__ u64 sm[RB * BROW + (RB * BROW >> 4)];
+  const int limb = blockIdx.y, poly = blockIdx.z;
+  const int mi = prm.mod_of_limb[limb];
+  const u64 q = prm.mods[mi].q, twoq = 2 * q;
+  const ulonglong2 *tw = prm.tw + (size_t)mi * prm.n;
+  const u64 *src = prm.src.p[poly] + (size_t)limb * prm.n;
+  u64 *dst = prm.dst.p[poly] + (size_t)limb * prm.n;
+  const int row0 = blockIdx.x * RB;
+  for (int x = threadIdx.x; x < RB * BROW; x += THREADS) sm[padb(x)] = src[(size_t)row0 * BROW + x];
+  __syncthreads();
+  for (int x = threadIdx.x; x < (RB << U1); x += THREADS) {
+    const int g = x % (1 << U1), rr = x / (1 << U1), b = row0 + rr;
+    u64 v[1 << U2];
+#pragma unroll
+    for (int e = 0; e < (1 << U2); ++e) v[e] = sm[padb(rr * BROW + (g << U2) + e)];
+    inv_step<U2>(v, ((u32)(H + b) << U1) + g, tw, q, twoq);
+#pragma unroll
+    for (int e = 0; e < (1 << U2); ++e) sm[padb(rr * BROW + (g << U2) + e)] = v[e];
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < RB * (BROW >> U1); x += THREADS) {
+    const int l0 = x % (BROW >> U1), rr = x / (BROW >> U1), b = row0 + rr;
+    u64 v[1 << U1];
+#pragma unroll
+    for (int e = 0; e < (1 << U1); ++e) v[e] = sm[padb(rr * BROW + l0 + (e << U2))];
+    inv_step<U1>(v, (u32)(H + b), tw, q, twoq);
+#pragma unroll
+    for (int e = 0; e < (1 << U1); ++e) dst[(size_t)b * BROW + l0 + (e << U2)] = v[e];
+  }
+}
+
+template <int LH, int S1>
+__global__ void __launch_bounds__(THREADS) inv_pass_a(const NttParams prm) {
+  constexpr int H = 1 << LH, S2 = LH - S1;
+  __shared__ u64 sm[H * CA];
+  const int limb = blockIdx.y, poly = blockIdx.z;
+  const int mi = prm.mod_of_limb[limb];
+  const ModInfo &m = prm.mods[mi];
+  const u64 q = m.q, twoq = 2 * q, ninv = m.ninv, ninv_s = m.ninv_s;
+  const ulonglong2 *tw = prm.tw + (size_t)mi * prm.n;
+  u64 *dst = prm.dst.p[poly] + (size_t)limb * prm.n;
+  const int c0 = blockIdx.x * CA;
+  for (int x = threadIdx.x; x < (1 << S1) * CA; x += THREADS) {
+    const int c = x % CA, g = x / CA;
+    u64 v[1 << S2];
+#pragma unroll
+    for (int e = 0; e < (1 << S2); ++e) v[e] = dst[(size_t)((g << S2) + e) * BROW + c0 + c];
+    inv_step<S2>(v, (1u << S1) + g, tw, q, twoq);
+#pragma unroll
+    for (int e = 0; e < (1 << S2); ++e) sm[((g << S2) + e) * CA + c] = v[e];
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < (H >> S1) * CA; x += THREADS) {
+    const int c = x % CA, r0 = x / CA;
+    u64 v[1 << S1];
+#pragma unroll
+    for (int e = 0; e < (1 << S1); ++e) v[e] = sm[(r0 + (e << S2)) * CA + c];
+    inv_step<S1>(v, 1u, tw, q, twoq);
+#pragma unroll
+    for (int e = 0; e < (1 << S1); ++e)
+      dst[(size_t)(r0 + (e << S2)) * BROW + c0 + c] = shoup(v[e], ninv, ninv_s, q);
+  }
+}
+
+template <int LH>
+void launch_lh(const NttParams &prm, int npoly, bool inverse, cudaStream_t st) {
+  constexpr int S1 = (LH + 1) / 2;
+  const int H = 1 << LH;
+  dim3 ga(BROW / CA, prm.n_limbs, npoly), gb(H / RB, prm.n_limbs, npoly);
+  if (!inverse) {
+    fwd_pass_a<LH, S1><<<ga, THREADS, 0, st>>>(prm);
+    fwd_pass_b<LH><<<gb, THREADS, 0, st>>>(prm, 0);
+  } else {
+    inv_pass_b<LH><<<gb, THREADS, 0, st>>>(prm);
+    inv_pass_a<LH, S1><<<ga, THREADS, 0, st>>>(prm);
+  }
+}
+
+}  // namespace
+
+int launch_ntt(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, int nl, const int *mods,
+               bool inverse) {
+  if (npoly <= 0 || nl <= 0) return CKKS_OK;
+  if (nl > MAX_MODS) return CKKS_E_PARAM;
+  NttParams prm;
+  prm.mods = c->d_mods;
+  prm.tw = inverse ? c->d_tw_inv : c->d_tw_fwd;
+  prm.n = c->n;
+  prm.n_limbs = nl;
+  for (int l = 0; l < nl; ++l) prm.mod_of_limb[l] = (unsigned char)mods[l];
+  for (int p0 = 0; p0 < npoly; p0 += MAX_POLYS) {
+    const int cnt = npoly - p0 < MAX_POLYS ? npoly - p0 : MAX_POLYS;
+    for (int i = 0; i < cnt; ++i) {
+      prm.src.p[i] = src[p0 + i];
+      prm.dst.p[i] = dst[p0 + i];
+    }
+    switch (c->log_n - LB) {
+      case 2: launch_lh<2>(prm, cnt, inverse, c->stream); break;
+      case 3: launch_lh<3>(prm, cnt, inverse, c->stream); break;
+      case 4: launch_lh<4>(prm, cnt, inverse, c->stream); break;
+      case 5: launch_lh<5>(prm, cnt, inverse, c->stream); break;
+      case 6: launch_lh<6>(prm, cnt, inverse, c->stream); break;
+      case 7: launch_lh<7>(prm, cnt, inverse, c->stream); break;
+      case 8: launch_lh<8>(prm, cnt, inverse, c->stream); break;
+      default: return CKKS_E_PARAM;
+    }
+  }
+  return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_CUDA;
+}

@@ -1,0 +1,270 @@
+// Element-wise RNS-CKKS kernels: slot-wise add/sub (Eq. add, sub), plaintext
+// multiply/add, integer-constant multiply, tensor product (reading C6),
+// Galois automorphisms in the NTT domain (C11), rescale (C10), encryption and
+// decryption (C5) and on-device uniform sampling (C4).  All of these are
+// HBM-bound streams over limb-major uint64 data: one thread per coefficient,
+// limbs on gridDim.y, ciphertexts on gridDim.z.
+#include "ops.cuh"
+
+namespace {
+
+constexpr int TPB = 256;
+
+__device__ __forceinline__ u64 mix64_dev(u64 z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ u64 draw_dev(u64 key, u64 ctr) {
+  return mix64_dev(key + (ctr + 1) * 0x9E3779B97F4A7C15ULL);
+}
+// (hi * 2^64 + lo) mod q with hi = draw(2 idx), lo = draw(2 idx + 1)
+__device__ __forceinline__ u64 uniform_dev(u64 key, u64 idx, const ModInfo &m) {
+  return reduce128(draw_dev(key, 2 * idx), draw_dev(key, 2 * idx + 1), m);
+}
+
+__device__ __forceinline__ u32 brv_dev(u32 x, int bits) { return __brev(x) >> (32 - bits); }
+
+// signed 64-bit integer -> residue in [0, q)
+__device__ __forceinline__ u64 signed_res(i64 x, const ModInfo &m) {
+  if (x >= 0) return reduce128(0, (u64)x, m);
+  const u64 mag = reduce128(0, (u64)(-(x + 1)) + 1, m);
+  return mag ? m.q - mag : 0;
+}
+
+__global__ void k_addsub(EwArgs a, int sub) {
+  const u32 k = blockIdx.x * TPB + threadIdx.x;
+  const int l = blockIdx.y, c = blockIdx.z;
+  if (k >= a.n) return;
+  const u64 q = a.mods[l].q;
+  const size_t off = (size_t)l * a.n + k;
+  const u64 x0 = a.x0[c][off], x1 = a.x1[c][off], y0 = a.y0[c][off], y1 = a.y1[c][off];
+  a.o0[c][off] = sub ? submod(x0, y0, q) : addmod(x0, y0, q);
+  a.o1[c][off] = sub ? submod(x1, y1, q) : addmod(x1, y1, q);
+}
+
+// mode 0: (c0 pt, c1 pt); mode 1: (c0 + pt, c1).  Plaintext pointer in y0.
+__global__ void k_plain(EwArgs a, int mode) {
+  const u32 k = blockIdx.x * TPB + threadIdx.x;
+  const int l = blockIdx.y, c = blockIdx.z;
+  if (k >= a.n) return;
+  const ModInfo &m = a.mods[l];
+  const size_t off = (size_t)l * a.n + k;
+  const u64 pt = a.y0[c][off], x0 = a.x0[c][off], x1 = a.x1[c][off];
+  if (mode == 0) {
+    a.o0[c][off] = mulmod(x0, pt, m);
+    a.o1[c][off] = mulmod(x1, pt, m);
+  } else {
+    a.o0[c][off] = addmod(x0, pt, m.q);
+    a.o1[c][off] = x1;
+  }
+}
+
+__global__ void k_mul_int(EwArgs a, i64 kconst) {
+  const u32 k = blockIdx.x * TPB + threadIdx.x;
+  const int l = blockIdx.y, c = blockIdx.z;
+  if (k >= a.n) return;
+  const ModInfo &m = a.mods[l];
+  const u64 kk = signed_res(kconst, m);
+  const size_t off = (size_t)l * a.n + k;
+  const u64 x0 = a.x0[c][off], x1 = a.x1[c][off];
+  a.o0[c][off] = mulmod(x0, kk, m);
+  a.o1[c][off] = mulmod(x1, kk, m);
+}
+
+// tensor product (C6): d0 = a0 b0 -> o0, d1 = a0 b1 + a1 b0 -> o1, d2 = a1 b1 -> d2
+struct D2Ptrs {
+  u64 *p[MAX_CTS];
+};
+__global__ void k_tensor(EwArgs a, D2Ptrs d2) {
+  const u32 k = blockIdx.x * TPB + threadIdx.x;
+  const int l = blockIdx.y, c = blockIdx.z;
+  if (k >= a.n) return;
+  const ModInfo &m = a.mods[l];
+  const size_t off = (size_t)l * a.n + k;
+  const u64 a0 = a.x0[c][off], a1 = a.x1[c][off];
+  const u64 b0 = a.y0[c][off], b1 = a.y1[c][off];
+  u64 hi = 0, lo = 0;
+  mac128(hi, lo, a0, b1);
+  mac128(hi, lo, a1, b0);
+  const u64 r0 = mulmod(a0, b0, m), r1 = reduce128(hi, lo, m), r2 = mulmod(a1, b1, m);
+  a.o0[c][off] = r0;
+  a.o1[c][off] = r1;
+  d2.p[c][off] = r2;
+}
+
+// automorphism X -> X^g in the canonical NTT order (C11):
+// out[j] = in[j'] with 2 brv(j') + 1 = g (2 brv(j) + 1) mod 2N.
+__global__ void k_automorph(EwArgs a, u32 g, int log_n, int both) {
+  const u32 j = blockIdx.x * TPB + threadIdx.x;
+  const int l = blockIdx.y, c = blockIdx.z;
+  if (j >= a.n) return;
+  const u32 mask = 2 * a.n - 1;
+  const u32 e = (u32)(((u64)g * (2 * brv_dev(j, log_n) + 1)) & mask);
+  const u32 jp = brv_dev((e - 1) >> 1, log_n);
+  const size_t off = (size_t)l * a.n;
+  a.o0[c][off + j] = a.x0[c][off + jp];
+  if (both) a.o1[c][off + j] = a.x1[c][off + jp];
+}
+
+// rescale stage 1: lift_i = [last]_centred mod q_i (coefficient domain)
+__global__ void k_rescale_lift(RescaleArgs r) {
+  const u32 k = blockIdx.x * TPB + threadIdx.x;
+  const int i = blockIdx.y, c = blockIdx.z;
+  if (k >= r.n) return;
+  const u64 ql = r.mods[r.level].q;
+  const ModInfo &m = r.mods[i];
+  for (int p = 0; p < 2; ++p) {
+    const u64 v = r.last[c][(size_t)p * r.n + k];
+    u64 res;
+    if (v > (ql >> 1)) {
+      const u64 mag = reduce128(0, ql - v, m);
+      res = mag ? m.q - mag : 0;
+    } else {
+      res = reduce128(0, v, m);
+    }
+    r.lift[c][((size_t)p * r.level + i) * r.n + k] = res;
+  }
+}
+// rescale stage 2: c_i = (c_i - lift_i) q_l^-1 (NTT domain), in place
+__global__ void k_rescale_finish(RescaleArgs r) {
+  const u32 k = blockIdx.x * TPB + threadIdx.x;
+  const int i = blockIdx.y, c = blockIdx.z;
+  if (k >= r.n) return;
+  const u64 q = r.mods[i].q;
+  const u64 w = r.qlinv[2 * i], ws = r.qlinv[2 * i + 1];
+  const size_t off = (size_t)i * r.n + k;
+  const u64 l0 = r.lift[c][off], l1 = r.lift[c][(size_t)r.level * r.n + off];
+  r.c0[c][off] = shoup(submod(r.c0[c][off], l0, q), w, ws, q);
+  r.c1[c][off] = shoup(submod(r.c1[c][off], l1, q), w, ws, q);
+}
+
+// encryption (C5): c1 = a (uniform, NTT domain, key_a), c0 = pt + e - a s
+__global__ void k_encrypt(EncArgs e) {
+  const u32 k = blockIdx.x * TPB + threadIdx.x;
+  const int t = blockIdx.y, c = blockIdx.z;
+  if (k >= e.n) return;
+  const ModInfo &m = e.mods[t];
+  const size_t off = (size_t)t * e.n + k;
+  const u64 a = uniform_dev(e.key_a[c], (u64)t * e.n + k, m);
+  const u64 as = mulmod(a, e.s_ntt[off], m);
+  const u64 v = addmod(e.pt[c][off], e.err[c][off], m.q);
+  e.c0[c][off] = submod(v, as, m.q);
+  e.c1[c][off] = a;
+}
+
+__global__ void k_decrypt(EwArgs a, const u64 *s_ntt) {
+  const u32 k = blockIdx.x * TPB + threadIdx.x;
+  const int l = blockIdx.y, c = blockIdx.z;
+  if (k >= a.n) return;
+  const ModInfo &m = a.mods[l];
+  const size_t off = (size_t)l * a.n + k;
+  a.o0[c][off] = addmod(a.x0[c][off], mulmod(a.x1[c][off], s_ntt[off], m), m.q);
+}
+
+__global__ void k_signed_to_res(const i64 *v, u64 *out, const ModInfo *mods, int first_mod, u32 n) {
+  const u32 k = blockIdx.x * TPB + threadIdx.x;
+  const int l = blockIdx.y;
+  if (k >= n) return;
+  out[(size_t)l * n + k] = signed_res(v[k], mods[first_mod + l]);
+}
+
+// switching-key row for digit j: a uniform; b = -a s + e (+ [P]_{q_t} s' on the digit's limbs)
+__global__ void k_keyrow(KeyArgs ka) {
+  const u32 k = blockIdx.x * TPB + threadIdx.x;
+  const int t = blockIdx.y;
+  if (k >= ka.n) return;
+  const ModInfo &m = ka.mods[t];
+  const size_t off = (size_t)t * ka.n + k;
+  const u64 a = uniform_dev(ka.key_a, (u64)t * ka.n + k, m);
+  u64 b = submod(ka.err[off], mulmod(a, ka.s_ntt[off], m), m.q);
+  if (t >= ka.lo && t < ka.hi) b = addmod(b, mulmod(ka.p_mod[t], ka.sp_ntt[off], m), m.q);
+  ka.b[off] = b;
+  ka.a[off] = a;
+}
+
+__global__ void k_square(u64 *out, const u64 *in, const ModInfo *mods, u32 n) {
+  const u32 k = blockIdx.x * TPB + threadIdx.x;
+  const int t = blockIdx.y;
+  if (k >= n) return;
+  const size_t off = (size_t)t * n + k;
+  out[off] = mulmod(in[off], in[off], mods[t]);
+}
+
+dim3 grid_for(u32 n, int limbs, int cts) { return dim3((n + TPB - 1) / TPB, limbs, cts); }
+int last_status() { return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_CUDA; }
+
+}  // namespace
+
+int ew_addsub(ckks_ctx *c, EwArgs &a, int nl, int ncts, bool sub) {
+  a.mods = c->d_mods;
+  a.n = c->n;
+  k_addsub<<<grid_for(c->n, nl, ncts), TPB, 0, c->stream>>>(a, sub ? 1 : 0);
+  return last_status();
+}
+int ew_plain(ckks_ctx *c, EwArgs &a, int nl, int ncts, int mode) {
+  a.mods = c->d_mods;
+  a.n = c->n;
+  k_plain<<<grid_for(c->n, nl, ncts), TPB, 0, c->stream>>>(a, mode);
+  return last_status();
+}
+int ew_mul_int(ckks_ctx *c, EwArgs &a, int nl, int ncts, i64 k) {
+  a.mods = c->d_mods;
+  a.n = c->n;
+  k_mul_int<<<grid_for(c->n, nl, ncts), TPB, 0, c->stream>>>(a, k);
+  return last_status();
+}
+int ew_tensor(ckks_ctx *c, EwArgs &a, u64 *const *d2, int nl, int ncts) {
+  a.mods = c->d_mods;
+  a.n = c->n;
+  D2Ptrs d;
+  for (int i = 0; i < ncts; ++i) d.p[i] = d2[i];
+  k_tensor<<<grid_for(c->n, nl, ncts), TPB, 0, c->stream>>>(a, d);
+  return last_status();
+}
+int ew_automorph(ckks_ctx *c, EwArgs &a, u32 g, int nl, int ncts, bool both_polys) {
+  a.mods = c->d_mods;
+  a.n = c->n;
+  k_automorph<<<grid_for(c->n, nl, ncts), TPB, 0, c->stream>>>(a, g, c->log_n, both_polys ? 1 : 0);
+  return last_status();
+}
+int ew_decrypt(ckks_ctx *c, EwArgs &a, int nl, int ncts) {
+  a.mods = c->d_mods;
+  a.n = c->n;
+  k_decrypt<<<grid_for(c->n, nl, ncts), TPB, 0, c->stream>>>(a, c->d_s_ntt);
+  return last_status();
+}
+int ew_rescale_lift(ckks_ctx *c, RescaleArgs &r, int ncts) {
+  r.mods = c->d_mods;
+  r.n = c->n;
+  k_rescale_lift<<<grid_for(c->n, r.level, ncts), TPB, 0, c->stream>>>(r);
+  return last_status();
+}
+int ew_rescale_finish(ckks_ctx *c, RescaleArgs &r, int ncts) {
+  r.mods = c->d_mods;
+  r.n = c->n;
+  k_rescale_finish<<<grid_for(c->n, r.level, ncts), TPB, 0, c->stream>>>(r);
+  return last_status();
+}
+int ew_encrypt(ckks_ctx *c, EncArgs &e, int nl, int ncts) {
+  e.mods = c->d_mods;
+  e.n = c->n;
+  e.s_ntt = c->d_s_ntt;
+  k_encrypt<<<grid_for(c->n, nl, ncts), TPB, 0, c->stream>>>(e);
+  return last_status();
+}
+int ew_signed_to_res(ckks_ctx *c, const i64 *v, u64 *out, int first_mod, int nl) {
+  k_signed_to_res<<<grid_for(c->n, nl, 1), TPB, 0, c->stream>>>(v, out, c->d_mods, first_mod, c->n);
+  return last_status();
+}
+int ew_keyrow(ckks_ctx *c, KeyArgs &k, int nl) {
+  k.mods = c->d_mods;
+  k.n = c->n;
+  k.s_ntt = c->d_s_ntt;
+  k_keyrow<<<grid_for(c->n, nl, 1), TPB, 0, c->stream>>>(k);
+  return last_status();
+}
+int ew_square(ckks_ctx *c, u64 *out, const u64 *in, int nl) {
+  k_square<<<grid_for(c->n, nl, 1), TPB, 0, c->stream>>>(out, in, c->d_mods, c->n);
+  return last_status();
+}
