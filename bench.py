@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Throughput of the RNS-CKKS evaluation core on GB300.
+
+One step = one pass of the hot path over one batch at N = 2^16 with 24
+ciphertext primes (q0 ~ 2^61, 23 x ~2^55), 8 special primes, dnum = 3:
+  * 64 ciphertext pairs: HMult + relinearise + rescale (batched), then
+  * every input rotated by 2^0 .. 2^14 (15 batched rotations of 64).
+`value` is HMult+relin(+rescale)/s over the multiply phase of the timed steps
+(device time, CUDA events on the library's stream); rotations/s is reported
+beside it.  Inputs (3.2 GB of ciphertexts per step) exceed L2, so no flush.
+
+--impl reference times the CPU oracle on the host cores instead (bounded
+sample: one HMult+relin+rescale of one ciphertext pair per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic_inputs as si  # noqa: E402
+
+METRIC = "HMult+relin/s and bootstraps/s at N=2^16 on 1 GB300, plain vs batched TC form"
+UNIT = "HMult+relin/s"
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_table():
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)
+    return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    mx.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[4:8]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle arm
+class OracleSample:
+    """The CPU oracle on one ciphertext pair of the workload (keys and inputs
+    prepared once, untimed); time() runs one HMult+relin+rescale."""
+
+    def __init__(self, w, seed=0):
+        import oracle
+        self.orc = oracle.Oracle(w.log_n, w.q_bits, w.p_bits, w.dnum, w.h, w.sigma)
+        self.orc.keygen(1)
+        level = len(w.q_bits) - 1
+        scale = 2.0 ** w.log2_scale
+        z = si.messages(seed, 2, w.slots)
+        self.cts = [self.orc.encrypt(self.orc.pt_from_int(self.orc.encode(z[i], scale), level), level, scale,
+                                     10 + i) for i in range(2)]
+        self.threads = _env_int("OMP_NUM_THREADS", os.cpu_count() or 1)
+
+    def time(self) -> float:
+        t0 = time.perf_counter()
+        self.orc.rescale(self.orc.mul_relin(self.cts[0], self.cts[1]))
+        return time.perf_counter() - t0
+
+
+def run_reference(args):
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    w = si.PLAIN
+    sample = OracleSample(w)
+    threads = sample.threads
+    for _ in range(min(args.warmup, 1)):
+        sample.time()
+    times = [sample.time() for _ in range(args.steps)]
+    v = 1.0 / float(np.mean(times))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * float(np.mean(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": config_of(w),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "per step: 1 HMult+relin+rescale of 1 ciphertext pair at N=2^16, L=24 "
+                                       "(1/64 of the batch), CPU oracle (128-bit % arithmetic, OpenMP over limbs)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def config_of(w):
+    return {"workload": w.name, "log_n": w.log_n, "n_q": len(w.q_bits), "n_p": len(w.p_bits), "dnum": w.dnum,
+            "log2_scale": w.log2_scale, "batch_pairs": w.batch, "rotations_per_ct": len(w.rot_steps),
+            "form": "uint64 CUDA-core", "l2": "inputs 3.2 GB per step > 126 MB L2; no flush"}
+
+
+# ---------------------------------------------------------------- GPU arm
+# Algorithmic work per unit the library's profiler counts (a limb of N words,
+# except bconv, whose unit is one multiply-accumulate per coefficient):
+#   HBM words moved per unit (8 bytes each, N per limb), and
+#   integer work per unit: Shoup butterflies or 64x64->128 MACs per coefficient.
+def kernel_work(name, units, launches, w, ndig):
+    n = 1 << w.log_n
+    lh = w.log_n - 8
+    hbm_words = {"ntt_fwd_pass_a": 2, "ntt_fwd_pass_b": 2, "ntt_inv_pass_a": 2, "ntt_inv_pass_b": 2,
+                 "automorph": 2, "tensor": 7, "ks_moddown_combine": 8, "ks_inner_product": ndig + 2}.get(name)
+    alu = None
+    if name in ("ntt_fwd_pass_a", "ntt_inv_pass_a"):
+        alu = ("bfly", units * (n // 2) * lh)
+    elif name in ("ntt_fwd_pass_b", "ntt_inv_pass_b"):
+        alu = ("bfly", units * (n // 2) * 8)
+    elif name == "bconv":
+        alu = ("mac", units * n)
+    elif name == "ks_inner_product":
+        alu = ("mac", units * 2 * ndig * n)
+    hbm = hbm_words * 8 * n * units if hbm_words is not None else None
+    return hbm, alu
+
+
+def roofline(prof, w, ndig, hbm_peak, hbm_kind, alu_peaks):
+    """Roofline of the kernel class with the most device time in the timed region."""
+    total = sum(v[0] for v in prof.values())
+    name, (ms, nlaunch, units) = max(prof.items(), key=lambda kv: kv[1][0])
+    if not nlaunch:
+        return None
+    sec = ms / 1e3
+    hbm, alu = kernel_work(name, units, nlaunch, w, ndig)
+    cands = []
+    if hbm is not None:
+        a = hbm / nlaunch / (sec / nlaunch) / 1e9
+        cands.append({"bound": "hbm", "achieved": a, "peak": hbm_peak, "unit": "GB/s", "frac": a / hbm_peak,
+                      "peak_source": f"{hbm_kind} hbm_gbs", "algorithmic_per_launch": hbm / nlaunch})
+    if alu is not None and alu_peaks:
+        kind, ops = alu
+        pk = alu_peaks["mac_per_s"] if kind == "mac" else alu_peaks["bfly_per_s"]
+        a = ops / sec
+        cands.append({"bound": "alu", "achieved": a / 1e12, "peak": pk / 1e12,
+                      "unit": "T 64x64->128 MAC/s" if kind == "mac" else "T Shoup butterflies/s",
+                      "frac": a / pk, "peak_source": "measured on this GPU by ckks_alu_peaks (register-only "
+                      "kernel of the same primitive)", "algorithmic_per_launch": ops / nlaunch})
+    if not cands:
+        return None
+    best = max(cands, key=lambda c: c["frac"])
+    tr = traffic_table().get(name)
+    best.update({"kernel": name, "avg_launch_us": ms / nlaunch * 1e3, "launches": nlaunch,
+                 "share_of_timed_device_ms": ms / total,
+                 "traffic": tr.get("dram_bytes_per_launch") if tr and tr.get("valid", True) else None,
+                 "other_bounds": [c for c in cands if c is not best]})
+    return best
+
+
+def run_gpu(args):
+    import torch
+    import paper_2506_19693_gb300 as ck
+
+    rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w = si.PLAIN
+    B = w.batch
+    level = len(w.q_bits) - 1
+    scale = 2.0 ** w.log2_scale
+    stream = torch.cuda.current_stream()
+    ctx = ck.Context.from_workload(w, stream=stream)
+    ctx.keygen(1, rot_steps=list(w.rot_steps))
+    z = si.messages(100 + rank, 2 * B, w.slots)
+    seeds = si.enc_seeds(100 + rank, 2 * B)
+    cts = [ctx.encrypt(ctx.encode(z[i], level, scale), level, scale, seeds[i]) for i in range(2 * B)]
+    A, Bc = cts[:B], cts[B:]
+    OUT = [ctx.new_ct(level + 1) for _ in range(B)]
+    ROT = [ctx.new_ct(level + 1) for _ in range(B)]
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(marks=None):
+        if marks:
+            marks[0].record(stream)
+        ctx.mul_relin_batch(A, Bc, OUT, rescale=True)
+        if marks:
+            marks[1].record(stream)
+        for k in w.rot_steps:
+            ctx.rotate_batch(A, [k] * B, ROT)
+        if marks:
+            marks[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # correctness spot check of the timed configuration (first product only)
+    got = ctx.decrypt_decode(OUT[0])
+    err_mul = float(np.max(np.abs(got - z[0] * z[B])))
+    got = ctx.decrypt_decode(ROT[0])
+    err_rot = float(np.max(np.abs(got - np.roll(z[0], -w.rot_steps[-1]))))
+
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ctx.profile(True)
+    launches0 = ctx.launch_count()
+    marks = [[ev(), ev(), ev()] for _ in range(args.steps)]
+    torch.cuda.nvtx.range_push("timed")
+    for s in range(args.steps):
+        step(marks[s])
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    launches = ctx.launch_count() - launches0
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    barrier()
+    clk = clocks.stop()
+
+    mul_ms = sum(m[0].elapsed_time(m[1]) for m in marks)
+    rot_ms = sum(m[1].elapsed_time(m[2]) for m in marks)
+    step_ms = sum(m[0].elapsed_time(m[2]) for m in marks) / args.steps
+    t = torch.tensor([mul_ms, rot_ms, step_ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    mul_ms, rot_ms, step_ms = t.tolist()
+    value = world * B * args.steps / (mul_ms / 1e3)
+    rot_rate = world * B * len(w.rot_steps) * args.steps / (rot_ms / 1e3)
+
+    # roofline of the dominant kernel class
+    hbm, peak_kind = peaks()
+    mac_s, bfly_s = ctx.alu_peaks()
+    alu = {"mac_per_s": mac_s, "bfly_per_s": bfly_s}
+    ndig = -(-len(w.q_bits) // (-(-len(w.q_bits) // w.dnum)))
+    roof = roofline(prof, w, ndig, hbm, peak_kind, alu)
+
+    # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(ctx, torch, A, Bc, OUT, level, args, dist)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample = OracleSample(w)
+        dt, threads = sample.time(), sample.threads
+        cpu = {"value": 1.0 / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "1 HMult+relin+rescale of 1 ciphertext pair at N=2^16, L=24 (1/64 of the batch)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": config_of(w),
+                "rotations_per_s": rot_rate, "bootstraps_per_s": None,
+                "slot_error": {"hmult_rescale": err_mul, "rotation": err_rot},
+                "e2e": e2e, "roofline": roof, "alu_peaks": alu, "cpu_baseline": cpu, "clocks": clk,
+                "gpu_launches": int(launches),
+                "kernel_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]}}
+        print(json.dumps(line))
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(ctx, torch, A, Bc, OUT, level, args, dist):
+    """HMult+relin+rescale of the batch with inputs imported from pinned host
+    memory and results exported to pinned host memory, via ckks_ct_import /
+    ckks_ct_export, all inside the timed region."""
+    n = ctx.n
+    B = len(A)
+    host_in = [torch.empty((2, level + 1, n), dtype=torch.int64, pin_memory=True) for _ in range(2 * B)]
+    host_out = [torch.empty((2, level, n), dtype=torch.int64, pin_memory=True) for _ in range(B)]
+    for i, c in enumerate(A + Bc):
+        host_in[i].copy_(c.data[:, : level + 1])
+    steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for i, c in enumerate(A + Bc):
+            ctx.import_host(c, host_in[i])
+        ctx.mul_relin_batch(A, Bc, OUT, rescale=True)
+        for i, c in enumerate(OUT):
+            ctx.export_host(c, host_out[i])
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = t.item()
+    world = 1 if dist is None else dist.get_world_size()
+    h2d = 2 * B * 2 * (level + 1) * n * 8
+    d2h = B * 2 * level * n * 8
+    return {"value": world * B * steps / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "steps": steps, "clock": "host perf_counter around synchronised steps"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

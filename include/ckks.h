@@ -95,6 +95,28 @@ int ckks_ctx_digits(const ckks_ctx *ctx, int *n_digits, int *alpha);
 /* Bytes of device memory the context holds (tables, keys, scratch). */
 int ckks_ctx_device_bytes(const ckks_ctx *ctx, uint64_t *bytes);
 
+/* ---- launch accounting (no paper counterpart: measurement support) ----- */
+
+/* Enable (1) or disable (0) per-kernel-class device timing: when on, every
+ * kernel launch on the context stream is bracketed by a CUDA event pair.
+ * Enabling clears earlier records. */
+int ckks_ctx_profile(ckks_ctx *ctx, int enable);
+/* Fold the recorded event pairs (synchronises them) and copy, per kernel class
+ * k < min(cap, ckks_profile_kinds()), the summed device milliseconds, the
+ * launch count and the limbs processed since the last reset; then reset.
+ * Any of the three arrays may be NULL.  Returns the number of classes. */
+int ckks_ctx_profile_read(ckks_ctx *ctx, double *ms, uint64_t *launches, uint64_t *limbs, int cap);
+/* Number of kernel classes and the name of class k. */
+int ckks_profile_kinds(void);
+const char *ckks_profile_kind_name(int k);
+/* Total kernels this context has launched since creation. */
+int ckks_ctx_launch_count(const ckks_ctx *ctx, uint64_t *count);
+/* Integer-pipe peaks measured on this GPU by register-only kernels built from
+ * the production primitives: 64x64->128-bit multiply-accumulates per second
+ * and lazy Shoup butterflies per second (either pointer may be NULL).
+ * Synchronises the context stream; uses the context's scratch memory. */
+int ckks_alu_peaks(ckks_ctx *ctx, double *mac_per_s, double *bfly_per_s);
+
 /* ---- keys (Sec. 3: "one key corresponding to each desired rotation index") */
 
 /* Draw the ternary secret from `seed` and build the relinearisation key

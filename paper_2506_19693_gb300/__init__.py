@@ -51,6 +51,12 @@ SIGNATURES = {
     "ckks_ctx_roots": (_I, [_V, _V, _I]),
     "ckks_ctx_digits": (_I, [_V, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "ckks_ctx_device_bytes": (_I, [_V, ctypes.POINTER(_U64)]),
+    "ckks_ctx_profile": (_I, [_V, _I]),
+    "ckks_ctx_profile_read": (_I, [_V, _V, _V, _V, _I]),
+    "ckks_profile_kinds": (_I, []),
+    "ckks_profile_kind_name": (ctypes.c_char_p, [_I]),
+    "ckks_ctx_launch_count": (_I, [_V, ctypes.POINTER(_U64)]),
+    "ckks_alu_peaks": (_I, [_V, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "ckks_keygen_from_seed": (_I, [_V, _U64, _V, _I, _I, _I]),
     "ckks_keygen_galois": (_I, [_V, _U64]),
     "ckks_galois_elt": (_U64, [_V, ctypes.c_int32]),
@@ -189,6 +195,31 @@ class Context:
         b = ctypes.c_uint64()
         _check(self.lib.ckks_ctx_device_bytes(self._h, ctypes.byref(b)), "ckks_ctx_device_bytes")
         return b.value
+
+    # ---- launch accounting ----
+    def profile(self, enable: bool) -> None:
+        _check(self.lib.ckks_ctx_profile(self._h, int(enable)), "ckks_ctx_profile")
+
+    def profile_read(self) -> dict:
+        """{kernel class: (device ms, launches, limbs)} since the last read."""
+        k = self.lib.ckks_profile_kinds()
+        ms = np.zeros(k)
+        la = np.zeros(k, dtype=np.uint64)
+        li = np.zeros(k, dtype=np.uint64)
+        self.lib.ckks_ctx_profile_read(self._h, ms.ctypes.data, la.ctypes.data, li.ctypes.data, k)
+        return {self.lib.ckks_profile_kind_name(i).decode(): (float(ms[i]), int(la[i]), int(li[i]))
+                for i in range(k)}
+
+    def alu_peaks(self) -> tuple[float, float]:
+        """(64x64->128 MACs/s, Shoup butterflies/s) measured on this GPU."""
+        m, b = ctypes.c_double(), ctypes.c_double()
+        _check(self.lib.ckks_alu_peaks(self._h, ctypes.byref(m), ctypes.byref(b)), "ckks_alu_peaks")
+        return m.value, b.value
+
+    def launch_count(self) -> int:
+        c = ctypes.c_uint64()
+        _check(self.lib.ckks_ctx_launch_count(self._h, ctypes.byref(c)), "ckks_ctx_launch_count")
+        return c.value
 
     # ---- keys ----
     def keygen(self, seed: int, rot_steps=(), conj: bool = False) -> None:
@@ -361,6 +392,18 @@ class Context:
         h = ct.handle(self.log_n)
         _check(self.lib.ckks_ct_export(self._h, ctypes.byref(h), out.ctypes.data), "ckks_ct_export")
         return out
+
+    def export_host(self, ct: Ciphertext, host) -> None:
+        """Copy the active limbs into a (pinned) host torch tensor [2, level+1, N]."""
+        assert host.device.type == "cpu" and host.is_contiguous() and host.numel() >= 2 * (ct.level + 1) * self.n
+        h = ct.handle(self.log_n)
+        _check(self.lib.ckks_ct_export(self._h, ctypes.byref(h), host.data_ptr()), "ckks_ct_export")
+
+    def import_host(self, ct: Ciphertext, host) -> None:
+        """Fill ct's active limbs from a (pinned) host torch tensor [2, level+1, N]."""
+        assert host.device.type == "cpu" and host.is_contiguous() and host.numel() >= 2 * (ct.level + 1) * self.n
+        h = ct.handle(self.log_n)
+        _check(self.lib.ckks_ct_import(self._h, host.data_ptr(), ctypes.byref(h)), "ckks_ct_import")
 
     def import_ct(self, arr: np.ndarray, level: int, scale: float, n_limbs: int | None = None) -> Ciphertext:
         arr = np.ascontiguousarray(arr, dtype=np.uint64)

@@ -117,7 +117,8 @@ int galois_key(ckks_ctx *c, u64 g) {
   EwArgs a;
   a.x0[0] = c->d_s_ntt;
   a.o0[0] = sp;
-  int rc = ew_automorph(c, a, (u32)g, ext, 1, false);
+  const u32 g32 = (u32)g;
+  int rc = ew_automorph(c, a, &g32, ext, 1, false);
   DevKey k;
   if (!rc) rc = make_key(c, g, sp, &k);
   cudaStreamSynchronize(c->stream);
@@ -241,20 +242,22 @@ int automorph_chunk(ckks_ctx *c, const ckks_ct *in, const u64 *g, ckks_ct *out, 
   if (rc) return rc;
   std::vector<const u64 *> t1(n), t0(n);
   std::vector<u64 *> o0(n), o1(n);
+  std::vector<u32> g32(n);
+  EwArgs e;
   for (int i = 0; i < n; ++i) {
     u64 *tmp = c->scratch + (size_t)2 * nl * nn * i;
-    EwArgs e;
-    e.x0[0] = in[i].data;
-    e.x1[0] = poly1(&in[i], nn);
-    e.o0[0] = tmp;
-    e.o1[0] = tmp + (size_t)nl * nn;
-    rc = ew_automorph(c, e, (u32)g[i], nl, 1, true);
-    if (rc) return rc;
+    e.x0[i] = in[i].data;
+    e.x1[i] = poly1(&in[i], nn);
+    e.o0[i] = tmp;
+    e.o1[i] = tmp + (size_t)nl * nn;
+    g32[i] = (u32)g[i];
     t0[i] = tmp;
     t1[i] = tmp + (size_t)nl * nn;
     o0[i] = out[i].data;
     o1[i] = poly1(&out[i], nn);
   }
+  rc = ew_automorph(c, e, g32.data(), nl, n, true);
+  if (rc) return rc;
   std::vector<double> scales(n);
   for (int i = 0; i < n; ++i) scales[i] = in[i].scale;
   rc = ks_batch(c, level, n, t1.data(), keys.data(), t0.data(), nullptr, o0.data(), o1.data(),
@@ -372,6 +375,41 @@ int ckks_ctx_device_bytes(const ckks_ctx *c, uint64_t *bytes) {
   if (c->relin.data) b += key_words(c) * 8;
   b += c->galois.size() * key_words(c) * 8;
   *bytes = b;
+  return CKKS_OK;
+}
+
+int ckks_ctx_profile(ckks_ctx *c, int enable) {
+  if (!c) return CKKS_E_PARAM;
+  c->prof.reset();
+  c->prof.on = enable != 0;
+  return CKKS_OK;
+}
+
+int ckks_ctx_profile_read(ckks_ctx *c, double *ms, uint64_t *launches, uint64_t *limbs, int cap) {
+  if (!c || cap < 0) return CKKS_E_PARAM;
+  c->prof.collect();
+  const int m = std::min(cap, (int)PK_COUNT);
+  for (int k = 0; k < m; ++k) {
+    if (ms) ms[k] = c->prof.kind_ms[k];
+    if (launches) launches[k] = c->prof.kind_launches[k];
+    if (limbs) limbs[k] = c->prof.kind_units[k];
+  }
+  c->prof.reset();
+  return (int)PK_COUNT;
+}
+
+int ckks_profile_kinds(void) { return (int)PK_COUNT; }
+
+const char *ckks_profile_kind_name(int k) {
+  static const char *names[PK_COUNT] = {"ntt_fwd_pass_a", "ntt_fwd_pass_b", "ntt_inv_pass_a", "ntt_inv_pass_b",
+                                        "bconv", "ks_inner_product", "ks_moddown_combine", "tensor",
+                                        "automorph", "rescale", "elementwise", "encode_decode"};
+  return (k >= 0 && k < PK_COUNT) ? names[k] : "unknown";
+}
+
+int ckks_ctx_launch_count(const ckks_ctx *c, uint64_t *count) {
+  if (!c || !count) return CKKS_E_PARAM;
+  *count = c->prof.launches;
   return CKKS_OK;
 }
 

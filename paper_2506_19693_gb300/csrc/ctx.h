@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "prof.h"
 
 // A Galois or relinearisation key resident in HBM:
 // uint64[n_digits][2][n_q + n_p][N] (b_j, a_j), NTT domain.
@@ -67,6 +68,7 @@ struct ckks_ctx {
   void *pinned = nullptr;            // pinned host staging
   size_t pinned_bytes = 0;
   size_t table_bytes = 0;
+  Profiler prof;
 
   size_t limb_words() const { return (size_t)n; }
   int ext_limbs(int level) const { return level + 1 + n_p; }

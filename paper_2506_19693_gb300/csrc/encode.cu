@@ -134,7 +134,8 @@ __global__ void k_dec_gather(const double2 *g, u32 n, double inv_scale, double *
 void fft(ckks_ctx *c, double2 *x, double sign) {
   const u32 n = c->n;
   const u32 blocks = (n / 2 + TPB - 1) / TPB;
-  for (u32 half = 1; half < n; half <<= 1) k_fft_stage<<<blocks, TPB, 0, c->stream>>>(x, n, half, sign);
+  for (u32 half = 1; half < n; half <<= 1)
+    PROF_LAUNCH(c, PK_ENCODE, 1, (k_fft_stage<<<blocks, TPB, 0, c->stream>>>(x, n, half, sign)));
 }
 
 }  // namespace
@@ -154,10 +155,13 @@ extern "C" int ckks_encode(ckks_ctx *c, const double *re, const double *im, int 
   CK_CUDA(cudaMemcpyAsync(d_re, re, sizeof(double) * n_slots, cudaMemcpyHostToDevice, c->stream));
   if (im) CK_CUDA(cudaMemcpyAsync(d_im, im, sizeof(double) * n_slots, cudaMemcpyHostToDevice, c->stream));
   CK_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
-  k_enc_scatter<<<(n / 2 + TPB - 1) / TPB, TPB, 0, c->stream>>>(d_re, im ? d_im : nullptr, n_slots, x, n,
-                                                                 c->log_n);
+  PROF_LAUNCH(c, PK_ENCODE, 1,
+              (k_enc_scatter<<<(n / 2 + TPB - 1) / TPB, TPB, 0, c->stream>>>(d_re, im ? d_im : nullptr, n_slots,
+                                                                              x, n, c->log_n)));
   fft(c, x, -1.0);
-  k_enc_finish<<<(n + TPB - 1) / TPB, TPB, 0, c->stream>>>(x, n, scale, c->d_mods, level + 1, pt_dev, flag);
+  PROF_LAUNCH(c, PK_ENCODE, level + 1,
+              (k_enc_finish<<<(n + TPB - 1) / TPB, TPB, 0, c->stream>>>(x, n, scale, c->d_mods, level + 1, pt_dev,
+                                                                         flag)));
   int mods[MAX_MODS];
   for (int l = 0; l <= (int)level; ++l) mods[l] = l;
   const u64 *src[1] = {pt_dev};
@@ -189,11 +193,13 @@ extern "C" int ckks_decode(ckks_ctx *c, const uint64_t *pt_dev, uint32_t level, 
   if (rc) return rc;
   double *d_re = c->fscratch, *d_im = d_re + n / 2;
   double2 *x = reinterpret_cast<double2 *>(c->fscratch + n);
-  k_dec_crt<<<(n + TPB - 1) / TPB, TPB, 0, c->stream>>>(coef, level, n, c->log_n, c->d_mods,
-                                                         c->d_conv + c->conv.garner_inv,
-                                                         c->d_conv + c->conv.halfq_digits, c->n_q, x);
+  PROF_LAUNCH(c, PK_ENCODE, level + 1,
+              (k_dec_crt<<<(n + TPB - 1) / TPB, TPB, 0, c->stream>>>(coef, level, n, c->log_n, c->d_mods,
+                                                                      c->d_conv + c->conv.garner_inv,
+                                                                      c->d_conv + c->conv.halfq_digits, c->n_q, x)));
   fft(c, x, 1.0);
-  k_dec_gather<<<(n / 2 + TPB - 1) / TPB, TPB, 0, c->stream>>>(x, n, 1.0 / scale, d_re, d_im, n_slots);
+  PROF_LAUNCH(c, PK_ENCODE, 1,
+              (k_dec_gather<<<(n / 2 + TPB - 1) / TPB, TPB, 0, c->stream>>>(x, n, 1.0 / scale, d_re, d_im, n_slots)));
   CK_CUDA(cudaMemcpyAsync(re, d_re, sizeof(double) * n_slots, cudaMemcpyDeviceToHost, c->stream));
   CK_CUDA(cudaMemcpyAsync(im, d_im, sizeof(double) * n_slots, cudaMemcpyDeviceToHost, c->stream));
   CK_CUDA(cudaStreamSynchronize(c->stream));

@@ -137,7 +137,8 @@ int launch_bconv(ckks_ctx *c, BConvArgs &a, int ns, int np) {
   a.n = c->n;
   dim3 g((c->n + TPB - 1) / TPB, np);
   switch (ns) {
-#define CASE(S) case S: k_bconv<S><<<g, TPB, 0, c->stream>>>(a); break;
+#define CASE(S) \
+  case S: PROF_LAUNCH(c, PK_BCONV, (u64)np * a.nt * S, (k_bconv<S><<<g, TPB, 0, c->stream>>>(a))); break;
     CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
     CASE(9) CASE(10) CASE(11) CASE(12) CASE(13) CASE(14) CASE(15) CASE(16)
 #undef CASE
@@ -237,7 +238,7 @@ int ks_batch(ckks_ctx *c, int level, int np, const u64 *const *d, const u64 *con
       a.acc[i] = acc[i];
     }
     dim3 g((n + TPB - 1) / TPB, ext);
-    k_inner<<<g, TPB, 0, c->stream>>>(a);
+    PROF_LAUNCH(c, PK_INNER, (u64)np * ext, (k_inner<<<g, TPB, 0, c->stream>>>(a)));
     if (cudaGetLastError() != cudaSuccess) return CKKS_E_CUDA;
   }
   // 4. ModDown
@@ -291,7 +292,7 @@ int ks_batch(ckks_ctx *c, int level, int np, const u64 *const *d, const u64 *con
       a.o1[i] = o1[i];
     }
     dim3 g((n + TPB - 1) / TPB, nl, np);
-    k_combine<<<g, TPB, 0, c->stream>>>(a, nl);
+    PROF_LAUNCH(c, PK_COMBINE, (u64)np * nl, (k_combine<<<g, TPB, 0, c->stream>>>(a, nl)));
     if (cudaGetLastError() != cudaSuccess) return CKKS_E_CUDA;
   }
   return CKKS_OK;

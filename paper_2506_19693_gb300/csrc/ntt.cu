@@ -221,16 +221,18 @@ __global__ void __launch_bounds__(THREADS) inv_pass_a(const NttParams prm) {
 }
 
 template <int LH>
-void launch_lh(const NttParams &prm, int npoly, bool inverse, cudaStream_t st) {
+void launch_lh(ckks_ctx *c, const NttParams &prm, int npoly, bool inverse) {
   constexpr int S1 = (LH + 1) / 2;
   const int H = 1 << LH;
+  cudaStream_t st = c->stream;
+  const unsigned long long units = (unsigned long long)prm.n_limbs * npoly;
   dim3 ga(BROW / CA, prm.n_limbs, npoly), gb(H / RB, prm.n_limbs, npoly);
   if (!inverse) {
-    fwd_pass_a<LH, S1><<<ga, THREADS, 0, st>>>(prm);
-    fwd_pass_b<LH><<<gb, THREADS, 0, st>>>(prm, 0);
+    PROF_LAUNCH(c, PK_NTT_FWD_A, units, (fwd_pass_a<LH, S1><<<ga, THREADS, 0, st>>>(prm)));
+    PROF_LAUNCH(c, PK_NTT_FWD_B, units, (fwd_pass_b<LH><<<gb, THREADS, 0, st>>>(prm, 0)));
   } else {
-    inv_pass_b<LH><<<gb, THREADS, 0, st>>>(prm);
-    inv_pass_a<LH, S1><<<ga, THREADS, 0, st>>>(prm);
+    PROF_LAUNCH(c, PK_NTT_INV_B, units, (inv_pass_b<LH><<<gb, THREADS, 0, st>>>(prm)));
+    PROF_LAUNCH(c, PK_NTT_INV_A, units, (inv_pass_a<LH, S1><<<ga, THREADS, 0, st>>>(prm)));
   }
 }
 
@@ -253,13 +255,13 @@ int launch_ntt(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, i
       prm.dst.p[i] = dst[p0 + i];
     }
     switch (c->log_n - LB) {
-      case 2: launch_lh<2>(prm, cnt, inverse, c->stream); break;
-      case 3: launch_lh<3>(prm, cnt, inverse, c->stream); break;
-      case 4: launch_lh<4>(prm, cnt, inverse, c->stream); break;
-      case 5: launch_lh<5>(prm, cnt, inverse, c->stream); break;
-      case 6: launch_lh<6>(prm, cnt, inverse, c->stream); break;
-      case 7: launch_lh<7>(prm, cnt, inverse, c->stream); break;
-      case 8: launch_lh<8>(prm, cnt, inverse, c->stream); break;
+      case 2: launch_lh<2>(c, prm, cnt, inverse); break;
+      case 3: launch_lh<3>(c, prm, cnt, inverse); break;
+      case 4: launch_lh<4>(c, prm, cnt, inverse); break;
+      case 5: launch_lh<5>(c, prm, cnt, inverse); break;
+      case 6: launch_lh<6>(c, prm, cnt, inverse); break;
+      case 7: launch_lh<7>(c, prm, cnt, inverse); break;
+      case 8: launch_lh<8>(c, prm, cnt, inverse); break;
       default: return CKKS_E_PARAM;
     }
   }

@@ -95,10 +95,14 @@ __global__ void k_tensor(EwArgs a, D2Ptrs d2) {
 
 // automorphism X -> X^g in the canonical NTT order (C11):
 // out[j] = in[j'] with 2 brv(j') + 1 = g (2 brv(j) + 1) mod 2N.
-__global__ void k_automorph(EwArgs a, u32 g, int log_n, int both) {
+struct Gal {
+  u32 g[MAX_CTS];
+};
+__global__ void k_automorph(EwArgs a, Gal gal, int log_n, int both) {
   const u32 j = blockIdx.x * TPB + threadIdx.x;
   const int l = blockIdx.y, c = blockIdx.z;
   if (j >= a.n) return;
+  const u32 g = gal.g[c];
   const u32 mask = 2 * a.n - 1;
   const u32 e = (u32)(((u64)g * (2 * brv_dev(j, log_n) + 1)) & mask);
   const u32 jp = brv_dev((e - 1) >> 1, log_n);
@@ -199,19 +203,22 @@ int last_status() { return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_
 int ew_addsub(ckks_ctx *c, EwArgs &a, int nl, int ncts, bool sub) {
   a.mods = c->d_mods;
   a.n = c->n;
-  k_addsub<<<grid_for(c->n, nl, ncts), TPB, 0, c->stream>>>(a, sub ? 1 : 0);
+  PROF_LAUNCH(c, PK_ELEMENTWISE, (u64)nl * ncts,
+              (k_addsub<<<grid_for(c->n, nl, ncts), TPB, 0, c->stream>>>(a, sub ? 1 : 0)));
   return last_status();
 }
 int ew_plain(ckks_ctx *c, EwArgs &a, int nl, int ncts, int mode) {
   a.mods = c->d_mods;
   a.n = c->n;
-  k_plain<<<grid_for(c->n, nl, ncts), TPB, 0, c->stream>>>(a, mode);
+  PROF_LAUNCH(c, PK_ELEMENTWISE, (u64)nl * ncts,
+              (k_plain<<<grid_for(c->n, nl, ncts), TPB, 0, c->stream>>>(a, mode)));
   return last_status();
 }
 int ew_mul_int(ckks_ctx *c, EwArgs &a, int nl, int ncts, i64 k) {
   a.mods = c->d_mods;
   a.n = c->n;
-  k_mul_int<<<grid_for(c->n, nl, ncts), TPB, 0, c->stream>>>(a, k);
+  PROF_LAUNCH(c, PK_ELEMENTWISE, (u64)nl * ncts,
+              (k_mul_int<<<grid_for(c->n, nl, ncts), TPB, 0, c->stream>>>(a, k)));
   return last_status();
 }
 int ew_tensor(ckks_ctx *c, EwArgs &a, u64 *const *d2, int nl, int ncts) {
@@ -219,52 +226,59 @@ int ew_tensor(ckks_ctx *c, EwArgs &a, u64 *const *d2, int nl, int ncts) {
   a.n = c->n;
   D2Ptrs d;
   for (int i = 0; i < ncts; ++i) d.p[i] = d2[i];
-  k_tensor<<<grid_for(c->n, nl, ncts), TPB, 0, c->stream>>>(a, d);
+  PROF_LAUNCH(c, PK_TENSOR, (u64)nl * ncts, (k_tensor<<<grid_for(c->n, nl, ncts), TPB, 0, c->stream>>>(a, d)));
   return last_status();
 }
-int ew_automorph(ckks_ctx *c, EwArgs &a, u32 g, int nl, int ncts, bool both_polys) {
+int ew_automorph(ckks_ctx *c, EwArgs &a, const u32 *g, int nl, int ncts, bool both_polys) {
   a.mods = c->d_mods;
   a.n = c->n;
-  k_automorph<<<grid_for(c->n, nl, ncts), TPB, 0, c->stream>>>(a, g, c->log_n, both_polys ? 1 : 0);
+  Gal gal;
+  for (int i = 0; i < ncts; ++i) gal.g[i] = g[i];
+  PROF_LAUNCH(c, PK_AUTOMORPH, (u64)nl * ncts * (both_polys ? 2 : 1),
+              (k_automorph<<<grid_for(c->n, nl, ncts), TPB, 0, c->stream>>>(a, gal, c->log_n, both_polys ? 1 : 0)));
   return last_status();
 }
 int ew_decrypt(ckks_ctx *c, EwArgs &a, int nl, int ncts) {
   a.mods = c->d_mods;
   a.n = c->n;
-  k_decrypt<<<grid_for(c->n, nl, ncts), TPB, 0, c->stream>>>(a, c->d_s_ntt);
+  PROF_LAUNCH(c, PK_ELEMENTWISE, (u64)nl * ncts,
+              (k_decrypt<<<grid_for(c->n, nl, ncts), TPB, 0, c->stream>>>(a, c->d_s_ntt)));
   return last_status();
 }
 int ew_rescale_lift(ckks_ctx *c, RescaleArgs &r, int ncts) {
   r.mods = c->d_mods;
   r.n = c->n;
-  k_rescale_lift<<<grid_for(c->n, r.level, ncts), TPB, 0, c->stream>>>(r);
+  PROF_LAUNCH(c, PK_RESCALE, (u64)r.level * ncts,
+              (k_rescale_lift<<<grid_for(c->n, r.level, ncts), TPB, 0, c->stream>>>(r)));
   return last_status();
 }
 int ew_rescale_finish(ckks_ctx *c, RescaleArgs &r, int ncts) {
   r.mods = c->d_mods;
   r.n = c->n;
-  k_rescale_finish<<<grid_for(c->n, r.level, ncts), TPB, 0, c->stream>>>(r);
+  PROF_LAUNCH(c, PK_RESCALE, (u64)r.level * ncts,
+              (k_rescale_finish<<<grid_for(c->n, r.level, ncts), TPB, 0, c->stream>>>(r)));
   return last_status();
 }
 int ew_encrypt(ckks_ctx *c, EncArgs &e, int nl, int ncts) {
   e.mods = c->d_mods;
   e.n = c->n;
   e.s_ntt = c->d_s_ntt;
-  k_encrypt<<<grid_for(c->n, nl, ncts), TPB, 0, c->stream>>>(e);
+  PROF_LAUNCH(c, PK_ELEMENTWISE, (u64)nl * ncts, (k_encrypt<<<grid_for(c->n, nl, ncts), TPB, 0, c->stream>>>(e)));
   return last_status();
 }
 int ew_signed_to_res(ckks_ctx *c, const i64 *v, u64 *out, int first_mod, int nl) {
-  k_signed_to_res<<<grid_for(c->n, nl, 1), TPB, 0, c->stream>>>(v, out, c->d_mods, first_mod, c->n);
+  PROF_LAUNCH(c, PK_ELEMENTWISE, (u64)nl,
+              (k_signed_to_res<<<grid_for(c->n, nl, 1), TPB, 0, c->stream>>>(v, out, c->d_mods, first_mod, c->n)));
   return last_status();
 }
 int ew_keyrow(ckks_ctx *c, KeyArgs &k, int nl) {
   k.mods = c->d_mods;
   k.n = c->n;
   k.s_ntt = c->d_s_ntt;
-  k_keyrow<<<grid_for(c->n, nl, 1), TPB, 0, c->stream>>>(k);
+  PROF_LAUNCH(c, PK_ELEMENTWISE, (u64)nl, (k_keyrow<<<grid_for(c->n, nl, 1), TPB, 0, c->stream>>>(k)));
   return last_status();
 }
 int ew_square(ckks_ctx *c, u64 *out, const u64 *in, int nl) {
-  k_square<<<grid_for(c->n, nl, 1), TPB, 0, c->stream>>>(out, in, c->d_mods, c->n);
+  PROF_LAUNCH(c, PK_ELEMENTWISE, (u64)nl, (k_square<<<grid_for(c->n, nl, 1), TPB, 0, c->stream>>>(out, in, c->d_mods, c->n)));
   return last_status();
 }

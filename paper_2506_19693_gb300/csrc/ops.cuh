@@ -50,7 +50,8 @@ int ew_addsub(ckks_ctx *c, EwArgs &a, int nl, int ncts, bool sub);
 int ew_plain(ckks_ctx *c, EwArgs &a, int nl, int ncts, int mode);  // 0 mul, 1 add
 int ew_mul_int(ckks_ctx *c, EwArgs &a, int nl, int ncts, i64 k);
 int ew_tensor(ckks_ctx *c, EwArgs &a, u64 *const *d2, int nl, int ncts);
-int ew_automorph(ckks_ctx *c, EwArgs &a, u32 g, int nl, int ncts, bool both_polys);
+// g[i]: Galois element applied to ciphertext i
+int ew_automorph(ckks_ctx *c, EwArgs &a, const u32 *g, int nl, int ncts, bool both_polys);
 int ew_decrypt(ckks_ctx *c, EwArgs &a, int nl, int ncts);
 int ew_rescale_lift(ckks_ctx *c, RescaleArgs &r, int ncts);
 int ew_rescale_finish(ckks_ctx *c, RescaleArgs &r, int ncts);

@@ -1,0 +1,87 @@
+// Per-kernel-class launch accounting: a launch counter that is always on and,
+// when enabled, a CUDA event pair around every launch on the context stream so
+// that device time per kernel class can be read back (ckks_ctx_profile_read).
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+enum ProfKind {
+  PK_NTT_FWD_A = 0,
+  PK_NTT_FWD_B,
+  PK_NTT_INV_A,
+  PK_NTT_INV_B,
+  PK_BCONV,
+  PK_INNER,
+  PK_COMBINE,
+  PK_TENSOR,
+  PK_AUTOMORPH,
+  PK_RESCALE,
+  PK_ELEMENTWISE,
+  PK_ENCODE,
+  PK_COUNT
+};
+
+struct Profiler {
+  bool on = false;
+  unsigned long long launches = 0;
+  unsigned long long kind_launches[PK_COUNT] = {0};
+  // work units per class: limbs processed, except basis conversion, which
+  // counts multiply-accumulates per coefficient (polys x targets x sources)
+  unsigned long long kind_units[PK_COUNT] = {0};
+  std::vector<cudaEvent_t> pool;
+  struct Rec {
+    int kind;
+    int ev;  // index of start event; stop is ev + 1
+  };
+  std::vector<Rec> recs;
+  double kind_ms[PK_COUNT] = {0};
+
+  int begin(int kind, unsigned long long units, cudaStream_t st) {
+    ++launches;
+    ++kind_launches[kind];
+    kind_units[kind] += units;
+    if (!on) return -1;
+    const size_t need = 2 * (recs.size() + 1);
+    while (pool.size() < need) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      pool.push_back(e);
+    }
+    const int ev = (int)(2 * recs.size());
+    cudaEventRecord(pool[ev], st);
+    recs.push_back({kind, ev});
+    return ev;
+  }
+  void end(int ev, cudaStream_t st) {
+    if (ev >= 0) cudaEventRecord(pool[ev + 1], st);
+  }
+  // fold recorded pairs into kind_ms (synchronises the events)
+  void collect() {
+    for (const Rec &r : recs) {
+      float ms = 0.f;
+      cudaEventSynchronize(pool[r.ev + 1]);
+      if (cudaEventElapsedTime(&ms, pool[r.ev], pool[r.ev + 1]) == cudaSuccess) kind_ms[r.kind] += ms;
+    }
+    recs.clear();
+  }
+  void reset() {
+    collect();
+    for (int k = 0; k < PK_COUNT; ++k) {
+      kind_ms[k] = 0;
+      kind_launches[k] = 0;
+      kind_units[k] = 0;
+    }
+  }
+  ~Profiler() {
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+};
+
+#define PROF_LAUNCH(ctx, kind, units, launch_stmt)                  \
+  do {                                                               \
+    const int _ev = (ctx)->prof.begin((kind), (units), (ctx)->stream); \
+    launch_stmt;                                                     \
+    (ctx)->prof.end(_ev, (ctx)->stream);                             \
+  } while (0)
