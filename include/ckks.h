@@ -188,6 +188,22 @@ int ckks_rescale(ckks_ctx *ctx, ckks_ct *inout);
 /* Rot(a, k): left cyclic shift of the slots by k (Sec. 3), via
  * X -> X^(5^k mod 2N) and key switching (reading C11). */
 int ckks_rotate(ckks_ctx *ctx, const ckks_ct *a, int32_t k, ckks_ct *out);
+/* Rescale that allocates nothing.  The paper has no counterpart: this exists
+ * for callers that cannot let the library call cudaMalloc -- a process whose
+ * device memory is capped or handed out by its own pool allocator, or a
+ * latency-bound path that cannot accept an allocation's implicit
+ * synchronisation.  ckks_rescale may grow the context's scratch buffer; this
+ * variant gives the same limbs (same arithmetic) using a fixed 5 MiB
+ * workspace in a file-scope device array that every GPU loading the library
+ * holds until exit.  Limit: N <= 2^16 (larger rings return CKKS_E_PARAM); any
+ * level.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current -- make that first call
+ * before any stream capture.  All calls share the array, so calls whose GPU
+ * work overlaps (other streams or threads) race; nothing in it must start at
+ * zero.  The current device must be the context's.  In place, like
+ * ckks_rescale; CKKS_E_LEVEL at level 0.  Allocates no device memory as long
+ * as event profiling (ckks_ctx_profile) is off. */
+int ckks_rescale_noalloc(ckks_ctx *ctx, ckks_ct *inout);
 /* Complex conjugation of every slot (X -> X^(2N-1)). */
 int ckks_conjugate(ckks_ctx *ctx, const ckks_ct *a, ckks_ct *out);
 /* Apply the automorphism X -> X^g (g odd, < 2N) and switch back to s. */

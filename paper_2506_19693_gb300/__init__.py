@@ -75,6 +75,7 @@ SIGNATURES = {
     "ckks_mul_int": (_I, [_V, _CTP, ctypes.c_int64, _CTP]),
     "ckks_mul_relin": (_I, [_V, _CTP, _CTP, _CTP]),
     "ckks_rescale": (_I, [_V, _CTP]),
+    "ckks_rescale_noalloc": (_I, [_V, _CTP]),
     "ckks_rotate": (_I, [_V, _CTP, ctypes.c_int32, _CTP]),
     "ckks_conjugate": (_I, [_V, _CTP, _CTP]),
     "ckks_automorph": (_I, [_V, _CTP, _U64, _CTP]),
@@ -336,6 +337,14 @@ class Context:
         """In place: drops the top prime."""
         h = a.handle(self.log_n)
         _check(self.lib.ckks_rescale(self._h, ctypes.byref(h)), "ckks_rescale")
+        a.level, a.scale = h.level, h.scale
+        return a
+
+    def rescale_noalloc(self, a: Ciphertext) -> Ciphertext:
+        """In place, like rescale(), without any device allocation (fixed
+        workspace inside the library; concurrent calls race)."""
+        h = a.handle(self.log_n)
+        _check(self.lib.ckks_rescale_noalloc(self._h, ctypes.byref(h)), "ckks_rescale_noalloc")
         a.level, a.scale = h.level, h.scale
         return a
 
