@@ -102,6 +102,7 @@ def _load():
         "oc_rescale": (P, [V, _u64p, P, _u64p]),
         "oc_automorph": (P, [V, _u64p, P, ctypes.c_uint64, _u64p]),
         "oc_automorph_coeff": (None, [V, _u64p, P, _ip, ctypes.c_uint64, _u64p]),
+        "oc_rotate_hoisted": (P, [V, _u64p, P, P, _u64p, _u64p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -420,6 +421,15 @@ class Oracle:
 
     def rotate(self, a: OCt, k: int) -> OCt:
         return self.automorph(a, self.galois_elt(k))
+
+    def rotate_hoisted(self, a: OCt, steps) -> list:
+        """Rotations of one ciphertext by every k in steps sharing one ModUp."""
+        gs = np.array([self.galois_elt(k) for k in steps], dtype=np.uint64)
+        outs = np.zeros((len(steps), 2, a.level + 1, self.n), dtype=np.uint64)
+        if self._lib.oc_rotate_hoisted(self._c, _p64(np.ascontiguousarray(a.data)), a.level, len(steps),
+                                       _p64(gs), _p64(outs)) != 0:
+            raise KeyError("galois key")
+        return [OCt(np.ascontiguousarray(outs[i]), a.level, a.scale) for i in range(len(steps))]
 
     def conjugate(self, a: OCt) -> OCt:
         return self.automorph(a, self.conj_elt())

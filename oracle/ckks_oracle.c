@@ -629,22 +629,27 @@ void oc_bconv(const oc_ctx *c, const u64 *x, int n_src, const int *src, u64 *y, 
 /* d: NTT-domain polynomial over q_0..q_level; key: [n_digits][2][n_q+n_p][N].   */
 /* out0/out1: NTT domain over q_0..q_level, with out0 + out1 s ~ d s'. */
 /* ------------------------------------------------------------------ */
-static void keyswitch(const oc_ctx *c, const u64 *d, int level, const u64 *key, u64 *out0, u64 *out1) {
+static void ext_basis(const oc_ctx *c, int level, int *ext_mods) {
+  for (int t = 0; t <= level; t++) ext_mods[t] = t;
+  for (int t = 0; t < c->n_p; t++) ext_mods[level + 1 + t] = c->n_q + t;
+}
+
+/* C7/C8 ModUp: digits[j] = NTT-domain lift of digit j of d to q_0..q_level, P;
+ * its own limbs are d's, the others come from BConv.  Returns the number of
+ * active digits; digits is [n_digits][level+1+n_p][N]. */
+static int modup(const oc_ctx *c, const u64 *d, int level, u64 *digits) {
   u64 n = c->n;
-  int nl = level + 1, np = c->n_p, ext = nl + np, key_ext = c->n_q + c->n_p;
+  int nl = level + 1, ext = nl + c->n_p, nact = 0;
   int ext_mods[OC_MAXMOD];
-  for (int t = 0; t < nl; t++) ext_mods[t] = t;
-  for (int t = 0; t < np; t++) ext_mods[nl + t] = c->n_q + t;
+  ext_basis(c, level, ext_mods);
   u64 *dc = (u64 *)malloc(sizeof(u64) * (u64)nl * n);
   memcpy(dc, d, sizeof(u64) * (u64)nl * n);
   oc_intt(c, dc, nl, ext_mods);
-  u64 *acc = (u64 *)calloc((u64)2 * ext * n, sizeof(u64));
-  u64 *dig = (u64 *)malloc(sizeof(u64) * (u64)ext * n);
   for (int j = 0; j < c->n_digits; j++) {
     int lo = j * c->alpha, hi = (j + 1) * c->alpha;
     if (hi > nl) hi = nl;
     if (lo >= hi) break;
-    /* ModUp of digit j: its own limbs are kept, the others come from BConv */
+    u64 *dig = digits + (u64)j * ext * n;
     int src[OC_MAXMOD], dst[OC_MAXMOD], dst_pos[OC_MAXMOD], n_src = hi - lo, n_dst = 0;
     for (int i = lo; i < hi; i++) src[i - lo] = i;
     for (int t = 0; t < ext; t++)
@@ -655,7 +660,23 @@ static void keyswitch(const oc_ctx *c, const u64 *d, int level, const u64 *key, 
     for (int i = lo; i < hi; i++) memcpy(dig + (u64)i * n, d + (u64)i * n, sizeof(u64) * n);
     for (int k = 0; k < n_dst; k++) memcpy(dig + (u64)dst_pos[k] * n, conv + (u64)k * n, sizeof(u64) * n);
     free(conv);
-    /* inner product with evk_j = (b_j, a_j); key limbs above the level are skipped */
+    nact++;
+  }
+  free(dc);
+  return nact;
+}
+
+/* inner product of the lifted digits with evk = (b_j, a_j), then ModDown (C9) */
+static void inner_moddown(const oc_ctx *c, const u64 *digits, int nact, int level, const u64 *key, u64 *out0,
+                          u64 *out1) {
+  u64 n = c->n;
+  int nl = level + 1, np = c->n_p, ext = nl + np, key_ext = c->n_q + c->n_p;
+  int ext_mods[OC_MAXMOD];
+  ext_basis(c, level, ext_mods);
+  u64 *acc = (u64 *)calloc((u64)2 * ext * n, sizeof(u64));
+  for (int j = 0; j < nact; j++) {
+    const u64 *dig = digits + (u64)j * ext * n;
+    /* key limbs above the level are skipped */
     const u64 *bj = key + ((u64)j * 2 + 0) * key_ext * n;
     const u64 *aj = key + ((u64)j * 2 + 1) * key_ext * n;
     for (int t = 0; t < ext; t++) {
@@ -668,7 +689,6 @@ static void keyswitch(const oc_ctx *c, const u64 *d, int level, const u64 *key, 
       }
     }
   }
-  free(dig);
   /* C9: ModDown, out_i = (x_i - BConv_{P->Q}(x_P)_i) * P^-1 mod q_i */
   int psrc[OC_MAXMOD], qdst[OC_MAXMOD];
   for (int t = 0; t < np; t++) psrc[t] = c->n_q + t;
@@ -695,7 +715,63 @@ static void keyswitch(const oc_ctx *c, const u64 *d, int level, const u64 *key, 
   free(xp);
   free(z);
   free(acc);
-  free(dc);
+}
+
+static void keyswitch(const oc_ctx *c, const u64 *d, int level, const u64 *key, u64 *out0, u64 *out1) {
+  int ext = level + 1 + c->n_p;
+  u64 *digits = (u64 *)malloc(sizeof(u64) * (u64)c->n_digits * ext * c->n);
+  int nact = modup(c, d, level, digits);
+  inner_moddown(c, digits, nact, level, key, out0, out1);
+  free(digits);
+}
+
+/* sigma_g of NTT-domain limbs: back to coefficients, X^i -> X^(ig), forward again */
+static void automorph_ntt_limbs(const oc_ctx *c, const u64 *in, int n_limbs, const int *mods, u64 g, u64 *out) {
+  u64 n = c->n;
+  u64 *tmp = (u64 *)malloc(sizeof(u64) * (u64)n_limbs * n);
+  memcpy(tmp, in, sizeof(u64) * (u64)n_limbs * n);
+  oc_intt(c, tmp, n_limbs, mods);
+  for (int l = 0; l < n_limbs; l++) automorph_limb(c, tmp + (u64)l * n, g, c->mod[mods[l]], out + (u64)l * n);
+  oc_ntt(c, out, n_limbs, mods);
+  free(tmp);
+}
+
+/* Hoisted rotations (Halevi-Shoup): one ModUp of c1 serves every Galois
+ * element g in gs.  For each g the lifted digits are mapped by sigma_g, then
+ * inner product with the key of g and ModDown: out_g = (sigma_g(c0) + u0, u1).
+ * outs: [n_g][2][level+1][N]. */
+int oc_rotate_hoisted(const oc_ctx *c, const u64 *in, int level, int n_g, const u64 *gs, u64 *outs) {
+  for (int i = 0; i < n_g; i++)
+    if (!find_key(c, gs[i])) return -1;
+  u64 n = c->n;
+  int nl = level + 1, ext = nl + c->n_p;
+  int ext_mods[OC_MAXMOD];
+  ext_basis(c, level, ext_mods);
+  u64 *digits = (u64 *)malloc(sizeof(u64) * (u64)c->n_digits * ext * n);
+  u64 *pdig = (u64 *)malloc(sizeof(u64) * (u64)c->n_digits * ext * n);
+  u64 *u0 = (u64 *)malloc(sizeof(u64) * (u64)nl * n);
+  u64 *u1 = (u64 *)malloc(sizeof(u64) * (u64)nl * n);
+  u64 *s0 = (u64 *)malloc(sizeof(u64) * (u64)nl * n);
+  int nact = modup(c, in + (u64)nl * n, level, digits);
+  for (int i = 0; i < n_g; i++) {
+    for (int j = 0; j < nact; j++)
+      automorph_ntt_limbs(c, digits + (u64)j * ext * n, ext, ext_mods, gs[i], pdig + (u64)j * ext * n);
+    inner_moddown(c, pdig, nact, level, find_key(c, gs[i])->data, u0, u1);
+    automorph_ntt_limbs(c, in, nl, ext_mods, gs[i], s0);
+    u64 *o = outs + (u64)i * 2 * nl * n;
+    for (int t = 0; t < nl; t++)
+      for (u64 x = 0; x < n; x++) {
+        u64 k = (u64)t * n + x;
+        o[k] = addmod(s0[k], u0[k], c->mod[t]);
+        o[(u64)nl * n + k] = u1[k];
+      }
+  }
+  free(digits);
+  free(pdig);
+  free(u0);
+  free(u1);
+  free(s0);
+  return 0;
 }
 
 /* expose key switching for tests: galois = 0 selects the relinearisation key */

@@ -61,6 +61,16 @@ MID = Workload("n8192_L8_dnum3", 13, (61,) + (55,) * 7, (61,) * 3, 3, 55.0,
                batch=2, rot_steps=(1, 8))
 
 
+# Bootstrapping chain (25 ciphertext primes = base + 24 levels, Table 3's l = 24):
+# q0 ~ 2^60 (message ratio Delta/q0 = 2^-10), q1..q8 ~ 2^50 for the user's
+# 8 levels (Table 3's tau_ReBoot = 8), q9..q11 ~ 2^50 for SlotToCoeff,
+# q12..q21 ~ 2^60 for EvalMod (scale ~ q0 stays put), q22..q24 ~ 2^60 for
+# CoeffToSlot; 9 special primes of 61 bits (alpha = ceil(25/3)), dnum = 3.
+BOOT_Q_BITS = (60,) + (50,) * 11 + (60,) * 13
+BOOT = Workload("n65536_boot_L24_dnum3_b16", 16, BOOT_Q_BITS, (61,) * 9, 3, 50.0, batch=16)
+BOOT_SMALL = Workload("n4096_boot_L24_dnum3", 12, BOOT_Q_BITS, (61,) * 9, 3, 50.0, batch=2)
+
+
 def rng(seed: int, stream: str) -> np.random.Generator:
     """An independent numpy generator per (seed, stream name)."""
     tag = int.from_bytes(stream.encode()[:8].ljust(8, b"\0"), "little")
