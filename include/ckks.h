@@ -122,7 +122,8 @@ int ckks_alu_peaks(ckks_ctx *ctx, double *mac_per_s, double *bfly_per_s);
 /* Draw the ternary secret from `seed` and build the relinearisation key
  * (s^2 -> s) plus one Galois key per rotation step in rot_steps[0..n_rot)
  * (left rotation by k, g = 5^(k mod N/2) mod 2N), the conjugation key when
- * want_conj.  want_boot must be 0 (CKKS_E_STATE otherwise).  Randomness:
+ * want_conj, and, when want_boot, the conjugation key and every rotation key
+ * the bootstrapping circuit uses (ckks_boot_rotation_steps).  Randomness:
  * counter-based SplitMix64 keyed by seed (reading C4).  Replaces earlier keys. */
 int ckks_keygen_from_seed(ckks_ctx *ctx, uint64_t seed, const int32_t *rot_steps, int n_rot,
                           int want_conj, int want_boot);
@@ -209,6 +210,39 @@ int ckks_conjugate(ckks_ctx *ctx, const ckks_ct *a, ckks_ct *out);
 /* Apply the automorphism X -> X^g (g odd, < 2N) and switch back to s. */
 int ckks_automorph(ckks_ctx *ctx, const ckks_ct *a, uint64_t galois_elt, ckks_ct *out);
 
+/* ---- bootstrapping (Sec. 3 last paragraph; Alg. 1; Sec. 5.1: tau_bs = 16) --- */
+
+/* Build the bootstrapping circuit for this parameter set (needs n_q >= 17)
+ * and generate its constants on the GPU in FP64: the diagonals of the three
+ * CoeffToSlot and three SlotToCoeff levels of the special DFT (readings
+ * B2-B4), encoded at the scale of the prime each level drops, and the
+ * degree-60 Chebyshev coefficients of EvalMod (B6).  Run once per context,
+ * before ckks_bootstrap; keys come from ckks_keygen_from_seed(want_boot=1). */
+int ckks_boot_setup(ckks_ctx *ctx);
+/* Left-rotation steps the circuit uses (sorted); returns their count and
+ * writes up to cap of them to out (NULL allowed). */
+int ckks_boot_rotation_steps(ckks_ctx *ctx, int32_t *out, int cap);
+/* Number of diagonal plaintexts of the circuit. */
+int ckks_boot_constant_count(ckks_ctx *ctx);
+/* Replace the circuit's constants: count = ckks_boot_constant_count integer
+ * coefficient vectors (host int64[count][N], plan order: CoeffToSlot levels
+ * then SlotToCoeff levels; per level ascending giant step, then ascending
+ * baby step) and the n_cheb = 61 Chebyshev coefficients.  Used to run the
+ * circuit on constants produced elsewhere (e.g. an independent oracle). */
+int ckks_boot_import(ckks_ctx *ctx, const int64_t *coeffs, int count, const double *cheb, int n_cheb);
+/* Copy the current constants out in the same layout (centred integer
+ * coefficients) and the Chebyshev coefficients; either array may be NULL. */
+int ckks_boot_export(ckks_ctx *ctx, int64_t *coeffs, int count, double *cheb, int n_cheb);
+/* Refresh ciphertexts whose modulus is exhausted: ModRaise, CoeffToSlot,
+ * EvalMod, SlotToCoeff (B1-B8).  Inputs are read at level 0 (limb q_0 only);
+ * outputs come back at level n_q - 1 - 16 with scale Delta_in * S / q_0
+ * (S ~ q_0), decrypting to the input slots within about 2^-12.  out[i] needs
+ * n_limbs >= n_q - 16.  Needs the relinearisation, conjugation and rotation
+ * keys of ckks_keygen_from_seed(want_boot=1) (CKKS_E_NOKEY) and
+ * ckks_boot_setup or ckks_boot_import (CKKS_E_STATE). */
+int ckks_bootstrap(ckks_ctx *ctx, const ckks_ct *in, ckks_ct *out);
+int ckks_bootstrap_batch(ckks_ctx *ctx, const ckks_ct *in, ckks_ct *out, int n);
+
 /* ---- batched variants: n independent ciphertexts in one set of launches -- */
 
 /* out[i] = mul_relin(a[i], b[i]) then, if do_rescale, rescale(out[i]).
@@ -217,6 +251,13 @@ int ckks_mul_relin_batch(ckks_ctx *ctx, const ckks_ct *a, const ckks_ct *b, ckks
                          int do_rescale);
 /* out[i] = rotate(in[i], k[i]). */
 int ckks_rotate_batch(ckks_ctx *ctx, const ckks_ct *in, const int32_t *k, ckks_ct *out, int n);
+/* Hoisted rotations (one ModUp of each input's c1 shared by all steps):
+ * out[j*n + i] = Rot(in[i], k[j]) for i < n, j < n_k.  The lifted digits are
+ * mapped by the automorphism before the key inner product, so the limbs
+ * differ from n_k separate ckks_rotate calls (by multiples of the digit
+ * moduli, absorbed by the gadget) while decrypting to the same slots.
+ * Outputs must not alias inputs (CKKS_E_PARAM). */
+int ckks_rotate_hoisted(ckks_ctx *ctx, const ckks_ct *in, int n, const int32_t *k, int n_k, ckks_ct *out);
 /* In-place rescale of n ciphertexts at one level. */
 int ckks_rescale_batch(ckks_ctx *ctx, ckks_ct *inout, int n);
 

@@ -82,6 +82,14 @@ SIGNATURES = {
     "ckks_mul_relin_batch": (_I, [_V, _CTP, _CTP, _CTP, _I, _I]),
     "ckks_rotate_batch": (_I, [_V, _CTP, _V, _CTP, _I]),
     "ckks_rescale_batch": (_I, [_V, _CTP, _I]),
+    "ckks_rotate_hoisted": (_I, [_V, _CTP, _I, _V, _I, _CTP]),
+    "ckks_boot_setup": (_I, [_V]),
+    "ckks_boot_rotation_steps": (_I, [_V, _V, _I]),
+    "ckks_boot_constant_count": (_I, [_V]),
+    "ckks_boot_import": (_I, [_V, _V, _I, _V, _I]),
+    "ckks_boot_export": (_I, [_V, _V, _I, _V, _I]),
+    "ckks_bootstrap": (_I, [_V, _CTP, _CTP]),
+    "ckks_bootstrap_batch": (_I, [_V, _CTP, _CTP, _I]),
     "ckks_ct_export": (_I, [_V, _CTP, _V]),
     "ckks_ct_import": (_I, [_V, _V, _CTP]),
     "ckks_status_str": (ctypes.c_char_p, [_I]),
@@ -389,11 +397,67 @@ class Context:
         for i, c in enumerate(out):
             c.level, c.scale = ho[i].level, ho[i].scale
 
+    def rotate_hoisted(self, cts, steps, out) -> None:
+        """out[j * len(cts) + i] = Rot(cts[i], steps[j]) sharing one ModUp per input."""
+        hi, ho = self._handles(cts), self._handles(out)
+        ks = (ctypes.c_int32 * len(steps))(*steps)
+        _check(self.lib.ckks_rotate_hoisted(self._h, hi, len(cts), ks, len(steps), ho), "ckks_rotate_hoisted")
+        for i, c in enumerate(out):
+            c.level, c.scale = ho[i].level, ho[i].scale
+
     def rescale_batch(self, cts) -> None:
         h = self._handles(cts)
         _check(self.lib.ckks_rescale_batch(self._h, h, len(cts)), "ckks_rescale_batch")
         for i, c in enumerate(cts):
             c.level, c.scale = h[i].level, h[i].scale
+
+    # ---- bootstrapping ----
+    def keygen_boot(self, seed: int, rot_steps=(), conj: bool = True) -> None:
+        arr = (ctypes.c_int32 * max(1, len(rot_steps)))(*rot_steps)
+        _check(self.lib.ckks_keygen_from_seed(self._h, seed, arr, len(rot_steps), int(conj), 1),
+               "ckks_keygen_from_seed")
+
+    def boot_setup(self) -> None:
+        _check(self.lib.ckks_boot_setup(self._h), "ckks_boot_setup")
+
+    def boot_rotation_steps(self) -> list:
+        n = self.lib.ckks_boot_rotation_steps(self._h, None, 0)
+        if n < 0:
+            raise CkksError(n, "ckks_boot_rotation_steps")
+        out = (ctypes.c_int32 * max(1, n))()
+        self.lib.ckks_boot_rotation_steps(self._h, out, n)
+        return [int(x) for x in out[:n]]
+
+    def boot_constant_count(self) -> int:
+        n = self.lib.ckks_boot_constant_count(self._h)
+        if n < 0:
+            raise CkksError(n, "ckks_boot_constant_count")
+        return n
+
+    def boot_import(self, coeffs, cheb) -> None:
+        arr = np.ascontiguousarray(np.stack(coeffs), dtype=np.int64)
+        ch = np.ascontiguousarray(cheb, dtype=np.float64)
+        _check(self.lib.ckks_boot_import(self._h, arr.ctypes.data, arr.shape[0], ch.ctypes.data, len(ch)),
+               "ckks_boot_import")
+
+    def boot_export(self):
+        cnt = self.boot_constant_count()
+        arr = np.zeros((cnt, self.n), dtype=np.int64)
+        ch = np.zeros(61)
+        _check(self.lib.ckks_boot_export(self._h, arr.ctypes.data, cnt, ch.ctypes.data, 61), "ckks_boot_export")
+        return arr, ch
+
+    def bootstrap_batch(self, cts, out=None) -> list:
+        out_level = self.n_q - 1 - 16
+        out = out if out is not None else [self.new_ct(out_level + 1) for _ in cts]
+        hi, ho = self._handles(cts), self._handles(out)
+        _check(self.lib.ckks_bootstrap_batch(self._h, hi, ho, len(cts)), "ckks_bootstrap_batch")
+        for i, c in enumerate(out):
+            c.level, c.scale = ho[i].level, ho[i].scale
+        return out
+
+    def bootstrap(self, ct) -> "Ciphertext":
+        return self.bootstrap_batch([ct])[0]
 
     # ---- host exchange ----
     def export_ct(self, ct: Ciphertext) -> np.ndarray:

@@ -128,10 +128,16 @@ int galois_key(ckks_ctx *c, u64 g) {
   return CKKS_OK;
 }
 
+}  // namespace
+int galois_key_for(ckks_ctx *c, u64 g) { return galois_key(c, g); }
+namespace {
+
 const DevKey *find_galois(const ckks_ctx *c, u64 g) {
   auto it = c->galois.find(g);
   return it == c->galois.end() ? nullptr : &it->second;
 }
+
+}  // namespace
 
 // in-place rescale of n <= MAX_CTS ciphertexts at one level (reading C10)
 int rescale_chunk(ckks_ctx *c, ckks_ct *cts, int n) {
@@ -272,9 +278,85 @@ int automorph_chunk(ckks_ctx *c, const ckks_ct *in, const u64 *g, ckks_ct *out, 
   return CKKS_OK;
 }
 
-}  // namespace
+// Hoisted rotations: one ModUp of c1 per input serves every Galois element;
+// out[j * n + i] = sigma_{g[j]}(in[i]) key-switched back to s.  Outputs must
+// not alias inputs.  All inputs at one level.
+int rotate_hoisted_internal(ckks_ctx *c, const ckks_ct *in, int n, const u64 *g, int m, ckks_ct *out) {
+  if (n <= 0 || m <= 0) return CKKS_OK;
+  const int level = in[0].level;
+  const u32 nn = c->n;
+  std::vector<const u64 *> keys(m);
+  for (int j = 0; j < m; ++j) {
+    const DevKey *k = find_galois(c, g[j]);
+    if (!k) return CKKS_E_NOKEY;
+    keys[j] = k->data;
+  }
+  // inputs per chunk: keep np * m outputs within one tail launch set of <= MAX_CTS each
+  const int np_max = std::max(1, std::min(MAX_CTS, MAX_CTS / m > 0 ? MAX_CTS / m : 1));
+  for (int i0 = 0; i0 < n; i0 += np_max) {
+    const int np = std::min(np_max, n - i0);
+    const size_t mw = ks_modup_words(c, level, np);
+    const int nv_max = std::min(MAX_CTS, np * m);
+    int rc = ensure_scratch(c, mw + ks_tail_words(c, level, nv_max));
+    if (rc) return rc;
+    std::vector<const u64 *> c1(np);
+    std::vector<u64 *> eb(np);
+    for (int i = 0; i < np; ++i) c1[i] = poly1(&in[i0 + i], nn);
+    rc = ks_modup(c, level, np, c1.data(), c->scratch, eb.data());
+    if (rc) return rc;
+    const int nv_total = np * m;
+    for (int v0 = 0; v0 < nv_total; v0 += MAX_CTS) {
+      const int nv = std::min(MAX_CTS, nv_total - v0);
+      std::vector<const u64 *> d(nv), e(nv), k(nv), b0(nv);
+      std::vector<u32> gal(nv);
+      std::vector<u64 *> o0(nv), o1(nv);
+      for (int v = 0; v < nv; ++v) {
+        const int idx = v0 + v, j = idx / np, i = idx % np;
+        d[v] = c1[i];
+        e[v] = eb[i];
+        k[v] = keys[j];
+        gal[v] = (u32)g[j];
+        b0[v] = in[i0 + i].data;
+        ckks_ct &o = out[(size_t)j * n + i0 + i];
+        o0[v] = o.data;
+        o1[v] = poly1(&o, nn);
+      }
+      rc = ks_tail(c, level, nv, d.data(), e.data(), k.data(), gal.data(), b0.data(), gal.data(), nullptr,
+                   o0.data(), o1.data(), c->scratch + mw);
+      if (rc) return rc;
+    }
+  }
+  for (int j = 0; j < m; ++j)
+    for (int i = 0; i < n; ++i) {
+      ckks_ct &o = out[(size_t)j * n + i];
+      o.level = level;
+      o.scale = in[i].scale;
+      o.is_ntt = 1;
+      o.log_n = c->log_n;
+    }
+  return CKKS_OK;
+}
 
 extern "C" {
+
+int ckks_rotate_hoisted(ckks_ctx *c, const ckks_ct *in, int n, const int32_t *k, int n_k, ckks_ct *out) {
+  if (!c || !in || !k || !out || n < 0 || n_k < 0) return CKKS_E_PARAM;
+  if (n == 0 || n_k == 0) return CKKS_OK;
+  const u32 level = in[0].level;
+  for (int i = 0; i < n; ++i) {
+    if (!ct_ok(c, &in[i])) return CKKS_E_PARAM;
+    if (in[i].level != level) return CKKS_E_LEVEL;
+  }
+  for (int i = 0; i < n * n_k; ++i) {
+    if (!out[i].data) return CKKS_E_PARAM;
+    if (out[i].n_limbs < level + 1) return CKKS_E_LEVEL;
+    for (int j = 0; j < n; ++j)
+      if (out[i].data == in[j].data) return CKKS_E_PARAM;  // no aliasing
+  }
+  std::vector<u64> g(n_k);
+  for (int j = 0; j < n_k; ++j) g[j] = ckks_galois_elt(c, k[j]);
+  return rotate_hoisted_internal(c, in, n, g.data(), n_k, out);
+}
 
 const char *ckks_status_str(int s) {
   switch (s) {
@@ -336,6 +418,7 @@ int ckks_ctx_destroy(ckks_ctx *c) {
   cudaFree(c->d_s_ntt);
   cudaFree(c->scratch);
   cudaFree(c->fscratch);
+  boot_free(c);
   if (c->pinned) cudaFreeHost(c->pinned);
   delete c;
   return CKKS_OK;
@@ -422,7 +505,11 @@ uint64_t ckks_galois_elt(const ckks_ctx *c, int32_t k) {
 int ckks_keygen_from_seed(ckks_ctx *c, uint64_t seed, const int32_t *rot, int n_rot, int want_conj,
                           int want_boot) {
   if (!c || n_rot < 0 || (n_rot > 0 && !rot)) return CKKS_E_PARAM;
-  if (want_boot) return CKKS_E_STATE;  // the bootstrapping key set is not part of this build
+  std::vector<int> boot_steps;
+  if (want_boot) {
+    int rc0 = boot_rotation_steps(c, boot_steps);
+    if (rc0) return rc0;
+  }
   CK_CUDA(cudaStreamSynchronize(c->stream));
   free_keys(c);
   const int ext = c->n_q + c->n_p;
@@ -465,8 +552,12 @@ int ckks_keygen_from_seed(ckks_ctx *c, uint64_t seed, const int32_t *rot, int n_
     rc = galois_key(c, ckks_galois_elt(c, rot[i]));
     if (rc) return rc;
   }
-  if (want_conj) {
+  if (want_conj || want_boot) {
     rc = galois_key(c, 2ULL * n - 1);
+    if (rc) return rc;
+  }
+  for (int k : boot_steps) {
+    rc = galois_key(c, ckks_galois_elt(c, k));
     if (rc) return rc;
   }
   CK_CUDA(cudaStreamSynchronize(c->stream));

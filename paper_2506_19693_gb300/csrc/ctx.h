@@ -33,7 +33,10 @@ struct ConvTables {
   size_t total = 0;
 };
 
+struct BootState;  // boot.cu
+
 struct ckks_ctx {
+  BootState *boot = nullptr;
   int device = 0;
   cudaStream_t stream = nullptr;
   int log_n = 0;
@@ -108,10 +111,29 @@ int launch_ntt(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, i
                const int *mods, bool inverse);
 
 // ---- element-wise and key-switch launchers (ops.cu / keyswitch.cu) ----
+// ---- batched ciphertext operations (capi.cu); n <= 128, all at one level ----
+int rescale_chunk(ckks_ctx *c, ckks_ct *cts, int n);
+int mul_relin_chunk(ckks_ctx *c, const ckks_ct *a, const ckks_ct *b, ckks_ct *out, int n);
+int automorph_chunk(ckks_ctx *c, const ckks_ct *in, const u64 *g, ckks_ct *out, int n);
+int rotate_hoisted_internal(ckks_ctx *c, const ckks_ct *in, int n, const u64 *g, int m, ckks_ct *out);
+int galois_key_for(ckks_ctx *c, u64 g);
+// encode.cu: N/2 device slots -> NTT plaintext over q_0..q_level at `scale`
+int encode_device_z(ckks_ctx *c, const double2 *z_dev, uint32_t level, double scale, u64 *pt_dev, int *flag_dev);
+// boot.cu
+void boot_free(ckks_ctx *c);
+int boot_ensure_plan(ckks_ctx *c);
+int boot_rotation_steps(ckks_ctx *c, std::vector<int> &steps);
+
 // Key switching of np <= 128 NTT-domain polynomials at `level`, one key per
 // polynomial: o_c = base_c + u_c (base may be null) with u0 + u1 s ~ d s'.
 // ws: device workspace of ks_ws_words(level, np) words.
 size_t ks_ws_words(const ckks_ctx *c, int level, int np);
+size_t ks_modup_words(const ckks_ctx *c, int level, int np);
+size_t ks_tail_words(const ckks_ctx *c, int level, int nv);
+int ks_modup(ckks_ctx *c, int level, int np, const u64 *const *d, u64 *ws, u64 **ext_out);
+int ks_tail(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *const *ext_digits,
+            const u64 *const *keys, const u32 *gal, const u64 *const *base0, const u32 *base0_gal,
+            const u64 *const *base1, u64 *const *o0, u64 *const *o1, u64 *ws);
 int ks_batch(ckks_ctx *c, int level, int np, const u64 *const *d, const u64 *const *keys,
              const u64 *const *base0, const u64 *const *base1, u64 *const *o0, u64 *const *o1,
              u64 *ws);

@@ -140,6 +140,40 @@ void fft(ckks_ctx *c, double2 *x, double sign) {
 
 }  // namespace
 
+namespace {
+// same as k_enc_scatter, slots given as interleaved complex values on the device
+__global__ void k_enc_scatter_z(const double2 *z, double2 *x, u32 n, int log_n) {
+  const u32 j = blockIdx.x * TPB + threadIdx.x;
+  if (j >= n / 2) return;
+  const double2 v = z[j];
+  const u32 u = (slot_exp(j, 2 * n) - 1) >> 1;
+  x[brv32(u, log_n)] = v;
+  x[brv32(n - 1 - u, log_n)] = make_double2(v.x, -v.y);
+}
+}  // namespace
+
+// Encode N/2 device-resident complex slots into an NTT-domain plaintext over
+// q_0..q_level (the ckks_encode arithmetic).  Sets *flag_dev to 1 when a
+// scaled coefficient reaches 2^62; never clears it.  Uses the FFT buffer in
+// the context's float scratch.
+int encode_device_z(ckks_ctx *c, const double2 *z_dev, uint32_t level, double scale, u64 *pt_dev, int *flag_dev) {
+  const u32 n = c->n;
+  int rc = ensure_fscratch(c, 3 * (size_t)n + 8);
+  if (rc) return rc;
+  double2 *x = reinterpret_cast<double2 *>(c->fscratch + n);
+  PROF_LAUNCH(c, PK_ENCODE, 1,
+              (k_enc_scatter_z<<<(n / 2 + TPB - 1) / TPB, TPB, 0, c->stream>>>(z_dev, x, n, c->log_n)));
+  fft(c, x, -1.0);
+  PROF_LAUNCH(c, PK_ENCODE, level + 1,
+              (k_enc_finish<<<(n + TPB - 1) / TPB, TPB, 0, c->stream>>>(x, n, scale, c->d_mods, level + 1, pt_dev,
+                                                                         flag_dev)));
+  int mods[MAX_MODS];
+  for (int l = 0; l <= (int)level; ++l) mods[l] = l;
+  const u64 *src[1] = {pt_dev};
+  u64 *dst[1] = {pt_dev};
+  return launch_ntt(c, src, dst, 1, level + 1, mods, false);
+}
+
 extern "C" int ckks_encode(ckks_ctx *c, const double *re, const double *im, int n_slots, uint32_t level,
                            double scale, uint64_t *pt_dev) {
   if (!c || !re || !pt_dev || n_slots < 0 || n_slots > (int)(c->n / 2)) return CKKS_E_PARAM;

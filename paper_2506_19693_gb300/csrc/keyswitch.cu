@@ -1,18 +1,24 @@
 // Hybrid key switching (readings C7-C9): ModUp by fast basis conversion,
 // inner product with the switching key, ModDown.
 //
-// For np polynomials d (NTT domain, limbs q_0..q_l) and one key per
+// For polynomials d (NTT domain, limbs q_0..q_l) and one key per
 // polynomial, computes (u0, u1) with u0 + u1 s ~ d s' and writes
 //   o0 = base0 + u0,   o1 = base1 + u1      (base may be null -> 0).
 //
-// Data flow (all buffers limb-major uint64, per polynomial):
-//   dc   = iNTT(d)                                   [l+1][N]
-//   for each active digit j (q-limbs [lo, hi) of the top-level digit j):
-//     ext_j[t] = BConv_{D_j -> t}(dc[lo:hi])  for t outside [lo, hi)   (C8)
-//     ext_j[t] = NTT(ext_j[t]); positions inside [lo, hi) reuse d itself
-//   acc_c[t] = sum_j ext_j[t] * key_j,c[t]          (c = 0 for b, 1 for a)
-//   acc_c[P] = iNTT(acc_c[P]);  z_c = NTT(BConv_{P -> Q_l}(acc_c[P]))  (C9)
-//   o_c      = base_c + (acc_c[Q] - z_c) * P^-1
+// Data flow (all buffers limb-major uint64):
+//   ModUp (per input polynomial):
+//     dc   = iNTT(d)                                   [l+1][N]
+//     for each active digit j (q-limbs [lo, hi) of the top-level digit j):
+//       ext_j[t] = NTT(BConv_{D_j -> t}(dc[lo:hi]))  for t outside [lo, hi)   (C8)
+//       positions inside [lo, hi) are d itself
+//   Tail (per output; several outputs may share one ModUp -- hoisting):
+//     acc_c[t] = sum_j sigma_g(ext_j)[t] * key_j,c[t]   (c = 0 for b, 1 for a)
+//     acc_c[P] = iNTT(acc_c[P]);  z_c = NTT(BConv_{P -> Q_l}(acc_c[P]))  (C9)
+//     o_c      = base_c + (acc_c[Q] - z_c) * P^-1
+// sigma_g is the Galois automorphism of the output (g = 1: none), applied in
+// the NTT domain as a gather: it maps aligned 32-word blocks onto aligned
+// 32-word blocks, so the gathered reads stay coalesced.  base0 may be read
+// through sigma_g too (rotations add sigma_g(c0)).
 // The key is read once per launch for a batch that shares it: the inner
 // product loops over the batch with the key words held in registers.
 #include "ops.cuh"
@@ -22,6 +28,14 @@ namespace {
 constexpr int TPB = 256;
 constexpr int MAXS = 16;   // source limbs of one basis conversion
 constexpr int MAXD = 8;    // digits
+
+__device__ __forceinline__ u32 brv_ks(u32 x, int bits) { return __brev(x) >> (32 - bits); }
+// index read by sigma_g at output position j (canonical NTT order)
+__device__ __forceinline__ u32 gal_src(u32 j, u32 g, u32 n, int log_n) {
+  if (g == 1) return j;
+  const u32 e = (u32)(((u64)g * (2 * brv_ks(j, log_n) + 1)) & (2 * n - 1));
+  return brv_ks((e - 1) >> 1, log_n);
+}
 
 struct BConvArgs {
   const ModInfo *mods;
@@ -61,6 +75,7 @@ __global__ void __launch_bounds__(TPB) k_bconv(const BConvArgs a) {
 struct IPArgs {
   const ModInfo *mods;
   u32 n;
+  int log_n;
   int ext, ndig, key_ext, np;
   unsigned char mod_of[MAX_MODS];
   unsigned char keylimb_of[MAX_MODS];
@@ -68,6 +83,7 @@ struct IPArgs {
   const u64 *d[MAX_CTS];
   const u64 *ext_buf[MAX_CTS];     // [ndig][ext][N]
   const u64 *key[MAX_CTS];         // [n_digits][2][key_ext][N]
+  u32 gal[MAX_CTS];
   u64 *acc[MAX_CTS];               // [2][ext][N]
 };
 
@@ -90,12 +106,13 @@ __global__ void __launch_bounds__(TPB) k_inner(const IPArgs a) {
         }
       }
     }
+    const u32 src = gal_src(k, a.gal[p], a.n, a.log_n);
     u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0;
 #pragma unroll
     for (int j = 0; j < MAXD; ++j) {
       if (j < a.ndig) {
-        const u64 v = (t >= a.lo[j] && t < a.hi[j]) ? a.d[p][(size_t)t * a.n + k]
-                                                     : a.ext_buf[p][((size_t)j * a.ext + t) * a.n + k];
+        const u64 v = (t >= a.lo[j] && t < a.hi[j]) ? a.d[p][(size_t)t * a.n + src]
+                                                     : a.ext_buf[p][((size_t)j * a.ext + t) * a.n + src];
         mac128(h0, l0, v, kb[j]);
         mac128(h1, l1, v, ka[j]);
       }
@@ -108,11 +125,13 @@ __global__ void __launch_bounds__(TPB) k_inner(const IPArgs a) {
 struct CombineArgs {
   const ModInfo *mods;
   u32 n;
+  int log_n;
   int ext;
   const u64 *pinv;                 // [n_q] pairs
   const u64 *acc[MAX_CTS];
   const u64 *z[MAX_CTS];           // [2][l+1][N]
   const u64 *base0[MAX_CTS], *base1[MAX_CTS];
+  u32 base0_gal[MAX_CTS];          // base0 read through sigma_g (1: as is)
   u64 *o0[MAX_CTS], *o1[MAX_CTS];
 };
 
@@ -126,7 +145,7 @@ __global__ void __launch_bounds__(TPB) k_combine(const CombineArgs a, int nl) {
   const u64 z0 = a.z[p][off], z1 = a.z[p][(size_t)nl * a.n + off];
   u64 r0 = shoup(submod(x0, z0, q), w, ws, q);
   u64 r1 = shoup(submod(x1, z1, q), w, ws, q);
-  if (a.base0[p]) r0 = addmod(r0, a.base0[p][off], q);
+  if (a.base0[p]) r0 = addmod(r0, a.base0[p][(size_t)t * a.n + gal_src(k, a.base0_gal[p], a.n, a.log_n)], q);
   if (a.base1[p]) r1 = addmod(r1, a.base1[p][off], q);
   a.o0[p][off] = r0;
   a.o1[p][off] = r1;
@@ -147,40 +166,51 @@ int launch_bconv(ckks_ctx *c, BConvArgs &a, int ns, int np) {
   return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_CUDA;
 }
 
-}  // namespace
-
-size_t ks_ws_words(const ckks_ctx *c, int level, int np) {
-  const int nl = level + 1, ext = nl + c->n_p;
+int check_shape(const ckks_ctx *c, int level) {
+  const int nl = level + 1;
   const int ndig = (nl + c->alpha - 1) / c->alpha;
-  return (size_t)c->n * (nl + (size_t)ndig * ext + 2 * ext + 2 * nl) * np;
+  if (ndig > MAXD || c->alpha > MAXS || c->n_p > MAXS) return CKKS_E_PARAM;
+  return CKKS_OK;
 }
 
-int ks_batch(ckks_ctx *c, int level, int np, const u64 *const *d, const u64 *const *keys,
-             const u64 *const *base0, const u64 *const *base1, u64 *const *o0, u64 *const *o1,
-             u64 *ws) {
+}  // namespace
+
+size_t ks_modup_words(const ckks_ctx *c, int level, int np) {
+  const int nl = level + 1, ext = nl + c->n_p;
+  const int ndig = (nl + c->alpha - 1) / c->alpha;
+  return (size_t)c->n * (nl + (size_t)ndig * ext) * np;
+}
+
+size_t ks_tail_words(const ckks_ctx *c, int level, int nv) {
+  const int nl = level + 1, ext = nl + c->n_p;
+  return (size_t)c->n * (2 * ext + 2 * nl) * nv;
+}
+
+size_t ks_ws_words(const ckks_ctx *c, int level, int np) {
+  return ks_modup_words(c, level, np) + ks_tail_words(c, level, np);
+}
+
+// ModUp of np <= MAX_CTS polynomials; ws holds per polynomial dc [l+1] then
+// ext [ndig][l+1+K].  ext_out[i] receives polynomial i's ext pointer.
+int ks_modup(ckks_ctx *c, int level, int np, const u64 *const *d, u64 *ws, u64 **ext_out) {
   if (np <= 0) return CKKS_OK;
   if (np > MAX_CTS) return CKKS_E_PARAM;
+  int rc = check_shape(c, level);
+  if (rc) return rc;
   const u32 n = c->n;
-  const int nl = level + 1, K = c->n_p, ext = nl + K;
+  const int nl = level + 1, ext = nl + c->n_p;
   const int ndig = (nl + c->alpha - 1) / c->alpha;
-  if (ndig > MAXD || c->alpha > MAXS || K > MAXS) return CKKS_E_PARAM;
-  // workspace per polynomial: dc [nl], ext [ndig][ext], acc [2][ext], z [2][nl]
-  const size_t per = ks_ws_words(c, level, 1);
-  int rc = CKKS_OK;
-  std::vector<u64 *> dc(np), eb(np), acc(np), z(np);
+  const size_t per = ks_modup_words(c, level, 1);
+  std::vector<u64 *> dc(np), eb(np);
   for (int i = 0; i < np; ++i) {
-    u64 *base = ws + per * i;
-    dc[i] = base;
+    dc[i] = ws + per * i;
     eb[i] = dc[i] + (size_t)nl * n;
-    acc[i] = eb[i] + (size_t)ndig * ext * n;
-    z[i] = acc[i] + (size_t)2 * ext * n;
+    ext_out[i] = eb[i];
   }
   int mods[MAX_MODS];
   for (int t = 0; t < ext; ++t) mods[t] = c->ext_mod(level, t);
-  // 1. dc = iNTT(d)
   rc = launch_ntt(c, d, dc.data(), np, nl, mods, true);
   if (rc) return rc;
-  // 2. ModUp per digit
   std::vector<const u64 *> srcs(np);
   std::vector<u64 *> dsts(np);
   for (int j = 0; j < ndig; ++j) {
@@ -204,7 +234,6 @@ int ks_batch(ckks_ctx *c, int level, int np, const u64 *const *d, const u64 *con
     }
     rc = launch_bconv(c, a, ns, np);
     if (rc) return rc;
-    // NTT of the converted limbs: positions [0, lo) and [hi, ext)
     if (lo > 0) {
       for (int i = 0; i < np; ++i) dsts[i] = eb[i] + (size_t)j * ext * n, srcs[i] = dsts[i];
       rc = launch_ntt(c, srcs.data(), dsts.data(), np, lo, mods, false);
@@ -214,15 +243,39 @@ int ks_batch(ckks_ctx *c, int level, int np, const u64 *const *d, const u64 *con
     rc = launch_ntt(c, srcs.data(), dsts.data(), np, ext - hi, mods + hi, false);
     if (rc) return rc;
   }
-  // 3. inner product with the keys
+  return CKKS_OK;
+}
+
+// Inner product + ModDown for nv <= MAX_CTS outputs.  Output v uses input
+// polynomial d[v] with its lifted digits ext[v], key keys[v] and automorphism
+// gal[v]; ws holds per output acc [2][l+1+K] then z [2][l+1].
+int ks_tail(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *const *ext_digits,
+            const u64 *const *keys, const u32 *gal, const u64 *const *base0, const u32 *base0_gal,
+            const u64 *const *base1, u64 *const *o0, u64 *const *o1, u64 *ws) {
+  if (nv <= 0) return CKKS_OK;
+  if (nv > MAX_CTS) return CKKS_E_PARAM;
+  int rc = check_shape(c, level);
+  if (rc) return rc;
+  const u32 n = c->n;
+  const int nl = level + 1, K = c->n_p, ext = nl + K;
+  const int ndig = (nl + c->alpha - 1) / c->alpha;
+  const size_t per = ks_tail_words(c, level, 1);
+  std::vector<u64 *> acc(nv), z(nv);
+  for (int i = 0; i < nv; ++i) {
+    acc[i] = ws + per * i;
+    z[i] = acc[i] + (size_t)2 * ext * n;
+  }
+  int mods[MAX_MODS];
+  for (int t = 0; t < ext; ++t) mods[t] = c->ext_mod(level, t);
   {
     IPArgs a;
     a.mods = c->d_mods;
     a.n = n;
+    a.log_n = c->log_n;
     a.ext = ext;
     a.ndig = ndig;
     a.key_ext = c->n_q + c->n_p;
-    a.np = np;
+    a.np = nv;
     for (int t = 0; t < ext; ++t) {
       a.mod_of[t] = (unsigned char)mods[t];
       a.keylimb_of[t] = (unsigned char)c->key_limb(level, t);
@@ -231,69 +284,82 @@ int ks_batch(ckks_ctx *c, int level, int np, const u64 *const *d, const u64 *con
       a.lo[j] = j * c->alpha;
       a.hi[j] = std::min((j + 1) * c->alpha, nl);
     }
-    for (int i = 0; i < np; ++i) {
+    for (int i = 0; i < nv; ++i) {
       a.d[i] = d[i];
-      a.ext_buf[i] = eb[i];
+      a.ext_buf[i] = ext_digits[i];
       a.key[i] = keys[i];
+      a.gal[i] = gal ? gal[i] : 1u;
       a.acc[i] = acc[i];
     }
     dim3 g((n + TPB - 1) / TPB, ext);
-    PROF_LAUNCH(c, PK_INNER, (u64)np * ext, (k_inner<<<g, TPB, 0, c->stream>>>(a)));
+    PROF_LAUNCH(c, PK_INNER, (u64)nv * ext, (k_inner<<<g, TPB, 0, c->stream>>>(a)));
     if (cudaGetLastError() != cudaSuccess) return CKKS_E_CUDA;
   }
-  // 4. ModDown
-  {
-    std::vector<const u64 *> ps(2 * np);
-    std::vector<u64 *> pd(2 * np);
-    for (int i = 0; i < np; ++i)
-      for (int cc = 0; cc < 2; ++cc) {
-        pd[2 * i + cc] = acc[i] + ((size_t)cc * ext + nl) * n;
-        ps[2 * i + cc] = pd[2 * i + cc];
-      }
-    rc = launch_ntt(c, ps.data(), pd.data(), 2 * np, K, mods + nl, true);
-    if (rc) return rc;
-    for (int p0 = 0; p0 < 2 * np; p0 += MAX_CTS) {
-      const int cnt = std::min(MAX_CTS, 2 * np - p0);
-      BConvArgs a;
-      a.inv = c->d_conv + c->conv.moddown_phat_inv;
-      a.tab = c->d_conv + c->conv.moddown_phat_mod;
-      a.nt = nl;
-      for (int i = 0; i < K; ++i) a.src_mod[i] = (unsigned char)(c->n_q + i);
-      for (int t = 0; t < nl; ++t) {
-        a.dst_mod[t] = (unsigned char)t;
-        a.dst_pos[t] = (unsigned char)t;
-      }
-      for (int x = 0; x < cnt; ++x) {
-        const int pp = p0 + x, i = pp / 2, cc = pp % 2;
-        a.src[x] = pd[pp];
-        a.dst[x] = z[i] + (size_t)cc * nl * n;
-      }
-      rc = launch_bconv(c, a, K, cnt);
-      if (rc) return rc;
+  std::vector<const u64 *> ps(2 * nv);
+  std::vector<u64 *> pd(2 * nv);
+  for (int i = 0; i < nv; ++i)
+    for (int cc = 0; cc < 2; ++cc) {
+      pd[2 * i + cc] = acc[i] + ((size_t)cc * ext + nl) * n;
+      ps[2 * i + cc] = pd[2 * i + cc];
     }
-    for (int i = 0; i < np; ++i)
-      for (int cc = 0; cc < 2; ++cc) {
-        pd[2 * i + cc] = z[i] + (size_t)cc * nl * n;
-        ps[2 * i + cc] = pd[2 * i + cc];
-      }
-    rc = launch_ntt(c, ps.data(), pd.data(), 2 * np, nl, mods, false);
-    if (rc) return rc;
-    CombineArgs a;
-    a.mods = c->d_mods;
-    a.n = n;
-    a.ext = ext;
-    a.pinv = c->d_conv + c->conv.moddown_pinv;
-    for (int i = 0; i < np; ++i) {
-      a.acc[i] = acc[i];
-      a.z[i] = z[i];
-      a.base0[i] = base0 ? base0[i] : nullptr;
-      a.base1[i] = base1 ? base1[i] : nullptr;
-      a.o0[i] = o0[i];
-      a.o1[i] = o1[i];
+  rc = launch_ntt(c, ps.data(), pd.data(), 2 * nv, K, mods + nl, true);
+  if (rc) return rc;
+  for (int p0 = 0; p0 < 2 * nv; p0 += MAX_CTS) {
+    const int cnt = std::min(MAX_CTS, 2 * nv - p0);
+    BConvArgs a;
+    a.inv = c->d_conv + c->conv.moddown_phat_inv;
+    a.tab = c->d_conv + c->conv.moddown_phat_mod;
+    a.nt = nl;
+    for (int i = 0; i < K; ++i) a.src_mod[i] = (unsigned char)(c->n_q + i);
+    for (int t = 0; t < nl; ++t) {
+      a.dst_mod[t] = (unsigned char)t;
+      a.dst_pos[t] = (unsigned char)t;
     }
-    dim3 g((n + TPB - 1) / TPB, nl, np);
-    PROF_LAUNCH(c, PK_COMBINE, (u64)np * nl, (k_combine<<<g, TPB, 0, c->stream>>>(a, nl)));
-    if (cudaGetLastError() != cudaSuccess) return CKKS_E_CUDA;
+    for (int x = 0; x < cnt; ++x) {
+      const int pp = p0 + x, i = pp / 2, cc = pp % 2;
+      a.src[x] = pd[pp];
+      a.dst[x] = z[i] + (size_t)cc * nl * n;
+    }
+    rc = launch_bconv(c, a, K, cnt);
+    if (rc) return rc;
   }
+  for (int i = 0; i < nv; ++i)
+    for (int cc = 0; cc < 2; ++cc) {
+      pd[2 * i + cc] = z[i] + (size_t)cc * nl * n;
+      ps[2 * i + cc] = pd[2 * i + cc];
+    }
+  rc = launch_ntt(c, ps.data(), pd.data(), 2 * nv, nl, mods, false);
+  if (rc) return rc;
+  CombineArgs a;
+  a.mods = c->d_mods;
+  a.n = n;
+  a.log_n = c->log_n;
+  a.ext = ext;
+  a.pinv = c->d_conv + c->conv.moddown_pinv;
+  for (int i = 0; i < nv; ++i) {
+    a.acc[i] = acc[i];
+    a.z[i] = z[i];
+    a.base0[i] = base0 ? base0[i] : nullptr;
+    a.base0_gal[i] = base0_gal ? base0_gal[i] : 1u;
+    a.base1[i] = base1 ? base1[i] : nullptr;
+    a.o0[i] = o0[i];
+    a.o1[i] = o1[i];
+  }
+  dim3 g((n + TPB - 1) / TPB, nl, nv);
+  PROF_LAUNCH(c, PK_COMBINE, (u64)nv * nl, (k_combine<<<g, TPB, 0, c->stream>>>(a, nl)));
+  if (cudaGetLastError() != cudaSuccess) return CKKS_E_CUDA;
   return CKKS_OK;
+}
+
+int ks_batch(ckks_ctx *c, int level, int np, const u64 *const *d, const u64 *const *keys,
+             const u64 *const *base0, const u64 *const *base1, u64 *const *o0, u64 *const *o1,
+             u64 *ws) {
+  if (np <= 0) return CKKS_OK;
+  if (np > MAX_CTS) return CKKS_E_PARAM;
+  std::vector<u64 *> eb(np);
+  int rc = ks_modup(c, level, np, d, ws, eb.data());
+  if (rc) return rc;
+  std::vector<const u64 *> ebc(eb.begin(), eb.end());
+  return ks_tail(c, level, np, d, ebc.data(), keys, nullptr, base0, nullptr, base1, o0, o1,
+                 ws + ks_modup_words(c, level, np));
 }

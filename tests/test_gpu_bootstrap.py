@@ -1,0 +1,106 @@
+"""GPU bootstrapping against the CPU oracle.
+
+* plan: the same rotation steps and constant count as the oracle's plan;
+* constants: GPU FP64 constants within FP64 rounding of the oracle's;
+* bit-exact: with the oracle's constants imported, every output limb equals
+  the oracle's bootstrap of the same ciphertext (N = 2^12, full 2^11 slots);
+* bound: with the GPU's own constants the decrypted slots are within 2^-12 of
+  the input, at N = 2^12 and at N = 2^16 with 2^15 slots (the configuration
+  bench.py times), output at level n_q - 17."""
+import numpy as np
+import pytest
+
+import synthetic_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def small():
+    import torch
+    import oracle
+    import oracle.bootstrap as ob
+    import paper_2506_19693_gb300 as ck
+    torch.cuda.set_device(0)
+    w = si.BOOT_SMALL
+    ctx = ck.Context.from_workload(w)
+    ctx.keygen_boot(1)
+    ctx.boot_setup()
+    plan = ob.make_plan(w.log_n, len(w.q_bits))
+    orc = oracle.Oracle(w.log_n, w.q_bits, w.p_bits, w.dnum, w.h, w.sigma)
+    orc.keygen(1)
+    orc.gen_rotation_keys(plan.rotation_steps())
+    orc.gen_galois_key(orc.conj_elt())
+    consts = ob.encode_constants(orc, plan)
+    yield w, ctx, orc, plan, consts
+    ctx.close()
+
+
+def test_plan_matches_oracle(small):
+    w, ctx, orc, plan, consts = small
+    assert ctx.boot_rotation_steps() == plan.rotation_steps()
+    assert ctx.boot_constant_count() == len(consts)
+
+
+def test_gpu_constants_match_oracle_constants(small):
+    w, ctx, orc, plan, consts = small
+    got, cheb = ctx.boot_export()
+    want = np.stack(consts)
+    scale = np.max(np.abs(want))
+    assert np.max(np.abs(got - want)) <= 1e-11 * scale + 2
+    assert np.max(np.abs(cheb - plan.cheb)) < 1e-13
+
+
+def test_bootstrap_bit_exact_with_oracle_constants(small):
+    import oracle.bootstrap as ob
+    w, ctx, orc, plan, consts = small
+    z = si.messages(21, 1, w.slots)[0]
+    delta = 2.0 ** w.log2_scale
+    m = orc.encode(z, delta)
+    co = orc.encrypt(orc.pt_from_int(m, 0), 0, delta, 77)
+    cg = ctx.encrypt(ctx.pt_from_int(m, 0), 0, delta, 77)
+    assert np.array_equal(ctx.export_ct(cg), co.data)
+    mine_c, mine_cheb = ctx.boot_export()
+    try:
+        ctx.boot_import(consts, plan.cheb)
+        out_g = ctx.bootstrap(cg)
+        ev = ob.Evaluator(orc, plan, consts)
+        out_o = ev.bootstrap(co)
+        assert (out_g.level, out_g.scale) == (out_o.level, out_o.scale)
+        got = ctx.export_ct(out_g)
+        assert np.array_equal(got, out_o.data), int(np.sum(got != out_o.data))
+    finally:
+        ctx.boot_import(list(mine_c), mine_cheb)
+
+
+def test_bootstrap_error_bound_small_ring(small):
+    w, ctx, orc, plan, consts = small
+    z = si.messages(22, 2, w.slots)
+    delta = 2.0 ** w.log2_scale
+    cts = [ctx.encrypt(ctx.encode(z[i], 0, delta), 0, delta, 500 + i) for i in range(2)]
+    outs = ctx.bootstrap_batch(cts)
+    for i in range(2):
+        assert outs[i].level == len(w.q_bits) - 17
+        err = np.max(np.abs(ctx.decrypt_decode(outs[i]) - z[i]))
+        assert err <= 2.0 ** -12, err
+
+
+def test_bootstrap_error_bound_full_ring():
+    import torch
+    import paper_2506_19693_gb300 as ck
+    torch.cuda.set_device(0)
+    w = si.BOOT
+    ctx = ck.Context.from_workload(w)
+    try:
+        ctx.keygen_boot(1)
+        ctx.boot_setup()
+        z = si.messages(23, 2, w.slots)
+        delta = 2.0 ** w.log2_scale
+        cts = [ctx.encrypt(ctx.encode(z[i], 0, delta), 0, delta, 600 + i) for i in range(2)]
+        outs = ctx.bootstrap_batch(cts)
+        for i in range(2):
+            assert outs[i].level == len(w.q_bits) - 17
+            err = np.max(np.abs(ctx.decrypt_decode(outs[i]) - z[i]))
+            assert err <= 2.0 ** -12, err
+    finally:
+        ctx.close()

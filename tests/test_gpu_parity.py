@@ -153,6 +153,20 @@ def test_batched_calls_equal_single_calls(pair):
     _same(ctx, rots[1], orc.rotate(items[1][2], -1))
 
 
+def test_hoisted_rotations_bit_exact(pair):
+    w, ctx, orc = pair
+    (za, a, ao), (zb, b, bo) = _enc_both(w, ctx, orc, 13, count=2)
+    steps = [1, 2, -1]
+    outs = [ctx.new_ct(a.level + 1) for _ in range(2 * len(steps))]
+    ctx.rotate_hoisted([a, b], steps, outs)
+    for i, co in enumerate((ao, bo)):
+        want = orc.rotate_hoisted(co, steps)
+        for j in range(len(steps)):
+            _same(ctx, outs[j * 2 + i], want[j])
+    got = ctx.decrypt_decode(outs[0])
+    assert np.max(np.abs(got - np.roll(za, -1))) < 2.0 ** -20
+
+
 def test_encode_matches_oracle_within_fp64_rounding(pair):
     import paper_2506_19693_gb300 as ck
     w, ctx, orc = pair
