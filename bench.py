@@ -1,13 +1,15 @@
 #!/usr/bin/env python
 """Throughput of the RNS-CKKS evaluation core on GB300.
 
-One step = one pass of the hot path over one batch at N = 2^16 with 24
-ciphertext primes (q0 ~ 2^61, 23 x ~2^55), 8 special primes, dnum = 3:
-  * 64 ciphertext pairs: HMult + relinearise + rescale (batched), then
-  * every input rotated by 2^0 .. 2^14 (15 batched rotations of 64).
+One step = one pass of the hot path over one batch at N = 2^16:
+  * 64 ciphertext pairs with 24 ciphertext primes (q0 ~ 2^61, 23 x ~2^55),
+    8 special primes, dnum = 3: HMult + relinearise + rescale (batched);
+  * every one of the 64 inputs rotated by 2^0 .. 2^14 (hoisted: 960 rotations);
+  * 16 exhausted ciphertexts bootstrapped (2^15 slots, 25 + 9 primes, 16 levels).
 `value` is HMult+relin(+rescale)/s over the multiply phase of the timed steps
-(device time, CUDA events on the library's stream); rotations/s is reported
-beside it.  Inputs (3.2 GB of ciphertexts per step) exceed L2, so no flush.
+(device time, CUDA events on the library's stream); rotations/s and
+bootstraps/s come from the other two phases.  Inputs (over 3 GB of
+ciphertexts per step) exceed L2, so no flush.
 
 --impl reference times the CPU oracle on the host cores instead (bounded
 sample: one HMult+relin+rescale of one ciphertext pair per step).
@@ -241,7 +243,18 @@ def run_gpu(args):
     cts = [ctx.encrypt(ctx.encode(z[i], level, scale), level, scale, seeds[i]) for i in range(2 * B)]
     A, Bc = cts[:B], cts[B:]
     OUT = [ctx.new_ct(level + 1) for _ in range(B)]
-    ROT = [ctx.new_ct(level + 1) for _ in range(B)]
+    ROT = [ctx.new_ct(level + 1) for _ in range(B * len(w.rot_steps))]
+
+    # bootstrapping workload: N = 2^16, 2^15 slots, 16 exhausted (level-0) ciphertexts
+    wb = si.BOOT
+    bctx = ck.Context.from_workload(wb, stream=stream)
+    bctx.keygen_boot(2)
+    bctx.boot_setup()
+    db = 2.0 ** wb.log2_scale
+    zb = si.messages(300 + rank, wb.batch, wb.slots)
+    bseeds = si.enc_seeds(300 + rank, wb.batch)
+    BIN = [bctx.encrypt(bctx.encode(zb[i], 0, db), 0, db, bseeds[i]) for i in range(wb.batch)]
+    BOUT = [bctx.new_ct(len(wb.q_bits) - 16) for _ in range(wb.batch)]
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
@@ -251,47 +264,58 @@ def run_gpu(args):
         ctx.mul_relin_batch(A, Bc, OUT, rescale=True)
         if marks:
             marks[1].record(stream)
-        for k in w.rot_steps:
-            ctx.rotate_batch(A, [k] * B, ROT)
+        ctx.rotate_hoisted(A, list(w.rot_steps), ROT)
         if marks:
             marks[2].record(stream)
+        bctx.bootstrap_batch(BIN, BOUT)
+        if marks:
+            marks[3].record(stream)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    # correctness spot check of the timed configuration (first product only)
+    # correctness spot checks of the timed configuration
     got = ctx.decrypt_decode(OUT[0])
     err_mul = float(np.max(np.abs(got - z[0] * z[B])))
-    got = ctx.decrypt_decode(ROT[0])
-    err_rot = float(np.max(np.abs(got - np.roll(z[0], -w.rot_steps[-1]))))
+    kk = len(w.rot_steps) - 1
+    got = ctx.decrypt_decode(ROT[kk * B])
+    err_rot = float(np.max(np.abs(got - np.roll(z[0], -w.rot_steps[kk]))))
+    err_boot = float(max(np.max(np.abs(bctx.decrypt_decode(BOUT[i]) - zb[i])) for i in range(2)))
 
     clocks = ClockSampler(local)
     barrier()
     torch.cuda.synchronize()
     clocks.start()
     ctx.profile(True)
-    launches0 = ctx.launch_count()
-    marks = [[ev(), ev(), ev()] for _ in range(args.steps)]
+    bctx.profile(True)
+    launches0 = ctx.launch_count() + bctx.launch_count()
+    marks = [[ev(), ev(), ev(), ev()] for _ in range(args.steps)]
     torch.cuda.nvtx.range_push("timed")
     for s in range(args.steps):
         step(marks[s])
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
-    launches = ctx.launch_count() - launches0
+    launches = ctx.launch_count() + bctx.launch_count() - launches0
     prof = ctx.profile_read()
+    for k, v in bctx.profile_read().items():
+        a = prof.get(k, (0.0, 0, 0))
+        prof[k] = (a[0] + v[0], a[1] + v[1], a[2] + v[2])
     ctx.profile(False)
+    bctx.profile(False)
     barrier()
     clk = clocks.stop()
 
     mul_ms = sum(m[0].elapsed_time(m[1]) for m in marks)
     rot_ms = sum(m[1].elapsed_time(m[2]) for m in marks)
-    step_ms = sum(m[0].elapsed_time(m[2]) for m in marks) / args.steps
-    t = torch.tensor([mul_ms, rot_ms, step_ms], dtype=torch.float64, device="cuda")
+    boot_ms = sum(m[2].elapsed_time(m[3]) for m in marks)
+    step_ms = sum(m[0].elapsed_time(m[3]) for m in marks) / args.steps
+    t = torch.tensor([mul_ms, rot_ms, boot_ms, step_ms], dtype=torch.float64, device="cuda")
     if dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    mul_ms, rot_ms, step_ms = t.tolist()
+    mul_ms, rot_ms, boot_ms, step_ms = t.tolist()
     value = world * B * args.steps / (mul_ms / 1e3)
     rot_rate = world * B * len(w.rot_steps) * args.steps / (rot_ms / 1e3)
+    boot_rate = world * wb.batch * args.steps / (boot_ms / 1e3)
 
     # roofline of the dominant kernel class
     hbm, peak_kind = peaks()
@@ -316,12 +340,20 @@ def run_gpu(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": config_of(w),
-                "rotations_per_s": rot_rate, "bootstraps_per_s": None,
-                "slot_error": {"hmult_rescale": err_mul, "rotation": err_rot},
+                "rotations_per_s": rot_rate, "bootstraps_per_s": boot_rate,
+                "phase_ms_per_step": {"hmult_relin_rescale_x64": mul_ms / args.steps,
+                                      "rotations_hoisted_64x15": rot_ms / args.steps,
+                                      "bootstrap_x16": boot_ms / args.steps},
+                "bootstrap_config": {"workload": wb.name, "log_n": wb.log_n, "slots": wb.slots,
+                                     "n_q": len(wb.q_bits), "n_p": len(wb.p_bits), "dnum": wb.dnum,
+                                     "batch": wb.batch, "levels_consumed": 16, "cheb_degree": 60,
+                                     "double_angles": 3, "input": "fresh encryptions at level 0"},
+                "slot_error": {"hmult_rescale": err_mul, "rotation": err_rot, "bootstrap": err_boot},
                 "e2e": e2e, "roofline": roof, "alu_peaks": alu, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": int(launches),
                 "kernel_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]}}
         print(json.dumps(line))
+    bctx.close()
     ctx.close()
     if dist is not None:
         dist.destroy_process_group()
