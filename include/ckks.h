@@ -258,6 +258,15 @@ int ckks_rotate_batch(ckks_ctx *ctx, const ckks_ct *in, const int32_t *k, ckks_c
  * moduli, absorbed by the gadget) while decrypting to the same slots.
  * Outputs must not alias inputs (CKKS_E_PARAM). */
 int ckks_rotate_hoisted(ckks_ctx *ctx, const ckks_ct *in, int n, const int32_t *k, int n_k, ckks_ct *out);
+/* Element-wise batches (Eq. add/sub; plaintext and integer variants):
+ * out[i] = a[i] +- b[i]; out[i] = k * a[i]; out[i] = a[i] * pt (same
+ * plaintext for all, scale a.scale * pt_scale); out[i] = a[i] + pt.
+ * All inputs at one level; out may alias a. */
+int ckks_add_batch(ckks_ctx *ctx, const ckks_ct *a, const ckks_ct *b, ckks_ct *out, int n, int subtract);
+int ckks_mul_int_batch(ckks_ctx *ctx, const ckks_ct *a, int64_t k, ckks_ct *out, int n);
+int ckks_mul_plain_batch(ckks_ctx *ctx, const ckks_ct *a, const uint64_t *pt_dev, double pt_scale, ckks_ct *out,
+                         int n);
+int ckks_add_plain_batch(ckks_ctx *ctx, const ckks_ct *a, const uint64_t *pt_dev, ckks_ct *out, int n);
 /* In-place rescale of n ciphertexts at one level. */
 int ckks_rescale_batch(ckks_ctx *ctx, ckks_ct *inout, int n);
 

@@ -83,6 +83,10 @@ SIGNATURES = {
     "ckks_rotate_batch": (_I, [_V, _CTP, _V, _CTP, _I]),
     "ckks_rescale_batch": (_I, [_V, _CTP, _I]),
     "ckks_rotate_hoisted": (_I, [_V, _CTP, _I, _V, _I, _CTP]),
+    "ckks_add_batch": (_I, [_V, _CTP, _CTP, _CTP, _I, _I]),
+    "ckks_mul_int_batch": (_I, [_V, _CTP, ctypes.c_int64, _CTP, _I]),
+    "ckks_mul_plain_batch": (_I, [_V, _CTP, _V, _D, _CTP, _I]),
+    "ckks_add_plain_batch": (_I, [_V, _CTP, _V, _CTP, _I]),
     "ckks_boot_setup": (_I, [_V]),
     "ckks_boot_rotation_steps": (_I, [_V, _V, _I]),
     "ckks_boot_constant_count": (_I, [_V]),
@@ -404,6 +408,39 @@ class Context:
         _check(self.lib.ckks_rotate_hoisted(self._h, hi, len(cts), ks, len(steps), ho), "ckks_rotate_hoisted")
         for i, c in enumerate(out):
             c.level, c.scale = ho[i].level, ho[i].scale
+
+    def _batch_out(self, a, out):
+        return out if out is not None else [self.new_ct(c.level + 1, c.level, c.scale) for c in a]
+
+    def _finish(self, out, ho):
+        for i, c in enumerate(out):
+            c.level, c.scale = ho[i].level, ho[i].scale
+        return out
+
+    def add_batch(self, a, b, out=None, subtract: bool = False):
+        out = self._batch_out(a, out)
+        ha, hb, ho = self._handles(a), self._handles(b), self._handles(out)
+        _check(self.lib.ckks_add_batch(self._h, ha, hb, ho, len(a), int(subtract)), "ckks_add_batch")
+        return self._finish(out, ho)
+
+    def mul_int_batch(self, a, k: int, out=None):
+        out = self._batch_out(a, out)
+        ha, ho = self._handles(a), self._handles(out)
+        _check(self.lib.ckks_mul_int_batch(self._h, ha, k, ho, len(a)), "ckks_mul_int_batch")
+        return self._finish(out, ho)
+
+    def mul_plain_batch(self, a, pt, pt_scale: float, out=None):
+        out = self._batch_out(a, out)
+        ha, ho = self._handles(a), self._handles(out)
+        _check(self.lib.ckks_mul_plain_batch(self._h, ha, pt.data_ptr(), pt_scale, ho, len(a)),
+               "ckks_mul_plain_batch")
+        return self._finish(out, ho)
+
+    def add_plain_batch(self, a, pt, out=None):
+        out = self._batch_out(a, out)
+        ha, ho = self._handles(a), self._handles(out)
+        _check(self.lib.ckks_add_plain_batch(self._h, ha, pt.data_ptr(), ho, len(a)), "ckks_add_plain_batch")
+        return self._finish(out, ho)
 
     def rescale_batch(self, cts) -> None:
         h = self._handles(cts)

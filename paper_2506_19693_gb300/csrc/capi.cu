@@ -783,6 +783,108 @@ int ckks_rescale_batch(ckks_ctx *c, ckks_ct *cts, int n) {
 
 int ckks_rescale(ckks_ctx *c, ckks_ct *ct) { return ckks_rescale_batch(c, ct, 1); }
 
+// ---- batched element-wise calls (one launch per <= 128 ciphertexts) ----
+namespace {
+int ew_batch_check(ckks_ctx *c, const ckks_ct *a, const ckks_ct *b, ckks_ct *out, int n) {
+  if (!c || !a || !out || n < 0) return CKKS_E_PARAM;
+  for (int i = 0; i < n; ++i) {
+    if (!ct_ok(c, &a[i]) || (b && !ct_ok(c, &b[i])) || !out[i].data) return CKKS_E_PARAM;
+    if (a[i].level != a[0].level || (b && b[i].level != a[0].level) || out[i].n_limbs < a[0].level + 1)
+      return CKKS_E_LEVEL;
+  }
+  return CKKS_OK;
+}
+void ew_fill(ckks_ctx *c, EwArgs &e, const ckks_ct *a, const ckks_ct *b, const u64 *pt, ckks_ct *out, int i0,
+             int cnt) {
+  for (int i = 0; i < cnt; ++i) {
+    e.x0[i] = a[i0 + i].data;
+    e.x1[i] = poly1(&a[i0 + i], c->n);
+    e.y0[i] = b ? b[i0 + i].data : pt;
+    e.y1[i] = b ? poly1(&b[i0 + i], c->n) : nullptr;
+    e.o0[i] = out[i0 + i].data;
+    e.o1[i] = poly1(&out[i0 + i], c->n);
+  }
+}
+void ew_finish(ckks_ctx *c, const ckks_ct *a, ckks_ct *out, int n, const double *scales) {
+  for (int i = 0; i < n; ++i) {
+    out[i].level = a[0].level;
+    out[i].scale = scales[i];
+    out[i].is_ntt = 1;
+    out[i].log_n = c->log_n;
+  }
+}
+}  // namespace
+
+int ckks_add_batch(ckks_ctx *c, const ckks_ct *a, const ckks_ct *b, ckks_ct *out, int n, int subtract) {
+  int rc = ew_batch_check(c, a, b, out, n);
+  if (rc || n == 0) return rc;
+  std::vector<double> s(n);
+  for (int i = 0; i < n; ++i) s[i] = a[i].scale;
+  const int nl = a[0].level + 1;
+  for (int i0 = 0; i0 < n; i0 += MAX_CTS) {
+    const int cnt = std::min(MAX_CTS, n - i0);
+    EwArgs e;
+    ew_fill(c, e, a, b, nullptr, out, i0, cnt);
+    rc = ew_addsub(c, e, nl, cnt, subtract != 0);
+    if (rc) return rc;
+  }
+  ew_finish(c, a, out, n, s.data());
+  return CKKS_OK;
+}
+
+int ckks_mul_int_batch(ckks_ctx *c, const ckks_ct *a, int64_t k, ckks_ct *out, int n) {
+  int rc = ew_batch_check(c, a, nullptr, out, n);
+  if (rc || n == 0) return rc;
+  std::vector<double> s(n);
+  for (int i = 0; i < n; ++i) s[i] = a[i].scale;
+  const int nl = a[0].level + 1;
+  for (int i0 = 0; i0 < n; i0 += MAX_CTS) {
+    const int cnt = std::min(MAX_CTS, n - i0);
+    EwArgs e;
+    ew_fill(c, e, a, nullptr, nullptr, out, i0, cnt);
+    rc = ew_mul_int(c, e, nl, cnt, k);
+    if (rc) return rc;
+  }
+  ew_finish(c, a, out, n, s.data());
+  return CKKS_OK;
+}
+
+int ckks_mul_plain_batch(ckks_ctx *c, const ckks_ct *a, const uint64_t *pt, double pt_scale, ckks_ct *out, int n) {
+  if (!pt) return CKKS_E_PARAM;
+  int rc = ew_batch_check(c, a, nullptr, out, n);
+  if (rc || n == 0) return rc;
+  std::vector<double> s(n);
+  for (int i = 0; i < n; ++i) s[i] = a[i].scale * pt_scale;
+  const int nl = a[0].level + 1;
+  for (int i0 = 0; i0 < n; i0 += MAX_CTS) {
+    const int cnt = std::min(MAX_CTS, n - i0);
+    EwArgs e;
+    ew_fill(c, e, a, nullptr, pt, out, i0, cnt);
+    rc = ew_plain(c, e, nl, cnt, 0);
+    if (rc) return rc;
+  }
+  ew_finish(c, a, out, n, s.data());
+  return CKKS_OK;
+}
+
+int ckks_add_plain_batch(ckks_ctx *c, const ckks_ct *a, const uint64_t *pt, ckks_ct *out, int n) {
+  if (!pt) return CKKS_E_PARAM;
+  int rc = ew_batch_check(c, a, nullptr, out, n);
+  if (rc || n == 0) return rc;
+  std::vector<double> s(n);
+  for (int i = 0; i < n; ++i) s[i] = a[i].scale;
+  const int nl = a[0].level + 1;
+  for (int i0 = 0; i0 < n; i0 += MAX_CTS) {
+    const int cnt = std::min(MAX_CTS, n - i0);
+    EwArgs e;
+    ew_fill(c, e, a, nullptr, pt, out, i0, cnt);
+    rc = ew_plain(c, e, nl, cnt, 1);
+    if (rc) return rc;
+  }
+  ew_finish(c, a, out, n, s.data());
+  return CKKS_OK;
+}
+
 int ckks_automorph(ckks_ctx *c, const ckks_ct *a, uint64_t g, ckks_ct *out) {
   if (!c || !ct_ok(c, a) || !out || !out->data) return CKKS_E_PARAM;
   if (out->n_limbs < a->level + 1) return CKKS_E_LEVEL;

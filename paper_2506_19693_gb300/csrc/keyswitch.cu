@@ -87,6 +87,10 @@ struct IPArgs {
   u64 *acc[MAX_CTS];               // [2][ext][N]
 };
 
+// Grid: (coefficient blocks, extended limbs, groups of IP_GROUP outputs).
+// Within a group the thread walks the outputs, reloading key words only when
+// the key changes (a relinearisation batch shares one key).
+constexpr int IP_GROUP = 8;
 __global__ void __launch_bounds__(TPB) k_inner(const IPArgs a) {
   const u32 k = blockIdx.x * TPB + threadIdx.x;
   const int t = blockIdx.y;
@@ -95,7 +99,9 @@ __global__ void __launch_bounds__(TPB) k_inner(const IPArgs a) {
   const int kl = a.keylimb_of[t];
   u64 kb[MAXD], ka[MAXD];
   const u64 *cur = nullptr;
-  for (int p = 0; p < a.np; ++p) {
+  const int p_end = min(a.np, (int)(blockIdx.z + 1) * IP_GROUP);
+#pragma unroll 2
+  for (int p = blockIdx.z * IP_GROUP; p < p_end; ++p) {
     if (a.key[p] != cur) {
       cur = a.key[p];
 #pragma unroll
@@ -291,7 +297,7 @@ int ks_tail(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *cons
       a.gal[i] = gal ? gal[i] : 1u;
       a.acc[i] = acc[i];
     }
-    dim3 g((n + TPB - 1) / TPB, ext);
+    dim3 g((n + TPB - 1) / TPB, ext, (nv + IP_GROUP - 1) / IP_GROUP);
     PROF_LAUNCH(c, PK_INNER, (u64)nv * ext, (k_inner<<<g, TPB, 0, c->stream>>>(a)));
     if (cudaGetLastError() != cudaSuccess) return CKKS_E_CUDA;
   }

@@ -1,0 +1,107 @@
+"""ReBoot RE-Block step on the GPU against the oracle (bit-exact limbs on a
+small ring, without the bootstrap whose own parity is tested separately)
+and against the FP64 slot computation at the config-3 size (N = 2^16,
+r x c = 256 x 128, 784 -> 128 -> 10) including the bootstrap of the weights."""
+import numpy as np
+import pytest
+
+import synthetic_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+
+def _data(seed, b, k0, k1, o):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0, 1, size=(b, k0))
+    y = np.eye(o)[rng.integers(0, o, size=b)]
+    w = rng.normal(0, 1 / np.sqrt(k0), size=(k0, k1))
+    ws = rng.normal(0, 1 / np.sqrt(k1), size=(k1, o))
+    return x, y, w, ws
+
+
+def test_reboot_step_bit_exact_small_ring():
+    import torch
+    import oracle
+    import oracle.bootstrap as ob
+    import oracle.reboot as orb
+    import paper_2506_19693_gb300 as ck
+    import paper_2506_19693_gb300.reboot as rb
+    torch.cuda.set_device(0)
+    w_ = si.BOOT_SMALL
+    g = rb.Geometry(32, 64, 60, 64, 10)
+    go = orb.Geometry(32, 64, 60, 64, 10)
+    ctx = ck.Context.from_workload(w_)
+    try:
+        ctx.keygen(1, rot_steps=g.rotation_steps())
+        o = oracle.Oracle(w_.log_n, w_.q_bits, w_.p_bits, w_.dnum, w_.h, w_.sigma)
+        o.keygen(1)
+        o.gen_rotation_keys(go.rotation_steps())
+        x, y, w, ws = _data(5, 2, g.k0, g.k1, g.o)
+        scale, lvl = 2.0 ** w_.log2_scale, 8
+        gamma, eta, mu = 0.01, 0.001, 0.9
+        seed = [1000]
+
+        def both(vec):
+            m = o.encode(vec, scale)
+            seed[0] += 1
+            return (ctx.encrypt(ctx.pt_from_int(m, lvl), lvl, scale, seed[0]),
+                    o.encrypt(o.pt_from_int(m, lvl), lvl, scale, seed[0]))
+
+        Wp = [both(t) for t in orb.tile_weights(w, go)]
+        Vp = [both(np.full(g.r * g.c, 0.01)) for _ in range(g.tiles)]
+        Wsp = both(orb.pack_colwise(ws, go))
+        Vsp = both(np.full(g.r * g.c, 0.02))
+        xsp = [[both(t) for t in orb.tile_inputs(xi, go)] for xi in x]
+        ysp = [both(orb.pack_expanded(yi, go)) for yi in y]
+        mask = {l: o.encode(orb.first_column_mask(go), float(o.q[l])) for l in range(lvl + 1)}
+        gpu = rb.REBlock(ctx, g, gamma, eta, mu, mask_coeffs=mask)
+        orc = orb.REBlock(o, go, gamma, eta, mu, mask_coeffs=None)
+        orc._mask = None
+        # the oracle encodes the same mask itself at each level (same function, same integers)
+        for first in (True, False):
+            st_g = ([p[0] for p in Wp], [p[0] for p in Vp], Wsp[0], Vsp[0], None)
+            st_o = ([p[1] for p in Wp], [p[1] for p in Vp], Wsp[1], Vsp[1], None)
+            rg = gpu.step(st_g, [[p[0] for p in s] for s in xsp], [p[0] for p in ysp], first, bootstrap=False)
+            ro = orc.step(st_o, [[p[1] for p in s] for s in xsp], [p[1] for p in ysp], first, bootstrap=False)
+            for cg, co in zip(rg[0] + rg[1] + [rg[2], rg[3], rg[4]], ro[0] + ro[1] + [ro[2], ro[3], ro[4]]):
+                assert (cg.level, cg.scale) == (co.level, co.scale)
+                assert np.array_equal(ctx.export_ct(cg), co.data)
+    finally:
+        ctx.close()
+
+
+def test_reboot_step_config3_size_with_bootstrap():
+    import torch
+    import oracle.reboot as orb
+    import paper_2506_19693_gb300 as ck
+    import paper_2506_19693_gb300.reboot as rb
+    torch.cuda.set_device(0)
+    w_ = si.BOOT
+    g = rb.Geometry(256, 128, 784, 128, 10)
+    go = orb.Geometry(256, 128, 784, 128, 10)
+    ctx = ck.Context.from_workload(w_)
+    try:
+        ctx.keygen_boot(1, rot_steps=g.rotation_steps())
+        ctx.boot_setup()
+        x, y, w, ws = _data(6, 4, g.k0, g.k1, g.o)
+        scale, lvl = 2.0 ** w_.log2_scale, 8
+        gamma, eta, mu = 0.001 / 4, 0.001, 0.9
+        seeds = iter(range(5000, 6000))
+        enc = lambda v: ctx.encrypt(ctx.encode(v, lvl, scale), lvl, scale, next(seeds))  # noqa: E731
+        W = [enc(t) for t in rb.weight_tiles(w, g)]
+        V = [enc(np.zeros(g.r * g.c)) for _ in range(g.tiles)]
+        Ws, Vs = enc(rb.pack_colwise(ws, g)), enc(np.zeros(g.r * g.c))
+        xs = [[enc(t) for t in rb.input_tiles(xi, g)] for xi in x]
+        ys = [enc(rb.pack_expanded(yi, g)) for yi in y]
+        blk = rb.REBlock(ctx, g, gamma, eta, mu)
+        nw, nv, ws1, vs1, dws = blk.step((W, V, Ws, Vs, None), xs, ys, first=True, bootstrap=True)
+        assert all(c.level == len(w_.q_bits) - 17 for c in nw + nv + [ws1, vs1])
+        pW = orb.tile_weights(w, go)
+        ref = orb.plain_step((pW, [np.zeros_like(t) for t in pW], orb.pack_colwise(ws, go),
+                              np.zeros(g.r * g.c), None),
+                             [orb.tile_inputs(xi, go) for xi in x], [orb.pack_expanded(yi, go) for yi in y], go,
+                             gamma, eta, mu, first=True)
+        for ct, want in zip(nw + [ws1], ref[0] + [ref[2]]):
+            assert np.max(np.abs(ctx.decrypt_decode(ct).real - want)) < 2.0 ** -12
+    finally:
+        ctx.close()
