@@ -232,7 +232,7 @@ def run_gpu(args):
             dist.barrier()
 
     w = si.PLAIN
-    B = w.batch
+    B = 8 if args.small else w.batch
     level = len(w.q_bits) - 1
     scale = 2.0 ** w.log2_scale
     stream = torch.cuda.current_stream()
@@ -247,14 +247,15 @@ def run_gpu(args):
 
     # bootstrapping workload: N = 2^16, 2^15 slots, 16 exhausted (level-0) ciphertexts
     wb = si.BOOT
+    nb = 2 if args.small else wb.batch
     bctx = ck.Context.from_workload(wb, stream=stream)
     bctx.keygen_boot(2)
     bctx.boot_setup()
     db = 2.0 ** wb.log2_scale
-    zb = si.messages(300 + rank, wb.batch, wb.slots)
-    bseeds = si.enc_seeds(300 + rank, wb.batch)
-    BIN = [bctx.encrypt(bctx.encode(zb[i], 0, db), 0, db, bseeds[i]) for i in range(wb.batch)]
-    BOUT = [bctx.new_ct(len(wb.q_bits) - 16) for _ in range(wb.batch)]
+    zb = si.messages(300 + rank, nb, wb.slots)
+    bseeds = si.enc_seeds(300 + rank, nb)
+    BIN = [bctx.encrypt(bctx.encode(zb[i], 0, db), 0, db, bseeds[i]) for i in range(nb)]
+    BOUT = [bctx.new_ct(len(wb.q_bits) - 16) for _ in range(nb)]
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
@@ -315,7 +316,7 @@ def run_gpu(args):
     mul_ms, rot_ms, boot_ms, step_ms = t.tolist()
     value = world * B * args.steps / (mul_ms / 1e3)
     rot_rate = world * B * len(w.rot_steps) * args.steps / (rot_ms / 1e3)
-    boot_rate = world * wb.batch * args.steps / (boot_ms / 1e3)
+    boot_rate = world * nb * args.steps / (boot_ms / 1e3)
 
     # roofline of the dominant kernel class
     hbm, peak_kind = peaks()
@@ -324,13 +325,20 @@ def run_gpu(args):
     ndig = -(-len(w.q_bits) // (-(-len(w.q_bits) // w.dnum)))
     roof = roofline(prof, w, ndig, hbm, peak_kind, alu)
 
+    # ReBoot RE-Block training step (Alg. 1 + Alg. 2 + Bootstrap of W, V), the
+    # synthetic MLP workload: 128 samples x 784 features in [0, 1], 784 -> 128 -> 10,
+    # r x c = 256 x 128, on the bootstrapping context
+    reboot = None
+    if not (args.no_reboot or args.small):
+        reboot = run_reboot_step(bctx, wb, torch, stream, rank)
+
     # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
-    if not args.no_e2e:
+    if not (args.no_e2e or args.small):
         e2e = run_e2e(ctx, torch, A, Bc, OUT, level, args, dist)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.small):
         sample = OracleSample(w)
         dt, threads = sample.time(), sample.threads
         cpu = {"value": 1.0 / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
@@ -346,9 +354,10 @@ def run_gpu(args):
                                       "bootstrap_x16": boot_ms / args.steps},
                 "bootstrap_config": {"workload": wb.name, "log_n": wb.log_n, "slots": wb.slots,
                                      "n_q": len(wb.q_bits), "n_p": len(wb.p_bits), "dnum": wb.dnum,
-                                     "batch": wb.batch, "levels_consumed": 16, "cheb_degree": 60,
+                                     "batch": nb, "levels_consumed": 16, "cheb_degree": 60,
                                      "double_angles": 3, "input": "fresh encryptions at level 0"},
                 "slot_error": {"hmult_rescale": err_mul, "rotation": err_rot, "bootstrap": err_boot},
+                "reboot_step": reboot,
                 "e2e": e2e, "roofline": roof, "alu_peaks": alu, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": int(launches),
                 "kernel_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]}}
@@ -358,6 +367,42 @@ def run_gpu(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def run_reboot_step(bctx, wb, torch, stream, rank):
+    """One warm-up and one timed RE-Block step at the config-3 size."""
+    import paper_2506_19693_gb300.reboot as rb
+    g = rb.Geometry(256, 128, 784, 128, 10)
+    for k in g.rotation_steps():
+        bctx.keygen_galois(bctx.galois_elt(k))
+    b = 128
+    rng = np.random.default_rng(400 + rank)
+    x = rng.uniform(0, 1, size=(b, g.k0))
+    y = np.eye(g.o)[rng.integers(0, g.o, size=b)]
+    w = rng.normal(0, 1 / np.sqrt(g.k0), size=(g.k0, g.k1))
+    ws = rng.normal(0, 1 / np.sqrt(g.k1), size=(g.k1, g.o))
+    scale, lvl = 2.0 ** wb.log2_scale, len(wb.q_bits) - 17
+    seeds = iter(range(10 ** 6, 2 * 10 ** 6))
+    enc = lambda v: bctx.encrypt(bctx.encode(v, lvl, scale), lvl, scale, next(seeds))  # noqa: E731
+    state = ([enc(t) for t in rb.weight_tiles(w, g)], [enc(np.zeros(g.r * g.c)) for _ in range(g.tiles)],
+             enc(rb.pack_colwise(ws, g)), enc(np.zeros(g.r * g.c)), None)
+    xs = [[enc(t) for t in rb.input_tiles(xi, g)] for xi in x]
+    ys = [enc(rb.pack_expanded(yi, g)) for yi in y]
+    # gamma 0.001 and eta 0.001, mu 0.9 (MNIST / eMLP-1 hyperparameters), 1/b folded into gamma
+    blk = rb.REBlock(bctx, g, 0.001 / b, 0.001, 0.9)
+    state = blk.step(state, xs, ys, first=True)  # warm-up (iteration 1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = bctx.launch_count()
+    e0.record(stream)
+    state = blk.step(state, xs, ys, first=False)  # iteration 2: NAG with velocity
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"seconds_per_step": ms / 1e3, "samples": b, "geometry": "r=256 c=128, 784->128->10, 4 input tiles",
+            "ops": "per sample 12 ct-ct mult + 30 rotations; NAG on 5 weight cts; 10 bootstraps",
+            "kernel_launches": bctx.launch_count() - l0,
+            "paper_cpu_context_s": {"eMLP-1 (Table 6, 2x Xeon Gold 5318S)": 190.32}}
 
 
 def run_e2e(ctx, torch, A, Bc, OUT, level, args, dist):
@@ -400,6 +445,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-reboot", action="store_true")
+    ap.add_argument("--small", action="store_true",
+                    help="8 pairs and 2 bootstraps: a few GB on the device, for ncu captures")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

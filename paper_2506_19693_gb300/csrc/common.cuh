@@ -50,11 +50,12 @@ __device__ __forceinline__ u64 reduce128(u64 hi, u64 lo, const ModInfo &m) {
 __device__ __forceinline__ u64 mulmod(u64 a, u64 b, const ModInfo &m) {
   return reduce128(__umul64hi(a, b), a * b, m);
 }
-// 128-bit multiply-accumulate
+// 128-bit multiply-accumulate (hi:lo += a * b) as one carry chain
 __device__ __forceinline__ void mac128(u64 &hi, u64 &lo, u64 a, u64 b) {
-  u64 pl = a * b, ph = __umul64hi(a, b);
-  lo += pl;
-  hi += ph + (lo < pl ? 1 : 0);
+  asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\t"
+      "madc.hi.u64 %1, %2, %3, %1;"
+      : "+l"(lo), "+l"(hi)
+      : "l"(a), "l"(b));
 }
 __device__ __forceinline__ u64 addmod(u64 a, u64 b, u64 q) { return csub(a + b, q); }
 __device__ __forceinline__ u64 submod(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }

@@ -87,41 +87,40 @@ struct IPArgs {
   u64 *acc[MAX_CTS];               // [2][ext][N]
 };
 
-// Grid: (coefficient blocks, extended limbs, groups of IP_GROUP outputs).
-// Within a group the thread walks the outputs, reloading key words only when
-// the key changes (a relinearisation batch shares one key).
+// Grid: (groups of IP_GROUP outputs, coefficient blocks, extended limbs).
+// The group index varies fastest, so the CTAs that read one block of the
+// lifted digits (all outputs of a hoisted rotation set, all ciphertexts of a
+// relinearisation batch) run back to back and share it through L2.  Within a
+// group the thread walks the outputs, reloading key words only when the key
+// changes.
 constexpr int IP_GROUP = 8;
-__global__ void __launch_bounds__(TPB) k_inner(const IPArgs a) {
-  const u32 k = blockIdx.x * TPB + threadIdx.x;
-  const int t = blockIdx.y;
+template <int NDIG>
+__global__ void __launch_bounds__(TPB, NDIG <= 3 ? 4 : 2) k_inner(const IPArgs a) {
+  const u32 k = blockIdx.y * TPB + threadIdx.x;
+  const int t = blockIdx.z;
   if (k >= a.n) return;
   const ModInfo &m = a.mods[a.mod_of[t]];
   const int kl = a.keylimb_of[t];
-  u64 kb[MAXD], ka[MAXD];
+  u64 kb[NDIG], ka[NDIG];
   const u64 *cur = nullptr;
-  const int p_end = min(a.np, (int)(blockIdx.z + 1) * IP_GROUP);
-#pragma unroll 2
-  for (int p = blockIdx.z * IP_GROUP; p < p_end; ++p) {
+  const int p_end = min(a.np, (int)(blockIdx.x + 1) * IP_GROUP);
+  for (int p = blockIdx.x * IP_GROUP; p < p_end; ++p) {
     if (a.key[p] != cur) {
       cur = a.key[p];
 #pragma unroll
-      for (int j = 0; j < MAXD; ++j) {
-        if (j < a.ndig) {
-          kb[j] = cur[((size_t)(2 * j) * a.key_ext + kl) * a.n + k];
-          ka[j] = cur[((size_t)(2 * j + 1) * a.key_ext + kl) * a.n + k];
-        }
+      for (int j = 0; j < NDIG; ++j) {
+        kb[j] = cur[((size_t)(2 * j) * a.key_ext + kl) * a.n + k];
+        ka[j] = cur[((size_t)(2 * j + 1) * a.key_ext + kl) * a.n + k];
       }
     }
     const u32 src = gal_src(k, a.gal[p], a.n, a.log_n);
     u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0;
 #pragma unroll
-    for (int j = 0; j < MAXD; ++j) {
-      if (j < a.ndig) {
-        const u64 v = (t >= a.lo[j] && t < a.hi[j]) ? a.d[p][(size_t)t * a.n + src]
-                                                     : a.ext_buf[p][((size_t)j * a.ext + t) * a.n + src];
-        mac128(h0, l0, v, kb[j]);
-        mac128(h1, l1, v, ka[j]);
-      }
+    for (int j = 0; j < NDIG; ++j) {
+      const u64 v = (t >= a.lo[j] && t < a.hi[j]) ? a.d[p][(size_t)t * a.n + src]
+                                                   : a.ext_buf[p][((size_t)j * a.ext + t) * a.n + src];
+      mac128(h0, l0, v, kb[j]);
+      mac128(h1, l1, v, ka[j]);
     }
     a.acc[p][(size_t)t * a.n + k] = reduce128(h0, l0, m);
     a.acc[p][((size_t)a.ext + t) * a.n + k] = reduce128(h1, l1, m);
@@ -297,8 +296,14 @@ int ks_tail(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *cons
       a.gal[i] = gal ? gal[i] : 1u;
       a.acc[i] = acc[i];
     }
-    dim3 g((n + TPB - 1) / TPB, ext, (nv + IP_GROUP - 1) / IP_GROUP);
-    PROF_LAUNCH(c, PK_INNER, (u64)nv * ext, (k_inner<<<g, TPB, 0, c->stream>>>(a)));
+    dim3 g((nv + IP_GROUP - 1) / IP_GROUP, (n + TPB - 1) / TPB, ext);
+    switch (ndig) {
+#define ICASE(D) \
+  case D: PROF_LAUNCH(c, PK_INNER, (u64)nv * ext, (k_inner<D><<<g, TPB, 0, c->stream>>>(a))); break;
+      ICASE(1) ICASE(2) ICASE(3) ICASE(4) ICASE(5) ICASE(6) ICASE(7) ICASE(8)
+#undef ICASE
+      default: return CKKS_E_PARAM;
+    }
     if (cudaGetLastError() != cudaSuccess) return CKKS_E_CUDA;
   }
   std::vector<const u64 *> ps(2 * nv);

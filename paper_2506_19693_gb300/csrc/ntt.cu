@@ -82,7 +82,7 @@ __device__ __forceinline__ void inv_step(u64 (&v)[1 << K], u32 mg, const ulonglo
 
 // ---------------------------------------------------------------- forward
 template <int LH, int S1>
-__global__ void __launch_bounds__(THREADS) fwd_pass_a(const NttParams prm) {
+__global__ void __launch_bounds__(THREADS, 4) fwd_pass_a(const NttParams prm) {
   constexpr int H = 1 << LH, S2 = LH - S1;
   __shared__ u64 sm[H * CA];
   const int limb = blockIdx.y, poly = blockIdx.z;
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(THREADS) fwd_pass_a(const NttParams prm) {
 }
 
 template <int LH>
-__global__ void __launch_bounds__(THREADS) fwd_pass_b(const NttParams prm, int from_src) {
+__global__ void __launch_bounds__(THREADS, 4) fwd_pass_b(const NttParams prm, int from_src) {
   constexpr int H = 1 << LH, U1 = 4, U2 = LB - U1;
   __shared__ u64 sm[RB * BROW + (RB * BROW >> 4)];
   const int limb = blockIdx.y, poly = blockIdx.z;
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(THREADS) fwd_pass_b(const NttParams prm, int f
 
 // ---------------------------------------------------------------- inverse
 template <int LH>
-__global__ void __launch_bounds__(THREADS) inv_pass_b(const NttParams prm) {
+__global__ void __launch_bounds__(THREADS, 4) inv_pass_b(const NttParams prm) {
   constexpr int H = 1 << LH, U1 = 4, U2 = LB - U1;
   __shared__ u64 sm[RB * BROW + (RB * BROW >> 4)];
   const int limb = blockIdx.y, poly = blockIdx.z;
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(THREADS) inv_pass_b(const NttParams prm) {
 }
 
 template <int LH, int S1>
-__global__ void __launch_bounds__(THREADS) inv_pass_a(const NttParams prm) {
+__global__ void __launch_bounds__(THREADS, 4) inv_pass_a(const NttParams prm) {
   constexpr int H = 1 << LH, S2 = LH - S1;
   __shared__ u64 sm[H * CA];
   const int limb = blockIdx.y, poly = blockIdx.z;
