@@ -331,6 +331,9 @@ def run_gpu(args):
     reboot = None
     if not (args.no_reboot or args.small):
         reboot = run_reboot_step(bctx, wb, torch, stream, rank)
+    uneven = None
+    if not (args.no_uneven or args.small):
+        uneven = run_uneven(ctx, w, torch, stream, rank, reps=max(3, args.steps), warmup=args.warmup)
 
     # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -357,7 +360,7 @@ def run_gpu(args):
                                      "batch": nb, "levels_consumed": 16, "cheb_degree": 60,
                                      "double_angles": 3, "input": "fresh encryptions at level 0"},
                 "slot_error": {"hmult_rescale": err_mul, "rotation": err_rot, "bootstrap": err_boot},
-                "reboot_step": reboot,
+                "reboot_step": reboot, "uneven_batch": uneven,
                 "e2e": e2e, "roofline": roof, "alu_peaks": alu, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": int(launches),
                 "kernel_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]}}
@@ -367,6 +370,56 @@ def run_gpu(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def run_uneven(ctx16, w, torch, stream, rank, reps, warmup):
+    """256 independent operations over ring degrees 2^15 / 2^16 (p = 1/2) and
+    levels uniform in 4..23, one third each HMult+relin(+rescale), rotation by
+    a random power of two and rescale; captured once as a CUDA graph and
+    replayed.  Returns ops/s of the graph replays and of the eager executor."""
+    import paper_2506_19693_gb300 as ck
+    ctx15 = ck.Context(15, w.q_bits, w.p_bits, w.dnum, w.h, w.sigma, w.log2_scale, stream=stream)
+    ctx15.keygen(5, rot_steps=[1 << k for k in range(14)])
+    tuned = {"n65536": ctx16.tune(len(w.q_bits) - 1, 64), "n32768": ctx15.tune(len(w.q_bits) - 1, 64)}
+    rng = np.random.default_rng(500 + rank)
+    scale = 2.0 ** w.log2_scale
+    ops = []
+    for i in range(256):
+        c = ctx16 if rng.random() < 0.5 else ctx15
+        level = int(rng.integers(4, len(w.q_bits)))
+        z = si.messages(600 + i, 2, c.n // 2)
+        a = c.encrypt(c.encode(z[0], level, scale), level, scale, 900000 + i)
+        out = c.new_ct(level + 1)
+        kind = i % 3
+        if kind == 0:
+            b = c.encrypt(c.encode(z[1], level, scale), level, scale, 950000 + i)
+            ops.append(ck.Op(c, ck.OP_MUL_RELIN, a, out, b=b, rescale=True))
+        elif kind == 1:
+            ops.append(ck.Op(c, ck.OP_ROTATE, a, out, k=int(1 << rng.integers(0, c.log_n - 2))))
+        else:
+            ops.append(ck.Op(c, ck.OP_RESCALE, a, out))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ck.execute(ops)
+    torch.cuda.synchronize()
+    eager_s = time.perf_counter() - t0
+    gs = torch.cuda.Stream()  # captured graphs replay on a created stream; time on that stream
+    g = ck.Graph(ops, stream=gs)
+    for _ in range(warmup):
+        g.launch()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(gs)
+    for _ in range(reps):
+        g.launch()
+    e1.record(gs)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    g.close()
+    ctx15.close()
+    return {"ops_per_s_graph": 256 / (ms / 1e3), "ms_per_batch_graph": ms, "ops_per_s_eager_first_run": 256 / eager_s,
+            "ops": "256: 1/3 HMult+relin+rescale, 1/3 Rot(2^k), 1/3 rescale; N in {2^15, 2^16} p=1/2; "
+                   "levels U{4..23}", "replays": reps, "tuned_inner_group": tuned}
 
 
 def run_reboot_step(bctx, wb, torch, stream, rank):
@@ -446,6 +499,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-reboot", action="store_true")
+    ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--small", action="store_true",
                     help="8 pairs and 2 bootstraps: a few GB on the device, for ncu captures")
     args = ap.parse_args()

@@ -270,6 +270,44 @@ int ckks_add_plain_batch(ckks_ctx *ctx, const ckks_ct *a, const uint64_t *pt_dev
 /* In-place rescale of n ciphertexts at one level. */
 int ckks_rescale_batch(ckks_ctx *ctx, ckks_ct *inout, int n);
 
+/* ---- uneven batches: executor, graph capture, tuning ------------------- */
+
+#define CKKS_OP_MUL_RELIN 1 /* out = a * b relinearised (rescaled when rescale != 0) */
+#define CKKS_OP_ROTATE 2    /* out = Rot(a, k)                                         */
+#define CKKS_OP_RESCALE 3   /* out = rescale(a), a left unchanged                      */
+
+/* One operation of an uneven batch.  a, b, out point to caller-owned handles;
+ * out must not alias a or b.  Operations of one batch are independent (none
+ * reads another's output); each may use its own context (ring degree). */
+typedef struct {
+  int op;
+  ckks_ctx *ctx;
+  const ckks_ct *a;
+  const ckks_ct *b;
+  ckks_ct *out;
+  int32_t k;
+  int rescale;
+} ckks_op_desc;
+
+typedef struct ckks_graph ckks_graph;
+
+/* Run n independent operations, grouped by (context, operation, level) so each
+ * group is one batched launch set on its context's stream; the out handles'
+ * level and scale are updated. */
+int ckks_exec(const ckks_op_desc *ops, int n);
+/* Run the batch once (sizing every scratch buffer), then capture the same
+ * grouped launches on `stream` into a CUDA graph; *out replays the whole
+ * batch with one cudaGraphLaunch.  The graph reads and writes the buffers the
+ * handles pointed to at capture time.  `cuda_stream` must be a created
+ * stream (not the legacy or per-thread default stream: CKKS_E_PARAM). */
+int ckks_exec_capture(const ckks_op_desc *ops, int n, void *cuda_stream, ckks_graph **out);
+int ckks_graph_launch(ckks_graph *graph, void *cuda_stream);
+int ckks_graph_destroy(ckks_graph *graph);
+/* Autotune the key inner product for this context: time outputs-per-thread
+ * groups of 2..32 on a batch of `batch` key switches at `level` and keep the
+ * fastest for later calls; *chosen (may be NULL) receives it. */
+int ckks_tune(ckks_ctx *ctx, int level, int batch, int *chosen);
+
 /* ---- checkpoint helpers ------------------------------------------------- */
 
 /* Copy a ciphertext's active limbs to/from host memory as

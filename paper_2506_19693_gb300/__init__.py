@@ -40,6 +40,15 @@ class CkksCt(ctypes.Structure):
                 ("n_limbs", ctypes.c_uint32), ("is_ntt", ctypes.c_uint32), ("scale", ctypes.c_double)]
 
 
+OP_MUL_RELIN, OP_ROTATE, OP_RESCALE = 1, 2, 3
+
+
+class CkksOpDesc(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("ctx", ctypes.c_void_p), ("a", ctypes.POINTER(CkksCt)),
+                ("b", ctypes.POINTER(CkksCt)), ("out", ctypes.POINTER(CkksCt)), ("k", ctypes.c_int32),
+                ("rescale", ctypes.c_int)]
+
+
 # C-ABI symbols and signatures, in header order.
 _V, _I, _U64, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_double
 _CTP = ctypes.POINTER(CkksCt)
@@ -94,6 +103,11 @@ SIGNATURES = {
     "ckks_boot_export": (_I, [_V, _V, _I, _V, _I]),
     "ckks_bootstrap": (_I, [_V, _CTP, _CTP]),
     "ckks_bootstrap_batch": (_I, [_V, _CTP, _CTP, _I]),
+    "ckks_exec": (_I, [_V, _I]),
+    "ckks_exec_capture": (_I, [_V, _I, _V, ctypes.POINTER(_V)]),
+    "ckks_graph_launch": (_I, [_V, _V]),
+    "ckks_graph_destroy": (_I, [_V]),
+    "ckks_tune": (_I, [_V, _I, _I, ctypes.POINTER(_I)]),
     "ckks_ct_export": (_I, [_V, _CTP, _V]),
     "ckks_ct_import": (_I, [_V, _V, _CTP]),
     "ckks_status_str": (ctypes.c_char_p, [_I]),
@@ -228,6 +242,12 @@ class Context:
         m, b = ctypes.c_double(), ctypes.c_double()
         _check(self.lib.ckks_alu_peaks(self._h, ctypes.byref(m), ctypes.byref(b)), "ckks_alu_peaks")
         return m.value, b.value
+
+    def tune(self, level: int, batch: int) -> int:
+        """Autotune the key inner product for batches of this shape; returns the choice."""
+        ch = ctypes.c_int()
+        _check(self.lib.ckks_tune(self._h, level, batch, ctypes.byref(ch)), "ckks_tune")
+        return ch.value
 
     def launch_count(self) -> int:
         c = ctypes.c_uint64()
@@ -521,6 +541,69 @@ class Context:
         h = ct.handle(self.log_n)
         _check(self.lib.ckks_ct_import(self._h, arr.ctypes.data, ctypes.byref(h)), "ckks_ct_import")
         return ct
+
+
+class Op:
+    """One operation of an uneven batch: (context, kind, a, b, out, k, rescale)."""
+
+    def __init__(self, ctx: Context, op: int, a: Ciphertext, out: Ciphertext, b: Ciphertext | None = None,
+                 k: int = 0, rescale: bool = False):
+        self.ctx, self.op, self.a, self.b, self.out, self.k, self.rescale = ctx, op, a, b, out, k, rescale
+
+
+def _op_array(ops):
+    arr = (CkksOpDesc * len(ops))()
+    keep = []
+    for i, o in enumerate(ops):
+        ha = o.a.handle(o.ctx.log_n)
+        hb = o.b.handle(o.ctx.log_n) if o.b is not None else None
+        ho = o.out.handle(o.ctx.log_n)
+        keep += [ha, hb, ho]
+        arr[i] = CkksOpDesc(o.op, o.ctx._h.value, ctypes.pointer(ha), ctypes.pointer(hb) if hb else None,
+                            ctypes.pointer(ho), o.k, int(o.rescale))
+    return arr, keep
+
+
+def execute(ops) -> None:
+    """Run independent operations grouped by (context, kind, level)."""
+    lib = load_library()
+    arr, keep = _op_array(ops)
+    _check(lib.ckks_exec(arr, len(ops)), "ckks_exec")
+    for i, o in enumerate(ops):
+        o.out.level, o.out.scale = arr[i].out.contents.level, arr[i].out.contents.scale
+
+
+class Graph:
+    """A captured uneven batch: launch() replays every operation at once."""
+
+    def __init__(self, ops, stream=None):
+        import torch
+        self.lib = load_library()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        if self.stream.cuda_stream == 0:  # the legacy default stream cannot be captured
+            self.stream = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        arr, self._keep = _op_array(ops)
+        g = ctypes.c_void_p()
+        _check(self.lib.ckks_exec_capture(arr, len(ops), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(g)),
+               "ckks_exec_capture")
+        self._g = g
+        for i, o in enumerate(ops):
+            o.out.level, o.out.scale = arr[i].out.contents.level, arr[i].out.contents.scale
+
+    def launch(self) -> None:
+        _check(self.lib.ckks_graph_launch(self._g, ctypes.c_void_p(self.stream.cuda_stream)), "ckks_graph_launch")
+
+    def close(self) -> None:
+        if getattr(self, "_g", None):
+            self.lib.ckks_graph_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def tensor_to_u64(t) -> np.ndarray:

@@ -12,6 +12,7 @@
 // ---------------------------------------------------------------- scratch
 int ensure_scratch(ckks_ctx *c, size_t words) {
   if (words <= c->scratch_words) return CKKS_OK;
+  if (c->capturing) return CKKS_E_STATE;  // no allocation inside a graph capture
   CK_CUDA(cudaStreamSynchronize(c->stream));
   if (c->scratch) cudaFree(c->scratch);
   c->scratch = nullptr;
@@ -25,6 +26,7 @@ int ensure_scratch(ckks_ctx *c, size_t words) {
 }
 int ensure_fscratch(ckks_ctx *c, size_t words) {
   if (words <= c->fscratch_words) return CKKS_OK;
+  if (c->capturing) return CKKS_E_STATE;
   CK_CUDA(cudaStreamSynchronize(c->stream));
   if (c->fscratch) cudaFree(c->fscratch);
   c->fscratch = nullptr;

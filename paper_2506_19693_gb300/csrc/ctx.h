@@ -72,6 +72,8 @@ struct ckks_ctx {
   size_t pinned_bytes = 0;
   size_t table_bytes = 0;
   Profiler prof;
+  int ip_group = 8;                  // key inner product: outputs per thread (ckks_tune)
+  bool capturing = false;            // inside a CUDA-graph capture: no allocation, no sync
 
   size_t limb_words() const { return (size_t)n; }
   int ext_limbs(int level) const { return level + 1 + n_p; }

@@ -1,0 +1,223 @@
+// Batched executor for uneven workloads: many independent operations on
+// ciphertexts of different ring degrees and levels, grouped so that each
+// (context, operation, level) group runs as one batched launch set, and
+// optionally captured once into a CUDA graph that later replays the whole
+// batch with a single cudaGraphLaunch (no per-call host work).  A small
+// autotuner picks, per context, the key inner product's outputs-per-thread
+// group by timing the candidates on the device.
+#include <algorithm>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "ops.cuh"
+
+struct ckks_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+struct GroupKey {
+  ckks_ctx *c;
+  int op, level, flag;
+  bool operator<(const GroupKey &o) const {
+    return std::tie(c, op, level, flag) < std::tie(o.c, o.op, o.level, o.flag);
+  }
+};
+
+int validate(const ckks_op_desc *ops, int n) {
+  if (!ops || n < 0) return CKKS_E_PARAM;
+  for (int i = 0; i < n; ++i) {
+    const ckks_op_desc &d = ops[i];
+    if (!d.ctx || !d.a || !d.out) return CKKS_E_PARAM;
+    if (d.op == CKKS_OP_MUL_RELIN && !d.b) return CKKS_E_PARAM;
+    if (d.op != CKKS_OP_MUL_RELIN && d.op != CKKS_OP_ROTATE && d.op != CKKS_OP_RESCALE) return CKKS_E_PARAM;
+    if (d.out->data == d.a->data || (d.b && d.out->data == d.b->data)) return CKKS_E_PARAM;  // out of place
+  }
+  return CKKS_OK;
+}
+
+int run_grouped(const ckks_op_desc *ops, int n) {
+  std::map<GroupKey, std::vector<int>> groups;
+  for (int i = 0; i < n; ++i) {
+    const ckks_op_desc &d = ops[i];
+    groups[{d.ctx, d.op, (int)d.a->level, d.op == CKKS_OP_MUL_RELIN ? d.rescale : 0}].push_back(i);
+  }
+  for (auto &kv : groups) {
+    ckks_ctx *c = kv.first.c;
+    const std::vector<int> &ix = kv.second;
+    const int m = (int)ix.size();
+    std::vector<ckks_ct> a(m), b(m), out(m);
+    std::vector<int32_t> ks(m);
+    for (int j = 0; j < m; ++j) {
+      a[j] = *ops[ix[j]].a;
+      if (ops[ix[j]].b) b[j] = *ops[ix[j]].b;
+      out[j] = *ops[ix[j]].out;
+      ks[j] = ops[ix[j]].k;
+    }
+    int rc = CKKS_OK;
+    switch (kv.first.op) {
+      case CKKS_OP_MUL_RELIN:
+        rc = ckks_mul_relin_batch(c, a.data(), b.data(), out.data(), m, kv.first.flag);
+        break;
+      case CKKS_OP_ROTATE:
+        rc = ckks_rotate_batch(c, a.data(), ks.data(), out.data(), m);
+        break;
+      case CKKS_OP_RESCALE: {
+        for (int j = 0; j < m; ++j) {  // out of place: copy the active limbs, then rescale the copy
+          if (out[j].n_limbs < a[j].level + 1) return CKKS_E_LEVEL;
+          const size_t w = (size_t)(a[j].level + 1) * c->n;
+          CK_CUDA(cudaMemcpyAsync(out[j].data, a[j].data, w * 8, cudaMemcpyDeviceToDevice, c->stream));
+          CK_CUDA(cudaMemcpyAsync(out[j].data + (size_t)out[j].n_limbs * c->n,
+                                  a[j].data + (size_t)a[j].n_limbs * c->n, w * 8, cudaMemcpyDeviceToDevice,
+                                  c->stream));
+          out[j].level = a[j].level;
+          out[j].scale = a[j].scale;
+          out[j].is_ntt = 1;
+          out[j].log_n = c->log_n;
+        }
+        rc = ckks_rescale_batch(c, out.data(), m);
+        break;
+      }
+      default:
+        return CKKS_E_PARAM;
+    }
+    if (rc) return rc;
+    for (int j = 0; j < m; ++j) *ops[ix[j]].out = out[j];
+  }
+  return CKKS_OK;
+}
+
+std::vector<ckks_ctx *> contexts_of(const ckks_op_desc *ops, int n) {
+  std::vector<ckks_ctx *> cs;
+  for (int i = 0; i < n; ++i)
+    if (std::find(cs.begin(), cs.end(), ops[i].ctx) == cs.end()) cs.push_back(ops[i].ctx);
+  return cs;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ckks_exec(const ckks_op_desc *ops, int n) {
+  int rc = validate(ops, n);
+  if (rc) return rc;
+  return run_grouped(ops, n);
+}
+
+int ckks_exec_capture(const ckks_op_desc *ops, int n, void *stream, ckks_graph **out) {
+  if (!out) return CKKS_E_PARAM;
+  *out = nullptr;
+  int rc = validate(ops, n);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread) return CKKS_E_PARAM;
+  std::vector<ckks_ctx *> cs = contexts_of(ops, n);
+  std::vector<cudaStream_t> saved;
+  for (ckks_ctx *c : cs) {
+    saved.push_back(c->stream);
+    c->stream = st;
+  }
+  auto restore = [&]() {
+    for (size_t i = 0; i < cs.size(); ++i) {
+      cs[i]->stream = saved[i];
+      cs[i]->capturing = false;
+    }
+  };
+  // one eager pass sizes every scratch buffer, so the capture allocates nothing
+  rc = run_grouped(ops, n);
+  if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = CKKS_E_CUDA;
+  if (rc) { restore(); return rc; }
+  for (ckks_ctx *c : cs) c->capturing = true;
+  ckks_graph *g = new ckks_graph();
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    restore();
+    delete g;
+    return CKKS_E_CUDA;
+  }
+  rc = run_grouped(ops, n);
+  cudaError_t e = cudaStreamEndCapture(st, &g->graph);
+  restore();
+  if (rc || e != cudaSuccess || !g->graph) {
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    cudaGetLastError();
+    return rc ? rc : CKKS_E_CUDA;
+  }
+  if (cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) {
+    cudaGraphDestroy(g->graph);
+    delete g;
+    cudaGetLastError();
+    return CKKS_E_CUDA;
+  }
+  *out = g;
+  return CKKS_OK;
+}
+
+int ckks_graph_launch(ckks_graph *g, void *stream) {
+  if (!g || !g->exec) return CKKS_E_PARAM;
+  return cudaGraphLaunch(g->exec, (cudaStream_t)stream) == cudaSuccess ? CKKS_OK : CKKS_E_CUDA;
+}
+
+int ckks_graph_destroy(ckks_graph *g) {
+  if (!g) return CKKS_E_PARAM;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+  return CKKS_OK;
+}
+
+int ckks_tune(ckks_ctx *c, int level, int batch, int *chosen) {
+  if (!c || level < 0 || level >= c->n_q || batch < 1 || batch > MAX_CTS) return CKKS_E_PARAM;
+  if (!c->relin.data) return CKKS_E_NOKEY;
+  const u32 n = c->n;
+  // inputs: the relinearisation key's own limbs are valid residues at every level
+  std::vector<const u64 *> d(batch), keys(batch);
+  std::vector<u64 *> o0(batch), o1(batch);
+  u64 *outs = nullptr;
+  if (cudaMalloc(&outs, sizeof(u64) * 2 * (size_t)(level + 1) * n * batch) != cudaSuccess) {
+    cudaGetLastError();
+    return CKKS_E_OOM;
+  }
+  for (int i = 0; i < batch; ++i) {
+    d[i] = c->relin.data;
+    keys[i] = c->relin.data;
+    o0[i] = outs + (size_t)2 * (level + 1) * n * i;
+    o1[i] = o0[i] + (size_t)(level + 1) * n;
+  }
+  int rc = ensure_scratch(c, ks_ws_words(c, level, batch));
+  const int cands[] = {2, 4, 8, 16, 32};
+  float best = 1e30f;
+  int best_g = c->ip_group;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int cand : cands) {
+    if (rc) break;
+    c->ip_group = cand;
+    float tot = 0.f;
+    for (int rep = 0; rep < 3 && !rc; ++rep) {
+      cudaEventRecord(e0, c->stream);
+      rc = ks_batch(c, level, batch, d.data(), keys.data(), nullptr, nullptr, o0.data(), o1.data(), c->scratch);
+      cudaEventRecord(e1, c->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep) tot += ms;  // first run warms up
+    }
+    if (!rc && tot < best) {
+      best = tot;
+      best_g = cand;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(outs);
+  c->ip_group = best_g;
+  if (chosen) *chosen = best_g;
+  return rc;
+}
+
+}  // extern "C"

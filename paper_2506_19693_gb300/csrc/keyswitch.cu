@@ -93,9 +93,9 @@ struct IPArgs {
 // relinearisation batch) run back to back and share it through L2.  Within a
 // group the thread walks the outputs, reloading key words only when the key
 // changes.
-constexpr int IP_GROUP = 8;
+// The group size (outputs per thread) is a per-context tunable (ckks_tune).
 template <int NDIG>
-__global__ void __launch_bounds__(TPB, NDIG <= 3 ? 4 : 2) k_inner(const IPArgs a) {
+__global__ void __launch_bounds__(TPB, NDIG <= 3 ? 4 : 2) k_inner(const IPArgs a, int group) {
   const u32 k = blockIdx.y * TPB + threadIdx.x;
   const int t = blockIdx.z;
   if (k >= a.n) return;
@@ -103,8 +103,8 @@ __global__ void __launch_bounds__(TPB, NDIG <= 3 ? 4 : 2) k_inner(const IPArgs a
   const int kl = a.keylimb_of[t];
   u64 kb[NDIG], ka[NDIG];
   const u64 *cur = nullptr;
-  const int p_end = min(a.np, (int)(blockIdx.x + 1) * IP_GROUP);
-  for (int p = blockIdx.x * IP_GROUP; p < p_end; ++p) {
+  const int p_end = min(a.np, (int)(blockIdx.x + 1) * group);
+  for (int p = blockIdx.x * group; p < p_end; ++p) {
     if (a.key[p] != cur) {
       cur = a.key[p];
 #pragma unroll
@@ -296,10 +296,11 @@ int ks_tail(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *cons
       a.gal[i] = gal ? gal[i] : 1u;
       a.acc[i] = acc[i];
     }
-    dim3 g((nv + IP_GROUP - 1) / IP_GROUP, (n + TPB - 1) / TPB, ext);
+    const int group = c->ip_group > 0 ? c->ip_group : 8;
+    dim3 g((nv + group - 1) / group, (n + TPB - 1) / TPB, ext);
     switch (ndig) {
 #define ICASE(D) \
-  case D: PROF_LAUNCH(c, PK_INNER, (u64)nv * ext, (k_inner<D><<<g, TPB, 0, c->stream>>>(a))); break;
+  case D: PROF_LAUNCH(c, PK_INNER, (u64)nv * ext, (k_inner<D><<<g, TPB, 0, c->stream>>>(a, group))); break;
       ICASE(1) ICASE(2) ICASE(3) ICASE(4) ICASE(5) ICASE(6) ICASE(7) ICASE(8)
 #undef ICASE
       default: return CKKS_E_PARAM;
