@@ -117,6 +117,21 @@ int ckks_ctx_launch_count(const ckks_ctx *ctx, uint64_t *count);
  * Synchronises the context stream; uses the context's scratch memory. */
 int ckks_alu_peaks(ckks_ctx *ctx, double *mac_per_s, double *bfly_per_s);
 
+/* ---- arithmetic form --------------------------------------------------- */
+
+#define CKKS_FORM_UINT64 0 /* basis conversion as 64x64->128 MACs on the CUDA cores (default) */
+#define CKKS_FORM_TENSOR 1 /* basis conversion as an exact byte-split fp16 GEMM on tcgen05   */
+
+/* Select how ModUp / ModDown basis conversion (reading C8/C9) runs.  Both forms
+ * give identical limbs.  The tensor form splits each residue into bytes and the
+ * constants into byte planes, multiplies on tcgen05 tensor cores with exact fp32
+ * accumulation in tensor memory, and recombines modularly. */
+int ckks_ctx_set_form(ckks_ctx *ctx, int form);
+/* CKKS_E_TIMEOUT if a bounded device-side wait of a tensor-core kernel expired
+ * since the last call (the affected outputs are invalid), else CKKS_OK.
+ * Synchronises the context stream and clears the flag. */
+int ckks_ctx_device_error(ckks_ctx *ctx);
+
 /* ---- keys (Sec. 3: "one key corresponding to each desired rotation index") */
 
 /* Draw the ternary secret from `seed` and build the relinearisation key

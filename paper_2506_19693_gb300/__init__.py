@@ -66,6 +66,8 @@ SIGNATURES = {
     "ckks_profile_kind_name": (ctypes.c_char_p, [_I]),
     "ckks_ctx_launch_count": (_I, [_V, ctypes.POINTER(_U64)]),
     "ckks_alu_peaks": (_I, [_V, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "ckks_ctx_set_form": (_I, [_V, _I]),
+    "ckks_ctx_device_error": (_I, [_V]),
     "ckks_keygen_from_seed": (_I, [_V, _U64, _V, _I, _I, _I]),
     "ckks_keygen_galois": (_I, [_V, _U64]),
     "ckks_galois_elt": (_U64, [_V, ctypes.c_int32]),
@@ -242,6 +244,13 @@ class Context:
         m, b = ctypes.c_double(), ctypes.c_double()
         _check(self.lib.ckks_alu_peaks(self._h, ctypes.byref(m), ctypes.byref(b)), "ckks_alu_peaks")
         return m.value, b.value
+
+    def set_form(self, tensor: bool) -> None:
+        """Basis conversion on the tensor cores (True) or the CUDA cores (False)."""
+        _check(self.lib.ckks_ctx_set_form(self._h, 1 if tensor else 0), "ckks_ctx_set_form")
+
+    def device_error(self) -> int:
+        return self.lib.ckks_ctx_device_error(self._h)
 
     def tune(self, level: int, batch: int) -> int:
         """Autotune the key inner product for batches of this shape; returns the choice."""

@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["params_host.cpp", "sampling_host.cpp", "ntt.cu", "ops.cu", "keyswitch.cu", "encode.cu",
-           "capi.cu", "microbench.cu", "rescale_noalloc.cu", "boot.cu", "exec.cu"]
+           "capi.cu", "microbench.cu", "rescale_noalloc.cu", "boot.cu", "exec.cu", "bconv_tc.cu"]
 LIB_NAME = "libckks.so"
 
 

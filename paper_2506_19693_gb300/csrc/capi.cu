@@ -420,6 +420,8 @@ int ckks_ctx_destroy(ckks_ctx *c) {
   cudaFree(c->d_s_ntt);
   cudaFree(c->scratch);
   cudaFree(c->fscratch);
+  for (auto &kv : c->tc_bmats) cudaFree(kv.second);
+  cudaFree(c->tc_err);
   boot_free(c);
   if (c->pinned) cudaFreeHost(c->pinned);
   delete c;
@@ -485,10 +487,29 @@ int ckks_ctx_profile_read(ckks_ctx *c, double *ms, uint64_t *launches, uint64_t 
 
 int ckks_profile_kinds(void) { return (int)PK_COUNT; }
 
+int ckks_ctx_set_form(ckks_ctx *c, int form) {
+  if (!c || (form != CKKS_FORM_UINT64 && form != CKKS_FORM_TENSOR)) return CKKS_E_PARAM;
+  c->use_tc = form == CKKS_FORM_TENSOR;
+  return CKKS_OK;
+}
+
+int ckks_ctx_device_error(ckks_ctx *c) {
+  if (!c) return CKKS_E_PARAM;
+  if (!c->tc_err) return CKKS_OK;
+  int h = 0;
+  CK_CUDA(cudaStreamSynchronize(c->stream));
+  CK_CUDA(cudaMemcpy(&h, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) {
+    CK_CUDA(cudaMemset(c->tc_err, 0, sizeof(int)));
+    return CKKS_E_TIMEOUT;
+  }
+  return CKKS_OK;
+}
+
 const char *ckks_profile_kind_name(int k) {
   static const char *names[PK_COUNT] = {"ntt_fwd_pass_a", "ntt_fwd_pass_b", "ntt_inv_pass_a", "ntt_inv_pass_b",
                                         "bconv", "ks_inner_product", "ks_moddown_combine", "tensor",
-                                        "automorph", "rescale", "elementwise", "encode_decode"};
+                                        "automorph", "rescale", "elementwise", "encode_decode", "bconv_tc"};
   return (k >= 0 && k < PK_COUNT) ? names[k] : "unknown";
 }
 

@@ -73,6 +73,9 @@ struct ckks_ctx {
   size_t table_bytes = 0;
   Profiler prof;
   int ip_group = 8;                  // key inner product: outputs per thread (ckks_tune)
+  bool use_tc = false;               // basis conversion on the tensor cores (ckks_ctx_set_form)
+  std::map<size_t, void *> tc_bmats; // byte-plane constants per conversion
+  int *tc_err = nullptr;             // device flag: a bounded wait expired
   bool capturing = false;            // inside a CUDA-graph capture: no allocation, no sync
 
   size_t limb_words() const { return (size_t)n; }
@@ -113,6 +116,11 @@ int launch_ntt(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, i
                const int *mods, bool inverse);
 
 // ---- element-wise and key-switch launchers (ops.cu / keyswitch.cu) ----
+// ---- tensor-core basis conversion (bconv_tc.cu) ----
+int launch_bconv_tc(ckks_ctx *c, size_t key, const u64 *inv_dev, const u64 *tab_host, int ns, int nt,
+                    const int *src_mod, const int *dst_mod, const int *dst_pos, const u64 *const *src,
+                    u64 *const *dst, int np);
+
 // ---- batched ciphertext operations (capi.cu); n <= 128, all at one level ----
 int rescale_chunk(ckks_ctx *c, ckks_ct *cts, int n);
 int mul_relin_chunk(ckks_ctx *c, const ckks_ct *a, const ckks_ct *b, ckks_ct *out, int n);

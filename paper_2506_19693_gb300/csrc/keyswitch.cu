@@ -237,7 +237,16 @@ int ks_modup(ckks_ctx *c, int level, int np, const u64 *const *d, u64 *ws, u64 *
       a.src[i] = dc[i] + (size_t)lo * n;
       a.dst[i] = eb[i] + (size_t)j * ext * n;
     }
-    rc = launch_bconv(c, a, ns, np);
+    if (c->use_tc) {
+      const size_t off = c->conv.modup_off[(size_t)level * c->n_digits + j];
+      int sm[MAXS], dm[MAX_MODS], dp[MAX_MODS];
+      for (int i = 0; i < ns; ++i) sm[i] = a.src_mod[i];
+      for (int t = 0; t < a.nt; ++t) dm[t] = a.dst_mod[t], dp[t] = a.dst_pos[t];
+      rc = launch_bconv_tc(c, off << 8 | (size_t)a.nt, tbl, c->h_conv.data() + off + 2 * ns, ns, a.nt, sm, dm, dp,
+                           a.src, a.dst, np);
+    } else {
+      rc = launch_bconv(c, a, ns, np);
+    }
     if (rc) return rc;
     if (lo > 0) {
       for (int i = 0; i < np; ++i) dsts[i] = eb[i] + (size_t)j * ext * n, srcs[i] = dsts[i];
@@ -332,7 +341,15 @@ int ks_tail(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *cons
       a.src[x] = pd[pp];
       a.dst[x] = z[i] + (size_t)cc * nl * n;
     }
-    rc = launch_bconv(c, a, K, cnt);
+    if (c->use_tc) {
+      int sm[MAXS], dm[MAX_MODS], dp[MAX_MODS];
+      for (int i = 0; i < K; ++i) sm[i] = a.src_mod[i];
+      for (int t = 0; t < nl; ++t) dm[t] = t, dp[t] = t;
+      rc = launch_bconv_tc(c, c->conv.moddown_phat_mod << 8 | (size_t)nl, a.inv,
+                           c->h_conv.data() + c->conv.moddown_phat_mod, K, nl, sm, dm, dp, a.src, a.dst, cnt);
+    } else {
+      rc = launch_bconv(c, a, K, cnt);
+    }
     if (rc) return rc;
   }
   for (int i = 0; i < nv; ++i)

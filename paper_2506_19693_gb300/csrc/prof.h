@@ -20,6 +20,7 @@ enum ProfKind {
   PK_RESCALE,
   PK_ELEMENTWISE,
   PK_ENCODE,
+  PK_BCONV_TC,
   PK_COUNT
 };
 
