@@ -42,12 +42,13 @@ def _env_int(name, default):
 
 
 def peaks():
+    """(HBM GB/s, dense bf16 TFLOP/s sustained, "measured" | "fallback")."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         with open(path) as f:
             p = json.load(f)
-        return float(p["hbm_gbs"]), "measured"
-    return 6800.0, "fallback"
+        return float(p["hbm_gbs"]), float(p.get("bf16_tflops_sustained", p["bf16_tflops"])), "measured"
+    return 6800.0, 1700.0, "fallback"
 
 
 def traffic_table():
@@ -146,7 +147,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * float(np.mean(times)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-            "data": "synthetic", "config": config_of(w),
+            "data": "synthetic", "config": config_of(w, w.batch, args.form),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": "per step: 1 HMult+relin+rescale of 1 ciphertext pair at N=2^16, L=24 "
                                        "(1/64 of the batch), CPU oracle (128-bit % arithmetic, OpenMP over limbs)"},
@@ -155,17 +156,23 @@ def run_reference(args):
     return 0
 
 
-def config_of(w):
+FORM_NAMES = {"uint64": "uint64 CUDA-core basis conversion",
+              "tensor": "byte-split basis conversion on tcgen05 tensor cores"}
+
+
+def config_of(w, batch, form):
     return {"workload": w.name, "log_n": w.log_n, "n_q": len(w.q_bits), "n_p": len(w.p_bits), "dnum": w.dnum,
-            "log2_scale": w.log2_scale, "batch_pairs": w.batch, "rotations_per_ct": len(w.rot_steps),
-            "form": "uint64 CUDA-core", "l2": "inputs 3.2 GB per step > 126 MB L2; no flush"}
+            "log2_scale": w.log2_scale, "batch_pairs": batch, "rotations_per_ct": len(w.rot_steps),
+            "form": FORM_NAMES[form], "l2": "inputs over 400 MB per step > 126 MB L2; no flush"}
 
 
 # ---------------------------------------------------------------- GPU arm
 # Algorithmic work per unit the library's profiler counts (a limb of N words,
-# except bconv, whose unit is one multiply-accumulate per coefficient):
-#   HBM words moved per unit (8 bytes each, N per limb), and
-#   integer work per unit: Shoup butterflies or 64x64->128 MACs per coefficient.
+# except the basis conversions, whose unit is one source-target limb pair):
+#   HBM words moved per unit (8 bytes each, N per limb),
+#   integer work per unit: Shoup butterflies or 64x64->128 MACs per coefficient,
+#   tensor work of bconv_tc: 8 x 8 byte products per coefficient and pair,
+#   2 flops each, at the fp16 dense rate (= the bf16 rate).
 def kernel_work(name, units, launches, w, ndig):
     n = 1 << w.log_n
     lh = w.log_n - 8
@@ -178,16 +185,21 @@ def kernel_work(name, units, launches, w, ndig):
         alu = ("bfly", units * (n // 2) * 8)
     elif name == "bconv":
         alu = ("mac", units * n)
+    elif name == "bconv_tc":
+        alu = ("tensor", units * n * 64 * 2)
     elif name == "ks_inner_product":
         alu = ("mac", units * 2 * ndig * n)
     hbm = hbm_words * 8 * n * units if hbm_words is not None else None
     return hbm, alu
 
 
-def roofline(prof, w, ndig, hbm_peak, hbm_kind, alu_peaks):
-    """Roofline of the kernel class with the most device time in the timed region."""
+def roofline(prof, w, ndig, hbm_peak, hbm_kind, alu_peaks, tensor_peak=None, name=None):
+    """Roofline of one kernel class (default: the one with the most device
+    time in the timed region)."""
     total = sum(v[0] for v in prof.values())
-    name, (ms, nlaunch, units) = max(prof.items(), key=lambda kv: kv[1][0])
+    if name is None:
+        name = max(prof.items(), key=lambda kv: kv[1][0])[0]
+    ms, nlaunch, units = prof.get(name, (0.0, 0, 0))
     if not nlaunch:
         return None
     sec = ms / 1e3
@@ -197,7 +209,12 @@ def roofline(prof, w, ndig, hbm_peak, hbm_kind, alu_peaks):
         a = hbm / nlaunch / (sec / nlaunch) / 1e9
         cands.append({"bound": "hbm", "achieved": a, "peak": hbm_peak, "unit": "GB/s", "frac": a / hbm_peak,
                       "peak_source": f"{hbm_kind} hbm_gbs", "algorithmic_per_launch": hbm / nlaunch})
-    if alu is not None and alu_peaks:
+    if alu is not None and alu[0] == "tensor" and tensor_peak:
+        a = alu[1] / sec / 1e12
+        cands.append({"bound": "tensor", "achieved": a, "peak": tensor_peak, "unit": "TFLOP/s",
+                      "frac": a / tensor_peak, "peak_source": f"{hbm_kind} bf16_tflops_sustained (fp16 = bf16 rate)",
+                      "algorithmic_per_launch": alu[1] / nlaunch})
+    elif alu is not None and alu_peaks:
         kind, ops = alu
         pk = alu_peaks["mac_per_s"] if kind == "mac" else alu_peaks["bfly_per_s"]
         a = ops / sec
@@ -272,58 +289,86 @@ def run_gpu(args):
         if marks:
             marks[3].record(stream)
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    # correctness spot checks of the timed configuration
-    got = ctx.decrypt_decode(OUT[0])
-    err_mul = float(np.max(np.abs(got - z[0] * z[B])))
-    kk = len(w.rot_steps) - 1
-    got = ctx.decrypt_decode(ROT[kk * B])
-    err_rot = float(np.max(np.abs(got - np.roll(z[0], -w.rot_steps[kk]))))
-    err_boot = float(max(np.max(np.abs(bctx.decrypt_decode(BOUT[i]) - zb[i])) for i in range(2)))
+    def spot_errors():
+        got = ctx.decrypt_decode(OUT[0])
+        e_mul = float(np.max(np.abs(got - z[0] * z[B])))
+        kk = len(w.rot_steps) - 1
+        got = ctx.decrypt_decode(ROT[kk * B])
+        e_rot = float(np.max(np.abs(got - np.roll(z[0], -w.rot_steps[kk]))))
+        e_boot = float(max(np.max(np.abs(bctx.decrypt_decode(BOUT[i]) - zb[i])) for i in range(2)))
+        return {"hmult_rescale": e_mul, "rotation": e_rot, "bootstrap": e_boot}
 
-    clocks = ClockSampler(local)
-    barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    ctx.profile(True)
-    bctx.profile(True)
-    launches0 = ctx.launch_count() + bctx.launch_count()
-    marks = [[ev(), ev(), ev(), ev()] for _ in range(args.steps)]
-    torch.cuda.nvtx.range_push("timed")
-    for s in range(args.steps):
-        step(marks[s])
-    torch.cuda.synchronize()
-    torch.cuda.nvtx.range_pop()
-    launches = ctx.launch_count() + bctx.launch_count() - launches0
-    prof = ctx.profile_read()
-    for k, v in bctx.profile_read().items():
-        a = prof.get(k, (0.0, 0, 0))
-        prof[k] = (a[0] + v[0], a[1] + v[1], a[2] + v[2])
-    ctx.profile(False)
-    bctx.profile(False)
-    barrier()
-    clk = clocks.stop()
+    def timed(form, warmup, clocks=None):
+        """Warm-up, spot checks, then `args.steps` timed steps in one form."""
+        ctx.set_form(form == "tensor")
+        bctx.set_form(form == "tensor")
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        errs = spot_errors()
+        barrier()
+        torch.cuda.synchronize()
+        if clocks is not None:
+            clocks.start()
+        ctx.profile(True)
+        bctx.profile(True)
+        launches0 = ctx.launch_count() + bctx.launch_count()
+        marks = [[ev(), ev(), ev(), ev()] for _ in range(args.steps)]
+        for s in range(args.steps):
+            step(marks[s])
+        torch.cuda.synchronize()
+        launches = ctx.launch_count() + bctx.launch_count() - launches0
+        prof = ctx.profile_read()
+        for k, v in bctx.profile_read().items():
+            a = prof.get(k, (0.0, 0, 0))
+            prof[k] = (a[0] + v[0], a[1] + v[1], a[2] + v[2])
+        ctx.profile(False)
+        bctx.profile(False)
+        barrier()
+        clk = clocks.stop() if clocks is not None else None
+        if ctx.device_error() or bctx.device_error():
+            raise RuntimeError(f"device wait expired in the {form} form")
+        t = torch.tensor([sum(m[0].elapsed_time(m[1]) for m in marks), sum(m[1].elapsed_time(m[2]) for m in marks),
+                          sum(m[2].elapsed_time(m[3]) for m in marks),
+                          sum(m[0].elapsed_time(m[3]) for m in marks) / args.steps],
+                         dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        mul_ms, rot_ms, boot_ms, step_ms = t.tolist()
+        return {"mul_ms": mul_ms, "rot_ms": rot_ms, "boot_ms": boot_ms, "step_ms": step_ms, "prof": prof,
+                "launches": launches, "errors": errs, "clocks": clk,
+                "hmult_per_s": world * B * args.steps / (mul_ms / 1e3),
+                "rotations_per_s": world * B * len(w.rot_steps) * args.steps / (rot_ms / 1e3),
+                "bootstraps_per_s": world * nb * args.steps / (boot_ms / 1e3)}
 
-    mul_ms = sum(m[0].elapsed_time(m[1]) for m in marks)
-    rot_ms = sum(m[1].elapsed_time(m[2]) for m in marks)
-    boot_ms = sum(m[2].elapsed_time(m[3]) for m in marks)
-    step_ms = sum(m[0].elapsed_time(m[3]) for m in marks) / args.steps
-    t = torch.tensor([mul_ms, rot_ms, boot_ms, step_ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    mul_ms, rot_ms, boot_ms, step_ms = t.tolist()
-    value = world * B * args.steps / (mul_ms / 1e3)
-    rot_rate = world * B * len(w.rot_steps) * args.steps / (rot_ms / 1e3)
-    boot_rate = world * nb * args.steps / (boot_ms / 1e3)
+    main = timed(args.form, args.warmup, ClockSampler(local))
+    mul_ms, rot_ms, boot_ms, step_ms = main["mul_ms"], main["rot_ms"], main["boot_ms"], main["step_ms"]
+    prof, launches, clk = main["prof"], main["launches"], main["clocks"]
+    value, rot_rate, boot_rate = main["hmult_per_s"], main["rotations_per_s"], main["bootstraps_per_s"]
+    errors = main["errors"]
 
     # roofline of the dominant kernel class
-    hbm, peak_kind = peaks()
+    hbm, tflops, peak_kind = peaks()
     mac_s, bfly_s = ctx.alu_peaks()
     alu = {"mac_per_s": mac_s, "bfly_per_s": bfly_s}
     ndig = -(-len(w.q_bits) // (-(-len(w.q_bits) // w.dnum)))
-    roof = roofline(prof, w, ndig, hbm, peak_kind, alu)
+    roof = roofline(prof, w, ndig, hbm, peak_kind, alu, tflops)
+
+    # the same three phases in the other basis-conversion form, for comparison
+    forms = {}
+    if not args.no_form_compare:
+        other = "tensor" if args.form == "uint64" else "uint64"
+        cmp = timed(other, 2)
+        ctx.set_form(args.form == "tensor")
+        bctx.set_form(args.form == "tensor")
+        for f, r in ((args.form, main), (other, cmp)):
+            conv = "bconv_tc" if f == "tensor" else "bconv"
+            total = sum(v[0] for v in r["prof"].values())
+            forms[f] = {"hmult_per_s": r["hmult_per_s"], "rotations_per_s": r["rotations_per_s"],
+                        "bootstraps_per_s": r["bootstraps_per_s"], "slot_error": r["errors"],
+                        "basis_conversion_share": r["prof"].get(conv, (0.0,))[0] / total,
+                        "basis_conversion_roofline": roofline(r["prof"], w, ndig, hbm, peak_kind, alu, tflops,
+                                                              name=conv)}
 
     # ReBoot RE-Block training step (Alg. 1 + Alg. 2 + Bootstrap of W, V), the
     # synthetic MLP workload: 128 samples x 784 features in [0, 1], 784 -> 128 -> 10,
@@ -350,7 +395,7 @@ def run_gpu(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": config_of(w),
+                "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": config_of(w, B, args.form),
                 "rotations_per_s": rot_rate, "bootstraps_per_s": boot_rate,
                 "phase_ms_per_step": {"hmult_relin_rescale_x64": mul_ms / args.steps,
                                       "rotations_hoisted_64x15": rot_ms / args.steps,
@@ -359,7 +404,7 @@ def run_gpu(args):
                                      "n_q": len(wb.q_bits), "n_p": len(wb.p_bits), "dnum": wb.dnum,
                                      "batch": nb, "levels_consumed": 16, "cheb_degree": 60,
                                      "double_angles": 3, "input": "fresh encryptions at level 0"},
-                "slot_error": {"hmult_rescale": err_mul, "rotation": err_rot, "bootstrap": err_boot},
+                "slot_error": errors, "forms": forms,
                 "reboot_step": reboot, "uneven_batch": uneven,
                 "e2e": e2e, "roofline": roof, "alu_peaks": alu, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": int(launches),
@@ -500,6 +545,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-reboot", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
+    ap.add_argument("--no-form-compare", action="store_true")
+    ap.add_argument("--form", default="uint64", choices=["uint64", "tensor"],
+                    help="basis conversion on the CUDA cores (uint64) or the tensor cores (tensor)")
     ap.add_argument("--small", action="store_true",
                     help="8 pairs and 2 bootstraps: a few GB on the device, for ncu captures")
     args = ap.parse_args()

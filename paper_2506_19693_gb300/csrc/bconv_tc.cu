@@ -9,19 +9,25 @@
 //   y_t = sum_b 2^(8b) sum_(i,a) y_(i,a) c'_(i,a,t,b)   mod t,
 // where the inner sum is a GEMM  D[n][(t,b)] = sum_(i,a) A[n][(i,a)] B[(t,b)][(i,a)]
 // with 8-bit operands (exact in fp16) and K = 8 * sources <= 128 terms, so every
-// accumulator is an integer below 128 * 255 * 255 < 2^23, exact in fp32.  The
-// epilogue recombines the 8 byte planes of each target in 128-bit integers and
-// reduces mod t: bit-identical to the uint64 kernel.
+// accumulator is an integer below 128 * 255 * 255 < 2^23, exact in fp32.
 //
-// GB300 mapping: one CTA owns a 128 x N accumulator in tensor memory (TMEM,
-// N = 8 * targets rounded up to 16 <= 256 columns).  Per tile of 128
-// coefficients, all 128 threads compute y_i for their coefficient and write its
-// bytes into the shared-memory A tile (canonical K-major, no swizzle); one
-// thread issues K/16 tcgen05.mma (kind::f16, fp32 accumulate) and commits them
-// to an mbarrier; each warp then reads its 32 TMEM lanes with tcgen05.ld and
-// finishes its 32 coefficients.  B (the constants) is loaded into shared memory
-// once per CTA.  Every wait is bounded: on expiry the kernel records an error
-// flag, frees its TMEM and returns.
+// Epilogue per target: adding 2^23 to an accumulator puts its integer in the low
+// 23 mantissa bits (one FADD, no conversion unit); bytes 0..3 and 4..7 of the
+// target are summed into S_lo, S_hi < 2^47.01, and y_t = S_lo + S_hi 2^32 is
+// reduced by two Shoup products and two conditional subtractions.  The result is
+// the fully reduced residue, bit-identical to the uint64 kernel.
+//
+// GB300 mapping: one persistent CTA of 16 warps per SM owns all 512 TMEM
+// columns as two 128 x (8 targets, <= 256) fp32 accumulators and two A tiles in
+// shared memory, so the MMAs of tile j+1 run on the tensor pipe while the 16
+// warps recombine tile j:
+//   build A(j+1) | sync | one thread issues MMA(j+1) -> mbar | wait mbar(j) | epilogue(j)
+// A rows are written with 16-byte stores in the canonical K-major, no-swizzle
+// layout; bytes become fp16 through PRMT (0x64bb = 1024 + b) and one HSUB2.
+// Warp w reads TMEM lanes 32 (w mod 4) .. +31 (its coefficients) for the
+// targets of column group w / 4.  B (the constants) is loaded into shared
+// memory once per CTA.  Every wait is bounded: on expiry the kernel records an
+// error flag, waits (bounded) for its MMAs in flight, frees its TMEM and returns.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -31,9 +37,13 @@
 namespace {
 
 constexpr int TC_M = 128;
-constexpr int TC_THREADS = 128;
-constexpr int TC_TMEM_COLS = 256;
-constexpr u64 TC_WAIT_NS = 1000000000ULL;  // bounded waits give up after about 1 s
+constexpr int TC_THREADS = 512;
+constexpr int TC_WARPS = TC_THREADS / 32;
+constexpr int TC_COL_GROUPS = TC_WARPS / 4;   // warps sharing one TMEM lane quarter
+constexpr int TC_ACC_COLS = 256;              // columns per accumulator
+constexpr int TC_TMEM_COLS = 2 * TC_ACC_COLS; // the whole TMEM of the SM
+constexpr int TC_MAX_S = 16, TC_MAX_T = 32;
+constexpr u64 TC_WAIT_NS = 1000000000ULL;     // bounded waits give up after about 1 s
 
 __device__ __forceinline__ u32 smem_u32(const void *p) { return (u32)__cvta_generic_to_shared(p); }
 
@@ -70,36 +80,125 @@ __device__ __forceinline__ u64 make_desc(u32 saddr, u32 lbo, u32 sbo) {
          (1ULL << 46);  // descriptor version 1; base offset 0; no swizzle
 }
 
+// Two bytes of w (selected by sel) as exact fp16 integers: PRMT builds the
+// half-words 0x64bb = 1024 + b, HSUB2 removes the 1024.
+__device__ __forceinline__ u32 bytes_to_half2(u32 w, u32 sel) {
+  const u32 h = __byte_perm(w, 0x64646464u, sel);
+  __half2 v = *reinterpret_cast<const __half2 *>(&h);
+  v = __hsub2(v, __half2half2(__ushort_as_half((unsigned short)0x6400)));
+  return *reinterpret_cast<const u32 *>(&v);
+}
+
+// Integer value of an exact fp32 accumulator below 2^23.
+__device__ __forceinline__ u32 acc_int(u32 bits) {
+  return __float_as_uint(__uint_as_float(bits) + 8388608.0f) & 0x7FFFFFu;
+}
+
+__device__ __forceinline__ u64 mad_wide(u32 x, u32 y, u64 z) {
+  u64 d;
+  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(x), "r"(y), "l"(z));
+  return d;
+}
+
+// s * w mod 2^64 for a 32-bit s
+__device__ __forceinline__ u64 mul_lo_32x64(u32 s, u64 w) {
+  return mad_wide(s, (u32)w, (u64)(s * (u32)(w >> 32)) << 32);
+}
+
+// Per-target constants of the recombination.
+struct TcTarget {
+  u64 q, one_s;    // t, floor(2^64 / t)
+  u64 r64, r64_s;  // 2^64 mod t and its Shoup companion
+};
+
+// y_t = sum_b 2^(8b) v_b mod t from the 8 fp32 accumulators of one target.
+__device__ __forceinline__ u64 recombine(const u32 *v, const TcTarget &tg) {
+  const u32 c0 = acc_int(v[0]), c1 = acc_int(v[1]), c2 = acc_int(v[2]), c3 = acc_int(v[3]);
+  const u32 c4 = acc_int(v[4]), c5 = acc_int(v[5]), c6 = acc_int(v[6]), c7 = acc_int(v[7]);
+  // bytes 0..3 and 4..7: L, H < 2^47.01
+  const u64 L = mad_wide(c3, 1u << 24, mad_wide(c2, 1u << 16, (u64)(c0 + (c1 << 8))));
+  const u64 H = mad_wide(c7, 1u << 24, mad_wide(c6, 1u << 16, (u64)(c4 + (c5 << 8))));
+  // y = L + H 2^32 = y_hi 2^64 + y_lo with y_hi < 2^16
+  const u64 y_lo = L + (H << 32);
+  const u32 y_hi = (u32)(H >> 32) + (y_lo < L ? 1u : 0u);
+  // y_lo mod t in [0, 2t): quotient estimate floor(y_lo floor(2^64/t) / 2^64)
+  const u64 r_lo = y_lo - __umul64hi(tg.one_s, y_lo) * tg.q;
+  // y_hi (2^64 mod t) mod t in [0, 2t): Shoup with a 16-bit multiplicand
+  const u64 qt = mad_wide(y_hi, (u32)(tg.r64_s >> 32), (u64)__umulhi(y_hi, (u32)tg.r64_s)) >> 32;
+  const u64 r_hi = mul_lo_32x64(y_hi, tg.r64) - mul_lo_32x64((u32)qt, tg.q);
+  return csub(csub(r_lo + r_hi, tg.q << 1), tg.q);
+}
+
+constexpr int TC_SRC_GROUPS = TC_THREADS / TC_M;        // threads sharing one A row
+constexpr int TC_SRC_PER = TC_MAX_S / TC_SRC_GROUPS;    // sources per thread at most
+
 struct TcArgs {
-  const ModInfo *mods;
   u32 n;
   int ns, nt, kpad, npad;
-  const u64 *inv;                   // [ns] pairs: [Bhat_i^-1]_{b_i}, Shoup
-  const __half *bmat;               // [npad][kpad] row-major constants (bytes)
-  unsigned char src_mod[16];
-  unsigned char dst_mod[MAX_MODS];
-  unsigned char dst_pos[MAX_MODS];
+  const __half *bmat;                         // [npad][kpad] row-major constants (bytes)
+  u64 sq[TC_MAX_S], inv[TC_MAX_S], inv_s[TC_MAX_S];  // b_i, [Bhat_i^-1]_(b_i), Shoup companion
+  TcTarget tg[TC_MAX_T];
+  unsigned char dst_pos[TC_MAX_T];
   const u64 *src[MAX_CTS];
   u64 *dst[MAX_CTS];
   int np;
-  int *err;                         // set to 1 when a bounded wait expires
+  int *err;                                   // set to 1 when a bounded wait expires
 };
+
+// Sources of one 128-coefficient block for this thread: row tid mod 128,
+// sources i = tid / 128 + 4 k.
+__device__ __forceinline__ void load_sources(const TcArgs &a, int tile, int tiles_per_poly, int tid,
+                                             u64 (&x)[TC_SRC_PER]) {
+  const u64 *src = a.src[tile / tiles_per_poly];
+  const u32 kc = (u32)(tile % tiles_per_poly) * TC_M + (u32)(tid & (TC_M - 1));
+#pragma unroll
+  for (int k = 0; k < TC_SRC_PER; ++k) {
+    const int i = tid / TC_M + k * TC_SRC_GROUPS;
+    if (i < a.ns) x[k] = __ldg(src + (size_t)i * a.n + kc);
+  }
+}
+
+// y_i = [x_i Bhat_i^-1]_(b_i) as 8 fp16 bytes into row tid mod 128 of an A tile.
+__device__ __forceinline__ void store_sources(const TcArgs &a, unsigned char *sA, int tid,
+                                              const u64 (&x)[TC_SRC_PER]) {
+  const int row = tid & (TC_M - 1);
+#pragma unroll
+  for (int k = 0; k < TC_SRC_PER; ++k) {
+    const int i = tid / TC_M + k * TC_SRC_GROUPS;
+    if (i < a.ns) {
+      const u64 y = shoup(x[k], a.inv[i], a.inv_s[i], a.sq[i]);
+      const u32 lo = (u32)y, hi = (u32)(y >> 32);
+      uint4 v;
+      v.x = bytes_to_half2(lo, 0x4140);
+      v.y = bytes_to_half2(lo, 0x4342);
+      v.z = bytes_to_half2(hi, 0x4140);
+      v.w = bytes_to_half2(hi, 0x4342);
+      *reinterpret_cast<uint4 *>(sA + canon_offset(row, i * 8, a.kpad)) = v;
+    }
+  }
+}
 
 __global__ void __launch_bounds__(TC_THREADS, 1) k_bconv_tc(const TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  __half *sA = reinterpret_cast<__half *>(smem);                               // 128 x kpad
-  __half *sB = reinterpret_cast<__half *>(smem + TC_M * a.kpad * 2);           // npad x kpad
-  u64 *mbar = reinterpret_cast<u64 *>(smem + TC_M * a.kpad * 2 + a.npad * a.kpad * 2);
-  u32 *tmem_slot = reinterpret_cast<u32 *>(mbar + 1);
+  const int a_bytes = TC_M * a.kpad * 2;
+  unsigned char *sB = smem + 2 * a_bytes;  // A tiles 0 and 1 precede it
+  u64 *mbar = reinterpret_cast<u64 *>(sB + a.npad * a.kpad * 2);  // two barriers
+  u32 *tmem_slot = reinterpret_cast<u32 *>(mbar + 2);
 
-  // constants into the canonical layout
+  // constants into the canonical layout; zero padding columns of both A tiles
   for (int idx = tid; idx < a.npad * a.kpad; idx += TC_THREADS) {
     const int r = idx / a.kpad, k = idx % a.kpad;
-    *reinterpret_cast<__half *>(reinterpret_cast<unsigned char *>(sB) + canon_offset(r, k, a.kpad)) = a.bmat[idx];
+    *reinterpret_cast<__half *>(sB + canon_offset(r, k, a.kpad)) = a.bmat[idx];
+  }
+  for (int idx = tid; idx < 2 * TC_M * (a.kpad / 8 - a.ns); idx += TC_THREADS) {
+    const int b = idx / (TC_M * (a.kpad / 8 - a.ns)), rem = idx % (TC_M * (a.kpad / 8 - a.ns));
+    const int r = rem % TC_M, i = a.ns + rem / TC_M;
+    *reinterpret_cast<uint4 *>(smem + b * a_bytes + canon_offset(r, i * 8, a.kpad)) = make_uint4(0, 0, 0, 0);
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + 1)));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   if (warp == 0) {
@@ -107,6 +206,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_bconv_tc(const TcArgs a) {
                  "r"(TC_TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
+
+  const int tiles_per_poly = (int)(a.n / TC_M);
+  const int total = tiles_per_poly * a.np;
+  const int grid = (int)gridDim.x;
+  int tile = blockIdx.x;
+  u64 x[TC_SRC_PER];  // sources of the next block to be written into an A tile
+  if (tile < total) {
+    load_sources(a, tile, tiles_per_poly, tid, x);
+    store_sources(a, smem, tid, x);
+  }
+  if (tile + grid < total) load_sources(a, tile + grid, tiles_per_poly, tid, x);
+  asm volatile("fence.proxy.async.shared::cta;");
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
@@ -114,84 +225,86 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_bconv_tc(const TcArgs a) {
 
   // instruction descriptor: D fp32, A and B fp16, both K-major, M = 128, N = npad
   const u32 idesc = (1u << 4) | ((u32)(a.npad >> 3) << 17) | ((u32)(TC_M >> 4) << 24);
-  const u32 sA_addr = smem_u32(sA), sB_addr = smem_u32(sB);
+  const u32 sB_addr = smem_u32(sB);
   const u32 sbo = (u32)(a.kpad / 8) * 128;
-  u32 phase = 0;
-  bool failed = false;
+  u32 phase = 0;    // bit b: parity of the next completion of mbar[b]
+  u32 pending = 0;  // bit b: an MMA group committed to mbar[b] and not yet waited for
 
-  const int tiles_per_poly = a.n / TC_M;
-  const int total = tiles_per_poly * a.np;
-  for (int tile = blockIdx.x; tile < total && !failed; tile += gridDim.x) {
-    const int p = tile / tiles_per_poly;
-    const u32 k0 = (u32)(tile % tiles_per_poly) * TC_M;
-    const u32 kc = k0 + tid;
-    // A row tid: the bytes of y_i for coefficient kc
-    const u64 *src = a.src[p];
-    unsigned char *rowbase = reinterpret_cast<unsigned char *>(sA);
-    for (int i = 0; i < a.kpad / 8; ++i) {  // core-matrix column i holds the 8 bytes of y_i
-      u64 y = 0;
-      if (i < a.ns) {
-        const u64 q = a.mods[a.src_mod[i]].q;
-        y = shoup(src[(size_t)i * a.n + kc], a.inv[2 * i], a.inv[2 * i + 1], q);
-      }
-      __align__(16) __half h[8];
-#pragma unroll
-      for (int b = 0; b < 8; ++b) h[b] = __uint2half_rn((unsigned)((y >> (8 * b)) & 0xFF));
-      *reinterpret_cast<uint4 *>(rowbase + canon_offset(tid, i * 8, a.kpad)) = *reinterpret_cast<uint4 *>(h);
-    }
-    asm volatile("fence.proxy.async.shared::cta;");
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
+  auto issue = [&](int b) {
     if (tid == 0) {
+      const u32 sa = smem_u32(smem + b * a_bytes);
       for (int kk = 0; kk < a.kpad / 16; ++kk) {
-        const u64 ad = make_desc(sA_addr + kk * 256, 128, sbo);
+        const u64 ad = make_desc(sa + kk * 256, 128, sbo);
         const u64 bd = make_desc(sB_addr + kk * 256, 128, sbo);
         const u32 acc = kk > 0 ? 1u : 0u;
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem + (u32)(b * TC_ACC_COLS)),
             "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(mbar)));
+          smem_u32(mbar + b)));
     }
-    // bounded wait for the MMAs; the outcome is agreed by the whole CTA
-    const u32 done = wait_parity(smem_u32(mbar), phase);
+    pending |= 1u << b;
+  };
+
+  if (tile < total) issue(0);
+  const int lq = warp & 3, cg = warp >> 2;
+  const int per_group = (a.nt + TC_COL_GROUPS - 1) / TC_COL_GROUPS;
+  const int t_lo = cg * per_group, t_hi = min(a.nt, t_lo + per_group);
+  bool failed = false;
+  for (int j = 0; tile < total; ++j, tile += grid) {
+    const int cur = j & 1, nxt = cur ^ 1;
+    const int next = tile + grid;
+    // A tile of the next block from the prefetched sources (its buffer's MMAs
+    // completed before epilogue j - 1), then prefetch the block after it
+    if (next < total) store_sources(a, smem + nxt * a_bytes, tid, x);
+    if (next + grid < total) load_sources(a, next + grid, tiles_per_poly, tid, x);
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (next < total) issue(nxt);
+    // bounded wait for the MMAs of this block; the outcome is agreed by the whole CTA
+    const u32 done = wait_parity(smem_u32(mbar + cur), (phase >> cur) & 1u);
     if (__syncthreads_or(done == 0)) {
       failed = true;
       break;
     }
-    phase ^= 1;
+    phase ^= 1u << cur;
+    pending &= ~(1u << cur);
     asm volatile("tcgen05.fence::after_thread_sync;");
-    // epilogue: warp w owns TMEM lanes 32w..32w+31 = coefficients k0 + 32w + lane
-    u64 *dst = a.dst[p];
-    for (int t = 0; t < a.nt; ++t) {
-      u32 v[8];
-      const u32 taddr = tmem + ((u32)(warp * 32) << 16) + (u32)(t * 8);
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-      u64 lo = 0, hi = 0;
-#pragma unroll
-      for (int b = 0; b < 8; ++b) {
-        const u64 x = (u64)__float2uint_rn(__uint_as_float(v[b]));  // exact integer < 2^23
-        const u64 sl = b ? x << (8 * b) : x, sh = b > 0 && 8 * b > 40 ? x >> (64 - 8 * b) : 0;
-        lo += sl;
-        hi += sh + (lo < sl ? 1 : 0);
+    // epilogue: lanes 32 lq .. +31 = coefficients k0 + 32 lq + lane, targets t_lo .. t_hi - 1
+    u64 *dst = a.dst[tile / tiles_per_poly];
+    const u32 kc = (u32)(tile % tiles_per_poly) * TC_M + (u32)(lq * 32 + lane);
+    const u32 tbase = tmem + ((u32)(lq * 32) << 16) + (u32)(cur * TC_ACC_COLS);
+    for (int t = t_lo; t < t_hi; t += 2) {
+      u32 v[16];
+      const bool two = t + 1 < t_hi;
+      if (two) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(tbase + (u32)(t * 8)));
+      } else {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+            : "r"(tbase + (u32)(t * 8)));
       }
-      dst[(size_t)a.dst_pos[t] * a.n + k0 + warp * 32 + lane] = reduce128(hi, lo, a.mods[a.dst_mod[t]]);
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      dst[(size_t)a.dst_pos[t] * a.n + kc] = recombine(v, a.tg[t]);
+      if (two) dst[(size_t)a.dst_pos[t + 1] * a.n + kc] = recombine(v + 8, a.tg[t + 1]);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();  // A tile and accumulator are reused by the next tile
-    asm volatile("tcgen05.fence::after_thread_sync;");
   }
   if (failed) {
     // record the error, give the MMAs in flight one more bounded wait, then free TMEM
     if (tid == 0) atomicExch(a.err, 1);
-    wait_parity(smem_u32(mbar), phase);
+    for (int b = 0; b < 2; ++b)
+      if ((pending >> b) & 1u) wait_parity(smem_u32(mbar + b), (phase >> b) & 1u);
     asm volatile("tcgen05.fence::before_thread_sync;");
   }
   __syncthreads();
@@ -203,10 +316,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_bconv_tc(const TcArgs a) {
 // Host: the byte-plane constant matrix of one conversion, cached on the device
 // (built on first use, outside any graph capture), then the launch.
 // key identifies the conversion (table offset); tab_host rows are [nt][ns].
-int launch_bconv_tc(ckks_ctx *c, size_t key, const u64 *inv_dev, const u64 *tab_host, int ns, int nt,
+int launch_bconv_tc(ckks_ctx *c, size_t key, const u64 *inv_host, const u64 *tab_host, int ns, int nt,
                     const int *src_mod, const int *dst_mod, const int *dst_pos, const u64 *const *src,
                     u64 *const *dst, int np) {
-  if (ns < 1 || ns > 16 || nt < 1 || 8 * nt > TC_TMEM_COLS || np < 1 || np > MAX_CTS) return CKKS_E_PARAM;
+  if (ns < 1 || ns > TC_MAX_S || nt < 1 || nt > TC_MAX_T || np < 1 || np > MAX_CTS) return CKKS_E_PARAM;
   if (c->n % TC_M) return CKKS_E_PARAM;
   const int kpad = ((8 * ns + 15) / 16) * 16, npad = ((8 * nt + 15) / 16) * 16;
   if (!c->tc_err) {
@@ -236,17 +349,25 @@ int launch_bconv_tc(ckks_ctx *c, size_t key, const u64 *inv_dev, const u64 *tab_
     it = c->tc_bmats.emplace(key, d).first;
   }
   TcArgs a;
-  a.mods = c->d_mods;
   a.n = c->n;
   a.ns = ns;
   a.nt = nt;
   a.kpad = kpad;
   a.npad = npad;
-  a.inv = inv_dev;
   a.bmat = reinterpret_cast<const __half *>(it->second);
-  for (int i = 0; i < ns; ++i) a.src_mod[i] = (unsigned char)src_mod[i];
+  for (int i = 0; i < ns; ++i) {
+    a.sq[i] = c->mod[src_mod[i]];
+    a.inv[i] = inv_host[2 * i];
+    a.inv_s[i] = inv_host[2 * i + 1];
+  }
+  const unsigned __int128 two64 = (unsigned __int128)1 << 64;
   for (int t = 0; t < nt; ++t) {
-    a.dst_mod[t] = (unsigned char)dst_mod[t];
+    const u64 m = c->mod[dst_mod[t]];
+    TcTarget &g = a.tg[t];
+    g.q = m;
+    g.one_s = (u64)(two64 / m);
+    g.r64 = (u64)(two64 % m);
+    g.r64_s = (u64)(((unsigned __int128)g.r64 << 64) / m);
     a.dst_pos[t] = (unsigned char)dst_pos[t];
   }
   for (int i = 0; i < np; ++i) {
@@ -255,15 +376,15 @@ int launch_bconv_tc(ckks_ctx *c, size_t key, const u64 *inv_dev, const u64 *tab_
   }
   a.np = np;
   a.err = c->tc_err;
-  // at least 100 KB of shared memory per CTA: at most two CTAs share an SM, so
-  // their two 256-column TMEM allocations always fit the SM's 512 columns
-  const size_t need = (size_t)TC_M * kpad * 2 + (size_t)npad * kpad * 2 + 16;
-  const size_t smem = std::max<size_t>(need, 100 * 1024);
+  // more than half of the SM's shared memory per CTA: one CTA per SM, so its
+  // 512-column TMEM allocation never waits for another CTA's
+  const size_t need = 2 * (size_t)TC_M * kpad * 2 + (size_t)npad * kpad * 2 + 32;
+  const size_t smem = std::max<size_t>(need, 120 * 1024);
   CK_CUDA(cudaFuncSetAttribute(k_bconv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
   const int total = (int)(c->n / TC_M) * np;
-  const int grid = std::min(total, 2 * sms);
+  const int grid = std::min(total, sms);
   PROF_LAUNCH(c, PK_BCONV_TC, (u64)np * nt * ns, (k_bconv_tc<<<grid, TC_THREADS, smem, c->stream>>>(a)));
   return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_CUDA;
 }

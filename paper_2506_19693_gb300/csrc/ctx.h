@@ -117,7 +117,7 @@ int launch_ntt(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, i
 
 // ---- element-wise and key-switch launchers (ops.cu / keyswitch.cu) ----
 // ---- tensor-core basis conversion (bconv_tc.cu) ----
-int launch_bconv_tc(ckks_ctx *c, size_t key, const u64 *inv_dev, const u64 *tab_host, int ns, int nt,
+int launch_bconv_tc(ckks_ctx *c, size_t key, const u64 *inv_host, const u64 *tab_host, int ns, int nt,
                     const int *src_mod, const int *dst_mod, const int *dst_pos, const u64 *const *src,
                     u64 *const *dst, int np);
 

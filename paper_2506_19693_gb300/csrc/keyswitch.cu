@@ -242,7 +242,8 @@ int ks_modup(ckks_ctx *c, int level, int np, const u64 *const *d, u64 *ws, u64 *
       int sm[MAXS], dm[MAX_MODS], dp[MAX_MODS];
       for (int i = 0; i < ns; ++i) sm[i] = a.src_mod[i];
       for (int t = 0; t < a.nt; ++t) dm[t] = a.dst_mod[t], dp[t] = a.dst_pos[t];
-      rc = launch_bconv_tc(c, off << 8 | (size_t)a.nt, tbl, c->h_conv.data() + off + 2 * ns, ns, a.nt, sm, dm, dp,
+      rc = launch_bconv_tc(c, off << 8 | (size_t)a.nt, c->h_conv.data() + off, c->h_conv.data() + off + 2 * ns, ns,
+                           a.nt, sm, dm, dp,
                            a.src, a.dst, np);
     } else {
       rc = launch_bconv(c, a, ns, np);
@@ -345,7 +346,7 @@ int ks_tail(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *cons
       int sm[MAXS], dm[MAX_MODS], dp[MAX_MODS];
       for (int i = 0; i < K; ++i) sm[i] = a.src_mod[i];
       for (int t = 0; t < nl; ++t) dm[t] = t, dp[t] = t;
-      rc = launch_bconv_tc(c, c->conv.moddown_phat_mod << 8 | (size_t)nl, a.inv,
+      rc = launch_bconv_tc(c, c->conv.moddown_phat_mod << 8 | (size_t)nl, c->h_conv.data() + c->conv.moddown_phat_inv,
                            c->h_conv.data() + c->conv.moddown_phat_mod, K, nl, sm, dm, dp, a.src, a.dst, cnt);
     } else {
       rc = launch_bconv(c, a, K, cnt);

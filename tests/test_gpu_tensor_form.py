@@ -58,22 +58,25 @@ def test_tensor_form_bit_exact_vs_oracle(name):
 
 
 def test_tensor_form_equals_uint64_form_full_size():
+    """N = 2^16, 24 + 8 primes, 16 pairs per batched launch (the batched
+    launch shape of the throughput benchmark, at a quarter of its batch)."""
     import torch
     import paper_2506_19693_gb300 as ck
     torch.cuda.set_device(0)
     w = si.PLAIN
+    pairs = 16
     ctx = ck.Context.from_workload(w)
     try:
         ctx.keygen(1, rot_steps=[1, 1 << 14])
         level = len(w.q_bits) - 1
         scale = 2.0 ** w.log2_scale
-        z = si.messages(77, 4, w.slots)
-        cts = [ctx.encrypt(ctx.encode(z[i], level, scale), level, scale, 90 + i) for i in range(4)]
+        z = si.messages(77, 2 * pairs, w.slots)
+        cts = [ctx.encrypt(ctx.encode(z[i], level, scale), level, scale, 90 + i) for i in range(2 * pairs)]
         res = {}
         for form in (False, True):
             ctx.set_form(form)
-            out = [ctx.new_ct(level + 1) for _ in range(2)]
-            ctx.mul_relin_batch(cts[:2], cts[2:], out, rescale=True)
+            out = [ctx.new_ct(level + 1) for _ in range(pairs)]
+            ctx.mul_relin_batch(cts[:pairs], cts[pairs:], out, rescale=True)
             rots = [ctx.new_ct(level + 1) for _ in range(4)]
             ctx.rotate_hoisted(cts[:2], [1, 1 << 14], rots)
             res[form] = [ctx.export_ct(c) for c in out + rots]
