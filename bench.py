@@ -546,7 +546,7 @@ def main():
     ap.add_argument("--no-reboot", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--no-form-compare", action="store_true")
-    ap.add_argument("--form", default="uint64", choices=["uint64", "tensor"],
+    ap.add_argument("--form", default="tensor", choices=["uint64", "tensor"],
                     help="basis conversion on the CUDA cores (uint64) or the tensor cores (tensor)")
     ap.add_argument("--small", action="store_true",
                     help="8 pairs and 2 bootstraps: a few GB on the device, for ncu captures")

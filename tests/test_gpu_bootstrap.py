@@ -3,7 +3,8 @@
 * plan: the same rotation steps and constant count as the oracle's plan;
 * constants: GPU FP64 constants within FP64 rounding of the oracle's;
 * bit-exact: with the oracle's constants imported, every output limb equals
-  the oracle's bootstrap of the same ciphertext (N = 2^12, full 2^11 slots);
+  the oracle's bootstrap of the same ciphertext (N = 2^12, full 2^11 slots),
+  with basis conversion on the CUDA cores and on the tensor cores;
 * bound: with the GPU's own constants the decrypted slots are within 2^-12 of
   the input, at N = 2^12 and at N = 2^16 with 2^15 slots (the configuration
   bench.py times), output at level n_q - 17."""
@@ -51,9 +52,11 @@ def test_gpu_constants_match_oracle_constants(small):
     assert np.max(np.abs(cheb - plan.cheb)) < 1e-13
 
 
-def test_bootstrap_bit_exact_with_oracle_constants(small):
+@pytest.mark.parametrize("tensor_form", [False, True], ids=["uint64", "tensor"])
+def test_bootstrap_bit_exact_with_oracle_constants(small, tensor_form):
     import oracle.bootstrap as ob
     w, ctx, orc, plan, consts = small
+    ctx.set_form(tensor_form)
     z = si.messages(21, 1, w.slots)[0]
     delta = 2.0 ** w.log2_scale
     m = orc.encode(z, delta)
@@ -69,7 +72,9 @@ def test_bootstrap_bit_exact_with_oracle_constants(small):
         assert (out_g.level, out_g.scale) == (out_o.level, out_o.scale)
         got = ctx.export_ct(out_g)
         assert np.array_equal(got, out_o.data), int(np.sum(got != out_o.data))
+        assert ctx.device_error() == 0
     finally:
+        ctx.set_form(False)
         ctx.boot_import(list(mine_c), mine_cheb)
 
 

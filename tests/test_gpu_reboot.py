@@ -19,7 +19,8 @@ def _data(seed, b, k0, k1, o):
     return x, y, w, ws
 
 
-def test_reboot_step_bit_exact_small_ring():
+@pytest.mark.parametrize("tensor_form", [False, True], ids=["uint64", "tensor"])
+def test_reboot_step_bit_exact_small_ring(tensor_form):
     import torch
     import oracle
     import oracle.bootstrap as ob
@@ -31,6 +32,7 @@ def test_reboot_step_bit_exact_small_ring():
     g = rb.Geometry(32, 64, 60, 64, 10)
     go = orb.Geometry(32, 64, 60, 64, 10)
     ctx = ck.Context.from_workload(w_)
+    ctx.set_form(tensor_form)
     try:
         ctx.keygen(1, rot_steps=g.rotation_steps())
         o = oracle.Oracle(w_.log_n, w_.q_bits, w_.p_bits, w_.dnum, w_.h, w_.sigma)
@@ -66,6 +68,7 @@ def test_reboot_step_bit_exact_small_ring():
             for cg, co in zip(rg[0] + rg[1] + [rg[2], rg[3], rg[4]], ro[0] + ro[1] + [ro[2], ro[3], ro[4]]):
                 assert (cg.level, cg.scale) == (co.level, co.scale)
                 assert np.array_equal(ctx.export_ct(cg), co.data)
+        assert ctx.device_error() == 0
     finally:
         ctx.close()
 
