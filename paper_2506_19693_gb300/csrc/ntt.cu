@@ -61,11 +61,12 @@ __device__ __forceinline__ void fwd_step(u64 (&v)[1 << K], u32 mg, const ulonglo
   }
 }
 
-template <int K>
+// Gentleman-Sande stages s = K-1 .. STOP of a 2^K-point block.
+template <int K, int STOP = 0>
 __device__ __forceinline__ void inv_step(u64 (&v)[1 << K], u32 mg, const ulonglong2 *__restrict__ tw,
                                          u64 q, u64 twoq) {
 #pragma unroll
-  for (int s = K - 1; s >= 0; --s) {
+  for (int s = K - 1; s >= STOP; --s) {
     const int half = 1 << (K - 1 - s);
 #pragma unroll
     for (int e = 0; e < (1 << K); ++e) {
@@ -149,7 +150,12 @@ __global__ void __launch_bounds__(THREADS, 4) fwd_pass_b(const NttParams prm, in
     }
   }
   __syncthreads();
-  for (int x = threadIdx.x; x < RB * BROW; x += THREADS) dst[(size_t)row0 * BROW + x] = sm[padb(x)];
+  ulonglong2 *d2 = reinterpret_cast<ulonglong2 *>(dst + (size_t)row0 * BROW);
+#pragma unroll 4
+  for (int x = threadIdx.x; x < RB * BROW / 2; x += THREADS) {
+    const int o = padb(2 * x);
+    d2[x] = make_ulonglong2(sm[o], sm[o + 1]);
+  }
 }
 
 // ---------------------------------------------------------------- inverse
@@ -164,7 +170,19 @@ __global__ void __launch_bounds__(THREADS, 4) inv_pass_b(const NttParams prm) {
   const u64 *src = prm.src.p[poly] + (size_t)limb * prm.n;
   u64 *dst = prm.dst.p[poly] + (size_t)limb * prm.n;
   const int row0 = blockIdx.x * RB;
-  for (int x = threadIdx.x; x < RB * BROW; x += THREADS) sm[padb(x)] = src[(size_t)row0 * BROW + x];
+  {  // the 16 rows (32 KB contiguous) in 16-byte loads, all issued before the first store
+    constexpr int PER = RB * BROW / 2 / THREADS;
+    const ulonglong2 *s2 = reinterpret_cast<const ulonglong2 *>(src + (size_t)row0 * BROW);
+    ulonglong2 t[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) t[k] = s2[threadIdx.x + k * THREADS];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int o = padb(2 * (threadIdx.x + k * THREADS));  // an even word and its odd neighbour
+      sm[o] = t[k].x;
+      sm[o + 1] = t[k].y;
+    }
+  }
   __syncthreads();
   for (int x = threadIdx.x; x < (RB << U1); x += THREADS) {
     const int g = x % (1 << U1), rr = x / (1 << U1), b = row0 + rr;
@@ -213,10 +231,17 @@ __global__ void __launch_bounds__(THREADS, 4) inv_pass_a(const NttParams prm) {
     u64 v[1 << S1];
 #pragma unroll
     for (int e = 0; e < (1 << S1); ++e) v[e] = sm[(r0 + (e << S2)) * CA + c];
-    inv_step<S1>(v, 1u, tw, q, twoq);
+    inv_step<S1, 1>(v, 1u, tw, q, twoq);
+    // last stage (twiddle psi^-brv(1)) with N^-1 folded in: the sum is scaled
+    // by N^-1, the difference by tw[0] = psi^-brv(1) N^-1; both fully reduced
+    constexpr int HALF = 1 << (S1 - 1);
+    const ulonglong2 w0 = __ldg(&tw[0]);
 #pragma unroll
-    for (int e = 0; e < (1 << S1); ++e)
-      dst[(size_t)(r0 + (e << S2)) * BROW + c0 + c] = shoup(v[e], ninv, ninv_s, q);
+    for (int e = 0; e < HALF; ++e) {
+      const u64 x = v[e], y = v[e + HALF];
+      dst[(size_t)(r0 + (e << S2)) * BROW + c0 + c] = shoup(x + y, ninv, ninv_s, q);
+      dst[(size_t)(r0 + ((e + HALF) << S2)) * BROW + c0 + c] = shoup(x + twoq - y, w0.x, w0.y, q);
+    }
   }
 }
 
@@ -248,6 +273,8 @@ int launch_ntt(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, i
   prm.n = c->n;
   prm.n_limbs = nl;
   for (int l = 0; l < nl; ++l) prm.mod_of_limb[l] = (unsigned char)mods[l];
+  for (int i = 0; i < npoly; ++i)  // the row passes move 16-byte words
+    if (((uintptr_t)src[i] | (uintptr_t)dst[i]) & 15) return CKKS_E_PARAM;
   for (int p0 = 0; p0 < npoly; p0 += MAX_POLYS) {
     const int cnt = npoly - p0 < MAX_POLYS ? npoly - p0 : MAX_POLYS;
     for (int i = 0; i < cnt; ++i) {

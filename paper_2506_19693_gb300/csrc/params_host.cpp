@@ -121,6 +121,11 @@ int build_tables(ckks_ctx *c) {
       fwd[(size_t)i * n + k] = make_ulonglong2(pw[e], host_shoup(pw[e], q));
       inv[(size_t)i * n + k] = make_ulonglong2(ipw[e], host_shoup(ipw[e], q));
     }
+    // index 0 is never a stage twiddle (stage m uses indices m..2m-1): the
+    // inverse table keeps there psi^-brv(1) N^-1, the last stage's twiddle
+    // with the final N^-1 folded in
+    const u64 w0 = host_mulmod(inv[(size_t)i * n + 1].x, mi[i].ninv, q);
+    inv[(size_t)i * n] = make_ulonglong2(w0, host_shoup(w0, q));
   }
   // ---- basis conversion constants ----
   ConvTables &t = c->conv;
