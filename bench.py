@@ -233,6 +233,20 @@ def roofline(prof, w, ndig, hbm_peak, hbm_kind, alu_peaks, tensor_peak=None, nam
     return best
 
 
+def kernel_rooflines(prof, w, ndig, hbm_peak, hbm_kind, alu_peaks, tensor_peak):
+    """Binding-roof fraction of every kernel class with a work model, by share of device time."""
+    total = sum(v[0] for v in prof.values())
+    out = {}
+    for name, (ms, nl, units) in sorted(prof.items(), key=lambda kv: -kv[1][0]):
+        if not nl:
+            continue
+        r = roofline(prof, w, ndig, hbm_peak, hbm_kind, alu_peaks, tensor_peak, name=name)
+        out[name] = {"share": round(ms / total, 4), "avg_launch_us": round(ms / nl * 1e3, 2),
+                     "bound": r["bound"] if r else None, "frac": round(r["frac"], 4) if r else None,
+                     "achieved": round(r["achieved"], 2) if r else None, "unit": r["unit"] if r else None}
+    return out
+
+
 def run_gpu(args):
     import torch
     import paper_2506_19693_gb300 as ck
@@ -408,7 +422,8 @@ def run_gpu(args):
                 "reboot_step": reboot, "uneven_batch": uneven,
                 "e2e": e2e, "roofline": roof, "alu_peaks": alu, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": int(launches),
-                "kernel_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]}}
+                "kernel_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]},
+                "kernel_rooflines": kernel_rooflines(prof, w, ndig, hbm, peak_kind, alu, tflops)}
         print(json.dumps(line))
     bctx.close()
     ctx.close()

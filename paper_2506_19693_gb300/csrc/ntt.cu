@@ -42,7 +42,11 @@ struct NttParams {
 // strided accesses of the row stages conflict-free.
 __device__ __forceinline__ int padb(int off) { return off + (off >> 4); }
 
-template <int K>
+// Cooley-Tukey stages of a 2^K-point block.  Strict (Harvey): inputs < 4q,
+// x brought below 2q before each butterfly, outputs < 4q.  LOOSE, for
+// q < 2^58 only: no correction, every stage raises the bound by 2q, so inputs
+// < q stay below (1 + 2 log2 N) q <= 33 q < 2^64 through all 16 stages.
+template <int K, bool LOOSE>
 __device__ __forceinline__ void fwd_step(u64 (&v)[1 << K], u32 mg, const ulonglong2 *__restrict__ tw,
                                          u64 q, u64 twoq) {
 #pragma unroll
@@ -53,7 +57,7 @@ __device__ __forceinline__ void fwd_step(u64 (&v)[1 << K], u32 mg, const ulonglo
       if (e & half) continue;
       const ulonglong2 w = __ldg(&tw[(mg << s) + (e >> (K - s))]);
       u64 x = v[e];
-      if (x >= twoq) x -= twoq;
+      if (!LOOSE && x >= twoq) x -= twoq;
       const u64 t = shoup_lazy(v[e + half], w.x, w.y, q);
       v[e] = x + t;
       v[e + half] = x + twoq - t;
@@ -81,24 +85,24 @@ __device__ __forceinline__ void inv_step(u64 (&v)[1 << K], u32 mg, const ulonglo
   }
 }
 
+// Primes below this bound take the forward transform without lazy corrections.
+constexpr u64 LOOSE_BOUND = 1ULL << 58;
+
 // ---------------------------------------------------------------- forward
-template <int LH, int S1>
-__global__ void __launch_bounds__(THREADS, 4) fwd_pass_a(const NttParams prm) {
+// One CTA's work of each pass, specialised on LOOSE; the kernels pick the body
+// from the limb's modulus (uniform per CTA).
+template <int LH, int S1, bool LOOSE>
+__device__ __forceinline__ void fwd_a_body(const NttParams &prm, u64 *sm, int mi, const u64 *src, u64 *dst) {
   constexpr int H = 1 << LH, S2 = LH - S1;
-  __shared__ u64 sm[H * CA];
-  const int limb = blockIdx.y, poly = blockIdx.z;
-  const int mi = prm.mod_of_limb[limb];
   const u64 q = prm.mods[mi].q, twoq = 2 * q;
   const ulonglong2 *tw = prm.tw + (size_t)mi * prm.n;
-  const u64 *src = prm.src.p[poly] + (size_t)limb * prm.n;
-  u64 *dst = prm.dst.p[poly] + (size_t)limb * prm.n;
   const int c0 = blockIdx.x * CA;
   for (int x = threadIdx.x; x < (H >> S1) * CA; x += THREADS) {
     const int c = x % CA, r0 = x / CA;
     u64 v[1 << S1];
 #pragma unroll
     for (int e = 0; e < (1 << S1); ++e) v[e] = src[(size_t)(r0 + (e << S2)) * BROW + c0 + c];
-    fwd_step<S1>(v, 1u, tw, q, twoq);
+    fwd_step<S1, LOOSE>(v, 1u, tw, q, twoq);
 #pragma unroll
     for (int e = 0; e < (1 << S1); ++e) sm[(r0 + (e << S2)) * CA + c] = v[e];
   }
@@ -108,29 +112,37 @@ __global__ void __launch_bounds__(THREADS, 4) fwd_pass_a(const NttParams prm) {
     u64 v[1 << S2];
 #pragma unroll
     for (int e = 0; e < (1 << S2); ++e) v[e] = sm[((g << S2) + e) * CA + c];
-    fwd_step<S2>(v, (1u << S1) + g, tw, q, twoq);
+    fwd_step<S2, LOOSE>(v, (1u << S1) + g, tw, q, twoq);
 #pragma unroll
     for (int e = 0; e < (1 << S2); ++e) dst[(size_t)((g << S2) + e) * BROW + c0 + c] = v[e];
   }
 }
 
-template <int LH>
-__global__ void __launch_bounds__(THREADS, 4) fwd_pass_b(const NttParams prm, int from_src) {
-  constexpr int H = 1 << LH, U1 = 4, U2 = LB - U1;
-  __shared__ u64 sm[RB * BROW + (RB * BROW >> 4)];
+template <int LH, int S1>
+__global__ void __launch_bounds__(THREADS, 3) fwd_pass_a(const NttParams prm) {
+  __shared__ u64 sm[(1 << LH) * CA];
   const int limb = blockIdx.y, poly = blockIdx.z;
   const int mi = prm.mod_of_limb[limb];
+  const u64 *src = prm.src.p[poly] + (size_t)limb * prm.n;
+  u64 *dst = prm.dst.p[poly] + (size_t)limb * prm.n;
+  if (prm.mods[mi].q < LOOSE_BOUND)
+    fwd_a_body<LH, S1, true>(prm, sm, mi, src, dst);
+  else
+    fwd_a_body<LH, S1, false>(prm, sm, mi, src, dst);
+}
+
+template <int LH, bool LOOSE>
+__device__ __forceinline__ void fwd_b_body(const NttParams &prm, u64 *sm, int mi, const u64 *src, u64 *dst) {
+  constexpr int H = 1 << LH, U1 = 4, U2 = LB - U1;
   const u64 q = prm.mods[mi].q, twoq = 2 * q;
   const ulonglong2 *tw = prm.tw + (size_t)mi * prm.n;
-  const u64 *src = (from_src ? prm.src.p[poly] : prm.dst.p[poly]) + (size_t)limb * prm.n;
-  u64 *dst = prm.dst.p[poly] + (size_t)limb * prm.n;
   const int row0 = blockIdx.x * RB;
   for (int x = threadIdx.x; x < RB * (BROW >> U1); x += THREADS) {
     const int l0 = x % (BROW >> U1), rr = x / (BROW >> U1), b = row0 + rr;
     u64 v[1 << U1];
 #pragma unroll
     for (int e = 0; e < (1 << U1); ++e) v[e] = src[(size_t)b * BROW + l0 + (e << U2)];
-    fwd_step<U1>(v, (u32)(H + b), tw, q, twoq);
+    fwd_step<U1, LOOSE>(v, (u32)(H + b), tw, q, twoq);
 #pragma unroll
     for (int e = 0; e < (1 << U1); ++e) sm[padb(rr * BROW + l0 + (e << U2))] = v[e];
   }
@@ -140,11 +152,16 @@ __global__ void __launch_bounds__(THREADS, 4) fwd_pass_b(const NttParams prm, in
     u64 v[1 << U2];
 #pragma unroll
     for (int e = 0; e < (1 << U2); ++e) v[e] = sm[padb(rr * BROW + (g << U2) + e)];
-    fwd_step<U2>(v, ((u32)(H + b) << U1) + g, tw, q, twoq);
+    fwd_step<U2, LOOSE>(v, ((u32)(H + b) << U1) + g, tw, q, twoq);
+    const u64 one_s = LOOSE ? prm.mods[mi].one_s : 0;
 #pragma unroll
     for (int e = 0; e < (1 << U2); ++e) {
       u64 r = v[e];
-      if (r >= twoq) r -= twoq;
+      if (LOOSE) {  // r < 33 q: Barrett with floor(2^64 / q) to [0, 2q), then [0, q)
+        r -= __umul64hi(r, one_s) * q;
+      } else if (r >= twoq) {
+        r -= twoq;
+      }
       if (r >= q) r -= q;
       sm[padb(rr * BROW + (g << U2) + e)] = r;
     }
@@ -156,6 +173,19 @@ __global__ void __launch_bounds__(THREADS, 4) fwd_pass_b(const NttParams prm, in
     const int o = padb(2 * x);
     d2[x] = make_ulonglong2(sm[o], sm[o + 1]);
   }
+}
+
+template <int LH>
+__global__ void __launch_bounds__(THREADS, 3) fwd_pass_b(const NttParams prm, int from_src) {
+  __shared__ u64 sm[RB * BROW + (RB * BROW >> 4)];
+  const int limb = blockIdx.y, poly = blockIdx.z;
+  const int mi = prm.mod_of_limb[limb];
+  const u64 *src = (from_src ? prm.src.p[poly] : prm.dst.p[poly]) + (size_t)limb * prm.n;
+  u64 *dst = prm.dst.p[poly] + (size_t)limb * prm.n;
+  if (prm.mods[mi].q < LOOSE_BOUND)
+    fwd_b_body<LH, true>(prm, sm, mi, src, dst);
+  else
+    fwd_b_body<LH, false>(prm, sm, mi, src, dst);
 }
 
 // ---------------------------------------------------------------- inverse
