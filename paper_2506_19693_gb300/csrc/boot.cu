@@ -171,7 +171,7 @@ __global__ void k_mac_plain(const MacArgs a) {
   const u32 k = blockIdx.x * TPB + threadIdx.x;
   const int t = blockIdx.y, c = blockIdx.z;
   if (k >= a.n) return;
-  const ModInfo &m = a.mods[t];
+  const ModInfo m = a.mods[t];
   const size_t off = (size_t)t * a.n + k;
   u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0;
   for (int i = 0; i < a.na; ++i) {
@@ -201,7 +201,7 @@ __global__ void k_lincomb(const CombArgs a) {
   const u32 k = blockIdx.x * TPB + threadIdx.x;
   const int t = blockIdx.y, c = blockIdx.z;
   if (k >= a.n) return;
-  const ModInfo &m = a.mods[t];
+  const ModInfo m = a.mods[t];
   const size_t off = (size_t)t * a.n + k;
   u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0;
   for (int i = 0; i < a.nt; ++i) {
@@ -225,7 +225,7 @@ __global__ void k_add_const(const ConstArgs a) {
   const u32 k = blockIdx.x * TPB + threadIdx.x;
   const int t = blockIdx.y, c = blockIdx.z;
   if (k >= a.n) return;
-  const ModInfo &m = a.mods[t];
+  const ModInfo m = a.mods[t];
   const size_t off = (size_t)t * a.n + k;
   a.o0[c][off] = addmod(a.x0[c][off], sres(a.k, m), m.q);
   a.o1[c][off] = a.x1[c][off];
@@ -243,7 +243,7 @@ __global__ void k_mod_raise(const RaiseArgs a) {
   const int t = blockIdx.y, c = blockIdx.z;
   if (k >= a.n) return;
   const u64 q0 = a.mods[0].q;
-  const ModInfo &m = a.mods[t];
+  const ModInfo m = a.mods[t];
   for (int p = 0; p < 2; ++p) {
     const u64 v = a.coef[c][(size_t)p * a.n + k];
     u64 r;

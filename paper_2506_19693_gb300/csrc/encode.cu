@@ -74,7 +74,7 @@ __global__ void k_enc_finish(const double2 *f, u32 n, double scale, const ModInf
   }
   const i64 m = llround(v);
   for (int l = 0; l < nl; ++l) {
-    const ModInfo &md = mods[l];
+    const ModInfo md = mods[l];
     u64 r;
     if (m >= 0) {
       r = reduce128(0, (u64)m, md);
@@ -93,7 +93,7 @@ __global__ void k_dec_crt(const u64 *res, int level, u32 n, int log_n, const Mod
   if (k >= n) return;
   u64 v[CKKS_MAX_Q];
   for (int i = 0; i <= level; ++i) {
-    const ModInfo &m = mods[i];
+    const ModInfo m = mods[i];
     u64 t = res[(size_t)i * n + k];
     for (int j = 0; j < i; ++j) {
       const u64 vj = reduce128(0, v[j], m);

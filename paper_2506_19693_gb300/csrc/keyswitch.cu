@@ -99,26 +99,30 @@ __global__ void __launch_bounds__(TPB, NDIG <= 3 ? 4 : 2) k_inner(const IPArgs a
   const u32 k = blockIdx.y * TPB + threadIdx.x;
   const int t = blockIdx.z;
   if (k >= a.n) return;
-  const ModInfo &m = a.mods[a.mod_of[t]];
+  const ModInfo m = a.mods[a.mod_of[t]];
   const int kl = a.keylimb_of[t];
   u64 kb[NDIG], ka[NDIG];
   const u64 *cur = nullptr;
   const int p_end = min(a.np, (int)(blockIdx.x + 1) * group);
+  // digits and keys are read-only here: non-coherent loads let the unrolled
+  // iterations issue their loads ahead of the previous ciphertexts' stores
+  // (more bytes in flight per warp; the kernel is bound by memory parallelism)
+#pragma unroll 4
   for (int p = blockIdx.x * group; p < p_end; ++p) {
     if (a.key[p] != cur) {
       cur = a.key[p];
 #pragma unroll
       for (int j = 0; j < NDIG; ++j) {
-        kb[j] = cur[((size_t)(2 * j) * a.key_ext + kl) * a.n + k];
-        ka[j] = cur[((size_t)(2 * j + 1) * a.key_ext + kl) * a.n + k];
+        kb[j] = __ldg(cur + ((size_t)(2 * j) * a.key_ext + kl) * a.n + k);
+        ka[j] = __ldg(cur + ((size_t)(2 * j + 1) * a.key_ext + kl) * a.n + k);
       }
     }
     const u32 src = gal_src(k, a.gal[p], a.n, a.log_n);
     u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0;
 #pragma unroll
     for (int j = 0; j < NDIG; ++j) {
-      const u64 v = (t >= a.lo[j] && t < a.hi[j]) ? a.d[p][(size_t)t * a.n + src]
-                                                   : a.ext_buf[p][((size_t)j * a.ext + t) * a.n + src];
+      const u64 v = (t >= a.lo[j] && t < a.hi[j]) ? __ldg(a.d[p] + (size_t)t * a.n + src)
+                                                   : __ldg(a.ext_buf[p] + ((size_t)j * a.ext + t) * a.n + src);
       mac128(h0, l0, v, kb[j]);
       mac128(h1, l1, v, ka[j]);
     }

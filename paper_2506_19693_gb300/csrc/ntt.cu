@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(THREADS, 4) inv_pass_a(const NttParams prm) {
   __shared__ u64 sm[H * CA];
   const int limb = blockIdx.y, poly = blockIdx.z;
   const int mi = prm.mod_of_limb[limb];
-  const ModInfo &m = prm.mods[mi];
+  const ModInfo m = prm.mods[mi];
   const u64 q = m.q, twoq = 2 * q, ninv = m.ninv, ninv_s = m.ninv_s;
   const ulonglong2 *tw = prm.tw + (size_t)mi * prm.n;
   u64 *dst = prm.dst.p[poly] + (size_t)limb * prm.n;

@@ -48,7 +48,7 @@ __global__ void k_plain(EwArgs a, int mode) {
   const u32 k = blockIdx.x * TPB + threadIdx.x;
   const int l = blockIdx.y, c = blockIdx.z;
   if (k >= a.n) return;
-  const ModInfo &m = a.mods[l];
+  const ModInfo m = a.mods[l];
   const size_t off = (size_t)l * a.n + k;
   const u64 pt = a.y0[c][off], x0 = a.x0[c][off], x1 = a.x1[c][off];
   if (mode == 0) {
@@ -64,7 +64,7 @@ __global__ void k_mul_int(EwArgs a, i64 kconst) {
   const u32 k = blockIdx.x * TPB + threadIdx.x;
   const int l = blockIdx.y, c = blockIdx.z;
   if (k >= a.n) return;
-  const ModInfo &m = a.mods[l];
+  const ModInfo m = a.mods[l];
   const u64 kk = signed_res(kconst, m);
   const size_t off = (size_t)l * a.n + k;
   const u64 x0 = a.x0[c][off], x1 = a.x1[c][off];
@@ -80,7 +80,7 @@ __global__ void k_tensor(EwArgs a, D2Ptrs d2) {
   const u32 k = blockIdx.x * TPB + threadIdx.x;
   const int l = blockIdx.y, c = blockIdx.z;
   if (k >= a.n) return;
-  const ModInfo &m = a.mods[l];
+  const ModInfo m = a.mods[l];
   const size_t off = (size_t)l * a.n + k;
   const u64 a0 = a.x0[c][off], a1 = a.x1[c][off];
   const u64 b0 = a.y0[c][off], b1 = a.y1[c][off];
@@ -117,7 +117,7 @@ __global__ void k_rescale_lift(RescaleArgs r) {
   const int i = blockIdx.y, c = blockIdx.z;
   if (k >= r.n) return;
   const u64 ql = r.mods[r.level].q;
-  const ModInfo &m = r.mods[i];
+  const ModInfo m = r.mods[i];
   for (int p = 0; p < 2; ++p) {
     const u64 v = r.last[c][(size_t)p * r.n + k];
     u64 res;
@@ -148,7 +148,7 @@ __global__ void k_encrypt(EncArgs e) {
   const u32 k = blockIdx.x * TPB + threadIdx.x;
   const int t = blockIdx.y, c = blockIdx.z;
   if (k >= e.n) return;
-  const ModInfo &m = e.mods[t];
+  const ModInfo m = e.mods[t];
   const size_t off = (size_t)t * e.n + k;
   const u64 a = uniform_dev(e.key_a[c], (u64)t * e.n + k, m);
   const u64 as = mulmod(a, e.s_ntt[off], m);
@@ -161,7 +161,7 @@ __global__ void k_decrypt(EwArgs a, const u64 *s_ntt) {
   const u32 k = blockIdx.x * TPB + threadIdx.x;
   const int l = blockIdx.y, c = blockIdx.z;
   if (k >= a.n) return;
-  const ModInfo &m = a.mods[l];
+  const ModInfo m = a.mods[l];
   const size_t off = (size_t)l * a.n + k;
   a.o0[c][off] = addmod(a.x0[c][off], mulmod(a.x1[c][off], s_ntt[off], m), m.q);
 }
@@ -178,7 +178,7 @@ __global__ void k_keyrow(KeyArgs ka) {
   const u32 k = blockIdx.x * TPB + threadIdx.x;
   const int t = blockIdx.y;
   if (k >= ka.n) return;
-  const ModInfo &m = ka.mods[t];
+  const ModInfo m = ka.mods[t];
   const size_t off = (size_t)t * ka.n + k;
   const u64 a = uniform_dev(ka.key_a, (u64)t * ka.n + k, m);
   u64 b = submod(ka.err[off], mulmod(a, ka.s_ntt[off], m), m.q);

@@ -49,7 +49,7 @@ __global__ void k_noalloc_lift(const ChunkArgs a) {
   const int gi = blockIdx.y;
   if (k >= a.n) return;
   const u64 ql = a.mods[a.level].q;
-  const ModInfo &m = a.mods[a.i0 + gi];
+  const ModInfo m = a.mods[a.i0 + gi];
   for (int p = 0; p < 2; ++p) {
     const u64 v = a.last[(size_t)p * a.n + k];
     u64 r;
