@@ -114,7 +114,8 @@ class ClockSampler:
 # ---------------------------------------------------------------- oracle arm
 class OracleSample:
     """The CPU oracle on one ciphertext pair of the workload (keys and inputs
-    prepared once, untimed); time() runs one HMult+relin+rescale."""
+    prepared once, untimed); time() runs one HMult+relin+rescale with the
+    merged ModDown-rescale, the computation the GPU arm times."""
 
     def __init__(self, w, seed=0):
         import oracle
@@ -129,7 +130,7 @@ class OracleSample:
 
     def time(self) -> float:
         t0 = time.perf_counter()
-        self.orc.rescale(self.orc.mul_relin(self.cts[0], self.cts[1]))
+        self.orc.mul_relin_rescale(self.cts[0], self.cts[1])
         return time.perf_counter() - t0
 
 
@@ -163,7 +164,8 @@ FORM_NAMES = {"uint64": "uint64 CUDA-core basis conversion",
 def config_of(w, batch, form):
     return {"workload": w.name, "log_n": w.log_n, "n_q": len(w.q_bits), "n_p": len(w.p_bits), "dnum": w.dnum,
             "log2_scale": w.log2_scale, "batch_pairs": batch, "rotations_per_ct": len(w.rot_steps),
-            "form": FORM_NAMES[form], "l2": "inputs over 400 MB per step > 126 MB L2; no flush"}
+            "form": FORM_NAMES[form], "rescale": "ModDown and rescale merged into one basis conversion",
+            "l2": "inputs over 400 MB per step > 126 MB L2; no flush"}
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -293,7 +295,7 @@ def run_gpu(args):
     def step(marks=None):
         if marks:
             marks[0].record(stream)
-        ctx.mul_relin_batch(A, Bc, OUT, rescale=True)
+        ctx.mul_relin_batch(A, Bc, OUT, rescale=ck.RESCALE_MERGED)
         if marks:
             marks[1].record(stream)
         ctx.rotate_hoisted(A, list(w.rot_steps), ROT)
@@ -361,6 +363,17 @@ def run_gpu(args):
     value, rot_rate, boot_rate = main["hmult_per_s"], main["rotations_per_s"], main["bootstraps_per_s"]
     errors = main["errors"]
 
+    # the same products with ModDown then rescale as two steps (C9, C10)
+    e0, e1 = ev(), ev()
+    ctx.mul_relin_batch(A, Bc, OUT, rescale=ck.RESCALE_SEPARATE)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.mul_relin_batch(A, Bc, OUT, rescale=ck.RESCALE_SEPARATE)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    hmult_separate = world * B * args.steps / (e0.elapsed_time(e1) / 1e3)
+
     # roofline of the dominant kernel class
     hbm, tflops, peak_kind = peaks()
     mac_s, bfly_s = ctx.alu_peaks()
@@ -411,6 +424,7 @@ def run_gpu(args):
                 "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": config_of(w, B, args.form),
                 "rotations_per_s": rot_rate, "bootstraps_per_s": boot_rate,
+                "hmult_separate_rescale_per_s": hmult_separate,
                 "phase_ms_per_step": {"hmult_relin_rescale_x64": mul_ms / args.steps,
                                       "rotations_hoisted_64x15": rot_ms / args.steps,
                                       "bootstrap_x16": boot_ms / args.steps},
@@ -519,6 +533,7 @@ def run_reboot_step(bctx, wb, torch, stream, rank):
 
 
 def run_e2e(ctx, torch, A, Bc, OUT, level, args, dist):
+    import paper_2506_19693_gb300 as ck
     """HMult+relin+rescale of the batch with inputs imported from pinned host
     memory and results exported to pinned host memory, via ckks_ct_import /
     ckks_ct_export, all inside the timed region."""
@@ -534,7 +549,7 @@ def run_e2e(ctx, torch, A, Bc, OUT, level, args, dist):
     for _ in range(steps):
         for i, c in enumerate(A + Bc):
             ctx.import_host(c, host_in[i])
-        ctx.mul_relin_batch(A, Bc, OUT, rescale=True)
+        ctx.mul_relin_batch(A, Bc, OUT, rescale=ck.RESCALE_MERGED)
         for i, c in enumerate(OUT):
             ctx.export_host(c, host_out[i])
     torch.cuda.synchronize()

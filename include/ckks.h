@@ -260,7 +260,19 @@ int ckks_bootstrap_batch(ckks_ctx *ctx, const ckks_ct *in, ckks_ct *out, int n);
 
 /* ---- batched variants: n independent ciphertexts in one set of launches -- */
 
-/* out[i] = mul_relin(a[i], b[i]) then, if do_rescale, rescale(out[i]).
+#define CKKS_RESCALE_NONE 0     /* out at the inputs' level                                   */
+#define CKKS_RESCALE_SEPARATE 1 /* ModDown (C9) then rescale (C10): the limbs of ckks_rescale */
+#define CKKS_RESCALE_MERGED 2   /* ModDown and rescale merged (no paper counterpart; an
+                                 * implementation choice the paper leaves open, reading C21):
+                                 * the key-switch accumulator plus P (d0, d1) is divided by
+                                 * P q_l in one uncentred fast basis conversion from
+                                 * {q_l, p_0..p_{K-1}} to q_0..q_{l-1}, rounding to nearest:
+                                 * out = round(x / (P q_l)) - u, 0 <= u <= K per coefficient.
+                                 * Saves the ModDown NTT of q_l's digit limbs and the rescale's
+                                 * own transforms; limbs differ from SEPARATE by at most K + 2. */
+
+/* out[i] = mul_relin(a[i], b[i]), rescaled per do_rescale (CKKS_RESCALE_*;
+ * another value: CKKS_E_PARAM; a rescale at level 0: CKKS_E_LEVEL).
  * All a[i], b[i] at one level. */
 int ckks_mul_relin_batch(ckks_ctx *ctx, const ckks_ct *a, const ckks_ct *b, ckks_ct *out, int n,
                          int do_rescale);
@@ -301,7 +313,7 @@ typedef struct {
   const ckks_ct *b;
   ckks_ct *out;
   int32_t k;
-  int rescale;
+  int rescale;         /* CKKS_OP_MUL_RELIN: a CKKS_RESCALE_* mode */
 } ckks_op_desc;
 
 typedef struct ckks_graph ckks_graph;

@@ -100,6 +100,8 @@ def _load():
         "oc_keyswitch": (P, [V, _u64p, P, ctypes.c_uint64, _u64p, _u64p]),
         "oc_mul_relin": (P, [V, _u64p, _u64p, P, _u64p]),
         "oc_rescale": (P, [V, _u64p, P, _u64p]),
+        "oc_moddown_rescale": (P, [V, _u64p, P, _u64p]),
+        "oc_mul_relin_rescale": (P, [V, _u64p, _u64p, P, _u64p]),
         "oc_automorph": (P, [V, _u64p, P, ctypes.c_uint64, _u64p]),
         "oc_automorph_coeff": (None, [V, _u64p, P, _ip, ctypes.c_uint64, _u64p]),
         "oc_rotate_hoisted": (P, [V, _u64p, P, P, _u64p, _u64p]),
@@ -412,6 +414,24 @@ class Oracle:
         if self._lib.oc_rescale(self._c, _p64(a.data), a.level, _p64(out)) != 0:
             raise ValueError("cannot rescale level 0")
         return OCt(out, a.level - 1, a.scale / self.q[a.level])
+
+    def moddown_rescale(self, x: np.ndarray, level: int) -> np.ndarray:
+        """Reading C21 on one polynomial: x [level+1+K][N] over q_0..q_l, P
+        (NTT domain) divided by P q_l; returns [level][N] (NTT domain)."""
+        x = np.ascontiguousarray(x, dtype=np.uint64)
+        out = np.zeros((level, self.n), dtype=np.uint64)
+        if self._lib.oc_moddown_rescale(self._c, _p64(x), level, _p64(out)) != 0:
+            raise ValueError("cannot rescale level 0")
+        return out
+
+    def mul_relin_rescale(self, a: OCt, b: OCt) -> OCt:
+        """Relinearised product with ModDown and rescale merged (reading C21)."""
+        if a.level != b.level:
+            raise ValueError("level mismatch")
+        out = self._new(a.level - 1)
+        if self._lib.oc_mul_relin_rescale(self._c, _p64(a.data), _p64(b.data), a.level, _p64(out)) != 0:
+            raise KeyError("relinearisation key or level 0")
+        return OCt(out, a.level - 1, a.scale * b.scale / self.q[a.level])
 
     def automorph(self, a: OCt, g: int) -> OCt:
         out = self._new(a.level)

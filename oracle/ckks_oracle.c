@@ -666,14 +666,14 @@ static int modup(const oc_ctx *c, const u64 *d, int level, u64 *digits) {
   return nact;
 }
 
-/* inner product of the lifted digits with evk = (b_j, a_j), then ModDown (C9) */
-static void inner_moddown(const oc_ctx *c, const u64 *digits, int nact, int level, const u64 *key, u64 *out0,
-                          u64 *out1) {
+/* inner product of the lifted digits with evk = (b_j, a_j): acc = [2][ext][N]
+ * over q_0..q_level, P (NTT domain) */
+static void inner(const oc_ctx *c, const u64 *digits, int nact, int level, const u64 *key, u64 *acc) {
   u64 n = c->n;
   int nl = level + 1, np = c->n_p, ext = nl + np, key_ext = c->n_q + c->n_p;
   int ext_mods[OC_MAXMOD];
   ext_basis(c, level, ext_mods);
-  u64 *acc = (u64 *)calloc((u64)2 * ext * n, sizeof(u64));
+  memset(acc, 0, sizeof(u64) * (u64)2 * ext * n);
   for (int j = 0; j < nact; j++) {
     const u64 *dig = digits + (u64)j * ext * n;
     /* key limbs above the level are skipped */
@@ -689,6 +689,15 @@ static void inner_moddown(const oc_ctx *c, const u64 *digits, int nact, int leve
       }
     }
   }
+}
+
+/* inner product, then ModDown (C9) */
+static void inner_moddown(const oc_ctx *c, const u64 *digits, int nact, int level, const u64 *key, u64 *out0,
+                          u64 *out1) {
+  u64 n = c->n;
+  int nl = level + 1, np = c->n_p, ext = nl + np;
+  u64 *acc = (u64 *)malloc(sizeof(u64) * (u64)2 * ext * n);
+  inner(c, digits, nact, level, key, acc);
   /* C9: ModDown, out_i = (x_i - BConv_{P->Q}(x_P)_i) * P^-1 mod q_i */
   int psrc[OC_MAXMOD], qdst[OC_MAXMOD];
   for (int t = 0; t < np; t++) psrc[t] = c->n_q + t;
@@ -836,6 +845,89 @@ int oc_rescale(const oc_ctx *c, const u64 *in, int level, u64 *out) {
   }
   free(last);
   free(lift);
+  return 0;
+}
+
+/* C21: ModDown and rescale merged.  x (NTT domain, [ext][N] over q_0..q_l,
+ * p_0..p_{K-1}) is divided by S = P q_l, rounding to nearest, in one uncentred
+ * fast basis conversion from the basis {q_l, p_0, .., p_{K-1}} to q_0..q_{l-1}.
+ * With H = (S - 1)/2 (S is odd):
+ *   x'_i = x_i + [H]_{s_i} on the sources ([H]_{s_i} = (s_i - 1)/2),
+ *   z_t  = BConv(x')_t - [H]_{q_t},
+ *   out_t = (x_t - z_t) * S^-1 mod q_t,
+ * and over the integers x_t - z_t = X + H - [X + H]_S - u S, so
+ * out = floor((X + H) / S) - u = round(X / S) - u with 0 <= u <= K
+ * (X the representative in [0, Q_l P), u the conversion's overflow).
+ * out: [level][N], NTT domain. */
+int oc_moddown_rescale(const oc_ctx *c, const u64 *x, int level, u64 *out) {
+  if (level < 1) return -1;
+  u64 n = c->n;
+  int nl = level + 1, np = c->n_p, ns = np + 1;
+  int src[OC_MAXMOD], dst[OC_MAXMOD];
+  src[0] = level;
+  for (int k = 0; k < np; k++) src[1 + k] = c->n_q + k;
+  for (int t = 0; t < level; t++) dst[t] = t;
+  /* the sources: limb q_l and the K special limbs, to coefficients, plus H */
+  u64 *xs = (u64 *)malloc(sizeof(u64) * (u64)ns * n);
+  memcpy(xs, x + (u64)level * n, sizeof(u64) * n);
+  memcpy(xs + n, x + (u64)nl * n, sizeof(u64) * (u64)np * n);
+  oc_intt(c, xs, ns, src);
+  for (int i = 0; i < ns; i++) {
+    u64 si = c->mod[src[i]];
+    for (u64 k = 0; k < n; k++) xs[(u64)i * n + k] = addmod(xs[(u64)i * n + k], (si - 1) / 2, si);
+  }
+  u64 *z = (u64 *)malloc(sizeof(u64) * (u64)level * n);
+  oc_bconv(c, xs, ns, src, z, level, dst);
+  for (int t = 0; t < level; t++) {
+    u64 q = c->mod[t], sm = c->mod[level] % q;
+    for (int k = 0; k < np; k++) sm = mulmod(sm, c->mod[c->n_q + k] % q, q);
+    u64 h = mulmod(submod(sm, 1, q), (q + 1) / 2, q); /* (S - 1)/2 mod q_t */
+    for (u64 k = 0; k < n; k++) z[(u64)t * n + k] = submod(z[(u64)t * n + k], h, q);
+  }
+  oc_ntt(c, z, level, dst);
+  for (int t = 0; t < level; t++) {
+    u64 q = c->mod[t], pq = c->mod[level] % q;
+    for (int k = 0; k < np; k++) pq = mulmod(pq, c->mod[c->n_q + k] % q, q);
+    u64 pqinv = invmod(pq, q);
+    for (u64 k = 0; k < n; k++) {
+      u64 i = (u64)t * n + k;
+      out[i] = mulmod(submod(x[i], z[i], q), pqinv, q);
+    }
+  }
+  free(xs);
+  free(z);
+  return 0;
+}
+
+/* C6 + C21: relinearised product divided by P q_l in the merged step.  The
+ * tensor's (d0, d1) join the key-switch accumulator as P d (which vanishes
+ * modulo the special primes), so out = round((acc + P d) / (P q_l)) - u.
+ * out: [2][level][N], level - 1, NTT domain. */
+int oc_mul_relin_rescale(const oc_ctx *c, const u64 *a, const u64 *b, int level, u64 *out) {
+  okey *k = find_key(c, 0);
+  if (!k || level < 1) return -1;
+  u64 n = c->n;
+  int nl = level + 1, np = c->n_p, ext = nl + np;
+  u64 *d = (u64 *)malloc(sizeof(u64) * (u64)3 * nl * n);
+  u64 *d0 = d, *d1 = d + (u64)nl * n, *d2 = d + (u64)2 * nl * n;
+  oc_tensor(c, a, b, level, d0, d1, d2);
+  u64 *digits = (u64 *)malloc(sizeof(u64) * (u64)c->n_digits * ext * n);
+  int nact = modup(c, d2, level, digits);
+  u64 *acc = (u64 *)malloc(sizeof(u64) * (u64)2 * ext * n);
+  inner(c, digits, nact, level, k->data, acc);
+  for (int pol = 0; pol < 2; pol++) {
+    u64 *x = acc + (u64)pol * ext * n;
+    const u64 *dp = pol == 0 ? d0 : d1;
+    for (int t = 0; t < nl; t++) {
+      u64 q = c->mod[t], pm = 1;
+      for (int kk = 0; kk < np; kk++) pm = mulmod(pm, c->mod[c->n_q + kk] % q, q);
+      for (u64 i = 0; i < n; i++) x[(u64)t * n + i] = addmod(x[(u64)t * n + i], mulmod(pm, dp[(u64)t * n + i], q), q);
+    }
+    oc_moddown_rescale(c, x, level, out + (u64)pol * level * n);
+  }
+  free(d);
+  free(digits);
+  free(acc);
   return 0;
 }
 

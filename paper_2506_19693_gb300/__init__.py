@@ -41,6 +41,7 @@ class CkksCt(ctypes.Structure):
 
 
 OP_MUL_RELIN, OP_ROTATE, OP_RESCALE = 1, 2, 3
+RESCALE_NONE, RESCALE_SEPARATE, RESCALE_MERGED = 0, 1, 2  # ckks_mul_relin_batch / Op.rescale
 
 
 class CkksOpDesc(ctypes.Structure):
@@ -417,7 +418,9 @@ class Context:
             arr[i] = c.handle(self.log_n)
         return arr
 
-    def mul_relin_batch(self, a, b, out, rescale: bool = False) -> None:
+    def mul_relin_batch(self, a, b, out, rescale: int = RESCALE_NONE) -> None:
+        """out[i] = a[i] * b[i] relinearised; rescale: RESCALE_NONE (False),
+        RESCALE_SEPARATE (True: ModDown, then rescale) or RESCALE_MERGED."""
         ha, hb, ho = self._handles(a), self._handles(b), self._handles(out)
         _check(self.lib.ckks_mul_relin_batch(self._h, ha, hb, ho, len(a), int(rescale)), "ckks_mul_relin_batch")
         for i, c in enumerate(out):

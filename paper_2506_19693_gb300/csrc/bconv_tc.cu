@@ -109,6 +109,7 @@ __device__ __forceinline__ u64 mul_lo_32x64(u32 s, u64 w) {
 struct TcTarget {
   u64 q, one_s;    // t, floor(2^64 / t)
   u64 r64, r64_s;  // 2^64 mod t and its Shoup companion
+  u64 sub;         // subtracted from the result mod t when TcArgs::has_sub
 };
 
 // y_t = sum_b 2^(8b) v_b mod t from the 8 fp32 accumulators of one target.
@@ -137,6 +138,8 @@ struct TcArgs {
   int ns, nt, kpad, npad;
   const __half *bmat;                         // [npad][kpad] row-major constants (bytes)
   u64 sq[TC_MAX_S], inv[TC_MAX_S], inv_s[TC_MAX_S];  // b_i, [Bhat_i^-1]_(b_i), Shoup companion
+  u64 src_add[TC_MAX_S];                      // added to y_i mod b_i when has_add
+  int has_add, has_sub;
   TcTarget tg[TC_MAX_T];
   unsigned char dst_pos[TC_MAX_T];
   const u64 *src[MAX_CTS];
@@ -166,7 +169,8 @@ __device__ __forceinline__ void store_sources(const TcArgs &a, unsigned char *sA
   for (int k = 0; k < TC_SRC_PER; ++k) {
     const int i = tid / TC_M + k * TC_SRC_GROUPS;
     if (i < a.ns) {
-      const u64 y = shoup(x[k], a.inv[i], a.inv_s[i], a.sq[i]);
+      u64 y = shoup(x[k], a.inv[i], a.inv_s[i], a.sq[i]);
+      if (a.has_add) y = addmod(y, a.src_add[i], a.sq[i]);
       const u32 lo = (u32)y, hi = (u32)(y >> 32);
       uint4 v;
       v.x = bytes_to_half2(lo, 0x4140);
@@ -295,8 +299,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_bconv_tc(const TcArgs a) {
             : "r"(tbase + (u32)(t * 8)));
       }
       asm volatile("tcgen05.wait::ld.sync.aligned;");
-      dst[(size_t)a.dst_pos[t] * a.n + kc] = recombine(v, a.tg[t]);
-      if (two) dst[(size_t)a.dst_pos[t + 1] * a.n + kc] = recombine(v + 8, a.tg[t + 1]);
+      u64 r0 = recombine(v, a.tg[t]);
+      if (a.has_sub) r0 = submod(r0, a.tg[t].sub, a.tg[t].q);
+      dst[(size_t)a.dst_pos[t] * a.n + kc] = r0;
+      if (two) {
+        u64 r1 = recombine(v + 8, a.tg[t + 1]);
+        if (a.has_sub) r1 = submod(r1, a.tg[t + 1].sub, a.tg[t + 1].q);
+        dst[(size_t)a.dst_pos[t + 1] * a.n + kc] = r1;
+      }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
   }
@@ -318,7 +328,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_bconv_tc(const TcArgs a) {
 // key identifies the conversion (table offset); tab_host rows are [nt][ns].
 int launch_bconv_tc(ckks_ctx *c, size_t key, const u64 *inv_host, const u64 *tab_host, int ns, int nt,
                     const int *src_mod, const int *dst_mod, const int *dst_pos, const u64 *const *src,
-                    u64 *const *dst, int np) {
+                    u64 *const *dst, int np, const u64 *src_add_host, const u64 *dst_sub_host) {
   if (ns < 1 || ns > TC_MAX_S || nt < 1 || nt > TC_MAX_T || np < 1 || np > MAX_CTS) return CKKS_E_PARAM;
   if (c->n % TC_M) return CKKS_E_PARAM;
   const int kpad = ((8 * ns + 15) / 16) * 16, npad = ((8 * nt + 15) / 16) * 16;
@@ -355,10 +365,13 @@ int launch_bconv_tc(ckks_ctx *c, size_t key, const u64 *inv_host, const u64 *tab
   a.kpad = kpad;
   a.npad = npad;
   a.bmat = reinterpret_cast<const __half *>(it->second);
+  a.has_add = src_add_host != nullptr;
+  a.has_sub = dst_sub_host != nullptr;
   for (int i = 0; i < ns; ++i) {
     a.sq[i] = c->mod[src_mod[i]];
     a.inv[i] = inv_host[2 * i];
     a.inv_s[i] = inv_host[2 * i + 1];
+    a.src_add[i] = src_add_host ? src_add_host[i] : 0;
   }
   const unsigned __int128 two64 = (unsigned __int128)1 << 64;
   for (int t = 0; t < nt; ++t) {
@@ -368,6 +381,7 @@ int launch_bconv_tc(ckks_ctx *c, size_t key, const u64 *inv_host, const u64 *tab
     g.one_s = (u64)(two64 / m);
     g.r64 = (u64)(two64 % m);
     g.r64_s = (u64)(((unsigned __int128)g.r64 << 64) / m);
+    g.sub = dst_sub_host ? dst_sub_host[t] : 0;
     a.dst_pos[t] = (unsigned char)dst_pos[t];
   }
   for (int i = 0; i < np; ++i) {

@@ -189,8 +189,9 @@ int rescale_chunk(ckks_ctx *c, ckks_ct *cts, int n) {
   return CKKS_OK;
 }
 
-int mul_relin_chunk(ckks_ctx *c, const ckks_ct *a, const ckks_ct *b, ckks_ct *out, int n) {
+int mul_relin_chunk(ckks_ctx *c, const ckks_ct *a, const ckks_ct *b, ckks_ct *out, int n, bool merged) {
   const int level = a[0].level, nl = level + 1;
+  if (merged && level < 1) return CKKS_E_LEVEL;
   const u32 nn = c->n;
   if (!c->relin.data) return CKKS_E_NOKEY;
   const size_t d2w = (size_t)nl * nn * n;
@@ -219,16 +220,14 @@ int mul_relin_chunk(ckks_ctx *c, const ckks_ct *a, const ckks_ct *b, ckks_ct *ou
     o0[i] = e.o0[i];
     o1[i] = e.o1[i];
   }
-  const double sa = a[0].scale;
   std::vector<double> scales(n);
   for (int i = 0; i < n; ++i) scales[i] = a[i].scale * b[i].scale;
   rc = ks_batch(c, level, n, dd.data(), keys.data(), b0.data(), b1.data(), o0.data(), o1.data(),
-                c->scratch + d2w);
+                c->scratch + d2w, merged);
   if (rc) return rc;
-  (void)sa;
   for (int i = 0; i < n; ++i) {
-    out[i].level = level;
-    out[i].scale = scales[i];
+    out[i].level = merged ? level - 1 : level;
+    out[i].scale = merged ? scales[i] / (double)c->mod[level] : scales[i];
     out[i].is_ntt = 1;
     out[i].log_n = c->log_n;
   }
@@ -771,12 +770,13 @@ int ckks_mul_relin_batch(ckks_ctx *c, const ckks_ct *a, const ckks_ct *b, ckks_c
     if (!ct_ok(c, &a[i]) || !ct_ok(c, &b[i]) || !out[i].data) return CKKS_E_PARAM;
     if (a[i].level != level || b[i].level != level || out[i].n_limbs < level + 1) return CKKS_E_LEVEL;
   }
+  if (do_rescale < CKKS_RESCALE_NONE || do_rescale > CKKS_RESCALE_MERGED) return CKKS_E_PARAM;
   if (do_rescale && level == 0) return CKKS_E_LEVEL;
   for (int i0 = 0; i0 < n; i0 += MAX_CTS) {
     const int cnt = std::min(MAX_CTS, n - i0);
-    int rc = mul_relin_chunk(c, a + i0, b + i0, out + i0, cnt);
+    int rc = mul_relin_chunk(c, a + i0, b + i0, out + i0, cnt, do_rescale == CKKS_RESCALE_MERGED);
     if (rc) return rc;
-    if (do_rescale) {
+    if (do_rescale == CKKS_RESCALE_SEPARATE) {
       rc = rescale_chunk(c, out + i0, cnt);
       if (rc) return rc;
     }

@@ -27,6 +27,16 @@ struct ConvTables {
   size_t moddown_pinv = 0;         // [n_q] pairs
   // rescale from level l: qlinv[l * n_q + i] (Shoup pair) = q_l^-1 mod q_i
   size_t rescale_qlinv = 0;
+  // ModDown and rescale merged at level l >= 1 (reading C21): S = P q_l,
+  // sources (q_l, p_0..p_{K-1}), targets q_0..q_{l-1}.  At mdr_off[l]:
+  //   inv[K+1] pairs   [Shat_i^-1]_{s_i}                 (Shat_i = S / s_i)
+  //   tab[l][K+1]      Shat_i mod q_t
+  //   src_add[K+1]     [((s_i - 1)/2) Shat_i^-1]_{s_i}    (adds H = (S-1)/2 to each source)
+  //   dst_sub[l]       [H]_{q_t}
+  //   sinv[l] pairs    S^-1 mod q_t
+  //   qlinv[l] pairs   q_l^-1 mod q_t
+  //   pmod pair        [P]_{q_l}
+  std::vector<size_t> mdr_off;     // index l (0 unused)
   // decode: Garner constants inv(q_j) mod q_i  [n_q][n_q] and half-Q digits per level
   size_t garner_inv = 0;
   size_t halfq_digits = 0;         // [n_q][n_q]: digits of (Q_l - 1)/2 for level l
@@ -117,13 +127,16 @@ int launch_ntt(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, i
 
 // ---- element-wise and key-switch launchers (ops.cu / keyswitch.cu) ----
 // ---- tensor-core basis conversion (bconv_tc.cu) ----
+// src_add_host [ns] / dst_sub_host [nt] (or null): constants added to y_i
+// mod b_i before the products / subtracted from the result mod t.
 int launch_bconv_tc(ckks_ctx *c, size_t key, const u64 *inv_host, const u64 *tab_host, int ns, int nt,
                     const int *src_mod, const int *dst_mod, const int *dst_pos, const u64 *const *src,
-                    u64 *const *dst, int np);
+                    u64 *const *dst, int np, const u64 *src_add_host, const u64 *dst_sub_host);
 
 // ---- batched ciphertext operations (capi.cu); n <= 128, all at one level ----
 int rescale_chunk(ckks_ctx *c, ckks_ct *cts, int n);
-int mul_relin_chunk(ckks_ctx *c, const ckks_ct *a, const ckks_ct *b, ckks_ct *out, int n);
+// merged: ModDown and rescale in one step (reading C21), output at level - 1
+int mul_relin_chunk(ckks_ctx *c, const ckks_ct *a, const ckks_ct *b, ckks_ct *out, int n, bool merged = false);
 int automorph_chunk(ckks_ctx *c, const ckks_ct *in, const u64 *g, ckks_ct *out, int n);
 int rotate_hoisted_internal(ckks_ctx *c, const ckks_ct *in, int n, const u64 *g, int m, ckks_ct *out);
 int galois_key_for(ckks_ctx *c, u64 g);
@@ -136,6 +149,8 @@ int boot_rotation_steps(ckks_ctx *c, std::vector<int> &steps);
 
 // Key switching of np <= 128 NTT-domain polynomials at `level`, one key per
 // polynomial: o_c = base_c + u_c (base may be null) with u0 + u1 s ~ d s'.
+// merged: instead o_c = round((acc_c + P base_c) / (P q_l)) - u over
+// q_0..q_{l-1} (reading C21; base required, not read through sigma_g).
 // ws: device workspace of ks_ws_words(level, np) words.
 size_t ks_ws_words(const ckks_ctx *c, int level, int np);
 size_t ks_modup_words(const ckks_ctx *c, int level, int np);
@@ -143,7 +158,7 @@ size_t ks_tail_words(const ckks_ctx *c, int level, int nv);
 int ks_modup(ckks_ctx *c, int level, int np, const u64 *const *d, u64 *ws, u64 **ext_out);
 int ks_tail(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *const *ext_digits,
             const u64 *const *keys, const u32 *gal, const u64 *const *base0, const u32 *base0_gal,
-            const u64 *const *base1, u64 *const *o0, u64 *const *o1, u64 *ws);
+            const u64 *const *base1, u64 *const *o0, u64 *const *o1, u64 *ws, bool merged = false);
 int ks_batch(ckks_ctx *c, int level, int np, const u64 *const *d, const u64 *const *keys,
              const u64 *const *base0, const u64 *const *base1, u64 *const *o0, u64 *const *o1,
-             u64 *ws);
+             u64 *ws, bool merged = false);

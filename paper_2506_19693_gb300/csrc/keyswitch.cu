@@ -48,6 +48,8 @@ struct BConvArgs {
   unsigned char dst_pos[MAX_MODS];
   const u64 *src[MAX_CTS];         // first source limb (limbs contiguous)
   u64 *dst[MAX_CTS];               // output polynomial base (limb positions dst_pos)
+  const u64 *src_add = nullptr;    // [ns] or null: added to y_i mod b_i
+  const u64 *dst_sub = nullptr;    // [nt] or null: subtracted from y_t mod t
 };
 
 template <int NS>
@@ -61,6 +63,7 @@ __global__ void __launch_bounds__(TPB) k_bconv(const BConvArgs a) {
   for (int i = 0; i < NS; ++i) {
     const u64 q = a.mods[a.src_mod[i]].q;
     y[i] = shoup(src[(size_t)i * a.n + k], a.inv[2 * i], a.inv[2 * i + 1], q);
+    if (a.src_add) y[i] = addmod(y[i], __ldg(a.src_add + i), q);
   }
   u64 *dst = a.dst[p];
   for (int t = 0; t < a.nt; ++t) {
@@ -68,7 +71,10 @@ __global__ void __launch_bounds__(TPB) k_bconv(const BConvArgs a) {
     u64 hi = 0, lo = 0;
 #pragma unroll
     for (int i = 0; i < NS; ++i) mac128(hi, lo, y[i], __ldg(&row[i]));
-    dst[(size_t)a.dst_pos[t] * a.n + k] = reduce128(hi, lo, a.mods[a.dst_mod[t]]);
+    const ModInfo m = a.mods[a.dst_mod[t]];
+    u64 r = reduce128(hi, lo, m);
+    if (a.dst_sub) r = submod(r, __ldg(a.dst_sub + t), m.q);
+    dst[(size_t)a.dst_pos[t] * a.n + k] = r;
   }
 }
 
@@ -160,6 +166,69 @@ __global__ void __launch_bounds__(TPB) k_combine(const CombineArgs a, int nl) {
   a.o1[p][off] = r1;
 }
 
+// ---- ModDown and rescale merged (reading C21) ----
+// Word offsets inside the level-l table block (ConvTables::mdr_off).
+struct MdrLayout {
+  size_t inv, tab, src_add, dst_sub, sinv, qlinv, pmod;
+  MdrLayout(size_t off, int K, int l) {
+    inv = off;
+    tab = inv + 2 * (size_t)(K + 1);
+    src_add = tab + (size_t)l * (K + 1);
+    dst_sub = src_add + (K + 1);
+    sinv = dst_sub + l;
+    qlinv = sinv + 2 * (size_t)l;
+    pmod = qlinv + 2 * (size_t)l;
+  }
+};
+
+struct FoldArgs {
+  u32 n;
+  int ext, l;
+  u64 q, pm, pm_s;                 // q_l, [P]_{q_l} and its Shoup companion
+  u64 *acc[MAX_CTS];               // [2][ext][N]
+  const u64 *d0[MAX_CTS], *d1[MAX_CTS];
+};
+
+// acc_c[l] += [P]_{q_l} d_c[l]: the tensor term P d joins the top source limb
+__global__ void __launch_bounds__(TPB) k_fold_top(const FoldArgs a) {
+  const u32 k = blockIdx.x * TPB + threadIdx.x;
+  const int p = blockIdx.y, cc = blockIdx.z;
+  if (k >= a.n) return;
+  u64 *x = a.acc[p] + ((size_t)cc * a.ext + a.l) * a.n;
+  const u64 *d = (cc ? a.d1[p] : a.d0[p]) + (size_t)a.l * a.n;
+  x[k] = addmod(x[k], shoup(d[k], a.pm, a.pm_s, a.q), a.q);
+}
+
+struct CombineRArgs {
+  const ModInfo *mods;
+  u32 n;
+  int ext, l;
+  const u64 *sinv, *qlinv;         // [l] pairs: S^-1 and q_l^-1 mod q_t
+  const u64 *acc[MAX_CTS];         // [2][ext][N]
+  const u64 *z[MAX_CTS];           // [2][l][N]
+  const u64 *d0[MAX_CTS], *d1[MAX_CTS];
+  u64 *o0[MAX_CTS], *o1[MAX_CTS];
+};
+
+// out_c[t] = (acc_c[t] - z_c[t]) S^-1 + d_c[t] q_l^-1 mod q_t, t < l
+// (= (acc + P d - z) S^-1; d and out may alias: each element is read first)
+__global__ void __launch_bounds__(TPB) k_combine_rescale(const CombineRArgs a) {
+  const u32 k = blockIdx.x * TPB + threadIdx.x;
+  const int t = blockIdx.y, p = blockIdx.z;
+  if (k >= a.n) return;
+  const u64 q = a.mods[t].q;
+  const u64 sw = a.sinv[2 * t], sws = a.sinv[2 * t + 1], qw = a.qlinv[2 * t], qws = a.qlinv[2 * t + 1];
+  const size_t off = (size_t)t * a.n + k;
+#pragma unroll
+  for (int cc = 0; cc < 2; ++cc) {
+    const u64 x = a.acc[p][(size_t)cc * a.ext * a.n + off];
+    const u64 zz = a.z[p][(size_t)cc * a.l * a.n + off];
+    const u64 d = (cc ? a.d1[p] : a.d0[p])[off];
+    const u64 r = addmod(shoup(submod(x, zz, q), sw, sws, q), shoup(d, qw, qws, q), q);
+    (cc ? a.o1[p] : a.o0[p])[off] = r;
+  }
+}
+
 int launch_bconv(ckks_ctx *c, BConvArgs &a, int ns, int np) {
   a.mods = c->d_mods;
   a.n = c->n;
@@ -247,8 +316,7 @@ int ks_modup(ckks_ctx *c, int level, int np, const u64 *const *d, u64 *ws, u64 *
       for (int i = 0; i < ns; ++i) sm[i] = a.src_mod[i];
       for (int t = 0; t < a.nt; ++t) dm[t] = a.dst_mod[t], dp[t] = a.dst_pos[t];
       rc = launch_bconv_tc(c, off << 8 | (size_t)a.nt, c->h_conv.data() + off, c->h_conv.data() + off + 2 * ns, ns,
-                           a.nt, sm, dm, dp,
-                           a.src, a.dst, np);
+                           a.nt, sm, dm, dp, a.src, a.dst, np, nullptr, nullptr);
     } else {
       rc = launch_bconv(c, a, ns, np);
     }
@@ -268,13 +336,107 @@ int ks_modup(ckks_ctx *c, int level, int np, const u64 *const *d, u64 *ws, u64 *
 // Inner product + ModDown for nv <= MAX_CTS outputs.  Output v uses input
 // polynomial d[v] with its lifted digits ext[v], key keys[v] and automorphism
 // gal[v]; ws holds per output acc [2][l+1+K] then z [2][l+1].
+// ModDown and rescale merged (reading C21) on the accumulators of nv outputs:
+// o_c = round((acc_c + P base_c) / (P q_l)) - u over q_0..q_{l-1}.
+static int ks_merged_tail(ckks_ctx *c, int level, int nv, u64 *const *acc, u64 *const *z, const int *mods,
+                          const u64 *const *base0, const u64 *const *base1, u64 *const *o0, u64 *const *o1) {
+  const u32 n = c->n;
+  const int l = level, nl = level + 1, K = c->n_p, ext = nl + K, ns = K + 1;
+  if (l < 1 || ns > MAXS || !base0 || !base1) return CKKS_E_PARAM;
+  const MdrLayout L(c->conv.mdr_off[l], K, l);
+  const u64 *hc = c->h_conv.data();
+  int rc;
+  {  // the tensor term P d joins the top limb (P d vanishes modulo P)
+    FoldArgs f;
+    f.n = n;
+    f.ext = ext;
+    f.l = l;
+    f.q = c->mod[l];
+    f.pm = hc[L.pmod];
+    f.pm_s = hc[L.pmod + 1];
+    for (int i = 0; i < nv; ++i) {
+      f.acc[i] = acc[i];
+      f.d0[i] = base0[i];
+      f.d1[i] = base1[i];
+    }
+    dim3 g((n + TPB - 1) / TPB, nv, 2);
+    PROF_LAUNCH(c, PK_ELEMENTWISE, (u64)nv * 2, (k_fold_top<<<g, TPB, 0, c->stream>>>(f)));
+    if (cudaGetLastError() != cudaSuccess) return CKKS_E_CUDA;
+  }
+  // the sources q_l, p_0..p_{K-1} are adjacent in the accumulator: to coefficients
+  std::vector<const u64 *> ps(2 * nv);
+  std::vector<u64 *> pd(2 * nv);
+  for (int i = 0; i < nv; ++i)
+    for (int cc = 0; cc < 2; ++cc) {
+      pd[2 * i + cc] = acc[i] + ((size_t)cc * ext + l) * n;
+      ps[2 * i + cc] = pd[2 * i + cc];
+    }
+  rc = launch_ntt(c, ps.data(), pd.data(), 2 * nv, ns, mods + l, true);
+  if (rc) return rc;
+  for (int p0 = 0; p0 < 2 * nv; p0 += MAX_CTS) {
+    const int cnt = std::min(MAX_CTS, 2 * nv - p0);
+    BConvArgs a;
+    a.inv = c->d_conv + L.inv;
+    a.tab = c->d_conv + L.tab;
+    a.src_add = c->d_conv + L.src_add;
+    a.dst_sub = c->d_conv + L.dst_sub;
+    a.nt = l;
+    a.src_mod[0] = (unsigned char)l;
+    for (int k = 0; k < K; ++k) a.src_mod[1 + k] = (unsigned char)(c->n_q + k);
+    for (int t = 0; t < l; ++t) {
+      a.dst_mod[t] = (unsigned char)t;
+      a.dst_pos[t] = (unsigned char)t;
+    }
+    for (int x = 0; x < cnt; ++x) {
+      const int pp = p0 + x, i = pp / 2, cc = pp % 2;
+      a.src[x] = pd[pp];
+      a.dst[x] = z[i] + (size_t)cc * l * n;
+    }
+    if (c->use_tc) {
+      int sm[MAXS], dm[MAX_MODS], dp[MAX_MODS];
+      for (int i = 0; i < ns; ++i) sm[i] = a.src_mod[i];
+      for (int t = 0; t < l; ++t) dm[t] = t, dp[t] = t;
+      rc = launch_bconv_tc(c, L.inv << 8 | (size_t)l, hc + L.inv, hc + L.tab, ns, l, sm, dm, dp, a.src, a.dst, cnt,
+                           hc + L.src_add, hc + L.dst_sub);
+    } else {
+      rc = launch_bconv(c, a, ns, cnt);
+    }
+    if (rc) return rc;
+  }
+  std::vector<u64 *> pz(2 * nv);
+  std::vector<const u64 *> pzc(2 * nv);
+  for (int i = 0; i < nv; ++i)
+    for (int cc = 0; cc < 2; ++cc) pz[2 * i + cc] = z[i] + (size_t)cc * l * n, pzc[2 * i + cc] = pz[2 * i + cc];
+  rc = launch_ntt(c, pzc.data(), pz.data(), 2 * nv, l, mods, false);
+  if (rc) return rc;
+  CombineRArgs r;
+  r.mods = c->d_mods;
+  r.n = n;
+  r.ext = ext;
+  r.l = l;
+  r.sinv = c->d_conv + L.sinv;
+  r.qlinv = c->d_conv + L.qlinv;
+  for (int i = 0; i < nv; ++i) {
+    r.acc[i] = acc[i];
+    r.z[i] = z[i];
+    r.d0[i] = base0[i];
+    r.d1[i] = base1[i];
+    r.o0[i] = o0[i];
+    r.o1[i] = o1[i];
+  }
+  dim3 g((n + TPB - 1) / TPB, l, nv);
+  PROF_LAUNCH(c, PK_COMBINE, (u64)nv * l, (k_combine_rescale<<<g, TPB, 0, c->stream>>>(r)));
+  return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_CUDA;
+}
+
 int ks_tail(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *const *ext_digits,
             const u64 *const *keys, const u32 *gal, const u64 *const *base0, const u32 *base0_gal,
-            const u64 *const *base1, u64 *const *o0, u64 *const *o1, u64 *ws) {
+            const u64 *const *base1, u64 *const *o0, u64 *const *o1, u64 *ws, bool merged) {
   if (nv <= 0) return CKKS_OK;
   if (nv > MAX_CTS) return CKKS_E_PARAM;
   int rc = check_shape(c, level);
   if (rc) return rc;
+  if (merged && (base0_gal || level < 1)) return CKKS_E_PARAM;
   const u32 n = c->n;
   const int nl = level + 1, K = c->n_p, ext = nl + K;
   const int ndig = (nl + c->alpha - 1) / c->alpha;
@@ -321,6 +483,7 @@ int ks_tail(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *cons
     }
     if (cudaGetLastError() != cudaSuccess) return CKKS_E_CUDA;
   }
+  if (merged) return ks_merged_tail(c, level, nv, acc.data(), z.data(), mods, base0, base1, o0, o1);
   std::vector<const u64 *> ps(2 * nv);
   std::vector<u64 *> pd(2 * nv);
   for (int i = 0; i < nv; ++i)
@@ -351,7 +514,8 @@ int ks_tail(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *cons
       for (int i = 0; i < K; ++i) sm[i] = a.src_mod[i];
       for (int t = 0; t < nl; ++t) dm[t] = t, dp[t] = t;
       rc = launch_bconv_tc(c, c->conv.moddown_phat_mod << 8 | (size_t)nl, c->h_conv.data() + c->conv.moddown_phat_inv,
-                           c->h_conv.data() + c->conv.moddown_phat_mod, K, nl, sm, dm, dp, a.src, a.dst, cnt);
+                           c->h_conv.data() + c->conv.moddown_phat_mod, K, nl, sm, dm, dp, a.src, a.dst, cnt,
+                           nullptr, nullptr);
     } else {
       rc = launch_bconv(c, a, K, cnt);
     }
@@ -387,7 +551,7 @@ int ks_tail(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *cons
 
 int ks_batch(ckks_ctx *c, int level, int np, const u64 *const *d, const u64 *const *keys,
              const u64 *const *base0, const u64 *const *base1, u64 *const *o0, u64 *const *o1,
-             u64 *ws) {
+             u64 *ws, bool merged) {
   if (np <= 0) return CKKS_OK;
   if (np > MAX_CTS) return CKKS_E_PARAM;
   std::vector<u64 *> eb(np);
@@ -395,5 +559,5 @@ int ks_batch(ckks_ctx *c, int level, int np, const u64 *const *d, const u64 *con
   if (rc) return rc;
   std::vector<const u64 *> ebc(eb.begin(), eb.end());
   return ks_tail(c, level, np, d, ebc.data(), keys, nullptr, base0, nullptr, base1, o0, o1,
-                 ws + ks_modup_words(c, level, np));
+                 ws + ks_modup_words(c, level, np), merged);
 }

@@ -181,6 +181,36 @@ int build_tables(ckks_ctx *c) {
     for (int k = 0; k < K; ++k) prod = host_mulmod(prod, c->mod[c->n_q + k] % qi, qi);
     push_pair(v, host_invmod(prod, qi), qi);
   }
+  t.mdr_off.assign(c->n_q, 0);
+  for (int l = 1; l < c->n_q; ++l) {
+    t.mdr_off[l] = v.size();
+    std::vector<u64> smod(K + 1);  // the sources s_0 = q_l, s_{1+k} = p_k
+    smod[0] = c->mod[l];
+    for (int k = 0; k < K; ++k) smod[1 + k] = c->mod[c->n_q + k];
+    auto shat_mod = [&](int i, u64 m) {  // (S / s_i) mod m; i = -1 gives S mod m
+      u64 prod = 1;
+      for (int r = 0; r <= K; ++r)
+        if (r != i) prod = host_mulmod(prod, smod[r] % m, m);
+      return prod;
+    };
+    std::vector<u64> inv(K + 1);
+    for (int i = 0; i <= K; ++i) {
+      inv[i] = host_invmod(shat_mod(i, smod[i]), smod[i]);
+      push_pair(v, inv[i], smod[i]);
+    }
+    for (int tt = 0; tt < l; ++tt)
+      for (int i = 0; i <= K; ++i) v.push_back(shat_mod(i, c->mod[tt]));
+    for (int i = 0; i <= K; ++i) v.push_back(host_mulmod((smod[i] - 1) / 2, inv[i], smod[i]));
+    for (int tt = 0; tt < l; ++tt) {  // (S - 1)/2 mod q_t
+      const u64 qt = c->mod[tt], sm = shat_mod(-1, qt);
+      v.push_back(host_mulmod((sm + qt - 1) % qt, (qt + 1) / 2, qt));
+    }
+    for (int tt = 0; tt < l; ++tt) push_pair(v, host_invmod(shat_mod(-1, c->mod[tt]), c->mod[tt]), c->mod[tt]);
+    for (int tt = 0; tt < l; ++tt) push_pair(v, host_invmod(c->mod[l] % c->mod[tt], c->mod[tt]), c->mod[tt]);
+    u64 pm = 1;
+    for (int k = 0; k < K; ++k) pm = host_mulmod(pm, c->mod[c->n_q + k] % c->mod[l], c->mod[l]);
+    push_pair(v, pm, c->mod[l]);
+  }
   t.rescale_qlinv = v.size();
   for (int l = 0; l < c->n_q; ++l)
     for (int i = 0; i < c->n_q; ++i) {

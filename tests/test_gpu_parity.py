@@ -125,6 +125,28 @@ def test_mul_relin_and_rescale_bit_exact(pair):
     _same(ctx, pg2, po2)
 
 
+@pytest.mark.parametrize("tensor_form", [False, True], ids=["uint64", "tensor"])
+def test_merged_moddown_rescale_bit_exact(pair, tensor_form):
+    """Reading C21 (ModDown and rescale in one conversion) against the oracle,
+    at the top level and again one level down (partial top digit)."""
+    import paper_2506_19693_gb300 as ck
+    w, ctx, orc = pair
+    ctx.set_form(tensor_form)
+    try:
+        (za, a, ao), (zb, b, bo) = _enc_both(w, ctx, orc, 6, count=2)
+        out = [ctx.new_ct(a.level + 1) for _ in range(2)]
+        ctx.mul_relin_batch([a, b], [b, a], out, rescale=ck.RESCALE_MERGED)
+        po = orc.mul_relin_rescale(ao, bo)
+        _same(ctx, out[0], po)
+        _same(ctx, out[1], orc.mul_relin_rescale(bo, ao))
+        out2 = [ctx.new_ct(out[0].level + 1)]
+        ctx.mul_relin_batch([out[0]], [out[1]], out2, rescale=ck.RESCALE_MERGED)
+        _same(ctx, out2[0], orc.mul_relin_rescale(po, orc.mul_relin_rescale(bo, ao)))
+        assert ctx.device_error() == 0
+    finally:
+        ctx.set_form(False)
+
+
 def test_rotations_and_conjugation_bit_exact(pair):
     w, ctx, orc = pair
     (z, a, ao), = _enc_both(w, ctx, orc, 6)

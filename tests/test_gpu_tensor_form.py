@@ -57,6 +57,38 @@ def test_tensor_form_bit_exact_vs_oracle(name):
         ctx.close()
 
 
+def test_merged_rescale_full_size_bit_exact_vs_oracle():
+    """One pair at N = 2^16, L = 24 (the benchmark's ring) through the merged
+    ModDown-rescale, tensor-core form, against the oracle."""
+    import torch
+    import oracle
+    import paper_2506_19693_gb300 as ck
+    torch.cuda.set_device(0)
+    w = si.PLAIN
+    ctx = ck.Context.from_workload(w)
+    orc = oracle.Oracle(w.log_n, w.q_bits, w.p_bits, w.dnum, w.h, w.sigma)
+    try:
+        ctx.set_form(True)
+        ctx.keygen(3)
+        orc.keygen(3)
+        level = len(w.q_bits) - 1
+        scale = 2.0 ** w.log2_scale
+        z = si.messages(88, 2, w.slots)
+        pair = []
+        for i in range(2):
+            m = orc.encode(z[i], scale)
+            pair.append((ctx.encrypt(ctx.pt_from_int(m, level), level, scale, 70 + i),
+                         orc.encrypt(orc.pt_from_int(m, level), level, scale, 70 + i)))
+        out = [ctx.new_ct(level + 1)]
+        ctx.mul_relin_batch([pair[0][0]], [pair[1][0]], out, rescale=ck.RESCALE_MERGED)
+        want = orc.mul_relin_rescale(pair[0][1], pair[1][1])
+        assert (out[0].level, out[0].scale) == (want.level, want.scale)
+        assert np.array_equal(ctx.export_ct(out[0]), want.data)
+        assert ctx.device_error() == 0
+    finally:
+        ctx.close()
+
+
 def test_tensor_form_equals_uint64_form_full_size():
     """N = 2^16, 24 + 8 primes, 16 pairs per batched launch (the batched
     launch shape of the throughput benchmark, at a quarter of its batch)."""
@@ -76,10 +108,12 @@ def test_tensor_form_equals_uint64_form_full_size():
         for form in (False, True):
             ctx.set_form(form)
             out = [ctx.new_ct(level + 1) for _ in range(pairs)]
-            ctx.mul_relin_batch(cts[:pairs], cts[pairs:], out, rescale=True)
+            ctx.mul_relin_batch(cts[:pairs], cts[pairs:], out, rescale=ck.RESCALE_SEPARATE)
+            merged = [ctx.new_ct(level + 1) for _ in range(pairs)]
+            ctx.mul_relin_batch(cts[:pairs], cts[pairs:], merged, rescale=ck.RESCALE_MERGED)
             rots = [ctx.new_ct(level + 1) for _ in range(4)]
             ctx.rotate_hoisted(cts[:2], [1, 1 << 14], rots)
-            res[form] = [ctx.export_ct(c) for c in out + rots]
+            res[form] = [ctx.export_ct(c) for c in out + merged + rots]
         assert ctx.device_error() == 0
         for x, y in zip(res[False], res[True]):
             assert np.array_equal(x, y)

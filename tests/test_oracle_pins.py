@@ -278,6 +278,59 @@ def test_rescale_is_exact_rounded_division(tiny_oracle):
     assert out.scale == 2.0 ** 90 / ql
 
 
+def _crt(residues, moduli):
+    """The integer in [0, prod moduli) with the given residues (Python ints)."""
+    M = math.prod(moduli)
+    x = 0
+    for r, m in zip(residues, moduli):
+        Mi = M // m
+        x += int(r) * Mi * pow(Mi, -1, m)
+    return x % M
+
+
+def test_merged_moddown_rescale_is_floor_division_minus_small_multiple(tiny_oracle):
+    """Reading C21: out = floor((X + H) / S) - u = round(X / S) - u with
+    S = P q_l, H = (S - 1)/2 and 0 <= u <= K, exactly."""
+    o = tiny_oracle
+    level, K = o.n_q - 1, o.n_p
+    ext = list(range(level + 1)) + [o.n_q + k for k in range(K)]
+    moduli = [int(o.moduli[m]) for m in ext]
+    rng = np.random.default_rng(21)
+    x = np.stack([rng.integers(0, m, size=o.n, dtype=np.uint64) for m in moduli])
+    out = o.moddown_rescale(o.ntt(x, ext), level)
+    y = o.intt(out, list(range(level)))
+    div = int(o.q[level]) * math.prod(int(o.moduli[o.n_q + k]) for k in range(K))
+    Qlow = math.prod(int(q) for q in o.q[:level])
+    us = []
+    for k in range(o.n):
+        X = _crt([x[t, k] for t in range(len(ext))], moduli)
+        Y = _crt([y[t, k] for t in range(level)], [int(q) for q in o.q[:level]])
+        u = ((X + (div - 1) // 2) // div - Y) % Qlow
+        assert u <= K, (k, u)
+        us.append(u)
+    assert len(set(us)) > 1  # the overflow term is exercised, not always 0
+
+
+def test_merged_mul_relin_rescale_matches_separate_steps(toy_oracle):
+    """Reading C21 against C9 then C10: the two roundings differ by at most
+    K + 2 per coefficient, and the merged product decrypts within 2^-25."""
+    o = toy_oracle
+    scale = 2.0 ** 40
+    level = o.n_q - 1
+    z = si.messages(31, 2, o.n // 2)
+    cts = [o.encrypt(o.pt_from_int(o.encode(z[i], scale), level), level, scale, 60 + i) for i in range(2)]
+    merged = o.mul_relin_rescale(cts[0], cts[1])
+    separate = o.rescale(o.mul_relin(cts[0], cts[1]))
+    assert (merged.level, merged.scale) == (separate.level, separate.scale)
+    Qlow = math.prod(int(q) for q in o.q[:level])
+    for pol in range(2):
+        a = o.crt_centred(o.intt(merged.data[pol], list(range(level))), level - 1)
+        b = o.crt_centred(o.intt(separate.data[pol], list(range(level))), level - 1)
+        assert max(abs(centred(p - q, Qlow)) for p, q in zip(a, b)) <= o.n_p + 2
+    err = np.max(np.abs(o.decrypt_decode(merged) - z[0] * z[1]))
+    assert err <= 2.0 ** -25, err
+
+
 # ---------------------------------------------------------------- automorphisms (C11)
 def test_automorphism_group_law(tiny_oracle):
     o = tiny_oracle
