@@ -227,10 +227,14 @@ def roofline(prof, w, ndig, hbm_peak, hbm_kind, alu_peaks, tensor_peak=None, nam
     if not cands:
         return None
     best = max(cands, key=lambda c: c["frac"])
+    # measured DRAM bytes per unit (ncu) scaled to this step's average launch
     tr = traffic_table().get(name)
+    traffic = (tr["dram_bytes_per_unit"] * units / nlaunch
+               if tr and tr.get("valid") and tr.get("dram_bytes_per_unit") else None)
     best.update({"kernel": name, "avg_launch_us": ms / nlaunch * 1e3, "launches": nlaunch,
-                 "share_of_timed_device_ms": ms / total,
-                 "traffic": tr.get("dram_bytes_per_launch") if tr and tr.get("valid", True) else None,
+                 "share_of_timed_device_ms": ms / total, "traffic": traffic,
+                 "traffic_source": "profiles/traffic.json (ncu dram__bytes_read.sum + dram__bytes_write.sum "
+                                   "per unit x units per launch)" if traffic else None,
                  "other_bounds": [c for c in cands if c is not best]})
     return best
 
@@ -330,9 +334,11 @@ def run_gpu(args):
         bctx.profile(True)
         launches0 = ctx.launch_count() + bctx.launch_count()
         marks = [[ev(), ev(), ev(), ev()] for _ in range(args.steps)]
+        torch.cuda.nvtx.range_push("timed")  # ncu --nvtx-include "timed/" selects these launches
         for s in range(args.steps):
             step(marks[s])
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         launches = ctx.launch_count() + bctx.launch_count() - launches0
         prof = ctx.profile_read()
         for k, v in bctx.profile_read().items():
