@@ -39,6 +39,8 @@ is named B1..B8 and listed in the design notes:
      one level l, rescaled once, plus round(c_0 S).  Products take the lower
      level of their operands; a sum takes the scale of its first operand.
   B8 Output scale = (scale after SlotToCoeff) * Delta_in / q0.
+  B9 Every ciphertext product (B6, B7) is the relinearised product with
+     ModDown and rescale merged into one conversion (reading C21).
 Parity unpinned: nothing here (see tests/test_oracle_bootstrap.py).
 """
 from __future__ import annotations
@@ -331,8 +333,9 @@ class Evaluator:
         return self.o.add_plain(a, self.o.pt_from_int(m, a.level))
 
     def mul(self, a: OCt, b: OCt) -> OCt:
+        """Relinearised product at the lower level, ModDown and rescale merged (C21)."""
         lv = min(a.level, b.level)
-        return self.o.rescale(self.o.mul_relin(self.drop(a, lv), self.drop(b, lv)))
+        return self.o.mul_relin_rescale(self.drop(a, lv), self.drop(b, lv))
 
     def times_i(self, a: OCt, sign: int) -> OCt:
         m = self._mono * sign

@@ -19,7 +19,9 @@ gamma; R3 the local classifier's update uses the previous iteration's
 gradient (Alg. 1) and, at the first iteration, the current one; R4 non-integer
 constants multiply as round(c q_l S_target / S) followed by a rescale, so every
 sum meets at one scale (an operand at a higher level is brought down the
-same way); integer constants (the 2 of delta Z) cost no level (C14).
+same way); integer constants (the 2 of delta Z) cost no level (C14); R5
+ciphertext products go through the bootstrapping evaluator's multiply, with
+ModDown and rescale merged (C21).
 `plain_step` is the same computation on FP64 slot vectors (numpy).
 """
 from __future__ import annotations

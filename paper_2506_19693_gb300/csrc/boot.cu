@@ -166,10 +166,12 @@ struct MacArgs {
   const u64 *pt[MAXA];
   u64 *o0[MAXB], *o1[MAXB];
 };
-// o = sum_a x_a * pt_a (BSGS inner sum)
+// o = sum_a x_a * pt_a (BSGS inner sum).  Grid (ciphertexts, coefficient
+// blocks, limbs): the ciphertext index varies fastest, so the CTAs that read
+// one block of the shared plaintexts run back to back and share it in L2.
 __global__ void k_mac_plain(const MacArgs a) {
-  const u32 k = blockIdx.x * TPB + threadIdx.x;
-  const int t = blockIdx.y, c = blockIdx.z;
+  const u32 k = blockIdx.y * TPB + threadIdx.x;
+  const int t = blockIdx.z, c = blockIdx.x;
   if (k >= a.n) return;
   const ModInfo m = a.mods[t];
   const size_t off = (size_t)t * a.n + k;
@@ -649,12 +651,15 @@ struct Eval {
     sync_fields(y);
     BV o = fresh(lv, a.scale * bb.scale);
     if (err) return o;
+    // relinearised product with ModDown and rescale merged (reading C21)
     for (int c0 = 0; c0 < nct && !err; c0 += MAX_CTS) {
-      int rc = mul_relin_chunk(c, x.v.data() + c0, y.v.data() + c0, o.v.data() + c0, std::min(MAX_CTS, nct - c0));
+      int rc = mul_relin_chunk(c, x.v.data() + c0, y.v.data() + c0, o.v.data() + c0, std::min(MAX_CTS, nct - c0),
+                               true);
       if (rc) err = rc;
     }
-    o.scale = a.scale * bb.scale;
-    return rescale(o);
+    o.level = lv - 1;
+    o.scale = o.v.empty() ? a.scale * bb.scale / (double)c->mod[lv] : o.v[0].scale;
+    return o;
   }
 
   // bring ct to `level` at exactly `scale` (B7)
@@ -798,7 +803,7 @@ struct Eval {
           a.o0[cc] = inner.v[c0 + cc].data;
           a.o1[cc] = p1(inner.v[c0 + cc]);
         }
-        const dim3 g((c->n + TPB - 1) / TPB, lv.level + 1, cn);
+        const dim3 g(cn, (c->n + TPB - 1) / TPB, lv.level + 1);
         PROF_LAUNCH(c, PK_ELEMENTWISE, (u64)(lv.level + 1) * cn * a.na, (k_mac_plain<<<g, TPB, 0, c->stream>>>(a)));
         if (cudaGetLastError() != cudaSuccess) err = CKKS_E_CUDA;
       }

@@ -110,9 +110,12 @@ class REBlock:
         return [x if x.level == level else Ciphertext(x.data, level, x.scale) for x in xs]
 
     def mul(self, a, b):
+        """Products at the lower level; ModDown and rescale merged (C21), as the
+        bootstrapping evaluator multiplies."""
+        from . import RESCALE_MERGED
         lv = min(self._lvl(a), self._lvl(b))
         out = [self.ctx.new_ct(lv + 1) for _ in a]
-        self.ctx.mul_relin_batch(self.view(a, lv), self.view(b, lv), out, rescale=True)
+        self.ctx.mul_relin_batch(self.view(a, lv), self.view(b, lv), out, rescale=RESCALE_MERGED)
         return out
 
     def rescale(self, xs, scale):
