@@ -101,6 +101,8 @@ def _load():
         "oc_mul_relin": (P, [V, _u64p, _u64p, P, _u64p]),
         "oc_rescale": (P, [V, _u64p, P, _u64p]),
         "oc_moddown_rescale": (P, [V, _u64p, P, _u64p]),
+        "oc_keyswitch_ext": (P, [V, _u64p, P, ctypes.c_uint64, _u64p]),
+        "oc_mul_scalars": (None, [V, _u64p, P, _ip, _u64p, _u64p]),
         "oc_mul_relin_rescale": (P, [V, _u64p, _u64p, P, _u64p]),
         "oc_automorph": (P, [V, _u64p, P, ctypes.c_uint64, _u64p]),
         "oc_automorph_coeff": (None, [V, _u64p, P, _ip, ctypes.c_uint64, _u64p]),
@@ -414,6 +416,23 @@ class Oracle:
         if self._lib.oc_rescale(self._c, _p64(a.data), a.level, _p64(out)) != 0:
             raise ValueError("cannot rescale level 0")
         return OCt(out, a.level - 1, a.scale / self.q[a.level])
+
+    def keyswitch_ext(self, d: np.ndarray, level: int, galois: int) -> np.ndarray:
+        """Key switch of d (NTT domain, level+1 limbs) stopped before ModDown:
+        [2][level+1+K][N] over q_0..q_level, P."""
+        d = np.ascontiguousarray(d, dtype=np.uint64)
+        acc = np.zeros((2, level + 1 + self.n_p, self.n), dtype=np.uint64)
+        if self._lib.oc_keyswitch_ext(self._c, _p64(d), level, galois, _p64(acc)) != 0:
+            raise KeyError(galois)
+        return acc
+
+    def mul_scalars(self, x: np.ndarray, mods, w) -> np.ndarray:
+        """x[t] * w[t] mod the t-th modulus (one scalar per limb)."""
+        x = np.ascontiguousarray(x, dtype=np.uint64)
+        ww = np.ascontiguousarray(np.array([int(v) for v in w], dtype=np.uint64))
+        out = np.zeros_like(x)
+        self._lib.oc_mul_scalars(self._c, _p64(x), len(mods), _pint(list(mods)), _p64(ww), _p64(out))
+        return out
 
     def moddown_rescale(self, x: np.ndarray, level: int) -> np.ndarray:
         """Reading C21 on one polynomial: x [level+1+K][N] over q_0..q_l, P

@@ -41,6 +41,11 @@ is named B1..B8 and listed in the design notes:
   B8 Output scale = (scale after SlotToCoeff) * Delta_in / q0.
   B9 Every ciphertext product (B6, B7) is the relinearised product with
      ModDown and rescale merged into one conversion (reading C21).
+  B10 In a merged level the giant steps meet before any ModDown: the sum
+     P inner_0 + sum_b (P sigma_b(inner_b.c0) + KS_acc(sigma_b(inner_b.c1)))
+     over Q_l P (KS_acc: ModUp and key inner product, no ModDown) is divided
+     by P q_l once (C21), replacing a ModDown per giant rotation and the
+     level's rescale.
 Parity unpinned: nothing here (see tests/test_oracle_bootstrap.py).
 """
 from __future__ import annotations
@@ -357,11 +362,28 @@ class Evaluator:
             out[p] = o.ntt(res, list(range(top + 1)))
         return OCt(out, top, float(q0))
 
-    # ---- B3
+    def sigma(self, ct: OCt, g: int) -> OCt:
+        """sigma_g on both polynomials of an NTT-domain ciphertext (no key switch)."""
+        o = self.o
+        mods = list(range(ct.level + 1))
+        out = np.empty_like(ct.data)
+        for p in range(2):
+            out[p] = o.ntt(o.automorph_coeff(o.intt(ct.data[p], mods), mods, g), mods)
+        return OCt(out, ct.level, ct.scale)
+
+    # ---- B3, B10
     def linear(self, x: OCt, lv: LinLevel, pts) -> OCt:
+        """One merged level: baby rotations hoisted; every giant step's term
+        inner_b (sum over a of pt_{b,a} Rot(x, a step)) joins one sum over Q_l P,
+        P inner_0 + sum_{b>0} (P sigma_b(inner_b.c0) + KS_acc(sigma_b(inner_b.c1))),
+        which one merged ModDown-rescale (C21) divides by P q_l (reading B10)."""
         o = self.o
         assert x.level >= lv.level, (x.level, lv.level)
         x = self.drop(x, lv.level)
+        l = lv.level
+        mods = list(range(l + 1))
+        P = math.prod(int(o.moduli[o.n_q + k]) for k in range(o.n_p))
+        pmod = [P % int(o.q[t]) for t in mods]
         babies = sorted({a for _, items in lv.plan for a, _ in items})
         rot_steps = [a * lv.step for a in babies if a]
         xa = {0: x}
@@ -369,17 +391,28 @@ class Evaluator:
             outs = o.rotate_hoisted(x, rot_steps)
             for a, c in zip([a for a in babies if a], outs):
                 xa[a] = c
-        acc = None
+        ext = l + 1 + o.n_p
+        X = np.zeros((2, ext, o.n), dtype=np.uint64)  # the sum over q_0..q_l, P
+        base = np.zeros((2, l + 1, o.n), dtype=np.uint64)  # its part P * base on q_0..q_l
+        qcol = np.array([int(q) for q in o.q[: l + 1]], dtype=np.uint64)[:, None]
+        extq = np.array([int(o.moduli[m]) for m in list(range(l + 1)) + [o.n_q + k for k in range(o.n_p)]],
+                        dtype=np.uint64)[:, None]
         for (b, items), row in zip(lv.plan, pts):
             inner = None
             for (a, _), pt in zip(items, row):
                 term = o.mul_plain(xa[a], pt, 1.0)
                 inner = term if inner is None else o.add(inner, term)
-            if b:
-                inner = o.rotate(inner, lv.g * b * lv.step)
-            acc = inner if acc is None else o.add(acc, inner)
-        acc.scale = x.scale * float(o.q[lv.level])
-        return o.rescale(acc)
+            if b == 0:
+                base = (base + inner.data) % qcol
+            else:
+                g = o.galois_elt(lv.g * b * lv.step)
+                t = self.sigma(inner, g)
+                X = (X + o.keyswitch_ext(t.data[1], l, g)) % extq
+                base[0] = (base[0] + t.data[0]) % qcol
+        for p in range(2):
+            X[p, : l + 1] = (X[p, : l + 1] + o.mul_scalars(base[p], mods, pmod)) % qcol
+        out = np.stack([o.moddown_rescale(X[p], l) for p in range(2)])
+        return OCt(out, l - 1, x.scale * float(o.q[l]) / float(o.q[l]))
 
     # ---- B7
     def chebyshev_basis(self, t1: OCt) -> dict:

@@ -784,6 +784,27 @@ int oc_rotate_hoisted(const oc_ctx *c, const u64 *in, int level, int n_g, const 
 }
 
 /* expose key switching for tests: galois = 0 selects the relinearisation key */
+/* The key switch of d stopped before ModDown: acc = sum_j ModUp_j(d) * key_j
+ * over q_0..q_level, P (NTT domain), [2][level+1+K][N]. */
+int oc_keyswitch_ext(const oc_ctx *c, const u64 *d, int level, u64 galois, u64 *acc) {
+  okey *k = find_key(c, galois);
+  if (!k) return -1;
+  int ext = level + 1 + c->n_p;
+  u64 *digits = (u64 *)malloc(sizeof(u64) * (u64)c->n_digits * ext * c->n);
+  int nact = modup(c, d, level, digits);
+  inner(c, digits, nact, level, k->data, acc);
+  free(digits);
+  return 0;
+}
+
+/* out[t][k] = x[t][k] * w[t] mod m_t: one scalar per limb */
+void oc_mul_scalars(const oc_ctx *c, const u64 *x, int n_limbs, const int *mods, const u64 *w, u64 *out) {
+  for (int t = 0; t < n_limbs; t++) {
+    u64 q = c->mod[mods[t]];
+    for (u64 k = 0; k < c->n; k++) out[(u64)t * c->n + k] = mulmod(x[(u64)t * c->n + k], w[t] % q, q);
+  }
+}
+
 int oc_keyswitch(const oc_ctx *c, const u64 *d, int level, u64 galois, u64 *out0, u64 *out1) {
   okey *k = find_key(c, galois);
   if (!k) return -1;

@@ -317,6 +317,8 @@ struct BootState {
   u64 *mono_p = nullptr, *mono_m = nullptr;
   std::vector<u64 *> chunks, free_slots;
   size_t slot_words = 0;
+  u64 *acc_qp = nullptr;    // giant-step sums over Q_l P, [nct][2][l+1+K][N]
+  size_t acc_qp_words = 0;
 };
 
 void boot_free(ckks_ctx *c) {
@@ -326,6 +328,7 @@ void boot_free(ckks_ctx *c) {
   cudaFree(b->mono_p);
   cudaFree(b->mono_m);
   for (u64 *p : b->chunks) cudaFree(p);
+  cudaFree(b->acc_qp);
   delete b;
   c->boot = nullptr;
 }
@@ -775,8 +778,30 @@ struct Eval {
       }
       for (int j = 0; j < m; ++j) xa[rot_as[j]] = outs[j];
     }
-    BV acc;
-    bool have = false;
+    // the giant steps meet over Q_l P before one merged ModDown-rescale (B10):
+    // acc = sum_{b>0} KS_acc(sigma_b(inner_b.c1)), base = inner_0 + (sum_{b>0}
+    // sigma_b(inner_b.c0), 0); the result is round((acc + P base) / (P q_l)) - u
+    const int l = lv.level, ext = l + 1 + c->n_p;
+    const size_t per = (size_t)2 * ext * c->n;
+    if (!err && b.acc_qp_words < per * nct) {
+      if (c->capturing) {
+        err = CKKS_E_STATE;
+      } else {
+        cudaFree(b.acc_qp);
+        b.acc_qp = nullptr;
+        b.acc_qp_words = 0;
+        if (cudaMalloc(&b.acc_qp, sizeof(u64) * per * nct) != cudaSuccess) {
+          cudaGetLastError();
+          err = CKKS_E_OOM;
+        } else {
+          b.acc_qp_words = per * nct;
+        }
+      }
+    }
+    std::vector<u64 *> accp(nct);
+    for (int i = 0; i < nct && !err; ++i) accp[i] = b.acc_qp + per * i;
+    BV base;
+    bool have_base = false, have_acc = false;
     for (const Giant &gi : lv.plan) {
       BV inner = fresh(lv.level, x.scale);
       int ci = lv.first_const;
@@ -807,24 +832,63 @@ struct Eval {
         PROF_LAUNCH(c, PK_ELEMENTWISE, (u64)(lv.level + 1) * cn * a.na, (k_mac_plain<<<g, TPB, 0, c->stream>>>(a)));
         if (cudaGetLastError() != cudaSuccess) err = CKKS_E_CUDA;
       }
-      if (gi.b) {
-        BV r = automorph(inner, ckks_galois_elt(c, lv.g * gi.b * lv.step));
-        release(inner);
-        inner = r;
+      if (gi.b == 0) {  // inner_0 enters the base as it is
+        if (!have_base) {
+          base = inner;
+          have_base = true;
+        } else {
+          BV s2 = addsub(base, inner, false);
+          release(base);
+          release(inner);
+          base = s2;
+        }
+        continue;
       }
-      if (!have) {
-        acc = inner;
-        have = true;
-      } else {
-        BV s = addsub(acc, inner, false);
-        release(acc);
-        release(inner);
-        acc = s;
+      if (!have_base) {  // no b = 0 term: the base starts at zero
+        base = fresh(lv.level, x.scale);
+        for (auto &ct : base.v)
+          if (!err && cudaMemsetAsync(ct.data, 0, sizeof(u64) * 2 * (size_t)ct.n_limbs * c->n, c->stream))
+            err = CKKS_E_CUDA;
+        have_base = true;
       }
+      sync_fields(inner);
+      const u64 gal = ckks_galois_elt(c, lv.g * gi.b * lv.step);
+      for (int c0 = 0; c0 < nct && !err; c0 += MAX_CTS) {
+        const int cn = std::min(MAX_CTS, nct - c0);
+        std::vector<u64 *> b0(cn);
+        for (int i = 0; i < cn; ++i) b0[i] = base.v[c0 + i].data;
+        int rc = rotate_accumulate_chunk(c, inner.v.data() + c0, gal, cn, accp.data() + c0, b0.data(), have_acc);
+        if (rc) err = rc;
+      }
+      have_acc = true;
+      release(inner);
     }
     for (int a : rot_as) release(xa[a]);
-    acc.scale = x.scale * (double)c->mod[lv.level];
-    return rescale(acc);
+    if (!have_acc)
+      for (int i = 0; i < nct && !err; ++i)
+        if (cudaMemsetAsync(accp[i], 0, sizeof(u64) * per, c->stream)) err = CKKS_E_CUDA;
+    BV out = fresh(l - 1, x.scale);
+    if (err) return out;
+    for (int c0 = 0; c0 < nct && !err; c0 += MAX_CTS) {
+      const int cn = std::min(MAX_CTS, nct - c0);
+      int rc = ensure_scratch(c, ks_merged_words(c, l, cn));
+      std::vector<const u64 *> b0(cn), b1(cn);
+      std::vector<u64 *> o0(cn), o1(cn);
+      for (int i = 0; i < cn; ++i) {
+        b0[i] = base.v[c0 + i].data;
+        b1[i] = p1(base.v[c0 + i]);
+        o0[i] = out.v[c0 + i].data;
+        o1[i] = p1(out.v[c0 + i]);
+      }
+      if (!rc) rc = ks_merged_finish(c, l, cn, accp.data() + c0, b0.data(), b1.data(), o0.data(), o1.data(),
+                                     c->scratch);
+      if (rc) err = rc;
+    }
+    release(base);
+    // the level's plaintexts sit at scale q_l: (x.scale q_l) / q_l, as a rescale would give
+    out.scale = x.scale * (double)c->mod[l] / (double)c->mod[l];
+    sync_fields(out);
+    return out;
   }
 
   // ---- B7 ----

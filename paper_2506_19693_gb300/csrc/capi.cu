@@ -279,6 +279,55 @@ int automorph_chunk(ckks_ctx *c, const ckks_ct *in, const u64 *g, ckks_ct *out, 
   return CKKS_OK;
 }
 
+// Giant step of a merged linear level (reading B10): t = sigma_g(in[i]) (both
+// polynomials, NTT domain), then acc[i] (= or, accumulate, +=) the key-switch
+// accumulator of t.c1 over q_0..q_l, P, and base0[i] += t.c0 over q_0..q_l.
+// n <= MAX_CTS, all at one level.
+int rotate_accumulate_chunk(ckks_ctx *c, const ckks_ct *in, u64 g, int n, u64 *const *acc, u64 *const *base0,
+                            bool accumulate) {
+  const int level = in[0].level, nl = level + 1;
+  const u32 nn = c->n;
+  const DevKey *k = find_galois(c, g);
+  if (!k) return CKKS_E_NOKEY;
+  const size_t tw = (size_t)2 * nl * nn * n;
+  int rc = ensure_scratch(c, tw + ks_modup_words(c, level, n));
+  if (rc) return rc;
+  std::vector<const u64 *> t0(n), t1(n), keys(n, k->data);
+  std::vector<u32> g32(n, (u32)g);
+  EwArgs e;
+  for (int i = 0; i < n; ++i) {
+    u64 *tmp = c->scratch + (size_t)2 * nl * nn * i;
+    e.x0[i] = in[i].data;
+    e.x1[i] = poly1(&in[i], nn);
+    e.o0[i] = tmp;
+    e.o1[i] = tmp + (size_t)nl * nn;
+    t0[i] = tmp;
+    t1[i] = tmp + (size_t)nl * nn;
+  }
+  rc = ew_automorph(c, e, g32.data(), nl, n, true);
+  if (rc) return rc;
+  std::vector<u64 *> eb(n);
+  rc = ks_modup(c, level, n, t1.data(), c->scratch + tw, eb.data());
+  if (rc) return rc;
+  std::vector<const u64 *> ebc(eb.begin(), eb.end());
+  rc = ks_accumulate(c, level, n, t1.data(), ebc.data(), keys.data(), acc, accumulate);
+  if (rc) return rc;
+  // base0[i] += t0[i]: two single polynomials per element-wise slot (an odd
+  // last one paired with itself: both lanes write the same sum)
+  EwArgs s;
+  const int slots = (n + 1) / 2;
+  for (int j = 0; j < slots; ++j) {
+    const int i0 = 2 * j, i1 = std::min(2 * j + 1, n - 1);
+    s.x0[j] = base0[i0];
+    s.y0[j] = t0[i0];
+    s.o0[j] = base0[i0];
+    s.x1[j] = base0[i1];
+    s.y1[j] = t0[i1];
+    s.o1[j] = base0[i1];
+  }
+  return ew_addsub(c, s, nl, slots, false);
+}
+
 // Hoisted rotations: one ModUp of c1 per input serves every Galois element;
 // out[j * n + i] = sigma_{g[j]}(in[i]) key-switched back to s.  Outputs must
 // not alias inputs.  All inputs at one level.

@@ -91,6 +91,7 @@ struct IPArgs {
   const u64 *key[MAX_CTS];         // [n_digits][2][key_ext][N]
   u32 gal[MAX_CTS];
   u64 *acc[MAX_CTS];               // [2][ext][N]
+  int accumulate;                  // 1: acc += result (mod t) instead of acc = result
 };
 
 // Grid: (groups of IP_GROUP outputs, coefficient blocks, extended limbs).
@@ -132,8 +133,14 @@ __global__ void __launch_bounds__(TPB, NDIG <= 3 ? 4 : 2) k_inner(const IPArgs a
       mac128(h0, l0, v, kb[j]);
       mac128(h1, l1, v, ka[j]);
     }
-    a.acc[p][(size_t)t * a.n + k] = reduce128(h0, l0, m);
-    a.acc[p][((size_t)a.ext + t) * a.n + k] = reduce128(h1, l1, m);
+    u64 r0 = reduce128(h0, l0, m), r1 = reduce128(h1, l1, m);
+    u64 *o0 = a.acc[p] + (size_t)t * a.n + k, *o1 = a.acc[p] + ((size_t)a.ext + t) * a.n + k;
+    if (a.accumulate) {
+      r0 = addmod(r0, *o0, m.q);
+      r1 = addmod(r1, *o1, m.q);
+    }
+    *o0 = r0;
+    *o1 = r1;
   }
 }
 
@@ -336,6 +343,49 @@ int ks_modup(ckks_ctx *c, int level, int np, const u64 *const *d, u64 *ws, u64 *
 // Inner product + ModDown for nv <= MAX_CTS outputs.  Output v uses input
 // polynomial d[v] with its lifted digits ext[v], key keys[v] and automorphism
 // gal[v]; ws holds per output acc [2][l+1+K] then z [2][l+1].
+// Key inner product of nv outputs into acc[i] ([2][ext][N], NTT domain),
+// overwriting or (accumulate) adding.
+static int launch_inner(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *const *ext_digits,
+                        const u64 *const *keys, const u32 *gal, u64 *const *acc, bool accumulate) {
+  const u32 n = c->n;
+  const int nl = level + 1, ext = nl + c->n_p;
+  const int ndig = (nl + c->alpha - 1) / c->alpha;
+  IPArgs a;
+  a.mods = c->d_mods;
+  a.n = n;
+  a.log_n = c->log_n;
+  a.ext = ext;
+  a.ndig = ndig;
+  a.key_ext = c->n_q + c->n_p;
+  a.np = nv;
+  a.accumulate = accumulate ? 1 : 0;
+  for (int t = 0; t < ext; ++t) {
+    a.mod_of[t] = (unsigned char)c->ext_mod(level, t);
+    a.keylimb_of[t] = (unsigned char)c->key_limb(level, t);
+  }
+  for (int j = 0; j < ndig; ++j) {
+    a.lo[j] = j * c->alpha;
+    a.hi[j] = std::min((j + 1) * c->alpha, nl);
+  }
+  for (int i = 0; i < nv; ++i) {
+    a.d[i] = d[i];
+    a.ext_buf[i] = ext_digits[i];
+    a.key[i] = keys[i];
+    a.gal[i] = gal ? gal[i] : 1u;
+    a.acc[i] = acc[i];
+  }
+  const int group = c->ip_group > 0 ? c->ip_group : 8;
+  dim3 g((nv + group - 1) / group, (n + TPB - 1) / TPB, ext);
+  switch (ndig) {
+#define ICASE(D) \
+  case D: PROF_LAUNCH(c, PK_INNER, (u64)nv * ext, (k_inner<D><<<g, TPB, 0, c->stream>>>(a, group))); break;
+    ICASE(1) ICASE(2) ICASE(3) ICASE(4) ICASE(5) ICASE(6) ICASE(7) ICASE(8)
+#undef ICASE
+    default: return CKKS_E_PARAM;
+  }
+  return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_CUDA;
+}
+
 // ModDown and rescale merged (reading C21) on the accumulators of nv outputs:
 // o_c = round((acc_c + P base_c) / (P q_l)) - u over q_0..q_{l-1}.
 static int ks_merged_tail(ckks_ctx *c, int level, int nv, u64 *const *acc, u64 *const *z, const int *mods,
@@ -439,7 +489,6 @@ int ks_tail(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *cons
   if (merged && (base0_gal || level < 1)) return CKKS_E_PARAM;
   const u32 n = c->n;
   const int nl = level + 1, K = c->n_p, ext = nl + K;
-  const int ndig = (nl + c->alpha - 1) / c->alpha;
   const size_t per = ks_tail_words(c, level, 1);
   std::vector<u64 *> acc(nv), z(nv);
   for (int i = 0; i < nv; ++i) {
@@ -448,41 +497,8 @@ int ks_tail(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *cons
   }
   int mods[MAX_MODS];
   for (int t = 0; t < ext; ++t) mods[t] = c->ext_mod(level, t);
-  {
-    IPArgs a;
-    a.mods = c->d_mods;
-    a.n = n;
-    a.log_n = c->log_n;
-    a.ext = ext;
-    a.ndig = ndig;
-    a.key_ext = c->n_q + c->n_p;
-    a.np = nv;
-    for (int t = 0; t < ext; ++t) {
-      a.mod_of[t] = (unsigned char)mods[t];
-      a.keylimb_of[t] = (unsigned char)c->key_limb(level, t);
-    }
-    for (int j = 0; j < ndig; ++j) {
-      a.lo[j] = j * c->alpha;
-      a.hi[j] = std::min((j + 1) * c->alpha, nl);
-    }
-    for (int i = 0; i < nv; ++i) {
-      a.d[i] = d[i];
-      a.ext_buf[i] = ext_digits[i];
-      a.key[i] = keys[i];
-      a.gal[i] = gal ? gal[i] : 1u;
-      a.acc[i] = acc[i];
-    }
-    const int group = c->ip_group > 0 ? c->ip_group : 8;
-    dim3 g((nv + group - 1) / group, (n + TPB - 1) / TPB, ext);
-    switch (ndig) {
-#define ICASE(D) \
-  case D: PROF_LAUNCH(c, PK_INNER, (u64)nv * ext, (k_inner<D><<<g, TPB, 0, c->stream>>>(a, group))); break;
-      ICASE(1) ICASE(2) ICASE(3) ICASE(4) ICASE(5) ICASE(6) ICASE(7) ICASE(8)
-#undef ICASE
-      default: return CKKS_E_PARAM;
-    }
-    if (cudaGetLastError() != cudaSuccess) return CKKS_E_CUDA;
-  }
+  rc = launch_inner(c, level, nv, d, ext_digits, keys, gal, acc.data(), false);
+  if (rc) return rc;
   if (merged) return ks_merged_tail(c, level, nv, acc.data(), z.data(), mods, base0, base1, o0, o1);
   std::vector<const u64 *> ps(2 * nv);
   std::vector<u64 *> pd(2 * nv);
@@ -547,6 +563,31 @@ int ks_tail(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *cons
   PROF_LAUNCH(c, PK_COMBINE, (u64)nv * nl, (k_combine<<<g, TPB, 0, c->stream>>>(a, nl)));
   if (cudaGetLastError() != cudaSuccess) return CKKS_E_CUDA;
   return CKKS_OK;
+}
+
+int ks_accumulate(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *const *ext_digits,
+                  const u64 *const *keys, u64 *const *acc, bool accumulate) {
+  if (nv <= 0) return CKKS_OK;
+  if (nv > MAX_CTS) return CKKS_E_PARAM;
+  int rc = check_shape(c, level);
+  if (rc) return rc;
+  return launch_inner(c, level, nv, d, ext_digits, keys, nullptr, acc, accumulate);
+}
+
+size_t ks_merged_words(const ckks_ctx *c, int level, int nv) { return (size_t)2 * level * c->n * nv; }
+
+int ks_merged_finish(ckks_ctx *c, int level, int nv, u64 *const *acc, const u64 *const *base0,
+                     const u64 *const *base1, u64 *const *o0, u64 *const *o1, u64 *ws) {
+  if (nv <= 0) return CKKS_OK;
+  if (nv > MAX_CTS || level < 1) return CKKS_E_PARAM;
+  int rc = check_shape(c, level);
+  if (rc) return rc;
+  const int ext = level + 1 + c->n_p;
+  std::vector<u64 *> z(nv);
+  for (int i = 0; i < nv; ++i) z[i] = ws + (size_t)2 * level * c->n * i;
+  int mods[MAX_MODS];
+  for (int t = 0; t < ext; ++t) mods[t] = c->ext_mod(level, t);
+  return ks_merged_tail(c, level, nv, acc, z.data(), mods, base0, base1, o0, o1);
 }
 
 int ks_batch(ckks_ctx *c, int level, int np, const u64 *const *d, const u64 *const *keys,
