@@ -297,6 +297,22 @@ int ckks_add_plain_batch(ckks_ctx *ctx, const ckks_ct *a, const uint64_t *pt_dev
 /* In-place rescale of n ciphertexts at one level. */
 int ckks_rescale_batch(ckks_ctx *ctx, ckks_ct *inout, int n);
 
+/* Relinearised products of n ciphertext pairs that live in HOST memory (no
+ * paper counterpart: the batched multiply of Eq. mult fed from the host).
+ * a_host, b_host: n x uint64[2][level+1][N] (NTT domain, the layout of
+ * ckks_ct_export), scales scale_a, scale_b; out_host: n x
+ * uint64[2][level'+1][N] with level' = level - (do_rescale != NONE);
+ * *out_scale (may be NULL) receives the products' scale.  The batch is cut
+ * into chunks of `chunk` (1..128) pairs: the host->device copy of chunk i+1,
+ * the products of chunk i (on the context stream) and the device->host copy
+ * of chunk i-1 overlap on two non-blocking copy streams and three staging
+ * slots owned by the context.  Copies are asynchronous only from page-locked
+ * host memory (otherwise they serialise but stay correct).  Returns when
+ * out_host is complete; CKKS_E_STATE during graph capture. */
+int ckks_mul_relin_host(ckks_ctx *ctx, const uint64_t *a_host, const uint64_t *b_host, double scale_a,
+                        double scale_b, uint32_t level, int n, int do_rescale, int chunk, uint64_t *out_host,
+                        double *out_scale);
+
 /* ---- uneven batches: executor, graph capture, tuning ------------------- */
 
 #define CKKS_OP_MUL_RELIN 1 /* out = a * b relinearised (rescaled when rescale != 0) */

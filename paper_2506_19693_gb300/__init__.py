@@ -94,6 +94,8 @@ SIGNATURES = {
     "ckks_mul_relin_batch": (_I, [_V, _CTP, _CTP, _CTP, _I, _I]),
     "ckks_rotate_batch": (_I, [_V, _CTP, _V, _CTP, _I]),
     "ckks_rescale_batch": (_I, [_V, _CTP, _I]),
+    "ckks_mul_relin_host": (_I, [_V, _V, _V, ctypes.c_double, ctypes.c_double, ctypes.c_uint32, _I, _I, _I, _V,
+                                 ctypes.POINTER(ctypes.c_double)]),
     "ckks_rotate_hoisted": (_I, [_V, _CTP, _I, _V, _I, _CTP]),
     "ckks_add_batch": (_I, [_V, _CTP, _CTP, _CTP, _I, _I]),
     "ckks_mul_int_batch": (_I, [_V, _CTP, ctypes.c_int64, _CTP, _I]),
@@ -473,6 +475,18 @@ class Context:
         ha, ho = self._handles(a), self._handles(out)
         _check(self.lib.ckks_add_plain_batch(self._h, ha, pt.data_ptr(), ho, len(a)), "ckks_add_plain_batch")
         return self._finish(out, ho)
+
+    def mul_relin_host(self, a_host, b_host, scale_a: float, scale_b: float, level: int, out_host,
+                       rescale: int = RESCALE_NONE, chunk: int = 16) -> float:
+        """Products of pairs held in host memory (page-locked torch tensors of
+        shape [n, 2, level+1, N], int64 view of the residues), streamed through
+        the GPU with copies overlapping compute; returns the products' scale."""
+        n = int(a_host.shape[0])
+        sc = ctypes.c_double()
+        _check(self.lib.ckks_mul_relin_host(self._h, a_host.data_ptr(), b_host.data_ptr(), scale_a, scale_b, level,
+                                            n, int(rescale), chunk, out_host.data_ptr(), ctypes.byref(sc)),
+               "ckks_mul_relin_host")
+        return sc.value
 
     def rescale_batch(self, cts) -> None:
         h = self._handles(cts)

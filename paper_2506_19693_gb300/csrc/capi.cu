@@ -470,6 +470,14 @@ int ckks_ctx_destroy(ckks_ctx *c) {
   cudaFree(c->fscratch);
   for (auto &kv : c->tc_bmats) cudaFree(kv.second);
   cudaFree(c->tc_err);
+  if (c->h2d) cudaStreamSynchronize(c->h2d), cudaStreamDestroy(c->h2d);
+  if (c->d2h) cudaStreamSynchronize(c->d2h), cudaStreamDestroy(c->d2h);
+  for (int i = 0; i < 3; ++i) {
+    if (c->ev_in[i]) cudaEventDestroy(c->ev_in[i]);
+    if (c->ev_comp[i]) cudaEventDestroy(c->ev_comp[i]);
+    if (c->ev_out[i]) cudaEventDestroy(c->ev_out[i]);
+  }
+  cudaFree(c->stage);
   boot_free(c);
   if (c->pinned) cudaFreeHost(c->pinned);
   delete c;
@@ -990,6 +998,78 @@ int ckks_rotate_batch(ckks_ctx *c, const ckks_ct *in, const int32_t *k, ckks_ct 
     if (rc) return rc;
   }
   return CKKS_OK;
+}
+
+int ckks_mul_relin_host(ckks_ctx *c, const uint64_t *a_host, const uint64_t *b_host, double scale_a,
+                        double scale_b, uint32_t level, int n, int do_rescale, int chunk, uint64_t *out_host,
+                        double *out_scale) {
+  if (!c || !a_host || !b_host || !out_host || n < 0 || chunk < 1 || chunk > MAX_CTS) return CKKS_E_PARAM;
+  if (level >= (uint32_t)c->n_q) return CKKS_E_LEVEL;
+  if (do_rescale < CKKS_RESCALE_NONE || do_rescale > CKKS_RESCALE_MERGED) return CKKS_E_PARAM;
+  if (do_rescale && level == 0) return CKKS_E_LEVEL;
+  if (c->capturing) return CKKS_E_STATE;
+  if (n == 0) return CKKS_OK;
+  const u32 nn = c->n;
+  const uint32_t out_level = do_rescale ? level - 1 : level;
+  const size_t in_w = (size_t)2 * (level + 1) * nn, out_w = (size_t)2 * (out_level + 1) * nn;
+  const size_t slot_w = (size_t)chunk * 3 * in_w;  // a, b and the product (full capacity) per pair
+  if (!c->h2d) CK_CUDA(cudaStreamCreateWithFlags(&c->h2d, cudaStreamNonBlocking));
+  if (!c->d2h) CK_CUDA(cudaStreamCreateWithFlags(&c->d2h, cudaStreamNonBlocking));
+  for (int i = 0; i < 3; ++i) {
+    if (!c->ev_in[i]) CK_CUDA(cudaEventCreateWithFlags(&c->ev_in[i], cudaEventDisableTiming));
+    if (!c->ev_comp[i]) CK_CUDA(cudaEventCreateWithFlags(&c->ev_comp[i], cudaEventDisableTiming));
+    if (!c->ev_out[i]) CK_CUDA(cudaEventCreateWithFlags(&c->ev_out[i], cudaEventDisableTiming));
+  }
+  if (c->stage_words < 3 * slot_w) {
+    CK_CUDA(cudaStreamSynchronize(c->d2h));
+    cudaFree(c->stage);
+    c->stage = nullptr;
+    c->stage_words = 0;
+    if (cudaMalloc(&c->stage, sizeof(u64) * 3 * slot_w) != cudaSuccess) {
+      cudaGetLastError();
+      return CKKS_E_OOM;
+    }
+    c->stage_words = 3 * slot_w;
+  }
+  double sc = 0.0;
+  const int nchunks = (n + chunk - 1) / chunk;
+  for (int ci = 0; ci < nchunks; ++ci) {
+    const int s = ci % 3, i0 = ci * chunk, cnt = std::min(chunk, n - i0);
+    u64 *sa = c->stage + (size_t)s * slot_w, *sb = sa + (size_t)chunk * in_w, *so = sb + (size_t)chunk * in_w;
+    // inputs of this chunk, once the slot's previous products have left
+    CK_CUDA(cudaStreamWaitEvent(c->h2d, c->ev_out[s], 0));
+    CK_CUDA(cudaMemcpyAsync(sa, a_host + (size_t)i0 * in_w, sizeof(u64) * cnt * in_w, cudaMemcpyHostToDevice,
+                            c->h2d));
+    CK_CUDA(cudaMemcpyAsync(sb, b_host + (size_t)i0 * in_w, sizeof(u64) * cnt * in_w, cudaMemcpyHostToDevice,
+                            c->h2d));
+    CK_CUDA(cudaEventRecord(c->ev_in[s], c->h2d));
+    // the products on the context stream
+    CK_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in[s], 0));
+    std::vector<ckks_ct> ha(cnt), hb(cnt), ho(cnt);
+    for (int i = 0; i < cnt; ++i) {
+      const uint32_t ln = (uint32_t)c->log_n;
+      ha[i] = ckks_ct{sa + (size_t)i * in_w, ln, level, level + 1, 1, scale_a};
+      hb[i] = ckks_ct{sb + (size_t)i * in_w, ln, level, level + 1, 1, scale_b};
+      ho[i] = ckks_ct{so + (size_t)i * in_w, ln, level, level + 1, 1, 1.0};
+    }
+    int rc = ckks_mul_relin_batch(c, ha.data(), hb.data(), ho.data(), cnt, do_rescale);
+    if (rc) return rc;
+    sc = ho[0].scale;
+    CK_CUDA(cudaEventRecord(c->ev_comp[s], c->stream));
+    // the products back: the active limbs of both polynomials, contiguous per pair
+    CK_CUDA(cudaStreamWaitEvent(c->d2h, c->ev_comp[s], 0));
+    const size_t half = out_w / 2;
+    for (int i = 0; i < cnt; ++i) {
+      u64 *dst = out_host + (size_t)(i0 + i) * out_w;
+      CK_CUDA(cudaMemcpyAsync(dst, ho[i].data, sizeof(u64) * half, cudaMemcpyDeviceToHost, c->d2h));
+      CK_CUDA(cudaMemcpyAsync(dst + half, ho[i].data + (size_t)(level + 1) * nn, sizeof(u64) * half,
+                              cudaMemcpyDeviceToHost, c->d2h));
+    }
+    CK_CUDA(cudaEventRecord(c->ev_out[s], c->d2h));
+  }
+  CK_CUDA(cudaStreamSynchronize(c->d2h));
+  if (out_scale) *out_scale = sc;
+  return last_err();
 }
 
 int ckks_ct_export(ckks_ctx *c, const ckks_ct *ct, uint64_t *out) {

@@ -86,6 +86,12 @@ struct ckks_ctx {
   bool use_tc = false;               // basis conversion on the tensor cores (ckks_ctx_set_form)
   std::map<size_t, void *> tc_bmats; // byte-plane constants per conversion
   int *tc_err = nullptr;             // device flag: a bounded wait expired
+  // host-streamed batches (ckks_mul_relin_host): copy streams, staging slots, events
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  u64 *stage = nullptr;
+  size_t stage_words = 0;
+  cudaEvent_t ev_in[3] = {nullptr, nullptr, nullptr}, ev_comp[3] = {nullptr, nullptr, nullptr},
+              ev_out[3] = {nullptr, nullptr, nullptr};
   bool capturing = false;            // inside a CUDA-graph capture: no allocation, no sync
 
   size_t limb_words() const { return (size_t)n; }
