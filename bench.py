@@ -296,6 +296,10 @@ def run_gpu(args):
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
+    # autotuning, untimed: key inner-product group and NTT row tile per context
+    tuning = {"ip_group": ctx.tune(level, B), "ntt_rows": ctx.tune_ntt(16),
+              "boot_ip_group": bctx.tune(len(wb.q_bits) - 1, nb), "boot_ntt_rows": bctx.tune_ntt(16)}
+
     def step(marks=None):
         if marks:
             marks[0].record(stream)
@@ -418,6 +422,12 @@ def run_gpu(args):
     if not (args.no_e2e or args.small):
         e2e = run_e2e(ctx, torch, A, Bc, OUT, level, args, dist)
 
+    # the gadget size for this prime chain (informational; the workload keeps dnum = 3)
+    if not args.small:
+        best_d, ms_d = ck.tune_dnum(w, cands=(2, 3, 4, 6), batch=8)
+        tuning["dnum_best"] = best_d
+        tuning["dnum_ms_per_hmult"] = {d: (round(v, 4) if v != float("inf") else None) for d, v in ms_d.items()}
+
     cpu = None
     if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.small):
         sample = OracleSample(w)
@@ -439,7 +449,7 @@ def run_gpu(args):
                                      "batch": nb, "levels_consumed": 16, "cheb_degree": 60,
                                      "double_angles": 3, "input": "fresh encryptions at level 0"},
                 "slot_error": errors, "forms": forms,
-                "reboot_step": reboot, "uneven_batch": uneven,
+                "reboot_step": reboot, "uneven_batch": uneven, "tuning": tuning,
                 "e2e": e2e, "roofline": roof, "alu_peaks": alu, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": int(launches),
                 "kernel_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]},

@@ -350,6 +350,24 @@ int ckks_graph_destroy(ckks_graph *graph);
  * groups of 2..32 on a batch of `batch` key switches at `level` and keep the
  * fastest for later calls; *chosen (may be NULL) receives it. */
 int ckks_tune(ckks_ctx *ctx, int level, int batch, int *chosen);
+/* Autotune the NTT's row pass for this context: time forward + inverse
+ * transforms of n_polys (1..64) polynomials over all ciphertext primes with
+ * 16 and 8 rows per CTA and keep the faster; *rows (may be NULL) receives it.
+ * Needs the relinearisation key (its limbs are the timing input);
+ * CKKS_E_STATE during graph capture. */
+int ckks_tune_ntt(ckks_ctx *ctx, int n_polys, int *rows);
+/* Set the NTT row-pass tile directly: 16 or 8 rows per CTA (else CKKS_E_PARAM). */
+int ckks_ctx_set_ntt_rows(ckks_ctx *ctx, int rows);
+/* Autotune the gadget (reading C7) of a parameter set: for each candidate
+ * dnum a context with alpha = ceil(n_q / dnum) special primes of p_bits[0]
+ * bits (P spans one digit) is created on cuda_stream, its relinearisation key
+ * generated from `seed`, and a batch of `batch` (1..128) HMult+relin with the
+ * merged rescale timed at the top level, then destroyed.  *best receives the
+ * fastest dnum; ms_per_op[i] (may be NULL) each candidate's milliseconds per
+ * product (HUGE_VAL where it does not fit: alpha + 1 > 16 sources).  Allocates
+ * and frees device memory; CKKS_E_PARAM when no candidate fits. */
+int ckks_tune_dnum(const ckks_params *params, void *cuda_stream, const uint32_t *cands, int n_cands, int batch,
+                   uint64_t seed, uint32_t *best, double *ms_per_op);
 
 /* ---- checkpoint helpers ------------------------------------------------- */
 

@@ -113,6 +113,10 @@ SIGNATURES = {
     "ckks_graph_launch": (_I, [_V, _V]),
     "ckks_graph_destroy": (_I, [_V]),
     "ckks_tune": (_I, [_V, _I, _I, ctypes.POINTER(_I)]),
+    "ckks_tune_ntt": (_I, [_V, _I, ctypes.POINTER(ctypes.c_int)]),
+    "ckks_ctx_set_ntt_rows": (_I, [_V, _I]),
+    "ckks_tune_dnum": (_I, [_V, _V, ctypes.POINTER(ctypes.c_uint32), _I, _I, ctypes.c_uint64,
+                            ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_double)]),
     "ckks_ct_export": (_I, [_V, _CTP, _V]),
     "ckks_ct_import": (_I, [_V, _V, _CTP]),
     "ckks_status_str": (ctypes.c_char_p, [_I]),
@@ -254,6 +258,15 @@ class Context:
 
     def device_error(self) -> int:
         return self.lib.ckks_ctx_device_error(self._h)
+
+    def set_ntt_rows(self, rows: int) -> None:
+        _check(self.lib.ckks_ctx_set_ntt_rows(self._h, rows), "ckks_ctx_set_ntt_rows")
+
+    def tune_ntt(self, n_polys: int = 16) -> int:
+        """Autotune the NTT row pass (rows per CTA); returns the choice."""
+        r = ctypes.c_int()
+        _check(self.lib.ckks_tune_ntt(self._h, n_polys, ctypes.byref(r)), "ckks_tune_ntt")
+        return r.value
 
     def tune(self, level: int, batch: int) -> int:
         """Autotune the key inner product for batches of this shape; returns the choice."""
@@ -567,6 +580,27 @@ class Context:
         h = ct.handle(self.log_n)
         _check(self.lib.ckks_ct_import(self._h, arr.ctypes.data, ctypes.byref(h)), "ckks_ct_import")
         return ct
+
+
+def tune_dnum(w, cands=(2, 3, 4, 6), batch: int = 16, seed: int = 1, stream=None):
+    """Autotune dnum for a workload's prime chain (ckks_tune_dnum): returns
+    (best dnum, {dnum: ms per HMult+relin+rescale, inf where it does not fit})."""
+    torch = _torch()
+    lib = load_library()
+    p = CkksParams()
+    p.log_n, p.n_q, p.n_p, p.dnum, p.h = w.log_n, len(w.q_bits), len(w.p_bits), w.dnum, w.h
+    for i, b in enumerate(w.q_bits):
+        p.q_bits[i] = b
+    for i, b in enumerate(w.p_bits):
+        p.p_bits[i] = b
+    p.log2_scale, p.sigma = w.log2_scale, w.sigma
+    st = stream if stream is not None else torch.cuda.current_stream()
+    cs = (ctypes.c_uint32 * len(cands))(*cands)
+    ms = (ctypes.c_double * len(cands))()
+    best = ctypes.c_uint32()
+    _check(lib.ckks_tune_dnum(ctypes.byref(p), ctypes.c_void_p(st.cuda_stream), cs, len(cands), batch, seed,
+                              ctypes.byref(best), ms), "ckks_tune_dnum")
+    return best.value, {int(d): float(ms[i]) for i, d in enumerate(cands)}
 
 
 class Op:

@@ -83,6 +83,7 @@ struct ckks_ctx {
   size_t table_bytes = 0;
   Profiler prof;
   int ip_group = 8;                  // key inner product: outputs per thread (ckks_tune)
+  int ntt_rows = 16;                 // NTT row pass: rows per CTA, 16 or 8 (ckks_tune_ntt)
   bool use_tc = false;               // basis conversion on the tensor cores (ckks_ctx_set_form)
   std::map<size_t, void *> tc_bmats; // byte-plane constants per conversion
   int *tc_err = nullptr;             // device flag: a bounded wait expired

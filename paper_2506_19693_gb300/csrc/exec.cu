@@ -10,6 +10,8 @@
 #include <tuple>
 #include <vector>
 
+#include <cmath>
+
 #include "ops.cuh"
 
 struct ckks_graph {
@@ -217,6 +219,131 @@ int ckks_tune(ckks_ctx *c, int level, int batch, int *chosen) {
   cudaFree(outs);
   c->ip_group = best_g;
   if (chosen) *chosen = best_g;
+  return rc;
+}
+
+int ckks_tune_dnum(const ckks_params *p, void *cuda_stream, const uint32_t *cands, int n_cands, int batch,
+                   uint64_t seed, uint32_t *best, double *ms_per_op) {
+  if (!p || !cands || n_cands < 1 || batch < 1 || batch > MAX_CTS || p->n_q < 2 || p->n_p < 1) return CKKS_E_PARAM;
+  double best_ms = 1e300;
+  uint32_t best_d = 0;
+  for (int i = 0; i < n_cands; ++i) {
+    if (ms_per_op) ms_per_op[i] = HUGE_VAL;
+    const uint32_t d = cands[i];
+    if (d < 1 || d > p->n_q) continue;
+    const uint32_t alpha = (p->n_q + d - 1) / d;
+    if (alpha + 1 > 16 || alpha > CKKS_MAX_P) continue;  // basis conversions of up to 16 sources
+    ckks_params q = *p;
+    q.dnum = d;
+    q.n_p = alpha;  // P spans one digit
+    for (uint32_t k = 0; k < alpha; ++k) q.p_bits[k] = p->p_bits[0];
+    ckks_ctx *c = nullptr;
+    int rc = ckks_ctx_create(&q, cuda_stream, &c);
+    if (!rc) rc = ckks_keygen_from_seed(c, seed, nullptr, 0, 0, 0);
+    double ms = HUGE_VAL;
+    if (!rc) {
+      // inputs: the relinearisation key's limbs are valid residues at every level
+      const int level = (int)q.n_q - 1;
+      const size_t w = (size_t)(level + 1) * c->n;
+      std::vector<ckks_ct> a(batch), o(batch);
+      u64 *outs = nullptr;
+      if (cudaMalloc(&outs, sizeof(u64) * 2 * w * batch) != cudaSuccess) {
+        cudaGetLastError();
+        rc = CKKS_E_OOM;
+      }
+      for (int j = 0; j < batch && !rc; ++j) {
+        a[j] = ckks_ct{c->relin.data, (uint32_t)c->log_n, (uint32_t)level, (uint32_t)(level + 1), 1, 1.0};
+        o[j] = ckks_ct{outs + 2 * w * j, (uint32_t)c->log_n, (uint32_t)level, (uint32_t)(level + 1), 1, 1.0};
+      }
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      float tot = 0.f;
+      for (int rep = 0; rep < 3 && !rc; ++rep) {
+        cudaEventRecord(e0, c->stream);
+        rc = ckks_mul_relin_batch(c, a.data(), a.data(), o.data(), batch, CKKS_RESCALE_MERGED);
+        cudaEventRecord(e1, c->stream);
+        cudaEventSynchronize(e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (rep) tot += t;  // first run warms up
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      cudaFree(outs);
+      if (!rc) ms = tot / 2 / batch;
+    }
+    if (c) ckks_ctx_destroy(c);
+    if (rc == CKKS_E_OOM) return rc;
+    if (rc) continue;
+    if (ms_per_op) ms_per_op[i] = ms;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best_d = d;
+    }
+  }
+  if (!best_d) return CKKS_E_PARAM;
+  if (best) *best = best_d;
+  return CKKS_OK;
+}
+
+int ckks_ctx_set_ntt_rows(ckks_ctx *c, int rows) {
+  if (!c || (rows != 8 && rows != 16)) return CKKS_E_PARAM;
+  c->ntt_rows = rows;
+  return CKKS_OK;
+}
+
+int ckks_tune_ntt(ckks_ctx *c, int n_polys, int *rows) {
+  if (!c || n_polys < 1 || n_polys > 64) return CKKS_E_PARAM;
+  if (c->capturing) return CKKS_E_STATE;
+  if (!c->relin.data) return CKKS_E_NOKEY;
+  const u32 n = c->n;
+  const int nl = c->n_q;
+  // inputs: the relinearisation key's limbs are valid residues of q_0..q_{n_q-1}
+  u64 *outs = nullptr;
+  if (cudaMalloc(&outs, sizeof(u64) * (size_t)nl * n * n_polys) != cudaSuccess) {
+    cudaGetLastError();
+    return CKKS_E_OOM;
+  }
+  std::vector<const u64 *> src(n_polys);
+  std::vector<u64 *> dst(n_polys);
+  std::vector<const u64 *> dstc(n_polys);
+  int mods[MAX_MODS];
+  for (int t = 0; t < nl; ++t) mods[t] = t;
+  for (int i = 0; i < n_polys; ++i) {
+    src[i] = c->relin.data;
+    dst[i] = outs + (size_t)nl * n * i;
+    dstc[i] = dst[i];
+  }
+  const int cands[] = {16, 8};
+  float best = 1e30f;
+  int best_r = c->ntt_rows, rc = CKKS_OK;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int cand : cands) {
+    c->ntt_rows = cand;
+    float tot = 0.f;
+    for (int rep = 0; rep < 3 && !rc; ++rep) {
+      cudaEventRecord(e0, c->stream);
+      rc = launch_ntt(c, src.data(), dst.data(), n_polys, nl, mods, false);
+      if (!rc) rc = launch_ntt(c, dstc.data(), dst.data(), n_polys, nl, mods, true);
+      cudaEventRecord(e1, c->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep) tot += ms;  // first run warms up
+    }
+    if (!rc && tot < best) {
+      best = tot;
+      best_r = cand;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(outs);
+  c->ntt_rows = best_r;
+  if (rows) *rows = best_r;
   return rc;
 }
 

@@ -25,8 +25,10 @@ namespace {
 constexpr int LB = 8;            // log2 of the row length handled by pass B
 constexpr int BROW = 1 << LB;    // 256
 constexpr int CA = 16;           // columns per pass-A tile
-constexpr int RB = 16;           // rows per pass-B tile
-constexpr int THREADS = 256;
+constexpr int THREADS = 256;     // pass A; pass B runs 16 threads per row of its tile
+// pass B tiles: RBT rows per CTA (16 or 8, chosen per context by ckks_tune_ntt)
+template <int RBT>
+__host__ __device__ constexpr int threads_b() { return RBT * 16; }
 
 struct NttParams {
   const ModInfo *mods;
@@ -131,9 +133,9 @@ __global__ void __launch_bounds__(THREADS, 3) fwd_pass_a(const NttParams prm) {
     fwd_a_body<LH, S1, false>(prm, sm, mi, src, dst);
 }
 
-template <int LH, bool LOOSE>
+template <int LH, bool LOOSE, int RB>
 __device__ __forceinline__ void fwd_b_body(const NttParams &prm, u64 *sm, int mi, const u64 *src, u64 *dst) {
-  constexpr int H = 1 << LH, U1 = 4, U2 = LB - U1;
+  constexpr int H = 1 << LH, U1 = 4, U2 = LB - U1, THREADS = threads_b<RB>();
   const u64 q = prm.mods[mi].q, twoq = 2 * q;
   const ulonglong2 *tw = prm.tw + (size_t)mi * prm.n;
   const int row0 = blockIdx.x * RB;
@@ -175,23 +177,23 @@ __device__ __forceinline__ void fwd_b_body(const NttParams &prm, u64 *sm, int mi
   }
 }
 
-template <int LH>
-__global__ void __launch_bounds__(THREADS, 3) fwd_pass_b(const NttParams prm, int from_src) {
+template <int LH, int RB>
+__global__ void __launch_bounds__(threads_b<RB>(), RB == 16 ? 3 : 6) fwd_pass_b(const NttParams prm, int from_src) {
   __shared__ u64 sm[RB * BROW + (RB * BROW >> 4)];
   const int limb = blockIdx.y, poly = blockIdx.z;
   const int mi = prm.mod_of_limb[limb];
   const u64 *src = (from_src ? prm.src.p[poly] : prm.dst.p[poly]) + (size_t)limb * prm.n;
   u64 *dst = prm.dst.p[poly] + (size_t)limb * prm.n;
   if (prm.mods[mi].q < LOOSE_BOUND)
-    fwd_b_body<LH, true>(prm, sm, mi, src, dst);
+    fwd_b_body<LH, true, RB>(prm, sm, mi, src, dst);
   else
-    fwd_b_body<LH, false>(prm, sm, mi, src, dst);
+    fwd_b_body<LH, false, RB>(prm, sm, mi, src, dst);
 }
 
 // ---------------------------------------------------------------- inverse
-template <int LH>
-__global__ void __launch_bounds__(THREADS, 4) inv_pass_b(const NttParams prm) {
-  constexpr int H = 1 << LH, U1 = 4, U2 = LB - U1;
+template <int LH, int RB>
+__global__ void __launch_bounds__(threads_b<RB>(), RB == 16 ? 4 : 8) inv_pass_b(const NttParams prm) {
+  constexpr int H = 1 << LH, U1 = 4, U2 = LB - U1, THREADS = threads_b<RB>();
   __shared__ u64 sm[RB * BROW + (RB * BROW >> 4)];
   const int limb = blockIdx.y, poly = blockIdx.z;
   const int mi = prm.mod_of_limb[limb];
@@ -281,13 +283,25 @@ void launch_lh(ckks_ctx *c, const NttParams &prm, int npoly, bool inverse) {
   const int H = 1 << LH;
   cudaStream_t st = c->stream;
   const unsigned long long units = (unsigned long long)prm.n_limbs * npoly;
-  dim3 ga(BROW / CA, prm.n_limbs, npoly), gb(H / RB, prm.n_limbs, npoly);
-  if (!inverse) {
-    PROF_LAUNCH(c, PK_NTT_FWD_A, units, (fwd_pass_a<LH, S1><<<ga, THREADS, 0, st>>>(prm)));
-    PROF_LAUNCH(c, PK_NTT_FWD_B, units, (fwd_pass_b<LH><<<gb, THREADS, 0, st>>>(prm, 0)));
+  dim3 ga(BROW / CA, prm.n_limbs, npoly);
+  if (c->ntt_rows == 8) {
+    dim3 gb(H / 8, prm.n_limbs, npoly);
+    if (!inverse) {
+      PROF_LAUNCH(c, PK_NTT_FWD_A, units, (fwd_pass_a<LH, S1><<<ga, THREADS, 0, st>>>(prm)));
+      PROF_LAUNCH(c, PK_NTT_FWD_B, units, (fwd_pass_b<LH, 8><<<gb, threads_b<8>(), 0, st>>>(prm, 0)));
+    } else {
+      PROF_LAUNCH(c, PK_NTT_INV_B, units, (inv_pass_b<LH, 8><<<gb, threads_b<8>(), 0, st>>>(prm)));
+      PROF_LAUNCH(c, PK_NTT_INV_A, units, (inv_pass_a<LH, S1><<<ga, THREADS, 0, st>>>(prm)));
+    }
   } else {
-    PROF_LAUNCH(c, PK_NTT_INV_B, units, (inv_pass_b<LH><<<gb, THREADS, 0, st>>>(prm)));
-    PROF_LAUNCH(c, PK_NTT_INV_A, units, (inv_pass_a<LH, S1><<<ga, THREADS, 0, st>>>(prm)));
+    dim3 gb(H / 16, prm.n_limbs, npoly);
+    if (!inverse) {
+      PROF_LAUNCH(c, PK_NTT_FWD_A, units, (fwd_pass_a<LH, S1><<<ga, THREADS, 0, st>>>(prm)));
+      PROF_LAUNCH(c, PK_NTT_FWD_B, units, (fwd_pass_b<LH, 16><<<gb, threads_b<16>(), 0, st>>>(prm, 0)));
+    } else {
+      PROF_LAUNCH(c, PK_NTT_INV_B, units, (inv_pass_b<LH, 16><<<gb, threads_b<16>(), 0, st>>>(prm)));
+      PROF_LAUNCH(c, PK_NTT_INV_A, units, (inv_pass_a<LH, S1><<<ga, THREADS, 0, st>>>(prm)));
+    }
   }
 }
 

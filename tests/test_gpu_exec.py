@@ -99,3 +99,43 @@ def test_executor_rejects_aliasing_and_bad_ops():
     finally:
         for _, c in ctxs:
             c.close()
+
+
+def test_ntt_row_tiles_agree_and_tuner_picks_one():
+    """Both NTT row-pass tiles (16 and 8 rows per CTA) give the same limbs; the
+    tuner keeps one of them."""
+    import torch
+    import paper_2506_19693_gb300 as ck
+    torch.cuda.set_device(0)
+    w = si.MID
+    ctx = ck.Context.from_workload(w)
+    try:
+        ctx.keygen(2)
+        level = len(w.q_bits) - 1
+        scale = 2.0 ** w.log2_scale
+        z = si.messages(70, 4, w.slots)
+        cts = [ctx.encrypt(ctx.encode(z[i], level, scale), level, scale, 70 + i) for i in range(4)]
+        outs = {}
+        for rows in (16, 8):
+            ctx.set_ntt_rows(rows)
+            out = [ctx.new_ct(level + 1) for _ in range(2)]
+            ctx.mul_relin_batch(cts[:2], cts[2:], out, rescale=ck.RESCALE_MERGED)
+            outs[rows] = [ctx.export_ct(o) for o in out]
+        for x, y in zip(outs[16], outs[8]):
+            assert np.array_equal(x, y)
+        assert ctx.tune_ntt(8) in (8, 16)
+    finally:
+        ctx.close()
+
+
+def test_dnum_tuner_times_every_fitting_candidate():
+    import math
+    import torch
+    import paper_2506_19693_gb300 as ck
+    torch.cuda.set_device(0)
+    best, ms = ck.tune_dnum(si.SMALL, cands=(1, 2, 3), batch=4)
+    # n_q = 6: dnum 1 -> alpha 6, 2 -> 3, 3 -> 2 special primes; all fit 16 sources
+    assert best in (1, 2, 3)
+    assert all(math.isfinite(v) and v > 0 for v in ms.values())
+    best, ms = ck.tune_dnum(si.PLAIN, cands=(1, 3), batch=2)
+    assert best == 3 and math.isinf(ms[1])  # alpha 24 does not fit a 16-source conversion
