@@ -185,14 +185,15 @@ def kernel_work(name, units, launches, w, ndig):
         alu = ("bfly", units * (n // 2) * lh)
     elif name in ("ntt_fwd_pass_b", "ntt_inv_pass_b"):
         alu = ("bfly", units * (n // 2) * 8)
-    elif name == "bconv":
+    elif name in ("bconv", "bconv_tc"):
+        # the conversion's modular MACs, whichever unit computes them (bconv_tc:
+        # against the CUDA-core MAC roof, as work-equivalent; tensor work below)
         alu = ("mac", units * n)
-    elif name == "bconv_tc":
-        alu = ("tensor", units * n * 64 * 2)
     elif name == "ks_inner_product":
         alu = ("mac", units * 2 * ndig * n)
     hbm = hbm_words * 8 * n * units if hbm_words is not None else None
-    return hbm, alu
+    tensor = units * n * 64 * 2 if name == "bconv_tc" else None
+    return hbm, alu, tensor
 
 
 def roofline(prof, w, ndig, hbm_peak, hbm_kind, alu_peaks, tensor_peak=None, name=None):
@@ -205,25 +206,30 @@ def roofline(prof, w, ndig, hbm_peak, hbm_kind, alu_peaks, tensor_peak=None, nam
     if not nlaunch:
         return None
     sec = ms / 1e3
-    hbm, alu = kernel_work(name, units, nlaunch, w, ndig)
+    hbm, alu, tensor = kernel_work(name, units, nlaunch, w, ndig)
     cands = []
     if hbm is not None:
         a = hbm / nlaunch / (sec / nlaunch) / 1e9
         cands.append({"bound": "hbm", "achieved": a, "peak": hbm_peak, "unit": "GB/s", "frac": a / hbm_peak,
                       "peak_source": f"{hbm_kind} hbm_gbs", "algorithmic_per_launch": hbm / nlaunch})
-    if alu is not None and alu[0] == "tensor" and tensor_peak:
-        a = alu[1] / sec / 1e12
+    if tensor is not None and tensor_peak:
+        a = tensor / sec / 1e12
         cands.append({"bound": "tensor", "achieved": a, "peak": tensor_peak, "unit": "TFLOP/s",
                       "frac": a / tensor_peak, "peak_source": f"{hbm_kind} bf16_tflops_sustained (fp16 = bf16 rate)",
-                      "algorithmic_per_launch": alu[1] / nlaunch})
-    elif alu is not None and alu_peaks:
+                      "algorithmic_per_launch": tensor / nlaunch})
+    if alu is not None and alu_peaks:
         kind, ops = alu
         pk = alu_peaks["mac_per_s"] if kind == "mac" else alu_peaks["bfly_per_s"]
         a = ops / sec
-        cands.append({"bound": "alu", "achieved": a / 1e12, "peak": pk / 1e12,
-                      "unit": "T 64x64->128 MAC/s" if kind == "mac" else "T Shoup butterflies/s",
-                      "frac": a / pk, "peak_source": "measured on this GPU by ckks_alu_peaks (register-only "
-                      "kernel of the same primitive)", "algorithmic_per_launch": ops / nlaunch})
+        c = {"bound": "alu", "achieved": a / 1e12, "peak": pk / 1e12,
+             "unit": "T 64x64->128 MAC/s" if kind == "mac" else "T Shoup butterflies/s",
+             "frac": a / pk, "peak_source": "measured on this GPU by ckks_alu_peaks (register-only "
+             "kernel of the same primitive)", "algorithmic_per_launch": ops / nlaunch}
+        if name == "bconv_tc":  # the same conversion work, done as byte-split MMAs + CUDA-core recombination
+            c["unit"] = "T modular MAC/s (work-equivalent)"
+            c["peak_source"] = ("the CUDA-core 64x64->128 MAC rate measured by ckks_alu_peaks, the roof of the "
+                                "uint64 form of the same conversion")
+        cands.append(c)
     if not cands:
         return None
     best = max(cands, key=lambda c: c["frac"])

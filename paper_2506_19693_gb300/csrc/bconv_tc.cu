@@ -109,7 +109,9 @@ __device__ __forceinline__ u64 mul_lo_32x64(u32 s, u64 w) {
 struct TcTarget {
   u64 q, one_s;    // t, floor(2^64 / t)
   u64 r64, r64_s;  // 2^64 mod t and its Shoup companion
+  u64 w96_s;       // floor(2^96 / t): Shoup companion of 2^32 (t > 2^32)
   u64 sub;         // subtracted from the result mod t when TcArgs::has_sub
+  int wide;        // t > 2^48: the low half L < 2^47.01 is already reduced
 };
 
 // y_t = sum_b 2^(8b) v_b mod t from the 8 fp32 accumulators of one target.
@@ -128,6 +130,38 @@ __device__ __forceinline__ u64 recombine(const u32 *v, const TcTarget &tg) {
   const u64 qt = mad_wide(y_hi, (u32)(tg.r64_s >> 32), (u64)__umulhi(y_hi, (u32)tg.r64_s)) >> 32;
   const u64 r_hi = mul_lo_32x64(y_hi, tg.r64) - mul_lo_32x64((u32)qt, tg.q);
   return csub(csub(r_lo + r_hi, tg.q << 1), tg.q);
+}
+
+// The same for t > 2^48, where L < 2^47.01 < t is already a residue:
+// y = L + (H 2^32 mod t), the latter one Shoup product with w = 2^32.
+__device__ __forceinline__ u64 recombine_wide(const u32 *v, const TcTarget &tg) {
+  const u32 c0 = acc_int(v[0]), c1 = acc_int(v[1]), c2 = acc_int(v[2]), c3 = acc_int(v[3]);
+  const u32 c4 = acc_int(v[4]), c5 = acc_int(v[5]), c6 = acc_int(v[6]), c7 = acc_int(v[7]);
+  const u64 L = mad_wide(c3, 1u << 24, mad_wide(c2, 1u << 16, (u64)(c0 + (c1 << 8))));
+  const u64 H = mad_wide(c7, 1u << 24, mad_wide(c6, 1u << 16, (u64)(c4 + (c5 << 8))));
+  const u64 r = (H << 32) - __umul64hi(H, tg.w96_s) * tg.q;  // [0, 2t)
+  return csub(csub(r + L, tg.q << 1), tg.q);
+}
+
+__device__ __forceinline__ u64 recombine_target(const u32 *v, const TcTarget &tg, int has_sub) {
+  u64 r = tg.wide ? recombine_wide(v, tg) : recombine(v, tg);
+  if (has_sub) r = submod(r, tg.sub, tg.q);
+  return r;
+}
+
+// Two adjacent targets' 16 accumulators of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld16(u32 (&v)[16], u32 addr) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+      "%14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(addr));
+}
+__device__ __forceinline__ void tmem_ld8(u32 *v, u32 addr) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(addr));
 }
 
 constexpr int TC_SRC_GROUPS = TC_THREADS / TC_M;        // threads sharing one A row
@@ -282,31 +316,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_bconv_tc(const TcArgs a) {
     u64 *dst = a.dst[tile / tiles_per_poly];
     const u32 kc = (u32)(tile % tiles_per_poly) * TC_M + (u32)(lq * 32 + lane);
     const u32 tbase = tmem + ((u32)(lq * 32) << 16) + (u32)(cur * TC_ACC_COLS);
-    for (int t = t_lo; t < t_hi; t += 2) {
-      u32 v[16];
-      const bool two = t + 1 < t_hi;
-      if (two) {
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-            "%14, %15}, [%16];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(tbase + (u32)(t * 8)));
-      } else {
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-            : "r"(tbase + (u32)(t * 8)));
-      }
+    // four targets per wait where possible, then a pair, then a single one
+    int t = t_lo;
+    for (; t + 4 <= t_hi; t += 4) {
+      u32 v[16], u[16];
+      tmem_ld16(v, tbase + (u32)(t * 8));
+      tmem_ld16(u, tbase + (u32)((t + 2) * 8));
       asm volatile("tcgen05.wait::ld.sync.aligned;");
-      u64 r0 = recombine(v, a.tg[t]);
-      if (a.has_sub) r0 = submod(r0, a.tg[t].sub, a.tg[t].q);
-      dst[(size_t)a.dst_pos[t] * a.n + kc] = r0;
-      if (two) {
-        u64 r1 = recombine(v + 8, a.tg[t + 1]);
-        if (a.has_sub) r1 = submod(r1, a.tg[t + 1].sub, a.tg[t + 1].q);
-        dst[(size_t)a.dst_pos[t + 1] * a.n + kc] = r1;
-      }
+      dst[(size_t)a.dst_pos[t] * a.n + kc] = recombine_target(v, a.tg[t], a.has_sub);
+      dst[(size_t)a.dst_pos[t + 1] * a.n + kc] = recombine_target(v + 8, a.tg[t + 1], a.has_sub);
+      dst[(size_t)a.dst_pos[t + 2] * a.n + kc] = recombine_target(u, a.tg[t + 2], a.has_sub);
+      dst[(size_t)a.dst_pos[t + 3] * a.n + kc] = recombine_target(u + 8, a.tg[t + 3], a.has_sub);
+    }
+    if (t + 2 <= t_hi) {
+      u32 v[16];
+      tmem_ld16(v, tbase + (u32)(t * 8));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      dst[(size_t)a.dst_pos[t] * a.n + kc] = recombine_target(v, a.tg[t], a.has_sub);
+      dst[(size_t)a.dst_pos[t + 1] * a.n + kc] = recombine_target(v + 8, a.tg[t + 1], a.has_sub);
+      t += 2;
+    }
+    if (t < t_hi) {
+      u32 v[8];
+      tmem_ld8(v, tbase + (u32)(t * 8));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      dst[(size_t)a.dst_pos[t] * a.n + kc] = recombine_target(v, a.tg[t], a.has_sub);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
   }
@@ -381,6 +415,8 @@ int launch_bconv_tc(ckks_ctx *c, size_t key, const u64 *inv_host, const u64 *tab
     g.one_s = (u64)(two64 / m);
     g.r64 = (u64)(two64 % m);
     g.r64_s = (u64)(((unsigned __int128)g.r64 << 64) / m);
+    g.w96_s = (u64)(((unsigned __int128)1 << 96) / m);  // < 2^64 since t > 2^32
+    g.wide = m > (1ULL << 48) ? 1 : 0;
     g.sub = dst_sub_host ? dst_sub_host[t] : 0;
     a.dst_pos[t] = (unsigned char)dst_pos[t];
   }
