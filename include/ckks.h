@@ -265,11 +265,12 @@ int ckks_bootstrap_batch(ckks_ctx *ctx, const ckks_ct *in, ckks_ct *out, int n);
 #define CKKS_RESCALE_MERGED 2   /* ModDown and rescale merged (no paper counterpart; an
                                  * implementation choice the paper leaves open, reading C21):
                                  * the key-switch accumulator plus P (d0, d1) is divided by
-                                 * P q_l in one uncentred fast basis conversion from
-                                 * {q_l, p_0..p_{K-1}} to q_0..q_{l-1}, rounding to nearest:
-                                 * out = round(x / (P q_l)) - u, 0 <= u <= K per coefficient.
-                                 * Saves the ModDown NTT of q_l's digit limbs and the rescale's
-                                 * own transforms; limbs differ from SEPARATE by at most K + 2. */
+                                 * P q_l in one fast basis conversion from {q_l, p_0..p_{K-1}}
+                                 * to q_0..q_{l-1} whose overflow is estimated in fixed point
+                                 * and removed, rounding to nearest: out = round(x / (P q_l))
+                                 * + e, e in {0, 1} and almost always 0.  Saves ModDown's NTT
+                                 * of 2(l+1) limbs and the rescale's own transforms; limbs
+                                 * differ from SEPARATE by at most 2 per coefficient. */
 
 /* out[i] = mul_relin(a[i], b[i]), rescaled per do_rescale (CKKS_RESCALE_*;
  * another value: CKKS_E_PARAM; a rescale at level 0: CKKS_E_LEVEL).

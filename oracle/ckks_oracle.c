@@ -870,15 +870,19 @@ int oc_rescale(const oc_ctx *c, const u64 *in, int level, u64 *out) {
 }
 
 /* C21: ModDown and rescale merged.  x (NTT domain, [ext][N] over q_0..q_l,
- * p_0..p_{K-1}) is divided by S = P q_l, rounding to nearest, in one uncentred
- * fast basis conversion from the basis {q_l, p_0, .., p_{K-1}} to q_0..q_{l-1}.
- * With H = (S - 1)/2 (S is odd):
+ * p_0..p_{K-1}) is divided by S = P q_l, rounding to nearest, in one fast
+ * basis conversion from the basis {q_l, p_0, .., p_{K-1}} to q_0..q_{l-1}
+ * whose overflow is estimated and removed.  With H = (S - 1)/2 (S is odd):
  *   x'_i = x_i + [H]_{s_i} on the sources ([H]_{s_i} = (s_i - 1)/2),
- *   z_t  = BConv(x')_t - [H]_{q_t},
+ *   y_i  = [x'_i Shat_i^-1]_{s_i},  sum_i y_i Shat_i = [X + H]_S + u S with
+ *          u = floor(sum_i y_i / s_i) in [0, K],
+ *   v    = floor(sum_i T_i / 2^32), T_i = floor(y_i R_i / 2^64),
+ *          R_i = floor(2^96 / s_i): y_i / s_i in 32.32 fixed point, so
+ *          v = u, or u - 1 when the sum lies within 2^-28 of an integer,
+ *   z_t  = sum_i y_i (Shat_i mod q_t) - v S - [H]_{q_t}  (mod q_t),
  *   out_t = (x_t - z_t) * S^-1 mod q_t,
- * and over the integers x_t - z_t = X + H - [X + H]_S - u S, so
- * out = floor((X + H) / S) - u = round(X / S) - u with 0 <= u <= K
- * (X the representative in [0, Q_l P), u the conversion's overflow).
+ * and over the integers out = floor((X + H) / S) + (u - v) = round(X / S) + e,
+ * e = u - v in {0, 1}, almost always 0 (X the representative in [0, Q_l P)).
  * out: [level][N], NTT domain. */
 int oc_moddown_rescale(const oc_ctx *c, const u64 *x, int level, u64 *out) {
   if (level < 1) return -1;
@@ -899,12 +903,30 @@ int oc_moddown_rescale(const oc_ctx *c, const u64 *x, int level, u64 *out) {
   }
   u64 *z = (u64 *)malloc(sizeof(u64) * (u64)level * n);
   oc_bconv(c, xs, ns, src, z, level, dst);
+  /* the overflow estimate v per coefficient, from y_i in 32.32 fixed point */
+  u64 *v = (u64 *)calloc(n, sizeof(u64));
+  for (int i = 0; i < ns; i++) {
+    u64 si = c->mod[src[i]], shat = 1;
+    for (int k = 0; k < ns; k++)
+      if (k != i) shat = mulmod(shat, c->mod[src[k]] % si, si);
+    u64 sinv = invmod(shat, si);
+    u64 r = (u64)((((u128)1) << 96) / si);
+    for (u64 k = 0; k < n; k++) {
+      u64 y = mulmod(xs[(u64)i * n + k], sinv, si);
+      v[k] += (u64)(((u128)y * r) >> 64);
+    }
+  }
+  for (u64 k = 0; k < n; k++) v[k] >>= 32;
   for (int t = 0; t < level; t++) {
     u64 q = c->mod[t], sm = c->mod[level] % q;
     for (int k = 0; k < np; k++) sm = mulmod(sm, c->mod[c->n_q + k] % q, q);
     u64 h = mulmod(submod(sm, 1, q), (q + 1) / 2, q); /* (S - 1)/2 mod q_t */
-    for (u64 k = 0; k < n; k++) z[(u64)t * n + k] = submod(z[(u64)t * n + k], h, q);
+    for (u64 k = 0; k < n; k++) {
+      u64 zt = submod(z[(u64)t * n + k], mulmod(v[k] % q, sm, q), q);
+      z[(u64)t * n + k] = submod(zt, h, q);
+    }
   }
+  free(v);
   oc_ntt(c, z, level, dst);
   for (int t = 0; t < level; t++) {
     u64 q = c->mod[t], pq = c->mod[level] % q;
@@ -922,7 +944,7 @@ int oc_moddown_rescale(const oc_ctx *c, const u64 *x, int level, u64 *out) {
 
 /* C6 + C21: relinearised product divided by P q_l in the merged step.  The
  * tensor's (d0, d1) join the key-switch accumulator as P d (which vanishes
- * modulo the special primes), so out = round((acc + P d) / (P q_l)) - u.
+ * modulo the special primes), so out = round((acc + P d) / (P q_l)) + e.
  * out: [2][level][N], level - 1, NTT domain. */
 int oc_mul_relin_rescale(const oc_ctx *c, const u64 *a, const u64 *b, int level, u64 *out) {
   okey *k = find_key(c, 0);

@@ -173,7 +173,9 @@ struct TcArgs {
   const __half *bmat;                         // [npad][kpad] row-major constants (bytes)
   u64 sq[TC_MAX_S], inv[TC_MAX_S], inv_s[TC_MAX_S];  // b_i, [Bhat_i^-1]_(b_i), Shoup companion
   u64 src_add[TC_MAX_S];                      // added to y_i mod b_i when has_add
+  u64 rdiv[TC_MAX_S];                         // floor(2^96 / b_i) when has_v
   int has_add, has_sub;
+  int has_v;                                  // overflow removal: A column 8 ns holds v, B row holds -B mod t
   TcTarget tg[TC_MAX_T];
   unsigned char dst_pos[TC_MAX_T];
   const u64 *src[MAX_CTS];
@@ -195,16 +197,20 @@ __device__ __forceinline__ void load_sources(const TcArgs &a, int tile, int tile
   }
 }
 
-// y_i = [x_i Bhat_i^-1]_(b_i) as 8 fp16 bytes into row tid mod 128 of an A tile.
+// y_i = [x_i Bhat_i^-1]_(b_i) as 8 fp16 bytes into row tid mod 128 of an A tile;
+// with overflow removal, this thread's part of sum_i floor(y_i rdiv_i / 2^64)
+// goes to part[group][row].
 __device__ __forceinline__ void store_sources(const TcArgs &a, unsigned char *sA, int tid,
-                                              const u64 (&x)[TC_SRC_PER]) {
+                                              const u64 (&x)[TC_SRC_PER], u64 *part) {
   const int row = tid & (TC_M - 1);
+  u64 fix = 0;
 #pragma unroll
   for (int k = 0; k < TC_SRC_PER; ++k) {
     const int i = tid / TC_M + k * TC_SRC_GROUPS;
     if (i < a.ns) {
       u64 y = shoup(x[k], a.inv[i], a.inv_s[i], a.sq[i]);
       if (a.has_add) y = addmod(y, a.src_add[i], a.sq[i]);
+      if (a.has_v) fix += __umul64hi(y, a.rdiv[i]);
       const u32 lo = (u32)y, hi = (u32)(y >> 32);
       uint4 v;
       v.x = bytes_to_half2(lo, 0x4140);
@@ -214,6 +220,13 @@ __device__ __forceinline__ void store_sources(const TcArgs &a, unsigned char *sA
       *reinterpret_cast<uint4 *>(sA + canon_offset(row, i * 8, a.kpad)) = v;
     }
   }
+  if (a.has_v) part[(tid / TC_M) * TC_M + row] = fix;
+}
+
+// v = floor(sum of the four parts / 2^32) into column 8 ns of row tid (tid < 128).
+__device__ __forceinline__ void store_overflow(const TcArgs &a, unsigned char *sA, int tid, const u64 *part) {
+  const u64 f = part[tid] + part[TC_M + tid] + part[2 * TC_M + tid] + part[3 * TC_M + tid];
+  *reinterpret_cast<__half *>(sA + canon_offset(tid, 8 * a.ns, a.kpad)) = __uint2half_rn((unsigned)(f >> 32));
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1) k_bconv_tc(const TcArgs a) {
@@ -223,6 +236,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_bconv_tc(const TcArgs a) {
   unsigned char *sB = smem + 2 * a_bytes;  // A tiles 0 and 1 precede it
   u64 *mbar = reinterpret_cast<u64 *>(sB + a.npad * a.kpad * 2);  // two barriers
   u32 *tmem_slot = reinterpret_cast<u32 *>(mbar + 2);
+  u64 *part = mbar + 4;  // [4][128] overflow parts (after the barriers and the TMEM slot)
 
   // constants into the canonical layout; zero padding columns of both A tiles
   for (int idx = tid; idx < a.npad * a.kpad; idx += TC_THREADS) {
@@ -252,9 +266,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_bconv_tc(const TcArgs a) {
   u64 x[TC_SRC_PER];  // sources of the next block to be written into an A tile
   if (tile < total) {
     load_sources(a, tile, tiles_per_poly, tid, x);
-    store_sources(a, smem, tid, x);
+    store_sources(a, smem, tid, x, part);
   }
   if (tile + grid < total) load_sources(a, tile + grid, tiles_per_poly, tid, x);
+  if (a.has_v && tile < total) {
+    __syncthreads();
+    if (tid < TC_M) store_overflow(a, smem, tid, part);
+  }
   asm volatile("fence.proxy.async.shared::cta;");
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -296,8 +314,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_bconv_tc(const TcArgs a) {
     const int next = tile + grid;
     // A tile of the next block from the prefetched sources (its buffer's MMAs
     // completed before epilogue j - 1), then prefetch the block after it
-    if (next < total) store_sources(a, smem + nxt * a_bytes, tid, x);
+    if (next < total) store_sources(a, smem + nxt * a_bytes, tid, x, part);
     if (next + grid < total) load_sources(a, next + grid, tiles_per_poly, tid, x);
+    if (a.has_v && next < total) {  // the parts are complete after this barrier
+      __syncthreads();
+      if (tid < TC_M) store_overflow(a, smem + nxt * a_bytes, tid, part);
+    }
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -362,10 +384,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_bconv_tc(const TcArgs a) {
 // key identifies the conversion (table offset); tab_host rows are [nt][ns].
 int launch_bconv_tc(ckks_ctx *c, size_t key, const u64 *inv_host, const u64 *tab_host, int ns, int nt,
                     const int *src_mod, const int *dst_mod, const int *dst_pos, const u64 *const *src,
-                    u64 *const *dst, int np, const u64 *src_add_host, const u64 *dst_sub_host) {
+                    u64 *const *dst, int np, const u64 *src_add_host, const u64 *dst_sub_host,
+                    const u64 *rdiv_host, const u64 *negs_host) {
   if (ns < 1 || ns > TC_MAX_S || nt < 1 || nt > TC_MAX_T || np < 1 || np > MAX_CTS) return CKKS_E_PARAM;
   if (c->n % TC_M) return CKKS_E_PARAM;
-  const int kpad = ((8 * ns + 15) / 16) * 16, npad = ((8 * nt + 15) / 16) * 16;
+  const bool has_v = rdiv_host && negs_host;
+  if (has_v && ns == TC_MAX_S) return CKKS_E_PARAM;  // the overflow column needs K <= 8 ns + 1 <= 128
+  const int kpad = ((8 * ns + (has_v ? 1 : 0) + 15) / 16) * 16, npad = ((8 * nt + 15) / 16) * 16;
   if (!c->tc_err) {
     if (c->capturing) return CKKS_E_STATE;
     if (cudaMalloc(&c->tc_err, sizeof(int)) != cudaSuccess) return CKKS_E_OOM;
@@ -386,6 +411,9 @@ int launch_bconv_tc(ckks_ctx *c, size_t key, const u64 *inv_host, const u64 *tab
             bm[(size_t)(t * 8 + b) * kpad + i * 8 + aa] = __float2half((float)((cf >> (8 * b)) & 0xFF));
         }
       }
+      if (has_v)  // column 8 ns: the bytes of -S mod t, times v in A
+        for (int b = 0; b < 8; ++b)
+          bm[(size_t)(t * 8 + b) * kpad + 8 * ns] = __float2half((float)((negs_host[t] % m >> (8 * b)) & 0xFF));
     }
     void *d = nullptr;
     if (cudaMalloc(&d, bm.size() * sizeof(__half)) != cudaSuccess) return CKKS_E_OOM;
@@ -401,11 +429,13 @@ int launch_bconv_tc(ckks_ctx *c, size_t key, const u64 *inv_host, const u64 *tab
   a.bmat = reinterpret_cast<const __half *>(it->second);
   a.has_add = src_add_host != nullptr;
   a.has_sub = dst_sub_host != nullptr;
+  a.has_v = has_v ? 1 : 0;
   for (int i = 0; i < ns; ++i) {
     a.sq[i] = c->mod[src_mod[i]];
     a.inv[i] = inv_host[2 * i];
     a.inv_s[i] = inv_host[2 * i + 1];
     a.src_add[i] = src_add_host ? src_add_host[i] : 0;
+    a.rdiv[i] = has_v ? rdiv_host[i] : 0;
   }
   const unsigned __int128 two64 = (unsigned __int128)1 << 64;
   for (int t = 0; t < nt; ++t) {
@@ -428,7 +458,7 @@ int launch_bconv_tc(ckks_ctx *c, size_t key, const u64 *inv_host, const u64 *tab
   a.err = c->tc_err;
   // more than half of the SM's shared memory per CTA: one CTA per SM, so its
   // 512-column TMEM allocation never waits for another CTA's
-  const size_t need = 2 * (size_t)TC_M * kpad * 2 + (size_t)npad * kpad * 2 + 32;
+  const size_t need = 2 * (size_t)TC_M * kpad * 2 + (size_t)npad * kpad * 2 + 32 + 4 * TC_M * 8;
   const size_t smem = std::max<size_t>(need, 120 * 1024);
   CK_CUDA(cudaFuncSetAttribute(k_bconv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int sms = 148;

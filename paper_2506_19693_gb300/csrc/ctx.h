@@ -36,6 +36,8 @@ struct ConvTables {
   //   sinv[l] pairs    S^-1 mod q_t
   //   qlinv[l] pairs   q_l^-1 mod q_t
   //   pmod pair        [P]_{q_l}
+  //   rdiv[K+1]        floor(2^96 / s_i): y_i / s_i in 32.32 fixed point
+  //   negs[l]          -S mod q_t (removes the overflow estimate v S)
   std::vector<size_t> mdr_off;     // index l (0 unused)
   // decode: Garner constants inv(q_j) mod q_i  [n_q][n_q] and half-Q digits per level
   size_t garner_inv = 0;
@@ -136,9 +138,12 @@ int launch_ntt(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, i
 // ---- tensor-core basis conversion (bconv_tc.cu) ----
 // src_add_host [ns] / dst_sub_host [nt] (or null): constants added to y_i
 // mod b_i before the products / subtracted from the result mod t.
+// rdiv_host [ns] / negs_host [nt] (or null): overflow removal, y_t += v negs_t
+// with v = floor(sum_i floor(y_i rdiv_i / 2^64) / 2^32).
 int launch_bconv_tc(ckks_ctx *c, size_t key, const u64 *inv_host, const u64 *tab_host, int ns, int nt,
                     const int *src_mod, const int *dst_mod, const int *dst_pos, const u64 *const *src,
-                    u64 *const *dst, int np, const u64 *src_add_host, const u64 *dst_sub_host);
+                    u64 *const *dst, int np, const u64 *src_add_host, const u64 *dst_sub_host,
+                    const u64 *rdiv_host, const u64 *negs_host);
 
 // ---- batched ciphertext operations (capi.cu); n <= 128, all at one level ----
 int rescale_chunk(ckks_ctx *c, ckks_ct *cts, int n);

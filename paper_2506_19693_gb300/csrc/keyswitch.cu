@@ -50,6 +50,10 @@ struct BConvArgs {
   u64 *dst[MAX_CTS];               // output polynomial base (limb positions dst_pos)
   const u64 *src_add = nullptr;    // [ns] or null: added to y_i mod b_i
   const u64 *dst_sub = nullptr;    // [nt] or null: subtracted from y_t mod t
+  // overflow removal (or null): v = floor(sum_i floor(y_i rdiv_i / 2^64) / 2^32),
+  // the overflow sum_i y_i / s_i in 32.32 fixed point; y_t += v negs_t
+  const u64 *rdiv = nullptr;       // [ns] floor(2^96 / b_i)
+  const u64 *negs = nullptr;       // [nt] -B mod t
 };
 
 template <int NS>
@@ -59,18 +63,22 @@ __global__ void __launch_bounds__(TPB) k_bconv(const BConvArgs a) {
   if (k >= a.n) return;
   const u64 *src = a.src[p];
   u64 y[NS];
+  u64 fix = 0;  // overflow estimate in 32.32 fixed point
 #pragma unroll
   for (int i = 0; i < NS; ++i) {
     const u64 q = a.mods[a.src_mod[i]].q;
     y[i] = shoup(src[(size_t)i * a.n + k], a.inv[2 * i], a.inv[2 * i + 1], q);
     if (a.src_add) y[i] = addmod(y[i], __ldg(a.src_add + i), q);
+    if (a.rdiv) fix += __umul64hi(y[i], __ldg(a.rdiv + i));
   }
+  const u64 v = fix >> 32;
   u64 *dst = a.dst[p];
   for (int t = 0; t < a.nt; ++t) {
     const u64 *row = a.tab + (size_t)t * NS;
     u64 hi = 0, lo = 0;
 #pragma unroll
     for (int i = 0; i < NS; ++i) mac128(hi, lo, y[i], __ldg(&row[i]));
+    if (a.negs) mac128(hi, lo, v, __ldg(a.negs + t));
     const ModInfo m = a.mods[a.dst_mod[t]];
     u64 r = reduce128(hi, lo, m);
     if (a.dst_sub) r = submod(r, __ldg(a.dst_sub + t), m.q);
@@ -176,7 +184,7 @@ __global__ void __launch_bounds__(TPB) k_combine(const CombineArgs a, int nl) {
 // ---- ModDown and rescale merged (reading C21) ----
 // Word offsets inside the level-l table block (ConvTables::mdr_off).
 struct MdrLayout {
-  size_t inv, tab, src_add, dst_sub, sinv, qlinv, pmod;
+  size_t inv, tab, src_add, dst_sub, sinv, qlinv, pmod, rdiv, negs;
   MdrLayout(size_t off, int K, int l) {
     inv = off;
     tab = inv + 2 * (size_t)(K + 1);
@@ -185,6 +193,8 @@ struct MdrLayout {
     sinv = dst_sub + l;
     qlinv = sinv + 2 * (size_t)l;
     pmod = qlinv + 2 * (size_t)l;
+    rdiv = pmod + 2;
+    negs = rdiv + (K + 1);
   }
 };
 
@@ -323,7 +333,7 @@ int ks_modup(ckks_ctx *c, int level, int np, const u64 *const *d, u64 *ws, u64 *
       for (int i = 0; i < ns; ++i) sm[i] = a.src_mod[i];
       for (int t = 0; t < a.nt; ++t) dm[t] = a.dst_mod[t], dp[t] = a.dst_pos[t];
       rc = launch_bconv_tc(c, off << 8 | (size_t)a.nt, c->h_conv.data() + off, c->h_conv.data() + off + 2 * ns, ns,
-                           a.nt, sm, dm, dp, a.src, a.dst, np, nullptr, nullptr);
+                           a.nt, sm, dm, dp, a.src, a.dst, np, nullptr, nullptr, nullptr, nullptr);
     } else {
       rc = launch_bconv(c, a, ns, np);
     }
@@ -430,6 +440,8 @@ static int ks_merged_tail(ckks_ctx *c, int level, int nv, u64 *const *acc, u64 *
     a.tab = c->d_conv + L.tab;
     a.src_add = c->d_conv + L.src_add;
     a.dst_sub = c->d_conv + L.dst_sub;
+    a.rdiv = c->d_conv + L.rdiv;
+    a.negs = c->d_conv + L.negs;
     a.nt = l;
     a.src_mod[0] = (unsigned char)l;
     for (int k = 0; k < K; ++k) a.src_mod[1 + k] = (unsigned char)(c->n_q + k);
@@ -447,7 +459,7 @@ static int ks_merged_tail(ckks_ctx *c, int level, int nv, u64 *const *acc, u64 *
       for (int i = 0; i < ns; ++i) sm[i] = a.src_mod[i];
       for (int t = 0; t < l; ++t) dm[t] = t, dp[t] = t;
       rc = launch_bconv_tc(c, L.inv << 8 | (size_t)l, hc + L.inv, hc + L.tab, ns, l, sm, dm, dp, a.src, a.dst, cnt,
-                           hc + L.src_add, hc + L.dst_sub);
+                           hc + L.src_add, hc + L.dst_sub, hc + L.rdiv, hc + L.negs);
     } else {
       rc = launch_bconv(c, a, ns, cnt);
     }
@@ -531,7 +543,7 @@ int ks_tail(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *cons
       for (int t = 0; t < nl; ++t) dm[t] = t, dp[t] = t;
       rc = launch_bconv_tc(c, c->conv.moddown_phat_mod << 8 | (size_t)nl, c->h_conv.data() + c->conv.moddown_phat_inv,
                            c->h_conv.data() + c->conv.moddown_phat_mod, K, nl, sm, dm, dp, a.src, a.dst, cnt,
-                           nullptr, nullptr);
+                           nullptr, nullptr, nullptr, nullptr);
     } else {
       rc = launch_bconv(c, a, K, cnt);
     }
