@@ -102,6 +102,9 @@ def _load():
         "oc_rescale": (P, [V, _u64p, P, _u64p]),
         "oc_moddown_rescale": (P, [V, _u64p, P, _u64p]),
         "oc_keyswitch_ext": (P, [V, _u64p, P, ctypes.c_uint64, _u64p]),
+        "oc_rotate_hoisted_ext": (P, [V, _u64p, P, P, _u64p, _u64p]),
+        "oc_moddown": (P, [V, _u64p, P, _u64p]),
+        "oc_mul_elem": (None, [V, _u64p, _u64p, P, _ip, _u64p]),
         "oc_mul_scalars": (None, [V, _u64p, P, _ip, _u64p, _u64p]),
         "oc_mul_relin_rescale": (P, [V, _u64p, _u64p, P, _u64p]),
         "oc_automorph": (P, [V, _u64p, P, ctypes.c_uint64, _u64p]),
@@ -425,6 +428,45 @@ class Oracle:
         if self._lib.oc_keyswitch_ext(self._c, _p64(d), level, galois, _p64(acc)) != 0:
             raise KeyError(galois)
         return acc
+
+    def ext_mods(self, level: int) -> list:
+        """Modulus indices of the extended basis q_0..q_level, p_0..p_{K-1}."""
+        return list(range(level + 1)) + [self.n_q + k for k in range(self.n_p)]
+
+    def rotate_hoisted_ext(self, a: OCt, steps) -> list:
+        """Hoisted rotations stopped before ModDown: per step [2][level+1+K][N]
+        = (P sigma(c0) + acc0, acc1) over q_0..q_level, P."""
+        gs = np.array([self.galois_elt(k) for k in steps], dtype=np.uint64)
+        ext = a.level + 1 + self.n_p
+        outs = np.zeros((len(steps), 2, ext, self.n), dtype=np.uint64)
+        if self._lib.oc_rotate_hoisted_ext(self._c, _p64(np.ascontiguousarray(a.data)), a.level, len(steps),
+                                           _p64(gs), _p64(outs)) != 0:
+            raise KeyError("galois key")
+        return [np.ascontiguousarray(outs[i]) for i in range(len(steps))]
+
+    def moddown(self, x: np.ndarray, level: int) -> np.ndarray:
+        """C9 on one polynomial over q_0..q_level, P: returns [level+1][N]."""
+        x = np.ascontiguousarray(x, dtype=np.uint64)
+        out = np.zeros((level + 1, self.n), dtype=np.uint64)
+        self._lib.oc_moddown(self._c, _p64(x), level, _p64(out))
+        return out
+
+    def mul_elem(self, x: np.ndarray, y: np.ndarray, mods) -> np.ndarray:
+        """x * y limb by limb mod the listed moduli."""
+        x = np.ascontiguousarray(x, dtype=np.uint64)
+        y = np.ascontiguousarray(y, dtype=np.uint64)
+        out = np.zeros_like(x)
+        self._lib.oc_mul_elem(self._c, _p64(x), _p64(y), len(mods), _pint(list(mods)), _p64(out))
+        return out
+
+    def pt_ext_from_int(self, m: np.ndarray, level: int) -> np.ndarray:
+        """Integer coefficients as an NTT-domain plaintext over q_0..q_level, P."""
+        q_part = self.pt_from_int(m, level)
+        m = np.asarray(m, dtype=np.int64)
+        p_res = np.stack([np.mod(m, np.int64(self.moduli[self.n_q + k])).astype(np.uint64)
+                          for k in range(self.n_p)])
+        p_part = self.ntt(p_res, [self.n_q + k for k in range(self.n_p)])
+        return np.concatenate([q_part, p_part])
 
     def mul_scalars(self, x: np.ndarray, mods, w) -> np.ndarray:
         """x[t] * w[t] mod the t-th modulus (one scalar per limb)."""

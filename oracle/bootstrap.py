@@ -42,10 +42,16 @@ is named B1..B8 and listed in the design notes:
   B9 Every ciphertext product (B6, B7) is the relinearised product with
      ModDown and rescale merged into one conversion (reading C21).
   B10 In a merged level the giant steps meet before any ModDown: the sum
-     P inner_0 + sum_b (P sigma_b(inner_b.c0) + KS_acc(sigma_b(inner_b.c1)))
+     inner_0 + sum_b (P sigma_b(inner_b.c0) + KS_acc(sigma_b(inner_b.c1)))
      over Q_l P (KS_acc: ModUp and key inner product, no ModDown) is divided
      by P q_l once (C21), replacing a ModDown per giant rotation and the
      level's rescale.
+  B11 Double hoisting: the baby rotations stay over Q_l P as well (x_a =
+     (P sigma_a(c0) + acc0, acc1), no ModDown), the giant terms inner_b are
+     sums over Q_l P (diagonal plaintexts carry residues mod P), inner_0
+     joins the B10 sum as it is and each other inner_b is ModDown'd once
+     before its giant rotation.  With the baby steps this cheap, the split
+     is g = 2^(w-1) baby steps (16 x 4 at w = 5) instead of 2^ceil(w/2).
 Parity unpinned: nothing here (see tests/test_oracle_bootstrap.py).
 """
 from __future__ import annotations
@@ -194,7 +200,7 @@ def linear_levels(n_slots: int, inverse: bool):
     for (s0, s1) in order:
         d = group_matrix(n_slots, s0, s1, inverse)
         w = s1 - s0
-        levels.append(LinLevel(step=1 << s0, g=1 << ((w + 1) // 2), diags=d))
+        levels.append(LinLevel(step=1 << s0, g=1 << max(w - 1, 0), diags=d))  # B11: 16 x 4 at w = 5
     return levels
 
 
@@ -283,7 +289,7 @@ class Evaluator:
             for _, items in lv.plan:
                 row = []
                 for _ in items:
-                    row.append(orc.pt_from_int(constants[idx], lv.level))
+                    row.append(orc.pt_ext_from_int(constants[idx], lv.level))  # over Q_l and P (B11)
                     idx += 1
                 per.append(row)
             self.pts.append(per)
@@ -371,44 +377,49 @@ class Evaluator:
             out[p] = o.ntt(o.automorph_coeff(o.intt(ct.data[p], mods), mods, g), mods)
         return OCt(out, ct.level, ct.scale)
 
-    # ---- B3, B10
+    # ---- B3, B10, B11
     def linear(self, x: OCt, lv: LinLevel, pts) -> OCt:
-        """One merged level: baby rotations hoisted; every giant step's term
-        inner_b (sum over a of pt_{b,a} Rot(x, a step)) joins one sum over Q_l P,
-        P inner_0 + sum_{b>0} (P sigma_b(inner_b.c0) + KS_acc(sigma_b(inner_b.c1))),
-        which one merged ModDown-rescale (C21) divides by P q_l (reading B10)."""
+        """One merged level, double hoisted (readings B10, B11): the baby
+        rotations stay over Q_l P (no ModDown): x_0 = P x, x_a = (P sigma_a(c0) +
+        acc0, acc1); each giant term inner_b = sum_a pt_{b,a} x_a over Q_l P
+        (plaintexts with residues mod P too); inner_0 joins the final sum as it
+        is, every other one is ModDown'd (C9), rotated by sigma_b as in B10
+        (P sigma_b(c0) + KS_acc(sigma_b(c1))); one merged ModDown-rescale (C21)
+        divides the sum by P q_l."""
         o = self.o
         assert x.level >= lv.level, (x.level, lv.level)
         x = self.drop(x, lv.level)
         l = lv.level
         mods = list(range(l + 1))
+        emods = o.ext_mods(l)
+        ext = len(emods)
         P = math.prod(int(o.moduli[o.n_q + k]) for k in range(o.n_p))
         pmod = [P % int(o.q[t]) for t in mods]
+        qcol = np.array([int(q) for q in o.q[: l + 1]], dtype=np.uint64)[:, None]
+        extq = np.array([int(o.moduli[m]) for m in emods], dtype=np.uint64)[:, None]
         babies = sorted({a for _, items in lv.plan for a, _ in items})
-        rot_steps = [a * lv.step for a in babies if a]
-        xa = {0: x}
-        if rot_steps:
-            outs = o.rotate_hoisted(x, rot_steps)
-            for a, c in zip([a for a in babies if a], outs):
-                xa[a] = c
-        ext = l + 1 + o.n_p
+        rot = [a for a in babies if a]
+        x0 = np.zeros((2, ext, o.n), dtype=np.uint64)
+        for p in range(2):
+            x0[p, : l + 1] = o.mul_scalars(x.data[p], mods, pmod)
+        xa = {0: x0}
+        if rot:
+            xa.update(zip(rot, o.rotate_hoisted_ext(x, [a * lv.step for a in rot])))
         X = np.zeros((2, ext, o.n), dtype=np.uint64)  # the sum over q_0..q_l, P
         base = np.zeros((2, l + 1, o.n), dtype=np.uint64)  # its part P * base on q_0..q_l
-        qcol = np.array([int(q) for q in o.q[: l + 1]], dtype=np.uint64)[:, None]
-        extq = np.array([int(o.moduli[m]) for m in list(range(l + 1)) + [o.n_q + k for k in range(o.n_p)]],
-                        dtype=np.uint64)[:, None]
         for (b, items), row in zip(lv.plan, pts):
-            inner = None
+            inner = np.zeros((2, ext, o.n), dtype=np.uint64)
             for (a, _), pt in zip(items, row):
-                term = o.mul_plain(xa[a], pt, 1.0)
-                inner = term if inner is None else o.add(inner, term)
+                for p in range(2):
+                    inner[p] = (inner[p] + o.mul_elem(xa[a][p], pt, emods)) % extq
             if b == 0:
-                base = (base + inner.data) % qcol
-            else:
-                g = o.galois_elt(lv.g * b * lv.step)
-                t = self.sigma(inner, g)
-                X = (X + o.keyswitch_ext(t.data[1], l, g)) % extq
-                base[0] = (base[0] + t.data[0]) % qcol
+                X = (X + inner) % extq
+                continue
+            c = OCt(np.stack([o.moddown(inner[p], l) for p in range(2)]), l, x.scale)
+            g = o.galois_elt(lv.g * b * lv.step)
+            t = self.sigma(c, g)
+            X = (X + o.keyswitch_ext(t.data[1], l, g)) % extq
+            base[0] = (base[0] + t.data[0]) % qcol
         for p in range(2):
             X[p, : l + 1] = (X[p, : l + 1] + o.mul_scalars(base[p], mods, pmod)) % qcol
         out = np.stack([o.moddown_rescale(X[p], l) for p in range(2)])

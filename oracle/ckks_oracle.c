@@ -783,6 +783,75 @@ int oc_rotate_hoisted(const oc_ctx *c, const u64 *in, int level, int n_g, const 
   return 0;
 }
 
+/* Hoisted rotations stopped before ModDown (the baby steps of reading B11):
+ * out_g = (P sigma_g(c0) + acc0, acc1) over q_0..q_level, P, with acc the key
+ * inner product of the sigma_g-mapped digits of ModUp(c1).
+ * outs: [n_g][2][level+1+K][N]. */
+int oc_rotate_hoisted_ext(const oc_ctx *c, const u64 *in, int level, int n_g, const u64 *gs, u64 *outs) {
+  for (int i = 0; i < n_g; i++)
+    if (!find_key(c, gs[i])) return -1;
+  u64 n = c->n;
+  int nl = level + 1, ext = nl + c->n_p;
+  int ext_mods[OC_MAXMOD];
+  ext_basis(c, level, ext_mods);
+  u64 *digits = (u64 *)malloc(sizeof(u64) * (u64)c->n_digits * ext * n);
+  u64 *pdig = (u64 *)malloc(sizeof(u64) * (u64)c->n_digits * ext * n);
+  u64 *s0 = (u64 *)malloc(sizeof(u64) * (u64)nl * n);
+  int nact = modup(c, in + (u64)nl * n, level, digits);
+  for (int i = 0; i < n_g; i++) {
+    for (int j = 0; j < nact; j++)
+      automorph_ntt_limbs(c, digits + (u64)j * ext * n, ext, ext_mods, gs[i], pdig + (u64)j * ext * n);
+    u64 *o = outs + (u64)i * 2 * ext * n;
+    inner(c, pdig, nact, level, find_key(c, gs[i])->data, o);
+    automorph_ntt_limbs(c, in, nl, ext_mods, gs[i], s0);
+    for (int t = 0; t < nl; t++) {
+      u64 q = c->mod[t], pm = 1;
+      for (int k = 0; k < c->n_p; k++) pm = mulmod(pm, c->mod[c->n_q + k] % q, q);
+      for (u64 x = 0; x < n; x++) o[(u64)t * n + x] = addmod(o[(u64)t * n + x], mulmod(pm, s0[(u64)t * n + x], q), q);
+    }
+  }
+  free(digits);
+  free(pdig);
+  free(s0);
+  return 0;
+}
+
+/* C9 ModDown of one polynomial x over q_0..q_level, P (NTT domain):
+ * out = (x_Q - BConv_{P->Q}(x_P)) * P^-1 over q_0..q_level. */
+int oc_moddown(const oc_ctx *c, const u64 *x, int level, u64 *out) {
+  u64 n = c->n;
+  int nl = level + 1, np = c->n_p;
+  int psrc[OC_MAXMOD], qdst[OC_MAXMOD];
+  for (int t = 0; t < np; t++) psrc[t] = c->n_q + t;
+  for (int t = 0; t < nl; t++) qdst[t] = t;
+  u64 *xp = (u64 *)malloc(sizeof(u64) * (u64)np * n);
+  u64 *z = (u64 *)malloc(sizeof(u64) * (u64)nl * n);
+  memcpy(xp, x + (u64)nl * n, sizeof(u64) * (u64)np * n);
+  oc_intt(c, xp, np, psrc);
+  oc_bconv(c, xp, np, psrc, z, nl, qdst);
+  oc_ntt(c, z, nl, qdst);
+  for (int t = 0; t < nl; t++) {
+    u64 q = c->mod[t], pinv = 1;
+    for (int pi = 0; pi < np; pi++) pinv = mulmod(pinv, c->mod[c->n_q + pi] % q, q);
+    pinv = invmod(pinv, q);
+    for (u64 k = 0; k < n; k++) {
+      u64 i = (u64)t * n + k;
+      out[i] = mulmod(submod(x[i], z[i], q), pinv, q);
+    }
+  }
+  free(xp);
+  free(z);
+  return 0;
+}
+
+/* out[t][k] = x[t][k] * y[t][k] mod m_t */
+void oc_mul_elem(const oc_ctx *c, const u64 *x, const u64 *y, int n_limbs, const int *mods, u64 *out) {
+  for (int t = 0; t < n_limbs; t++) {
+    u64 q = c->mod[mods[t]];
+    for (u64 k = 0; k < c->n; k++) out[(u64)t * c->n + k] = mulmod(x[(u64)t * c->n + k], y[(u64)t * c->n + k], q);
+  }
+}
+
 /* expose key switching for tests: galois = 0 selects the relinearisation key */
 /* The key switch of d stopped before ModDown: acc = sum_j ModUp_j(d) * key_j
  * over q_0..q_level, P (NTT domain), [2][level+1+K][N]. */

@@ -185,6 +185,80 @@ __global__ void k_mac_plain(const MacArgs a) {
   a.o1[c][off] = reduce128(h1, l1, m);
 }
 
+// ---- double-hoisted linear levels (B11) ----
+__device__ __forceinline__ u32 brv_b(u32 x, int bits) { return __brev(x) >> (32 - bits); }
+// index read by sigma_g at output position j (canonical NTT order)
+__device__ __forceinline__ u32 gal_src_b(u32 j, u32 g, u32 n, int log_n) {
+  if (g == 1) return j;
+  const u32 e = (u32)(((u64)g * (2 * brv_b(j, log_n) + 1)) & (2 * n - 1));
+  return brv_b((e - 1) >> 1, log_n);
+}
+
+struct PTimesArgs {
+  const ModInfo *mods;
+  u32 n;
+  int log_n;
+  int accumulate;                  // 1: dst += ..., 0: dst = ...
+  u64 pm[CKKS_MAX_Q], pm_s[CKKS_MAX_Q];  // [P]_{q_t} and its Shoup companion
+  const u64 *src[MAX_CTS];         // [l+1][N] NTT domain
+  u32 gal[MAX_CTS];
+  u64 *dst[MAX_CTS];               // q-limbs of an extended polynomial
+};
+// dst[t] (=|+=) [P]_{q_t} sigma_g(src)[t], t <= l
+__global__ void k_ptimes(const PTimesArgs a) {
+  const u32 k = blockIdx.x * TPB + threadIdx.x;
+  const int t = blockIdx.y, v = blockIdx.z;
+  if (k >= a.n) return;
+  const u64 q = a.mods[t].q;
+  const u64 x = a.src[v][(size_t)t * a.n + gal_src_b(k, a.gal[v], a.n, a.log_n)];
+  const u64 r = shoup(x, a.pm[t], a.pm_s[t], q);
+  u64 *d = a.dst[v] + (size_t)t * a.n + k;
+  *d = a.accumulate ? addmod(*d, r, q) : r;
+}
+
+constexpr int MAXG = 4;  // giant steps of a double-hoisted level
+struct MacExtArgs {
+  const ModInfo *mods;
+  u32 n;
+  int ext, na, ng;
+  unsigned char mod_of[MAX_MODS];
+  const u64 *pt[MAXG][MAXA];       // [giant][baby] plaintext over Q_l P, or null
+  const u64 *xq;                   // babies: [ct][baby][2][ext][N]
+  size_t x_ct, x_baby;
+  u64 *out;                        // giant terms: [ct][giant][2][ext][N]
+  size_t o_ct, o_giant;
+};
+// inner_j = sum_a pt[j][a] x_a over Q_l P, every giant of the level in one pass
+// over the babies.  Grid (ciphertexts, coefficient blocks, extended limbs).
+__global__ void __launch_bounds__(TPB) k_mac_ext(const MacExtArgs a) {
+  const u32 k = blockIdx.y * TPB + threadIdx.x;
+  const int t = blockIdx.z, c = blockIdx.x;
+  if (k >= a.n) return;
+  const ModInfo m = a.mods[a.mod_of[t]];
+  const size_t poly = (size_t)a.ext * a.n, off = (size_t)t * a.n + k;
+  u64 h[MAXG][2], lo[MAXG][2];
+#pragma unroll
+  for (int j = 0; j < MAXG; ++j) h[j][0] = h[j][1] = lo[j][0] = lo[j][1] = 0;
+  for (int b = 0; b < a.na; ++b) {
+    const u64 *x = a.xq + c * a.x_ct + b * a.x_baby + off;
+    const u64 x0 = x[0], x1 = x[poly];
+#pragma unroll
+    for (int j = 0; j < MAXG; ++j) {
+      if (j >= a.ng || !a.pt[j][b]) continue;
+      const u64 p = __ldg(a.pt[j][b] + off);
+      mac128(h[j][0], lo[j][0], x0, p);
+      mac128(h[j][1], lo[j][1], x1, p);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < MAXG; ++j) {
+    if (j >= a.ng) continue;
+    u64 *o = a.out + c * a.o_ct + j * a.o_giant + off;
+    o[0] = reduce128(h[j][0], lo[j][0], m);
+    o[poly] = reduce128(h[j][1], lo[j][1], m);
+  }
+}
+
 struct CombArgs {
   const ModInfo *mods;
   u32 n;
@@ -283,7 +357,7 @@ void make_levels(int n_slots, bool inverse, std::vector<LinLevel> &out) {
     L.s1 = pr.second;
     L.w = L.s1 - L.s0;
     L.step = 1 << L.s0;
-    L.g = 1 << ((L.w + 1) / 2);
+    L.g = 1 << std::max(L.w - 1, 0);  // B11: 2^(w-1) baby steps (16 x 4 giant steps at w = 5)
     L.inverse = inverse;
     L.span = n_slots / L.step;
     L.W = (1 << L.w) - 1;
@@ -319,6 +393,10 @@ struct BootState {
   size_t slot_words = 0;
   u64 *acc_qp = nullptr;    // giant-step sums over Q_l P, [nct][2][l+1+K][N]
   size_t acc_qp_words = 0;
+  u64 *baby_qp = nullptr;   // baby rotations over Q_l P, [nct][g][2][l+1+K][N]
+  size_t baby_qp_words = 0;
+  u64 *inner_qp = nullptr;  // giant terms over Q_l P, [nct][giants][2][l+1+K][N]
+  size_t inner_qp_words = 0;
 };
 
 void boot_free(ckks_ctx *c) {
@@ -329,6 +407,8 @@ void boot_free(ckks_ctx *c) {
   cudaFree(b->mono_m);
   for (u64 *p : b->chunks) cudaFree(p);
   cudaFree(b->acc_qp);
+  cudaFree(b->baby_qp);
+  cudaFree(b->inner_qp);
   delete b;
   c->boot = nullptr;
 }
@@ -381,8 +461,9 @@ int boot_rotation_steps(ckks_ctx *c, std::vector<int> &steps) {
 
 namespace {
 
+// a diagonal plaintext over q_0..q_level and p_0..p_{K-1} (B11)
 int alloc_pt(ckks_ctx *c, int level, u64 **out) {
-  if (cudaMalloc(out, sizeof(u64) * (size_t)(level + 1) * c->n) != cudaSuccess) {
+  if (cudaMalloc(out, sizeof(u64) * (size_t)(level + 1 + c->n_p) * c->n) != cudaSuccess) {
     cudaGetLastError();
     return CKKS_E_OOM;
   }
@@ -430,7 +511,7 @@ int level_constants(ckks_ctx *c, const LinLevel &lv, double factor, double2 *D0,
         int rc = alloc_pt(c, lv.level, &b.pts[idx]);
         if (rc) return rc;
       }
-      int rc = encode_device_z(c, vec, lv.level, scale, b.pts[idx], flag);
+      int rc = encode_device_z_ext(c, vec, lv.level, scale, b.pts[idx], flag);
       if (rc) return rc;
       ++idx;
     }
@@ -751,139 +832,179 @@ struct Eval {
   }
 
   // ---- B3 ----
+  // device buffer of at least `words` words, grown outside graph capture
+  int grow_buf(u64 *&buf, size_t &have, size_t words) {
+    if (have >= words) return CKKS_OK;
+    if (c->capturing) return CKKS_E_STATE;
+    cudaFree(buf);
+    buf = nullptr;
+    have = 0;
+    if (cudaMalloc(&buf, sizeof(u64) * words) != cudaSuccess) {
+      cudaGetLastError();
+      return CKKS_E_OOM;
+    }
+    have = words;
+    return CKKS_OK;
+  }
+
+  // dst[i] q-limbs (=|+=) [P]_{q_t} sigma_g(src[i]) for nv <= MAX_CTS polynomials
+  int ptimes(int level, int nv, const u64 *const *src, const u32 *gal, u64 *const *dst, bool accumulate) {
+    PTimesArgs a;
+    a.mods = c->d_mods;
+    a.n = c->n;
+    a.log_n = c->log_n;
+    a.accumulate = accumulate ? 1 : 0;
+    for (int t = 0; t <= level; ++t) {
+      const u64 q = c->mod[t];
+      u64 pm = 1;
+      for (int k = 0; k < c->n_p; ++k) pm = host_mulmod(pm, c->mod[c->n_q + k] % q, q);
+      a.pm[t] = pm;
+      a.pm_s[t] = host_shoup(pm, q);
+    }
+    for (int i = 0; i < nv; ++i) {
+      a.src[i] = src[i];
+      a.gal[i] = gal ? gal[i] : 1u;
+      a.dst[i] = dst[i];
+    }
+    const dim3 g((c->n + TPB - 1) / TPB, level + 1, nv);
+    PROF_LAUNCH(c, PK_ELEMENTWISE, (u64)(level + 1) * nv, (k_ptimes<<<g, TPB, 0, c->stream>>>(a)));
+    return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_CUDA;
+  }
+
+  // One merged level, double hoisted (B10, B11): baby rotations over Q_l P
+  // (x_0 = P x, x_a = (P sigma_a(c0) + acc0_a, acc1_a), no ModDown), every
+  // giant term inner_b = sum_a pt_{b,a} x_a over Q_l P in one pass, inner_0
+  // joins the sum X as it is, each other inner_b is ModDown'd (C9) and rotated
+  // as in B10 (X += KS_acc(sigma_b(c1)), base0 += sigma_b(c0)); one merged
+  // ModDown-rescale (C21) divides X + P base by P q_l.
   BV linear(const BV &xin, const LinLevel &lv) {
     BV x = view(xin, lv.level);
     sync_fields(x);
-    std::vector<int> babies;
-    for (const Giant &gi : lv.plan)
-      for (auto &it : gi.items) babies.push_back(it.first);
-    std::sort(babies.begin(), babies.end());
-    babies.erase(std::unique(babies.begin(), babies.end()), babies.end());
-    std::vector<BV> xa(lv.g);
+    const int l = lv.level, nl = l + 1, ext = nl + c->n_p, ng = (int)lv.plan.size();
+    const size_t N = c->n, poly = (size_t)ext * N;
+    if (ng > MAXG || lv.g > MAXA || nct > MAX_CTS) err = err ? err : CKKS_E_PARAM;
     std::vector<int> rot_as;
-    for (int a : babies)
-      if (a) rot_as.push_back(a);
-    if (!rot_as.empty()) {
-      const int m = (int)rot_as.size();
-      std::vector<BV> outs;
-      for (int j = 0; j < m; ++j) outs.push_back(fresh(lv.level, x.scale));
-      std::vector<ckks_ct> flat((size_t)m * nct);
-      for (int j = 0; j < m; ++j)
-        for (int i = 0; i < nct; ++i) flat[(size_t)j * nct + i] = outs[j].v[i];
-      std::vector<u64> gs(m);
-      for (int j = 0; j < m; ++j) gs[j] = ckks_galois_elt(c, rot_as[j] * lv.step);
-      if (!err) {
-        int rc = rotate_hoisted_internal(c, x.v.data(), nct, gs.data(), m, flat.data());
-        if (rc) err = rc;
-      }
-      for (int j = 0; j < m; ++j) xa[rot_as[j]] = outs[j];
-    }
-    // the giant steps meet over Q_l P before one merged ModDown-rescale (B10):
-    // acc = sum_{b>0} KS_acc(sigma_b(inner_b.c1)), base = inner_0 + (sum_{b>0}
-    // sigma_b(inner_b.c0), 0); the result is round((acc + P base) / (P q_l)) - u
-    const int l = lv.level, ext = l + 1 + c->n_p;
-    const size_t per = (size_t)2 * ext * c->n;
-    if (!err && b.acc_qp_words < per * nct) {
-      if (c->capturing) {
-        err = CKKS_E_STATE;
-      } else {
-        cudaFree(b.acc_qp);
-        b.acc_qp = nullptr;
-        b.acc_qp_words = 0;
-        if (cudaMalloc(&b.acc_qp, sizeof(u64) * per * nct) != cudaSuccess) {
-          cudaGetLastError();
-          err = CKKS_E_OOM;
-        } else {
-          b.acc_qp_words = per * nct;
-        }
-      }
-    }
-    std::vector<u64 *> accp(nct);
-    for (int i = 0; i < nct && !err; ++i) accp[i] = b.acc_qp + per * i;
-    BV base;
-    bool have_base = false, have_acc = false;
-    for (const Giant &gi : lv.plan) {
-      BV inner = fresh(lv.level, x.scale);
-      int ci = lv.first_const;
-      for (const Giant &g2 : lv.plan) {
-        if (&g2 == &gi) break;
-        ci += (int)g2.items.size();
-      }
-      for (int c0 = 0; c0 < nct && !err; c0 += MAXB) {
-        const int cn = std::min(MAXB, nct - c0);
-        MacArgs a;
-        a.mods = c->d_mods;
-        a.n = c->n;
-        a.na = (int)gi.items.size();
-        for (int t = 0; t < a.na; ++t) {
-          const int aa = gi.items[t].first;
-          const BV &src = aa ? xa[aa] : x;
-          a.pt[t] = b.pts[ci + t];
-          for (int cc = 0; cc < cn; ++cc) {
-            a.x0[cc][t] = src.v[c0 + cc].data;
-            a.x1[cc][t] = p1(src.v[c0 + cc]);
-          }
-        }
-        for (int cc = 0; cc < cn; ++cc) {
-          a.o0[cc] = inner.v[c0 + cc].data;
-          a.o1[cc] = p1(inner.v[c0 + cc]);
-        }
-        const dim3 g(cn, (c->n + TPB - 1) / TPB, lv.level + 1);
-        PROF_LAUNCH(c, PK_ELEMENTWISE, (u64)(lv.level + 1) * cn * a.na, (k_mac_plain<<<g, TPB, 0, c->stream>>>(a)));
-        if (cudaGetLastError() != cudaSuccess) err = CKKS_E_CUDA;
-      }
-      if (gi.b == 0) {  // inner_0 enters the base as it is
-        if (!have_base) {
-          base = inner;
-          have_base = true;
-        } else {
-          BV s2 = addsub(base, inner, false);
-          release(base);
-          release(inner);
-          base = s2;
-        }
-        continue;
-      }
-      if (!have_base) {  // no b = 0 term: the base starts at zero
-        base = fresh(lv.level, x.scale);
-        for (auto &ct : base.v)
-          if (!err && cudaMemsetAsync(ct.data, 0, sizeof(u64) * 2 * (size_t)ct.n_limbs * c->n, c->stream))
-            err = CKKS_E_CUDA;
-        have_base = true;
-      }
-      sync_fields(inner);
-      const u64 gal = ckks_galois_elt(c, lv.g * gi.b * lv.step);
-      for (int c0 = 0; c0 < nct && !err; c0 += MAX_CTS) {
-        const int cn = std::min(MAX_CTS, nct - c0);
-        std::vector<u64 *> b0(cn);
-        for (int i = 0; i < cn; ++i) b0[i] = base.v[c0 + i].data;
-        int rc = rotate_accumulate_chunk(c, inner.v.data() + c0, gal, cn, accp.data() + c0, b0.data(), have_acc);
-        if (rc) err = rc;
-      }
-      have_acc = true;
-      release(inner);
-    }
-    for (int a : rot_as) release(xa[a]);
-    if (!have_acc)
-      for (int i = 0; i < nct && !err; ++i)
-        if (cudaMemsetAsync(accp[i], 0, sizeof(u64) * per, c->stream)) err = CKKS_E_CUDA;
+    for (const Giant &gi : lv.plan)
+      for (auto &it : gi.items)
+        if (it.first) rot_as.push_back(it.first);
+    std::sort(rot_as.begin(), rot_as.end());
+    rot_as.erase(std::unique(rot_as.begin(), rot_as.end()), rot_as.end());
+    const int na = lv.g;
+    const size_t x_baby = 2 * poly, x_ct = (size_t)na * x_baby, o_giant = 2 * poly, o_ct = (size_t)ng * o_giant;
+    if (!err) err = grow_buf(b.baby_qp, b.baby_qp_words, x_ct * nct);
+    if (!err) err = grow_buf(b.inner_qp, b.inner_qp_words, o_ct * nct);
+    // scratch for every step below, reserved once so that no call reallocates it
+    size_t ws = std::max(ks_modup_words(c, l, nct), ks_merged_words(c, l, nct));
+    ws = std::max(ws, (size_t)2 * nl * N * nct + ks_modup_words(c, l, nct));
+    if (!err) err = ensure_scratch(c, ws);
     BV out = fresh(l - 1, x.scale);
     if (err) return out;
-    for (int c0 = 0; c0 < nct && !err; c0 += MAX_CTS) {
-      const int cn = std::min(MAX_CTS, nct - c0);
-      int rc = ensure_scratch(c, ks_merged_words(c, l, cn));
-      std::vector<const u64 *> b0(cn), b1(cn);
-      std::vector<u64 *> o0(cn), o1(cn);
-      for (int i = 0; i < cn; ++i) {
-        b0[i] = base.v[c0 + i].data;
-        b1[i] = p1(base.v[c0 + i]);
-        o0[i] = out.v[c0 + i].data;
-        o1[i] = p1(out.v[c0 + i]);
-      }
-      if (!rc) rc = ks_merged_finish(c, l, cn, accp.data() + c0, b0.data(), b1.data(), o0.data(), o1.data(),
-                                     c->scratch);
-      if (rc) err = rc;
+    auto baby = [&](int i, int a) { return b.baby_qp + i * x_ct + a * x_baby; };
+    std::vector<const u64 *> x0(nct), x1(nct);
+    std::vector<u64 *> d0(nct), d1(nct);
+    for (int i = 0; i < nct; ++i) {
+      x0[i] = x.v[i].data;
+      x1[i] = p1(x.v[i]);
     }
+    // x_0 = (P c0, P c1) on q_0..q_l, zero on the special limbs
+    for (int i = 0; i < nct && !err; ++i) {
+      d0[i] = baby(i, 0);
+      d1[i] = baby(i, 0) + poly;
+      if (cudaMemsetAsync(d0[i] + nl * N, 0, sizeof(u64) * c->n_p * N, c->stream) ||
+          cudaMemsetAsync(d1[i] + nl * N, 0, sizeof(u64) * c->n_p * N, c->stream))
+        err = CKKS_E_CUDA;
+    }
+    if (!err) err = ptimes(l, nct, x0.data(), nullptr, d0.data(), false);
+    if (!err) err = ptimes(l, nct, x1.data(), nullptr, d1.data(), false);
+    // baby rotations: one ModUp of c1, one inner product per step with sigma_a
+    if (!rot_as.empty() && !err) {
+      std::vector<u64 *> eb(nct);
+      err = ks_modup(c, l, nct, x1.data(), c->scratch, eb.data());
+      std::vector<const u64 *> ebc(eb.begin(), eb.end());
+      for (int a : rot_as) {
+        if (err) break;
+        const u64 g = ckks_galois_elt(c, a * lv.step);
+        const u64 *key = galois_key_data(c, g);
+        if (!key) {
+          err = CKKS_E_NOKEY;
+          break;
+        }
+        std::vector<const u64 *> keys(nct, key);
+        std::vector<u32> gal(nct, (u32)g);
+        std::vector<u64 *> acc(nct);
+        for (int i = 0; i < nct; ++i) acc[i] = baby(i, a);
+        err = ks_accumulate(c, l, nct, x1.data(), ebc.data(), keys.data(), gal.data(), acc.data(), false);
+        if (!err) err = ptimes(l, nct, x0.data(), gal.data(), acc.data(), true);  // + P sigma_a(c0)
+      }
+    }
+    // every giant term in one pass over the babies
+    for (int c0 = 0; c0 < nct && !err; c0 += MAXB) {
+      const int cn = std::min(MAXB, nct - c0);
+      MacExtArgs a;
+      a.mods = c->d_mods;
+      a.n = c->n;
+      a.ext = ext;
+      a.na = na;
+      a.ng = ng;
+      for (int t = 0; t < ext; ++t) a.mod_of[t] = (unsigned char)c->ext_mod(l, t);
+      for (int j = 0; j < MAXG; ++j)
+        for (int t = 0; t < MAXA; ++t) a.pt[j][t] = nullptr;
+      int ci = lv.first_const;
+      for (int j = 0; j < ng; ++j)
+        for (auto &it : lv.plan[j].items) a.pt[j][it.first] = b.pts[ci++];
+      a.xq = baby(c0, 0);
+      a.x_ct = x_ct;
+      a.x_baby = x_baby;
+      a.out = b.inner_qp + c0 * o_ct;
+      a.o_ct = o_ct;
+      a.o_giant = o_giant;
+      const dim3 g(cn, (c->n + TPB - 1) / TPB, ext);
+      PROF_LAUNCH(c, PK_ELEMENTWISE, (u64)ext * cn * na, (k_mac_ext<<<g, TPB, 0, c->stream>>>(a)));
+      if (cudaGetLastError() != cudaSuccess) err = CKKS_E_CUDA;
+    }
+    auto inner = [&](int i, int j) { return b.inner_qp + i * o_ct + j * o_giant; };
+    // X: the b = 0 term itself, or zero
+    int j0 = -1;
+    for (int j = 0; j < ng; ++j)
+      if (lv.plan[j].b == 0) j0 = j;
+    std::vector<u64 *> X(nct);
+    if (j0 < 0) {
+      if (!err) err = grow_buf(b.acc_qp, b.acc_qp_words, 2 * poly * nct);
+      for (int i = 0; i < nct && !err; ++i) {
+        X[i] = b.acc_qp + 2 * poly * i;
+        if (cudaMemsetAsync(X[i], 0, sizeof(u64) * 2 * poly, c->stream)) err = CKKS_E_CUDA;
+      }
+    } else {
+      for (int i = 0; i < nct; ++i) X[i] = inner(i, j0);
+    }
+    BV base = fresh(l, x.scale);
+    for (auto &ct : base.v)
+      if (!err && cudaMemsetAsync(ct.data, 0, sizeof(u64) * 2 * (size_t)ct.n_limbs * N, c->stream)) err = CKKS_E_CUDA;
+    for (int j = 0; j < ng && !err; ++j) {
+      if (j == j0) continue;
+      BV cb = fresh(l, x.scale);  // ModDown of the giant term (C9)
+      std::vector<u64 *> acc(nct), o0(nct), o1(nct), b0(nct);
+      for (int i = 0; i < nct; ++i) {
+        acc[i] = inner(i, j);
+        o0[i] = cb.v[i].data;
+        o1[i] = p1(cb.v[i]);
+        b0[i] = base.v[i].data;
+      }
+      if (!err) err = ks_moddown_finish(c, l, nct, acc.data(), o0.data(), o1.data(), c->scratch);
+      sync_fields(cb);
+      const u64 gal = ckks_galois_elt(c, lv.g * lv.plan[j].b * lv.step);
+      if (!err) err = rotate_accumulate_chunk(c, cb.v.data(), gal, nct, X.data(), b0.data(), true);
+      release(cb);
+    }
+    std::vector<const u64 *> b0(nct), b1(nct);
+    std::vector<u64 *> o0(nct), o1(nct);
+    for (int i = 0; i < nct; ++i) {
+      b0[i] = base.v[i].data;
+      b1[i] = p1(base.v[i]);
+      o0[i] = out.v[i].data;
+      o1[i] = p1(out.v[i]);
+    }
+    if (!err) err = ks_merged_finish(c, l, nct, X.data(), b0.data(), b1.data(), o0.data(), o1.data(), c->scratch);
     release(base);
     // the level's plaintexts sit at scale q_l: (x.scale q_l) / q_l, as a rescale would give
     out.scale = x.scale * (double)c->mod[l] / (double)c->mod[l];
@@ -1084,7 +1205,7 @@ int ckks_boot_import(ckks_ctx *c, const int64_t *coeffs, int count, const double
       for (int i = 0; i < lv.n_const; ++i) {
         const int idx = lv.first_const + i;
         if (!b.pts[idx] && (rc = alloc_pt(c, lv.level, &b.pts[idx]))) return rc;
-        rc = ckks_pt_from_int(c, coeffs + (size_t)idx * c->n, lv.level, b.pts[idx]);
+        rc = pt_from_int_ext(c, coeffs + (size_t)idx * c->n, lv.level, b.pts[idx]);
         if (rc) return rc;
       }
   b.cheb.assign(cheb, cheb + n_cheb);

@@ -279,6 +279,11 @@ int automorph_chunk(ckks_ctx *c, const ckks_ct *in, const u64 *g, ckks_ct *out, 
   return CKKS_OK;
 }
 
+const u64 *galois_key_data(ckks_ctx *c, u64 g) {
+  const DevKey *k = find_galois(c, g);
+  return k ? k->data : nullptr;
+}
+
 // Giant step of a merged linear level (reading B10): t = sigma_g(in[i]) (both
 // polynomials, NTT domain), then acc[i] (= or, accumulate, +=) the key-switch
 // accumulator of t.c1 over q_0..q_l, P, and base0[i] += t.c0 over q_0..q_l.
@@ -310,7 +315,7 @@ int rotate_accumulate_chunk(ckks_ctx *c, const ckks_ct *in, u64 g, int n, u64 *c
   rc = ks_modup(c, level, n, t1.data(), c->scratch + tw, eb.data());
   if (rc) return rc;
   std::vector<const u64 *> ebc(eb.begin(), eb.end());
-  rc = ks_accumulate(c, level, n, t1.data(), ebc.data(), keys.data(), acc, accumulate);
+  rc = ks_accumulate(c, level, n, t1.data(), ebc.data(), keys.data(), nullptr, acc, accumulate);
   if (rc) return rc;
   // base0[i] += t0[i]: two single polynomials per element-wise slot (an odd
   // last one paired with itself: both lanes write the same sum)
@@ -682,6 +687,28 @@ int ckks_pt_from_int(ckks_ctx *c, const int64_t *m, uint32_t level, uint64_t *pt
   const u64 *s1[1] = {pt};
   u64 *d1[1] = {pt};
   rc = launch_ntt(c, s1, d1, 1, level + 1, mods, false);
+  if (rc) return rc;
+  CK_CUDA(cudaStreamSynchronize(c->stream));
+  return CKKS_OK;
+}
+
+int pt_from_int_ext(ckks_ctx *c, const int64_t *m, uint32_t level, uint64_t *pt) {
+  if (!c || !m || !pt) return CKKS_E_PARAM;
+  if ((int)level >= c->n_q) return CKKS_E_LEVEL;
+  const u32 n = c->n;
+  int rc = ensure_scratch(c, n);
+  if (rc) return rc;
+  i64 *dv = reinterpret_cast<i64 *>(c->scratch);
+  CK_CUDA(cudaMemcpyAsync(dv, m, sizeof(i64) * n, cudaMemcpyHostToDevice, c->stream));
+  rc = ew_signed_to_res(c, dv, pt, 0, level + 1);
+  if (!rc) rc = ew_signed_to_res(c, dv, pt + (size_t)(level + 1) * n, c->n_q, c->n_p);
+  if (rc) return rc;
+  int mods[MAX_MODS];
+  for (u32 l = 0; l <= level; ++l) mods[l] = l;
+  for (int k = 0; k < c->n_p; ++k) mods[level + 1 + k] = c->n_q + k;
+  const u64 *s1[1] = {pt};
+  u64 *d1[1] = {pt};
+  rc = launch_ntt(c, s1, d1, 1, level + 1 + c->n_p, mods, false);
   if (rc) return rc;
   CK_CUDA(cudaStreamSynchronize(c->stream));
   return CKKS_OK;

@@ -151,6 +151,8 @@ int rescale_chunk(ckks_ctx *c, ckks_ct *cts, int n);
 int mul_relin_chunk(ckks_ctx *c, const ckks_ct *a, const ckks_ct *b, ckks_ct *out, int n, bool merged = false);
 int automorph_chunk(ckks_ctx *c, const ckks_ct *in, const u64 *g, ckks_ct *out, int n);
 int rotate_hoisted_internal(ckks_ctx *c, const ckks_ct *in, int n, const u64 *g, int m, ckks_ct *out);
+// the switching key of Galois element g (device), or null when absent
+const u64 *galois_key_data(ckks_ctx *c, u64 g);
 // giant step of a merged linear level: acc (=/+=) KS accumulator of sigma_g(c1)
 // over Q_l P, base0 += sigma_g(c0)
 int rotate_accumulate_chunk(ckks_ctx *c, const ckks_ct *in, u64 g, int n, u64 *const *acc, u64 *const *base0,
@@ -158,6 +160,11 @@ int rotate_accumulate_chunk(ckks_ctx *c, const ckks_ct *in, u64 g, int n, u64 *c
 int galois_key_for(ckks_ctx *c, u64 g);
 // encode.cu: N/2 device slots -> NTT plaintext over q_0..q_level at `scale`
 int encode_device_z(ckks_ctx *c, const double2 *z_dev, uint32_t level, double scale, u64 *pt_dev, int *flag_dev);
+// the same over q_0..q_level, then p_0..p_{K-1} (pt_dev holds level + 1 + K limbs)
+int encode_device_z_ext(ckks_ctx *c, const double2 *z_dev, uint32_t level, double scale, u64 *pt_dev,
+                        int *flag_dev);
+// signed integer coefficients (host) -> NTT plaintext over q_0..q_level, p_0..p_{K-1}
+extern "C" int pt_from_int_ext(ckks_ctx *c, const int64_t *m, uint32_t level, uint64_t *pt);
 // boot.cu
 void boot_free(ckks_ctx *c);
 int boot_ensure_plan(ckks_ctx *c);
@@ -179,12 +186,17 @@ int ks_batch(ckks_ctx *c, int level, int np, const u64 *const *d, const u64 *con
              const u64 *const *base0, const u64 *const *base1, u64 *const *o0, u64 *const *o1,
              u64 *ws, bool merged = false);
 // The key inner product alone: acc[i] ([2][level+1+K][N], NTT domain) = or +=
-// sum_j ModUp_j(d_i) key_j_i, from ks_modup's digits (no automorphism).
+// sum_j sigma_gal_i(ModUp_j(d_i)) key_j_i, from ks_modup's digits (gal null:
+// no automorphism).
 int ks_accumulate(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *const *ext_digits,
-                  const u64 *const *keys, u64 *const *acc, bool accumulate);
+                  const u64 *const *keys, const u32 *gal, u64 *const *acc, bool accumulate);
 // Merged ModDown and rescale (reading C21) of caller-built sums acc + P base:
 // o_c = round((acc_c + P base_c) / (P q_l)) - u.  acc is overwritten (its top
 // and special limbs); ws: ks_merged_words(level, nv) words.
 size_t ks_merged_words(const ckks_ctx *c, int level, int nv);
+// C9 ModDown of caller-built accumulators acc ([2][level+1+K][N], NTT
+// domain; the special limbs are consumed): o_c = (acc_c[Q] - z_c) P^-1.
+// ws: 2 (level + 1) N words per accumulator.
+int ks_moddown_finish(ckks_ctx *c, int level, int nv, u64 *const *acc, u64 *const *o0, u64 *const *o1, u64 *ws);
 int ks_merged_finish(ckks_ctx *c, int level, int nv, u64 *const *acc, const u64 *const *base0,
                      const u64 *const *base1, u64 *const *o0, u64 *const *o1, u64 *ws);

@@ -174,6 +174,31 @@ int encode_device_z(ckks_ctx *c, const double2 *z_dev, uint32_t level, double sc
   return launch_ntt(c, src, dst, 1, level + 1, mods, false);
 }
 
+int encode_device_z_ext(ckks_ctx *c, const double2 *z_dev, uint32_t level, double scale, u64 *pt_dev,
+                        int *flag_dev) {
+  const u32 n = c->n;
+  int rc = ensure_fscratch(c, 3 * (size_t)n + 8);
+  if (rc) return rc;
+  double2 *x = reinterpret_cast<double2 *>(c->fscratch + n);
+  PROF_LAUNCH(c, PK_ENCODE, 1,
+              (k_enc_scatter_z<<<(n / 2 + TPB - 1) / TPB, TPB, 0, c->stream>>>(z_dev, x, n, c->log_n)));
+  fft(c, x, -1.0);
+  // the same integer coefficients reduced mod q_0..q_level, then mod p_0..p_{K-1}
+  PROF_LAUNCH(c, PK_ENCODE, level + 1,
+              (k_enc_finish<<<(n + TPB - 1) / TPB, TPB, 0, c->stream>>>(x, n, scale, c->d_mods, level + 1, pt_dev,
+                                                                         flag_dev)));
+  PROF_LAUNCH(c, PK_ENCODE, c->n_p,
+              (k_enc_finish<<<(n + TPB - 1) / TPB, TPB, 0, c->stream>>>(x, n, scale, c->d_mods + c->n_q, c->n_p,
+                                                                         pt_dev + (size_t)(level + 1) * n,
+                                                                         flag_dev)));
+  int mods[MAX_MODS];
+  for (int l = 0; l <= (int)level; ++l) mods[l] = l;
+  for (int k = 0; k < c->n_p; ++k) mods[level + 1 + k] = c->n_q + k;
+  const u64 *src[1] = {pt_dev};
+  u64 *dst[1] = {pt_dev};
+  return launch_ntt(c, src, dst, 1, level + 1 + c->n_p, mods, false);
+}
+
 extern "C" int ckks_encode(ckks_ctx *c, const double *re, const double *im, int n_slots, uint32_t level,
                            double scale, uint64_t *pt_dev) {
   if (!c || !re || !pt_dev || n_slots < 0 || n_slots > (int)(c->n / 2)) return CKKS_E_PARAM;

@@ -491,27 +491,15 @@ static int ks_merged_tail(ckks_ctx *c, int level, int nv, u64 *const *acc, u64 *
   return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_CUDA;
 }
 
-int ks_tail(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *const *ext_digits,
-            const u64 *const *keys, const u32 *gal, const u64 *const *base0, const u32 *base0_gal,
-            const u64 *const *base1, u64 *const *o0, u64 *const *o1, u64 *ws, bool merged) {
-  if (nv <= 0) return CKKS_OK;
-  if (nv > MAX_CTS) return CKKS_E_PARAM;
-  int rc = check_shape(c, level);
-  if (rc) return rc;
-  if (merged && (base0_gal || level < 1)) return CKKS_E_PARAM;
+// C9 ModDown of nv accumulators acc[i] ([2][l+1+K][N], NTT domain; their
+// special limbs are consumed) plus the optional base: o_c = base_c +
+// (acc_c[Q] - z_c) P^-1, base0 read through sigma_g (base0_gal) when given.
+static int moddown_tail(ckks_ctx *c, int level, int nv, u64 *const *acc, u64 *const *z, const int *mods,
+                        const u64 *const *base0, const u32 *base0_gal, const u64 *const *base1, u64 *const *o0,
+                        u64 *const *o1) {
   const u32 n = c->n;
   const int nl = level + 1, K = c->n_p, ext = nl + K;
-  const size_t per = ks_tail_words(c, level, 1);
-  std::vector<u64 *> acc(nv), z(nv);
-  for (int i = 0; i < nv; ++i) {
-    acc[i] = ws + per * i;
-    z[i] = acc[i] + (size_t)2 * ext * n;
-  }
-  int mods[MAX_MODS];
-  for (int t = 0; t < ext; ++t) mods[t] = c->ext_mod(level, t);
-  rc = launch_inner(c, level, nv, d, ext_digits, keys, gal, acc.data(), false);
-  if (rc) return rc;
-  if (merged) return ks_merged_tail(c, level, nv, acc.data(), z.data(), mods, base0, base1, o0, o1);
+  int rc;
   std::vector<const u64 *> ps(2 * nv);
   std::vector<u64 *> pd(2 * nv);
   for (int i = 0; i < nv; ++i)
@@ -577,16 +565,54 @@ int ks_tail(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *cons
   return CKKS_OK;
 }
 
-int ks_accumulate(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *const *ext_digits,
-                  const u64 *const *keys, u64 *const *acc, bool accumulate) {
+
+int ks_tail(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *const *ext_digits,
+            const u64 *const *keys, const u32 *gal, const u64 *const *base0, const u32 *base0_gal,
+            const u64 *const *base1, u64 *const *o0, u64 *const *o1, u64 *ws, bool merged) {
   if (nv <= 0) return CKKS_OK;
   if (nv > MAX_CTS) return CKKS_E_PARAM;
   int rc = check_shape(c, level);
   if (rc) return rc;
-  return launch_inner(c, level, nv, d, ext_digits, keys, nullptr, acc, accumulate);
+  if (merged && (base0_gal || level < 1)) return CKKS_E_PARAM;
+  const u32 n = c->n;
+  const int nl = level + 1, K = c->n_p, ext = nl + K;
+  const size_t per = ks_tail_words(c, level, 1);
+  std::vector<u64 *> acc(nv), z(nv);
+  for (int i = 0; i < nv; ++i) {
+    acc[i] = ws + per * i;
+    z[i] = acc[i] + (size_t)2 * ext * n;
+  }
+  int mods[MAX_MODS];
+  for (int t = 0; t < ext; ++t) mods[t] = c->ext_mod(level, t);
+  rc = launch_inner(c, level, nv, d, ext_digits, keys, gal, acc.data(), false);
+  if (rc) return rc;
+  if (merged) return ks_merged_tail(c, level, nv, acc.data(), z.data(), mods, base0, base1, o0, o1);
+  return moddown_tail(c, level, nv, acc.data(), z.data(), mods, base0, base0_gal, base1, o0, o1);
+}
+
+int ks_accumulate(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *const *ext_digits,
+                  const u64 *const *keys, const u32 *gal, u64 *const *acc, bool accumulate) {
+  if (nv <= 0) return CKKS_OK;
+  if (nv > MAX_CTS) return CKKS_E_PARAM;
+  int rc = check_shape(c, level);
+  if (rc) return rc;
+  return launch_inner(c, level, nv, d, ext_digits, keys, gal, acc, accumulate);
 }
 
 size_t ks_merged_words(const ckks_ctx *c, int level, int nv) { return (size_t)2 * level * c->n * nv; }
+
+int ks_moddown_finish(ckks_ctx *c, int level, int nv, u64 *const *acc, u64 *const *o0, u64 *const *o1, u64 *ws) {
+  if (nv <= 0) return CKKS_OK;
+  if (nv > MAX_CTS) return CKKS_E_PARAM;
+  int rc = check_shape(c, level);
+  if (rc) return rc;
+  const int ext = level + 1 + c->n_p;
+  std::vector<u64 *> z(nv);
+  for (int i = 0; i < nv; ++i) z[i] = ws + (size_t)2 * (level + 1) * c->n * i;
+  int mods[MAX_MODS];
+  for (int t = 0; t < ext; ++t) mods[t] = c->ext_mod(level, t);
+  return moddown_tail(c, level, nv, acc, z.data(), mods, nullptr, nullptr, nullptr, o0, o1);
+}
 
 int ks_merged_finish(ckks_ctx *c, int level, int nv, u64 *const *acc, const u64 *const *base0,
                      const u64 *const *base1, u64 *const *o0, u64 *const *o1, u64 *ws) {
