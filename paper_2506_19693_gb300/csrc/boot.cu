@@ -158,78 +158,24 @@ __global__ void k_cheb(double *c, int d, double kr, int r) {
 }
 
 // ---------------------------------------------------------------- batched kernels
-struct MacArgs {
-  const ModInfo *mods;
-  u32 n;
-  int na;
-  const u64 *x0[MAXB][MAXA], *x1[MAXB][MAXA];
-  const u64 *pt[MAXA];
-  u64 *o0[MAXB], *o1[MAXB];
-};
-// o = sum_a x_a * pt_a (BSGS inner sum).  Grid (ciphertexts, coefficient
-// blocks, limbs): the ciphertext index varies fastest, so the CTAs that read
-// one block of the shared plaintexts run back to back and share it in L2.
-__global__ void k_mac_plain(const MacArgs a) {
-  const u32 k = blockIdx.y * TPB + threadIdx.x;
-  const int t = blockIdx.z, c = blockIdx.x;
-  if (k >= a.n) return;
-  const ModInfo m = a.mods[t];
-  const size_t off = (size_t)t * a.n + k;
-  u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0;
-  for (int i = 0; i < a.na; ++i) {
-    const u64 p = a.pt[i][off];
-    mac128(h0, l0, a.x0[c][i][off], p);
-    mac128(h1, l1, a.x1[c][i][off], p);
-  }
-  a.o0[c][off] = reduce128(h0, l0, m);
-  a.o1[c][off] = reduce128(h1, l1, m);
-}
-
 // ---- double-hoisted linear levels (B11) ----
-__device__ __forceinline__ u32 brv_b(u32 x, int bits) { return __brev(x) >> (32 - bits); }
-// index read by sigma_g at output position j (canonical NTT order)
-__device__ __forceinline__ u32 gal_src_b(u32 j, u32 g, u32 n, int log_n) {
-  if (g == 1) return j;
-  const u32 e = (u32)(((u64)g * (2 * brv_b(j, log_n) + 1)) & (2 * n - 1));
-  return brv_b((e - 1) >> 1, log_n);
-}
-
-struct PTimesArgs {
-  const ModInfo *mods;
-  u32 n;
-  int log_n;
-  int accumulate;                  // 1: dst += ..., 0: dst = ...
-  u64 pm[CKKS_MAX_Q], pm_s[CKKS_MAX_Q];  // [P]_{q_t} and its Shoup companion
-  const u64 *src[MAX_CTS];         // [l+1][N] NTT domain
-  u32 gal[MAX_CTS];
-  u64 *dst[MAX_CTS];               // q-limbs of an extended polynomial
-};
-// dst[t] (=|+=) [P]_{q_t} sigma_g(src)[t], t <= l
-__global__ void k_ptimes(const PTimesArgs a) {
-  const u32 k = blockIdx.x * TPB + threadIdx.x;
-  const int t = blockIdx.y, v = blockIdx.z;
-  if (k >= a.n) return;
-  const u64 q = a.mods[t].q;
-  const u64 x = a.src[v][(size_t)t * a.n + gal_src_b(k, a.gal[v], a.n, a.log_n)];
-  const u64 r = shoup(x, a.pm[t], a.pm_s[t], q);
-  u64 *d = a.dst[v] + (size_t)t * a.n + k;
-  *d = a.accumulate ? addmod(*d, r, q) : r;
-}
-
 constexpr int MAXG = 4;  // giant steps of a double-hoisted level
 struct MacExtArgs {
   const ModInfo *mods;
   u32 n;
-  int ext, na, ng;
+  int ext, na, ng, nq;             // nq = l + 1 q-limbs
   unsigned char mod_of[MAX_MODS];
   const u64 *pt[MAXG][MAXA];       // [giant][baby] plaintext over Q_l P, or null
-  const u64 *xq;                   // babies: [ct][baby][2][ext][N]
+  const u64 *xq;                   // babies a >= 1: [ct][baby][2][ext][N] (slot 0 unused)
   size_t x_ct, x_baby;
+  const u64 *c0[MAXB], *c1[MAXB];  // baby 0 = P x, formed on the fly from x over q_0..q_l
+  u64 pm[CKKS_MAX_Q], pm_s[CKKS_MAX_Q];
   u64 *out;                        // giant terms: [ct][giant][2][ext][N]
   size_t o_ct, o_giant;
 };
 // inner_j = sum_a pt[j][a] x_a over Q_l P, every giant of the level in one pass
-// over the babies.  Grid (ciphertexts, coefficient blocks, extended limbs).
+// over the babies; x_0 = (P c0, P c1) on q-limbs and 0 on the special limbs.
+// Grid (ciphertexts, coefficient blocks, extended limbs).
 __global__ void __launch_bounds__(TPB) k_mac_ext(const MacExtArgs a) {
   const u32 k = blockIdx.y * TPB + threadIdx.x;
   const int t = blockIdx.z, c = blockIdx.x;
@@ -239,9 +185,23 @@ __global__ void __launch_bounds__(TPB) k_mac_ext(const MacExtArgs a) {
   u64 h[MAXG][2], lo[MAXG][2];
 #pragma unroll
   for (int j = 0; j < MAXG; ++j) h[j][0] = h[j][1] = lo[j][0] = lo[j][1] = 0;
-  for (int b = 0; b < a.na; ++b) {
-    const u64 *x = a.xq + c * a.x_ct + b * a.x_baby + off;
-    const u64 x0 = x[0], x1 = x[poly];
+  // baby 0: P x on the q-limbs, nothing on the special limbs
+  if (t < a.nq) {
+    const u64 x0 = shoup(__ldg(a.c0[c] + off), a.pm[t], a.pm_s[t], m.q);
+    const u64 x1 = shoup(__ldg(a.c1[c] + off), a.pm[t], a.pm_s[t], m.q);
+#pragma unroll
+    for (int j = 0; j < MAXG; ++j) {
+      if (j >= a.ng || !a.pt[j][0]) continue;
+      const u64 p = __ldg(a.pt[j][0] + off);
+      mac128(h[j][0], lo[j][0], x0, p);
+      mac128(h[j][1], lo[j][1], x1, p);
+    }
+  }
+  // babies 1..na-1, read-only here: unrolled so that several babies' loads are in flight
+  const u64 *xb = a.xq + c * a.x_ct + off;
+#pragma unroll 4
+  for (int b = 1; b < a.na; ++b) {
+    const u64 x0 = __ldg(xb + b * a.x_baby), x1 = __ldg(xb + b * a.x_baby + poly);
 #pragma unroll
     for (int j = 0; j < MAXG; ++j) {
       if (j >= a.ng || !a.pt[j][b]) continue;
@@ -847,30 +807,6 @@ struct Eval {
     return CKKS_OK;
   }
 
-  // dst[i] q-limbs (=|+=) [P]_{q_t} sigma_g(src[i]) for nv <= MAX_CTS polynomials
-  int ptimes(int level, int nv, const u64 *const *src, const u32 *gal, u64 *const *dst, bool accumulate) {
-    PTimesArgs a;
-    a.mods = c->d_mods;
-    a.n = c->n;
-    a.log_n = c->log_n;
-    a.accumulate = accumulate ? 1 : 0;
-    for (int t = 0; t <= level; ++t) {
-      const u64 q = c->mod[t];
-      u64 pm = 1;
-      for (int k = 0; k < c->n_p; ++k) pm = host_mulmod(pm, c->mod[c->n_q + k] % q, q);
-      a.pm[t] = pm;
-      a.pm_s[t] = host_shoup(pm, q);
-    }
-    for (int i = 0; i < nv; ++i) {
-      a.src[i] = src[i];
-      a.gal[i] = gal ? gal[i] : 1u;
-      a.dst[i] = dst[i];
-    }
-    const dim3 g((c->n + TPB - 1) / TPB, level + 1, nv);
-    PROF_LAUNCH(c, PK_ELEMENTWISE, (u64)(level + 1) * nv, (k_ptimes<<<g, TPB, 0, c->stream>>>(a)));
-    return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_CUDA;
-  }
-
   // One merged level, double hoisted (B10, B11): baby rotations over Q_l P
   // (x_0 = P x, x_a = (P sigma_a(c0) + acc0_a, acc1_a), no ModDown), every
   // giant term inner_b = sum_a pt_{b,a} x_a over Q_l P in one pass, inner_0
@@ -901,22 +837,13 @@ struct Eval {
     if (err) return out;
     auto baby = [&](int i, int a) { return b.baby_qp + i * x_ct + a * x_baby; };
     std::vector<const u64 *> x0(nct), x1(nct);
-    std::vector<u64 *> d0(nct), d1(nct);
     for (int i = 0; i < nct; ++i) {
       x0[i] = x.v[i].data;
       x1[i] = p1(x.v[i]);
     }
-    // x_0 = (P c0, P c1) on q_0..q_l, zero on the special limbs
-    for (int i = 0; i < nct && !err; ++i) {
-      d0[i] = baby(i, 0);
-      d1[i] = baby(i, 0) + poly;
-      if (cudaMemsetAsync(d0[i] + nl * N, 0, sizeof(u64) * c->n_p * N, c->stream) ||
-          cudaMemsetAsync(d1[i] + nl * N, 0, sizeof(u64) * c->n_p * N, c->stream))
-        err = CKKS_E_CUDA;
-    }
-    if (!err) err = ptimes(l, nct, x0.data(), nullptr, d0.data(), false);
-    if (!err) err = ptimes(l, nct, x1.data(), nullptr, d1.data(), false);
-    // baby rotations: one ModUp of c1, one inner product per step with sigma_a
+    // baby rotations: one ModUp of c1, one inner product per step with sigma_a,
+    // whose output gets P sigma_a(c0) on poly 0's q-limbs (baby 0 = P x is
+    // formed inside the MAC)
     if (!rot_as.empty() && !err) {
       std::vector<u64 *> eb(nct);
       err = ks_modup(c, l, nct, x1.data(), c->scratch, eb.data());
@@ -933,8 +860,8 @@ struct Eval {
         std::vector<u32> gal(nct, (u32)g);
         std::vector<u64 *> acc(nct);
         for (int i = 0; i < nct; ++i) acc[i] = baby(i, a);
-        err = ks_accumulate(c, l, nct, x1.data(), ebc.data(), keys.data(), gal.data(), acc.data(), false);
-        if (!err) err = ptimes(l, nct, x0.data(), gal.data(), acc.data(), true);  // + P sigma_a(c0)
+        err = ks_accumulate(c, l, nct, x1.data(), ebc.data(), keys.data(), gal.data(), acc.data(), false,
+                            x0.data());
       }
     }
     // every giant term in one pass over the babies
@@ -946,7 +873,19 @@ struct Eval {
       a.ext = ext;
       a.na = na;
       a.ng = ng;
+      a.nq = nl;
       for (int t = 0; t < ext; ++t) a.mod_of[t] = (unsigned char)c->ext_mod(l, t);
+      for (int t = 0; t < nl; ++t) {
+        const u64 q = c->mod[t];
+        u64 pm = 1;
+        for (int k = 0; k < c->n_p; ++k) pm = host_mulmod(pm, c->mod[c->n_q + k] % q, q);
+        a.pm[t] = pm;
+        a.pm_s[t] = host_shoup(pm, q);
+      }
+      for (int i = 0; i < cn; ++i) {
+        a.c0[i] = x0[c0 + i];
+        a.c1[i] = x1[c0 + i];
+      }
       for (int j = 0; j < MAXG; ++j)
         for (int t = 0; t < MAXA; ++t) a.pt[j][t] = nullptr;
       int ci = lv.first_const;

@@ -187,9 +187,11 @@ int ks_batch(ckks_ctx *c, int level, int np, const u64 *const *d, const u64 *con
              u64 *ws, bool merged = false);
 // The key inner product alone: acc[i] ([2][level+1+K][N], NTT domain) = or +=
 // sum_j sigma_gal_i(ModUp_j(d_i)) key_j_i, from ks_modup's digits (gal null:
-// no automorphism).
+// no automorphism); with pbase0, poly 0's q-limbs also get [P]_{q_t}
+// sigma_gal_i(pbase0_i)[t] (the P sigma(c0) of a rotation kept over Q P).
 int ks_accumulate(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *const *ext_digits,
-                  const u64 *const *keys, const u32 *gal, u64 *const *acc, bool accumulate);
+                  const u64 *const *keys, const u32 *gal, u64 *const *acc, bool accumulate,
+                  const u64 *const *pbase0 = nullptr);
 // Merged ModDown and rescale (reading C21) of caller-built sums acc + P base:
 // o_c = round((acc_c + P base_c) / (P q_l)) - u.  acc is overwritten (its top
 // and special limbs); ws: ks_merged_words(level, nv) words.

@@ -100,6 +100,10 @@ struct IPArgs {
   u32 gal[MAX_CTS];
   u64 *acc[MAX_CTS];               // [2][ext][N]
   int accumulate;                  // 1: acc += result (mod t) instead of acc = result
+  // optional: poly 0 q-limbs t <= l also get [P]_{q_t} sigma_gal(base0)[t]
+  const u64 *base0[MAX_CTS];
+  int nq_base;                     // l + 1 when base0 is used, else 0
+  u64 pm[CKKS_MAX_Q], pm_s[CKKS_MAX_Q];
 };
 
 // Grid: (groups of IP_GROUP outputs, coefficient blocks, extended limbs).
@@ -109,7 +113,7 @@ struct IPArgs {
 // group the thread walks the outputs, reloading key words only when the key
 // changes.
 // The group size (outputs per thread) is a per-context tunable (ckks_tune).
-template <int NDIG>
+template <int NDIG, bool BASE>
 __global__ void __launch_bounds__(TPB, NDIG <= 3 ? 4 : 2) k_inner(const IPArgs a, int group) {
   const u32 k = blockIdx.y * TPB + threadIdx.x;
   const int t = blockIdx.z;
@@ -142,6 +146,8 @@ __global__ void __launch_bounds__(TPB, NDIG <= 3 ? 4 : 2) k_inner(const IPArgs a
       mac128(h1, l1, v, ka[j]);
     }
     u64 r0 = reduce128(h0, l0, m), r1 = reduce128(h1, l1, m);
+    if (BASE && t < a.nq_base)
+      r0 = addmod(r0, shoup(__ldg(a.base0[p] + (size_t)t * a.n + src), a.pm[t], a.pm_s[t], m.q), m.q);
     u64 *o0 = a.acc[p] + (size_t)t * a.n + k, *o1 = a.acc[p] + ((size_t)a.ext + t) * a.n + k;
     if (a.accumulate) {
       r0 = addmod(r0, *o0, m.q);
@@ -356,7 +362,8 @@ int ks_modup(ckks_ctx *c, int level, int np, const u64 *const *d, u64 *ws, u64 *
 // Key inner product of nv outputs into acc[i] ([2][ext][N], NTT domain),
 // overwriting or (accumulate) adding.
 static int launch_inner(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *const *ext_digits,
-                        const u64 *const *keys, const u32 *gal, u64 *const *acc, bool accumulate) {
+                        const u64 *const *keys, const u32 *gal, u64 *const *acc, bool accumulate,
+                        const u64 *const *pbase0 = nullptr) {
   const u32 n = c->n;
   const int nl = level + 1, ext = nl + c->n_p;
   const int ndig = (nl + c->alpha - 1) / c->alpha;
@@ -369,6 +376,15 @@ static int launch_inner(ckks_ctx *c, int level, int nv, const u64 *const *d, con
   a.key_ext = c->n_q + c->n_p;
   a.np = nv;
   a.accumulate = accumulate ? 1 : 0;
+  a.nq_base = pbase0 ? nl : 0;
+  if (pbase0)
+    for (int t = 0; t < nl; ++t) {
+      const u64 q = c->mod[t];
+      u64 pm = 1;
+      for (int k = 0; k < c->n_p; ++k) pm = host_mulmod(pm, c->mod[c->n_q + k] % q, q);
+      a.pm[t] = pm;
+      a.pm_s[t] = host_shoup(pm, q);
+    }
   for (int t = 0; t < ext; ++t) {
     a.mod_of[t] = (unsigned char)c->ext_mod(level, t);
     a.keylimb_of[t] = (unsigned char)c->key_limb(level, t);
@@ -383,12 +399,18 @@ static int launch_inner(ckks_ctx *c, int level, int nv, const u64 *const *d, con
     a.key[i] = keys[i];
     a.gal[i] = gal ? gal[i] : 1u;
     a.acc[i] = acc[i];
+    a.base0[i] = pbase0 ? pbase0[i] : nullptr;
   }
   const int group = c->ip_group > 0 ? c->ip_group : 8;
   dim3 g((nv + group - 1) / group, (n + TPB - 1) / TPB, ext);
   switch (ndig) {
-#define ICASE(D) \
-  case D: PROF_LAUNCH(c, PK_INNER, (u64)nv * ext, (k_inner<D><<<g, TPB, 0, c->stream>>>(a, group))); break;
+#define ICASE(D)                                                                                  \
+  case D:                                                                                         \
+    if (pbase0)                                                                                   \
+      PROF_LAUNCH(c, PK_INNER, (u64)nv * ext, (k_inner<D, true><<<g, TPB, 0, c->stream>>>(a, group))); \
+    else                                                                                          \
+      PROF_LAUNCH(c, PK_INNER, (u64)nv * ext, (k_inner<D, false><<<g, TPB, 0, c->stream>>>(a, group))); \
+    break;
     ICASE(1) ICASE(2) ICASE(3) ICASE(4) ICASE(5) ICASE(6) ICASE(7) ICASE(8)
 #undef ICASE
     default: return CKKS_E_PARAM;
@@ -591,12 +613,13 @@ int ks_tail(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *cons
 }
 
 int ks_accumulate(ckks_ctx *c, int level, int nv, const u64 *const *d, const u64 *const *ext_digits,
-                  const u64 *const *keys, const u32 *gal, u64 *const *acc, bool accumulate) {
+                  const u64 *const *keys, const u32 *gal, u64 *const *acc, bool accumulate,
+                  const u64 *const *pbase0) {
   if (nv <= 0) return CKKS_OK;
-  if (nv > MAX_CTS) return CKKS_E_PARAM;
+  if (nv > MAX_CTS || level + 1 > CKKS_MAX_Q) return CKKS_E_PARAM;
   int rc = check_shape(c, level);
   if (rc) return rc;
-  return launch_inner(c, level, nv, d, ext_digits, keys, gal, acc, accumulate);
+  return launch_inner(c, level, nv, d, ext_digits, keys, gal, acc, accumulate, pbase0);
 }
 
 size_t ks_merged_words(const ckks_ctx *c, int level, int nv) { return (size_t)2 * level * c->n * nv; }
