@@ -111,6 +111,34 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ---------------------------------------------------------------- ranks
+# Weak scaling: the N ranks process N independent batches (their own messages
+# and encryption randomness), so the data path has no exchange; the only
+# collectives are the barriers around the timed region and the max-over-ranks
+# of the timings.
+def shard_seeds(rank):
+    """Seeds of one rank's inputs: messages and encryption randomness of the
+    products and rotations, of the bootstraps, of the RE-Block step and of
+    the uneven batch."""
+    return {"mul": 100 + rank, "boot": 300 + rank, "reboot": 400 + rank, "uneven": 500 + rank}
+
+
+def max_over_ranks(values, dist=None, device="cpu"):
+    """Element-wise maximum of per-rank timings (a float list) over all ranks."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_rates(world, pairs, rotations_per_ct, boots, steps, mul_ms, rot_ms, boot_ms):
+    """Whole-job rates: every rank's units over the slowest rank's time."""
+    return {"hmult_per_s": world * pairs * steps / (mul_ms / 1e3),
+            "rotations_per_s": world * pairs * rotations_per_ct * steps / (rot_ms / 1e3),
+            "bootstraps_per_s": world * boots * steps / (boot_ms / 1e3)}
+
+
 # ---------------------------------------------------------------- oracle arm
 class OracleSample:
     """The CPU oracle on one ciphertext pair of the workload (keys and inputs
@@ -281,8 +309,9 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     ctx = ck.Context.from_workload(w, stream=stream)
     ctx.keygen(1, rot_steps=list(w.rot_steps))
-    z = si.messages(100 + rank, 2 * B, w.slots)
-    seeds = si.enc_seeds(100 + rank, 2 * B)
+    seed = shard_seeds(rank)
+    z = si.messages(seed["mul"], 2 * B, w.slots)
+    seeds = si.enc_seeds(seed["mul"], 2 * B)
     cts = [ctx.encrypt(ctx.encode(z[i], level, scale), level, scale, seeds[i]) for i in range(2 * B)]
     A, Bc = cts[:B], cts[B:]
     OUT = [ctx.new_ct(level + 1) for _ in range(B)]
@@ -295,8 +324,8 @@ def run_gpu(args):
     bctx.keygen_boot(2)
     bctx.boot_setup()
     db = 2.0 ** wb.log2_scale
-    zb = si.messages(300 + rank, nb, wb.slots)
-    bseeds = si.enc_seeds(300 + rank, nb)
+    zb = si.messages(seed["boot"], nb, wb.slots)
+    bseeds = si.enc_seeds(seed["boot"], nb)
     BIN = [bctx.encrypt(bctx.encode(zb[i], 0, db), 0, db, bseeds[i]) for i in range(nb)]
     BOUT = [bctx.new_ct(len(wb.q_bits) - 16) for _ in range(nb)]
 
@@ -360,18 +389,13 @@ def run_gpu(args):
         clk = clocks.stop() if clocks is not None else None
         if ctx.device_error() or bctx.device_error():
             raise RuntimeError(f"device wait expired in the {form} form")
-        t = torch.tensor([sum(m[0].elapsed_time(m[1]) for m in marks), sum(m[1].elapsed_time(m[2]) for m in marks),
-                          sum(m[2].elapsed_time(m[3]) for m in marks),
-                          sum(m[0].elapsed_time(m[3]) for m in marks) / args.steps],
-                         dtype=torch.float64, device="cuda")
-        if dist is not None:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        mul_ms, rot_ms, boot_ms, step_ms = t.tolist()
+        mul_ms, rot_ms, boot_ms, step_ms = max_over_ranks(
+            [sum(m[0].elapsed_time(m[1]) for m in marks), sum(m[1].elapsed_time(m[2]) for m in marks),
+             sum(m[2].elapsed_time(m[3]) for m in marks), sum(m[0].elapsed_time(m[3]) for m in marks) / args.steps],
+            dist, "cuda")
         return {"mul_ms": mul_ms, "rot_ms": rot_ms, "boot_ms": boot_ms, "step_ms": step_ms, "prof": prof,
                 "launches": launches, "errors": errs, "clocks": clk,
-                "hmult_per_s": world * B * args.steps / (mul_ms / 1e3),
-                "rotations_per_s": world * B * len(w.rot_steps) * args.steps / (rot_ms / 1e3),
-                "bootstraps_per_s": world * nb * args.steps / (boot_ms / 1e3)}
+                **job_rates(world, B, len(w.rot_steps), nb, args.steps, mul_ms, rot_ms, boot_ms)}
 
     main = timed(args.form, args.warmup, ClockSampler(local))
     mul_ms, rot_ms, boot_ms, step_ms = main["mul_ms"], main["rot_ms"], main["boot_ms"], main["step_ms"]
@@ -388,7 +412,7 @@ def run_gpu(args):
         ctx.mul_relin_batch(A, Bc, OUT, rescale=ck.RESCALE_SEPARATE)
     e1.record(stream)
     torch.cuda.synchronize()
-    hmult_separate = world * B * args.steps / (e0.elapsed_time(e1) / 1e3)
+    hmult_separate = world * B * args.steps / (max_over_ranks([e0.elapsed_time(e1)], dist, "cuda")[0] / 1e3)
 
     # roofline of the dominant kernel class
     hbm, tflops, peak_kind = peaks()
@@ -477,7 +501,7 @@ def run_uneven(ctx16, w, torch, stream, rank, reps, warmup):
     ctx15 = ck.Context(15, w.q_bits, w.p_bits, w.dnum, w.h, w.sigma, w.log2_scale, stream=stream)
     ctx15.keygen(5, rot_steps=[1 << k for k in range(14)])
     tuned = {"n65536": ctx16.tune(len(w.q_bits) - 1, 64), "n32768": ctx15.tune(len(w.q_bits) - 1, 64)}
-    rng = np.random.default_rng(500 + rank)
+    rng = np.random.default_rng(shard_seeds(rank)["uneven"])
     scale = 2.0 ** w.log2_scale
     ops = []
     for i in range(256):
@@ -525,7 +549,7 @@ def run_reboot_step(bctx, wb, torch, stream, rank):
     for k in g.rotation_steps():
         bctx.keygen_galois(bctx.galois_elt(k))
     b = 128
-    rng = np.random.default_rng(400 + rank)
+    rng = np.random.default_rng(shard_seeds(rank)["reboot"])
     x = rng.uniform(0, 1, size=(b, g.k0))
     y = np.eye(g.o)[rng.integers(0, g.o, size=b)]
     w = rng.normal(0, 1 / np.sqrt(g.k0), size=(g.k0, g.k1))
@@ -591,10 +615,7 @@ def run_e2e(ctx, torch, A, Bc, OUT, level, args, dist):
         once(best)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([dt], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = t.item()
+    dt = max_over_ranks([dt], dist, "cuda")[0]
     world = 1 if dist is None else dist.get_world_size()
     h2d = 2 * B * 2 * (level + 1) * n * 8
     d2h = B * 2 * (out_level + 1) * n * 8
