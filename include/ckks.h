@@ -149,7 +149,9 @@ uint64_t ckks_galois_elt(const ckks_ctx *ctx, int32_t k);
 /* TEST ONLY: host copy of the ternary secret (int8[N]). */
 int ckks_debug_secret(const ckks_ctx *ctx, int8_t *out_host);
 /* TEST ONLY: host copy of one switching key, uint64[n_digits][2][n_q+n_p][N]
- * (b_j, a_j per digit, NTT domain); galois_elt 0 selects relinearisation. */
+ * (b_j, a_j per digit, NTT domain, residues in [0, q)); galois_elt 0 selects
+ * relinearisation.  The device keeps keys in Montgomery form (x 2^64 mod q);
+ * this call converts them back. */
 int ckks_debug_key(const ckks_ctx *ctx, uint64_t galois_elt, uint64_t *out_host);
 
 /* ---- plaintexts (Sec. 3 batching) --------------------------------------- */

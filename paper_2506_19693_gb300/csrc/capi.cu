@@ -669,6 +669,16 @@ int ckks_debug_key(const ckks_ctx *c, uint64_t g, uint64_t *out) {
   if (!k) return CKKS_E_NOKEY;
   CK_CUDA(cudaStreamSynchronize(c->stream));
   CK_CUDA(cudaMemcpy(out, k->data, key_words(c) * sizeof(u64), cudaMemcpyDeviceToHost));
+  // stored in Montgomery form (x 2^64 mod q): multiply by 2^-64 mod q
+  const int ext = c->n_q + c->n_p;
+  for (int t = 0; t < ext; ++t) {
+    const u64 q = c->mod[t];
+    const u64 rinv = host_invmod((u64)(((unsigned __int128)1 << 64) % q), q);
+    for (size_t r = 0; r < (size_t)c->n_digits * 2; ++r) {
+      u64 *row = out + (r * ext + t) * c->n;
+      for (u32 k2 = 0; k2 < c->n; ++k2) row[k2] = host_mulmod(row[k2], rinv, q);
+    }
+  }
   return CKKS_OK;
 }
 

@@ -22,7 +22,7 @@ struct ModInfo {
   u64 one_s;      // floor(2^64 / q): Shoup companion of 1
   u64 ninv;       // N^-1 mod q
   u64 ninv_s;
-  u64 pad;
+  u64 qinv_neg;   // -q^-1 mod 2^64 (Montgomery reduction)
 };
 
 #if defined(__CUDACC__)
@@ -49,6 +49,15 @@ __device__ __forceinline__ u64 reduce128(u64 hi, u64 lo, const ModInfo &m) {
 }
 __device__ __forceinline__ u64 mulmod(u64 a, u64 b, const ModInfo &m) {
   return reduce128(__umul64hi(a, b), a * b, m);
+}
+// Montgomery reduction: (hi 2^64 + lo) 2^-64 mod q, for hi 2^64 + lo < 2^65 q.
+// With m = lo (-q^-1) mod 2^64, lo + m q vanishes mod 2^64 (a carry out exactly
+// when lo != 0), so (T + m q) / 2^64 = hi + floor(m q / 2^64) + [lo != 0] < 3q.
+__device__ __forceinline__ u64 redc128(u64 hi, u64 lo, const ModInfo &m) {
+  const u64 mm = lo * m.qinv_neg;
+  u64 r = hi + __umul64hi(mm, m.q) + (lo != 0 ? 1 : 0);
+  r = csub(r, m.twoq);
+  return csub(r, m.q);
 }
 // 128-bit multiply-accumulate (hi:lo += a * b) as one carry chain
 __device__ __forceinline__ void mac128(u64 &hi, u64 &lo, u64 a, u64 b) {

@@ -96,24 +96,27 @@ struct IPArgs {
   int lo[MAXD], hi[MAXD];
   const u64 *d[MAX_CTS];
   const u64 *ext_buf[MAX_CTS];     // [ndig][ext][N]
-  const u64 *key[MAX_CTS];         // [n_digits][2][key_ext][N]
+  const u64 *key[MAX_CTS];         // [n_digits][2][key_ext][N], Montgomery form
   u32 gal[MAX_CTS];
   u64 *acc[MAX_CTS];               // [2][ext][N]
-  int accumulate;                  // 1: acc += result (mod t) instead of acc = result
-  // optional: poly 0 q-limbs t <= l also get [P]_{q_t} sigma_gal(base0)[t]
+  // IP_BASE: poly 0 q-limbs t <= l also get [P]_{q_t} sigma_gal(base0)[t]
   const u64 *base0[MAX_CTS];
-  int nq_base;                     // l + 1 when base0 is used, else 0
-  u64 pm[CKKS_MAX_Q], pm_s[CKKS_MAX_Q];
+  int nq_base;                     // l + 1
+  u64 pm_mont[CKKS_MAX_Q];         // [P]_{q_t} 2^64 mod q_t
 };
+
+enum IPMode { IP_SET = 0, IP_BASE = 1, IP_ACC = 2 };  // acc = r; acc = r + P base0; acc += r
 
 // Grid: (groups of IP_GROUP outputs, coefficient blocks, extended limbs).
 // The group index varies fastest, so the CTAs that read one block of the
 // lifted digits (all outputs of a hoisted rotation set, all ciphertexts of a
 // relinearisation batch) run back to back and share it through L2.  Within a
 // group the thread walks the outputs, reloading key words only when the key
-// changes.
+// changes.  The products sum in 128 bits against Montgomery-form keys, and one
+// Montgomery reduction per output removes the 2^64: sum_j v_j k_j 2^64 < 2^65 q
+// for reduced digits v_j < q < 2^62 and up to 8 digits (plus the base term).
 // The group size (outputs per thread) is a per-context tunable (ckks_tune).
-template <int NDIG, bool BASE>
+template <int NDIG, int MODE>
 __global__ void __launch_bounds__(TPB, NDIG <= 3 ? 4 : 2) k_inner(const IPArgs a, int group) {
   const u32 k = blockIdx.y * TPB + threadIdx.x;
   const int t = blockIdx.z;
@@ -123,9 +126,10 @@ __global__ void __launch_bounds__(TPB, NDIG <= 3 ? 4 : 2) k_inner(const IPArgs a
   u64 kb[NDIG], ka[NDIG];
   const u64 *cur = nullptr;
   const int p_end = min(a.np, (int)(blockIdx.x + 1) * group);
+  const bool with_base = MODE == IP_BASE && t < a.nq_base;
+  const u64 pm = with_base ? a.pm_mont[t] : 0;
   // digits and keys are read-only here: non-coherent loads let the unrolled
   // iterations issue their loads ahead of the previous ciphertexts' stores
-  // (more bytes in flight per warp; the kernel is bound by memory parallelism)
 #pragma unroll 4
   for (int p = blockIdx.x * group; p < p_end; ++p) {
     if (a.key[p] != cur) {
@@ -140,16 +144,16 @@ __global__ void __launch_bounds__(TPB, NDIG <= 3 ? 4 : 2) k_inner(const IPArgs a
     u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0;
 #pragma unroll
     for (int j = 0; j < NDIG; ++j) {
+      // digit j's limb t: the input's own limb (t in [lo_j, hi_j)) or a lifted one
       const u64 v = (t >= a.lo[j] && t < a.hi[j]) ? __ldg(a.d[p] + (size_t)t * a.n + src)
                                                    : __ldg(a.ext_buf[p] + ((size_t)j * a.ext + t) * a.n + src);
       mac128(h0, l0, v, kb[j]);
       mac128(h1, l1, v, ka[j]);
     }
-    u64 r0 = reduce128(h0, l0, m), r1 = reduce128(h1, l1, m);
-    if (BASE && t < a.nq_base)
-      r0 = addmod(r0, shoup(__ldg(a.base0[p] + (size_t)t * a.n + src), a.pm[t], a.pm_s[t], m.q), m.q);
+    if (MODE == IP_BASE && with_base) mac128(h0, l0, __ldg(a.base0[p] + (size_t)t * a.n + src), pm);
+    u64 r0 = redc128(h0, l0, m), r1 = redc128(h1, l1, m);
     u64 *o0 = a.acc[p] + (size_t)t * a.n + k, *o1 = a.acc[p] + ((size_t)a.ext + t) * a.n + k;
-    if (a.accumulate) {
+    if (MODE == IP_ACC) {
       r0 = addmod(r0, *o0, m.q);
       r1 = addmod(r1, *o1, m.q);
     }
@@ -367,6 +371,11 @@ static int launch_inner(ckks_ctx *c, int level, int nv, const u64 *const *d, con
   const u32 n = c->n;
   const int nl = level + 1, ext = nl + c->n_p;
   const int ndig = (nl + c->alpha - 1) / c->alpha;
+  if (pbase0 && accumulate) return CKKS_E_PARAM;
+  // the Montgomery reduction's input bound: (terms) max q < 2^65
+  for (int t = 0; t < ext; ++t)
+    if ((unsigned __int128)(ndig + (pbase0 ? 1 : 0)) * c->mod[c->ext_mod(level, t)] >= ((unsigned __int128)1 << 65))
+      return CKKS_E_PARAM;
   IPArgs a;
   a.mods = c->d_mods;
   a.n = n;
@@ -375,15 +384,13 @@ static int launch_inner(ckks_ctx *c, int level, int nv, const u64 *const *d, con
   a.ndig = ndig;
   a.key_ext = c->n_q + c->n_p;
   a.np = nv;
-  a.accumulate = accumulate ? 1 : 0;
   a.nq_base = pbase0 ? nl : 0;
   if (pbase0)
     for (int t = 0; t < nl; ++t) {
       const u64 q = c->mod[t];
       u64 pm = 1;
       for (int k = 0; k < c->n_p; ++k) pm = host_mulmod(pm, c->mod[c->n_q + k] % q, q);
-      a.pm[t] = pm;
-      a.pm_s[t] = host_shoup(pm, q);
+      a.pm_mont[t] = host_mulmod(pm, (u64)(((unsigned __int128)1 << 64) % q), q);
     }
   for (int t = 0; t < ext; ++t) {
     a.mod_of[t] = (unsigned char)c->ext_mod(level, t);
@@ -404,12 +411,14 @@ static int launch_inner(ckks_ctx *c, int level, int nv, const u64 *const *d, con
   const int group = c->ip_group > 0 ? c->ip_group : 8;
   dim3 g((nv + group - 1) / group, (n + TPB - 1) / TPB, ext);
   switch (ndig) {
-#define ICASE(D)                                                                                  \
-  case D:                                                                                         \
-    if (pbase0)                                                                                   \
-      PROF_LAUNCH(c, PK_INNER, (u64)nv * ext, (k_inner<D, true><<<g, TPB, 0, c->stream>>>(a, group))); \
-    else                                                                                          \
-      PROF_LAUNCH(c, PK_INNER, (u64)nv * ext, (k_inner<D, false><<<g, TPB, 0, c->stream>>>(a, group))); \
+#define ICASE(D)                                                                                    \
+  case D:                                                                                           \
+    if (pbase0)                                                                                     \
+      PROF_LAUNCH(c, PK_INNER, (u64)nv * ext, (k_inner<D, IP_BASE><<<g, TPB, 0, c->stream>>>(a, group))); \
+    else if (accumulate)                                                                            \
+      PROF_LAUNCH(c, PK_INNER, (u64)nv * ext, (k_inner<D, IP_ACC><<<g, TPB, 0, c->stream>>>(a, group)));  \
+    else                                                                                            \
+      PROF_LAUNCH(c, PK_INNER, (u64)nv * ext, (k_inner<D, IP_SET><<<g, TPB, 0, c->stream>>>(a, group)));  \
     break;
     ICASE(1) ICASE(2) ICASE(3) ICASE(4) ICASE(5) ICASE(6) ICASE(7) ICASE(8)
 #undef ICASE

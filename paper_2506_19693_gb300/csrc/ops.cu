@@ -173,7 +173,9 @@ __global__ void k_signed_to_res(const i64 *v, u64 *out, const ModInfo *mods, int
   out[(size_t)l * n + k] = signed_res(v[k], mods[first_mod + l]);
 }
 
-// switching-key row for digit j: a uniform; b = -a s + e (+ [P]_{q_t} s' on the digit's limbs)
+// switching-key row for digit j: a uniform; b = -a s + e (+ [P]_{q_t} s' on the digit's limbs).
+// Both are stored in Montgomery form (x 2^64 mod q_t), the form the key inner
+// product's Montgomery reduction expects; ckks_debug_key converts back.
 __global__ void k_keyrow(KeyArgs ka) {
   const u32 k = blockIdx.x * TPB + threadIdx.x;
   const int t = blockIdx.y;
@@ -183,8 +185,8 @@ __global__ void k_keyrow(KeyArgs ka) {
   const u64 a = uniform_dev(ka.key_a, (u64)t * ka.n + k, m);
   u64 b = submod(ka.err[off], mulmod(a, ka.s_ntt[off], m), m.q);
   if (t >= ka.lo && t < ka.hi) b = addmod(b, mulmod(ka.p_mod[t], ka.sp_ntt[off], m), m.q);
-  ka.b[off] = b;
-  ka.a[off] = a;
+  ka.b[off] = shoup(b, m.r64, m.r64_s, m.q);
+  ka.a[off] = shoup(a, m.r64, m.r64_s, m.q);
 }
 
 __global__ void k_square(u64 *out, const u64 *in, const ModInfo *mods, u32 n) {

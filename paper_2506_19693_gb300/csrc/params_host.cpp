@@ -104,6 +104,9 @@ int build_tables(ckks_ctx *c) {
     m.one_s = (u64)(((u128)1 << 64) / q);
     m.ninv = host_invmod(n % q, q);
     m.ninv_s = host_shoup(m.ninv, q);
+    u64 inv = q;  // q^-1 mod 2^64 by Newton's iteration (q odd: 5 doublings of 3 correct bits)
+    for (int it = 0; it < 5; ++it) inv *= 2 - q * inv;
+    m.qinv_neg = (u64)0 - inv;
     mi[i] = m;
   }
   // ---- twiddles: tw[k] = psi^brv(k) (k in [0, N)), inverse with psi^-1 ----
