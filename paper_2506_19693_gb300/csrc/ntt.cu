@@ -44,10 +44,26 @@ struct NttParams {
 // strided accesses of the row stages conflict-free.
 __device__ __forceinline__ int padb(int off) { return off + (off >> 4); }
 
+// High word of a 64 x 64-bit product less e, e in {0, 1, 2}: the low x low
+// partial product and the carries out of the cross products' low halves are
+// dropped (each of the three dropped terms is below 2^32 after the shift, so
+// together they carry at most 2 into the high word).  Three 32-bit multiplies
+// instead of the exact high word's four and its carry chain.
+__device__ __forceinline__ u64 umulhi_approx(u64 a, u64 b) {
+  const u32 al = (u32)a, ah = (u32)(a >> 32), bl = (u32)b, bh = (u32)(b >> 32);
+  return (u64)ah * bh + __umulhi(ah, bl) + __umulhi(al, bh);
+}
+// Shoup product with that quotient: w x - (floor(w_s x / 2^64) - e) q lies in
+// [0, 4q) (the exact quotient gives [0, 2q)); q < 2^62.
+__device__ __forceinline__ u64 shoup_approx(u64 x, u64 w, u64 w_s, u64 q) {
+  return w * x - umulhi_approx(w_s, x) * q;
+}
+
 // Cooley-Tukey stages of a 2^K-point block.  Strict (Harvey): inputs < 4q,
 // x brought below 2q before each butterfly, outputs < 4q.  LOOSE, for
-// q < 2^58 only: no correction, every stage raises the bound by 2q, so inputs
-// < q stay below (1 + 2 log2 N) q <= 33 q < 2^64 through all 16 stages.
+// 65 q < 2^64 only: no correction and the approximate Shoup product (t < 4q),
+// every stage raises the bound by 4q, so inputs < q stay below
+// (1 + 4 log2 N) q <= 65 q < 2^64 through all 16 stages.
 template <int K, bool LOOSE>
 __device__ __forceinline__ void fwd_step(u64 (&v)[1 << K], u32 mg, const ulonglong2 *__restrict__ tw,
                                          u64 q, u64 twoq) {
@@ -59,18 +75,27 @@ __device__ __forceinline__ void fwd_step(u64 (&v)[1 << K], u32 mg, const ulonglo
       if (e & half) continue;
       const ulonglong2 w = __ldg(&tw[(mg << s) + (e >> (K - s))]);
       u64 x = v[e];
-      if (!LOOSE && x >= twoq) x -= twoq;
-      const u64 t = shoup_lazy(v[e + half], w.x, w.y, q);
-      v[e] = x + t;
-      v[e + half] = x + twoq - t;
+      if (LOOSE) {
+        const u64 t = shoup_approx(v[e + half], w.x, w.y, q);
+        v[e] = x + t;
+        v[e + half] = x + 2 * twoq - t;
+      } else {
+        if (x >= twoq) x -= twoq;
+        const u64 t = shoup_lazy(v[e + half], w.x, w.y, q);
+        v[e] = x + t;
+        v[e + half] = x + twoq - t;
+      }
     }
   }
 }
 
-// Gentleman-Sande stages s = K-1 .. STOP of a 2^K-point block.
-template <int K, int STOP = 0>
+// Gentleman-Sande stages s = K-1 .. STOP of a 2^K-point block.  Values stay
+// in [0, R) with R = 2q (exact Shoup products); APPROX, for q < 2^61 only,
+// takes the approximate product and R = 4q (x + R - y < 8q < 2^64).
+template <int K, bool APPROX, int STOP = 0>
 __device__ __forceinline__ void inv_step(u64 (&v)[1 << K], u32 mg, const ulonglong2 *__restrict__ tw,
                                          u64 q, u64 twoq) {
+  const u64 r = APPROX ? 2 * twoq : twoq;
 #pragma unroll
   for (int s = K - 1; s >= STOP; --s) {
     const int half = 1 << (K - 1 - s);
@@ -80,15 +105,17 @@ __device__ __forceinline__ void inv_step(u64 (&v)[1 << K], u32 mg, const ulonglo
       const ulonglong2 w = __ldg(&tw[(mg << s) + (e >> (K - s))]);
       const u64 x = v[e], y = v[e + half];
       u64 sum = x + y;
-      if (sum >= twoq) sum -= twoq;
+      if (sum >= r) sum -= r;
       v[e] = sum;
-      v[e + half] = shoup_lazy(x + twoq - y, w.x, w.y, q);
+      v[e + half] = APPROX ? shoup_approx(x + r - y, w.x, w.y, q) : shoup_lazy(x + r - y, w.x, w.y, q);
     }
   }
 }
 
-// Primes below this bound take the forward transform without lazy corrections.
-constexpr u64 LOOSE_BOUND = 1ULL << 58;
+// Primes below this bound take the forward transform without lazy corrections
+// (65 q < 2^64), and primes below 2^61 the inverse with approximate products.
+constexpr u64 LOOSE_BOUND = ~0ULL / 65;
+constexpr u64 APPROX_INV_BOUND = 1ULL << 61;
 
 // ---------------------------------------------------------------- forward
 // One CTA's work of each pass, specialised on LOOSE; the kernels pick the body
@@ -159,7 +186,7 @@ __device__ __forceinline__ void fwd_b_body(const NttParams &prm, u64 *sm, int mi
 #pragma unroll
     for (int e = 0; e < (1 << U2); ++e) {
       u64 r = v[e];
-      if (LOOSE) {  // r < 33 q: Barrett with floor(2^64 / q) to [0, 2q), then [0, q)
+      if (LOOSE) {  // r < 65 q: Barrett with floor(2^64 / q) to [0, 2q), then [0, q)
         r -= __umul64hi(r, one_s) * q;
       } else if (r >= twoq) {
         r -= twoq;
@@ -191,18 +218,15 @@ __global__ void __launch_bounds__(threads_b<RB>(), RB == 16 ? 3 : 6) fwd_pass_b(
 }
 
 // ---------------------------------------------------------------- inverse
-template <int LH, int RB>
-__global__ void __launch_bounds__(threads_b<RB>(), RB == 16 ? 4 : 8) inv_pass_b(const NttParams prm) {
+// Specialised on APPROX (every modulus of the launch below 2^61: values in
+// [0, 4q) between stages and passes), chosen by the host per launch.
+template <int LH, bool APPROX, int RB>
+__device__ __forceinline__ void inv_b_body(const NttParams &prm, u64 *sm, int mi, const u64 *src, u64 *dst) {
   constexpr int H = 1 << LH, U1 = 4, U2 = LB - U1, THREADS = threads_b<RB>();
-  __shared__ u64 sm[RB * BROW + (RB * BROW >> 4)];
-  const int limb = blockIdx.y, poly = blockIdx.z;
-  const int mi = prm.mod_of_limb[limb];
   const u64 q = prm.mods[mi].q, twoq = 2 * q;
   const ulonglong2 *tw = prm.tw + (size_t)mi * prm.n;
-  const u64 *src = prm.src.p[poly] + (size_t)limb * prm.n;
-  u64 *dst = prm.dst.p[poly] + (size_t)limb * prm.n;
   const int row0 = blockIdx.x * RB;
-  {  // the 16 rows (32 KB contiguous) in 16-byte loads, all issued before the first store
+  {  // the rows (contiguous) in 16-byte loads, all issued before the first store
     constexpr int PER = RB * BROW / 2 / THREADS;
     const ulonglong2 *s2 = reinterpret_cast<const ulonglong2 *>(src + (size_t)row0 * BROW);
     ulonglong2 t[PER];
@@ -221,7 +245,7 @@ __global__ void __launch_bounds__(threads_b<RB>(), RB == 16 ? 4 : 8) inv_pass_b(
     u64 v[1 << U2];
 #pragma unroll
     for (int e = 0; e < (1 << U2); ++e) v[e] = sm[padb(rr * BROW + (g << U2) + e)];
-    inv_step<U2>(v, ((u32)(H + b) << U1) + g, tw, q, twoq);
+    inv_step<U2, APPROX>(v, ((u32)(H + b) << U1) + g, tw, q, twoq);
 #pragma unroll
     for (int e = 0; e < (1 << U2); ++e) sm[padb(rr * BROW + (g << U2) + e)] = v[e];
   }
@@ -231,29 +255,36 @@ __global__ void __launch_bounds__(threads_b<RB>(), RB == 16 ? 4 : 8) inv_pass_b(
     u64 v[1 << U1];
 #pragma unroll
     for (int e = 0; e < (1 << U1); ++e) v[e] = sm[padb(rr * BROW + l0 + (e << U2))];
-    inv_step<U1>(v, (u32)(H + b), tw, q, twoq);
+    inv_step<U1, APPROX>(v, (u32)(H + b), tw, q, twoq);
 #pragma unroll
     for (int e = 0; e < (1 << U1); ++e) dst[(size_t)b * BROW + l0 + (e << U2)] = v[e];
   }
 }
 
-template <int LH, int S1>
-__global__ void __launch_bounds__(THREADS, 4) inv_pass_a(const NttParams prm) {
-  constexpr int H = 1 << LH, S2 = LH - S1;
-  __shared__ u64 sm[H * CA];
+template <int LH, int RB, bool APPROX>
+__global__ void __launch_bounds__(threads_b<RB>(), RB == 16 ? 4 : 8) inv_pass_b(const NttParams prm) {
+  __shared__ u64 sm[RB * BROW + (RB * BROW >> 4)];
   const int limb = blockIdx.y, poly = blockIdx.z;
   const int mi = prm.mod_of_limb[limb];
+  const u64 *src = prm.src.p[poly] + (size_t)limb * prm.n;
+  u64 *dst = prm.dst.p[poly] + (size_t)limb * prm.n;
+  inv_b_body<LH, APPROX, RB>(prm, sm, mi, src, dst);
+}
+
+template <int LH, int S1, bool APPROX>
+__device__ __forceinline__ void inv_a_body(const NttParams &prm, u64 *sm, int mi, u64 *dst) {
+  constexpr int H = 1 << LH, S2 = LH - S1;
   const ModInfo m = prm.mods[mi];
   const u64 q = m.q, twoq = 2 * q, ninv = m.ninv, ninv_s = m.ninv_s;
+  const u64 r = APPROX ? 2 * twoq : twoq;
   const ulonglong2 *tw = prm.tw + (size_t)mi * prm.n;
-  u64 *dst = prm.dst.p[poly] + (size_t)limb * prm.n;
   const int c0 = blockIdx.x * CA;
   for (int x = threadIdx.x; x < (1 << S1) * CA; x += THREADS) {
     const int c = x % CA, g = x / CA;
     u64 v[1 << S2];
 #pragma unroll
     for (int e = 0; e < (1 << S2); ++e) v[e] = dst[(size_t)((g << S2) + e) * BROW + c0 + c];
-    inv_step<S2>(v, (1u << S1) + g, tw, q, twoq);
+    inv_step<S2, APPROX>(v, (1u << S1) + g, tw, q, twoq);
 #pragma unroll
     for (int e = 0; e < (1 << S2); ++e) sm[((g << S2) + e) * CA + c] = v[e];
   }
@@ -263,45 +294,60 @@ __global__ void __launch_bounds__(THREADS, 4) inv_pass_a(const NttParams prm) {
     u64 v[1 << S1];
 #pragma unroll
     for (int e = 0; e < (1 << S1); ++e) v[e] = sm[(r0 + (e << S2)) * CA + c];
-    inv_step<S1, 1>(v, 1u, tw, q, twoq);
+    inv_step<S1, APPROX, 1>(v, 1u, tw, q, twoq);
     // last stage (twiddle psi^-brv(1)) with N^-1 folded in: the sum is scaled
     // by N^-1, the difference by tw[0] = psi^-brv(1) N^-1; both fully reduced
+    // by exact Shoup products
     constexpr int HALF = 1 << (S1 - 1);
     const ulonglong2 w0 = __ldg(&tw[0]);
 #pragma unroll
     for (int e = 0; e < HALF; ++e) {
       const u64 x = v[e], y = v[e + HALF];
       dst[(size_t)(r0 + (e << S2)) * BROW + c0 + c] = shoup(x + y, ninv, ninv_s, q);
-      dst[(size_t)(r0 + ((e + HALF) << S2)) * BROW + c0 + c] = shoup(x + twoq - y, w0.x, w0.y, q);
+      dst[(size_t)(r0 + ((e + HALF) << S2)) * BROW + c0 + c] = shoup(x + r - y, w0.x, w0.y, q);
     }
   }
 }
 
+template <int LH, int S1, bool APPROX>
+__global__ void __launch_bounds__(THREADS, 4) inv_pass_a(const NttParams prm) {
+  __shared__ u64 sm[(1 << LH) * CA];
+  const int limb = blockIdx.y, poly = blockIdx.z;
+  const int mi = prm.mod_of_limb[limb];
+  u64 *dst = prm.dst.p[poly] + (size_t)limb * prm.n;
+  inv_a_body<LH, S1, APPROX>(prm, sm, mi, dst);
+}
+
+template <int LH, int RB, bool APPROX>
+void launch_inv(ckks_ctx *c, const NttParams &prm, int npoly) {
+  constexpr int S1 = (LH + 1) / 2;
+  const unsigned long long units = (unsigned long long)prm.n_limbs * npoly;
+  dim3 ga(BROW / CA, prm.n_limbs, npoly), gb((1 << LH) / RB, prm.n_limbs, npoly);
+  PROF_LAUNCH(c, PK_NTT_INV_B, units, (inv_pass_b<LH, RB, APPROX><<<gb, threads_b<RB>(), 0, c->stream>>>(prm)));
+  PROF_LAUNCH(c, PK_NTT_INV_A, units, (inv_pass_a<LH, S1, APPROX><<<ga, THREADS, 0, c->stream>>>(prm)));
+}
+
 template <int LH>
-void launch_lh(ckks_ctx *c, const NttParams &prm, int npoly, bool inverse) {
+void launch_lh(ckks_ctx *c, const NttParams &prm, int npoly, bool inverse, bool approx) {
+  if (inverse) {
+    if (c->ntt_rows == 8)
+      approx ? launch_inv<LH, 8, true>(c, prm, npoly) : launch_inv<LH, 8, false>(c, prm, npoly);
+    else
+      approx ? launch_inv<LH, 16, true>(c, prm, npoly) : launch_inv<LH, 16, false>(c, prm, npoly);
+    return;
+  }
   constexpr int S1 = (LH + 1) / 2;
   const int H = 1 << LH;
   cudaStream_t st = c->stream;
   const unsigned long long units = (unsigned long long)prm.n_limbs * npoly;
   dim3 ga(BROW / CA, prm.n_limbs, npoly);
+  PROF_LAUNCH(c, PK_NTT_FWD_A, units, (fwd_pass_a<LH, S1><<<ga, THREADS, 0, st>>>(prm)));
   if (c->ntt_rows == 8) {
     dim3 gb(H / 8, prm.n_limbs, npoly);
-    if (!inverse) {
-      PROF_LAUNCH(c, PK_NTT_FWD_A, units, (fwd_pass_a<LH, S1><<<ga, THREADS, 0, st>>>(prm)));
-      PROF_LAUNCH(c, PK_NTT_FWD_B, units, (fwd_pass_b<LH, 8><<<gb, threads_b<8>(), 0, st>>>(prm, 0)));
-    } else {
-      PROF_LAUNCH(c, PK_NTT_INV_B, units, (inv_pass_b<LH, 8><<<gb, threads_b<8>(), 0, st>>>(prm)));
-      PROF_LAUNCH(c, PK_NTT_INV_A, units, (inv_pass_a<LH, S1><<<ga, THREADS, 0, st>>>(prm)));
-    }
+    PROF_LAUNCH(c, PK_NTT_FWD_B, units, (fwd_pass_b<LH, 8><<<gb, threads_b<8>(), 0, st>>>(prm, 0)));
   } else {
     dim3 gb(H / 16, prm.n_limbs, npoly);
-    if (!inverse) {
-      PROF_LAUNCH(c, PK_NTT_FWD_A, units, (fwd_pass_a<LH, S1><<<ga, THREADS, 0, st>>>(prm)));
-      PROF_LAUNCH(c, PK_NTT_FWD_B, units, (fwd_pass_b<LH, 16><<<gb, threads_b<16>(), 0, st>>>(prm, 0)));
-    } else {
-      PROF_LAUNCH(c, PK_NTT_INV_B, units, (inv_pass_b<LH, 16><<<gb, threads_b<16>(), 0, st>>>(prm)));
-      PROF_LAUNCH(c, PK_NTT_INV_A, units, (inv_pass_a<LH, S1><<<ga, THREADS, 0, st>>>(prm)));
-    }
+    PROF_LAUNCH(c, PK_NTT_FWD_B, units, (fwd_pass_b<LH, 16><<<gb, threads_b<16>(), 0, st>>>(prm, 0)));
   }
 }
 
@@ -316,7 +362,11 @@ int launch_ntt(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, i
   prm.tw = inverse ? c->d_tw_inv : c->d_tw_fwd;
   prm.n = c->n;
   prm.n_limbs = nl;
-  for (int l = 0; l < nl; ++l) prm.mod_of_limb[l] = (unsigned char)mods[l];
+  bool approx = true;  // inverse: every modulus below 2^61
+  for (int l = 0; l < nl; ++l) {
+    prm.mod_of_limb[l] = (unsigned char)mods[l];
+    approx = approx && c->mod[mods[l]] < APPROX_INV_BOUND;
+  }
   for (int i = 0; i < npoly; ++i)  // the row passes move 16-byte words
     if (((uintptr_t)src[i] | (uintptr_t)dst[i]) & 15) return CKKS_E_PARAM;
   for (int p0 = 0; p0 < npoly; p0 += MAX_POLYS) {
@@ -326,13 +376,13 @@ int launch_ntt(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, i
       prm.dst.p[i] = dst[p0 + i];
     }
     switch (c->log_n - LB) {
-      case 2: launch_lh<2>(c, prm, cnt, inverse); break;
-      case 3: launch_lh<3>(c, prm, cnt, inverse); break;
-      case 4: launch_lh<4>(c, prm, cnt, inverse); break;
-      case 5: launch_lh<5>(c, prm, cnt, inverse); break;
-      case 6: launch_lh<6>(c, prm, cnt, inverse); break;
-      case 7: launch_lh<7>(c, prm, cnt, inverse); break;
-      case 8: launch_lh<8>(c, prm, cnt, inverse); break;
+      case 2: launch_lh<2>(c, prm, cnt, inverse, approx); break;
+      case 3: launch_lh<3>(c, prm, cnt, inverse, approx); break;
+      case 4: launch_lh<4>(c, prm, cnt, inverse, approx); break;
+      case 5: launch_lh<5>(c, prm, cnt, inverse, approx); break;
+      case 6: launch_lh<6>(c, prm, cnt, inverse, approx); break;
+      case 7: launch_lh<7>(c, prm, cnt, inverse, approx); break;
+      case 8: launch_lh<8>(c, prm, cnt, inverse, approx); break;
       default: return CKKS_E_PARAM;
     }
   }
