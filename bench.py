@@ -198,7 +198,9 @@ def config_of(w, batch, form):
 
 # ---------------------------------------------------------------- GPU arm
 # Algorithmic work per unit the library's profiler counts (a limb of N words,
-# except the basis conversions, whose unit is one source-target limb pair):
+# except the basis conversions, whose unit is one source-target limb pair, and
+# the bootstrap's plaintext MAC and linear combination, whose unit is one limb
+# of N words moved to or from HBM):
 #   HBM words moved per unit (8 bytes each, N per limb),
 #   integer work per unit: Shoup butterflies or 64x64->128 MACs per coefficient,
 #   tensor work of bconv_tc: 8 x 8 byte products per coefficient and pair,
@@ -207,7 +209,8 @@ def kernel_work(name, units, launches, w, ndig):
     n = 1 << w.log_n
     lh = w.log_n - 8
     hbm_words = {"ntt_fwd_pass_a": 2, "ntt_fwd_pass_b": 2, "ntt_inv_pass_a": 2, "ntt_inv_pass_b": 2,
-                 "automorph": 2, "tensor": 7, "ks_moddown_combine": 8, "ks_inner_product": ndig + 2}.get(name)
+                 "automorph": 2, "tensor": 7, "ks_moddown_combine": 8, "ks_inner_product": ndig + 2,
+                 "boot_mac_ext": 1, "boot_lincomb": 1}.get(name)
     alu = None
     if name in ("ntt_fwd_pass_a", "ntt_inv_pass_a"):
         alu = ("bfly", units * (n // 2) * lh)

@@ -46,6 +46,13 @@ constexpr int MAXB = 16;   // ciphertexts per fused launch
 constexpr int MAXA = 16;   // baby steps
 constexpr int MAXT = 8;    // terms of an integer linear combination
 
+// [k]_q of a signed integer (host)
+static u64 host_sres(i64 k, u64 q) {
+  if (k >= 0) return (u64)k % q;
+  const u64 mag = ((u64)(-(k + 1)) + 1) % q;
+  return mag ? q - mag : 0;
+}
+
 struct Giant {
   int b;
   std::vector<std::pair<int, int>> items;  // (a, k) ascending a
@@ -173,65 +180,48 @@ struct MacExtArgs {
   u64 *out;                        // giant terms: [ct][giant][2][ext][N]
   size_t o_ct, o_giant;
 };
-// inner_j = sum_a pt[j][a] x_a over Q_l P, every giant of the level in one pass
-// over the babies; x_0 = (P c0, P c1) on q-limbs and 0 on the special limbs.
-// Grid (ciphertexts, coefficient blocks, extended limbs).
+// inner_j = sum_a pt[j][a] x_a over Q_l P for every giant j of the level;
+// x_0 = (P c0, P c1) on q-limbs and 0 on the special limbs.
+// Grid (giants x ciphertexts, coefficient blocks, extended limbs), the giant
+// fastest: the ng CTAs that read one ciphertext's babies at one coefficient
+// block run back to back and share them through L2, so the babies stream from
+// HBM once while each thread keeps only one giant's two 128-bit sums.
 __global__ void __launch_bounds__(TPB) k_mac_ext(const MacExtArgs a) {
   const u32 k = blockIdx.y * TPB + threadIdx.x;
-  const int t = blockIdx.z, c = blockIdx.x;
+  const int t = blockIdx.z, j = blockIdx.x % a.ng, c = blockIdx.x / a.ng;
   if (k >= a.n) return;
   const ModInfo m = a.mods[a.mod_of[t]];
   const size_t poly = (size_t)a.ext * a.n, off = (size_t)t * a.n + k;
-  u64 h[MAXG][2], lo[MAXG][2];
-#pragma unroll
-  for (int j = 0; j < MAXG; ++j) h[j][0] = h[j][1] = lo[j][0] = lo[j][1] = 0;
+  u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0;
   // baby 0: P x on the q-limbs, nothing on the special limbs
-  if (t < a.nq) {
-    const u64 x0 = shoup(__ldg(a.c0[c] + off), a.pm[t], a.pm_s[t], m.q);
-    const u64 x1 = shoup(__ldg(a.c1[c] + off), a.pm[t], a.pm_s[t], m.q);
-#pragma unroll
-    for (int j = 0; j < MAXG; ++j) {
-      if (j >= a.ng || !a.pt[j][0]) continue;
-      const u64 p = __ldg(a.pt[j][0] + off);
-      mac128(h[j][0], lo[j][0], x0, p);
-      mac128(h[j][1], lo[j][1], x1, p);
-    }
+  if (t < a.nq && a.pt[j][0]) {
+    const u64 p = __ldg(a.pt[j][0] + off);
+    mac128(h0, l0, shoup(__ldg(a.c0[c] + off), a.pm[t], a.pm_s[t], m.q), p);
+    mac128(h1, l1, shoup(__ldg(a.c1[c] + off), a.pm[t], a.pm_s[t], m.q), p);
   }
   // babies 1..na-1, read-only here: unrolled so that several babies' loads are in flight
   const u64 *xb = a.xq + c * a.x_ct + off;
-#pragma unroll 4
+#pragma unroll 8
   for (int b = 1; b < a.na; ++b) {
-    const u64 x0 = __ldg(xb + b * a.x_baby), x1 = __ldg(xb + b * a.x_baby + poly);
-#pragma unroll
-    for (int j = 0; j < MAXG; ++j) {
-      if (j >= a.ng || !a.pt[j][b]) continue;
-      const u64 p = __ldg(a.pt[j][b] + off);
-      mac128(h[j][0], lo[j][0], x0, p);
-      mac128(h[j][1], lo[j][1], x1, p);
-    }
+    const u64 *pt = a.pt[j][b];
+    if (!pt) continue;
+    const u64 p = __ldg(pt + off);
+    mac128(h0, l0, __ldg(xb + b * a.x_baby), p);
+    mac128(h1, l1, __ldg(xb + b * a.x_baby + poly), p);
   }
-#pragma unroll
-  for (int j = 0; j < MAXG; ++j) {
-    if (j >= a.ng) continue;
-    u64 *o = a.out + c * a.o_ct + j * a.o_giant + off;
-    o[0] = reduce128(h[j][0], lo[j][0], m);
-    o[poly] = reduce128(h[j][1], lo[j][1], m);
-  }
+  u64 *o = a.out + c * a.o_ct + j * a.o_giant + off;
+  o[0] = reduce128(h0, l0, m);
+  o[poly] = reduce128(h1, l1, m);
 }
 
 struct CombArgs {
   const ModInfo *mods;
   u32 n;
   int nt;
-  i64 kc[MAXT];
+  u64 kr[MAXT][CKKS_MAX_Q];        // [k_i]_{q_t}, reduced on the host
   const u64 *x0[MAXB][MAXT], *x1[MAXB][MAXT];
   u64 *o0[MAXB], *o1[MAXB];
 };
-__device__ __forceinline__ u64 sres(i64 x, const ModInfo &m) {
-  if (x >= 0) return reduce128(0, (u64)x, m);
-  const u64 mag = reduce128(0, (u64)(-(x + 1)) + 1, m);
-  return mag ? m.q - mag : 0;
-}
 // o = sum_i k_i x_i
 __global__ void k_lincomb(const CombArgs a) {
   const u32 k = blockIdx.x * TPB + threadIdx.x;
@@ -240,10 +230,11 @@ __global__ void k_lincomb(const CombArgs a) {
   const ModInfo m = a.mods[t];
   const size_t off = (size_t)t * a.n + k;
   u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0;
+#pragma unroll 4
   for (int i = 0; i < a.nt; ++i) {
-    const u64 kk = sres(a.kc[i], m);
-    mac128(h0, l0, a.x0[c][i][off], kk);
-    mac128(h1, l1, a.x1[c][i][off], kk);
+    const u64 kk = a.kr[i][t];
+    mac128(h0, l0, __ldg(a.x0[c][i] + off), kk);
+    mac128(h1, l1, __ldg(a.x1[c][i] + off), kk);
   }
   a.o0[c][off] = reduce128(h0, l0, m);
   a.o1[c][off] = reduce128(h1, l1, m);
@@ -252,7 +243,7 @@ __global__ void k_lincomb(const CombArgs a) {
 struct ConstArgs {
   const ModInfo *mods;
   u32 n;
-  i64 k;
+  u64 kr[CKKS_MAX_Q];               // [k]_{q_t}, reduced on the host
   const u64 *x0[MAXB], *x1[MAXB];
   u64 *o0[MAXB], *o1[MAXB];
 };
@@ -263,7 +254,7 @@ __global__ void k_add_const(const ConstArgs a) {
   if (k >= a.n) return;
   const ModInfo m = a.mods[t];
   const size_t off = (size_t)t * a.n + k;
-  a.o0[c][off] = addmod(a.x0[c][off], sres(a.k, m), m.q);
+  a.o0[c][off] = addmod(a.x0[c][off], a.kr[t], m.q);
   a.o1[c][off] = a.x1[c][off];
 }
 
@@ -571,7 +562,8 @@ struct Eval {
         a.mods = c->d_mods;
         a.n = c->n;
         a.nt = tn;
-        for (int i = 0; i < tn; ++i) a.kc[i] = ks[t0 + i];
+        for (int i = 0; i < tn; ++i)
+          for (int l = 0; l <= o.level; ++l) a.kr[i][l] = host_sres(ks[t0 + i], c->mod[l]);
         for (int cc = 0; cc < cn; ++cc) {
           for (int i = 0; i < tn; ++i) {
             a.x0[cc][i] = xs[t0 + i]->v[c0 + cc].data;
@@ -586,7 +578,8 @@ struct Eval {
           return o;
         }
         const dim3 g((c->n + TPB - 1) / TPB, level + 1, cn);
-        PROF_LAUNCH(c, PK_ELEMENTWISE, (u64)(level + 1) * cn, (k_lincomb<<<g, TPB, 0, c->stream>>>(a)));
+        PROF_LAUNCH(c, PK_BOOT_LINCOMB, (u64)(level + 1) * cn * (2 * tn + 2),
+                    (k_lincomb<<<g, TPB, 0, c->stream>>>(a)));
       }
     }
     if (cudaGetLastError() != cudaSuccess) err = CKKS_E_CUDA;
@@ -633,7 +626,7 @@ struct Eval {
       ConstArgs a;
       a.mods = c->d_mods;
       a.n = c->n;
-      a.k = k;
+      for (int l = 0; l <= x.level; ++l) a.kr[l] = host_sres(k, c->mod[l]);
       for (int i = 0; i < cn; ++i) {
         a.x0[i] = x.v[c0 + i].data;
         a.x1[i] = p1(x.v[c0 + i]);
@@ -897,8 +890,12 @@ struct Eval {
       a.out = b.inner_qp + c0 * o_ct;
       a.o_ct = o_ct;
       a.o_giant = o_giant;
-      const dim3 g(cn, (c->n + TPB - 1) / TPB, ext);
-      PROF_LAUNCH(c, PK_ELEMENTWISE, (u64)ext * cn * na, (k_mac_ext<<<g, TPB, 0, c->stream>>>(a)));
+      // limbs moved: babies 1.. and outputs per ciphertext, x's q-limbs, the plaintexts once
+      int npt = 0;
+      for (int j = 0; j < ng; ++j) npt += (int)lv.plan[j].items.size();
+      const u64 moved = (u64)cn * ext * (2 * (na - 1) + 2 * ng) + (u64)cn * 2 * nl + (u64)npt * ext;
+      const dim3 g(cn * ng, (c->n + TPB - 1) / TPB, ext);
+      PROF_LAUNCH(c, PK_BOOT_MAC, moved, (k_mac_ext<<<g, TPB, 0, c->stream>>>(a)));
       if (cudaGetLastError() != cudaSuccess) err = CKKS_E_CUDA;
     }
     auto inner = [&](int i, int j) { return b.inner_qp + i * o_ct + j * o_giant; };

@@ -570,7 +570,8 @@ int ckks_ctx_device_error(ckks_ctx *c) {
 const char *ckks_profile_kind_name(int k) {
   static const char *names[PK_COUNT] = {"ntt_fwd_pass_a", "ntt_fwd_pass_b", "ntt_inv_pass_a", "ntt_inv_pass_b",
                                         "bconv", "ks_inner_product", "ks_moddown_combine", "tensor",
-                                        "automorph", "rescale", "elementwise", "encode_decode", "bconv_tc"};
+                                        "automorph", "rescale", "elementwise", "encode_decode", "bconv_tc",
+                                        "boot_mac_ext", "boot_lincomb"};
   return (k >= 0 && k < PK_COUNT) ? names[k] : "unknown";
 }
 

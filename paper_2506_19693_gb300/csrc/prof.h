@@ -21,6 +21,8 @@ enum ProfKind {
   PK_ELEMENTWISE,
   PK_ENCODE,
   PK_BCONV_TC,
+  PK_BOOT_MAC,        // units: limbs of N words moved (algorithmic)
+  PK_BOOT_LINCOMB,    // units: limbs of N words moved (algorithmic)
   PK_COUNT
 };
 
