@@ -446,6 +446,9 @@ def run_gpu(args):
     reboot = None
     if not (args.no_reboot or args.small):
         reboot = run_reboot_step(bctx, wb, torch, stream, rank)
+    iterative = None
+    if not (args.no_iterative or args.small):
+        iterative = run_iterative(bctx, wb, BIN, BOUT, zb, torch, stream, reps=max(2, min(args.steps, 3)))
     uneven = None
     if not (args.no_uneven or args.small):
         uneven = run_uneven(ctx, w, torch, stream, rank, reps=max(3, args.steps), warmup=args.warmup)
@@ -482,7 +485,8 @@ def run_gpu(args):
                                      "batch": nb, "levels_consumed": 16, "cheb_degree": 60,
                                      "double_angles": 3, "input": "fresh encryptions at level 0"},
                 "slot_error": errors, "forms": forms,
-                "reboot_step": reboot, "uneven_batch": uneven, "tuning": tuning,
+                "reboot_step": reboot, "uneven_batch": uneven, "iterative_bootstrap": iterative,
+                "tuning": tuning,
                 "e2e": e2e, "roofline": roof, "alu_peaks": alu, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": int(launches),
                 "kernel_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]},
@@ -543,6 +547,24 @@ def run_uneven(ctx16, w, torch, stream, rank, reps, warmup):
     return {"ops_per_s_graph": 256 / (ms / 1e3), "ms_per_batch_graph": ms, "ops_per_s_eager_first_run": 256 / eager_s,
             "ops": "256: 1/3 HMult+relin+rescale, 1/3 Rot(2^k), 1/3 rescale; N in {2^15, 2^16} p=1/2; "
                    "levels U{4..23}", "replays": reps, "tuned_inner_group": tuned}
+
+
+def run_iterative(bctx, wb, BIN, BOUT, zb, torch, stream, reps, log2_k=16):
+    """The same 16 exhausted ciphertexts through two-pass (iterative)
+    bootstrapping (reading B12): throughput and slot error against one pass."""
+    bctx.bootstrap_iterative_batch(BIN, log2_k, out=BOUT)  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        bctx.bootstrap_iterative_batch(BIN, log2_k, out=BOUT)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    err = float(max(np.max(np.abs(bctx.decrypt_decode(BOUT[i]) - zb[i])) for i in range(2)))
+    return {"bootstraps_per_s": len(BIN) / (ms / 1e3), "ms_per_batch": ms, "batch": len(BIN), "log2_k": log2_k,
+            "slot_error": err, "reps": reps, "output_level": BOUT[0].level,
+            "clock": "CUDA events on the library stream, inputs resident"}
 
 
 def run_reboot_step(bctx, wb, torch, stream, rank):
@@ -637,6 +659,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-reboot", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
+    ap.add_argument("--no-iterative", action="store_true")
     ap.add_argument("--no-form-compare", action="store_true")
     ap.add_argument("--form", default="tensor", choices=["uint64", "tensor"],
                     help="basis conversion on the CUDA cores (uint64) or the tensor cores (tensor)")

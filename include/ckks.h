@@ -259,6 +259,17 @@ int ckks_boot_export(ckks_ctx *ctx, int64_t *coeffs, int count, double *cheb, in
  * ckks_boot_setup or ckks_boot_import (CKKS_E_STATE). */
 int ckks_bootstrap(ckks_ctx *ctx, const ckks_ct *in, ckks_ct *out);
 int ckks_bootstrap_batch(ckks_ctx *ctx, const ckks_ct *in, ckks_ct *out, int n);
+/* Iterative bootstrapping (Sec. 5.1 sizes tau_bs for it, citing Bae et al.
+ * 2022; reading B12): ct1 = Bootstrap(ct); the level-0 difference
+ * align(ct1, 0, Delta_in) - ct is multiplied by 2^log2_k and bootstrapped
+ * again (ct2); out = 2^log2_k ct1 - ct2 at the same level n_q - 1 - 16, with
+ * scale 2^log2_k * Delta_in * S / q_0.  Twice the work of ckks_bootstrap for
+ * an error about 2^log2_k times smaller, down to the inputs' own noise.
+ * All n inputs share one scale (CKKS_E_SCALE); 1 <= log2_k <= 30
+ * (CKKS_E_PARAM); log2_k must keep 2^log2_k times the first pass's error
+ * inside the sine's range (about 2^-22 at N = 2^16: log2_k <= 20).  Other
+ * requirements and errors as ckks_bootstrap_batch. */
+int ckks_bootstrap_iterative_batch(ckks_ctx *ctx, const ckks_ct *in, ckks_ct *out, int n, int log2_k);
 
 /* ---- batched variants: n independent ciphertexts in one set of launches -- */
 

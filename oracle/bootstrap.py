@@ -52,6 +52,13 @@ is named B1..B8 and listed in the design notes:
      joins the B10 sum as it is and each other inner_b is ModDown'd once
      before its giant rotation.  With the baby steps this cheap, the split
      is g = 2^(w-1) baby steps (16 x 4 at w = 5) instead of 2^ceil(w/2).
+  B12 Iterative bootstrapping (Bae et al. 2022, which Sec. 5.1 cites for the
+     depth tau_bs): ct1 = Bootstrap(ct) decrypts to m + e1; the difference
+     d = align(ct1, level 0, Delta) - ct carries e1, is multiplied by the
+     integer 2^k (no level) and bootstrapped again with the same scale label,
+     giving ct2 ~ 2^k e1 + e2.  The result 2^k ct1 - ct2, read at scale
+     2^k * (ct1's scale), decrypts to m - e2 / 2^k at ct1's level: the
+     division by 2^k is a change of the scale label, so no level is spent.
 Parity unpinned: nothing here (see tests/test_oracle_bootstrap.py).
 """
 from __future__ import annotations
@@ -523,6 +530,23 @@ class Evaluator:
             v = self.linear(v, lv, self.pts[ncts + i])
         v.scale = v.scale * delta / float(o.q[0])
         return v
+
+
+    # ---- B12
+    def bootstrap_iterative(self, ct: OCt, log2_k: int) -> OCt:
+        """Two bootstraps: the second refreshes 2^k times the first's error."""
+        o = self.o
+        delta = ct.scale
+        ct1 = self.bootstrap(ct)
+        d = o.sub(self.align(ct1, 0, delta), self.drop(ct, 0))
+        d.scale = delta
+        d2 = o.mul_int(d, 1 << log2_k)
+        d2.scale = delta
+        ct2 = self.bootstrap(d2)
+        up = o.mul_int(ct1, 1 << log2_k)
+        out = o.sub(up, ct2)
+        out.scale = ct1.scale * float(1 << log2_k)
+        return out
 
 
 def round_half_away(x: float) -> int:

@@ -108,6 +108,7 @@ SIGNATURES = {
     "ckks_boot_export": (_I, [_V, _V, _I, _V, _I]),
     "ckks_bootstrap": (_I, [_V, _CTP, _CTP]),
     "ckks_bootstrap_batch": (_I, [_V, _CTP, _CTP, _I]),
+    "ckks_bootstrap_iterative_batch": (_I, [_V, _CTP, _CTP, _I, _I]),
     "ckks_exec": (_I, [_V, _I]),
     "ckks_exec_capture": (_I, [_V, _I, _V, ctypes.POINTER(_V)]),
     "ckks_graph_launch": (_I, [_V, _V]),
@@ -554,6 +555,16 @@ class Context:
 
     def bootstrap(self, ct) -> "Ciphertext":
         return self.bootstrap_batch([ct])[0]
+
+    def bootstrap_iterative_batch(self, cts, log2_k: int, out=None) -> list:
+        out_level = self.n_q - 1 - 16
+        out = out if out is not None else [self.new_ct(out_level + 1) for _ in cts]
+        hi, ho = self._handles(cts), self._handles(out)
+        _check(self.lib.ckks_bootstrap_iterative_batch(self._h, hi, ho, len(cts), int(log2_k)),
+               "ckks_bootstrap_iterative_batch")
+        for i, c in enumerate(out):
+            c.level, c.scale = ho[i].level, ho[i].scale
+        return out
 
     # ---- host exchange ----
     def export_ct(self, ct: Ciphertext) -> np.ndarray:

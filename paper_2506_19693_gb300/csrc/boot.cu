@@ -1063,6 +1063,73 @@ struct Eval {
 
 }  // namespace
 
+static int boot_check(ckks_ctx *c, const ckks_ct *in, ckks_ct *out, int n) {
+  if (!c || !in || !out || n < 0) return CKKS_E_PARAM;
+  if (n == 0) return CKKS_OK;
+  if (!c->boot || !c->boot->have_consts) return CKKS_E_STATE;
+  const int out_level = c->boot->top - BOOT_DEPTH;
+  for (int i = 0; i < n; ++i) {
+    if (!in[i].data || in[i].log_n != (u32)c->log_n || in[i].n_limbs < 1 || !out[i].data) return CKKS_E_PARAM;
+    if ((int)out[i].n_limbs < out_level + 1) return CKKS_E_LEVEL;
+  }
+  if (c->relin.data == nullptr || !c->have_secret) return CKKS_E_NOKEY;
+  c->boot->slot_words = (size_t)2 * (c->boot->top + 1) * c->n;
+  return CKKS_OK;
+}
+
+// ModRaise, CoeffToSlot, EvalMod, SlotToCoeff (B1-B8) of ev.nct ciphertexts
+// read at level 0; the result sits at the output level with the circuit's
+// own scale (the caller applies Delta_in / q_0, B8).
+static BV boot_core(Eval &ev, const ckks_ct *in) {
+  ckks_ctx *c = ev.c;
+  BootState &b = *c->boot;
+  BV x = ev.mod_raise(in);
+  for (const LinLevel &lv : b.cts) {
+    BV y = ev.linear(x, lv);
+    ev.release(x);
+    x = y;
+  }
+  BV xc = ev.automorph(x, 2ULL * c->n - 1);
+  BV ure = ev.addsub(x, xc, false);
+  BV d = ev.addsub(x, xc, true);
+  ev.release(x);
+  ev.release(xc);
+  BV uim = ev.times_i(d, -1);
+  ev.release(d);
+  BV vre = ev.evalmod(ure, b.cheb);
+  ev.release(ure);
+  BV vim = ev.evalmod(uim, b.cheb);
+  ev.release(uim);
+  BV vi = ev.times_i(vim, 1);
+  ev.release(vim);
+  BV v = ev.add(vre, vi);
+  ev.release(vre);
+  ev.release(vi);
+  for (const LinLevel &lv : b.stc) {
+    BV y = ev.linear(v, lv);
+    ev.release(v);
+    v = y;
+  }
+  if (!ev.err && v.level != b.top - BOOT_DEPTH) ev.err = CKKS_E_STATE;
+  return v;
+}
+
+static int boot_copy_out(Eval &ev, const BV &v, ckks_ct *out, const double *scales) {
+  ckks_ctx *c = ev.c;
+  for (int i = 0; i < ev.nct; ++i) {
+    ckks_ct &o = out[i];
+    const size_t w = (size_t)(v.level + 1) * c->n;
+    CK_CUDA(cudaMemcpyAsync(o.data, v.v[i].data, w * 8, cudaMemcpyDeviceToDevice, c->stream));
+    CK_CUDA(cudaMemcpyAsync(o.data + (size_t)o.n_limbs * c->n, ev.p1(v.v[i]), w * 8, cudaMemcpyDeviceToDevice,
+                            c->stream));
+    o.level = v.level;
+    o.scale = scales[i];
+    o.is_ntt = 1;
+    o.log_n = c->log_n;
+  }
+  return CKKS_OK;
+}
+
 extern "C" {
 
 int ckks_boot_setup(ckks_ctx *c) {
@@ -1177,67 +1244,85 @@ int ckks_boot_export(ckks_ctx *c, int64_t *coeffs, int count, double *cheb, int 
 }
 
 int ckks_bootstrap_batch(ckks_ctx *c, const ckks_ct *in, ckks_ct *out, int n) {
-  if (!c || !in || !out || n < 0) return CKKS_E_PARAM;
-  if (n == 0) return CKKS_OK;
-  if (!c->boot || !c->boot->have_consts) return CKKS_E_STATE;
-  BootState &b = *c->boot;
-  const int out_level = b.top - BOOT_DEPTH;
-  for (int i = 0; i < n; ++i) {
-    if (!in[i].data || in[i].log_n != (u32)c->log_n || in[i].n_limbs < 1 || !out[i].data) return CKKS_E_PARAM;
-    if ((int)out[i].n_limbs < out_level + 1) return CKKS_E_LEVEL;
-  }
-  if (c->relin.data == nullptr || !c->have_secret) return CKKS_E_NOKEY;
-  b.slot_words = (size_t)2 * (b.top + 1) * c->n;
+  int rc = boot_check(c, in, out, n);
+  if (rc || n == 0) return rc;
   for (int i0 = 0; i0 < n; i0 += MAX_CTS) {
     const int cnt = std::min(MAX_CTS, n - i0);
     Eval ev(c, cnt);
-    BV x = ev.mod_raise(in + i0);
-    for (const LinLevel &lv : b.cts) {
-      BV y = ev.linear(x, lv);
-      ev.release(x);
-      x = y;
-    }
-    BV xc = ev.automorph(x, 2ULL * c->n - 1);
-    BV ure = ev.addsub(x, xc, false);
-    BV d = ev.addsub(x, xc, true);
-    ev.release(x);
-    ev.release(xc);
-    BV uim = ev.times_i(d, -1);
-    ev.release(d);
-    BV vre = ev.evalmod(ure, b.cheb);
-    ev.release(ure);
-    BV vim = ev.evalmod(uim, b.cheb);
-    ev.release(uim);
-    BV vi = ev.times_i(vim, 1);
-    ev.release(vim);
-    BV v = ev.add(vre, vi);
-    ev.release(vre);
-    ev.release(vi);
-    for (const LinLevel &lv : b.stc) {
-      BV y = ev.linear(v, lv);
-      ev.release(v);
-      v = y;
-    }
+    BV v = boot_core(ev, in + i0);
     if (ev.err) {
       ev.release(v);
       return ev.err;
     }
-    if (v.level != out_level) {
-      ev.release(v);
-      return CKKS_E_STATE;
-    }
-    for (int i = 0; i < cnt; ++i) {
-      ckks_ct &o = out[i0 + i];
-      const size_t w = (size_t)(v.level + 1) * c->n;
-      CK_CUDA(cudaMemcpyAsync(o.data, v.v[i].data, w * 8, cudaMemcpyDeviceToDevice, c->stream));
-      CK_CUDA(cudaMemcpyAsync(o.data + (size_t)o.n_limbs * c->n, ev.p1(v.v[i]), w * 8, cudaMemcpyDeviceToDevice,
-                              c->stream));
-      o.level = v.level;
-      o.scale = v.scale * in[i0 + i].scale / (double)c->mod[0];
-      o.is_ntt = 1;
-      o.log_n = c->log_n;
-    }
+    std::vector<double> sc(cnt);
+    for (int i = 0; i < cnt; ++i) sc[i] = v.scale * in[i0 + i].scale / (double)c->mod[0];
+    rc = boot_copy_out(ev, v, out + i0, sc.data());
     ev.release(v);
+    if (rc) return rc;
+  }
+  return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_CUDA;
+}
+
+// Iterative bootstrapping (reading B12): ct1 = Bootstrap(ct); the level-0
+// difference align(ct1, 0, Delta) - ct, times 2^k, is bootstrapped again with
+// the same scale label (ct2); the result 2^k ct1 - ct2 is read at scale
+// 2^k * scale(ct1), which divides the correction by 2^k without a level.
+int ckks_bootstrap_iterative_batch(ckks_ctx *c, const ckks_ct *in, ckks_ct *out, int n, int log2_k) {
+  if (log2_k < 1 || log2_k > 30) return CKKS_E_PARAM;
+  int rc = boot_check(c, in, out, n);
+  if (rc || n == 0) return rc;
+  const double delta = in[0].scale;
+  for (int i = 1; i < n; ++i)
+    if (in[i].scale != delta) return CKKS_E_SCALE;
+  const i64 two_k = (i64)1 << log2_k;
+  for (int i0 = 0; i0 < n; i0 += MAX_CTS) {
+    const int cnt = std::min(MAX_CTS, n - i0);
+    Eval ev(c, cnt);
+    BV v1 = boot_core(ev, in + i0);
+    if (ev.err) {
+      ev.release(v1);
+      return ev.err;
+    }
+    v1.scale *= delta / (double)c->mod[0];
+    const double out_scale = v1.scale * (double)two_k;
+    // the first bootstrap's error, at level 0 and scale Delta, times 2^k
+    BV a = ev.align(v1, 0, delta);
+    BV x0;
+    x0.level = 0;
+    x0.scale = delta;
+    for (int i = 0; i < cnt; ++i) x0.v.push_back(in[i0 + i]);
+    BV d = ev.err ? BV() : ev.addsub(a, x0, true);
+    ev.release(a);
+    BV d2 = ev.err ? BV() : ev.mul_int(d, two_k);
+    ev.release(d);
+    if (ev.err) {
+      ev.release(d2);
+      ev.release(v1);
+      return ev.err;
+    }
+    d2.scale = delta;
+    ev.sync_fields(d2);
+    BV v2 = boot_core(ev, d2.v.data());
+    ev.release(d2);
+    if (ev.err) {
+      ev.release(v2);
+      ev.release(v1);
+      return ev.err;
+    }
+    BV up = ev.mul_int(v1, two_k);
+    ev.release(v1);
+    BV o = ev.err ? BV() : ev.addsub(up, v2, true);
+    ev.release(up);
+    ev.release(v2);
+    if (ev.err) {
+      ev.release(o);
+      return ev.err;
+    }
+    o.scale = out_scale;
+    std::vector<double> sc(cnt, o.scale);
+    rc = boot_copy_out(ev, o, out + i0, sc.data());
+    ev.release(o);
+    if (rc) return rc;
   }
   return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_CUDA;
 }

@@ -109,3 +109,70 @@ def test_bootstrap_error_bound_full_ring():
             assert err <= 2.0 ** -12, err
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("tensor_form", [False, True], ids=["uint64", "tensor"])
+def test_iterative_bootstrap_bit_exact_with_oracle_constants(small, tensor_form):
+    """Reading B12 on the GPU: every limb of the two-pass result equals the
+    oracle's, with the oracle's constants imported."""
+    import oracle.bootstrap as ob
+    w, ctx, orc, plan, consts = small
+    ctx.set_form(tensor_form)
+    z = si.messages(24, 1, w.slots)[0]
+    delta = 2.0 ** w.log2_scale
+    m = orc.encode(z, delta)
+    co = orc.encrypt(orc.pt_from_int(m, 0), 0, delta, 78)
+    cg = ctx.encrypt(ctx.pt_from_int(m, 0), 0, delta, 78)
+    mine_c, mine_cheb = ctx.boot_export()
+    try:
+        ctx.boot_import(consts, plan.cheb)
+        out_g = ctx.bootstrap_iterative_batch([cg], 14)[0]
+        out_o = ob.Evaluator(orc, plan, consts).bootstrap_iterative(co, 14)
+        assert (out_g.level, out_g.scale) == (out_o.level, out_o.scale)
+        got = ctx.export_ct(out_g)
+        assert np.array_equal(got, out_o.data), int(np.sum(got != out_o.data))
+        assert ctx.device_error() == 0
+    finally:
+        ctx.set_form(False)
+        ctx.boot_import(list(mine_c), mine_cheb)
+
+
+def test_iterative_bootstrap_rejects_bad_arguments(small):
+    import paper_2506_19693_gb300 as ck
+    w, ctx, orc, plan, consts = small
+    delta = 2.0 ** w.log2_scale
+    z = si.messages(25, 2, w.slots)
+    a = ctx.encrypt(ctx.encode(z[0], 0, delta), 0, delta, 1)
+    b = ctx.encrypt(ctx.encode(z[1], 0, 2 * delta), 0, 2 * delta, 2)
+    with pytest.raises(ck.CkksError, match="E_SCALE|scale"):
+        ctx.bootstrap_iterative_batch([a, b], 10)
+    for k in (0, 31):
+        with pytest.raises(ck.CkksError):
+            ctx.bootstrap_iterative_batch([a], k)
+
+
+def test_iterative_bootstrap_error_full_ring():
+    """N = 2^16, 2^15 slots: the two-pass result is within 2^-32 of the input
+    (one pass: about 2^-22), at the single bootstrap's output level."""
+    import torch
+    import paper_2506_19693_gb300 as ck
+    torch.cuda.set_device(0)
+    w = si.BOOT
+    ctx = ck.Context.from_workload(w)
+    try:
+        ctx.keygen_boot(1)
+        ctx.boot_setup()
+        z = si.messages(26, 2, w.slots)
+        delta = 2.0 ** w.log2_scale
+        cts = [ctx.encrypt(ctx.encode(z[i], 0, delta), 0, delta, 610 + i) for i in range(2)]
+        one = ctx.bootstrap_batch(cts)
+        two = ctx.bootstrap_iterative_batch(cts, 16)
+        for i in range(2):
+            assert two[i].level == one[i].level == len(w.q_bits) - 17
+            assert two[i].scale == one[i].scale * 2.0 ** 16
+            e1 = np.max(np.abs(ctx.decrypt_decode(one[i]) - z[i]))
+            e2 = np.max(np.abs(ctx.decrypt_decode(two[i]) - z[i]))
+            assert e2 <= 2.0 ** -32 and e2 <= e1 * 2.0 ** -8, (e1, e2)
+        assert ctx.device_error() == 0
+    finally:
+        ctx.close()

@@ -179,3 +179,21 @@ def test_linear_level_decrypts_to_the_level_matrix(boot_env, which):
     assert (out.level, out.scale) == (lv.level - 1, delta * float(o.q[lv.level]) / float(o.q[lv.level]))
     err = np.max(np.abs(o.decrypt_decode(out) - ob.diag_apply(lv.diags, z)))
     assert err < 2.0 ** -30, err
+
+
+def test_iterative_bootstrap_refines_precision(boot_env):
+    """Reading B12: the second pass refreshes 2^k times the first pass's
+    error, so the result decrypts to the input about 2^k times closer, at the
+    single bootstrap's level, with the scale label multiplied by 2^k."""
+    w, plan, o, ev = boot_env
+    z = si.messages(16, 1, w.slots)[0]
+    delta = 2.0 ** w.log2_scale
+    ct = o.encrypt(o.pt_from_int(o.encode(z, delta), 0), 0, delta, 19)
+    one = ev.bootstrap(ct)
+    e1 = np.max(np.abs(o.decrypt_decode(one) - z))
+    k = 14
+    two = ev.bootstrap_iterative(ct, k)
+    e2 = np.max(np.abs(o.decrypt_decode(two) - z))
+    assert (two.level, two.scale) == (one.level, one.scale * 2.0 ** k)
+    assert e2 <= 2.0 ** -36, e2
+    assert e2 <= e1 * 2.0 ** -8, (e1, e2)
