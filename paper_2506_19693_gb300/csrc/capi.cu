@@ -1070,9 +1070,32 @@ int ckks_mul_relin_host(ckks_ctx *c, const uint64_t *a_host, const uint64_t *b_h
     c->stage_words = 3 * slot_w;
   }
   double sc = 0.0;
-  const int nchunks = (n + chunk - 1) / chunk;
-  for (int ci = 0; ci < nchunks; ++ci) {
-    const int s = ci % 3, i0 = ci * chunk, cnt = std::min(chunk, n - i0);
+  // chunk sizes: ramped up at the start and down at the end (chunk/4, chunk/2,
+  // chunk, ..., chunk/2, chunk/4), so that the first copy-in and the last
+  // product and copy-out, which overlap nothing, are short
+  std::vector<int> sizes;
+  {
+    std::vector<int> head, tail;
+    int left = n;
+    for (int d = 4; d >= 2 && left > 0; d /= 2) {
+      const int a = std::max(1, chunk / d);
+      if (left >= 2 * a + chunk) {
+        head.push_back(a);
+        tail.push_back(a);
+        left -= 2 * a;
+      }
+    }
+    sizes = head;
+    while (left > 0) {
+      const int a = std::min(chunk, left);
+      sizes.push_back(a);
+      left -= a;
+    }
+    sizes.insert(sizes.end(), tail.rbegin(), tail.rend());
+  }
+  const int nchunks = (int)sizes.size();
+  for (int ci = 0, i0 = 0; ci < nchunks; i0 += sizes[ci], ++ci) {
+    const int s = ci % 3, cnt = sizes[ci];
     u64 *sa = c->stage + (size_t)s * slot_w, *sb = sa + (size_t)chunk * in_w, *so = sb + (size_t)chunk * in_w;
     // inputs of this chunk, once the slot's previous products have left
     CK_CUDA(cudaStreamWaitEvent(c->h2d, c->ev_out[s], 0));
