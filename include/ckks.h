@@ -53,10 +53,10 @@ extern "C" {
 
 typedef struct ckks_ctx ckks_ctx;
 
-/* Parameter set Theta = {N, q, Delta} (Sec. 3).  N = 2^log_n (2^12..2^16).
- * The chain q_0..q_{n_q-1} and the special primes p_0..p_{n_p-1} are the
- * largest primes = 1 mod 2^17 below 2^bits, taken in chain order per bit size
- * (reading C1).  dnum = number of key-switching digits: alpha = ceil(n_q/dnum)
+/* Parameter set Theta = {N, q, Delta} (Sec. 3).  N = 2^log_n (2^12..2^17;
+ * Table 3 uses 2^16 and 2^17).  The chain q_0..q_{n_q-1} and the special
+ * primes p_0..p_{n_p-1} are the largest primes = 1 mod 2^max(17, log_n + 1)
+ * below 2^bits, taken in chain order per bit size (reading C1).  dnum = number of key-switching digits: alpha = ceil(n_q/dnum)
  * q-primes per digit (reading C7).  h = Hamming weight of the ternary secret,
  * sigma = standard deviation of the rounded Gaussian error (tail cut at
  * floor(6 sigma)).  log2_scale is the default scale used by ckks_encode when

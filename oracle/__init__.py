@@ -74,7 +74,7 @@ def _load():
         "oc_alpha": (P, [V]),
         "oc_moduli": (None, [V, _u64p]),
         "oc_psis": (None, [V, _u64p]),
-        "oc_gen_primes": (P, [P, _up, _u64p]),
+        "oc_gen_primes": (P, [P, _up, P, _u64p]),
         "oc_find_psi": (ctypes.c_uint64, [ctypes.c_uint64, ctypes.c_uint64]),
         "oc_splitmix_draw": (ctypes.c_uint64, [ctypes.c_uint64, ctypes.c_uint64]),
         "oc_ntt": (None, [V, _u64p, P, _ip]),
@@ -134,12 +134,13 @@ def _pint(seq) -> ctypes.Array:
     return arr
 
 
-def gen_primes(bits) -> list[int]:
-    """C1 prime chain for a list of bit sizes (q's then p's)."""
+def gen_primes(bits, log_n: int = 16) -> list[int]:
+    """C1 prime chain for a list of bit sizes (q's then p's): primes
+    = 1 mod 2^max(17, log2(2N))."""
     lib = _load()
     b = (ctypes.c_uint * len(bits))(*bits)
     out = np.zeros(len(bits), dtype=np.uint64)
-    if lib.oc_gen_primes(len(bits), b, _p64(out)) != 0:
+    if lib.oc_gen_primes(len(bits), b, max(17, log_n + 1), _p64(out)) != 0:
         raise ValueError("no prime chain for these bit sizes")
     return [int(x) for x in out]
 

@@ -145,18 +145,20 @@ typedef struct {
   okey *keys;
 } oc_ctx;
 
-/* C1: for each bit size b scan t = 2^b + 1 - m * 2^17, m = 1, 2, ...,
- * keep primes; the chain q_0..q_{n_q-1}, p_0..p_{n_p-1} takes, in order,
- * the next unused prime of its bit size.  Returns 0 or -1. */
-int oc_gen_primes(int count, const unsigned *bits, u64 *out) {
+/* C1: for each bit size b scan t = 2^b + 1 - m * 2^e, m = 1, 2, ..., with
+ * e = max(17, log2(2N)) (2N divides q - 1, so the 2N-th roots exist), keep
+ * primes; the chain q_0..q_{n_q-1}, p_0..p_{n_p-1} takes, in order, the next
+ * unused prime of its bit size.  Returns 0 or -1. */
+int oc_gen_primes(int count, const unsigned *bits, int log_step, u64 *out) {
   u64 next_m[64];
+  if (log_step < 17 || log_step > 40) return -1;
   for (int b = 0; b < 64; b++) next_m[b] = 1;
   for (int i = 0; i < count; i++) {
     unsigned b = bits[i];
     if (b < 20 || b > 62) return -1;
     for (;;) {
       u64 m = next_m[b]++;
-      u64 step = m << 17;
+      u64 step = m << log_step;
       if (step >= ((u64)1 << b)) return -1;
       u64 t = ((u64)1 << b) + 1 - step;
       if (is_prime_u64(t)) { out[i] = t; break; }
@@ -175,7 +177,7 @@ u64 oc_find_psi(u64 q, u64 n) {
 
 oc_ctx *oc_create(int log_n, int n_q, int n_p, int dnum, const unsigned *q_bits,
                   const unsigned *p_bits, int h, double sigma) {
-  if (log_n < 2 || log_n > 16 || n_q < 1 || n_p < 1 || dnum < 1 || n_q + n_p > OC_MAXMOD)
+  if (log_n < 2 || log_n > 17 || n_q < 1 || n_p < 1 || dnum < 1 || n_q + n_p > OC_MAXMOD)
     return NULL;
   oc_ctx *c = (oc_ctx *)calloc(1, sizeof(oc_ctx));
   c->log_n = log_n;
@@ -191,7 +193,7 @@ oc_ctx *oc_create(int log_n, int n_q, int n_p, int dnum, const unsigned *q_bits,
   unsigned bits[OC_MAXMOD];
   for (int i = 0; i < n_q; i++) bits[i] = q_bits[i];
   for (int i = 0; i < n_p; i++) bits[n_q + i] = p_bits[i];
-  if (oc_gen_primes(n_q + n_p, bits, c->mod) != 0) { free(c); return NULL; }
+  if (oc_gen_primes(n_q + n_p, bits, log_n + 1 > 17 ? log_n + 1 : 17, c->mod) != 0) { free(c); return NULL; }
   for (int i = 0; i < n_q + n_p; i++) c->psi[i] = oc_find_psi(c->mod[i], c->n);
   return c;
 }

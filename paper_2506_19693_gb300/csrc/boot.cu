@@ -43,7 +43,7 @@ constexpr int LEVELS_STC = 3;
 constexpr int EVALMOD_DEPTH = 7 + DOUBLE_ANGLES;
 constexpr int BOOT_DEPTH = LEVELS_CTS + EVALMOD_DEPTH + LEVELS_STC;  // 16
 constexpr int MAXB = 16;   // ciphertexts per fused launch
-constexpr int MAXA = 16;   // baby steps
+constexpr int MAXA = 32;   // baby steps (2^(w-1) at a level of w <= 6 stages: N <= 2^17)
 constexpr int MAXT = 8;    // terms of an integer linear combination
 
 // [k]_q of a signed integer (host)
@@ -386,9 +386,12 @@ int boot_ensure_plan(ckks_ctx *c) {
     for (auto &gi : b.stc[i].plan) idx += (int)gi.items.size();
     b.stc[i].n_const = idx - b.stc[i].first_const;
   }
-  for (auto &lv : b.cts)
-    for (auto &gi : lv.plan)
-      if ((int)gi.items.size() > MAXA || lv.g > MAXA) return CKKS_E_PARAM;
+  for (const auto *lvs : {&b.cts, &b.stc})
+    for (const LinLevel &lv : *lvs) {
+      if (lv.g > MAXA || (int)lv.plan.size() > MAXG) return CKKS_E_PARAM;
+      for (auto &gi : lv.plan)
+        if ((int)gi.items.size() > MAXA) return CKKS_E_PARAM;
+    }
   b.n_consts = idx;
   b.planned = true;
   return CKKS_OK;

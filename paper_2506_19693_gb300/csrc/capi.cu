@@ -431,7 +431,7 @@ const char *ckks_status_str(int s) {
 int ckks_ctx_create(const ckks_params *p, void *stream, ckks_ctx **out) {
   if (!p || !out) return CKKS_E_PARAM;
   *out = nullptr;
-  if (p->log_n < 12 || p->log_n > 16 || p->n_q < 1 || p->n_q > CKKS_MAX_Q || p->n_p < 1 ||
+  if (p->log_n < 12 || p->log_n > 17 || p->n_q < 1 || p->n_q > CKKS_MAX_Q || p->n_p < 1 ||
       p->n_p > CKKS_MAX_P || p->dnum < 1 || p->n_q + p->n_p > MAX_MODS || p->h < 1 ||
       p->h > (1u << p->log_n) || !(p->sigma > 0))
     return CKKS_E_PARAM;
@@ -454,7 +454,10 @@ int ckks_ctx_create(const ckks_params *p, void *stream, ckks_ctx **out) {
   unsigned bits[MAX_MODS];
   for (int i = 0; i < c->n_q; ++i) bits[i] = p->q_bits[i];
   for (int i = 0; i < c->n_p; ++i) bits[c->n_q + i] = p->p_bits[i];
-  if (host_gen_primes(c->n_q + c->n_p, bits, c->mod) != CKKS_OK) { delete c; return CKKS_E_PARAM; }
+  if (host_gen_primes(c->n_q + c->n_p, bits, std::max(17, c->log_n + 1), c->mod) != CKKS_OK) {
+    delete c;
+    return CKKS_E_PARAM;
+  }
   for (int i = 0; i < c->n_q + c->n_p; ++i) c->psi[i] = host_find_psi(c->mod[i], c->n);
   int rc = build_tables(c);
   if (rc) { ckks_ctx_destroy(c); return rc; }

@@ -106,7 +106,7 @@ struct ckks_ctx {
 };
 
 // ---- host parameter derivation (params_host.cpp) ----
-int host_gen_primes(int count, const unsigned *bits, u64 *out);
+int host_gen_primes(int count, const unsigned *bits, int log_step, u64 *out);
 u64 host_find_psi(u64 q, u64 n);
 u64 host_powmod(u64 b, u64 e, u64 q);
 u64 host_mulmod(u64 a, u64 b, u64 q);

@@ -24,7 +24,9 @@ namespace {
 
 constexpr int LB = 8;            // log2 of the row length handled by pass B
 constexpr int BROW = 1 << LB;    // 256
-constexpr int CA = 16;           // columns per pass-A tile
+// columns per pass-A tile: 16 (128-byte row segments); 8 at 2^9 rows, so that
+// the 2^LH x CA tile stays within the 48 KB of static shared memory
+__host__ __device__ constexpr int ca_of(int lh) { return lh >= 9 ? 8 : 16; }
 constexpr int THREADS = 256;     // pass A; pass B runs 16 threads per row of its tile
 // pass B tiles: RBT rows per CTA (16 or 8, chosen per context by ckks_tune_ntt)
 template <int RBT>
@@ -122,7 +124,7 @@ constexpr u64 APPROX_INV_BOUND = 1ULL << 61;
 // from the limb's modulus (uniform per CTA).
 template <int LH, int S1, bool LOOSE>
 __device__ __forceinline__ void fwd_a_body(const NttParams &prm, u64 *sm, int mi, const u64 *src, u64 *dst) {
-  constexpr int H = 1 << LH, S2 = LH - S1;
+  constexpr int H = 1 << LH, S2 = LH - S1, CA = ca_of(LH);
   const u64 q = prm.mods[mi].q, twoq = 2 * q;
   const ulonglong2 *tw = prm.tw + (size_t)mi * prm.n;
   const int c0 = blockIdx.x * CA;
@@ -147,17 +149,65 @@ __device__ __forceinline__ void fwd_a_body(const NttParams &prm, u64 *sm, int mi
   }
 }
 
+// Pass A at 2^9 rows: three register phases of three stages each (8 values
+// per thread), the first from global memory, the last to it, shared memory
+// between.  Phase p starts at stage 3p, where the column splits into 2^(3p)
+// blocks of 2^(9-3p) rows; block blk takes twiddle group 2^(3p) + blk.
+template <bool LOOSE>
+__device__ __forceinline__ void fwd_a3_body(const NttParams &prm, u64 *sm, int mi, const u64 *src, u64 *dst) {
+  constexpr int H = 1 << 9, CA = ca_of(9);
+  const u64 q = prm.mods[mi].q, twoq = 2 * q;
+  const ulonglong2 *tw = prm.tw + (size_t)mi * prm.n;
+  const int c0 = blockIdx.x * CA;
+  for (int x = threadIdx.x; x < (H >> 3) * CA; x += THREADS) {  // stages 0..2: rows r0 + 64 e
+    const int c = x % CA, r0 = x / CA;
+    u64 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = src[(size_t)(r0 + (e << 6)) * BROW + c0 + c];
+    fwd_step<3, LOOSE>(v, 1u, tw, q, twoq);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) sm[(r0 + (e << 6)) * CA + c] = v[e];
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < (H >> 3) * CA; x += THREADS) {  // stages 3..5: rows 64 blk + r0 + 8 e
+    const int c = x % CA, y = x / CA, blk = y >> 3, r0 = y & 7;
+    u64 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = sm[((blk << 6) + r0 + (e << 3)) * CA + c];
+    fwd_step<3, LOOSE>(v, 8u + blk, tw, q, twoq);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) sm[((blk << 6) + r0 + (e << 3)) * CA + c] = v[e];
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < (H >> 3) * CA; x += THREADS) {  // stages 6..8: rows 8 blk + e
+    const int c = x % CA, blk = x / CA;
+    u64 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = sm[((blk << 3) + e) * CA + c];
+    fwd_step<3, LOOSE>(v, 64u + blk, tw, q, twoq);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) dst[(size_t)((blk << 3) + e) * BROW + c0 + c] = v[e];
+  }
+}
+
 template <int LH, int S1>
 __global__ void __launch_bounds__(THREADS, 3) fwd_pass_a(const NttParams prm) {
-  __shared__ u64 sm[(1 << LH) * CA];
+  __shared__ u64 sm[(1 << LH) * ca_of(LH)];
   const int limb = blockIdx.y, poly = blockIdx.z;
   const int mi = prm.mod_of_limb[limb];
   const u64 *src = prm.src.p[poly] + (size_t)limb * prm.n;
   u64 *dst = prm.dst.p[poly] + (size_t)limb * prm.n;
-  if (prm.mods[mi].q < LOOSE_BOUND)
-    fwd_a_body<LH, S1, true>(prm, sm, mi, src, dst);
-  else
-    fwd_a_body<LH, S1, false>(prm, sm, mi, src, dst);
+  if constexpr (LH == 9) {
+    if (prm.mods[mi].q < LOOSE_BOUND)
+      fwd_a3_body<true>(prm, sm, mi, src, dst);
+    else
+      fwd_a3_body<false>(prm, sm, mi, src, dst);
+  } else {
+    if (prm.mods[mi].q < LOOSE_BOUND)
+      fwd_a_body<LH, S1, true>(prm, sm, mi, src, dst);
+    else
+      fwd_a_body<LH, S1, false>(prm, sm, mi, src, dst);
+  }
 }
 
 template <int LH, bool LOOSE, int RB>
@@ -273,7 +323,7 @@ __global__ void __launch_bounds__(threads_b<RB>(), RB == 16 ? 4 : 8) inv_pass_b(
 
 template <int LH, int S1, bool APPROX>
 __device__ __forceinline__ void inv_a_body(const NttParams &prm, u64 *sm, int mi, u64 *dst) {
-  constexpr int H = 1 << LH, S2 = LH - S1;
+  constexpr int H = 1 << LH, S2 = LH - S1, CA = ca_of(LH);
   const ModInfo m = prm.mods[mi];
   const u64 q = m.q, twoq = 2 * q, ninv = m.ninv, ninv_s = m.ninv_s;
   const u64 r = APPROX ? 2 * twoq : twoq;
@@ -309,20 +359,69 @@ __device__ __forceinline__ void inv_a_body(const NttParams &prm, u64 *sm, int mi
   }
 }
 
+// The inverse of fwd_a3_body: stages 8..6 on blocks of 8 rows, 5..3 on
+// blocks of 64, then 2..1 and the last stage with N^-1 folded in.
+template <bool APPROX>
+__device__ __forceinline__ void inv_a3_body(const NttParams &prm, u64 *sm, int mi, u64 *dst) {
+  constexpr int H = 1 << 9, CA = ca_of(9);
+  const ModInfo m = prm.mods[mi];
+  const u64 q = m.q, twoq = 2 * q, ninv = m.ninv, ninv_s = m.ninv_s;
+  const u64 r = APPROX ? 2 * twoq : twoq;
+  const ulonglong2 *tw = prm.tw + (size_t)mi * prm.n;
+  const int c0 = blockIdx.x * CA;
+  for (int x = threadIdx.x; x < (H >> 3) * CA; x += THREADS) {
+    const int c = x % CA, blk = x / CA;
+    u64 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = dst[(size_t)((blk << 3) + e) * BROW + c0 + c];
+    inv_step<3, APPROX>(v, 64u + blk, tw, q, twoq);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) sm[((blk << 3) + e) * CA + c] = v[e];
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < (H >> 3) * CA; x += THREADS) {
+    const int c = x % CA, y = x / CA, blk = y >> 3, r0 = y & 7;
+    u64 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = sm[((blk << 6) + r0 + (e << 3)) * CA + c];
+    inv_step<3, APPROX>(v, 8u + blk, tw, q, twoq);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) sm[((blk << 6) + r0 + (e << 3)) * CA + c] = v[e];
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < (H >> 3) * CA; x += THREADS) {
+    const int c = x % CA, r0 = x / CA;
+    u64 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = sm[(r0 + (e << 6)) * CA + c];
+    inv_step<3, APPROX, 1>(v, 1u, tw, q, twoq);
+    const ulonglong2 w0 = __ldg(&tw[0]);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const u64 a = v[e], b = v[e + 4];
+      dst[(size_t)(r0 + (e << 6)) * BROW + c0 + c] = shoup(a + b, ninv, ninv_s, q);
+      dst[(size_t)(r0 + ((e + 4) << 6)) * BROW + c0 + c] = shoup(a + r - b, w0.x, w0.y, q);
+    }
+  }
+}
+
 template <int LH, int S1, bool APPROX>
 __global__ void __launch_bounds__(THREADS, 4) inv_pass_a(const NttParams prm) {
-  __shared__ u64 sm[(1 << LH) * CA];
+  __shared__ u64 sm[(1 << LH) * ca_of(LH)];
   const int limb = blockIdx.y, poly = blockIdx.z;
   const int mi = prm.mod_of_limb[limb];
   u64 *dst = prm.dst.p[poly] + (size_t)limb * prm.n;
-  inv_a_body<LH, S1, APPROX>(prm, sm, mi, dst);
+  if constexpr (LH == 9)
+    inv_a3_body<APPROX>(prm, sm, mi, dst);
+  else
+    inv_a_body<LH, S1, APPROX>(prm, sm, mi, dst);
 }
 
 template <int LH, int RB, bool APPROX>
 void launch_inv(ckks_ctx *c, const NttParams &prm, int npoly) {
   constexpr int S1 = (LH + 1) / 2;
   const unsigned long long units = (unsigned long long)prm.n_limbs * npoly;
-  dim3 ga(BROW / CA, prm.n_limbs, npoly), gb((1 << LH) / RB, prm.n_limbs, npoly);
+  dim3 ga(BROW / ca_of(LH), prm.n_limbs, npoly), gb((1 << LH) / RB, prm.n_limbs, npoly);
   PROF_LAUNCH(c, PK_NTT_INV_B, units, (inv_pass_b<LH, RB, APPROX><<<gb, threads_b<RB>(), 0, c->stream>>>(prm)));
   PROF_LAUNCH(c, PK_NTT_INV_A, units, (inv_pass_a<LH, S1, APPROX><<<ga, THREADS, 0, c->stream>>>(prm)));
 }
@@ -340,7 +439,7 @@ void launch_lh(ckks_ctx *c, const NttParams &prm, int npoly, bool inverse, bool 
   const int H = 1 << LH;
   cudaStream_t st = c->stream;
   const unsigned long long units = (unsigned long long)prm.n_limbs * npoly;
-  dim3 ga(BROW / CA, prm.n_limbs, npoly);
+  dim3 ga(BROW / ca_of(LH), prm.n_limbs, npoly);
   PROF_LAUNCH(c, PK_NTT_FWD_A, units, (fwd_pass_a<LH, S1><<<ga, THREADS, 0, st>>>(prm)));
   if (c->ntt_rows == 8) {
     dim3 gb(H / 8, prm.n_limbs, npoly);
@@ -383,6 +482,7 @@ int launch_ntt(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, i
       case 6: launch_lh<6>(c, prm, cnt, inverse, approx); break;
       case 7: launch_lh<7>(c, prm, cnt, inverse, approx); break;
       case 8: launch_lh<8>(c, prm, cnt, inverse, approx); break;
+      case 9: launch_lh<9>(c, prm, cnt, inverse, approx); break;
       default: return CKKS_E_PARAM;
     }
   }

@@ -59,18 +59,20 @@ static bool is_prime(u64 n) {
   return true;
 }
 
-// C1: per bit size b, candidates 2^b + 1 - m 2^17 (m = 1, 2, ...), primes kept
-// in order of discovery; each chain entry takes the next one of its size.
-int host_gen_primes(int count, const unsigned *bits, u64 *out) {
+// C1: per bit size b, candidates 2^b + 1 - m 2^e (m = 1, 2, ...) with
+// e = log_step = max(17, log2(2N)), primes kept in order of discovery; each
+// chain entry takes the next one of its size.
+int host_gen_primes(int count, const unsigned *bits, int log_step, u64 *out) {
   u64 cursor[64];
+  if (log_step < 17 || log_step > 40) return CKKS_E_PARAM;
   for (int i = 0; i < 64; ++i) cursor[i] = 1;
   for (int i = 0; i < count; ++i) {
     unsigned b = bits[i];
     if (b < 20 || b > 62) return CKKS_E_PARAM;
     while (true) {
       u64 m = cursor[b]++;
-      if ((m << 17) >= (1ULL << b)) return CKKS_E_PARAM;
-      u64 cand = (1ULL << b) + 1 - (m << 17);
+      if ((m << log_step) >= (1ULL << b)) return CKKS_E_PARAM;
+      u64 cand = (1ULL << b) + 1 - (m << log_step);
       if (is_prime(cand)) { out[i] = cand; break; }
     }
   }

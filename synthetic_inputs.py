@@ -71,6 +71,18 @@ BOOT = Workload("n65536_boot_L24_dnum3_b16", 16, BOOT_Q_BITS, (61,) * 9, 3, 50.0
 BOOT_SMALL = Workload("n4096_boot_L24_dnum3", 12, BOOT_Q_BITS, (61,) * 9, 3, 50.0, batch=2)
 
 
+# N = 2^17 (Table 3's eMLP-2/3 ring): a short chain the CPU oracle handles in
+# seconds (4 ciphertext primes, 2 special), and the bootstrapping chain of
+# eMLP-2, l = 27 = 11 + 16: q0 ~ 2^60, q1..q14 ~ 2^50 (11 user levels plus
+# SlotToCoeff), q15..q27 ~ 2^60 (EvalMod and CoeffToSlot), 10 special primes
+# of 61 bits (alpha = ceil(28/3)), dnum = 3, Delta = 2^50 (Table 3's 2^59
+# would need q0 >= 2^69 for the same message ratio, beyond a 64-bit word).
+N17 = Workload("n131072_L4_dnum2", 17, (60,) + (55,) * 3, (61,) * 2, 2, 55.0,
+               batch=2, rot_steps=(1, -1, 1 << 15))
+BOOT17_Q_BITS = (60,) + (50,) * 14 + (60,) * 13
+BOOT17 = Workload("n131072_boot_L27_dnum3_b8", 17, BOOT17_Q_BITS, (61,) * 10, 3, 50.0, batch=8)
+
+
 def rng(seed: int, stream: str) -> np.random.Generator:
     """An independent numpy generator per (seed, stream name)."""
     tag = int.from_bytes(stream.encode()[:8].ljust(8, b"\0"), "little")

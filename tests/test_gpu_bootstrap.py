@@ -176,3 +176,28 @@ def test_iterative_bootstrap_error_full_ring():
         assert ctx.device_error() == 0
     finally:
         ctx.close()
+
+
+def test_bootstrap_error_bound_n17():
+    """N = 2^17 with 2^16 slots on the eMLP-2 chain (l = 27 = 11 + 16): the
+    levels are 6, 5 and 5 stages wide (32 baby steps at the widest); output at
+    level 11, slots within 2^-12 of the input."""
+    import torch
+    import paper_2506_19693_gb300 as ck
+    torch.cuda.set_device(0)
+    w = si.BOOT17
+    ctx = ck.Context.from_workload(w)
+    try:
+        ctx.keygen_boot(1)
+        ctx.boot_setup()
+        z = si.messages(27, 2, w.slots)
+        delta = 2.0 ** w.log2_scale
+        cts = [ctx.encrypt(ctx.encode(z[i], 0, delta), 0, delta, 620 + i) for i in range(2)]
+        outs = ctx.bootstrap_batch(cts)
+        for i in range(2):
+            assert outs[i].level == len(w.q_bits) - 17 == 11
+            err = np.max(np.abs(ctx.decrypt_decode(outs[i]) - z[i]))
+            assert err <= 2.0 ** -12, err
+        assert ctx.device_error() == 0
+    finally:
+        ctx.close()

@@ -61,14 +61,16 @@ def test_error_distribution_matches_rounded_gaussian(toy_oracle):
 
 
 # ---------------------------------------------------------------- C1, C2
-def test_prime_chain_is_prime_ntt_friendly_and_complete():
+@pytest.mark.parametrize("log_n", [16, 17])
+def test_prime_chain_is_prime_ntt_friendly_and_complete(log_n):
     sympy = pytest.importorskip("sympy")
     bits = [61, 55, 55, 55, 40, 61, 61]
-    primes = oracle.gen_primes(bits)
+    primes = oracle.gen_primes(bits, log_n)
+    step = 1 << max(17, log_n + 1)  # 2N divides q - 1
     assert len(set(primes)) == len(primes)
     for b, q in zip(bits, primes):
         assert sympy.isprime(q)
-        assert q % (1 << 17) == 1
+        assert q % step == 1
         assert q < (1 << b)
     # completeness: no skipped candidate of the scan is prime
     for b in (55, 61):
@@ -76,7 +78,7 @@ def test_prime_chain_is_prime_ntt_friendly_and_complete():
         m = 1
         seen = []
         while len(seen) < len(chosen):
-            t = (1 << b) + 1 - m * (1 << 17)
+            t = (1 << b) + 1 - m * step
             if sympy.isprime(t):
                 seen.append(t)
             m += 1
@@ -98,6 +100,10 @@ def test_psi_is_primitive_2n_root_from_smallest_nonresidue():
             while legendre_symbol(g, q) != -1:
                 g += 1
             assert psi == pow(g, (q - 1) // (2 * n), q)
+    for q in oracle.gen_primes([55, 60], 17):  # N = 2^17 takes primes = 1 mod 2^18
+        n = 1 << 17
+        psi = _oracle_psi(q, n)
+        assert pow(psi, n, q) == q - 1
 
 
 def _oracle_psi(q, n):
@@ -399,3 +405,21 @@ def test_tensor_decrypts_under_s_squared(tiny_oracle):
     ea, eb = [int(v) for v in o.enc_error(1)], [int(v) for v in o.enc_error(2)]
     want = negacyclic_mul_int([int(x) + y for x, y in zip(ma, ea)], [int(x) + y for x, y in zip(mb, eb)], n)
     assert [centred(x - y, Q) for x, y in zip(dec, want)] == [0] * n
+
+
+def test_ring_2_17_product_and_rotations_decrypt_to_slot_math():
+    """N = 2^17 (Table 3's eMLP-2/3 ring; primes = 1 mod 2^18): the merged
+    product and rotations by 1 and 2^15 decrypt to the slot-wise product and
+    the cyclic shifts of the 2^16 slots."""
+    import synthetic_inputs as si
+    w = si.N17
+    o = oracle.Oracle(w.log_n, w.q_bits, w.p_bits, w.dnum, w.h, w.sigma)
+    assert all(q % (1 << 18) == 1 for q in o.moduli)
+    o.keygen(3)
+    o.gen_rotation_keys([1, 1 << 15])
+    z = si.messages(1, 2, w.slots)
+    sc, lv = 2.0 ** w.log2_scale, len(w.q_bits) - 1
+    a, b = (o.encrypt(o.pt_from_int(o.encode(z[i], sc), lv), lv, sc, 1 + i) for i in range(2))
+    assert np.max(np.abs(o.decrypt_decode(o.mul_relin_rescale(a, b)) - z[0] * z[1])) < 2.0 ** -30
+    for k in (1, 1 << 15):
+        assert np.max(np.abs(o.decrypt_decode(o.rotate(a, k)) - np.roll(z[0], -k))) < 2.0 ** -30
