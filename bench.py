@@ -446,6 +446,9 @@ def run_gpu(args):
     reboot = None
     if not (args.no_reboot or args.small):
         reboot = run_reboot_step(bctx, wb, torch, stream, rank)
+    n_scaling = None
+    if not (args.no_n_scaling or args.small):
+        n_scaling = run_n_scaling(torch, stream, reps=max(2, min(args.steps, 3)))
     iterative = None
     if not (args.no_iterative or args.small):
         iterative = run_iterative(bctx, wb, BIN, BOUT, zb, torch, stream, reps=max(2, min(args.steps, 3)))
@@ -486,6 +489,7 @@ def run_gpu(args):
                                      "double_angles": 3, "input": "fresh encryptions at level 0"},
                 "slot_error": errors, "forms": forms,
                 "reboot_step": reboot, "uneven_batch": uneven, "iterative_bootstrap": iterative,
+                "n_scaling": n_scaling,
                 "tuning": tuning,
                 "e2e": e2e, "roofline": roof, "alu_peaks": alu, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": int(launches),
@@ -547,6 +551,77 @@ def run_uneven(ctx16, w, torch, stream, rank, reps, warmup):
     return {"ops_per_s_graph": 256 / (ms / 1e3), "ms_per_batch_graph": ms, "ops_per_s_eager_first_run": 256 / eager_s,
             "ops": "256: 1/3 HMult+relin+rescale, 1/3 Rot(2^k), 1/3 rescale; N in {2^15, 2^16} p=1/2; "
                    "levels U{4..23}", "replays": reps, "tuned_inner_group": tuned}
+
+
+def run_n_scaling(torch, stream, reps):
+    """Ring-degree scaling (the paper's Fig. 3 axis): merged HMult+relin+rescale
+    on the 24 + 8 prime chain at N = 2^15, 2^16, 2^17 with the same number of
+    coefficients per batch (128, 64, 32 pairs), and bootstrapping at N = 2^17
+    (2^16 slots, Table 3's eMLP-2 chain l = 27, 8 ciphertexts)."""
+    import paper_2506_19693_gb300 as ck
+    w = si.PLAIN
+    level = len(w.q_bits) - 1
+    scale = 2.0 ** w.log2_scale
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    out = {"hmult": {}}
+    for log_n in (15, 16, 17):
+        ctx = ck.Context(log_n, w.q_bits, w.p_bits, w.dnum, w.h, w.sigma, w.log2_scale, stream=stream)
+        try:
+            ctx.keygen(9)
+            B = 64 << 16 >> log_n
+            z = si.messages(700 + log_n, 2, 1 << (log_n - 1))
+            base = [ctx.encrypt(ctx.encode(z[i], level, scale), level, scale, 900 + i) for i in range(2)]
+            cts = [ctx.new_ct(level + 1) for _ in range(2 * B)]
+            for i, c in enumerate(cts):  # pairs (base 0, base 1)
+                c.data.copy_(base[i // B].data)
+                c.level, c.scale = base[i // B].level, base[i // B].scale
+            outs = [ctx.new_ct(level + 1) for _ in range(B)]
+            ctx.tune(level, B)
+            ctx.tune_ntt(16)
+            ctx.mul_relin_batch(cts[:B], cts[B:], outs, rescale=ck.RESCALE_MERGED)
+            torch.cuda.synchronize()
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            for _ in range(reps):
+                ctx.mul_relin_batch(cts[:B], cts[B:], outs, rescale=ck.RESCALE_MERGED)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            err = float(np.max(np.abs(ctx.decrypt_decode(outs[0]) - z[0] * z[1])))
+            out["hmult"][f"n{1 << log_n}"] = {"pairs": B, "hmult_per_s": B / (ms / 1e3),
+                                              "coeff_hmult_per_s": B * (1 << log_n) / (ms / 1e3),
+                                              "ms_per_batch": ms, "slot_error": err}
+        finally:
+            ctx.close()
+    wb = si.BOOT17
+    bctx = ck.Context.from_workload(wb, stream=stream)
+    try:
+        bctx.keygen_boot(2)
+        bctx.boot_setup()
+        nb = wb.batch
+        db = 2.0 ** wb.log2_scale
+        zb = si.messages(710, nb, wb.slots)
+        seeds = si.enc_seeds(710, nb)
+        bin_ = [bctx.encrypt(bctx.encode(zb[i], 0, db), 0, db, seeds[i]) for i in range(nb)]
+        bout = [bctx.new_ct(len(wb.q_bits) - 16) for _ in range(nb)]
+        bctx.tune(len(wb.q_bits) - 1, nb)
+        bctx.tune_ntt(16)
+        bctx.bootstrap_batch(bin_, bout)
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        for _ in range(reps):
+            bctx.bootstrap_batch(bin_, bout)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        err = float(max(np.max(np.abs(bctx.decrypt_decode(bout[i]) - zb[i])) for i in range(2)))
+        out["bootstrap_n131072"] = {"workload": wb.name, "batch": nb, "bootstraps_per_s": nb / (ms / 1e3),
+                                    "ms_per_batch": ms, "slot_error": err, "output_level": bout[0].level}
+    finally:
+        bctx.close()
+    out["clock"] = "CUDA events on the library stream, inputs resident; untimed tuning and warm-up"
+    return out
 
 
 def run_iterative(bctx, wb, BIN, BOUT, zb, torch, stream, reps, log2_k=16):
@@ -660,6 +735,7 @@ def main():
     ap.add_argument("--no-reboot", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--no-iterative", action="store_true")
+    ap.add_argument("--no-n-scaling", action="store_true")
     ap.add_argument("--no-form-compare", action="store_true")
     ap.add_argument("--form", default="tensor", choices=["uint64", "tensor"],
                     help="basis conversion on the CUDA cores (uint64) or the tensor cores (tensor)")
