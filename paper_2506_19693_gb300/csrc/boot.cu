@@ -167,12 +167,16 @@ __global__ void k_cheb(double *c, int d, double kr, int r) {
 // ---------------------------------------------------------------- batched kernels
 // ---- double-hoisted linear levels (B11) ----
 constexpr int MAXG = 4;  // giant steps of a double-hoisted level
+constexpr int MB_K = 128;          // coefficients per CTA of k_mac_ext
+constexpr int MB_THREADS = 512;    // 4 groups of MB_K threads, each a share of the ciphertexts
+constexpr int MB_GROUPS = MB_THREADS / MB_K;
 struct MacExtArgs {
   const ModInfo *mods;
   u32 n;
-  int ext, na, ng, nq;             // nq = l + 1 q-limbs
+  int ext, na, ng, nq, cn, npt;    // nq = l + 1 q-limbs; npt plaintexts of the level
   unsigned char mod_of[MAX_MODS];
-  const u64 *pt[MAXG][MAXA];       // [giant][baby] plaintext over Q_l P, or null
+  const u64 *pt[MAXG * MAXA];      // the level's plaintexts over Q_l P, slot s
+  signed char slot[MAXG][MAXA];    // [giant][baby] -> slot, or -1 (no diagonal)
   const u64 *xq;                   // babies a >= 1: [ct][baby][2][ext][N] (slot 0 unused)
   size_t x_ct, x_baby;
   const u64 *c0[MAXB], *c1[MAXB];  // baby 0 = P x, formed on the fly from x over q_0..q_l
@@ -182,36 +186,63 @@ struct MacExtArgs {
 };
 // inner_j = sum_a pt[j][a] x_a over Q_l P for every giant j of the level;
 // x_0 = (P c0, P c1) on q-limbs and 0 on the special limbs.
-// Grid (giants x ciphertexts, coefficient blocks, extended limbs), the giant
-// fastest: the ng CTAs that read one ciphertext's babies at one coefficient
-// block run back to back and share them through L2, so the babies stream from
-// HBM once while each thread keeps only one giant's two 128-bit sums.
-__global__ void __launch_bounds__(TPB) k_mac_ext(const MacExtArgs a) {
-  const u32 k = blockIdx.y * TPB + threadIdx.x;
-  const int t = blockIdx.z, j = blockIdx.x % a.ng, c = blockIdx.x / a.ng;
-  if (k >= a.n) return;
+// Grid (coefficient blocks of MB_K, extended limbs).  The CTA first stages
+// the block's words of every plaintext of the level in shared memory (npt x
+// MB_K words, 16-byte loads); its four thread groups then walk their shares
+// of the ciphertexts, each thread streaming its coefficient of every baby once
+// and keeping all giants' 128-bit sums.  Every byte of babies, plaintexts and
+// outputs crosses HBM once.
+__global__ void __launch_bounds__(MB_THREADS, 2) k_mac_ext(const MacExtArgs a) {
+  extern __shared__ u64 spt[];     // [npt][MB_K]
+  const int t = blockIdx.y;
+  const u32 k0 = blockIdx.x * MB_K;
+  for (int i = threadIdx.x; i < a.npt * (MB_K / 2); i += MB_THREADS) {
+    const int s = i / (MB_K / 2), w = i % (MB_K / 2);
+    const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(a.pt[s] + (size_t)t * a.n + k0) + w);
+    spt[s * MB_K + 2 * w] = v.x;
+    spt[s * MB_K + 2 * w + 1] = v.y;
+  }
+  __syncthreads();
+  const int kk = threadIdx.x % MB_K, grp = threadIdx.x / MB_K;
   const ModInfo m = a.mods[a.mod_of[t]];
-  const size_t poly = (size_t)a.ext * a.n, off = (size_t)t * a.n + k;
-  u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0;
-  // baby 0: P x on the q-limbs, nothing on the special limbs
-  if (t < a.nq && a.pt[j][0]) {
-    const u64 p = __ldg(a.pt[j][0] + off);
-    mac128(h0, l0, shoup(__ldg(a.c0[c] + off), a.pm[t], a.pm_s[t], m.q), p);
-    mac128(h1, l1, shoup(__ldg(a.c1[c] + off), a.pm[t], a.pm_s[t], m.q), p);
+  const size_t poly = (size_t)a.ext * a.n, off = (size_t)t * a.n + k0 + kk;
+  for (int c = grp; c < a.cn; c += MB_GROUPS) {
+    u64 h[MAXG][2], lo[MAXG][2];
+#pragma unroll
+    for (int j = 0; j < MAXG; ++j) h[j][0] = h[j][1] = lo[j][0] = lo[j][1] = 0;
+    if (t < a.nq) {  // baby 0: P x on the q-limbs, nothing on the special limbs
+      const u64 x0 = shoup(__ldg(a.c0[c] + off), a.pm[t], a.pm_s[t], m.q);
+      const u64 x1 = shoup(__ldg(a.c1[c] + off), a.pm[t], a.pm_s[t], m.q);
+#pragma unroll
+      for (int j = 0; j < MAXG; ++j) {
+        const int s = j < a.ng ? a.slot[j][0] : -1;
+        if (s < 0) continue;
+        const u64 p = spt[s * MB_K + kk];
+        mac128(h[j][0], lo[j][0], x0, p);
+        mac128(h[j][1], lo[j][1], x1, p);
+      }
+    }
+    const u64 *xb = a.xq + c * a.x_ct + off;
+#pragma unroll 4
+    for (int b = 1; b < a.na; ++b) {
+      const u64 x0 = __ldg(xb + b * a.x_baby), x1 = __ldg(xb + b * a.x_baby + poly);
+#pragma unroll
+      for (int j = 0; j < MAXG; ++j) {
+        const int s = j < a.ng ? a.slot[j][b] : -1;
+        if (s < 0) continue;
+        const u64 p = spt[s * MB_K + kk];
+        mac128(h[j][0], lo[j][0], x0, p);
+        mac128(h[j][1], lo[j][1], x1, p);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < MAXG; ++j) {
+      if (j >= a.ng) continue;
+      u64 *o = a.out + c * a.o_ct + j * a.o_giant + off;
+      o[0] = reduce128(h[j][0], lo[j][0], m);
+      o[poly] = reduce128(h[j][1], lo[j][1], m);
+    }
   }
-  // babies 1..na-1, read-only here: unrolled so that several babies' loads are in flight
-  const u64 *xb = a.xq + c * a.x_ct + off;
-#pragma unroll 8
-  for (int b = 1; b < a.na; ++b) {
-    const u64 *pt = a.pt[j][b];
-    if (!pt) continue;
-    const u64 p = __ldg(pt + off);
-    mac128(h0, l0, __ldg(xb + b * a.x_baby), p);
-    mac128(h1, l1, __ldg(xb + b * a.x_baby + poly), p);
-  }
-  u64 *o = a.out + c * a.o_ct + j * a.o_giant + off;
-  o[0] = reduce128(h0, l0, m);
-  o[poly] = reduce128(h1, l1, m);
 }
 
 struct CombArgs {
@@ -883,10 +914,15 @@ struct Eval {
         a.c1[i] = x1[c0 + i];
       }
       for (int j = 0; j < MAXG; ++j)
-        for (int t = 0; t < MAXA; ++t) a.pt[j][t] = nullptr;
-      int ci = lv.first_const;
+        for (int t = 0; t < MAXA; ++t) a.slot[j][t] = -1;
+      int ci = lv.first_const, npt = 0;
       for (int j = 0; j < ng; ++j)
-        for (auto &it : lv.plan[j].items) a.pt[j][it.first] = b.pts[ci++];
+        for (auto &it : lv.plan[j].items) {
+          a.pt[npt] = b.pts[ci++];
+          a.slot[j][it.first] = (signed char)npt++;
+        }
+      a.npt = npt;
+      a.cn = cn;
       a.xq = baby(c0, 0);
       a.x_ct = x_ct;
       a.x_baby = x_baby;
@@ -894,11 +930,20 @@ struct Eval {
       a.o_ct = o_ct;
       a.o_giant = o_giant;
       // limbs moved: babies 1.. and outputs per ciphertext, x's q-limbs, the plaintexts once
-      int npt = 0;
-      for (int j = 0; j < ng; ++j) npt += (int)lv.plan[j].items.size();
       const u64 moved = (u64)cn * ext * (2 * (na - 1) + 2 * ng) + (u64)cn * 2 * nl + (u64)npt * ext;
-      const dim3 g(cn * ng, (c->n + TPB - 1) / TPB, ext);
-      PROF_LAUNCH(c, PK_BOOT_MAC, moved, (k_mac_ext<<<g, TPB, 0, c->stream>>>(a)));
+      const size_t smem = (size_t)npt * MB_K * sizeof(u64);
+      // the opt-in above 48 KB is a per-device function attribute: set before each launch
+      if (cudaFuncSetAttribute(k_mac_ext, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               MAXG * MAXA * MB_K * (int)sizeof(u64)) != cudaSuccess) {
+        err = CKKS_E_CUDA;
+        break;
+      }
+      if (c->n % MB_K || npt > MAXG * MAXA) {
+        err = CKKS_E_PARAM;
+        break;
+      }
+      const dim3 g(c->n / MB_K, ext);
+      PROF_LAUNCH(c, PK_BOOT_MAC, moved, (k_mac_ext<<<g, MB_THREADS, smem, c->stream>>>(a)));
       if (cudaGetLastError() != cudaSuccess) err = CKKS_E_CUDA;
     }
     auto inner = [&](int i, int j) { return b.inner_qp + i * o_ct + j * o_giant; };
