@@ -472,6 +472,8 @@ int ckks_ctx_destroy(ckks_ctx *c) {
   cudaFree(c->d_mods);
   cudaFree(c->d_tw_fwd);
   cudaFree(c->d_tw_inv);
+  cudaFree(c->d_tw_row_fwd);
+  cudaFree(c->d_tw_row_inv);
   cudaFree(c->d_conv);
   cudaFree(c->d_s_ntt);
   cudaFree(c->scratch);

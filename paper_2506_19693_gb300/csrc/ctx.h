@@ -63,6 +63,11 @@ struct ckks_ctx {
   ModInfo *d_mods = nullptr;         // [n_q + n_p]
   ulonglong2 *d_tw_fwd = nullptr;    // [n_q + n_p][N]: (psi^brv(k), Shoup)
   ulonglong2 *d_tw_inv = nullptr;    // [n_q + n_p][N]: (psi^-brv(k), Shoup)
+  // the row pass's per-thread twiddles (second register phase) regrouped so
+  // that a warp's load is contiguous: [n_q + n_p][s < 4][i < 2^s][N/16] holds
+  // tw[((N/16 + m) << s) + i] at m (forward and inverse tables)
+  ulonglong2 *d_tw_row_fwd = nullptr;
+  ulonglong2 *d_tw_row_inv = nullptr;
   u64 *d_conv = nullptr;             // ConvTables payload
   ConvTables conv;
   std::vector<u64> h_conv;           // host copy of the payload

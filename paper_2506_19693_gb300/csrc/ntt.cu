@@ -35,6 +35,7 @@ __host__ __device__ constexpr int threads_b() { return RBT * 16; }
 struct NttParams {
   const ModInfo *mods;
   const ulonglong2 *tw;          // [modulus][N]
+  const ulonglong2 *tw_row;      // [modulus][15 N / 16]: the row pass's second phase, regrouped
   u32 n;
   int n_limbs;
   unsigned char mod_of_limb[MAX_MODS];
@@ -66,16 +67,16 @@ __device__ __forceinline__ u64 shoup_approx(u64 x, u64 w, u64 w_s, u64 q) {
 // 65 q < 2^64 only: no correction and the approximate Shoup product (t < 4q),
 // every stage raises the bound by 4q, so inputs < q stay below
 // (1 + 4 log2 N) q <= 65 q < 2^64 through all 16 stages.
-template <int K, bool LOOSE>
-__device__ __forceinline__ void fwd_step(u64 (&v)[1 << K], u32 mg, const ulonglong2 *__restrict__ tw,
-                                         u64 q, u64 twoq) {
+// tw_of(s, i): the twiddle of local stage s, group i within the block.
+template <int K, bool LOOSE, class TW>
+__device__ __forceinline__ void fwd_step_t(u64 (&v)[1 << K], TW tw_of, u64 q, u64 twoq) {
 #pragma unroll
   for (int s = 0; s < K; ++s) {
     const int half = 1 << (K - 1 - s);
 #pragma unroll
     for (int e = 0; e < (1 << K); ++e) {
       if (e & half) continue;
-      const ulonglong2 w = __ldg(&tw[(mg << s) + (e >> (K - s))]);
+      const ulonglong2 w = tw_of(s, e >> (K - s));
       u64 x = v[e];
       if (LOOSE) {
         const u64 t = shoup_approx(v[e + half], w.x, w.y, q);
@@ -91,12 +92,27 @@ __device__ __forceinline__ void fwd_step(u64 (&v)[1 << K], u32 mg, const ulonglo
   }
 }
 
+// block mg of the merged-psi order: twiddle psi^brv((mg << s) + i)
+template <int K, bool LOOSE>
+__device__ __forceinline__ void fwd_step(u64 (&v)[1 << K], u32 mg, const ulonglong2 *__restrict__ tw,
+                                         u64 q, u64 twoq) {
+  fwd_step_t<K, LOOSE>(v, [&](int s, int i) { return __ldg(&tw[(mg << s) + i]); }, q, twoq);
+}
+// the row pass's second phase: block N/16 + m, twiddles from the regrouped
+// table, where the 16 threads of a row read 16 consecutive entries
+template <int K, bool LOOSE>
+__device__ __forceinline__ void fwd_step_row(u64 (&v)[1 << K], u32 m, const ulonglong2 *__restrict__ twr,
+                                             u32 n16, u64 q, u64 twoq) {
+  static_assert(K <= 4, "the regrouped table holds four stages");
+  fwd_step_t<K, LOOSE>(v, [&](int s, int i) { return __ldg(&twr[(size_t)((1 << s) - 1 + i) * n16 + m]); }, q,
+                       twoq);
+}
+
 // Gentleman-Sande stages s = K-1 .. STOP of a 2^K-point block.  Values stay
 // in [0, R) with R = 2q (exact Shoup products); APPROX, for q < 2^61 only,
 // takes the approximate product and R = 4q (x + R - y < 8q < 2^64).
-template <int K, bool APPROX, int STOP = 0>
-__device__ __forceinline__ void inv_step(u64 (&v)[1 << K], u32 mg, const ulonglong2 *__restrict__ tw,
-                                         u64 q, u64 twoq) {
+template <int K, bool APPROX, int STOP, class TW>
+__device__ __forceinline__ void inv_step_t(u64 (&v)[1 << K], TW tw_of, u64 q, u64 twoq) {
   const u64 r = APPROX ? 2 * twoq : twoq;
 #pragma unroll
   for (int s = K - 1; s >= STOP; --s) {
@@ -104,7 +120,7 @@ __device__ __forceinline__ void inv_step(u64 (&v)[1 << K], u32 mg, const ulonglo
 #pragma unroll
     for (int e = 0; e < (1 << K); ++e) {
       if (e & half) continue;
-      const ulonglong2 w = __ldg(&tw[(mg << s) + (e >> (K - s))]);
+      const ulonglong2 w = tw_of(s, e >> (K - s));
       const u64 x = v[e], y = v[e + half];
       u64 sum = x + y;
       if (sum >= r) sum -= r;
@@ -112,6 +128,19 @@ __device__ __forceinline__ void inv_step(u64 (&v)[1 << K], u32 mg, const ulonglo
       v[e + half] = APPROX ? shoup_approx(x + r - y, w.x, w.y, q) : shoup_lazy(x + r - y, w.x, w.y, q);
     }
   }
+}
+
+template <int K, bool APPROX, int STOP = 0>
+__device__ __forceinline__ void inv_step(u64 (&v)[1 << K], u32 mg, const ulonglong2 *__restrict__ tw,
+                                         u64 q, u64 twoq) {
+  inv_step_t<K, APPROX, STOP>(v, [&](int s, int i) { return __ldg(&tw[(mg << s) + i]); }, q, twoq);
+}
+template <int K, bool APPROX>
+__device__ __forceinline__ void inv_step_row(u64 (&v)[1 << K], u32 m, const ulonglong2 *__restrict__ twr,
+                                             u32 n16, u64 q, u64 twoq) {
+  static_assert(K <= 4, "the regrouped table holds four stages");
+  inv_step_t<K, APPROX, 0>(v, [&](int s, int i) { return __ldg(&twr[(size_t)((1 << s) - 1 + i) * n16 + m]); },
+                           q, twoq);
 }
 
 // Primes below this bound take the forward transform without lazy corrections
@@ -231,7 +260,8 @@ __device__ __forceinline__ void fwd_b_body(const NttParams &prm, u64 *sm, int mi
     u64 v[1 << U2];
 #pragma unroll
     for (int e = 0; e < (1 << U2); ++e) v[e] = sm[padb(rr * BROW + (g << U2) + e)];
-    fwd_step<U2, LOOSE>(v, ((u32)(H + b) << U1) + g, tw, q, twoq);
+    fwd_step_row<U2, LOOSE>(v, ((u32)b << U1) + g, prm.tw_row + (size_t)mi * 15 * (prm.n / 16), prm.n / 16, q,
+                            twoq);
     const u64 one_s = LOOSE ? prm.mods[mi].one_s : 0;
 #pragma unroll
     for (int e = 0; e < (1 << U2); ++e) {
@@ -295,7 +325,8 @@ __device__ __forceinline__ void inv_b_body(const NttParams &prm, u64 *sm, int mi
     u64 v[1 << U2];
 #pragma unroll
     for (int e = 0; e < (1 << U2); ++e) v[e] = sm[padb(rr * BROW + (g << U2) + e)];
-    inv_step<U2, APPROX>(v, ((u32)(H + b) << U1) + g, tw, q, twoq);
+    inv_step_row<U2, APPROX>(v, ((u32)b << U1) + g, prm.tw_row + (size_t)mi * 15 * (prm.n / 16), prm.n / 16, q,
+                             twoq);
 #pragma unroll
     for (int e = 0; e < (1 << U2); ++e) sm[padb(rr * BROW + (g << U2) + e)] = v[e];
   }
@@ -459,6 +490,7 @@ int launch_ntt(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, i
   NttParams prm;
   prm.mods = c->d_mods;
   prm.tw = inverse ? c->d_tw_inv : c->d_tw_fwd;
+  prm.tw_row = inverse ? c->d_tw_row_inv : c->d_tw_row_fwd;
   prm.n = c->n;
   prm.n_limbs = nl;
   bool approx = true;  // inverse: every modulus below 2^61

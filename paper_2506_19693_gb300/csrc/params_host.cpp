@@ -132,6 +132,18 @@ int build_tables(ckks_ctx *c) {
     const u64 w0 = host_mulmod(inv[(size_t)i * n + 1].x, mi[i].ninv, q);
     inv[(size_t)i * n] = make_ulonglong2(w0, host_shoup(w0, q));
   }
+  // ---- the row pass's twiddles, regrouped (see ctx.h) ----
+  const size_t n16 = n / 16, row_per = 15 * n16;
+  std::vector<ulonglong2> rfwd((size_t)nm * row_per), rinv((size_t)nm * row_per);
+  for (int i = 0; i < nm; ++i)
+    for (int s2 = 0; s2 < 4; ++s2)
+      for (int ii = 0; ii < (1 << s2); ++ii)
+        for (size_t m2 = 0; m2 < n16; ++m2) {
+          const size_t dst = (size_t)i * row_per + (size_t)((1 << s2) - 1 + ii) * n16 + m2;
+          const size_t src = (size_t)i * n + (((n16 + m2) << s2) + ii);
+          rfwd[dst] = fwd[src];
+          rinv[dst] = inv[src];
+        }
   // ---- basis conversion constants ----
   ConvTables &t = c->conv;
   std::vector<u64> &v = c->h_conv;
@@ -282,7 +294,12 @@ int build_tables(ckks_ctx *c) {
   CK_CUDA(cudaMemcpy(c->d_mods, mi.data(), bytes_mods, cudaMemcpyHostToDevice));
   CK_CUDA(cudaMemcpy(c->d_tw_fwd, fwd.data(), bytes_tw, cudaMemcpyHostToDevice));
   CK_CUDA(cudaMemcpy(c->d_tw_inv, inv.data(), bytes_tw, cudaMemcpyHostToDevice));
+  const size_t bytes_row = sizeof(ulonglong2) * rfwd.size();
+  if (cudaMalloc(&c->d_tw_row_fwd, bytes_row) != cudaSuccess) return CKKS_E_OOM;
+  if (cudaMalloc(&c->d_tw_row_inv, bytes_row) != cudaSuccess) return CKKS_E_OOM;
+  CK_CUDA(cudaMemcpy(c->d_tw_row_fwd, rfwd.data(), bytes_row, cudaMemcpyHostToDevice));
+  CK_CUDA(cudaMemcpy(c->d_tw_row_inv, rinv.data(), bytes_row, cudaMemcpyHostToDevice));
   if (t.total) CK_CUDA(cudaMemcpy(c->d_conv, v.data(), sizeof(u64) * t.total, cudaMemcpyHostToDevice));
-  c->table_bytes = bytes_mods + 2 * bytes_tw + sizeof(u64) * t.total;
+  c->table_bytes = bytes_mods + 2 * bytes_tw + 2 * bytes_row + sizeof(u64) * t.total;
   return CKKS_OK;
 }
