@@ -338,17 +338,26 @@ def run_gpu(args):
     tuning = {"ip_group": ctx.tune(level, B), "ntt_rows": ctx.tune_ntt(16),
               "boot_ip_group": bctx.tune(len(wb.q_bits) - 1, nb), "boot_ntt_rows": bctx.tune_ntt(16)}
 
+    nvtx = torch.cuda.nvtx
+
     def step(marks=None):
+        # NVTX ranges name the phases (ncu --nvtx-include "timed/hmult/" selects one)
         if marks:
             marks[0].record(stream)
+            nvtx.range_push("hmult")
         ctx.mul_relin_batch(A, Bc, OUT, rescale=ck.RESCALE_MERGED)
         if marks:
+            nvtx.range_pop()
             marks[1].record(stream)
+            nvtx.range_push("rotations")
         ctx.rotate_hoisted(A, list(w.rot_steps), ROT)
         if marks:
+            nvtx.range_pop()
             marks[2].record(stream)
+            nvtx.range_push("bootstrap")
         bctx.bootstrap_batch(BIN, BOUT)
         if marks:
+            nvtx.range_pop()
             marks[3].record(stream)
 
     def spot_errors():
