@@ -161,6 +161,13 @@ class OracleSample:
         self.orc.mul_relin_rescale(self.cts[0], self.cts[1])
         return time.perf_counter() - t0
 
+    def time_rotation(self, k: int = 1) -> float:
+        """One rotation of the same ciphertext (its key generated untimed)."""
+        self.orc.gen_rotation_keys([k])
+        t0 = time.perf_counter()
+        self.orc.rotate(self.cts[0], k)
+        return time.perf_counter() - t0
+
 
 def run_reference(args):
     rank = _env_int("RANK", 0)
@@ -480,8 +487,11 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.small):
         sample = OracleSample(w)
         dt, threads = sample.time(), sample.threads
+        dr = sample.time_rotation(1)
         cpu = {"value": 1.0 / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": "1 HMult+relin+rescale of 1 ciphertext pair at N=2^16, L=24 (1/64 of the batch)"}
+               "sample": "1 HMult+relin+rescale of 1 ciphertext pair at N=2^16, L=24 (1/64 of the batch)",
+               "rotations_per_s": 1.0 / dr,
+               "rotation_sample": "1 rotation by 1 slot of 1 ciphertext at N=2^16, L=24 (key generated untimed)"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
