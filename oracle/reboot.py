@@ -23,6 +23,16 @@ same way); integer constants (the 2 of delta Z) cost no level (C14); R5
 ciphertext products go through the bootstrapping evaluator's multiply, with
 ModDown and rescale merged (C21).
 `plain_step` is the same computation on FP64 slot vectors (numpy).
+
+CE-Block (Sec. 4.2.3: the alternation of RE- and CE-Blocks; Sec. 4.3 notes
+that the extension of Alg. 1 to CE-Blocks is straightforward) -- reading R6:
+the dual of Alg. 1 with the formats swapped.  Input A_rep (a RE-Block's
+activations); Z_exp = CE-Matmul(A_rep, W_col); A_exp = EncryptedPolyReLU(Z);
+the local classifier is a RE-FC layer, Yhat_rep = RE-Matmul(A_exp, W_row*);
+grad = Yhat - Y_rep; delta W_row* = A_exp x grad; delta A_exp =
+CE-Matmul(grad, W_row*); delta Z = 1 + 2 delta A; delta W_col = A_rep x
+delta Z; the same Alg. 2 updates and bootstraps (R2-R5 as for the RE-Block).
+`plain_step_ce` is its FP64 slot form.
 """
 from __future__ import annotations
 
@@ -155,6 +165,28 @@ def plain_step(state, xs, ys, g: Geometry, gamma, eta, mu, first):
     return newW, newV, ws1, vs1, dWs
 
 
+def plain_step_ce(state, as_rep, ys_rep, g: Geometry, gamma, eta, mu, first):
+    """CE-Block (reading R6) on FP64 slot vectors; also returns A_exp per sample."""
+    W, V, Ws, Vs, dWs_prev = state
+    dW = np.zeros(g.r * g.c)
+    dWs = np.zeros(g.r * g.c)
+    acts = []
+    for a, y in zip(as_rep, ys_rep):
+        z = plain_sumcols(a * W, g)
+        act = z * z + z
+        acts.append(act)
+        yhat = plain_sumrows(act * Ws, g)
+        grad = yhat - y
+        dWs = dWs + act * grad
+        da = plain_sumcols(grad * Ws, g)
+        dz = 1 + 2 * da
+        dW = dW + a * dz
+    w1, v1 = plain_update(W, V, dW, gamma, eta, mu, first)
+    grad_s = dWs if dWs_prev is None else dWs_prev
+    ws1, vs1 = plain_update(Ws, Vs, grad_s, gamma, eta, mu, first)
+    return (w1, v1, ws1, vs1, dWs), acts
+
+
 # ---------------------------------------------------------------- encrypted step
 class REBlock:
     """Alg. 1 + Alg. 2 for one RE-Block over the oracle's primitives."""
@@ -232,6 +264,7 @@ class REBlock:
         T = self.g.tiles
         dW = [None] * T
         dWs = None
+        self.last_activations = []  # A_rep per sample: the next (CE-)Block's input
         for x, y in zip(xs, ys):
             acc = None
             for t in range(T):
@@ -239,6 +272,7 @@ class REBlock:
                 acc = p if acc is None else self.o.add(acc, p)
             z = self.sumrows(acc)                                  # RE-Matmul
             a = self.add(self.mul(z, z), z)                        # EncryptedPolyReLU
+            self.last_activations.append(a)
             yhat = self.sumcols(self.mul(a, Ws))                   # CE-Matmul
             grad = self.sub(yhat, y)                               # RSS gradient
             dws = self.mul(a, grad)                                # delta W_col
@@ -260,3 +294,31 @@ class REBlock:
             ws1 = self.boot.bootstrap(ws1)
             vs1 = self.boot.bootstrap(vs1)
         return newW, newV, ws1, vs1, dWs
+
+
+class CEBlock(REBlock):
+    """Reading R6: a CE-Block's step over the oracle's primitives (the dual of
+    Alg. 1); W is the CE-FC layer's column-wise matrix, Ws the RE-FC local
+    classifier's row-wise matrix."""
+
+    def step(self, state, as_rep, ys, first: bool, bootstrap: bool = True):
+        W, V, Ws, Vs, dWs_prev = state
+        dW = dWs = None
+        self.last_activations = []  # A_exp per sample
+        for a, y in zip(as_rep, ys):
+            z = self.sumcols(self.mul(a, W))                       # CE-Matmul
+            act = self.add(self.mul(z, z), z)                      # EncryptedPolyReLU
+            self.last_activations.append(act)
+            yhat = self.sumrows(self.mul(act, Ws))                 # RE-Matmul (local classifier)
+            grad = self.sub(yhat, y)                               # RSS gradient
+            dws = self.mul(act, grad)                              # delta W_row*
+            da = self.sumcols(self.mul(grad, Ws))                  # CE-Matmul(grad, W_row*)
+            dz = self.add_const(self.o.mul_int(da, 2), 1.0)        # EncryptedPolyReLU'
+            dw = self.mul(a, dz)                                   # delta W_col
+            dWs = dws if dWs is None else self.o.add(dWs, dws)
+            dW = dw if dW is None else self.o.add(dW, dw)
+        w1, v1 = self.update(W, V, dW, first)
+        ws1, vs1 = self.update(Ws, Vs, dWs if dWs_prev is None else dWs_prev, first)
+        if bootstrap:
+            w1, v1, ws1, vs1 = (self.boot.bootstrap(c) for c in (w1, v1, ws1, vs1))
+        return w1, v1, ws1, vs1, dWs

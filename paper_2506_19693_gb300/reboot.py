@@ -5,6 +5,10 @@ bootstrap of one RE-Block, batched across the mini-batch: every operation is
 one batched library call over all samples (or over the block's weight
 ciphertexts), so each kernel launch serves the whole batch.
 
+CEBlock is the dual step of a CE-Block (reading R6: CE-Matmul forward, a
+RE-FC local classifier, delta A by CE-Matmul), which takes a RE-Block's
+activations; RE- and CE-Blocks alternate in eMLP-2/3 (Table 3).
+
 Paper passages: packing (Sec. 4.1); sum across rows / columns (Sec. 3,
 Eq. sumrows / sumcols); RE-Matmul and CE-Matmul (Sec. 4.2.1);
 EncryptedPolyReLU A = Z x Z + Z (Sec. 4.2.2); Alg. 1 (forward, RSS gradient,
@@ -222,6 +226,7 @@ class REBlock:
             acc = p if acc is None else self.plain_add(acc, p)
         z = self.sumrows(acc)                                         # RE-Matmul
         a = self.add(self.mul(z, z), z)                               # EncryptedPolyReLU
+        self.last_activations = a                                     # A_rep: a CE-Block's input
         yhat = self.sumcols(self.mul(a, [Ws] * S))                    # CE-Matmul
         grad = self.add(yhat, ys, subtract=True)                      # RSS gradient
         dws = self.mul(a, grad)                                       # delta W_col per sample
@@ -246,3 +251,45 @@ class REBlock:
             return new
         refreshed = self.ctx.bootstrap_batch(nw + nv + ws1 + vs1)
         return refreshed[:T], refreshed[T:2 * T], refreshed[2 * T], refreshed[2 * T + 1], dWs
+
+
+def pack_repeated(vec, g: Geometry) -> np.ndarray:
+    m = np.zeros((g.r, g.c))
+    m[:, : len(vec)] = np.asarray(vec)[None, :]
+    return m.ravel()
+
+
+def pack_rowwise(w, g: Geometry) -> np.ndarray:
+    m = np.zeros((g.r, g.c))
+    m[: w.shape[0], : w.shape[1]] = w
+    return m.ravel()
+
+
+class CEBlock(REBlock):
+    """One CE-Block (reading R6): W is the CE-FC layer's column-wise matrix
+    and Ws the RE-FC local classifier's row-wise matrix; the inputs are a
+    RE-Block's activations A_rep, the labels are in the repeated format."""
+
+    def step(self, state, as_rep, ys, first: bool, bootstrap: bool = True):
+        W, V, Ws, Vs, dWs_prev = state
+        S = len(as_rep)
+        z = self.sumcols(self.mul(as_rep, [W] * S))                   # CE-Matmul
+        a = self.add(self.mul(z, z), z)                               # EncryptedPolyReLU
+        self.last_activations = a                                     # A_exp
+        yhat = self.sumrows(self.mul(a, [Ws] * S))                    # RE-Matmul (local classifier)
+        grad = self.add(yhat, ys, subtract=True)                      # RSS gradient
+        dws = self.mul(a, grad)                                       # delta W_row* per sample
+        da = self.sumcols(self.mul(grad, [Ws] * S))                   # CE-Matmul(grad, W_row*)
+        dz = self.add_const(self.ctx.mul_int_batch(da, 2), 1.0)       # EncryptedPolyReLU'
+        dw = self.mul(as_rep, dz)                                     # delta W_col per sample
+        dW, dWs = [dw[0]], [dws[0]]
+        for s in range(1, S):
+            dW = self.plain_add(dW, [dw[s]])
+            dWs = self.plain_add(dWs, [dws[s]])
+        nw, nv = self.update([W], [V], dW, first)
+        grad_s = dWs if dWs_prev is None else [dWs_prev]
+        ws1, vs1 = self.update([Ws], [Vs], grad_s, first)
+        if not bootstrap:
+            return nw[0], nv[0], ws1[0], vs1[0], dWs[0]
+        refreshed = self.ctx.bootstrap_batch(nw + nv + ws1 + vs1)
+        return refreshed[0], refreshed[1], refreshed[2], refreshed[3], dWs[0]

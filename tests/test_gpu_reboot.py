@@ -108,3 +108,112 @@ def test_reboot_step_config3_size_with_bootstrap():
             assert np.max(np.abs(ctx.decrypt_decode(ct).real - want)) < 2.0 ** -12
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("tensor_form", [False, True], ids=["uint64", "tensor"])
+def test_ce_block_step_bit_exact_small_ring(tensor_form):
+    """Reading R6: the CE-Block step (inputs at level 9 as a RE-Block leaves
+    them, weights at level 11) equals the oracle's limb for limb."""
+    import torch
+    import oracle
+    import oracle.reboot as orb
+    import paper_2506_19693_gb300 as ck
+    import paper_2506_19693_gb300.reboot as rb
+    torch.cuda.set_device(0)
+    w_ = si.BOOT_SMALL
+    g = rb.Geometry(32, 64, 48, 24, 10)
+    go = orb.Geometry(32, 64, 48, 24, 10)
+    ctx = ck.Context.from_workload(w_)
+    ctx.set_form(tensor_form)
+    try:
+        ctx.keygen(1, rot_steps=g.rotation_steps())
+        o = oracle.Oracle(w_.log_n, w_.q_bits, w_.p_bits, w_.dnum, w_.h, w_.sigma)
+        o.keygen(1)
+        o.gen_rotation_keys(go.rotation_steps())
+        a, y, w, ws = _data(6, 2, g.k0, g.k1, g.o)
+        scale = 2.0 ** w_.log2_scale
+        gamma, eta, mu = 0.01, 0.001, 0.9
+        seed = [2000]
+
+        def both(vec, lvl):
+            m = o.encode(vec, scale)
+            seed[0] += 1
+            return (ctx.encrypt(ctx.pt_from_int(m, lvl), lvl, scale, seed[0]),
+                    o.encrypt(o.pt_from_int(m, lvl), lvl, scale, seed[0]))
+
+        Wp, Wsp = both(orb.pack_colwise(w, go), 11), both(orb.pack_rowwise(ws, go), 11)
+        Vp, Vsp = both(np.full(g.r * g.c, 0.01), 11), both(np.full(g.r * g.c, 0.02), 11)
+        asp = [both(orb.pack_repeated(ai, go), 9) for ai in a]
+        ysp = [both(orb.pack_repeated(yi, go), 9) for yi in y]
+        mask = {l: o.encode(orb.first_column_mask(go), float(o.q[l])) for l in range(12)}
+        gpu = rb.CEBlock(ctx, g, gamma, eta, mu, mask_coeffs=mask)
+        orc = orb.CEBlock(o, go, gamma, eta, mu)
+        for first in (True, False):
+            rg = gpu.step((Wp[0], Vp[0], Wsp[0], Vsp[0], None), [p[0] for p in asp], [p[0] for p in ysp], first,
+                          bootstrap=False)
+            ro = orc.step((Wp[1], Vp[1], Wsp[1], Vsp[1], None), [p[1] for p in asp], [p[1] for p in ysp], first,
+                          bootstrap=False)
+            assert rg[0].level == 0
+            for cg, co in zip(list(rg) + gpu.last_activations, list(ro) + orc.last_activations):
+                assert (cg.level, cg.scale) == (co.level, co.scale)
+                assert np.array_equal(ctx.export_ct(cg), co.data)
+        assert ctx.device_error() == 0
+    finally:
+        ctx.close()
+
+
+def test_emlp2_step_at_2_17_matches_fp64():
+    """eMLP-2 (Table 3: RE-Block(64) -> CE-Block(32), N = 2^17, l = 27): one
+    step of both blocks, the CE-Block fed the RE-Block's activations, with the
+    bootstraps; the refreshed weights decrypt to the FP64 slot computation."""
+    import torch
+    import oracle.reboot as orb
+    import paper_2506_19693_gb300 as ck
+    import paper_2506_19693_gb300.reboot as rb
+    torch.cuda.set_device(0)
+    wb = si.BOOT17
+    g1, g2 = rb.Geometry(256, 256, 784, 64, 10), rb.Geometry(256, 256, 64, 32, 10)
+    o1, o2 = orb.Geometry(256, 256, 784, 64, 10), orb.Geometry(256, 256, 64, 32, 10)
+    ctx = ck.Context.from_workload(wb)
+    try:
+        ctx.keygen_boot(1)
+        ctx.boot_setup()
+        for k in sorted(set(g1.rotation_steps()) | set(g2.rotation_steps())):
+            ctx.keygen_galois(ctx.galois_elt(k))
+        b = 2
+        rng = np.random.default_rng(31)
+        x = rng.uniform(0, 1, size=(b, 784))
+        y = np.eye(10)[rng.integers(0, 10, size=b)]
+        w1 = rng.normal(0, 1 / np.sqrt(784), size=(784, 64))
+        ws1 = rng.normal(0, 1 / 8, size=(64, 10))
+        w2 = rng.normal(0, 1 / 8, size=(64, 32))
+        ws2 = rng.normal(0, 1 / np.sqrt(32), size=(32, 10))
+        gamma, eta, mu = 0.01, 0.001, 0.9
+        scale, lvl = 2.0 ** wb.log2_scale, len(wb.q_bits) - 17
+        seeds = iter(range(5000, 9000))
+        enc = lambda v: ctx.encrypt(ctx.encode(v, lvl, scale), lvl, scale, next(seeds))  # noqa: E731
+        zero = np.zeros(g1.r * g1.c)
+        W1p, Ws1p = orb.tile_weights(w1, o1), orb.pack_colwise(ws1, o1)
+        W2p, Ws2p = orb.pack_colwise(w2, o2), orb.pack_rowwise(ws2, o2)
+        st1 = ([enc(t) for t in W1p], [enc(zero) for _ in W1p], enc(Ws1p), enc(zero), None)
+        st2 = (enc(W2p), enc(zero), enc(Ws2p), enc(zero), None)
+        xp = [orb.tile_inputs(xi, o1) for xi in x]
+        yexp = [orb.pack_expanded(yi, o1) for yi in y]
+        yrep = [orb.pack_repeated(yi, o2) for yi in y]
+        blk1 = rb.REBlock(ctx, g1, gamma, eta, mu)
+        blk2 = rb.CEBlock(ctx, g2, gamma, eta, mu)
+        r1 = blk1.step(st1, [[enc(t) for t in xs] for xs in xp], [enc(v) for v in yexp], True)
+        r2 = blk2.step(st2, blk1.last_activations, [enc(v) for v in yrep], True)
+        # FP64: the RE-Block, its activations, then the CE-Block on them
+        p1 = orb.plain_step((W1p, [zero] * len(W1p), Ws1p, zero, None), xp, yexp, o1, gamma, eta, mu, True)
+        acts = []
+        for xs in xp:
+            z = orb.plain_sumrows(sum(a * w for a, w in zip(xs, W1p)), o1)
+            acts.append(z * z + z)
+        p2, _ = orb.plain_step_ce((W2p, zero, Ws2p, zero, None), acts, yrep, o2, gamma, eta, mu, True)
+        assert r1[0][0].level == r2[0].level == lvl
+        for ct, want in ((r1[0][0], p1[0][0]), (r1[2], p1[2]), (r2[0], p2[0]), (r2[2], p2[2])):
+            assert np.max(np.abs(ctx.decrypt_decode(ct).real - want)) < 2.0 ** -12
+        assert ctx.device_error() == 0
+    finally:
+        ctx.close()

@@ -127,3 +127,69 @@ def test_encrypted_step_matches_fp64_and_uses_eight_levels(env):
     refreshed = boot.bootstrap(newW[0])
     assert refreshed.level == 8
     assert np.max(np.abs(o.decrypt_decode(refreshed).real - ref[0][0])) < 2.0 ** -12
+
+
+# ---------------------------------------------------------------- CE-Block (reading R6)
+GC = rb.Geometry(r=32, c=64, k0=48, k1=24, o=10)  # CE-FC 48 -> 24, RE-FC classifier 24 -> 10
+
+
+def _data_ce(seed, b):
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(0, 1, size=(b, GC.k0))       # the previous RE-Block's activations
+    y = np.eye(GC.o)[rng.integers(0, GC.o, size=b)]
+    w = rng.normal(0, 1 / np.sqrt(GC.k0), size=(GC.k0, GC.k1))
+    ws = rng.normal(0, 1 / np.sqrt(GC.k1), size=(GC.k1, GC.o))
+    return a, y, w, ws
+
+
+def test_plain_ce_step_is_the_dual_of_alg1_in_matrix_form():
+    a, y, w, ws = _data_ce(5, 3)
+    gamma, eta, mu = 0.01, 0.001, 0.9
+    W, Ws = rb.pack_colwise(w, GC), rb.pack_rowwise(ws, GC)
+    state = (W, np.zeros_like(W), Ws, np.zeros_like(Ws), None)
+    (w1p, v1p, ws1p, vs1p, _), acts = rb.plain_step_ce(
+        state, [rb.pack_repeated(ai, GC) for ai in a], [rb.pack_repeated(yi, GC) for yi in y], GC,
+        gamma, eta, mu, first=True)
+    dW = np.zeros_like(w)
+    dWs = np.zeros_like(ws)
+    for s, (ai, yi) in enumerate(zip(a, y)):
+        z = ai @ w
+        act = z * z + z
+        assert np.allclose(_unpack(acts[s], GC)[: GC.k1], np.tile(act[:, None], (1, GC.c)))  # expanded
+        g = act @ ws - yi
+        dWs += np.outer(act, g)
+        dz = 1 + 2 * (ws @ g)
+        dW += np.outer(ai, dz)
+    def upd(wm, dwm):
+        dwm = dwm + eta * dwm
+        return wm - (gamma * dwm + gamma * mu * dwm), dwm
+    w1, v1 = upd(w, dW)
+    ws1, vs1 = upd(ws, dWs)
+    assert np.allclose(_unpack(w1p, GC)[: GC.k1, : GC.k0], w1.T)
+    assert np.allclose(_unpack(v1p, GC)[: GC.k1, : GC.k0], v1.T)
+    assert np.allclose(_unpack(ws1p, GC)[: GC.k1, : GC.o], ws1)
+    assert np.allclose(_unpack(vs1p, GC)[: GC.k1, : GC.o], vs1)
+
+
+def test_encrypted_ce_step_matches_fp64_within_eleven_levels(env):
+    """A CE-Block fed at level 9 (a RE-Block's activations from level-11
+    inputs) with weights at level 11 ends at level 0: Table 3's
+    tau_ReBoot = 11 for eMLP-2's two blocks."""
+    w_, o, boot = env
+    a, y, w, ws = _data_ce(6, 2)
+    scale = 2.0 ** w_.log2_scale
+    gamma, eta, mu = 0.01, 0.001, 0.9
+    enc = lambda v, lv, sd: o.encrypt(o.pt_from_int(o.encode(v, scale), lv), lv, scale, sd)  # noqa: E731
+    W, Ws = enc(rb.pack_colwise(w, GC), 11, 700), enc(rb.pack_rowwise(ws, GC), 11, 701)
+    V, Vs = enc(np.zeros(GC.r * GC.c), 11, 702), enc(np.zeros(GC.r * GC.c), 11, 703)
+    acts = [enc(rb.pack_repeated(a[s], GC), 9, 710 + s) for s in range(len(a))]
+    ys = [enc(rb.pack_repeated(y[s], GC), 9, 720 + s) for s in range(len(y))]
+    blk = rb.CEBlock(o, GC, gamma, eta, mu, boot)
+    w1, v1, ws1, vs1, dws = blk.step((W, V, Ws, Vs, None), acts, ys, first=True, bootstrap=False)
+    assert w1.level == 0
+    (pw, pv, pws, pvs, _), pacts = rb.plain_step_ce(
+        (rb.pack_colwise(w, GC), np.zeros(GC.r * GC.c), rb.pack_rowwise(ws, GC), np.zeros(GC.r * GC.c), None),
+        [rb.pack_repeated(ai, GC) for ai in a], [rb.pack_repeated(yi, GC) for yi in y], GC,
+        gamma, eta, mu, first=True)
+    for ct, want in ((w1, pw), (ws1, pws), (blk.last_activations[0], pacts[0])):
+        assert np.max(np.abs(o.decrypt_decode(ct).real - want)) < 2.0 ** -16
