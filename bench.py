@@ -637,62 +637,83 @@ def run_n_scaling(torch, stream, reps):
         err = float(max(np.max(np.abs(bctx.decrypt_decode(bout[i]) - zb[i])) for i in range(2)))
         out["bootstrap_n131072"] = {"workload": wb.name, "batch": nb, "bootstraps_per_s": nb / (ms / 1e3),
                                     "ms_per_batch": ms, "slot_error": err, "output_level": bout[0].level}
-        out["emlp2_step"] = run_emlp2_step(bctx, wb, torch, stream)
+        out["emlp2_step"] = run_emlp_step(bctx, wb, torch, stream, [(784, 64), (64, 32)],
+                                          {"eMLP-2 (Table 6, 2x Xeon Gold 5318S)": 629.65})
+    finally:
+        bctx.close()
+    wb3 = si.BOOT17_L29
+    bctx = ck.Context.from_workload(wb3, stream=stream)
+    try:
+        bctx.keygen_boot(3)
+        bctx.boot_setup()
+        bctx.tune(len(wb3.q_bits) - 1, 8)
+        bctx.tune_ntt(16)
+        out["emlp3_step"] = run_emlp_step(bctx, wb3, torch, stream, [(784, 128), (128, 64), (64, 32)],
+                                          {"eMLP-3": "not in Table 6"})
     finally:
         bctx.close()
     out["clock"] = "CUDA events on the library stream, inputs resident; untimed tuning and warm-up"
     return out
 
 
-def run_emlp2_step(bctx, wb, torch, stream, b=128):
-    """One eMLP-2 training step (Table 3: RE-Block(64) -> CE-Block(32) at
-    N = 2^17, l = 27) on b synthetic samples: the RE-Block step, then the
-    CE-Block step (reading R6) on the RE-Block's activations, each with the
-    bootstrap of its weights and velocities.  One untimed warm-up iteration,
-    one timed iteration (NAG with velocity)."""
+def run_emlp_step(bctx, wb, torch, stream, dims, paper_s, b=128):
+    """One training step of an eMLP of Table 3 at N = 2^17 (r = c = 256): blocks
+    alternate RE, CE, RE (reading R6 for the CE-Block), each block fed the
+    previous block's activations and bootstrapping its weights and
+    velocities.  b synthetic samples; one untimed warm-up iteration, one timed
+    iteration (NAG with velocity)."""
     import paper_2506_19693_gb300.reboot as rb
-    g1 = rb.Geometry(256, 256, 784, 64, 10)
-    g2 = rb.Geometry(256, 256, 64, 32, 10)
-    for k in sorted(set(g1.rotation_steps()) | set(g2.rotation_steps())):
+    gs = [rb.Geometry(256, 256, k0, k1, 10) for k0, k1 in dims]
+    for k in sorted(set(gs[0].rotation_steps())):
         bctx.keygen_galois(bctx.galois_elt(k))
-    rng = np.random.default_rng(800)
-    x = rng.uniform(0, 1, size=(b, g1.k0))
-    y = np.eye(g1.o)[rng.integers(0, g1.o, size=b)]
-    w1 = rng.normal(0, 1 / np.sqrt(g1.k0), size=(g1.k0, g1.k1))
-    ws1 = rng.normal(0, 1 / np.sqrt(g1.k1), size=(g1.k1, g1.o))
-    w2 = rng.normal(0, 1 / np.sqrt(g2.k0), size=(g2.k0, g2.k1))
-    ws2 = rng.normal(0, 1 / np.sqrt(g2.k1), size=(g2.k1, g2.o))
+    rng = np.random.default_rng(800 + len(dims))
+    x = rng.uniform(0, 1, size=(b, dims[0][0]))
+    y = np.eye(10)[rng.integers(0, 10, size=b)]
     scale, lvl = 2.0 ** wb.log2_scale, len(wb.q_bits) - 17
     seeds = iter(range(3 * 10 ** 6, 4 * 10 ** 6))
     enc = lambda v: bctx.encrypt(bctx.encode(v, lvl, scale), lvl, scale, next(seeds))  # noqa: E731
-    zero = np.zeros(g1.r * g1.c)
-    st1 = ([enc(t) for t in rb.weight_tiles(w1, g1)], [enc(zero) for _ in range(g1.tiles)],
-           enc(rb.pack_colwise(ws1, g1)), enc(zero), None)
-    st2 = (enc(rb.pack_colwise(w2, g2)), enc(zero), enc(rb.pack_rowwise(ws2, g2)), enc(zero), None)
-    xs = [[enc(t) for t in rb.input_tiles(xi, g1)] for xi in x]
-    ys_exp = [enc(rb.pack_expanded(yi, g1)) for yi in y]
-    ys_rep = [enc(rb.pack_repeated(yi, g2)) for yi in y]
-    blk1 = rb.REBlock(bctx, g1, 0.001 / b, 0.001, 0.9)
-    blk2 = rb.CEBlock(bctx, g2, 0.001 / b, 0.001, 0.9)
+    zero = np.zeros(256 * 256)
+    states, blocks = [], []
+    for h, (g, (k0, k1)) in enumerate(zip(gs, dims)):
+        w = rng.normal(0, 1 / np.sqrt(k0), size=(k0, k1))
+        ws = rng.normal(0, 1 / np.sqrt(k1), size=(k1, 10))
+        if h % 2 == 0:  # RE-Block: row-wise tiles, column-wise classifier
+            tiles = rb.weight_tiles(w, g)
+            states.append(([enc(t) for t in tiles], [enc(zero) for _ in tiles], enc(rb.pack_colwise(ws, g)),
+                           enc(zero), None))
+            blocks.append(rb.REBlock(bctx, g, 0.001 / b, 0.001, 0.9))
+        else:           # CE-Block: column-wise layer, row-wise classifier
+            states.append((enc(rb.pack_colwise(w, g)), enc(zero), enc(rb.pack_rowwise(ws, g)), enc(zero), None))
+            blocks.append(rb.CEBlock(bctx, g, 0.001 / b, 0.001, 0.9))
+    xs = [[enc(t) for t in rb.input_tiles(xi, gs[0])] for xi in x]
+    ys_exp = [enc(rb.pack_expanded(yi, gs[0])) for yi in y]
+    ys_rep = [enc(rb.pack_repeated(yi, gs[0])) for yi in y]
 
-    def iteration(st1, st2, first):
-        st1 = blk1.step(st1, xs, ys_exp, first)
-        st2 = blk2.step(st2, blk1.last_activations, ys_rep, first)
-        return st1, st2
+    def iteration(states, first):
+        out, inp = [], xs
+        for h, (blk, st) in enumerate(zip(blocks, states)):
+            if h % 2 == 0:
+                out.append(blk.step(st, inp, ys_exp, first))
+            else:
+                out.append(blk.step(st, inp, ys_rep, first))
+            acts = blk.last_activations
+            inp = acts if h % 2 == 0 else [[a] for a in acts]
+        return out
 
-    st1, st2 = iteration(st1, st2, True)
+    states = iteration(states, True)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0 = bctx.launch_count()
     e0.record(stream)
-    st1, st2 = iteration(st1, st2, False)
+    states = iteration(states, False)
     e1.record(stream)
     torch.cuda.synchronize()
+    nboot = sum(2 * g.tiles + 2 if h % 2 == 0 else 4 for h, g in enumerate(gs))
     return {"seconds_per_step": e0.elapsed_time(e1) / 1e3, "samples": b, "workload": wb.name,
-            "geometry": "r = c = 256; RE-Block 784 -> 64 (4 input tiles, classifier 64 -> 10), "
-                        "CE-Block 64 -> 32 (classifier 32 -> 10)",
-            "bootstraps": 2 * g1.tiles + 2 + 4, "kernel_launches": bctx.launch_count() - l0,
-            "paper_cpu_context_s": {"eMLP-2 (Table 6, 2x Xeon Gold 5318S)": 629.65}}
+            "blocks": " -> ".join(("RE" if h % 2 == 0 else "CE") + f"({k1})" for h, (_, k1) in enumerate(dims)),
+            "geometry": "r = c = 256, 784 inputs in 4 row tiles, classifiers to 10 outputs",
+            "bootstraps": nboot, "kernel_launches": bctx.launch_count() - l0,
+            "paper_cpu_context_s": paper_s}
 
 
 def run_iterative(bctx, wb, BIN, BOUT, zb, torch, stream, reps, log2_k=16):

@@ -81,6 +81,9 @@ N17 = Workload("n131072_L4_dnum2", 17, (60,) + (55,) * 3, (61,) * 2, 2, 55.0,
                batch=2, rot_steps=(1, -1, 1 << 15))
 BOOT17_Q_BITS = (60,) + (50,) * 14 + (60,) * 13
 BOOT17 = Workload("n131072_boot_L27_dnum3_b8", 17, BOOT17_Q_BITS, (61,) * 10, 3, 50.0, batch=8)
+# eMLP-3 (Table 3: l = 29 = 13 + 16): two more user levels on the same plan
+BOOT17_L29 = Workload("n131072_boot_L29_dnum3", 17, (60,) + (50,) * 16 + (60,) * 13, (61,) * 10, 3, 50.0,
+                      batch=8)
 
 
 def rng(seed: int, stream: str) -> np.random.Generator:

@@ -217,3 +217,71 @@ def test_emlp2_step_at_2_17_matches_fp64():
         assert ctx.device_error() == 0
     finally:
         ctx.close()
+
+
+def test_emlp3_step_at_2_17_matches_fp64():
+    """eMLP-3 (Table 3: RE-Block(128) -> CE-Block(64) -> RE-Block(32), N = 2^17,
+    l = 29 = 13 + 16): the third block is a RE-Block fed the CE-Block's
+    activations as its single input tile; it ends exactly at level 0 before
+    its bootstrap.  All refreshed weights decrypt to the FP64 computation."""
+    import torch
+    import oracle.reboot as orb
+    import paper_2506_19693_gb300 as ck
+    import paper_2506_19693_gb300.reboot as rb
+    torch.cuda.set_device(0)
+    wb = si.BOOT17_L29
+    dims = [(784, 128), (128, 64), (64, 32)]
+    gs = [rb.Geometry(256, 256, k0, k1, 10) for k0, k1 in dims]
+    os_ = [orb.Geometry(256, 256, k0, k1, 10) for k0, k1 in dims]
+    ctx = ck.Context.from_workload(wb)
+    try:
+        ctx.keygen_boot(1)
+        ctx.boot_setup()
+        for k in sorted(set(gs[0].rotation_steps())):
+            ctx.keygen_galois(ctx.galois_elt(k))
+        b = 2
+        rng = np.random.default_rng(41)
+        x = rng.uniform(0, 1, size=(b, 784))
+        y = np.eye(10)[rng.integers(0, 10, size=b)]
+        ws_ = [rng.normal(0, 1 / np.sqrt(k0), size=(k0, k1)) for k0, k1 in dims]
+        cs_ = [rng.normal(0, 1 / np.sqrt(k1), size=(k1, 10)) for _, k1 in dims]
+        gamma, eta, mu = 0.01, 0.001, 0.9
+        scale, lvl = 2.0 ** wb.log2_scale, len(wb.q_bits) - 17
+        assert lvl == 13
+        seeds = iter(range(9000, 13000))
+        enc = lambda v: ctx.encrypt(ctx.encode(v, lvl, scale), lvl, scale, next(seeds))  # noqa: E731
+        zero = np.zeros(256 * 256)
+        # block 1 (RE), block 2 (CE), block 3 (RE) in their packings
+        P1 = (orb.tile_weights(ws_[0], os_[0]), orb.pack_colwise(cs_[0], os_[0]))
+        P2 = (orb.pack_colwise(ws_[1], os_[1]), orb.pack_rowwise(cs_[1], os_[1]))
+        P3 = (orb.tile_weights(ws_[2], os_[2]), orb.pack_colwise(cs_[2], os_[2]))
+        st1 = ([enc(t) for t in P1[0]], [enc(zero) for _ in P1[0]], enc(P1[1]), enc(zero), None)
+        st2 = (enc(P2[0]), enc(zero), enc(P2[1]), enc(zero), None)
+        st3 = ([enc(t) for t in P3[0]], [enc(zero) for _ in P3[0]], enc(P3[1]), enc(zero), None)
+        xp = [orb.tile_inputs(xi, os_[0]) for xi in x]
+        yexp = [orb.pack_expanded(yi, os_[0]) for yi in y]
+        yrep = [orb.pack_repeated(yi, os_[0]) for yi in y]
+        b1, b2 = rb.REBlock(ctx, gs[0], gamma, eta, mu), rb.CEBlock(ctx, gs[1], gamma, eta, mu)
+        b3 = rb.REBlock(ctx, gs[2], gamma, eta, mu)
+        r1 = b1.step(st1, [[enc(t) for t in xs] for xs in xp], [enc(v) for v in yexp], True)
+        r2 = b2.step(st2, b1.last_activations, [enc(v) for v in yrep], True)
+        ye = [enc(v) for v in yexp]
+        r3 = b3.step(st3, [[a] for a in b2.last_activations], ye, True, bootstrap=False)
+        assert r3[0][0].level == 0  # tau_ReBoot = 13 used exactly
+        r3 = b3.step(st3, [[a] for a in b2.last_activations], ye, True)
+        # FP64
+        p1 = orb.plain_step((P1[0], [zero] * len(P1[0]), P1[1], zero, None), xp, yexp, os_[0], gamma, eta, mu, True)
+        a1 = []
+        for xs in xp:
+            z = orb.plain_sumrows(sum(u * w for u, w in zip(xs, P1[0])), os_[0])
+            a1.append(z * z + z)
+        p2, a2 = orb.plain_step_ce((P2[0], zero, P2[1], zero, None), a1, yrep, os_[1], gamma, eta, mu, True)
+        p3 = orb.plain_step((P3[0], [zero] * len(P3[0]), P3[1], zero, None), [[a] for a in a2], yexp, os_[2],
+                            gamma, eta, mu, True)
+        for ct, want in ((r1[0][0], p1[0][0]), (r2[0], p2[0]), (r2[2], p2[2]), (r3[0][0], p3[0][0]),
+                         (r3[2], p3[2])):
+            assert ct.level == lvl
+            assert np.max(np.abs(ctx.decrypt_decode(ct).real - want)) < 2.0 ** -12
+        assert ctx.device_error() == 0
+    finally:
+        ctx.close()
