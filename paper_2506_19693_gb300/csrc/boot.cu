@@ -513,7 +513,6 @@ struct BV {
   int level = 0;
   double scale = 1.0;
   bool owned = false;
-  int n() const { return (int)v.size(); }
 };
 
 struct Eval {
