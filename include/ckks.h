@@ -327,6 +327,25 @@ int ckks_mul_relin_host(ckks_ctx *ctx, const uint64_t *a_host, const uint64_t *b
                         double scale_b, uint32_t level, int n, int do_rescale, int chunk, uint64_t *out_host,
                         double *out_scale);
 
+/* Packed wire format (no paper counterpart): a ciphertext at level l is its
+ * polynomial 0 then polynomial 1, each the limbs t = 0..l in order, limb t
+ * holding the N residues in bits(q_t) bits each, residue k at bits
+ * [k b, k b + b) of the limb's little-endian 64-bit words.  With 55-bit
+ * primes that is 14% fewer bytes than uint64 limbs.  ckks_wire_bytes gives the
+ * size of one ciphertext at `level`.  export/import pack / unpack on the GPU
+ * (ct's level and capacity as for ckks_ct_export/import); host buffers must
+ * be 8-byte aligned (CKKS_E_PARAM). */
+int ckks_wire_bytes(const ckks_ctx *ctx, uint32_t level, uint64_t *bytes);
+int ckks_ct_export_packed(ckks_ctx *ctx, const ckks_ct *ct, uint8_t *out_host);
+int ckks_ct_import_packed(ckks_ctx *ctx, const uint8_t *in_host, ckks_ct *ct);
+/* ckks_mul_relin_host with packed host buffers: a_host, b_host hold n
+ * ciphertexts of ckks_wire_bytes(level) bytes each, out_host n of
+ * ckks_wire_bytes(level') bytes; the GPU unpacks each chunk after its copy-in
+ * and packs the products before their copy-out. */
+int ckks_mul_relin_host_packed(ckks_ctx *ctx, const uint8_t *a_host, const uint8_t *b_host, double scale_a,
+                               double scale_b, uint32_t level, int n, int do_rescale, int chunk, uint8_t *out_host,
+                               double *out_scale);
+
 /* ---- uneven batches: executor, graph capture, tuning ------------------- */
 
 #define CKKS_OP_MUL_RELIN 1 /* out = a * b relinearised (rescaled when rescale != 0) */

@@ -120,6 +120,11 @@ SIGNATURES = {
                             ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_double)]),
     "ckks_ct_export": (_I, [_V, _CTP, _V]),
     "ckks_ct_import": (_I, [_V, _V, _CTP]),
+    "ckks_wire_bytes": (_I, [_V, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)]),
+    "ckks_ct_export_packed": (_I, [_V, _CTP, _V]),
+    "ckks_ct_import_packed": (_I, [_V, _V, _CTP]),
+    "ckks_mul_relin_host_packed": (_I, [_V, _V, _V, ctypes.c_double, ctypes.c_double, ctypes.c_uint32, _I, _I, _I,
+                                        _V, ctypes.POINTER(ctypes.c_double)]),
     "ckks_status_str": (ctypes.c_char_p, [_I]),
 }
 
@@ -584,6 +589,41 @@ class Context:
         assert host.device.type == "cpu" and host.is_contiguous() and host.numel() >= 2 * (ct.level + 1) * self.n
         h = ct.handle(self.log_n)
         _check(self.lib.ckks_ct_import(self._h, host.data_ptr(), ctypes.byref(h)), "ckks_ct_import")
+
+    # ---- packed wire format ----
+    def wire_bytes(self, level: int) -> int:
+        b = ctypes.c_uint64()
+        _check(self.lib.ckks_wire_bytes(self._h, level, ctypes.byref(b)), "ckks_wire_bytes")
+        return int(b.value)
+
+    def export_packed(self, ct: Ciphertext, host=None):
+        """Pack on the GPU and copy out: a uint8 numpy array, or into `host`
+        (an 8-byte aligned CPU torch tensor of at least wire_bytes bytes)."""
+        h = ct.handle(self.log_n)
+        if host is None:
+            out = np.zeros(self.wire_bytes(ct.level) // 8, dtype=np.uint64)
+            _check(self.lib.ckks_ct_export_packed(self._h, ctypes.byref(h), out.ctypes.data), "ckks_ct_export_packed")
+            return out.view(np.uint8)
+        _check(self.lib.ckks_ct_export_packed(self._h, ctypes.byref(h), host.data_ptr()), "ckks_ct_export_packed")
+        return host
+
+    def import_packed(self, data, level: int, scale: float, n_limbs: int | None = None) -> Ciphertext:
+        ct = self.new_ct(n_limbs or level + 1, level, scale)
+        h = ct.handle(self.log_n)
+        ptr = data.data_ptr() if hasattr(data, "data_ptr") else np.ascontiguousarray(data).ctypes.data
+        _check(self.lib.ckks_ct_import_packed(self._h, ptr, ctypes.byref(h)), "ckks_ct_import_packed")
+        return ct
+
+    def mul_relin_host_packed(self, a_host, b_host, scale_a: float, scale_b: float, level: int, out_host,
+                              rescale: int = RESCALE_NONE, chunk: int = 16) -> float:
+        """ckks_mul_relin_host on packed host buffers (page-locked uint8 torch
+        tensors of n x wire_bytes(level) and n x wire_bytes(level') bytes)."""
+        n = int(a_host.numel() // self.wire_bytes(level))
+        sc = ctypes.c_double()
+        _check(self.lib.ckks_mul_relin_host_packed(self._h, a_host.data_ptr(), b_host.data_ptr(), scale_a, scale_b,
+                                                   level, n, int(rescale), chunk, out_host.data_ptr(),
+                                                   ctypes.byref(sc)), "ckks_mul_relin_host_packed")
+        return sc.value
 
     def import_ct(self, arr: np.ndarray, level: int, scale: float, n_limbs: int | None = None) -> Ciphertext:
         arr = np.ascontiguousarray(arr, dtype=np.uint64)

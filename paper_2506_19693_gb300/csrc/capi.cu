@@ -1043,9 +1043,11 @@ int ckks_rotate_batch(ckks_ctx *c, const ckks_ct *in, const int32_t *k, ckks_ct 
   return CKKS_OK;
 }
 
-int ckks_mul_relin_host(ckks_ctx *c, const uint64_t *a_host, const uint64_t *b_host, double scale_a,
-                        double scale_b, uint32_t level, int n, int do_rescale, int chunk, uint64_t *out_host,
-                        double *out_scale) {
+// The host-streamed multiply in either wire format: raw (uint64 limbs) or
+// packed (limbs at their primes' bit widths, unpacked and packed on the GPU).
+static int mul_relin_host_impl(ckks_ctx *c, const void *a_host, const void *b_host, double scale_a,
+                               double scale_b, uint32_t level, int n, int do_rescale, int chunk, void *out_host,
+                               double *out_scale, bool packed) {
   if (!c || !a_host || !b_host || !out_host || n < 0 || chunk < 1 || chunk > MAX_CTS) return CKKS_E_PARAM;
   if (level >= (uint32_t)c->n_q) return CKKS_E_LEVEL;
   if (do_rescale < CKKS_RESCALE_NONE || do_rescale > CKKS_RESCALE_MERGED) return CKKS_E_PARAM;
@@ -1055,7 +1057,11 @@ int ckks_mul_relin_host(ckks_ctx *c, const uint64_t *a_host, const uint64_t *b_h
   const u32 nn = c->n;
   const uint32_t out_level = do_rescale ? level - 1 : level;
   const size_t in_w = (size_t)2 * (level + 1) * nn, out_w = (size_t)2 * (out_level + 1) * nn;
-  const size_t slot_w = (size_t)chunk * 3 * in_w;  // a, b and the product (full capacity) per pair
+  const WireLayout Lin = wire_layout(c, (int)level), Lout = wire_layout(c, (int)out_level);
+  const size_t win = packed ? (size_t)2 * Lin.off[Lin.nl] / 8 : 0;    // words per packed input
+  const size_t wout = packed ? (size_t)2 * Lout.off[Lout.nl] / 8 : 0;  // words per packed output
+  // per slot: a, b and the product (full capacity), then the packed a, b and product
+  const size_t slot_w = (size_t)chunk * (3 * in_w + 2 * win + wout);
   if (!c->h2d) CK_CUDA(cudaStreamCreateWithFlags(&c->h2d, cudaStreamNonBlocking));
   if (!c->d2h) CK_CUDA(cudaStreamCreateWithFlags(&c->d2h, cudaStreamNonBlocking));
   for (int i = 0; i < 3; ++i) {
@@ -1099,43 +1105,126 @@ int ckks_mul_relin_host(ckks_ctx *c, const uint64_t *a_host, const uint64_t *b_h
     sizes.insert(sizes.end(), tail.rbegin(), tail.rend());
   }
   const int nchunks = (int)sizes.size();
+  const u64 *a64 = static_cast<const u64 *>(a_host), *b64 = static_cast<const u64 *>(b_host);
+  u64 *o64 = static_cast<u64 *>(out_host);
   for (int ci = 0, i0 = 0; ci < nchunks; i0 += sizes[ci], ++ci) {
     const int s = ci % 3, cnt = sizes[ci];
     u64 *sa = c->stage + (size_t)s * slot_w, *sb = sa + (size_t)chunk * in_w, *so = sb + (size_t)chunk * in_w;
+    u64 *pa = so + (size_t)chunk * in_w, *pb = pa + (size_t)chunk * win, *po = pb + (size_t)chunk * win;
     // inputs of this chunk, once the slot's previous products have left
     CK_CUDA(cudaStreamWaitEvent(c->h2d, c->ev_out[s], 0));
-    CK_CUDA(cudaMemcpyAsync(sa, a_host + (size_t)i0 * in_w, sizeof(u64) * cnt * in_w, cudaMemcpyHostToDevice,
+    const size_t iw = packed ? win : in_w;
+    CK_CUDA(cudaMemcpyAsync(packed ? pa : sa, a64 + (size_t)i0 * iw, sizeof(u64) * cnt * iw, cudaMemcpyHostToDevice,
                             c->h2d));
-    CK_CUDA(cudaMemcpyAsync(sb, b_host + (size_t)i0 * in_w, sizeof(u64) * cnt * in_w, cudaMemcpyHostToDevice,
+    CK_CUDA(cudaMemcpyAsync(packed ? pb : sb, b64 + (size_t)i0 * iw, sizeof(u64) * cnt * iw, cudaMemcpyHostToDevice,
                             c->h2d));
     CK_CUDA(cudaEventRecord(c->ev_in[s], c->h2d));
     // the products on the context stream
     CK_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in[s], 0));
     std::vector<ckks_ct> ha(cnt), hb(cnt), ho(cnt);
+    std::vector<unsigned char *> wa(cnt), wb(cnt), wo(cnt);
+    std::vector<u64 *> ca(cnt), cb(cnt), co(cnt);
+    std::vector<u32> nlim(cnt, level + 1);
     for (int i = 0; i < cnt; ++i) {
       const uint32_t ln = (uint32_t)c->log_n;
       ha[i] = ckks_ct{sa + (size_t)i * in_w, ln, level, level + 1, 1, scale_a};
       hb[i] = ckks_ct{sb + (size_t)i * in_w, ln, level, level + 1, 1, scale_b};
       ho[i] = ckks_ct{so + (size_t)i * in_w, ln, level, level + 1, 1, 1.0};
+      wa[i] = reinterpret_cast<unsigned char *>(pa + (size_t)i * win);
+      wb[i] = reinterpret_cast<unsigned char *>(pb + (size_t)i * win);
+      wo[i] = reinterpret_cast<unsigned char *>(po + (size_t)i * wout);
+      ca[i] = ha[i].data;
+      cb[i] = hb[i].data;
+      co[i] = ho[i].data;
     }
-    int rc = ckks_mul_relin_batch(c, ha.data(), hb.data(), ho.data(), cnt, do_rescale);
+    int rc = CKKS_OK;
+    if (packed) {
+      rc = ew_wire(c, Lin, wa.data(), ca.data(), nlim.data(), cnt, false);
+      if (!rc) rc = ew_wire(c, Lin, wb.data(), cb.data(), nlim.data(), cnt, false);
+      if (rc) return rc;
+    }
+    rc = ckks_mul_relin_batch(c, ha.data(), hb.data(), ho.data(), cnt, do_rescale);
     if (rc) return rc;
+    if (packed) {
+      rc = ew_wire(c, Lout, wo.data(), co.data(), nlim.data(), cnt, true);
+      if (rc) return rc;
+    }
     sc = ho[0].scale;
     CK_CUDA(cudaEventRecord(c->ev_comp[s], c->stream));
-    // the products back: the active limbs of both polynomials, contiguous per pair
+    // the products back
     CK_CUDA(cudaStreamWaitEvent(c->d2h, c->ev_comp[s], 0));
-    const size_t half = out_w / 2;
-    for (int i = 0; i < cnt; ++i) {
-      u64 *dst = out_host + (size_t)(i0 + i) * out_w;
-      CK_CUDA(cudaMemcpyAsync(dst, ho[i].data, sizeof(u64) * half, cudaMemcpyDeviceToHost, c->d2h));
-      CK_CUDA(cudaMemcpyAsync(dst + half, ho[i].data + (size_t)(level + 1) * nn, sizeof(u64) * half,
-                              cudaMemcpyDeviceToHost, c->d2h));
+    if (packed) {  // contiguous per chunk
+      CK_CUDA(cudaMemcpyAsync(o64 + (size_t)i0 * wout, po, sizeof(u64) * cnt * wout, cudaMemcpyDeviceToHost,
+                              c->d2h));
+    } else {  // the active limbs of both polynomials, contiguous per pair
+      const size_t half = out_w / 2;
+      for (int i = 0; i < cnt; ++i) {
+        u64 *dst = o64 + (size_t)(i0 + i) * out_w;
+        CK_CUDA(cudaMemcpyAsync(dst, ho[i].data, sizeof(u64) * half, cudaMemcpyDeviceToHost, c->d2h));
+        CK_CUDA(cudaMemcpyAsync(dst + half, ho[i].data + (size_t)(level + 1) * nn, sizeof(u64) * half,
+                                cudaMemcpyDeviceToHost, c->d2h));
+      }
     }
     CK_CUDA(cudaEventRecord(c->ev_out[s], c->d2h));
   }
   CK_CUDA(cudaStreamSynchronize(c->d2h));
   if (out_scale) *out_scale = sc;
   return last_err();
+}
+
+int ckks_mul_relin_host(ckks_ctx *c, const uint64_t *a_host, const uint64_t *b_host, double scale_a,
+                        double scale_b, uint32_t level, int n, int do_rescale, int chunk, uint64_t *out_host,
+                        double *out_scale) {
+  return mul_relin_host_impl(c, a_host, b_host, scale_a, scale_b, level, n, do_rescale, chunk, out_host, out_scale,
+                             false);
+}
+
+int ckks_mul_relin_host_packed(ckks_ctx *c, const uint8_t *a_host, const uint8_t *b_host, double scale_a,
+                               double scale_b, uint32_t level, int n, int do_rescale, int chunk, uint8_t *out_host,
+                               double *out_scale) {
+  if (((uintptr_t)a_host | (uintptr_t)b_host | (uintptr_t)out_host) & 7) return CKKS_E_PARAM;
+  return mul_relin_host_impl(c, a_host, b_host, scale_a, scale_b, level, n, do_rescale, chunk, out_host, out_scale,
+                             true);
+}
+
+int ckks_wire_bytes(const ckks_ctx *c, uint32_t level, uint64_t *bytes) {
+  if (!c || !bytes) return CKKS_E_PARAM;
+  if (level >= (uint32_t)c->n_q) return CKKS_E_LEVEL;
+  const WireLayout L = wire_layout(c, (int)level);
+  *bytes = (uint64_t)2 * L.off[L.nl];
+  return CKKS_OK;
+}
+
+int ckks_ct_export_packed(ckks_ctx *c, const ckks_ct *ct, uint8_t *out) {
+  if (!c || !ct_ok(c, ct) || !out || ((uintptr_t)out & 7)) return CKKS_E_PARAM;
+  const WireLayout L = wire_layout(c, (int)ct->level);
+  const size_t bytes = (size_t)2 * L.off[L.nl];
+  int rc = ensure_scratch(c, bytes / 8);
+  if (rc) return rc;
+  unsigned char *w = reinterpret_cast<unsigned char *>(c->scratch);
+  u64 *d = ct->data;
+  const u32 nl = ct->n_limbs;
+  rc = ew_wire(c, L, &w, &d, &nl, 1, true);
+  if (rc) return rc;
+  CK_CUDA(cudaMemcpyAsync(out, w, bytes, cudaMemcpyDeviceToHost, c->stream));
+  CK_CUDA(cudaStreamSynchronize(c->stream));
+  return CKKS_OK;
+}
+
+int ckks_ct_import_packed(ckks_ctx *c, const uint8_t *in, ckks_ct *ct) {
+  if (!c || !ct_ok(c, ct) || !in || ((uintptr_t)in & 7)) return CKKS_E_PARAM;
+  const WireLayout L = wire_layout(c, (int)ct->level);
+  const size_t bytes = (size_t)2 * L.off[L.nl];
+  int rc = ensure_scratch(c, bytes / 8);
+  if (rc) return rc;
+  unsigned char *w = reinterpret_cast<unsigned char *>(c->scratch);
+  CK_CUDA(cudaMemcpyAsync(w, in, bytes, cudaMemcpyHostToDevice, c->stream));
+  u64 *d = ct->data;
+  const u32 nl = ct->n_limbs;
+  rc = ew_wire(c, L, &w, &d, &nl, 1, false);
+  if (rc) return rc;
+  CK_CUDA(cudaStreamSynchronize(c->stream));
+  return CKKS_OK;
 }
 
 int ckks_ct_export(ckks_ctx *c, const ckks_ct *ct, uint64_t *out) {

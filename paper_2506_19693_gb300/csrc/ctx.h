@@ -139,6 +139,22 @@ int ensure_fscratch(ckks_ctx *c, size_t words);
 int launch_ntt(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, int nl,
                const int *mods, bool inverse);
 
+// ---- packed wire format (ops.cu) ----
+// A ciphertext at level l on the wire: polynomial 0 then polynomial 1, each
+// the limbs t = 0..l in order, limb t packed as N residues of bits(q_t) bits
+// (little-endian bit order within 64-bit words).  off[t] = byte offset of
+// limb t in one polynomial, off[l+1] = the polynomial's size.
+struct WireLayout {
+  int nl = 0;
+  unsigned char bits[MAX_MODS];
+  u32 off[MAX_MODS + 1];
+};
+WireLayout wire_layout(const ckks_ctx *c, int level);
+// unpack (to_wire false) or pack ncts ciphertexts between wire[i] and ct[i]
+// ([2][n_limbs[i]][N] limb-major); ncts <= MAX_CTS.
+int ew_wire(ckks_ctx *c, const WireLayout &L, unsigned char *const *wire, u64 *const *ct, const u32 *n_limbs,
+            int ncts, bool to_wire);
+
 // ---- element-wise and key-switch launchers (ops.cu / keyswitch.cu) ----
 // ---- tensor-core basis conversion (bconv_tc.cu) ----
 // src_add_host [ns] / dst_sub_host [nt] (or null): constants added to y_i

@@ -197,10 +197,92 @@ __global__ void k_square(u64 *out, const u64 *in, const ModInfo *mods, u32 n) {
   out[off] = mulmod(in[off], in[off], mods[t]);
 }
 
+struct WireArgs {
+  u32 n;
+  int nl;
+  unsigned char bits[MAX_MODS];
+  u32 off[MAX_MODS + 1];
+  unsigned char *wire[MAX_CTS];
+  u64 *ct[MAX_CTS];
+  u32 n_limbs[MAX_CTS];
+};
+
+// residue k of limb t: bits [k b, k b + b) of the limb's 64-bit words
+__global__ void k_unpack(const WireArgs a) {
+  const u32 k = blockIdx.x * TPB + threadIdx.x;
+  const int t = blockIdx.y, i = blockIdx.z >> 1, pl = blockIdx.z & 1;
+  if (k >= a.n) return;
+  const u64 *src = reinterpret_cast<const u64 *>(a.wire[i] + (size_t)pl * a.off[a.nl] + a.off[t]);
+  const u32 b = a.bits[t];
+  const u64 o = (u64)k * b;
+  const u32 w = (u32)(o >> 6), sh = (u32)(o & 63);
+  u64 v = __ldg(src + w) >> sh;
+  if (sh + b > 64) v |= __ldg(src + w + 1) << (64 - sh);
+  if (b < 64) v &= (1ULL << b) - 1;
+  a.ct[i][((size_t)pl * a.n_limbs[i] + t) * a.n + k] = v;
+}
+
+// 64-bit word j of limb t: the residues overlapping bits [64 j, 64 j + 64)
+__global__ void k_pack(const WireArgs a) {
+  const u32 j = blockIdx.x * TPB + threadIdx.x;
+  const int t = blockIdx.y, i = blockIdx.z >> 1, pl = blockIdx.z & 1;
+  const u32 b = a.bits[t];
+  if ((u64)j * 64 >= (u64)a.n * b) return;
+  const u64 *src = a.ct[i] + ((size_t)pl * a.n_limbs[i] + t) * a.n;
+  u64 acc = 0;
+  for (u32 k = (u32)(((u64)j * 64) / b); k < a.n && (u64)k * b < (u64)(j + 1) * 64; ++k) {
+    const long long s = (long long)k * b - (long long)j * 64;
+    const u64 v = src[k];
+    acc |= s >= 0 ? v << s : v >> (-s);
+  }
+  reinterpret_cast<u64 *>(a.wire[i] + (size_t)pl * a.off[a.nl] + a.off[t])[j] = acc;
+}
+
 dim3 grid_for(u32 n, int limbs, int cts) { return dim3((n + TPB - 1) / TPB, limbs, cts); }
 int last_status() { return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_CUDA; }
 
 }  // namespace
+
+WireLayout wire_layout(const ckks_ctx *c, int level) {
+  WireLayout L;
+  L.nl = level + 1;
+  u32 off = 0;
+  for (int t = 0; t < L.nl; ++t) {
+    int b = 0;
+    while (b < 64 && (c->mod[t] >> b)) ++b;
+    L.bits[t] = (unsigned char)b;
+    L.off[t] = off;
+    off += (u32)((u64)c->n * b / 8);
+  }
+  L.off[L.nl] = off;
+  return L;
+}
+
+int ew_wire(ckks_ctx *c, const WireLayout &L, unsigned char *const *wire, u64 *const *ct, const u32 *n_limbs,
+            int ncts, bool to_wire) {
+  if (ncts <= 0) return CKKS_OK;
+  if (ncts > MAX_CTS || c->n % 64) return CKKS_E_PARAM;
+  WireArgs a;
+  a.n = c->n;
+  a.nl = L.nl;
+  for (int t = 0; t < L.nl; ++t) a.bits[t] = L.bits[t];
+  for (int t = 0; t <= L.nl; ++t) a.off[t] = L.off[t];
+  for (int i = 0; i < ncts; ++i) {
+    if (((uintptr_t)wire[i] & 7) || n_limbs[i] < (u32)L.nl) return CKKS_E_PARAM;
+    a.wire[i] = wire[i];
+    a.ct[i] = ct[i];
+    a.n_limbs[i] = n_limbs[i];
+  }
+  if (to_wire) {
+    const u32 words = c->n;  // at most N words per limb (64-bit primes); the kernel stops at N b / 64
+    PROF_LAUNCH(c, PK_ELEMENTWISE, (u64)L.nl * 2 * ncts,
+                (k_pack<<<grid_for(words, L.nl, 2 * ncts), TPB, 0, c->stream>>>(a)));
+  } else {
+    PROF_LAUNCH(c, PK_ELEMENTWISE, (u64)L.nl * 2 * ncts,
+                (k_unpack<<<grid_for(c->n, L.nl, 2 * ncts), TPB, 0, c->stream>>>(a)));
+  }
+  return last_status();
+}
 
 int ew_addsub(ckks_ctx *c, EwArgs &a, int nl, int ncts, bool sub) {
   a.mods = c->d_mods;
