@@ -95,12 +95,31 @@ class REBlock:
     """One RE-Block on a bootstrapping-capable context (keys: relinearisation,
     conjugation, bootstrapping rotations and Geometry.rotation_steps())."""
 
-    def __init__(self, ctx, g: Geometry, gamma: float, eta: float, mu: float, mask_coeffs=None):
+    def __init__(self, ctx, g: Geometry, gamma: float, eta: float, mu: float, mask_coeffs=None,
+                 iterative_log2_k: int | None = None):
         self.ctx = ctx
         self.g = g
         self.gamma, self.eta, self.mu = gamma, eta, mu
         self._mask_coeffs = mask_coeffs
         self._mask_pt = {}
+        # None: one bootstrap per weight ciphertext (reading C16); k: the
+        # two-pass iterative bootstrap with 2^k (reading B12), the other
+        # reading of the step's "two iterations of approximate bootstrapping"
+        self.iterative_log2_k = iterative_log2_k
+
+    def refresh(self, cts):
+        """Bootstrap the block's updated weights and velocities."""
+        if self.iterative_log2_k is None:
+            return self.ctx.bootstrap_batch(cts)
+        # the iterative batch takes one input scale: one call per scale
+        groups = {}
+        for i, c in enumerate(cts):
+            groups.setdefault(c.scale, []).append(i)
+        out = [None] * len(cts)
+        for idx in groups.values():
+            for i, r in zip(idx, self.ctx.bootstrap_iterative_batch([cts[i] for i in idx], self.iterative_log2_k)):
+                out[i] = r
+        return out
 
     # ---- list helpers: every list shares one level and one scale ----
     @staticmethod
@@ -249,7 +268,7 @@ class REBlock:
         new = (nw, nv, ws1[0], vs1[0], dWs)
         if not bootstrap:
             return new
-        refreshed = self.ctx.bootstrap_batch(nw + nv + ws1 + vs1)
+        refreshed = self.refresh(nw + nv + ws1 + vs1)
         return refreshed[:T], refreshed[T:2 * T], refreshed[2 * T], refreshed[2 * T + 1], dWs
 
 
@@ -291,5 +310,5 @@ class CEBlock(REBlock):
         ws1, vs1 = self.update([Ws], [Vs], grad_s, first)
         if not bootstrap:
             return nw[0], nv[0], ws1[0], vs1[0], dWs[0]
-        refreshed = self.ctx.bootstrap_batch(nw + nv + ws1 + vs1)
+        refreshed = self.refresh(nw + nv + ws1 + vs1)
         return refreshed[0], refreshed[1], refreshed[2], refreshed[3], dWs[0]

@@ -285,3 +285,43 @@ def test_emlp3_step_at_2_17_matches_fp64():
         assert ctx.device_error() == 0
     finally:
         ctx.close()
+
+
+def test_reboot_step_with_iterative_bootstrap_is_more_precise():
+    """The other reading of the step's two bootstrapping iterations (C16 / B12):
+    with the two-pass bootstrap the refreshed weights are much closer to FP64."""
+    import torch
+    import oracle.reboot as orb
+    import paper_2506_19693_gb300 as ck
+    import paper_2506_19693_gb300.reboot as rb
+    torch.cuda.set_device(0)
+    wb = si.BOOT
+    g, go = rb.Geometry(256, 128, 784, 128, 10), orb.Geometry(256, 128, 784, 128, 10)
+    ctx = ck.Context.from_workload(wb)
+    try:
+        ctx.keygen_boot(1)
+        ctx.boot_setup()
+        for k in g.rotation_steps():
+            ctx.keygen_galois(ctx.galois_elt(k))
+        x, y, w, ws = _data(7, 2, g.k0, g.k1, g.o)
+        gamma, eta, mu = 0.01, 0.001, 0.9
+        scale, lvl = 2.0 ** wb.log2_scale, len(wb.q_bits) - 17
+        seeds = iter(range(20000, 30000))
+        enc = lambda v: ctx.encrypt(ctx.encode(v, lvl, scale), lvl, scale, next(seeds))  # noqa: E731
+        Wp, Wsp = orb.tile_weights(w, go), orb.pack_colwise(ws, go)
+        zero = np.zeros(g.r * g.c)
+        xs = [[enc(t) for t in orb.tile_inputs(xi, go)] for xi in x]
+        ys = [enc(orb.pack_expanded(yi, go)) for yi in y]
+        ref = orb.plain_step((Wp, [zero] * len(Wp), Wsp, zero, None), [orb.tile_inputs(xi, go) for xi in x],
+                             [orb.pack_expanded(yi, go) for yi in y], go, gamma, eta, mu, True)
+        errs = {}
+        for k in (None, 16):
+            st = ([enc(t) for t in Wp], [enc(zero) for _ in Wp], enc(Wsp), enc(zero), None)
+            r = rb.REBlock(ctx, g, gamma, eta, mu, iterative_log2_k=k).step(st, xs, ys, True)
+            assert r[0][0].level == lvl
+            errs[k] = max(np.max(np.abs(ctx.decrypt_decode(c).real - want))
+                          for c, want in zip(r[0] + [r[2]], ref[0] + [ref[2]]))
+        assert errs[None] < 2.0 ** -12 and errs[16] < 2.0 ** -26 and errs[16] < errs[None] / 64, errs
+        assert ctx.device_error() == 0
+    finally:
+        ctx.close()
