@@ -236,6 +236,13 @@ int ckks_automorph(ckks_ctx *ctx, const ckks_ct *a, uint64_t galois_elt, ckks_ct
  * degree-60 Chebyshev coefficients of EvalMod (B6).  Run once per context,
  * before ckks_bootstrap; keys come from ckks_keygen_from_seed(want_boot=1). */
 int ckks_boot_setup(ckks_ctx *ctx);
+/* Sparse slots (reading B13): bootstrap messages of n_slots (a power of two,
+ * 2 .. N/2) complex slots, each stored as the full-slot vector repeated with
+ * period n_slots (ckks_encode of the repeated vector).  The circuit adds the
+ * sub-sum rotations by n_slots 2^i after ModRaise and runs n_slots-point
+ * transforms.  Call before ckks_keygen_from_seed(want_boot=1) and
+ * ckks_boot_setup; CKKS_E_STATE once a plan with another count exists. */
+int ckks_boot_set_slots(ckks_ctx *ctx, uint32_t n_slots);
 /* Left-rotation steps the circuit uses (sorted); returns their count and
  * writes up to cap of them to out (NULL allowed). */
 int ckks_boot_rotation_steps(ckks_ctx *ctx, int32_t *out, int cap);

@@ -59,6 +59,13 @@ is named B1..B8 and listed in the design notes:
      giving ct2 ~ 2^k e1 + e2.  The result 2^k ct1 - ct2, read at scale
      2^k * (ct1's scale), decrypts to m - e2 / 2^k at ct1's level: the
      division by 2^k is a change of the scale label, so no level is spent.
+  B13 Sparse slots (n = 2^s < N/2): a message of n slots is the full-slot
+     vector of period n, i.e. a polynomial in X^(N/2n).  After ModRaise the
+     sub-sum x <- x + Rot(x, n 2^i), i < log2(N/2n), is the trace onto that
+     subring: it keeps d = N/(2n) times the subring part (q0 I included) and
+     cancels the rest; 1/d joins the first CoeffToSlot level's 1/(2K).  The
+     linear levels are the n-slot transforms with their diagonals repeated
+     across the N/2 slots; EvalMod and SlotToCoeff are unchanged.
 Parity unpinned: nothing here (see tests/test_oracle_bootstrap.py).
 """
 from __future__ import annotations
@@ -242,21 +249,28 @@ class BootPlan:
     cheb: np.ndarray
     k_range: int = K_RANGE
 
+    @property
+    def subsum_steps(self) -> list:
+        """B13: rotations by n_slots 2^i, i < log2(N / (2 n_slots)) (none at full slots)."""
+        return [self.n_slots << i for i in range(int(math.log2(self.n // (2 * self.n_slots))))]
+
     def rotation_steps(self) -> list:
-        rs = set()
+        rs = set(self.subsum_steps)
         for lv in self.cts + self.stc:
             rs |= lv.rotations(self.n_slots)
         return sorted(rs)
 
 
-def make_plan(log_n: int, n_q: int) -> BootPlan:
+def make_plan(log_n: int, n_q: int, log_slots: int | None = None) -> BootPlan:
     n = 1 << log_n
-    ns = n // 2
+    ns = n // 2 if log_slots is None else 1 << log_slots
     top = n_q - 1
     cts = linear_levels(ns, inverse=True)
     stc = linear_levels(ns, inverse=False)
-    # B4: fold 1/(2K) into the first CoeffToSlot level and 1/(2 pi) into the first SlotToCoeff level
-    cts[0].diags = {d: v / (2 * K_RANGE) for d, v in cts[0].diags.items()}
+    # B4: fold 1/(2K) into the first CoeffToSlot level and 1/(2 pi) into the first SlotToCoeff level;
+    # B13: with sparse slots also 1/d, d = N / (2 n_slots), which the sub-sum multiplies in
+    sparse = n // (2 * ns)
+    cts[0].diags = {d: v / (2 * K_RANGE * sparse) for d, v in cts[0].diags.items()}
     stc[0].diags = {d: v / (2 * np.pi) for d, v in stc[0].diags.items()}
     for i, lv in enumerate(cts):
         lv.level = top - i
@@ -273,11 +287,12 @@ def encode_constants(orc: Oracle, plan: BootPlan) -> list:
     CoeffToSlot levels, then SlotToCoeff levels; per level ascending giant b,
     then ascending baby a; each encoded at the scale of the level's prime."""
     out = []
+    reps = plan.n // (2 * plan.n_slots)  # B13: a sparse diagonal repeats across the N/2 slots
     for lv in plan.cts + plan.stc:
         scale = float(orc.q[lv.level])
         for _, items in lv.plan:
             for _, vec in items:
-                out.append(orc.encode(vec, scale))
+                out.append(orc.encode(np.tile(vec, reps), scale))
     return out
 
 
@@ -423,7 +438,7 @@ class Evaluator:
                 X = (X + inner) % extq
                 continue
             c = OCt(np.stack([o.moddown(inner[p], l) for p in range(2)]), l, x.scale)
-            g = o.galois_elt(lv.g * b * lv.step)
+            g = o.galois_elt((lv.g * b * lv.step) % self.plan.n_slots)  # B13: amounts taken mod the slot count
             t = self.sigma(c, g)
             X = (X + o.keyswitch_ext(t.data[1], l, g)) % extq
             base[0] = (base[0] + t.data[0]) % qcol
@@ -517,6 +532,8 @@ class Evaluator:
         o = self.o
         delta = ct.scale
         x = self.mod_raise(self.drop(ct, 0))
+        for k in self.plan.subsum_steps:  # B13: the trace onto the subring of the sparse slots
+            x = o.add(x, o.rotate(x, k))
         ncts = len(self.plan.cts)
         for i, lv in enumerate(self.plan.cts):
             x = self.linear(x, lv, self.pts[i])

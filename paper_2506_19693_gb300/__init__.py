@@ -108,6 +108,7 @@ SIGNATURES = {
     "ckks_boot_export": (_I, [_V, _V, _I, _V, _I]),
     "ckks_bootstrap": (_I, [_V, _CTP, _CTP]),
     "ckks_bootstrap_batch": (_I, [_V, _CTP, _CTP, _I]),
+    "ckks_boot_set_slots": (_I, [_V, ctypes.c_uint32]),
     "ckks_bootstrap_iterative_batch": (_I, [_V, _CTP, _CTP, _I, _I]),
     "ckks_exec": (_I, [_V, _I]),
     "ckks_exec_capture": (_I, [_V, _I, _V, ctypes.POINTER(_V)]),
@@ -518,6 +519,10 @@ class Context:
         arr = (ctypes.c_int32 * max(1, len(rot_steps)))(*rot_steps)
         _check(self.lib.ckks_keygen_from_seed(self._h, seed, arr, len(rot_steps), int(conj), 1),
                "ckks_keygen_from_seed")
+
+    def boot_set_slots(self, n_slots: int) -> None:
+        """Sparse-slot bootstrapping (before keygen_boot and boot_setup)."""
+        _check(self.lib.ckks_boot_set_slots(self._h, n_slots), "ckks_boot_set_slots")
 
     def boot_setup(self) -> None:
         _check(self.lib.ckks_boot_setup(self._h), "ckks_boot_setup")

@@ -148,6 +148,12 @@ __global__ void k_diag_gather(const double2 *D, double2 *vec, DiagShape s, int i
   vec[r] = make_double2(v.x * factor, v.y * factor);
 }
 
+// B13: a diagonal of n_slots entries repeated across the N/2 slots
+__global__ void k_tile_slots(double2 *vec, int n_slots, int half_n) {
+  const int i = blockIdx.x * TPB + threadIdx.x;
+  if (i >= n_slots && i < half_n) vec[i] = vec[i % n_slots];
+}
+
 // c_k = 2/(d+1) sum_j f(x_j) cos(k pi (j + 1/2)/(d+1)), c_0 halved;
 // f(x) = cos(2 pi (K x - 1/4) / 2^r)
 __global__ void k_cheb(double *c, int d, double kr, int r) {
@@ -401,7 +407,7 @@ int boot_ensure_plan(ckks_ctx *c) {
   if (!c->boot) c->boot = new BootState();
   BootState &b = *c->boot;
   b.top = c->n_q - 1;
-  b.n_slots = (int)(c->n / 2);
+  b.n_slots = (int)(c->boot_slots ? c->boot_slots : c->n / 2);
   make_levels(b.n_slots, true, b.cts);
   make_levels(b.n_slots, false, b.stc);
   int idx = 0;
@@ -433,6 +439,7 @@ int boot_rotation_steps(ckks_ctx *c, std::vector<int> &steps) {
   if (rc) return rc;
   const BootState &b = *c->boot;
   std::set<int> rs;
+  for (int k = b.n_slots; k < (int)(c->n / 2); k <<= 1) rs.insert(k);  // B13: the sub-sum
   for (const auto *lvs : {&b.cts, &b.stc})
     for (const LinLevel &lv : *lvs)
       for (const Giant &gi : lv.plan) {
@@ -496,6 +503,8 @@ int level_constants(ckks_ctx *c, const LinLevel &lv, double factor, double2 *D0,
         int rc = alloc_pt(c, lv.level, &b.pts[idx]);
         if (rc) return rc;
       }
+      if (n < c->n / 2)
+        k_tile_slots<<<(c->n / 2 + TPB - 1) / TPB, TPB, 0, c->stream>>>(vec, (int)n, (int)(c->n / 2));
       int rc = encode_device_z_ext(c, vec, lv.level, scale, b.pts[idx], flag);
       if (rc) return rc;
       ++idx;
@@ -975,7 +984,8 @@ struct Eval {
       }
       if (!err) err = ks_moddown_finish(c, l, nct, acc.data(), o0.data(), o1.data(), c->scratch);
       sync_fields(cb);
-      const u64 gal = ckks_galois_elt(c, lv.g * lv.plan[j].b * lv.step);
+      const int amt = lv.g * lv.plan[j].b * lv.step;
+      const u64 gal = ckks_galois_elt(c, (amt % b.n_slots + b.n_slots) % b.n_slots);  // B13: mod the slots
       if (!err) err = rotate_accumulate_chunk(c, cb.v.data(), gal, nct, X.data(), b0.data(), true);
       release(cb);
     }
@@ -1131,6 +1141,13 @@ static BV boot_core(Eval &ev, const ckks_ct *in) {
   ckks_ctx *c = ev.c;
   BootState &b = *c->boot;
   BV x = ev.mod_raise(in);
+  for (int k = b.n_slots; k < (int)(c->n / 2) && !ev.err; k <<= 1) {  // B13: the trace onto the subring
+    BV r = ev.automorph(x, ckks_galois_elt(c, k));
+    BV y = ev.addsub(x, r, false);
+    ev.release(x);
+    ev.release(r);
+    x = y;
+  }
   for (const LinLevel &lv : b.cts) {
     BV y = ev.linear(x, lv);
     ev.release(x);
@@ -1179,6 +1196,13 @@ static int boot_copy_out(Eval &ev, const BV &v, ckks_ct *out, const double *scal
 
 extern "C" {
 
+int ckks_boot_set_slots(ckks_ctx *c, uint32_t n_slots) {
+  if (!c || n_slots < 2 || n_slots > c->n / 2 || (n_slots & (n_slots - 1))) return CKKS_E_PARAM;
+  if (c->boot && c->boot->planned && (u32)c->boot->n_slots != n_slots) return CKKS_E_STATE;
+  c->boot_slots = n_slots == c->n / 2 ? 0 : n_slots;
+  return CKKS_OK;
+}
+
 int ckks_boot_setup(ckks_ctx *c) {
   if (!c) return CKKS_E_PARAM;
   int rc = boot_ensure_plan(c);
@@ -1196,15 +1220,17 @@ int ckks_boot_setup(ckks_ctx *c) {
   double *dcheb = nullptr;
   const size_t dbytes = sizeof(double2) * (size_t)maxnd * n;
   if (cudaMalloc(&D0, dbytes) != cudaSuccess || cudaMalloc(&D1, dbytes) != cudaSuccess ||
-      cudaMalloc(&vec, sizeof(double2) * n) != cudaSuccess || cudaMalloc(&flag, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&vec, sizeof(double2) * (c->n / 2)) != cudaSuccess || cudaMalloc(&flag, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&dcheb, sizeof(double) * (CHEB_DEGREE + 1)) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(D0); cudaFree(D1); cudaFree(vec); cudaFree(flag); cudaFree(dcheb);
     return CKKS_E_OOM;
   }
   cudaMemsetAsync(flag, 0, sizeof(int), c->stream);
+  // B4 (and B13: 1/d, d = N / (2 n_slots), for the sub-sum's factor)
+  const double d_sub = (double)(c->n / 2) / (double)n;
   for (size_t i = 0; i < b.cts.size() && !rc; ++i)
-    rc = level_constants(c, b.cts[i], i == 0 ? 1.0 / (2.0 * K_RANGE) : 1.0, D0, D1, vec, flag);
+    rc = level_constants(c, b.cts[i], i == 0 ? 1.0 / (2.0 * K_RANGE * d_sub) : 1.0, D0, D1, vec, flag);
   for (size_t i = 0; i < b.stc.size() && !rc; ++i)
     rc = level_constants(c, b.stc[i], i == 0 ? 1.0 / (2.0 * M_PI) : 1.0, D0, D1, vec, flag);
   if (!rc) {

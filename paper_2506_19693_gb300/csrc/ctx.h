@@ -49,6 +49,7 @@ struct BootState;  // boot.cu
 
 struct ckks_ctx {
   BootState *boot = nullptr;
+  u32 boot_slots = 0;                // bootstrapping slot count (0: N/2; reading B13 below that)
   int device = 0;
   cudaStream_t stream = nullptr;
   int log_n = 0;

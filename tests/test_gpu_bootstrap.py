@@ -201,3 +201,71 @@ def test_bootstrap_error_bound_n17():
         assert ctx.device_error() == 0
     finally:
         ctx.close()
+
+
+def test_sparse_slot_bootstrap_bit_exact_and_error_bound():
+    """Reading B13 at N = 2^12 with 512 slots (4 copies): the GPU plan equals the
+    oracle's, the GPU constants match, the output limbs equal the oracle's with
+    the oracle's constants imported, and with the GPU's own constants the slots
+    come back within 2^-12, still repeated with period 512."""
+    import torch
+    import oracle
+    import oracle.bootstrap as ob
+    import paper_2506_19693_gb300 as ck
+    torch.cuda.set_device(0)
+    w = si.BOOT_SMALL
+    ctx = ck.Context.from_workload(w)
+    try:
+        ctx.boot_set_slots(512)
+        ctx.keygen_boot(1)
+        ctx.boot_setup()
+        plan = ob.make_plan(w.log_n, len(w.q_bits), log_slots=9)
+        assert ctx.boot_rotation_steps() == plan.rotation_steps()
+        orc = oracle.Oracle(w.log_n, w.q_bits, w.p_bits, w.dnum, w.h, w.sigma)
+        orc.keygen(1)
+        orc.gen_rotation_keys(plan.rotation_steps())
+        orc.gen_galois_key(orc.conj_elt())
+        consts = ob.encode_constants(orc, plan)
+        got, cheb = ctx.boot_export()
+        want = np.stack(consts)
+        assert np.max(np.abs(got - want)) <= 1e-11 * np.max(np.abs(want)) + 2
+        z = si.messages(32, 1, 512)[0]
+        delta = 2.0 ** w.log2_scale
+        cg = ctx.encrypt(ctx.encode(np.tile(z, 4), 0, delta), 0, delta, 41)
+        out = ctx.bootstrap(cg)
+        assert out.level == len(w.q_bits) - 17
+        assert np.max(np.abs(ctx.decrypt_decode(out) - np.tile(z, 4))) <= 2.0 ** -12
+        m = orc.encode(np.tile(z, 4), delta)
+        co = orc.encrypt(orc.pt_from_int(m, 0), 0, delta, 42)
+        cg = ctx.encrypt(ctx.pt_from_int(m, 0), 0, delta, 42)
+        ctx.boot_import(consts, plan.cheb)
+        out_g = ctx.bootstrap(cg)
+        out_o = ob.Evaluator(orc, plan, consts).bootstrap(co)
+        assert (out_g.level, out_g.scale) == (out_o.level, out_o.scale)
+        assert np.array_equal(ctx.export_ct(out_g), out_o.data)
+        assert ctx.device_error() == 0
+    finally:
+        ctx.close()
+
+
+def test_sparse_slot_bootstrap_full_ring():
+    """N = 2^16 with 2^13 slots (4 copies): within 2^-12, output at level n_q - 17."""
+    import torch
+    import paper_2506_19693_gb300 as ck
+    torch.cuda.set_device(0)
+    w = si.BOOT
+    ctx = ck.Context.from_workload(w)
+    try:
+        ctx.boot_set_slots(1 << 13)
+        ctx.keygen_boot(1)
+        ctx.boot_setup()
+        z = si.messages(33, 2, 1 << 13)
+        delta = 2.0 ** w.log2_scale
+        cts = [ctx.encrypt(ctx.encode(np.tile(z[i], 4), 0, delta), 0, delta, 630 + i) for i in range(2)]
+        outs = ctx.bootstrap_batch(cts)
+        for i in range(2):
+            assert outs[i].level == len(w.q_bits) - 17
+            assert np.max(np.abs(ctx.decrypt_decode(outs[i]) - np.tile(z[i], 4))) <= 2.0 ** -12
+        assert ctx.device_error() == 0
+    finally:
+        ctx.close()

@@ -197,3 +197,25 @@ def test_iterative_bootstrap_refines_precision(boot_env):
     assert (two.level, two.scale) == (one.level, one.scale * 2.0 ** k)
     assert e2 <= 2.0 ** -36, e2
     assert e2 <= e1 * 2.0 ** -8, (e1, e2)
+
+
+def test_sparse_slot_bootstrap_error_bound():
+    """Reading B13: 512 slots at N = 2^12 (d = 4 copies): the sub-sum keeps the
+    subring part, the 512-slot transforms refresh it, and the output decrypts to
+    the input within 2^-12, still repeated with period 512."""
+    w = si.BOOT_SMALL
+    plan = ob.make_plan(w.log_n, len(w.q_bits), log_slots=9)
+    assert plan.subsum_steps == [512, 1024]
+    assert set(plan.subsum_steps) <= set(plan.rotation_steps())
+    o = oracle.Oracle(w.log_n, w.q_bits, w.p_bits, w.dnum, w.h, w.sigma)
+    o.keygen(2)
+    o.gen_rotation_keys(plan.rotation_steps())
+    o.gen_galois_key(o.conj_elt())
+    ev = ob.Evaluator(o, plan, ob.encode_constants(o, plan))
+    z = si.messages(30, 1, 512)[0]
+    delta = 2.0 ** w.log2_scale
+    ct = o.encrypt(o.pt_from_int(o.encode(np.tile(z, 4), delta), 0), 0, delta, 31)
+    out = ev.bootstrap(ct)
+    assert out.level == plan.top - 16
+    got = o.decrypt_decode(out)
+    assert np.max(np.abs(got - np.tile(z, 4))) <= 2.0 ** -12
