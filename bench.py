@@ -466,6 +466,9 @@ def run_gpu(args):
     n_scaling = None
     if not (args.no_n_scaling or args.small):
         n_scaling = run_n_scaling(torch, stream, reps=max(2, min(args.steps, 3)))
+    key_compression = None
+    if not (args.no_key_compression or args.small):
+        key_compression = run_key_compression(torch, stream, max(3, min(args.steps, 5)), args.form == "tensor")
     iterative = None
     if not (args.no_iterative or args.small):
         iterative = run_iterative(bctx, wb, BIN, BOUT, zb, torch, stream, reps=max(2, min(args.steps, 3)))
@@ -510,6 +513,7 @@ def run_gpu(args):
                 "slot_error": errors, "forms": forms,
                 "reboot_step": reboot, "uneven_batch": uneven, "iterative_bootstrap": iterative,
                 "n_scaling": n_scaling,
+                "key_compression": key_compression,
                 "tuning": tuning,
                 "e2e": e2e, "roofline": roof, "alu_peaks": alu, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": int(launches),
@@ -653,6 +657,63 @@ def run_n_scaling(torch, stream, reps):
                                           {"eMLP-3": "not in Table 6"})
     finally:
         bctx.close()
+    out["clock"] = "CUDA events on the library stream, inputs resident; untimed tuning and warm-up"
+    return out
+
+
+def run_key_compression(torch, stream, reps, tensor_form):
+    """Compressed switching keys (b rows plus the generator state of a) against
+    full keys, on the HMult workload: merged HMult+relin+rescale over 64 pairs and
+    over 1 pair, and one input rotated by the 15 powers of two in one hoisted
+    call.  Results are bit-identical; what changes is key memory and key reads."""
+    import paper_2506_19693_gb300 as ck
+    w = si.PLAIN
+    level = len(w.q_bits) - 1
+    scale = 2.0 ** w.log2_scale
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    out = {}
+    for compressed in (False, True):
+        ctx = ck.Context.from_workload(w, stream=stream)
+        try:
+            ctx.set_key_compression(compressed)
+            ctx.set_form(tensor_form)
+            ctx.keygen(9, rot_steps=list(w.rot_steps))
+            z = si.messages(720, 2, w.slots)
+            base = [ctx.encrypt(ctx.encode(z[i], level, scale), level, scale, 920 + i) for i in range(2)]
+            B = w.batch
+            cts = [ctx.new_ct(level + 1) for _ in range(2 * B)]
+            for i, c in enumerate(cts):
+                c.data.copy_(base[i // B].data)
+                c.level, c.scale = base[i // B].level, base[i // B].scale
+            outs = [ctx.new_ct(level + 1) for _ in range(B)]
+            rots = [ctx.new_ct(level + 1) for _ in w.rot_steps]
+            ctx.tune(level, B)
+            ctx.tune_ntt(16)
+
+            def time_it(fn, n):
+                fn()
+                torch.cuda.synchronize()
+                e0, e1 = ev(), ev()
+                e0.record(stream)
+                for _ in range(n):
+                    fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                return e0.elapsed_time(e1) / n
+
+            ms64 = time_it(lambda: ctx.mul_relin_batch(cts[:B], cts[B:], outs, rescale=ck.RESCALE_MERGED), reps)
+            ms1 = time_it(lambda: ctx.mul_relin_batch(cts[:1], cts[B:B + 1], outs[:1],
+                                                      rescale=ck.RESCALE_MERGED), 16 * reps)
+            msr = time_it(lambda: ctx.rotate_hoisted(cts[:1], list(w.rot_steps), rots), 4 * reps)
+            n_keys = 1 + len(w.rot_steps)
+            words = ctx.n_digits * (ctx.n_q + ctx.n_p) * ctx.n * (1 if compressed else 2) + (16 if compressed else 0)
+            row = {"device_key_mb": n_keys * words * 8 / 1e6,
+                   "hmult_per_s_64_pairs": B / (ms64 / 1e3), "hmult_ms_1_pair": ms1,
+                   "hoisted_15_rotations_ms_1_input": msr,
+                   "slot_error": float(np.max(np.abs(ctx.decrypt_decode(outs[0]) - z[0] * z[1])))}
+            out["compressed" if compressed else "full"] = row
+        finally:
+            ctx.close()
     out["clock"] = "CUDA events on the library stream, inputs resident; untimed tuning and warm-up"
     return out
 
@@ -848,6 +909,7 @@ def main():
     ap.add_argument("--no-reboot", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--no-iterative", action="store_true")
+    ap.add_argument("--no-key-compression", action="store_true")
     ap.add_argument("--no-n-scaling", action="store_true")
     ap.add_argument("--no-form-compare", action="store_true")
     ap.add_argument("--form", default="tensor", choices=["uint64", "tensor"],

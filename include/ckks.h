@@ -142,6 +142,13 @@ int ckks_ctx_device_error(ckks_ctx *ctx);
  * counter-based SplitMix64 keyed by seed (reading C4).  Replaces earlier keys. */
 int ckks_keygen_from_seed(ckks_ctx *ctx, uint64_t seed, const int32_t *rot_steps, int n_rot,
                           int want_conj, int want_boot);
+/* Key compression (reading C22; no paper counterpart).  With on = 1, keys
+ * generated afterwards keep only their b rows and, per digit, the state of
+ * the counter-based generator that drew a_j; the key inner product
+ * regenerates a_j.  The keys' values are unchanged, so every result is
+ * bit-identical; device key memory and key reads halve.  CKKS_E_STATE once a
+ * key exists (call it before the first keygen). */
+int ckks_set_key_compression(ckks_ctx *ctx, int on);
 /* Add the Galois key for element g (odd, < 2N) to the current key set. */
 int ckks_keygen_galois(ckks_ctx *ctx, uint64_t galois_elt);
 /* Galois element of a left rotation by k. */

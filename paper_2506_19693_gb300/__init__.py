@@ -109,6 +109,7 @@ SIGNATURES = {
     "ckks_bootstrap": (_I, [_V, _CTP, _CTP]),
     "ckks_bootstrap_batch": (_I, [_V, _CTP, _CTP, _I]),
     "ckks_boot_set_slots": (_I, [_V, ctypes.c_uint32]),
+    "ckks_set_key_compression": (_I, [_V, _I]),
     "ckks_bootstrap_iterative_batch": (_I, [_V, _CTP, _CTP, _I, _I]),
     "ckks_exec": (_I, [_V, _I]),
     "ckks_exec_capture": (_I, [_V, _I, _V, ctypes.POINTER(_V)]),
@@ -513,6 +514,10 @@ class Context:
         _check(self.lib.ckks_rescale_batch(self._h, h, len(cts)), "ckks_rescale_batch")
         for i, c in enumerate(cts):
             c.level, c.scale = h[i].level, h[i].scale
+
+    def set_key_compression(self, on: bool) -> None:
+        """Keys generated afterwards store b and the generator state of a only."""
+        _check(self.lib.ckks_set_key_compression(self._h, int(on)), "ckks_set_key_compression")
 
     # ---- bootstrapping ----
     def keygen_boot(self, seed: int, rot_steps=(), conj: bool = True) -> None:

@@ -55,7 +55,10 @@ void free_keys(ckks_ctx *c) {
   c->galois.clear();
 }
 
-size_t key_words(const ckks_ctx *c) { return (size_t)c->n_digits * 2 * (c->n_q + c->n_p) * c->n; }
+size_t full_key_words(const ckks_ctx *c) { return (size_t)c->n_digits * 2 * (c->n_q + c->n_p) * c->n; }
+size_t key_words(const ckks_ctx *c) {
+  return c->key_compressed ? KEY_HDR + (size_t)c->n_digits * (c->n_q + c->n_p) * c->n : full_key_words(c);
+}
 
 // Build a switching key from s' (NTT domain over all n_q + n_p moduli) to s
 // (reading C7); key_id 0 = relinearisation, else the Galois element.
@@ -67,10 +70,12 @@ int make_key(ckks_ctx *c, u64 key_id, const u64 *sp_ntt, DevKey *out) {
     cudaGetLastError();
     return CKKS_E_OOM;
   }
-  int rc = ensure_scratch(c, (size_t)ext * n + n);
+  int rc = ensure_scratch(c, (size_t)(c->key_compressed ? 2 : 1) * ext * n + n);
   if (rc) { cudaFree(data); return rc; }
   u64 *e_res = c->scratch;
   i64 *e_dev = reinterpret_cast<i64 *>(c->scratch + (size_t)ext * n);
+  u64 *a_drop = c->scratch + (size_t)ext * n + n;  // compressed keys: the a row is not kept
+  u64 seeds[KEY_HDR] = {0};
   std::vector<i64> e(n);
   int mods[MAX_MODS];
   for (int i = 0; i < ext; ++i) mods[i] = i;
@@ -92,15 +97,25 @@ int make_key(ckks_ctx *c, u64 key_id, const u64 *sp_ntt, DevKey *out) {
     rc = launch_ntt(c, s1, d1, 1, ext, mods, false);
     if (rc) break;
     ka.key_a = sm_stream(c->key_seed, TAG_KEY_A, key_id * 256 + j);
+    seeds[j] = ka.key_a;
     ka.lo = j * c->alpha;
     ka.hi = std::min((j + 1) * c->alpha, c->n_q);
-    ka.b = data + (size_t)(2 * j) * ext * n;
-    ka.a = data + (size_t)(2 * j + 1) * ext * n;
+    if (c->key_compressed) {
+      ka.b = data + KEY_HDR + (size_t)j * ext * n;
+      ka.a = a_drop;
+    } else {
+      ka.b = data + (size_t)(2 * j) * ext * n;
+      ka.a = data + (size_t)(2 * j + 1) * ext * n;
+    }
     rc = ew_keyrow(c, ka, ext);
     if (rc) break;
     // the host error buffer is reused next digit: finish the copy first
     CK_CUDA(cudaStreamSynchronize(c->stream));
   }
+  if (!rc && c->key_compressed &&
+      (cudaMemcpyAsync(data, seeds, sizeof(seeds), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+       cudaStreamSynchronize(c->stream) != cudaSuccess))
+    rc = CKKS_E_CUDA;
   if (rc) { cudaFree(data); return rc; }
   out->data = data;
   return CKKS_OK;
@@ -654,6 +669,13 @@ int ckks_keygen_from_seed(ckks_ctx *c, uint64_t seed, const int32_t *rot, int n_
   return CKKS_OK;
 }
 
+int ckks_set_key_compression(ckks_ctx *c, int on) {
+  if (!c) return CKKS_E_PARAM;
+  if (c->relin.data || !c->galois.empty()) return CKKS_E_STATE;
+  c->key_compressed = on != 0;
+  return CKKS_OK;
+}
+
 int ckks_keygen_galois(ckks_ctx *c, uint64_t g) {
   if (!c) return CKKS_E_PARAM;
   int rc = galois_key(c, g);
@@ -674,9 +696,26 @@ int ckks_debug_key(const ckks_ctx *c, uint64_t g, uint64_t *out) {
   const DevKey *k = g == 0 ? (c->relin.data ? &c->relin : nullptr) : find_galois(c, g);
   if (!k) return CKKS_E_NOKEY;
   CK_CUDA(cudaStreamSynchronize(c->stream));
-  CK_CUDA(cudaMemcpy(out, k->data, key_words(c) * sizeof(u64), cudaMemcpyDeviceToHost));
-  // stored in Montgomery form (x 2^64 mod q): multiply by 2^-64 mod q
   const int ext = c->n_q + c->n_p;
+  const size_t row = (size_t)ext * c->n;
+  if (c->key_compressed) {
+    // b rows from the device; a rows regenerated from the header (C22), in Montgomery form like b
+    u64 seeds[KEY_HDR];
+    CK_CUDA(cudaMemcpy(seeds, k->data, sizeof(seeds), cudaMemcpyDeviceToHost));
+    for (int j = 0; j < c->n_digits; ++j) {
+      CK_CUDA(cudaMemcpy(out + 2 * j * row, k->data + KEY_HDR + j * row, row * sizeof(u64), cudaMemcpyDeviceToHost));
+      for (int t = 0; t < ext; ++t) {
+        const u64 q = c->mod[t];
+        const u64 r64 = (u64)(((unsigned __int128)1 << 64) % q);
+        for (u32 k2 = 0; k2 < c->n; ++k2)
+          out[(2 * j + 1) * row + (size_t)t * c->n + k2] =
+              host_mulmod(sample_uniform(seeds[j], (u64)t * c->n + k2, q), r64, q);
+      }
+    }
+  } else {
+    CK_CUDA(cudaMemcpy(out, k->data, key_words(c) * sizeof(u64), cudaMemcpyDeviceToHost));
+  }
+  // stored in Montgomery form (x 2^64 mod q): multiply by 2^-64 mod q
   for (int t = 0; t < ext; ++t) {
     const u64 q = c->mod[t];
     const u64 rinv = host_invmod((u64)(((unsigned __int128)1 << 64) % q), q);

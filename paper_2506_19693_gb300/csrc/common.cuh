@@ -67,6 +67,20 @@ __device__ __forceinline__ void mac128(u64 &hi, u64 &lo, u64 a, u64 b) {
       : "l"(a), "l"(b));
 }
 __device__ __forceinline__ u64 addmod(u64 a, u64 b, u64 q) { return csub(a + b, q); }
+// Counter-based uniform sampling (reading C4): draw(key, c) is output c + 1 of
+// SplitMix64 (Steele, Lea and Flood 2014) started at state `key`, and a
+// uniform residue is (draw(2 idx) 2^64 + draw(2 idx + 1)) mod q.
+__device__ __forceinline__ u64 mix64_dev(u64 z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ u64 draw_dev(u64 key, u64 ctr) {
+  return mix64_dev(key + (ctr + 1) * 0x9E3779B97F4A7C15ULL);
+}
+__device__ __forceinline__ u64 uniform_dev(u64 key, u64 idx, const ModInfo &m) {
+  return reduce128(draw_dev(key, 2 * idx), draw_dev(key, 2 * idx + 1), m);
+}
 __device__ __forceinline__ u64 submod(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
 #endif  // __CUDACC__
 

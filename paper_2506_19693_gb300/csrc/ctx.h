@@ -12,6 +12,10 @@
 struct DevKey {
   u64 *data = nullptr;
 };
+// A compressed switching key stores KEY_HDR header words (the uniform
+// generator's state for each digit's a row) and the b rows [n_digits][ext][N];
+// the key inner product regenerates a from the header (reading C22).
+constexpr int KEY_HDR = 16;
 
 // Per-level basis-conversion constants for ModUp of digit j at level l and for
 // ModDown / rescale.  All live in one device buffer; these are host offsets.
@@ -80,6 +84,7 @@ struct ckks_ctx {
   u64 key_seed = 0;
   DevKey relin;
   std::map<u64, DevKey> galois;
+  bool key_compressed = false;       // keys generated with a regenerated from its seed (C22)
 
   // scratch (grown on demand, owned)
   u64 *scratch = nullptr;

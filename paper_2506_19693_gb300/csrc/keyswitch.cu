@@ -96,7 +96,9 @@ struct IPArgs {
   int lo[MAXD], hi[MAXD];
   const u64 *d[MAX_CTS];
   const u64 *ext_buf[MAX_CTS];     // [ndig][ext][N]
-  const u64 *key[MAX_CTS];         // [n_digits][2][key_ext][N], Montgomery form
+  const u64 *key[MAX_CTS];         // [n_digits][2][key_ext][N], Montgomery form; compressed (C22):
+                                   // KEY_HDR seeds, then the b rows [n_digits][key_ext][N]
+  int kc;                          // keys compressed
   u32 gal[MAX_CTS];
   u64 *acc[MAX_CTS];               // [2][ext][N]
   // IP_BASE: poly 0 q-limbs t <= l also get [P]_{q_t} sigma_gal(base0)[t]
@@ -116,7 +118,7 @@ enum IPMode { IP_SET = 0, IP_BASE = 1, IP_ACC = 2 };  // acc = r; acc = r + P ba
 // Montgomery reduction per output removes the 2^64: sum_j v_j k_j 2^64 < 2^65 q
 // for reduced digits v_j < q < 2^62 and up to 8 digits (plus the base term).
 // The group size (outputs per thread) is a per-context tunable (ckks_tune).
-template <int NDIG, int MODE>
+template <int NDIG, int MODE, bool KC>
 __global__ void __launch_bounds__(TPB, NDIG <= 3 ? 4 : 2) k_inner(const IPArgs a, int group) {
   const u32 k = blockIdx.y * TPB + threadIdx.x;
   const int t = blockIdx.z;
@@ -136,8 +138,13 @@ __global__ void __launch_bounds__(TPB, NDIG <= 3 ? 4 : 2) k_inner(const IPArgs a
       cur = a.key[p];
 #pragma unroll
       for (int j = 0; j < NDIG; ++j) {
-        kb[j] = __ldg(cur + ((size_t)(2 * j) * a.key_ext + kl) * a.n + k);
-        ka[j] = __ldg(cur + ((size_t)(2 * j + 1) * a.key_ext + kl) * a.n + k);
+        if (KC) {  // a regenerated from the digit's seed, then put in Montgomery form (C22)
+          kb[j] = __ldg(cur + KEY_HDR + ((size_t)j * a.key_ext + kl) * a.n + k);
+          ka[j] = shoup(uniform_dev(__ldg(cur + j), (u64)kl * a.n + k, m), m.r64, m.r64_s, m.q);
+        } else {
+          kb[j] = __ldg(cur + ((size_t)(2 * j) * a.key_ext + kl) * a.n + k);
+          ka[j] = __ldg(cur + ((size_t)(2 * j + 1) * a.key_ext + kl) * a.n + k);
+        }
       }
     }
     const u32 src = gal_src(k, a.gal[p], a.n, a.log_n);
@@ -383,6 +390,7 @@ static int launch_inner(ckks_ctx *c, int level, int nv, const u64 *const *d, con
   a.ext = ext;
   a.ndig = ndig;
   a.key_ext = c->n_q + c->n_p;
+  a.kc = c->key_compressed ? 1 : 0;
   a.np = nv;
   a.nq_base = pbase0 ? nl : 0;
   if (pbase0)
@@ -411,17 +419,25 @@ static int launch_inner(ckks_ctx *c, int level, int nv, const u64 *const *d, con
   const int group = c->ip_group > 0 ? c->ip_group : 8;
   dim3 g((nv + group - 1) / group, (n + TPB - 1) / TPB, ext);
   switch (ndig) {
+#define ILAUNCH(D, M)                                                                                        \
+  do {                                                                                                       \
+    if (a.kc)                                                                                                \
+      PROF_LAUNCH(c, PK_INNER, (u64)nv * ext, (k_inner<D, M, true><<<g, TPB, 0, c->stream>>>(a, group)));   \
+    else                                                                                                     \
+      PROF_LAUNCH(c, PK_INNER, (u64)nv * ext, (k_inner<D, M, false><<<g, TPB, 0, c->stream>>>(a, group)));  \
+  } while (0)
 #define ICASE(D)                                                                                    \
   case D:                                                                                           \
     if (pbase0)                                                                                     \
-      PROF_LAUNCH(c, PK_INNER, (u64)nv * ext, (k_inner<D, IP_BASE><<<g, TPB, 0, c->stream>>>(a, group))); \
+      ILAUNCH(D, IP_BASE);                                                                          \
     else if (accumulate)                                                                            \
-      PROF_LAUNCH(c, PK_INNER, (u64)nv * ext, (k_inner<D, IP_ACC><<<g, TPB, 0, c->stream>>>(a, group)));  \
+      ILAUNCH(D, IP_ACC);                                                                           \
     else                                                                                            \
-      PROF_LAUNCH(c, PK_INNER, (u64)nv * ext, (k_inner<D, IP_SET><<<g, TPB, 0, c->stream>>>(a, group)));  \
+      ILAUNCH(D, IP_SET);                                                                           \
     break;
     ICASE(1) ICASE(2) ICASE(3) ICASE(4) ICASE(5) ICASE(6) ICASE(7) ICASE(8)
 #undef ICASE
+#undef ILAUNCH
     default: return CKKS_E_PARAM;
   }
   return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_CUDA;

@@ -10,19 +10,6 @@ namespace {
 
 constexpr int TPB = 256;
 
-__device__ __forceinline__ u64 mix64_dev(u64 z) {
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
-  return z ^ (z >> 31);
-}
-__device__ __forceinline__ u64 draw_dev(u64 key, u64 ctr) {
-  return mix64_dev(key + (ctr + 1) * 0x9E3779B97F4A7C15ULL);
-}
-// (hi * 2^64 + lo) mod q with hi = draw(2 idx), lo = draw(2 idx + 1)
-__device__ __forceinline__ u64 uniform_dev(u64 key, u64 idx, const ModInfo &m) {
-  return reduce128(draw_dev(key, 2 * idx), draw_dev(key, 2 * idx + 1), m);
-}
-
 __device__ __forceinline__ u32 brv_dev(u32 x, int bits) { return __brev(x) >> (32 - bits); }
 
 // signed 64-bit integer -> residue in [0, q)
