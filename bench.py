@@ -469,6 +469,9 @@ def run_gpu(args):
     key_compression = None
     if not (args.no_key_compression or args.small):
         key_compression = run_key_compression(torch, stream, max(3, min(args.steps, 5)), args.form == "tensor")
+    sparse_boot = None
+    if not (args.no_sparse_boot or args.small):
+        sparse_boot = run_sparse_boot(torch, stream, max(2, min(args.steps, 3)), args.form == "tensor")
     iterative = None
     if not (args.no_iterative or args.small):
         iterative = run_iterative(bctx, wb, BIN, BOUT, zb, torch, stream, reps=max(2, min(args.steps, 3)))
@@ -514,6 +517,7 @@ def run_gpu(args):
                 "reboot_step": reboot, "uneven_batch": uneven, "iterative_bootstrap": iterative,
                 "n_scaling": n_scaling,
                 "key_compression": key_compression,
+                "sparse_slot_bootstrap": sparse_boot,
                 "tuning": tuning,
                 "e2e": e2e, "roofline": roof, "alu_peaks": alu, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": int(launches),
@@ -659,6 +663,45 @@ def run_n_scaling(torch, stream, reps):
         bctx.close()
     out["clock"] = "CUDA events on the library stream, inputs resident; untimed tuning and warm-up"
     return out
+
+
+def run_sparse_boot(torch, stream, reps, tensor_form, log_slots=13):
+    """Sparse-slot bootstrapping at N = 2^16 (reading B13): 2^13-slot messages
+    repeated 4 times across the 2^15 slots, 16 ciphertexts per batch on the
+    bootstrapping chain (25 + 9 primes), fresh encryptions at level 0."""
+    import paper_2506_19693_gb300 as ck
+    wb = si.BOOT
+    ctx = ck.Context.from_workload(wb, stream=stream)
+    try:
+        ctx.set_form(tensor_form)
+        ctx.boot_set_slots(1 << log_slots)
+        ctx.keygen_boot(4)
+        ctx.boot_setup()
+        nb = wb.batch
+        db = 2.0 ** wb.log2_scale
+        reps_copies = wb.slots >> log_slots
+        zb = si.messages(730, nb, 1 << log_slots)
+        seeds = si.enc_seeds(730, nb)
+        bin_ = [ctx.encrypt(ctx.encode(np.tile(zb[i], reps_copies), 0, db), 0, db, seeds[i]) for i in range(nb)]
+        bout = [ctx.new_ct(len(wb.q_bits) - 16) for _ in range(nb)]
+        ctx.tune(len(wb.q_bits) - 1, nb)
+        ctx.tune_ntt(16)
+        ctx.bootstrap_batch(bin_, bout)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            ctx.bootstrap_batch(bin_, bout)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        err = float(max(np.max(np.abs(ctx.decrypt_decode(bout[i]) - np.tile(zb[i], reps_copies)))
+                        for i in range(2)))
+        return {"workload": wb.name, "slots": 1 << log_slots, "batch": nb, "bootstraps_per_s": nb / (ms / 1e3),
+                "ms_per_batch": ms, "slot_error": err, "output_level": bout[0].level,
+                "clock": "CUDA events on the library stream, inputs resident; untimed tuning and warm-up"}
+    finally:
+        ctx.close()
 
 
 def run_key_compression(torch, stream, reps, tensor_form):
@@ -910,6 +953,7 @@ def main():
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--no-iterative", action="store_true")
     ap.add_argument("--no-key-compression", action="store_true")
+    ap.add_argument("--no-sparse-boot", action="store_true")
     ap.add_argument("--no-n-scaling", action="store_true")
     ap.add_argument("--no-form-compare", action="store_true")
     ap.add_argument("--form", default="tensor", choices=["uint64", "tensor"],

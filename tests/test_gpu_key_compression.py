@@ -118,3 +118,29 @@ def test_key_compression_after_keygen_is_refused():
         assert ck.STATUS[e.value.status] == "CKKS_E_STATE"
     finally:
         ctx.close()
+
+
+def test_compressed_full_size_batch_equals_full_keys():
+    """N = 2^16, 24 + 8 primes, dnum = 3: 16 merged products and 4 inputs x 3
+    hoisted rotations with compressed keys equal the full-key context's limbs."""
+    import paper_2506_19693_gb300 as ck
+    w = si.PLAIN
+    level = len(w.q_bits) - 1
+    scale = 2.0 ** w.log2_scale
+    res = []
+    for compressed in (False, True):
+        ctx = _ctx(w, compressed, form=True)
+        try:
+            z = si.messages(74, 32, w.slots)
+            cts = [ctx.encrypt(ctx.encode(z[i], level, scale), level, scale, 740 + i) for i in range(32)]
+            out = [ctx.new_ct(level + 1) for _ in range(16)]
+            ctx.mul_relin_batch(cts[:16], cts[16:], out, rescale=ck.RESCALE_MERGED)
+            rot = [ctx.new_ct(level + 1) for _ in range(4 * len(ROT))]
+            ctx.rotate_hoisted(cts[:4], list(ROT), rot)
+            assert ctx.device_error() == 0
+            assert np.max(np.abs(ctx.decrypt_decode(out[5]) - z[5] * z[21])) < 2.0 ** -30
+            res.append([ctx.export_ct(c) for c in out + rot])
+        finally:
+            ctx.close()
+    for a, b in zip(*res):
+        assert np.array_equal(a, b)
