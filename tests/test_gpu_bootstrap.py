@@ -269,3 +269,24 @@ def test_sparse_slot_bootstrap_full_ring():
         assert ctx.device_error() == 0
     finally:
         ctx.close()
+
+
+def test_sparse_slot_count_checks():
+    import torch
+    import paper_2506_19693_gb300 as ck
+    torch.cuda.set_device(0)
+    w = si.BOOT_SMALL
+    ctx = ck.Context.from_workload(w)
+    try:
+        for bad in (0, 1, 3, 768, 4096):  # not a power of two in 2 .. N/2
+            with pytest.raises(ck.CkksError) as e:
+                ctx.boot_set_slots(bad)
+            assert ck.STATUS[e.value.status] == "CKKS_E_PARAM"
+        ctx.boot_set_slots(512)
+        assert 512 in ctx.boot_rotation_steps() and 1024 in ctx.boot_rotation_steps()
+        ctx.boot_set_slots(512)  # the planned count again: accepted
+        with pytest.raises(ck.CkksError) as e:
+            ctx.boot_set_slots(1024)
+        assert ck.STATUS[e.value.status] == "CKKS_E_STATE"
+    finally:
+        ctx.close()
