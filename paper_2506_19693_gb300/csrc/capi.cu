@@ -60,6 +60,8 @@ size_t key_words(const ckks_ctx *c) {
   return c->key_compressed ? KEY_HDR + (size_t)c->n_digits * (c->n_q + c->n_p) * c->n : full_key_words(c);
 }
 
+static_assert(KEY_HDR >= 8, "a compressed key's header holds one generator state per digit (at most 8)");
+
 // Build a switching key from s' (NTT domain over all n_q + n_p moduli) to s
 // (reading C7); key_id 0 = relinearisation, else the Galois element.
 int make_key(ckks_ctx *c, u64 key_id, const u64 *sp_ntt, DevKey *out) {
