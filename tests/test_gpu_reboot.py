@@ -10,9 +10,9 @@ import synthetic_inputs as si
 pytestmark = pytest.mark.gpu
 
 
-def _data(seed, b, k0, k1, o):
+def _data(seed, b, k0, k1, o, x_hi=1.0):
     rng = np.random.default_rng(seed)
-    x = rng.uniform(0, 1, size=(b, k0))
+    x = rng.uniform(0, x_hi, size=(b, k0))
     y = np.eye(o)[rng.integers(0, o, size=b)]
     w = rng.normal(0, 1 / np.sqrt(k0), size=(k0, k1))
     ws = rng.normal(0, 1 / np.sqrt(k1), size=(k1, o))
@@ -322,6 +322,55 @@ def test_reboot_step_with_iterative_bootstrap_is_more_precise():
             errs[k] = max(np.max(np.abs(ctx.decrypt_decode(c).real - want))
                           for c, want in zip(r[0] + [r[2]], ref[0] + [ref[2]]))
         assert errs[None] < 2.0 ** -12 and errs[16] < 2.0 ** -26 and errs[16] < errs[None] / 64, errs
+        assert ctx.device_error() == 0
+    finally:
+        ctx.close()
+
+
+def test_reboot_trajectory_follows_fp64_simulator():
+    """Five chained RE-Block steps (NAG with velocity after the first), a new
+    two-sample mini-batch each step, W, V, W*, V* bootstrapped at the end of
+    every step and fed to the next: after every step the decrypted weights stay
+    within 2^-14 of the FP64 simulator carried along the same data.  Inputs in
+    [0, 1/4] and gamma = 10^-3 keep the simulator's own trajectory bounded
+    (|V| <= 2 over the five steps; at gamma = 0.05 it diverges in FP64 too)."""
+    import torch
+    import oracle.reboot as orb
+    import paper_2506_19693_gb300 as ck
+    import paper_2506_19693_gb300.reboot as rb
+    torch.cuda.set_device(0)
+    w_ = si.BOOT_SMALL
+    g = rb.Geometry(32, 64, 60, 64, 10)
+    go = orb.Geometry(32, 64, 60, 64, 10)
+    ctx = ck.Context.from_workload(w_)
+    try:
+        ctx.keygen_boot(1, rot_steps=g.rotation_steps())
+        ctx.boot_setup()
+        _, _, w, ws = _data(9, 2, g.k0, g.k1, g.o)
+        scale, lvl = 2.0 ** w_.log2_scale, len(w_.q_bits) - 17
+        gamma, eta, mu = 0.001, 0.001, 0.9
+        seeds = iter(range(7000, 9000))
+        enc = lambda v: ctx.encrypt(ctx.encode(v, lvl, scale), lvl, scale, next(seeds))  # noqa: E731
+        state = ([enc(t) for t in rb.weight_tiles(w, g)], [enc(np.zeros(g.r * g.c)) for _ in range(g.tiles)],
+                 enc(rb.pack_colwise(ws, g)), enc(np.zeros(g.r * g.c)), None)
+        pW = orb.tile_weights(w, go)
+        ref = (pW, [np.zeros_like(t) for t in pW], orb.pack_colwise(ws, go), np.zeros(g.r * g.c), None)
+        blk = rb.REBlock(ctx, g, gamma, eta, mu)
+        errs = []
+        for step in range(5):
+            x, y, _, _ = _data(100 + step, 2, g.k0, g.k1, g.o, x_hi=0.25)
+            xs = [[enc(t) for t in rb.input_tiles(xi, g)] for xi in x]
+            ys = [enc(rb.pack_expanded(yi, g)) for yi in y]
+            state = blk.step(state, xs, ys, first=step == 0, bootstrap=True)
+            ref = orb.plain_step(ref, [orb.tile_inputs(xi, go) for xi in x],
+                                 [orb.pack_expanded(yi, go) for yi in y], go, gamma, eta, mu, first=step == 0)
+            got = state[0] + state[1] + [state[2], state[3]]
+            want = ref[0] + ref[1] + [ref[2], ref[3]]
+            errs.append(max(np.max(np.abs(ctx.decrypt_decode(c).real - v)) for c, v in zip(got, want)))
+            assert all(c.level == lvl for c in got)
+        assert max(errs) < 2.0 ** -14, errs
+        # the weights moved: the trajectory is not the starting point
+        assert np.max(np.abs(ref[0][0] - pW[0])) > 20 * max(errs)
         assert ctx.device_error() == 0
     finally:
         ctx.close()
