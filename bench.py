@@ -882,7 +882,7 @@ def run_e2e(ctx, torch, A, Bc, OUT, level, args, dist):
     region.  Two wire formats: plain uint64 limbs (ckks_mul_relin_host, the
     headline `e2e`) and limbs packed at their primes' bit widths
     (ckks_mul_relin_host_packed).  The chunk size of each is the fastest of two
-    untimed passes at each of 8, 16, 32."""
+    untimed passes at each of 4, 8, 16, 32."""
     import paper_2506_19693_gb300 as ck
     n = ctx.n
     B = len(A)
@@ -893,7 +893,7 @@ def run_e2e(ctx, torch, A, Bc, OUT, level, args, dist):
 
     def measure(once):
         best, best_t = 16, None
-        for chunk in (8, 16, 32):
+        for chunk in (4, 8, 16, 32):
             once(chunk)  # staging allocated outside the timing
             for _ in range(2):  # the faster of two passes per candidate
                 torch.cuda.synchronize()
@@ -935,8 +935,9 @@ def run_e2e(ctx, torch, A, Bc, OUT, level, args, dist):
                                                              rescale=ck.RESCALE_MERGED, chunk=ch))
     packed = {"value": world * B * steps / dt, "unit": UNIT, "chunk_pairs": chunk, "h2d_bytes_per_step": 2 * B * wi,
               "d2h_bytes_per_step": B * wo, "call": "ckks_mul_relin_host_packed (limbs at their primes' bit widths)"}
-    # the headline: uint64 limbs (the pipeline is bound by the products, so the
-    # packed format's 14% fewer bytes do not pay for its pack/unpack kernels)
+    # the headline: uint64 limbs.  That pipeline is bound by the host link (both
+    # directions at once); the packed one moves 14% fewer bytes but is bound by
+    # the products plus its pack/unpack kernels
     return dict(raw, steps=steps, call="ckks_mul_relin_host (page-locked host buffers)",
                 clock="host perf_counter around synchronised steps", packed_limbs=packed)
 
