@@ -194,35 +194,59 @@ struct WireArgs {
   u32 n_limbs[MAX_CTS];
 };
 
+// A block takes one segment of WSEG residues of a limb.  WSEG is a multiple of
+// 64, so the segment's bits [k0 b, (k0 + WSEG) b) start and end on 64-bit
+// words: WSEG b / 64 words.  The segment is staged in shared memory with
+// independent coalesced loads (WR per thread), then split or joined there.
+constexpr int WR = 4;
+constexpr int WSEG = TPB * WR;
+
 // residue k of limb t: bits [k b, k b + b) of the limb's 64-bit words
 __global__ void k_unpack(const WireArgs a) {
-  const u32 k = blockIdx.x * TPB + threadIdx.x;
+  __shared__ u64 sw[WSEG];
   const int t = blockIdx.y, i = blockIdx.z >> 1, pl = blockIdx.z & 1;
-  if (k >= a.n) return;
-  const u64 *src = reinterpret_cast<const u64 *>(a.wire[i] + (size_t)pl * a.off[a.nl] + a.off[t]);
   const u32 b = a.bits[t];
-  const u64 o = (u64)k * b;
-  const u32 w = (u32)(o >> 6), sh = (u32)(o & 63);
-  u64 v = __ldg(src + w) >> sh;
-  if (sh + b > 64) v |= __ldg(src + w + 1) << (64 - sh);
-  if (b < 64) v &= (1ULL << b) - 1;
-  a.ct[i][((size_t)pl * a.n_limbs[i] + t) * a.n + k] = v;
+  const u32 k0 = blockIdx.x * WSEG, nw = (WSEG / 64) * b;
+  const u64 *src = reinterpret_cast<const u64 *>(a.wire[i] + (size_t)pl * a.off[a.nl] + a.off[t]) + (k0 / 64) * b;
+#pragma unroll
+  for (int r = 0; r < WR; ++r) {
+    const u32 x = threadIdx.x + r * TPB;
+    if (x < nw) sw[x] = __ldg(src + x);
+  }
+  __syncthreads();
+  u64 *dst = a.ct[i] + ((size_t)pl * a.n_limbs[i] + t) * a.n + k0;
+  const u64 mask = b < 64 ? (1ULL << b) - 1 : ~0ULL;
+#pragma unroll
+  for (int r = 0; r < WR; ++r) {
+    const u32 k = threadIdx.x + r * TPB;
+    const u32 o = k * b, w = o >> 6, sh = o & 63;  // w + 1 < nw whenever the residue straddles
+    u64 v = sw[w] >> sh;
+    if (sh + b > 64) v |= sw[w + 1] << (64 - sh);
+    dst[k] = v & mask;
+  }
 }
 
 // 64-bit word j of limb t: the residues overlapping bits [64 j, 64 j + 64)
 __global__ void k_pack(const WireArgs a) {
-  const u32 j = blockIdx.x * TPB + threadIdx.x;
+  __shared__ u64 sr[WSEG];
   const int t = blockIdx.y, i = blockIdx.z >> 1, pl = blockIdx.z & 1;
   const u32 b = a.bits[t];
-  if ((u64)j * 64 >= (u64)a.n * b) return;
-  const u64 *src = a.ct[i] + ((size_t)pl * a.n_limbs[i] + t) * a.n;
-  u64 acc = 0;
-  for (u32 k = (u32)(((u64)j * 64) / b); k < a.n && (u64)k * b < (u64)(j + 1) * 64; ++k) {
-    const long long s = (long long)k * b - (long long)j * 64;
-    const u64 v = src[k];
-    acc |= s >= 0 ? v << s : v >> (-s);
+  const u32 k0 = blockIdx.x * WSEG, nw = (WSEG / 64) * b;
+  const u64 *src = a.ct[i] + ((size_t)pl * a.n_limbs[i] + t) * a.n + k0;
+#pragma unroll
+  for (int r = 0; r < WR; ++r) sr[threadIdx.x + r * TPB] = __ldg(src + threadIdx.x + r * TPB);
+  __syncthreads();
+  u64 *dst = reinterpret_cast<u64 *>(a.wire[i] + (size_t)pl * a.off[a.nl] + a.off[t]) + (k0 / 64) * b;
+  for (u32 j = threadIdx.x; j < nw; j += TPB) {
+    const u32 lo_bit = j * 64u;  // segment-local bit offsets stay below WSEG * 64
+    u64 acc = 0;
+    for (u32 k = lo_bit / b; k < (u32)WSEG && k * b < lo_bit + 64u; ++k) {
+      const int sft = (int)(k * b) - (int)lo_bit;
+      const u64 v = sr[k];
+      acc |= sft >= 0 ? v << sft : v >> (-sft);
+    }
+    dst[j] = acc;
   }
-  reinterpret_cast<u64 *>(a.wire[i] + (size_t)pl * a.off[a.nl] + a.off[t])[j] = acc;
 }
 
 dim3 grid_for(u32 n, int limbs, int cts) { return dim3((n + TPB - 1) / TPB, limbs, cts); }
@@ -248,7 +272,7 @@ WireLayout wire_layout(const ckks_ctx *c, int level) {
 int ew_wire(ckks_ctx *c, const WireLayout &L, unsigned char *const *wire, u64 *const *ct, const u32 *n_limbs,
             int ncts, bool to_wire) {
   if (ncts <= 0) return CKKS_OK;
-  if (ncts > MAX_CTS || c->n % 64) return CKKS_E_PARAM;
+  if (ncts > MAX_CTS || c->n % WSEG) return CKKS_E_PARAM;
   WireArgs a;
   a.n = c->n;
   a.nl = L.nl;
@@ -261,12 +285,11 @@ int ew_wire(ckks_ctx *c, const WireLayout &L, unsigned char *const *wire, u64 *c
     a.n_limbs[i] = n_limbs[i];
   }
   if (to_wire) {
-    const u32 words = c->n;  // at most N words per limb (64-bit primes); the kernel stops at N b / 64
     PROF_LAUNCH(c, PK_ELEMENTWISE, (u64)L.nl * 2 * ncts,
-                (k_pack<<<grid_for(words, L.nl, 2 * ncts), TPB, 0, c->stream>>>(a)));
+                (k_pack<<<dim3(c->n / WSEG, L.nl, 2 * ncts), TPB, 0, c->stream>>>(a)));
   } else {
     PROF_LAUNCH(c, PK_ELEMENTWISE, (u64)L.nl * 2 * ncts,
-                (k_unpack<<<grid_for(c->n, L.nl, 2 * ncts), TPB, 0, c->stream>>>(a)));
+                (k_unpack<<<dim3(c->n / WSEG, L.nl, 2 * ncts), TPB, 0, c->stream>>>(a)));
   }
   return last_status();
 }
