@@ -219,3 +219,26 @@ def test_sparse_slot_bootstrap_error_bound():
     assert out.level == plan.top - 16
     got = o.decrypt_decode(out)
     assert np.max(np.abs(got - np.tile(z, 4))) <= 2.0 ** -12
+
+
+def test_sparse_subsum_is_the_trace_onto_the_subring():
+    """Reading B13's sub-sum, by its algebra: the rotations by n 2^i (n 2^i < N/2)
+    generate the automorphisms g = 1 mod 4n, whose fixed ring is Z[X^d],
+    d = N/(2n).  Summing over them maps X^j to d X^j when d divides j and to 0
+    otherwise, so the decrypted coefficients are d m_j on multiples of d and
+    noise elsewhere (N = 2^12, n = 512, d = 4)."""
+    w = si.BOOT_SMALL
+    plan = ob.make_plan(w.log_n, len(w.q_bits), log_slots=9)
+    o = oracle.Oracle(w.log_n, w.q_bits, w.p_bits, w.dnum, w.h, w.sigma)
+    o.keygen(3)
+    o.gen_rotation_keys(plan.subsum_steps)
+    n, d = 1 << w.log_n, (1 << w.log_n) // (2 * 512)
+    rng = np.random.default_rng(11)
+    m = rng.integers(-(1 << 30), 1 << 30, size=n)
+    ct = o.encrypt(o.pt_from_int(m, 0), 0, 1.0, 12)
+    for k in plan.subsum_steps:
+        ct = o.add(ct, o.rotate(ct, k))
+    got = np.array([float(v) for v in o.decrypt_coeffs(ct)])
+    want = np.where(np.arange(n) % d == 0, d * m, 0).astype(np.float64)
+    assert np.max(np.abs(got - want)) < 2.0 ** 16
+    assert np.max(np.abs(got[np.arange(n) % d == 0])) > 2.0 ** 29  # the kept part is the message, not noise
