@@ -128,11 +128,22 @@ int ckks_alu_peaks(ckks_ctx *ctx, double *mac_per_s, double *bfly_per_s);
  * accumulation in tensor memory, and recombines modularly. */
 int ckks_ctx_set_form(ckks_ctx *ctx, int form);
 /* CKKS_E_TIMEOUT if a bounded device-side wait of a tensor-core kernel expired
- * since the last call (the affected outputs are invalid), else CKKS_OK.
+ * since the last call (the affected outputs are invalid; no matrix multiply was
+ * left running), CKKS_E_CUDA if, in addition, multiplies committed by the
+ * expired kernel had still not completed after a second, longer bounded wait
+ * when it released its tensor memory (destroy the context), else CKKS_OK.
  * Synchronises the context stream and clears the flag. */
 int ckks_ctx_device_error(ckks_ctx *ctx);
+/* TEST ONLY (no paper counterpart): run the tensor-core conversion kernel once
+ * on a scratch polynomial with its CTAs made to wait, before issuing any
+ * matrix multiply, on a barrier that nothing arrives on.  The wait gives up
+ * after wait_ns (clamped to 1 ms .. 1 s), so the kernel takes its failure
+ * path: it records the error and frees its tensor memory, and the next
+ * ckks_ctx_device_error returns CKKS_E_TIMEOUT.  Nothing faults and the
+ * context stays usable.  CKKS_E_STATE during graph capture. */
+int ckks_debug_tc_expire(ckks_ctx *ctx, uint64_t wait_ns);
 
-/* ---- keys (Sec. 3: "one key corresponding to each desired rotation index") */
+/* ---- keys (Sec. 3: one Galois key per rotation step) -------------------- */
 
 /* Draw the ternary secret from `seed` and build the relinearisation key
  * (s^2 -> s) plus one Galois key per rotation step in rot_steps[0..n_rot)
@@ -220,10 +231,12 @@ int ckks_rotate(ckks_ctx *ctx, const ckks_ct *a, int32_t k, ckks_ct *out);
  * synchronisation.  ckks_rescale may grow the context's scratch buffer; this
  * variant gives the same limbs (same arithmetic) using a fixed 5 MiB
  * workspace in a file-scope device array that every GPU loading the library
- * holds until exit.  Limit: N <= 2^16 (larger rings return CKKS_E_PARAM); any
- * level.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current -- make that first call
- * before any stream capture.  All calls share the array, so calls whose GPU
+ * holds until exit.  Limit: N <= 2^17 (larger rings return CKKS_E_PARAM); any
+ * level.  At N = 2^17 the array holds one lifted limb of each polynomial per
+ * pass, at N = 2^16 four.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current -- make that
+ * first call before any stream capture; a failed lookup returns CKKS_E_CUDA
+ * and is retried by the next call.  All calls share the array, so calls whose GPU
  * work overlaps (other streams or threads) race; nothing in it must start at
  * zero.  The current device must be the context's.  In place, like
  * ckks_rescale; CKKS_E_LEVEL at level 0.  Allocates no device memory as long
@@ -273,6 +286,17 @@ int ckks_boot_export(ckks_ctx *ctx, int64_t *coeffs, int count, double *cheb, in
  * ckks_boot_setup or ckks_boot_import (CKKS_E_STATE). */
 int ckks_bootstrap(ckks_ctx *ctx, const ckks_ct *in, ckks_ct *out);
 int ckks_bootstrap_batch(ckks_ctx *ctx, const ckks_ct *in, ckks_ct *out, int n);
+/* One merged level of the circuit's special DFT on its own (readings B3,
+ * B10, B11; the linear transforms of the bootstrapping Sec. 3 cites): plan
+ * level `index`, 0..2 the CoeffToSlot levels and 3..5 the SlotToCoeff levels
+ * in circuit order, applied to n ciphertexts exactly as ckks_bootstrap applies
+ * it (same constants, same launches).  Inputs at a level >= the plan level's
+ * (ckks_boot_export gives the plan's constants; CKKS_E_LEVEL below), all at
+ * one scale (CKKS_E_SCALE); outputs one level below the plan level with the
+ * input scale (the diagonals are encoded at the dropped prime).  Needs
+ * ckks_boot_setup or ckks_boot_import (CKKS_E_STATE) and the level's
+ * rotation keys. */
+int ckks_boot_linear(ckks_ctx *ctx, int index, const ckks_ct *in, ckks_ct *out, int n);
 /* Iterative bootstrapping (Sec. 5.1 sizes tau_bs for it, citing Bae et al.
  * 2022; reading B12): ct1 = Bootstrap(ct); the level-0 difference
  * align(ct1, 0, Delta_in) - ct is multiplied by 2^log2_k and bootstrapped
@@ -328,7 +352,7 @@ int ckks_rescale_batch(ckks_ctx *ctx, ckks_ct *inout, int n);
 /* Relinearised products of n ciphertext pairs that live in HOST memory (no
  * paper counterpart: the batched multiply of Eq. mult fed from the host).
  * a_host, b_host: n x uint64[2][level+1][N] (NTT domain, the layout of
- * ckks_ct_export), scales scale_a, scale_b; out_host: n x
+ * ckks_ct_export_ntt), scales scale_a, scale_b; out_host: n x
  * uint64[2][level'+1][N] with level' = level - (do_rescale != NONE);
  * *out_scale (may be NULL) receives the products' scale.  The batch is cut
  * into chunks of `chunk` (1..128) pairs: the host->device copy of chunk i+1,
@@ -416,12 +440,37 @@ int ckks_ctx_set_ntt_rows(ckks_ctx *ctx, int rows);
 int ckks_tune_dnum(const ckks_params *params, void *cuda_stream, const uint32_t *cands, int n_cands, int batch,
                    uint64_t seed, uint32_t *best, double *ms_per_op);
 
-/* ---- checkpoint helpers ------------------------------------------------- */
+/* ---- ciphertext buffers and host exchange (Sec. 3: a ciphertext is a pair
+ * of polynomials of R_q; these calls move one between HBM and the host) ---- */
 
-/* Copy a ciphertext's active limbs to/from host memory as
- * uint64[2][level+1][N] (NTT domain). */
+/* Allocate a ciphertext buffer of n_limbs (1..n_q) limbs per polynomial on the
+ * context's device (uint64[2][n_limbs][N], zero-filled on the context
+ * stream) and fill *out: level = n_limbs - 1, is_ntt = 1, scale = the default
+ * scale.  The buffer belongs to the caller, who releases it with
+ * ckks_ct_free (not cudaFree).  For callers that do not wrap their own device
+ * memory.  CKKS_E_OOM when the allocation fails, CKKS_E_STATE during graph
+ * capture. */
+int ckks_ct_alloc(ckks_ctx *ctx, uint32_t n_limbs, ckks_ct *out);
+/* Release a buffer from ckks_ct_alloc after the context stream's work is
+ * done (synchronises it); sets ct->data to NULL.  A NULL data is a no-op.
+ * Passing a buffer not from ckks_ct_alloc is undefined. */
+int ckks_ct_free(ckks_ctx *ctx, ckks_ct *ct);
+/* Copy a ciphertext's active limbs to host memory as uint64[2][level+1][N]
+ * in the COEFFICIENT domain: both polynomials c0, c1 of ct = (c0, c1) with
+ * coefficient k of limb t in [0, q_t).  The inverse NTT runs on the GPU into
+ * the context's scratch (which may grow); ct is unchanged.  Synchronises the
+ * stream. */
 int ckks_ct_export(ckks_ctx *ctx, const ckks_ct *ct, uint64_t *out_host);
+/* The inverse: in_host (uint64[2][level+1][N], coefficient domain, residues
+ * in [0, q_t), else CKKS_E_PARAM before anything is copied) fills ct's
+ * active limbs (ct->level and n_limbs as set by the caller), transformed to
+ * the NTT domain on the GPU.  Synchronises the stream. */
 int ckks_ct_import(ckks_ctx *ctx, const uint64_t *in_host, ckks_ct *ct);
+/* The same two copies without the transforms: the NTT-domain limbs as they
+ * live in HBM (canonical order).  Used by checkpointing and by the tests'
+ * limb-for-limb comparisons. */
+int ckks_ct_export_ntt(ckks_ctx *ctx, const ckks_ct *ct, uint64_t *out_host);
+int ckks_ct_import_ntt(ckks_ctx *ctx, const uint64_t *in_host, ckks_ct *ct);
 
 const char *ckks_status_str(int status);
 

@@ -300,18 +300,21 @@ def encode_constants(orc: Oracle, plan: BootPlan) -> list:
 class Evaluator:
     """The bootstrapping circuit over the oracle's primitives (B1-B8)."""
 
-    def __init__(self, orc: Oracle, plan: BootPlan, constants: list, cheb=None):
+    def __init__(self, orc: Oracle, plan: BootPlan, constants: list, cheb=None, levels=None):
+        """levels: plan-level indices whose plaintexts are prepared (default:
+        all; a single linear level can then run without the others')."""
         self.o = orc
         self.plan = plan
         self.cheb = plan.cheb if cheb is None else np.asarray(cheb, dtype=np.float64)
         self.pts = []  # NTT-domain plaintexts per level
         idx = 0
-        for lv in plan.cts + plan.stc:
+        for li, lv in enumerate(plan.cts + plan.stc):
             per = []
             for _, items in lv.plan:
                 row = []
                 for _ in items:
-                    row.append(orc.pt_ext_from_int(constants[idx], lv.level))  # over Q_l and P (B11)
+                    if levels is None or li in levels:
+                        row.append(orc.pt_ext_from_int(constants[idx], lv.level))  # over Q_l and P (B11)
                     idx += 1
                 per.append(row)
             self.pts.append(per)

@@ -940,82 +940,128 @@ int oc_rescale(const oc_ctx *c, const u64 *in, int level, u64 *out) {
   return 0;
 }
 
-/* C21: ModDown and rescale merged.  x (NTT domain, [ext][N] over q_0..q_l,
- * p_0..p_{K-1}) is divided by S = P q_l, rounding to nearest, in one fast
- * basis conversion from the basis {q_l, p_0, .., p_{K-1}} to q_0..q_{l-1}
- * whose overflow is estimated and removed.  With H = (S - 1)/2 (S is odd):
- *   x'_i = x_i + [H]_{s_i} on the sources ([H]_{s_i} = (s_i - 1)/2),
- *   y_i  = [x'_i Shat_i^-1]_{s_i},  sum_i y_i Shat_i = [X + H]_S + u S with
- *          u = floor(sum_i y_i / s_i) in [0, K],
- *   v    = floor(sum_i T_i / 2^32), T_i = floor(y_i R_i / 2^64),
- *          R_i = floor(2^96 / s_i): y_i / s_i in 32.32 fixed point, so
- *          v = u, or u - 1 when the sum lies within 2^-28 of an integer,
- *   z_t  = sum_i y_i (Shat_i mod q_t) - v S - [H]_{q_t}  (mod q_t),
- *   out_t = (x_t - z_t) * S^-1 mod q_t,
- * and over the integers out = floor((X + H) / S) + (u - v) = round(X / S) + e,
- * e = u - v in {0, 1}, almost always 0 (X the representative in [0, Q_l P)).
+/* Multi-word unsigned integers (little-endian 64-bit words), just enough for
+ * the exact division below: a word times a number, sums, comparisons,
+ * differences and the remainder by one word. */
+static void mw_mul_word(const u64 *a, int w, u64 b, u64 *out) {
+  u128 carry = 0;
+  for (int i = 0; i < w; i++) {
+    u128 t = (u128)a[i] * b + carry;
+    out[i] = (u64)t;
+    carry = t >> 64;
+  }
+}
+static void mw_add(u64 *acc, const u64 *b, int w) {
+  u128 carry = 0;
+  for (int i = 0; i < w; i++) {
+    u128 t = (u128)acc[i] + b[i] + carry;
+    acc[i] = (u64)t;
+    carry = t >> 64;
+  }
+}
+static void mw_sub(u64 *acc, const u64 *b, int w) { /* acc >= b */
+  u64 borrow = 0;
+  for (int i = 0; i < w; i++) {
+    u128 t = (u128)acc[i] - b[i] - borrow;
+    acc[i] = (u64)t;
+    borrow = (u64)(t >> 64) ? 1 : 0;
+  }
+}
+static int mw_cmp(const u64 *a, const u64 *b, int w) {
+  for (int i = w - 1; i >= 0; i--)
+    if (a[i] != b[i]) return a[i] > b[i] ? 1 : -1;
+  return 0;
+}
+static u64 mw_mod(const u64 *a, int w, u64 q) {
+  u128 r = 0;
+  for (int i = w - 1; i >= 0; i--) r = ((r << 64) | a[i]) % q;
+  return (u64)r;
+}
+
+/* C21: ModDown and rescale merged, written as its definition.  x (NTT domain,
+ * [ext][N] over q_0..q_l, p_0..p_{K-1}) represents the integer polynomial X
+ * with coefficients in [0, Q_l P); the result is round(X / S), S = P q_l,
+ * over q_0..q_{l-1}.  Per coefficient: the exact residue V = X mod S by the
+ * CRT over the sources {q_l, p_0..p_{K-1}} in multi-word integers
+ * (V = sum_i y_i Shat_i minus the multiple of S that brings it below S), its
+ * centred form r in (-S/2, S/2) (S is odd: no ties), and then
+ *   out_t = (x_t - r) S^-1 mod q_t,
+ * which is the integer (X - r) / S = round(X / S) reduced mod q_t.
  * out: [level][N], NTT domain. */
 int oc_moddown_rescale(const oc_ctx *c, const u64 *x, int level, u64 *out) {
   if (level < 1) return -1;
   u64 n = c->n;
-  int nl = level + 1, np = c->n_p, ns = np + 1;
+  int nl = level + 1, np = c->n_p, ns = np + 1, w = ns + 1;
   int src[OC_MAXMOD], dst[OC_MAXMOD];
   src[0] = level;
   for (int k = 0; k < np; k++) src[1 + k] = c->n_q + k;
   for (int t = 0; t < level; t++) dst[t] = t;
-  /* the sources: limb q_l and the K special limbs, to coefficients, plus H */
+  /* the sources to coefficients */
   u64 *xs = (u64 *)malloc(sizeof(u64) * (u64)ns * n);
   memcpy(xs, x + (u64)level * n, sizeof(u64) * n);
   memcpy(xs + n, x + (u64)nl * n, sizeof(u64) * (u64)np * n);
   oc_intt(c, xs, ns, src);
+  /* S, Shat_i = S / s_i and [Shat_i^-1]_{s_i} */
+  u64 *big = (u64 *)calloc((u64)(ns + 2) * w, sizeof(u64));
+  u64 *S = big, *half = big + w, *shat = big + 2 * w;
+  u64 *shat_inv = (u64 *)malloc(sizeof(u64) * ns);
+  S[0] = 1;
   for (int i = 0; i < ns; i++) {
-    u64 si = c->mod[src[i]];
-    for (u64 k = 0; k < n; k++) xs[(u64)i * n + k] = addmod(xs[(u64)i * n + k], (si - 1) / 2, si);
+    u64 tmp[OC_MAXMOD];
+    mw_mul_word(S, w, c->mod[src[i]], tmp);
+    memcpy(S, tmp, sizeof(u64) * w);
   }
-  u64 *z = (u64 *)malloc(sizeof(u64) * (u64)level * n);
-  oc_bconv(c, xs, ns, src, z, level, dst);
-  /* the overflow estimate v per coefficient, from y_i in 32.32 fixed point */
-  u64 *v = (u64 *)calloc(n, sizeof(u64));
+  for (int i = 0; i < w; i++) half[i] = (S[i] >> 1) | (i + 1 < w ? S[i + 1] << 63 : 0); /* (S - 1) / 2 */
   for (int i = 0; i < ns; i++) {
-    u64 si = c->mod[src[i]], shat = 1;
+    u64 *h = shat + (u64)i * w, tmp[OC_MAXMOD];
+    memset(h, 0, sizeof(u64) * w);
+    h[0] = 1;
     for (int k = 0; k < ns; k++)
-      if (k != i) shat = mulmod(shat, c->mod[src[k]] % si, si);
-    u64 sinv = invmod(shat, si);
-    u64 r = (u64)((((u128)1) << 96) / si);
-    for (u64 k = 0; k < n; k++) {
-      u64 y = mulmod(xs[(u64)i * n + k], sinv, si);
-      v[k] += (u64)(((u128)y * r) >> 64);
+      if (k != i) {
+        mw_mul_word(h, w, c->mod[src[k]], tmp);
+        memcpy(h, tmp, sizeof(u64) * w);
+      }
+    shat_inv[i] = invmod(mw_mod(h, w, c->mod[src[i]]), c->mod[src[i]]);
+  }
+  /* r mod q_t per coefficient (coefficient domain) */
+  u64 *z = (u64 *)malloc(sizeof(u64) * (u64)level * n);
+  u64 smod_t[OC_MAXMOD];
+  for (int t = 0; t < level; t++) smod_t[t] = mw_mod(S, w, c->mod[t]);
+#pragma omp parallel for schedule(static)
+  for (u64 k = 0; k < n; k++) {
+    u64 v[OC_MAXMOD], tmp[OC_MAXMOD];
+    memset(v, 0, sizeof(u64) * w);
+    for (int i = 0; i < ns; i++) {
+      u64 si = c->mod[src[i]];
+      u64 y = mulmod(xs[(u64)i * n + k], shat_inv[i], si);
+      mw_mul_word(shat + (u64)i * w, w, y, tmp);
+      mw_add(v, tmp, w);
+    }
+    while (mw_cmp(v, S, w) >= 0) mw_sub(v, S, w); /* V = X mod S */
+    int neg = mw_cmp(v, half, w) > 0;               /* r = V - S when V > (S - 1)/2 */
+    for (int t = 0; t < level; t++) {
+      u64 q = c->mod[t], vm = mw_mod(v, w, q);
+      z[(u64)t * n + k] = neg ? submod(vm, smod_t[t], q) : vm;
     }
   }
-  for (u64 k = 0; k < n; k++) v[k] >>= 32;
-  for (int t = 0; t < level; t++) {
-    u64 q = c->mod[t], sm = c->mod[level] % q;
-    for (int k = 0; k < np; k++) sm = mulmod(sm, c->mod[c->n_q + k] % q, q);
-    u64 h = mulmod(submod(sm, 1, q), (q + 1) / 2, q); /* (S - 1)/2 mod q_t */
-    for (u64 k = 0; k < n; k++) {
-      u64 zt = submod(z[(u64)t * n + k], mulmod(v[k] % q, sm, q), q);
-      z[(u64)t * n + k] = submod(zt, h, q);
-    }
-  }
-  free(v);
   oc_ntt(c, z, level, dst);
   for (int t = 0; t < level; t++) {
-    u64 q = c->mod[t], pq = c->mod[level] % q;
-    for (int k = 0; k < np; k++) pq = mulmod(pq, c->mod[c->n_q + k] % q, q);
-    u64 pqinv = invmod(pq, q);
+    u64 q = c->mod[t], sinv = invmod(smod_t[t], q);
     for (u64 k = 0; k < n; k++) {
       u64 i = (u64)t * n + k;
-      out[i] = mulmod(submod(x[i], z[i], q), pqinv, q);
+      out[i] = mulmod(submod(x[i], z[i], q), sinv, q);
     }
   }
   free(xs);
   free(z);
+  free(big);
+  free(shat_inv);
   return 0;
 }
 
 /* C6 + C21: relinearised product divided by P q_l in the merged step.  The
  * tensor's (d0, d1) join the key-switch accumulator as P d (which vanishes
- * modulo the special primes), so out = round((acc + P d) / (P q_l)) + e.
+ * modulo the special primes), so out = round((acc + P d) / (P q_l)).
  * out: [2][level][N], level - 1, NTT domain. */
 int oc_mul_relin_rescale(const oc_ctx *c, const u64 *a, const u64 *b, int level, u64 *out) {
   okey *k = find_key(c, 0);

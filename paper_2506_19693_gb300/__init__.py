@@ -69,6 +69,7 @@ SIGNATURES = {
     "ckks_alu_peaks": (_I, [_V, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "ckks_ctx_set_form": (_I, [_V, _I]),
     "ckks_ctx_device_error": (_I, [_V]),
+    "ckks_debug_tc_expire": (_I, [_V, _U64]),
     "ckks_keygen_from_seed": (_I, [_V, _U64, _V, _I, _I, _I]),
     "ckks_keygen_galois": (_I, [_V, _U64]),
     "ckks_galois_elt": (_U64, [_V, ctypes.c_int32]),
@@ -108,6 +109,7 @@ SIGNATURES = {
     "ckks_boot_export": (_I, [_V, _V, _I, _V, _I]),
     "ckks_bootstrap": (_I, [_V, _CTP, _CTP]),
     "ckks_bootstrap_batch": (_I, [_V, _CTP, _CTP, _I]),
+    "ckks_boot_linear": (_I, [_V, _I, _CTP, _CTP, _I]),
     "ckks_boot_set_slots": (_I, [_V, ctypes.c_uint32]),
     "ckks_set_key_compression": (_I, [_V, _I]),
     "ckks_bootstrap_iterative_batch": (_I, [_V, _CTP, _CTP, _I, _I]),
@@ -120,8 +122,12 @@ SIGNATURES = {
     "ckks_ctx_set_ntt_rows": (_I, [_V, _I]),
     "ckks_tune_dnum": (_I, [_V, _V, ctypes.POINTER(ctypes.c_uint32), _I, _I, ctypes.c_uint64,
                             ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_double)]),
+    "ckks_ct_alloc": (_I, [_V, ctypes.c_uint32, _CTP]),
+    "ckks_ct_free": (_I, [_V, _CTP]),
     "ckks_ct_export": (_I, [_V, _CTP, _V]),
     "ckks_ct_import": (_I, [_V, _V, _CTP]),
+    "ckks_ct_export_ntt": (_I, [_V, _CTP, _V]),
+    "ckks_ct_import_ntt": (_I, [_V, _V, _CTP]),
     "ckks_wire_bytes": (_I, [_V, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)]),
     "ckks_ct_export_packed": (_I, [_V, _CTP, _V]),
     "ckks_ct_import_packed": (_I, [_V, _V, _CTP]),
@@ -266,6 +272,10 @@ class Context:
 
     def device_error(self) -> int:
         return self.lib.ckks_ctx_device_error(self._h)
+
+    def debug_tc_expire(self, wait_ns: int = 1_000_000) -> None:
+        """TEST ONLY: make the tensor-core kernel's bounded wait run out once."""
+        _check(self.lib.ckks_debug_tc_expire(self._h, wait_ns), "ckks_debug_tc_expire")
 
     def set_ntt_rows(self, rows: int) -> None:
         _check(self.lib.ckks_ctx_set_ntt_rows(self._h, rows), "ckks_ctx_set_ntt_rows")
@@ -568,6 +578,16 @@ class Context:
             c.level, c.scale = ho[i].level, ho[i].scale
         return out
 
+    def boot_linear(self, index: int, cts, out=None) -> list:
+        """Plan level `index` of the bootstrap's special DFT alone (ckks_boot_linear)."""
+        if out is None:
+            out = [self.new_ct(c.level) for c in cts]
+        hi, ho = self._handles(cts), self._handles(out)
+        _check(self.lib.ckks_boot_linear(self._h, index, hi, ho, len(cts)), "ckks_boot_linear")
+        for i, c in enumerate(out):
+            c.level, c.scale = ho[i].level, ho[i].scale
+        return out
+
     def bootstrap(self, ct) -> "Ciphertext":
         return self.bootstrap_batch([ct])[0]
 
@@ -583,22 +603,46 @@ class Context:
 
     # ---- host exchange ----
     def export_ct(self, ct: Ciphertext) -> np.ndarray:
+        """The active limbs as they live in HBM: uint64 [2, level+1, N], NTT domain."""
         out = np.zeros((2, ct.level + 1, self.n), dtype=np.uint64)
         h = ct.handle(self.log_n)
+        _check(self.lib.ckks_ct_export_ntt(self._h, ctypes.byref(h), out.ctypes.data), "ckks_ct_export_ntt")
+        return out
+
+    def export_coeff(self, ct) -> np.ndarray:
+        """The active limbs in the coefficient domain (ckks_ct_export); ct is a
+        Ciphertext or a raw CkksCt handle."""
+        h = ct if isinstance(ct, CkksCt) else ct.handle(self.log_n)
+        out = np.zeros((2, h.level + 1, self.n), dtype=np.uint64)
         _check(self.lib.ckks_ct_export(self._h, ctypes.byref(h), out.ctypes.data), "ckks_ct_export")
         return out
 
+    def import_coeff(self, arr: np.ndarray, ct) -> None:
+        """Fill ct's active limbs from coefficient-domain limbs (ckks_ct_import)."""
+        arr = np.ascontiguousarray(arr, dtype=np.uint64)
+        h = ct if isinstance(ct, CkksCt) else ct.handle(self.log_n)
+        _check(self.lib.ckks_ct_import(self._h, arr.ctypes.data, ctypes.byref(h)), "ckks_ct_import")
+
+    def ct_alloc(self, n_limbs: int) -> CkksCt:
+        """A library-owned ciphertext buffer (ckks_ct_alloc): a raw handle."""
+        h = CkksCt()
+        _check(self.lib.ckks_ct_alloc(self._h, n_limbs, ctypes.byref(h)), "ckks_ct_alloc")
+        return h
+
+    def ct_free(self, h: CkksCt) -> None:
+        _check(self.lib.ckks_ct_free(self._h, ctypes.byref(h)), "ckks_ct_free")
+
     def export_host(self, ct: Ciphertext, host) -> None:
-        """Copy the active limbs into a (pinned) host torch tensor [2, level+1, N]."""
+        """Copy the active NTT-domain limbs into a (pinned) host torch tensor [2, level+1, N]."""
         assert host.device.type == "cpu" and host.is_contiguous() and host.numel() >= 2 * (ct.level + 1) * self.n
         h = ct.handle(self.log_n)
-        _check(self.lib.ckks_ct_export(self._h, ctypes.byref(h), host.data_ptr()), "ckks_ct_export")
+        _check(self.lib.ckks_ct_export_ntt(self._h, ctypes.byref(h), host.data_ptr()), "ckks_ct_export_ntt")
 
     def import_host(self, ct: Ciphertext, host) -> None:
-        """Fill ct's active limbs from a (pinned) host torch tensor [2, level+1, N]."""
+        """Fill ct's active NTT-domain limbs from a (pinned) host torch tensor [2, level+1, N]."""
         assert host.device.type == "cpu" and host.is_contiguous() and host.numel() >= 2 * (ct.level + 1) * self.n
         h = ct.handle(self.log_n)
-        _check(self.lib.ckks_ct_import(self._h, host.data_ptr(), ctypes.byref(h)), "ckks_ct_import")
+        _check(self.lib.ckks_ct_import_ntt(self._h, host.data_ptr(), ctypes.byref(h)), "ckks_ct_import_ntt")
 
     # ---- packed wire format ----
     def wire_bytes(self, level: int) -> int:
@@ -636,10 +680,11 @@ class Context:
         return sc.value
 
     def import_ct(self, arr: np.ndarray, level: int, scale: float, n_limbs: int | None = None) -> Ciphertext:
+        """A new ciphertext from NTT-domain limbs uint64 [2, level+1, N]."""
         arr = np.ascontiguousarray(arr, dtype=np.uint64)
         ct = self.new_ct(n_limbs or level + 1, level, scale)
         h = ct.handle(self.log_n)
-        _check(self.lib.ckks_ct_import(self._h, arr.ctypes.data, ctypes.byref(h)), "ckks_ct_import")
+        _check(self.lib.ckks_ct_import_ntt(self._h, arr.ctypes.data, ctypes.byref(h)), "ckks_ct_import_ntt")
         return ct
 
 

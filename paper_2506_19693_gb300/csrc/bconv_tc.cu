@@ -28,6 +28,9 @@
 // targets of column group w / 4.  B (the constants) is loaded into shared
 // memory once per CTA.  Every wait is bounded: on expiry the kernel records an
 // error flag, waits (bounded) for its MMAs in flight, frees its TMEM and returns.
+// Flag values: 1 = a wait expired and no MMA was outstanding when the TMEM was
+// freed; 2 = MMAs committed to the freed TMEM had still not completed after a
+// second, longer bounded wait (the tensor memory was released under them).
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -44,6 +47,7 @@ constexpr int TC_ACC_COLS = 256;              // columns per accumulator
 constexpr int TC_TMEM_COLS = 2 * TC_ACC_COLS; // the whole TMEM of the SM
 constexpr int TC_MAX_S = 16, TC_MAX_T = 32;
 constexpr u64 TC_WAIT_NS = 1000000000ULL;     // bounded waits give up after about 1 s
+constexpr u64 TC_DRAIN_NS = 4 * TC_WAIT_NS;   // the failure path's wait for MMAs in flight
 
 __device__ __forceinline__ u32 smem_u32(const void *p) { return (u32)__cvta_generic_to_shared(p); }
 
@@ -53,8 +57,8 @@ __device__ __forceinline__ u64 global_ns() {
   return t;
 }
 
-// Spin on an mbarrier phase for at most TC_WAIT_NS; 1 when the phase completed.
-__device__ __forceinline__ u32 wait_parity(u32 mbar_addr, u32 phase) {
+// Spin on an mbarrier phase for at most limit_ns; 1 when the phase completed.
+__device__ __forceinline__ u32 wait_parity(u32 mbar_addr, u32 phase, u64 limit_ns) {
   const u64 t0 = global_ns();
   u32 done = 0;
   while (!done) {
@@ -63,7 +67,7 @@ __device__ __forceinline__ u32 wait_parity(u32 mbar_addr, u32 phase) {
         "selp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(done)
         : "r"(mbar_addr), "r"(phase));
-    if (!done && global_ns() - t0 > TC_WAIT_NS) break;
+    if (!done && global_ns() - t0 > limit_ns) break;
   }
   return done;
 }
@@ -181,7 +185,12 @@ struct TcArgs {
   const u64 *src[MAX_CTS];
   u64 *dst[MAX_CTS];
   int np;
-  int *err;                                   // set to 1 when a bounded wait expires
+  int *err;                                   // set to 1 (or 2) when a bounded wait expires
+  u64 wait_ns;                                // the bound of every wait for an MMA group
+  // test only: before any MMA is issued, every CTA waits (bounded by wait_ns)
+  // on barrier 0, which nothing arrives on, so the wait expires with no MMA
+  // outstanding and the failure path runs
+  int test_expire;
 };
 
 // Sources of one 128-coefficient block for this thread: row tid mod 128,
@@ -304,12 +313,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_bconv_tc(const TcArgs a) {
     pending |= 1u << b;
   };
 
-  if (tile < total) issue(0);
+  bool failed = false;
+  if (a.test_expire) {  // nothing arrives on barrier 0: the wait runs out
+    wait_parity(smem_u32(mbar), 0u, a.wait_ns);
+    failed = true;
+  }
+  if (!failed && tile < total) issue(0);
   const int lq = warp & 3, cg = warp >> 2;
   const int per_group = (a.nt + TC_COL_GROUPS - 1) / TC_COL_GROUPS;
   const int t_lo = cg * per_group, t_hi = min(a.nt, t_lo + per_group);
-  bool failed = false;
-  for (int j = 0; tile < total; ++j, tile += grid) {
+  for (int j = 0; !failed && tile < total; ++j, tile += grid) {
     const int cur = j & 1, nxt = cur ^ 1;
     const int next = tile + grid;
     // A tile of the next block from the prefetched sources (its buffer's MMAs
@@ -326,7 +339,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_bconv_tc(const TcArgs a) {
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (next < total) issue(nxt);
     // bounded wait for the MMAs of this block; the outcome is agreed by the whole CTA
-    const u32 done = wait_parity(smem_u32(mbar + cur), (phase >> cur) & 1u);
+    const u32 done = wait_parity(smem_u32(mbar + cur), (phase >> cur) & 1u, a.wait_ns);
     if (__syncthreads_or(done == 0)) {
       failed = true;
       break;
@@ -367,10 +380,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_bconv_tc(const TcArgs a) {
     asm volatile("tcgen05.fence::before_thread_sync;");
   }
   if (failed) {
-    // record the error, give the MMAs in flight one more bounded wait, then free TMEM
-    if (tid == 0) atomicExch(a.err, 1);
+    // give the MMAs in flight one more (longer) bounded wait, then record the
+    // error: 1 when none is outstanding any more, 2 when some still are (the
+    // TMEM is freed all the same: a CTA that exits holding it would stall the
+    // next allocation on its SM without bound)
+    u32 drained = 1;
     for (int b = 0; b < 2; ++b)
-      if ((pending >> b) & 1u) wait_parity(smem_u32(mbar + b), (phase >> b) & 1u);
+      if ((pending >> b) & 1u) drained &= wait_parity(smem_u32(mbar + b), (phase >> b) & 1u, TC_DRAIN_NS);
+    const int stuck = __syncthreads_or(drained == 0);
+    if (tid == 0) atomicMax(a.err, stuck ? 2 : 1);
     asm volatile("tcgen05.fence::before_thread_sync;");
   }
   __syncthreads();
@@ -382,10 +400,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_bconv_tc(const TcArgs a) {
 // Host: the byte-plane constant matrix of one conversion, cached on the device
 // (built on first use, outside any graph capture), then the launch.
 // key identifies the conversion (table offset); tab_host rows are [nt][ns].
-int launch_bconv_tc(ckks_ctx *c, size_t key, const u64 *inv_host, const u64 *tab_host, int ns, int nt,
-                    const int *src_mod, const int *dst_mod, const int *dst_pos, const u64 *const *src,
-                    u64 *const *dst, int np, const u64 *src_add_host, const u64 *dst_sub_host,
-                    const u64 *rdiv_host, const u64 *negs_host) {
+static int launch_bconv_tc_ex(ckks_ctx *c, size_t key, const u64 *inv_host, const u64 *tab_host, int ns, int nt,
+                              const int *src_mod, const int *dst_mod, const int *dst_pos, const u64 *const *src,
+                              u64 *const *dst, int np, const u64 *src_add_host, const u64 *dst_sub_host,
+                              const u64 *rdiv_host, const u64 *negs_host, u64 wait_ns, int test_expire) {
   if (ns < 1 || ns > TC_MAX_S || nt < 1 || nt > TC_MAX_T || np < 1 || np > MAX_CTS) return CKKS_E_PARAM;
   if (c->n % TC_M) return CKKS_E_PARAM;
   const bool has_v = rdiv_host && negs_host;
@@ -456,6 +474,8 @@ int launch_bconv_tc(ckks_ctx *c, size_t key, const u64 *inv_host, const u64 *tab
   }
   a.np = np;
   a.err = c->tc_err;
+  a.wait_ns = wait_ns;
+  a.test_expire = test_expire;
   // more than half of the SM's shared memory per CTA: one CTA per SM, so its
   // 512-column TMEM allocation never waits for another CTA's
   const size_t need = 2 * (size_t)TC_M * kpad * 2 + (size_t)npad * kpad * 2 + 32 + 4 * TC_M * 8;
@@ -467,4 +487,32 @@ int launch_bconv_tc(ckks_ctx *c, size_t key, const u64 *inv_host, const u64 *tab
   const int grid = std::min(total, sms);
   PROF_LAUNCH(c, PK_BCONV_TC, (u64)np * nt * ns, (k_bconv_tc<<<grid, TC_THREADS, smem, c->stream>>>(a)));
   return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_CUDA;
+}
+
+int launch_bconv_tc(ckks_ctx *c, size_t key, const u64 *inv_host, const u64 *tab_host, int ns, int nt,
+                    const int *src_mod, const int *dst_mod, const int *dst_pos, const u64 *const *src,
+                    u64 *const *dst, int np, const u64 *src_add_host, const u64 *dst_sub_host,
+                    const u64 *rdiv_host, const u64 *negs_host) {
+  return launch_bconv_tc_ex(c, key, inv_host, tab_host, ns, nt, src_mod, dst_mod, dst_pos, src, dst, np,
+                            src_add_host, dst_sub_host, rdiv_host, negs_host, TC_WAIT_NS, 0);
+}
+
+// TEST ONLY (ckks_debug_tc_expire): one launch of the conversion kernel on a
+// one-source, one-target conversion of a scratch polynomial, whose CTAs wait
+// on a barrier that nothing arrives on before issuing any MMA.  The wait runs
+// out after wait_ns (clamped to 1 ms .. 1 s), the failure path records flag 1
+// and frees the TMEM; the scratch target holds garbage afterwards.
+extern "C" int ckks_debug_tc_expire(ckks_ctx *c, uint64_t wait_ns) {
+  if (!c) return CKKS_E_PARAM;
+  if (c->capturing) return CKKS_E_STATE;
+  wait_ns = std::min<u64>(std::max<u64>(wait_ns, 1000000ULL), TC_WAIT_NS);
+  int rc = ensure_scratch(c, 2 * (size_t)c->n);
+  if (rc) return rc;
+  const u64 inv[2] = {1, host_shoup(1, c->mod[0])}, tab[1] = {1};
+  const int sm[1] = {0}, dm[1] = {1 % (c->n_q + c->n_p)}, dp[1] = {0};
+  CK_CUDA(cudaMemsetAsync(c->scratch, 0, 2 * (size_t)c->n * sizeof(u64), c->stream));
+  const u64 *src[1] = {c->scratch};
+  u64 *dst[1] = {c->scratch + c->n};
+  return launch_bconv_tc_ex(c, ~(size_t)0, inv, tab, 1, 1, sm, dm, dp, src, dst, 1, nullptr, nullptr, nullptr,
+                            nullptr, wait_ns, 1);
 }

@@ -1402,4 +1402,45 @@ int ckks_bootstrap_iterative_batch(ckks_ctx *c, const ckks_ct *in, ckks_ct *out,
 
 int ckks_bootstrap(ckks_ctx *c, const ckks_ct *in, ckks_ct *out) { return ckks_bootstrap_batch(c, in, out, 1); }
 
+// One merged level of the circuit's special DFT (B3, B10, B11) on n
+// ciphertexts: plan level `index` (CoeffToSlot levels first, then SlotToCoeff),
+// the same launches ckks_bootstrap runs for it.
+int ckks_boot_linear(ckks_ctx *c, int index, const ckks_ct *in, ckks_ct *out, int n) {
+  if (!c || !in || !out || n < 0) return CKKS_E_PARAM;
+  if (!c->boot || !c->boot->have_consts) return CKKS_E_STATE;
+  BootState &b = *c->boot;
+  const int nlev = (int)(b.cts.size() + b.stc.size());
+  if (index < 0 || index >= nlev) return CKKS_E_PARAM;
+  if (n == 0) return CKKS_OK;
+  const LinLevel &lv = index < (int)b.cts.size() ? b.cts[index] : b.stc[index - b.cts.size()];
+  for (int i = 0; i < n; ++i) {
+    if (!in[i].data || !out[i].data || in[i].log_n != (u32)c->log_n || out[i].log_n != (u32)c->log_n)
+      return CKKS_E_PARAM;
+    if ((int)in[i].level < lv.level || in[i].n_limbs < in[i].level + 1 || (int)out[i].n_limbs < lv.level)
+      return CKKS_E_LEVEL;
+    if (in[i].scale != in[0].scale) return CKKS_E_SCALE;
+  }
+  if (c->relin.data == nullptr || !c->have_secret) return CKKS_E_NOKEY;
+  b.slot_words = (size_t)2 * (b.top + 1) * c->n;
+  for (int i0 = 0; i0 < n; i0 += MAX_CTS) {
+    const int cnt = std::min(MAX_CTS, n - i0);
+    Eval ev(c, cnt);
+    BV x;
+    x.level = (int)in[i0].level;
+    x.scale = in[i0].scale;
+    for (int i = 0; i < cnt; ++i) x.v.push_back(in[i0 + i]);
+    for (int i = 0; i < cnt; ++i) x.v[i].level = in[i0].level;
+    BV y = ev.linear(x, lv);
+    if (ev.err) {
+      ev.release(y);
+      return ev.err;
+    }
+    std::vector<double> sc(cnt, y.scale);
+    int rc = boot_copy_out(ev, y, out + i0, sc.data());
+    ev.release(y);
+    if (rc) return rc;
+  }
+  return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_CUDA;
+}
+
 }  // extern "C"

@@ -584,7 +584,7 @@ int ckks_ctx_device_error(ckks_ctx *c) {
   CK_CUDA(cudaMemcpy(&h, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (h) {
     CK_CUDA(cudaMemset(c->tc_err, 0, sizeof(int)));
-    return CKKS_E_TIMEOUT;
+    return h == 1 ? CKKS_E_TIMEOUT : CKKS_E_CUDA;
   }
   return CKKS_OK;
 }
@@ -1268,7 +1268,7 @@ int ckks_ct_import_packed(ckks_ctx *c, const uint8_t *in, ckks_ct *ct) {
   return CKKS_OK;
 }
 
-int ckks_ct_export(ckks_ctx *c, const ckks_ct *ct, uint64_t *out) {
+int ckks_ct_export_ntt(ckks_ctx *c, const ckks_ct *ct, uint64_t *out) {
   if (!c || !ct_ok(c, ct) || !out) return CKKS_E_PARAM;
   const size_t w = (size_t)(ct->level + 1) * c->n;
   CK_CUDA(cudaMemcpyAsync(out, ct->data, w * 8, cudaMemcpyDeviceToHost, c->stream));
@@ -1277,12 +1277,83 @@ int ckks_ct_export(ckks_ctx *c, const ckks_ct *ct, uint64_t *out) {
   return CKKS_OK;
 }
 
-int ckks_ct_import(ckks_ctx *c, const uint64_t *in, ckks_ct *ct) {
+int ckks_ct_import_ntt(ckks_ctx *c, const uint64_t *in, ckks_ct *ct) {
   if (!c || !ct_ok(c, ct) || !in) return CKKS_E_PARAM;
   const size_t w = (size_t)(ct->level + 1) * c->n;
   CK_CUDA(cudaMemcpyAsync(ct->data, in, w * 8, cudaMemcpyHostToDevice, c->stream));
   CK_CUDA(cudaMemcpyAsync(poly1(ct, c->n), in + w, w * 8, cudaMemcpyHostToDevice, c->stream));
   CK_CUDA(cudaStreamSynchronize(c->stream));
+  return CKKS_OK;
+}
+
+// Coefficient domain: the active limbs of both polynomials go through the
+// inverse NTT into the context scratch, then to the host.
+int ckks_ct_export(ckks_ctx *c, const ckks_ct *ct, uint64_t *out) {
+  if (!c || !ct_ok(c, ct) || !out) return CKKS_E_PARAM;
+  if (c->capturing) return CKKS_E_STATE;
+  const int nl = (int)ct->level + 1;
+  const size_t w = (size_t)nl * c->n;
+  int rc = ensure_scratch(c, 2 * w);
+  if (rc) return rc;
+  int mods[MAX_MODS];
+  for (int t = 0; t < nl; ++t) mods[t] = t;
+  const u64 *src[2] = {ct->data, poly1(ct, c->n)};
+  u64 *dst[2] = {c->scratch, c->scratch + w};
+  rc = launch_ntt(c, src, dst, 2, nl, mods, true);
+  if (rc) return rc;
+  CK_CUDA(cudaMemcpyAsync(out, c->scratch, 2 * w * 8, cudaMemcpyDeviceToHost, c->stream));
+  CK_CUDA(cudaStreamSynchronize(c->stream));
+  return CKKS_OK;
+}
+
+// Coefficient-domain limbs in [0, q_t) (checked on the host: CKKS_E_PARAM),
+// copied in, then transformed to the NTT domain in place.
+int ckks_ct_import(ckks_ctx *c, const uint64_t *in, ckks_ct *ct) {
+  if (!c || !ct_ok(c, ct) || !in) return CKKS_E_PARAM;
+  const int nl = (int)ct->level + 1;
+  const size_t w = (size_t)nl * c->n;
+  for (int p = 0; p < 2; ++p)
+    for (int t = 0; t < nl; ++t) {
+      const u64 q = c->mod[t], *row = in + (size_t)p * w + (size_t)t * c->n;
+      for (u32 k = 0; k < c->n; ++k)
+        if (row[k] >= q) return CKKS_E_PARAM;
+    }
+  CK_CUDA(cudaMemcpyAsync(ct->data, in, w * 8, cudaMemcpyHostToDevice, c->stream));
+  CK_CUDA(cudaMemcpyAsync(poly1(ct, c->n), in + w, w * 8, cudaMemcpyHostToDevice, c->stream));
+  int mods[MAX_MODS];
+  for (int t = 0; t < nl; ++t) mods[t] = t;
+  const u64 *src[2] = {ct->data, poly1(ct, c->n)};
+  u64 *dst[2] = {ct->data, poly1(ct, c->n)};
+  int rc = launch_ntt(c, src, dst, 2, nl, mods, false);
+  if (rc) return rc;
+  CK_CUDA(cudaStreamSynchronize(c->stream));
+  return CKKS_OK;
+}
+
+int ckks_ct_alloc(ckks_ctx *c, uint32_t n_limbs, ckks_ct *out) {
+  if (!c || !out || n_limbs < 1 || n_limbs > (uint32_t)c->n_q) return CKKS_E_PARAM;
+  if (c->capturing) return CKKS_E_STATE;
+  void *p = nullptr;
+  const size_t bytes = (size_t)2 * n_limbs * c->n * sizeof(u64);
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return CKKS_E_OOM;
+  }
+  if (cudaMemsetAsync(p, 0, bytes, c->stream) != cudaSuccess) {
+    cudaFree(p);
+    return CKKS_E_CUDA;
+  }
+  *out = ckks_ct{static_cast<uint64_t *>(p), (uint32_t)c->log_n, n_limbs - 1, n_limbs, 1, c->default_scale};
+  return CKKS_OK;
+}
+
+int ckks_ct_free(ckks_ctx *c, ckks_ct *ct) {
+  if (!c || !ct) return CKKS_E_PARAM;
+  if (c->capturing) return CKKS_E_STATE;
+  if (!ct->data) return CKKS_OK;
+  CK_CUDA(cudaStreamSynchronize(c->stream));
+  CK_CUDA(cudaFree(ct->data));
+  ct->data = nullptr;
   return CKKS_OK;
 }
 

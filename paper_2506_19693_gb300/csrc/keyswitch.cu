@@ -115,8 +115,11 @@ enum IPMode { IP_SET = 0, IP_BASE = 1, IP_ACC = 2 };  // acc = r; acc = r + P ba
 // relinearisation batch) run back to back and share it through L2.  Within a
 // group the thread walks the outputs, reloading key words only when the key
 // changes.  The products sum in 128 bits against Montgomery-form keys, and one
-// Montgomery reduction per output removes the 2^64: sum_j v_j k_j 2^64 < 2^65 q
-// for reduced digits v_j < q < 2^62 and up to 8 digits (plus the base term).
+// Montgomery reduction per output removes the 2^64.  That reduction needs its
+// input below 2^65 q; with T terms (the digits, plus the base term in IP_BASE)
+// of reduced factors below q the sum is below T q^2, so T q < 2^65 suffices.
+// launch_inner checks T q < 2^65 on the host for every limb's modulus and
+// refuses the launch otherwise (T <= 7 for 62-bit primes, T <= 9 below 2^61.8).
 // The group size (outputs per thread) is a per-context tunable (ckks_tune).
 template <int NDIG, int MODE, bool KC>
 __global__ void __launch_bounds__(TPB, NDIG <= 3 ? 4 : 2) k_inner(const IPArgs a, int group) {

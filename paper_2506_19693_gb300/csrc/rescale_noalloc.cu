@@ -11,7 +11,8 @@
 //
 // Workspace: the coefficient-domain top limb of both polynomials (2 N words)
 // plus G lifted limbs of both polynomials (2 G N words), G chosen to fill the
-// array (G = 4 at N = 2^16); the lifted limbs are processed in chunks of G.
+// array (G = 4 at N = 2^16, G = 1 at N = 2^17); the lifted limbs are processed
+// in chunks of G.  Rings above 2^17 do not fit (G would be 0).
 // Nothing in the array needs to start at zero: every word is written before it
 // is read within one call.  The array is shared by every call on a device, so
 // calls whose GPU work overlaps (other streams, other host threads) race.
@@ -30,7 +31,7 @@ static __device__ __align__(256) u64 g_rescale_ws[kNoAllocWords];
 
 u64 *g_ws_ptr[kMaxDevices];
 cudaError_t g_ws_err[kMaxDevices];
-std::once_flag g_ws_once[kMaxDevices];
+std::mutex g_ws_mu;
 
 struct ChunkArgs {
   const ModInfo *mods;
@@ -83,16 +84,25 @@ extern "C" int ckks_rescale_noalloc(ckks_ctx *c, ckks_ct *ct) {
     return CKKS_E_PARAM;
   if (ct->level == 0) return CKKS_E_LEVEL;
   const u32 n = c->n;
-  if (4 * (size_t)n > kNoAllocWords) return CKKS_E_PARAM;  // N above 2^16 does not fit the array
+  if (4 * (size_t)n > kNoAllocWords) return CKKS_E_PARAM;  // G >= 1 needs 4 N words: N <= 2^17
   int dev = 0;
   CK_CUDA(cudaGetDevice(&dev));
   if (dev != c->device || dev < 0 || dev >= kMaxDevices) return CKKS_E_PARAM;
-  // One-time set-up per device: the host-side symbol is not a device address,
-  // so ask the runtime for the array's device address on this device.
-  std::call_once(g_ws_once[dev], [dev] {
-    g_ws_err[dev] = cudaGetSymbolAddress(reinterpret_cast<void **>(&g_ws_ptr[dev]), g_rescale_ws);
-  });
-  if (g_ws_err[dev] != cudaSuccess || !g_ws_ptr[dev]) return CKKS_E_CUDA;
+  // Set-up per device: the host-side symbol is not a device address, so ask
+  // the runtime for the array's device address on this device.  A failed
+  // lookup is not cached: the next call tries again.
+  {
+    std::lock_guard<std::mutex> lock(g_ws_mu);
+    if (!g_ws_ptr[dev]) {
+      g_ws_err[dev] = cudaGetSymbolAddress(reinterpret_cast<void **>(&g_ws_ptr[dev]), g_rescale_ws);
+      if (g_ws_err[dev] != cudaSuccess) {
+        g_ws_ptr[dev] = nullptr;
+        cudaGetLastError();
+        return CKKS_E_CUDA;
+      }
+    }
+  }
+  if (!g_ws_ptr[dev]) return CKKS_E_CUDA;
 
   const int level = (int)ct->level;
   const int G = (int)std::min<size_t>((size_t)level, (kNoAllocWords - 2 * (size_t)n) / (2 * (size_t)n));

@@ -104,7 +104,7 @@ class REBlock:
         self._mask_pt = {}
         # None: one bootstrap per weight ciphertext (reading C16); k: the
         # two-pass iterative bootstrap with 2^k (reading B12), the other
-        # reading of the step's "two iterations of approximate bootstrapping"
+        # reading of the step's two bootstrapping passes (Sec. 4.3.4)
         self.iterative_log2_k = iterative_log2_k
 
     def refresh(self, cts):

@@ -59,6 +59,10 @@ SMALL = Workload("n4096_L6_dnum3", 12, (61,) + (55,) * 5, (61,) * 2, 3, 55.0,
                  batch=3, rot_steps=(1, 2, 4, -1))
 MID = Workload("n8192_L8_dnum3", 13, (61,) + (55,) * 7, (61,) * 3, 3, 55.0,
                batch=2, rot_steps=(1, 8))
+# N = 2^15, the other ring degree of the uneven batch, on a short chain of the
+# same prime sizes (the primes are shared with N = 2^16: all = 1 mod 2^17)
+N15 = Workload("n32768_L6_dnum3", 15, (61,) + (55,) * 5, (61,) * 2, 3, 55.0,
+               batch=2, rot_steps=(1, 1 << 13))
 
 
 # Bootstrapping chain (25 ciphertext primes = base + 24 levels, Table 3's l = 24):

@@ -27,9 +27,9 @@ def _pair(w, rot=ROT_STEPS, conj=True):
     return ctx, orc
 
 
-@pytest.fixture(scope="module", params=["toy", "small", "mid", "n17"])
+@pytest.fixture(scope="module", params=["toy", "small", "mid", "n15", "n17"])
 def pair(request):
-    w = {"toy": si.TOY, "small": si.SMALL, "mid": si.MID, "n17": si.N17}[request.param]
+    w = {"toy": si.TOY, "small": si.SMALL, "mid": si.MID, "n15": si.N15, "n17": si.N17}[request.param]
     ctx, orc = _pair(w)
     yield w, ctx, orc
     ctx.close()

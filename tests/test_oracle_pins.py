@@ -294,28 +294,38 @@ def _crt(residues, moduli):
     return x % M
 
 
-def test_merged_moddown_rescale_is_rounded_division(tiny_oracle):
-    """Reading C21: out = floor((X + H) / S) + e = round(X / S) + e with
-    S = P q_l, H = (S - 1)/2 and e in {0, 1}, e = 1 only where the overflow
-    estimate's fixed-point sum falls within 2^-28 of an integer."""
-    o = tiny_oracle
+def _merged_is_rounded_division(o, seed):
+    """The oracle's merged ModDown-rescale of random residues X over
+    q_0..q_l, P equals round(X / (P q_l)) by Python big integers, on every
+    coefficient (the integer X is the CRT representative in [0, Q_l P))."""
     level, K = o.n_q - 1, o.n_p
     ext = list(range(level + 1)) + [o.n_q + k for k in range(K)]
     moduli = [int(o.moduli[m]) for m in ext]
-    rng = np.random.default_rng(21)
+    rng = np.random.default_rng(seed)
     x = np.stack([rng.integers(0, m, size=o.n, dtype=np.uint64) for m in moduli])
     out = o.moddown_rescale(o.ntt(x, ext), level)
     y = o.intt(out, list(range(level)))
     div = int(o.q[level]) * math.prod(int(o.moduli[o.n_q + k]) for k in range(K))
     Qlow = math.prod(int(q) for q in o.q[:level])
-    us = []
     for k in range(o.n):
         X = _crt([x[t, k] for t in range(len(ext))], moduli)
         Y = _crt([y[t, k] for t in range(level)], [int(q) for q in o.q[:level]])
-        e = (Y - (X + (div - 1) // 2) // div) % Qlow
-        assert e in (0, 1), (k, e)
-        us.append(e)
-    assert sum(us) <= 1  # e = 1 needs a near-integer fixed-point sum
+        assert (Y - (X + (div - 1) // 2) // div) % Qlow == 0, k
+
+
+def test_merged_moddown_rescale_is_rounded_division(tiny_oracle):
+    """Reading C21: the merged step's result is round(X / S), S = P q_l."""
+    _merged_is_rounded_division(tiny_oracle, 21)
+
+
+def test_merged_moddown_rescale_is_rounded_division_with_eight_special_primes():
+    """The same at the benchmark's gadget shape: K = 8 special primes of 61 bits
+    (S spans nine primes, about 2^540), 61- and 55-bit ciphertext primes, on a
+    2^6 ring, four independent draws."""
+    from oracle import Oracle
+    o = Oracle(6, (61, 55, 55, 55, 55), (61,) * 8, 2, h=8, sigma=3.2)
+    for seed in range(4):
+        _merged_is_rounded_division(o, 40 + seed)
 
 
 def test_merged_mul_relin_rescale_matches_separate_steps(toy_oracle):

@@ -22,7 +22,8 @@ def _random_ct(ctx, level, seed):
     return arr
 
 
-@pytest.mark.parametrize("w", [si.TOY, si.PLAIN], ids=["n4096", "n65536_L24"])
+# N = 2^17 leaves room for one lifted limb per pass (the chunk loop at G = 1)
+@pytest.mark.parametrize("w", [si.TOY, si.PLAIN, si.N17], ids=["n4096", "n65536_L24", "n131072_g1"])
 def test_rescale_noalloc_equals_rescale_on_two_calls_in_a_row(w):
     import torch
     import paper_2506_19693_gb300 as ck
