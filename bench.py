@@ -205,97 +205,214 @@ def config_of(w, batch, form):
 
 
 # ---------------------------------------------------------------- GPU arm
-# Algorithmic work per unit the library's profiler counts (a limb of N words,
-# except the basis conversions, whose unit is one source-target limb pair, and
-# the bootstrap's plaintext MAC and linear combination, whose unit is one limb
-# of N words moved to or from HBM):
-#   HBM words moved per unit (8 bytes each, N per limb),
-#   integer work per unit: Shoup butterflies or 64x64->128 MACs per coefficient,
-#   tensor work of bconv_tc: 8 x 8 byte products per coefficient and pair,
-#   2 flops each, at the fp16 dense rate (= the bf16 rate).
-def kernel_work(name, units, launches, w, ndig):
+# Roofline model (the roofs of each form): every kernel class is measured
+# against HBM and against the compute pipe its form runs on -- the integer
+# pipe for the uint64 CUDA-core kernels (the measured rate of the production
+# instruction sequence, ckks_alu_peaks), the tensor pipe for the byte-split
+# basis conversion (fp16 MMA at the measured dense bf16 rate).  The binding
+# roof is the one with the larger fraction (the tighter lower bound on time).
+# Units are the library profiler's: a limb of N words, except the basis
+# conversions (one source-target limb pair of one polynomial) and the
+# bootstrap's plaintext MAC and linear combination (one limb of N words moved
+# to or from HBM).
+ALU_UNITS = {"mac_per_s": "64x64->128 MAC/s", "bfly_fwd_loose_per_s": "Shoup butterflies/s",
+             "bfly_fwd_strict_per_s": "Shoup butterflies/s", "bfly_inv_approx_per_s": "Shoup butterflies/s",
+             "bfly_inv_exact_per_s": "Shoup butterflies/s"}
+
+
+def ip_digits(ks_hist, w):
+    """Average digit count of the key inner products, weighted by their
+    extended limbs (from the key-switch histogram); the top level's count
+    when no histogram is given."""
+    nq = len(w.q_bits)
+    alpha = -(-nq // w.dnum)
+    num = den = 0
+    for lvl, cnt in enumerate(ks_hist or []):
+        if cnt:
+            ext = lvl + 1 + len(w.p_bits)
+            num += cnt * ext * (-(-(lvl + 1) // alpha))
+            den += cnt * ext
+    return num / den if den else -(-nq // alpha)
+
+
+def kernel_work(name, units, w, ndig, prof):  # noqa: C901
+    """(HBM bytes, [(integer ops, roof key)], tensor flops) of `units` units of
+    kernel class `name`."""
     n = 1 << w.log_n
     lh = w.log_n - 8
     hbm_words = {"ntt_fwd_pass_a": 2, "ntt_fwd_pass_b": 2, "ntt_inv_pass_a": 2, "ntt_inv_pass_b": 2,
                  "automorph": 2, "tensor": 7, "ks_moddown_combine": 8, "ks_inner_product": ndig + 2,
-                 "boot_mac_ext": 1, "boot_lincomb": 1}.get(name)
-    alu = None
-    if name in ("ntt_fwd_pass_a", "ntt_inv_pass_a"):
-        alu = ("bfly", units * (n // 2) * lh)
-    elif name in ("ntt_fwd_pass_b", "ntt_inv_pass_b"):
-        alu = ("bfly", units * (n // 2) * 8)
-    elif name in ("bconv", "bconv_tc"):
-        # the conversion's modular MACs, whichever unit computes them (bconv_tc:
-        # against the CUDA-core MAC roof, as work-equivalent; tensor work below)
-        alu = ("mac", units * n)
+                 "boot_mac_ext": 1, "boot_lincomb": 1, "bconv": None, "bconv_tc": None}.get(name)
+    alu, tensor = [], None
+    if name.startswith("ntt_"):
+        per_limb = (n // 2) * (lh if name.endswith("pass_a") else 8)
+        if name.startswith("ntt_fwd"):
+            f = prof.get("ntt_fwd_strict_limbs", (0, 0, 0))[2] / max(1, prof.get("ntt_fwd_pass_a", (0, 0, 1))[2])
+            alu = [(units * (1 - f) * per_limb, "bfly_fwd_loose_per_s"), (units * f * per_limb, "bfly_fwd_strict_per_s")]
+        else:
+            f = prof.get("ntt_inv_exact_limbs", (0, 0, 0))[2] / max(1, prof.get("ntt_inv_pass_a", (0, 0, 1))[2])
+            alu = [(units * (1 - f) * per_limb, "bfly_inv_approx_per_s"), (units * f * per_limb, "bfly_inv_exact_per_s")]
+    elif name == "bconv":
+        alu = [(units * n, "mac_per_s")]
     elif name == "ks_inner_product":
-        alu = ("mac", units * 2 * ndig * n)
-    hbm = hbm_words * 8 * n * units if hbm_words is not None else None
-    tensor = units * n * 64 * 2 if name == "bconv_tc" else None
+        alu = [(units * 2 * ndig * n, "mac_per_s")]
+    if name == "bconv_tc":
+        tensor = units * n * 64 * 2  # 8 x 8 byte products per coefficient and pair, 2 flops each
+    if name in ("bconv", "bconv_tc"):
+        # the sources once, the targets once: per pair that is at least 8 N / sources
+        # + 8 N / targets; the launch's pairs come as 8 x 24 (ModUp) or 9 x 23 (merged)
+        hbm = units * 8 * n * (1 / 24 + 1 / 8)
+    else:
+        hbm = hbm_words * 8 * n * units if hbm_words is not None else None
     return hbm, alu, tensor
 
 
-def roofline(prof, w, ndig, hbm_peak, hbm_kind, alu_peaks, tensor_peak=None, name=None):
-    """Roofline of one kernel class (default: the one with the most device
-    time in the timed region)."""
-    total = sum(v[0] for v in prof.values())
+def part(prof, ks_hist, w):
+    """One context's profile: (profile, workload, inner-product digits)."""
+    return (prof, w, ip_digits(ks_hist, w))
+
+
+def class_work(parts, name):
+    """Device ms, launches, units and algorithmic work of one kernel class,
+    summed over the contexts' profiles."""
+    ms = nl = units = 0
+    hbm, alu, tensor = 0.0, [], 0.0
+    have_hbm = have_tc = False
+    for prof, w, ndig in parts:
+        m, l, u = prof.get(name, (0.0, 0, 0))
+        if not l:
+            continue
+        ms, nl, units = ms + m, nl + l, units + u
+        h, a, t = kernel_work(name, u, w, ndig, prof)
+        if h is not None:
+            hbm, have_hbm = hbm + h, True
+        alu += a
+        if t is not None:
+            tensor, have_tc = tensor + t, True
+    return ms, nl, units, (hbm if have_hbm else None), alu, (tensor if have_tc else None)
+
+
+def timed_classes(parts):
+    out = {}
+    for prof, _, _ in parts:
+        for k, v in prof.items():
+            if v[1]:
+                out[k] = out.get(k, 0.0) + v[0]
+    return out
+
+
+def roofline(parts, hbm_peak, peak_kind, alu_peaks, tensor_peak=None, name=None):
+    """Roofs of one kernel class (default: the one with the most device time in
+    the timed region): HBM plus the compute pipe of its form."""
+    classes = timed_classes(parts)
+    total = sum(classes.values())
     if name is None:
-        name = max(prof.items(), key=lambda kv: kv[1][0])[0]
-    ms, nlaunch, units = prof.get(name, (0.0, 0, 0))
+        name = max(classes.items(), key=lambda kv: kv[1])[0]
+    ms, nlaunch, units, hbm, alu, tensor = class_work(parts, name)
     if not nlaunch:
         return None
     sec = ms / 1e3
-    hbm, alu, tensor = kernel_work(name, units, nlaunch, w, ndig)
-    cands = []
+    roofs = {}
     if hbm is not None:
-        a = hbm / nlaunch / (sec / nlaunch) / 1e9
-        cands.append({"bound": "hbm", "achieved": a, "peak": hbm_peak, "unit": "GB/s", "frac": a / hbm_peak,
-                      "peak_source": f"{hbm_kind} hbm_gbs", "algorithmic_per_launch": hbm / nlaunch})
+        a = hbm / sec / 1e9
+        roofs["hbm"] = {"achieved": a, "peak": hbm_peak, "unit": "GB/s", "frac": a / hbm_peak,
+                        "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json copy bandwidth)",
+                        "algorithmic_per_launch": hbm / nlaunch}
     if tensor is not None and tensor_peak:
         a = tensor / sec / 1e12
-        cands.append({"bound": "tensor", "achieved": a, "peak": tensor_peak, "unit": "TFLOP/s",
-                      "frac": a / tensor_peak, "peak_source": f"{hbm_kind} bf16_tflops_sustained (fp16 = bf16 rate)",
-                      "algorithmic_per_launch": tensor / nlaunch})
-    if alu is not None and alu_peaks:
-        kind, ops = alu
-        pk = alu_peaks["mac_per_s"] if kind == "mac" else alu_peaks["bfly_per_s"]
-        a = ops / sec
-        c = {"bound": "alu", "achieved": a / 1e12, "peak": pk / 1e12,
-             "unit": "T 64x64->128 MAC/s" if kind == "mac" else "T Shoup butterflies/s",
-             "frac": a / pk, "peak_source": "measured on this GPU by ckks_alu_peaks (register-only "
-             "kernel of the same primitive)", "algorithmic_per_launch": ops / nlaunch}
-        if name == "bconv_tc":  # the same conversion work, done as byte-split MMAs + CUDA-core recombination
-            c["unit"] = "T modular MAC/s (work-equivalent)"
-            c["peak_source"] = ("the CUDA-core 64x64->128 MAC rate measured by ckks_alu_peaks, the roof of the "
-                                "uint64 form of the same conversion")
-        cands.append(c)
-    if not cands:
+        roofs["tensor"] = {"achieved": a, "peak": tensor_peak, "unit": "TFLOP/s", "frac": a / tensor_peak,
+                           "peak_source": f"{peak_kind} bf16_tflops_sustained (fp16 runs at the bf16 rate)",
+                           "algorithmic_per_launch": tensor / nlaunch}
+    if alu and alu_peaks:
+        t_min = sum(ops / alu_peaks[key] for ops, key in alu)
+        ops = sum(o for o, _ in alu)
+        keys = sorted({k for o, k in alu if o})
+        roofs["alu"] = {"achieved": ops / sec / 1e12, "peak": ops / t_min / 1e12 if t_min else None,
+                        "unit": "T " + ALU_UNITS[keys[0] if keys else alu[0][1]], "frac": t_min / sec,
+                        "peak_source": "measured on this GPU by ckks_alu_peaks: register-only kernels running "
+                                       "the production instruction sequence (" + ", ".join(keys) + ")",
+                        "algorithmic_per_launch": ops / nlaunch}
+    if not roofs:
         return None
-    best = max(cands, key=lambda c: c["frac"])
-    # measured DRAM bytes per unit (ncu) scaled to this step's average launch
+    bound = max(roofs, key=lambda k: roofs[k]["frac"])
+    best = dict(roofs[bound])
     tr = traffic_table().get(name)
     traffic = (tr["dram_bytes_per_unit"] * units / nlaunch
                if tr and tr.get("valid") and tr.get("dram_bytes_per_unit") else None)
-    best.update({"kernel": name, "avg_launch_us": ms / nlaunch * 1e3, "launches": nlaunch,
-                 "share_of_timed_device_ms": ms / total, "traffic": traffic,
+    best.update({"bound": bound, "kernel": name, "avg_launch_us": ms / nlaunch * 1e3, "launches": nlaunch,
+                 "share_of_timed_device_ms": ms / total if total else None, "traffic": traffic,
                  "traffic_source": "profiles/traffic.json (ncu dram__bytes_read.sum + dram__bytes_write.sum "
                                    "per unit x units per launch)" if traffic else None,
-                 "other_bounds": [c for c in cands if c is not best]})
+                 "roofs": {k: {kk: vv for kk, vv in v.items() if kk != "peak_source"} for k, v in roofs.items()}})
     return best
 
 
-def kernel_rooflines(prof, w, ndig, hbm_peak, hbm_kind, alu_peaks, tensor_peak):
-    """Binding-roof fraction of every kernel class with a work model, by share of device time."""
-    total = sum(v[0] for v in prof.values())
+def kernel_rooflines(parts, hbm_peak, peak_kind, alu_peaks, tensor_peak):
+    """Every kernel class with a work model, by share of device time: the
+    binding roof and the fraction of each roof."""
+    classes = timed_classes(parts)
+    total = sum(classes.values())
     out = {}
-    for name, (ms, nl, units) in sorted(prof.items(), key=lambda kv: -kv[1][0]):
-        if not nl:
-            continue
-        r = roofline(prof, w, ndig, hbm_peak, hbm_kind, alu_peaks, tensor_peak, name=name)
+    for name, ms in sorted(classes.items(), key=lambda kv: -kv[1]):
+        r = roofline(parts, hbm_peak, peak_kind, alu_peaks, tensor_peak, name=name)
+        nl = class_work(parts, name)[1]
         out[name] = {"share": round(ms / total, 4), "avg_launch_us": round(ms / nl * 1e3, 2),
                      "bound": r["bound"] if r else None, "frac": round(r["frac"], 4) if r else None,
-                     "achieved": round(r["achieved"], 2) if r else None, "unit": r["unit"] if r else None}
+                     "fracs": {k: round(v["frac"], 4) for k, v in r["roofs"].items()} if r else None}
     return out
+
+
+def op_roofline(parts, ops, seconds, hbm_peak, alu_peaks, tensor_peak, bytes_per_op):
+    """Op-level roofline of one phase: `ops` operations took `seconds` of device
+    time.  HBM: bytes_per_op (the method's own minimum) at the copy bandwidth.
+    Compute: every kernel class's algorithmic integer and tensor work in the
+    phase (profiler units) at its measured roof, summed."""
+    t_alu = t_tc = 0.0
+    for name in timed_classes(parts):
+        _, _, _, _, alu, tensor = class_work(parts, name)
+        t_alu += sum(o / alu_peaks[k] for o, k in alu)
+        if tensor:
+            t_tc += tensor / (tensor_peak * 1e12)
+    rate = ops / seconds
+    hbm_frac = bytes_per_op * rate / (hbm_peak * 1e9)
+    comp_frac = (t_alu + t_tc) / seconds
+    return {"ops_per_s": rate, "hbm": {"bytes_per_op": bytes_per_op, "achieved_gbs": bytes_per_op * rate / 1e9,
+                                       "frac": hbm_frac},
+            "compute": {"integer_pipe_s_per_op": t_alu / ops, "tensor_pipe_s_per_op": t_tc / ops,
+                        "frac": comp_frac},
+            "bound": "hbm" if hbm_frac >= comp_frac else "compute", "frac": max(hbm_frac, comp_frac)}
+
+
+def hmult_bytes(w, batch):
+    """Fused lower bound of one HMult+relin+rescale: read both inputs, the
+    relinearisation key once per batch, write the product one level down."""
+    n, L, K = 1 << w.log_n, len(w.q_bits), len(w.p_bits)
+    alpha = -(-L // w.dnum)
+    ndig = -(-L // alpha)
+    return 8 * n * (2 * 2 * L + ndig * 2 * (L + K) / batch + 2 * (L - 1))
+
+
+def rotation_bytes(w, batch, n_rot):
+    """One of n_rot hoisted rotations of a ciphertext: its input once per
+    n_rot rotations, one Galois key per batch, the output."""
+    n, L, K = 1 << w.log_n, len(w.q_bits), len(w.p_bits)
+    alpha = -(-L // w.dnum)
+    ndig = -(-L // alpha)
+    return 8 * n * (2 * L / n_rot + ndig * 2 * (L + K) / batch + 2 * L)
+
+
+def bootstrap_bytes(ks_hist, w, batch):
+    """The bootstrap's key-switch traffic per ciphertext: sum over its key
+    switches at level l of input (2 (l+1) limbs) + key (digits x 2 x (l+1+K)
+    limbs, shared by the batch) + output (2 l limbs)."""
+    n, K = 1 << w.log_n, len(w.p_bits)
+    alpha = -(-len(w.q_bits) // w.dnum)
+    words = 0.0
+    for lvl, cnt in enumerate(ks_hist):
+        if cnt:
+            ndig = -(-(lvl + 1) // alpha)
+            words += cnt / batch * (2 * (lvl + 1) + ndig * 2 * (lvl + 1 + K) / batch + 2 * lvl)
+    return 8 * n * words
 
 
 def run_gpu(args):
@@ -399,8 +516,11 @@ def run_gpu(args):
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         launches = ctx.launch_count() + bctx.launch_count() - launches0
-        prof = ctx.profile_read()
-        for k, v in bctx.profile_read().items():
+        hist_p, hist_b = ctx.ks_histogram(), bctx.ks_histogram()
+        prof_p, prof_b = ctx.profile_read(), bctx.profile_read()
+        parts = [part(prof_p, hist_p, w), part(prof_b, hist_b, wb)]
+        prof = dict(prof_p)
+        for k, v in prof_b.items():
             a = prof.get(k, (0.0, 0, 0))
             prof[k] = (a[0] + v[0], a[1] + v[1], a[2] + v[2])
         ctx.profile(False)
@@ -414,7 +534,7 @@ def run_gpu(args):
              sum(m[2].elapsed_time(m[3]) for m in marks), sum(m[0].elapsed_time(m[3]) for m in marks) / args.steps],
             dist, "cuda")
         return {"mul_ms": mul_ms, "rot_ms": rot_ms, "boot_ms": boot_ms, "step_ms": step_ms, "prof": prof,
-                "launches": launches, "errors": errs, "clocks": clk,
+                "parts": parts, "launches": launches, "errors": errs, "clocks": clk,
                 **job_rates(world, B, len(w.rot_steps), nb, args.steps, mul_ms, rot_ms, boot_ms)}
 
     main = timed(args.form, args.warmup, ClockSampler(local))
@@ -436,26 +556,62 @@ def run_gpu(args):
 
     # roofline of the dominant kernel class
     hbm, tflops, peak_kind = peaks()
-    mac_s, bfly_s = ctx.alu_peaks()
-    alu = {"mac_per_s": mac_s, "bfly_per_s": bfly_s}
-    ndig = -(-len(w.q_bits) // (-(-len(w.q_bits) // w.dnum)))
-    roof = roofline(prof, w, ndig, hbm, peak_kind, alu, tflops)
+    alu = ctx.alu_peaks()
+    roof = roofline(main["parts"], hbm, peak_kind, alu, tflops)
+
+    def phase_profiles():
+        """One more step, profiled phase by phase: each phase's kernel work and
+        key switches by level (for the op-level roofline)."""
+        out = {}
+        for name, fn, c, wl in (("hmult", lambda: ctx.mul_relin_batch(A, Bc, OUT, rescale=ck.RESCALE_MERGED), ctx, w),
+                                ("rotations", lambda: ctx.rotate_hoisted(A, list(w.rot_steps), ROT), ctx, w),
+                                ("bootstrap", lambda: bctx.bootstrap_batch(BIN, BOUT), bctx, wb)):
+            torch.cuda.synchronize()
+            c.profile(True)
+            fn()
+            torch.cuda.synchronize()
+            hist = c.ks_histogram()
+            out[name] = (part(c.profile_read(), hist, wl), hist)
+            c.profile(False)
+        return out
+
+    def op_rooflines(r):
+        ph = phase_profiles()
+        hm = op_roofline([ph["hmult"][0]], world * B * args.steps, r["mul_ms"] / 1e3, hbm, alu, tflops,
+                         hmult_bytes(w, B))
+        hm["bytes_model"] = ("2 inputs + the relinearisation key / batch + the product one level down "
+                             "(the fused minimum)")
+        ro = op_roofline([ph["rotations"][0]], world * B * len(w.rot_steps) * args.steps, r["rot_ms"] / 1e3, hbm,
+                         alu, tflops, rotation_bytes(w, B, len(w.rot_steps)))
+        ro["bytes_model"] = "the input once per 15 hoisted rotations + one Galois key / batch + the output"
+        bo = op_roofline([ph["bootstrap"][0]], world * nb * args.steps, r["boot_ms"] / 1e3, hbm, alu, tflops,
+                         bootstrap_bytes(ph["bootstrap"][1], wb, nb))
+        bo["bytes_model"] = ("sum over the circuit's key switches at level l of input (2(l+1) limbs) + key "
+                             "(digits x 2(l+1+K) limbs) / batch + output (2l limbs)")
+        bo["key_switches_per_bootstrap"] = sum(ph["bootstrap"][1]) / nb
+        bo["key_switches_by_level"] = {lvl: c / nb for lvl, c in enumerate(ph["bootstrap"][1]) if c}
+        return {"hmult": hm, "rotation": ro, "bootstrap": bo}
+
+    op_roofs = op_rooflines(main)
 
     # the same three phases in the other basis-conversion form, for comparison
     forms = {}
     if not args.no_form_compare:
         other = "tensor" if args.form == "uint64" else "uint64"
         cmp = timed(other, 2)
+        cmp_roofs = op_rooflines(cmp)
         ctx.set_form(args.form == "tensor")
         bctx.set_form(args.form == "tensor")
-        for f, r in ((args.form, main), (other, cmp)):
+        for f, r, orf in ((args.form, main, op_roofs), (other, cmp, cmp_roofs)):
             conv = "bconv_tc" if f == "tensor" else "bconv"
-            total = sum(v[0] for v in r["prof"].values())
+            total = sum(timed_classes(r["parts"]).values())
             forms[f] = {"hmult_per_s": r["hmult_per_s"], "rotations_per_s": r["rotations_per_s"],
                         "bootstraps_per_s": r["bootstraps_per_s"], "slot_error": r["errors"],
-                        "basis_conversion_share": r["prof"].get(conv, (0.0,))[0] / total,
-                        "basis_conversion_roofline": roofline(r["prof"], w, ndig, hbm, peak_kind, alu, tflops,
-                                                              name=conv)}
+                        "basis_conversion_share": timed_classes(r["parts"]).get(conv, 0.0) / total,
+                        "basis_conversion_roofline": roofline(r["parts"], hbm, peak_kind, alu, tflops, name=conv),
+                        "dominant_kernel_roofline": roofline(r["parts"], hbm, peak_kind, alu, tflops),
+                        "op_rooflines": {k: {"frac": v["frac"], "bound": v["bound"], "hbm_frac": v["hbm"]["frac"],
+                                             "compute_frac": v["compute"]["frac"]} for k, v in orf.items()}}
 
     # ReBoot RE-Block training step (Alg. 1 + Alg. 2 + Bootstrap of W, V), the
     # synthetic MLP workload: 128 samples x 784 features in [0, 1], 784 -> 128 -> 10,
@@ -477,7 +633,9 @@ def run_gpu(args):
         iterative = run_iterative(bctx, wb, BIN, BOUT, zb, torch, stream, reps=max(2, min(args.steps, 3)))
     uneven = None
     if not (args.no_uneven or args.small):
-        uneven = run_uneven(ctx, w, torch, stream, rank, reps=max(3, args.steps), warmup=args.warmup)
+        uneven = run_uneven(ctx, w, torch, stream, rank, reps=max(3, args.steps), warmup=args.warmup,
+                            hbm_peak=hbm)
+        ctx.set_form(args.form == "tensor")
 
     # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -519,10 +677,11 @@ def run_gpu(args):
                 "key_compression": key_compression,
                 "sparse_slot_bootstrap": sparse_boot,
                 "tuning": tuning,
-                "e2e": e2e, "roofline": roof, "alu_peaks": alu, "cpu_baseline": cpu, "clocks": clk,
+                "e2e": e2e, "roofline": roof, "op_rooflines": op_roofs, "alu_peaks": alu, "cpu_baseline": cpu,
+                "clocks": clk,
                 "gpu_launches": int(launches),
                 "kernel_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]},
-                "kernel_rooflines": kernel_rooflines(prof, w, ndig, hbm, peak_kind, alu, tflops)}
+                "kernel_rooflines": kernel_rooflines(main["parts"], hbm, peak_kind, alu, tflops)}
         print(json.dumps(line))
     bctx.close()
     ctx.close()
@@ -531,54 +690,119 @@ def run_gpu(args):
     return 0
 
 
-def run_uneven(ctx16, w, torch, stream, rank, reps, warmup):
-    """256 independent operations over ring degrees 2^15 / 2^16 (p = 1/2) and
-    levels uniform in 4..23, one third each HMult+relin(+rescale), rotation by
-    a random power of two and rescale; captured once as a CUDA graph and
-    replayed.  Returns ops/s of the graph replays and of the eager executor."""
+def run_uneven(ctx16, w, torch, stream, rank, reps, warmup, dnums=(3, 2), hbm_peak=None):
+    """256 independent operations over ring degrees 2^15 / 2^16 (p = 1/2) with
+    limb counts uniform in 4..24 (level index 3..23), one third each
+    HMult+relin(+rescale), rotation by a random power of two and rescale;
+    captured as one CUDA graph and replayed, in both basis-conversion forms and
+    for each gadget in `dnums` (3: the workload's; 2: the tuner's choice for
+    this chain), the same inputs every time.  Returns ops/s of the replays, of
+    the eager first run, and the algorithmic bytes of one replay."""
     import paper_2506_19693_gb300 as ck
-    ctx15 = ck.Context(15, w.q_bits, w.p_bits, w.dnum, w.h, w.sigma, w.log2_scale, stream=stream)
-    ctx15.keygen(5, rot_steps=[1 << k for k in range(14)])
-    tuned = {"n65536": ctx16.tune(len(w.q_bits) - 1, 64), "n32768": ctx15.tune(len(w.q_bits) - 1, 64)}
+    ctxs = {}  # (dnum, log_n) -> context
+    for d in dnums:
+        alpha = -(-len(w.q_bits) // d)
+        for log_n in (15, 16):
+            if d == w.dnum and log_n == 16:
+                c = ctx16
+            else:
+                c = ck.Context(log_n, w.q_bits, (w.p_bits[0],) * alpha, d, w.h, w.sigma, w.log2_scale, stream=stream)
+                c.keygen(5 if log_n == 15 else 1, rot_steps=[1 << k for k in range(log_n - 2)])
+                c._owned_by_uneven = True
+            ctxs[(d, log_n)] = c
+    tuned = {}
+    for (d, log_n), c in ctxs.items():
+        tuned[f"dnum{d}_n{1 << log_n}"] = {"ip_group": c.tune(len(w.q_bits) - 1, 64), "ntt_rows": c.tune_ntt(16)}
     rng = np.random.default_rng(shard_seeds(rank)["uneven"])
     scale = 2.0 ** w.log2_scale
-    ops = []
+    specs = []  # (log_n, kind, a, b, out, k)
+    n_bytes = 0.0
+    keys = set()
     for i in range(256):
-        c = ctx16 if rng.random() < 0.5 else ctx15
-        level = int(rng.integers(4, len(w.q_bits)))
+        log_n = 16 if rng.random() < 0.5 else 15
+        c = ctxs[(w.dnum, log_n)]
+        level = int(rng.integers(3, len(w.q_bits)))  # 4..24 limbs
         z = si.messages(600 + i, 2, c.n // 2)
         a = c.encrypt(c.encode(z[0], level, scale), level, scale, 900000 + i)
         out = c.new_ct(level + 1)
         kind = i % 3
+        limb = 8 * c.n
+        b, k = None, 0
         if kind == 0:
             b = c.encrypt(c.encode(z[1], level, scale), level, scale, 950000 + i)
-            ops.append(ck.Op(c, ck.OP_MUL_RELIN, a, out, b=b, rescale=True))
+            n_bytes += limb * (2 * 2 * (level + 1) + 2 * level)
+            keys.add((log_n, 0, level))
         elif kind == 1:
-            ops.append(ck.Op(c, ck.OP_ROTATE, a, out, k=int(1 << rng.integers(0, c.log_n - 2))))
+            k = int(1 << rng.integers(0, c.log_n - 2))
+            n_bytes += limb * 2 * 2 * (level + 1)
+            keys.add((log_n, k, level))
         else:
-            ops.append(ck.Op(c, ck.OP_RESCALE, a, out))
+            n_bytes += limb * (2 * (level + 1) + 2 * level)
+        specs.append((log_n, kind, a, b, out, k))
+    alpha = -(-len(w.q_bits) // w.dnum)
+    for log_n, _, level in keys:  # each key group reads its key once per replay (dnum 3)
+        n_bytes += 8 * (1 << log_n) * (-(-(level + 1) // alpha)) * 2 * (level + 1 + len(w.p_bits))
+
+    def ops_for(d):
+        ops = []
+        for log_n, kind, a, b, out, k in specs:
+            c = ctxs[(d, log_n)]
+            if kind == 0:
+                ops.append(ck.Op(c, ck.OP_MUL_RELIN, a, out, b=b, rescale=True))
+            elif kind == 1:
+                ops.append(ck.Op(c, ck.OP_ROTATE, a, out, k=k))
+            else:
+                ops.append(ck.Op(c, ck.OP_RESCALE, a, out))
+        return ops
+
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ck.execute(ops)
-    torch.cuda.synchronize()
-    eager_s = time.perf_counter() - t0
     gs = torch.cuda.Stream()  # captured graphs replay on a created stream; time on that stream
-    g = ck.Graph(ops, stream=gs)
-    for _ in range(warmup):
-        g.launch()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(gs)
-    for _ in range(reps):
-        g.launch()
-    e1.record(gs)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
-    g.close()
-    ctx15.close()
-    return {"ops_per_s_graph": 256 / (ms / 1e3), "ms_per_batch_graph": ms, "ops_per_s_eager_first_run": 256 / eager_s,
+    res = {}
+    eager = None
+    try:
+        for d in dnums:
+            for form in ("uint64", "tensor"):
+                for (dd, _), c in ctxs.items():
+                    if dd == d:
+                        c.set_form(form == "tensor")
+                ops = ops_for(d)
+                if eager is None:
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    ck.execute(ops)
+                    torch.cuda.synchronize()
+                    eager = time.perf_counter() - t0
+                g = ck.Graph(ops, stream=gs)
+                for _ in range(warmup):
+                    g.launch()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(gs)
+                for _ in range(reps):
+                    g.launch()
+                e1.record(gs)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                g.close()
+                row = {"ops_per_s_graph": 256 / (ms / 1e3), "ms_per_batch_graph": ms}
+                if d == w.dnum and hbm_peak:
+                    row["hbm_frac"] = n_bytes / (ms / 1e3) / (hbm_peak * 1e9)
+                res[f"dnum{d}_{form}"] = row
+    finally:
+        for c in ctxs.values():
+            c.set_form(False)
+        ctx16.set_form(True)
+        for c in ctxs.values():
+            if getattr(c, "_owned_by_uneven", False):
+                c.close()
+    best = max(res, key=lambda k: res[k]["ops_per_s_graph"])
+    return {"forms": res, "best": best, "ops_per_s_graph": res[best]["ops_per_s_graph"],
+            "ops_per_s_eager_first_run": 256 / eager,
+            "algorithmic_bytes_per_batch": n_bytes,
+            "bytes_model": "per op its inputs and output at their levels, plus each (ring, key, level) group's "
+                           "switching key once (dnum 3)",
             "ops": "256: 1/3 HMult+relin+rescale, 1/3 Rot(2^k), 1/3 rescale; N in {2^15, 2^16} p=1/2; "
-                   "levels U{4..23}", "replays": reps, "tuned_inner_group": tuned}
+                   "limbs U{4..24} (level index 3..23)", "replays": reps, "tuned": tuned}
 
 
 def run_n_scaling(torch, stream, reps):

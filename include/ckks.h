@@ -106,16 +106,27 @@ int ckks_ctx_profile(ckks_ctx *ctx, int enable);
  * launch count and the limbs processed since the last reset; then reset.
  * Any of the three arrays may be NULL.  Returns the number of classes. */
 int ckks_ctx_profile_read(ckks_ctx *ctx, double *ms, uint64_t *launches, uint64_t *limbs, int cap);
+/* Key switches by level since the last ckks_ctx_profile_read or
+ * ckks_ctx_profile call (counted whether timing is on or not): counts[l] =
+ * outputs of key inner products at level l (each reads one switching key),
+ * for l < min(cap, 64).  Call it before ckks_ctx_profile_read, which resets
+ * it.  Returns 64. */
+int ckks_ctx_ks_histogram(ckks_ctx *ctx, uint64_t *counts, int cap);
 /* Number of kernel classes and the name of class k. */
 int ckks_profile_kinds(void);
 const char *ckks_profile_kind_name(int k);
 /* Total kernels this context has launched since creation. */
 int ckks_ctx_launch_count(const ckks_ctx *ctx, uint64_t *count);
-/* Integer-pipe peaks measured on this GPU by register-only kernels built from
- * the production primitives: 64x64->128-bit multiply-accumulates per second
- * and lazy Shoup butterflies per second (either pointer may be NULL).
- * Synchronises the context stream; uses the context's scratch memory. */
-int ckks_alu_peaks(ckks_ctx *ctx, double *mac_per_s, double *bfly_per_s);
+/* Integer-pipe roofs measured on this GPU by register-only kernels that run
+ * the production instruction sequences themselves: out[0] = 128-bit
+ * multiply-accumulates per second (the basis conversion's and the key inner
+ * product's MAC), out[1] = loose forward NTT butterflies per second (primes
+ * with 65 q < 2^64), out[2] = strict forward butterflies, out[3] = inverse
+ * butterflies with the approximate quotient (primes below 2^61), out[4] =
+ * inverse butterflies with the exact quotient.  Writes min(cap, 5) values and
+ * returns 5 (or a negative status).  Synchronises the context stream; uses the
+ * context's scratch memory. */
+int ckks_alu_peaks(ckks_ctx *ctx, double *out, int cap);
 
 /* ---- arithmetic form --------------------------------------------------- */
 

@@ -66,9 +66,10 @@ SIGNATURES = {
     "ckks_profile_kinds": (_I, []),
     "ckks_profile_kind_name": (ctypes.c_char_p, [_I]),
     "ckks_ctx_launch_count": (_I, [_V, ctypes.POINTER(_U64)]),
-    "ckks_alu_peaks": (_I, [_V, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "ckks_alu_peaks": (_I, [_V, ctypes.POINTER(_D), _I]),
     "ckks_ctx_set_form": (_I, [_V, _I]),
     "ckks_ctx_device_error": (_I, [_V]),
+    "ckks_ctx_ks_histogram": (_I, [_V, _V, _I]),
     "ckks_debug_tc_expire": (_I, [_V, _U64]),
     "ckks_keygen_from_seed": (_I, [_V, _U64, _V, _I, _I, _I]),
     "ckks_keygen_galois": (_I, [_V, _U64]),
@@ -260,11 +261,22 @@ class Context:
         return {self.lib.ckks_profile_kind_name(i).decode(): (float(ms[i]), int(la[i]), int(li[i]))
                 for i in range(k)}
 
-    def alu_peaks(self) -> tuple[float, float]:
-        """(64x64->128 MACs/s, Shoup butterflies/s) measured on this GPU."""
-        m, b = ctypes.c_double(), ctypes.c_double()
-        _check(self.lib.ckks_alu_peaks(self._h, ctypes.byref(m), ctypes.byref(b)), "ckks_alu_peaks")
-        return m.value, b.value
+    def ks_histogram(self) -> list:
+        """Key switches per level since the last profile read (index = level)."""
+        out = np.zeros(64, dtype=np.uint64)
+        self.lib.ckks_ctx_ks_histogram(self._h, out.ctypes.data, 64)
+        return [int(v) for v in out]
+
+    def alu_peaks(self) -> dict:
+        """Integer-pipe roofs of the production sequences measured on this GPU:
+        {"mac_per_s", "bfly_fwd_loose_per_s", "bfly_fwd_strict_per_s", "bfly_inv_approx_per_s",
+        "bfly_inv_exact_per_s"}."""
+        out = (ctypes.c_double * 5)()
+        rc = self.lib.ckks_alu_peaks(self._h, out, 5)
+        if rc < 0:
+            raise CkksError(rc, "ckks_alu_peaks")
+        return dict(zip(("mac_per_s", "bfly_fwd_loose_per_s", "bfly_fwd_strict_per_s", "bfly_inv_approx_per_s",
+                         "bfly_inv_exact_per_s"), (float(v) for v in out)))
 
     def set_form(self, tensor: bool) -> None:
         """Basis conversion on the tensor cores (True) or the CUDA cores (False)."""

@@ -555,6 +555,12 @@ int ckks_ctx_profile(ckks_ctx *c, int enable) {
   return CKKS_OK;
 }
 
+int ckks_ctx_ks_histogram(ckks_ctx *c, uint64_t *counts, int cap) {
+  if (!c || cap < 0 || (cap > 0 && !counts)) return CKKS_E_PARAM;
+  for (int l = 0; l < cap && l < PROF_MAX_LEVEL; ++l) counts[l] = c->prof.ks_level[l];
+  return PROF_MAX_LEVEL;
+}
+
 int ckks_ctx_profile_read(ckks_ctx *c, double *ms, uint64_t *launches, uint64_t *limbs, int cap) {
   if (!c || cap < 0) return CKKS_E_PARAM;
   c->prof.collect();
@@ -593,7 +599,8 @@ const char *ckks_profile_kind_name(int k) {
   static const char *names[PK_COUNT] = {"ntt_fwd_pass_a", "ntt_fwd_pass_b", "ntt_inv_pass_a", "ntt_inv_pass_b",
                                         "bconv", "ks_inner_product", "ks_moddown_combine", "tensor",
                                         "automorph", "rescale", "elementwise", "encode_decode", "bconv_tc",
-                                        "boot_mac_ext", "boot_lincomb"};
+                                        "boot_mac_ext", "boot_lincomb", "ntt_fwd_strict_limbs",
+                                        "ntt_inv_exact_limbs"};
   return (k >= 0 && k < PK_COUNT) ? names[k] : "unknown";
 }
 

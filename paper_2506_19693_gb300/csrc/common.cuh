@@ -67,6 +67,47 @@ __device__ __forceinline__ void mac128(u64 &hi, u64 &lo, u64 a, u64 b) {
       : "l"(a), "l"(b));
 }
 __device__ __forceinline__ u64 addmod(u64 a, u64 b, u64 q) { return csub(a + b, q); }
+// High word of a 64 x 64-bit product less e, e in {0, 1, 2}: the low x low
+// partial product and the carries out of the cross products' low halves are
+// dropped (each of the three dropped terms is below 2^32 after the shift, so
+// together they carry at most 2 into the high word).  Three 32-bit multiplies
+// instead of the exact high word's four and its carry chain.
+__device__ __forceinline__ u64 umulhi_approx(u64 a, u64 b) {
+  const u32 al = (u32)a, ah = (u32)(a >> 32), bl = (u32)b, bh = (u32)(b >> 32);
+  return (u64)ah * bh + __umulhi(ah, bl) + __umulhi(al, bh);
+}
+// Shoup product with that quotient: w x - (floor(w_s x / 2^64) - e) q lies in
+// [0, 4q) (the exact quotient gives [0, 2q)); q < 2^62.
+__device__ __forceinline__ u64 shoup_approx(u64 x, u64 w, u64 w_s, u64 q) {
+  return w * x - umulhi_approx(w_s, x) * q;
+}
+// The NTT's butterflies, one per call (the production sequences, also timed
+// alone by the integer-pipe microbenchmark):
+// forward, loose (65 q < 2^64): no correction, approximate quotient
+__device__ __forceinline__ void bfly_fwd_loose(u64 &a, u64 &b, u64 w, u64 w_s, u64 q, u64 twoq) {
+  const u64 t = shoup_approx(b, w, w_s, q);
+  const u64 x = a;
+  a = x + t;
+  b = x + 2 * twoq - t;
+}
+// forward, strict (Harvey): inputs < 4q, x brought below 2q, outputs < 4q
+__device__ __forceinline__ void bfly_fwd_strict(u64 &a, u64 &b, u64 w, u64 w_s, u64 q, u64 twoq) {
+  u64 x = a;
+  if (x >= twoq) x -= twoq;
+  const u64 t = shoup_lazy(b, w, w_s, q);
+  a = x + t;
+  b = x + twoq - t;
+}
+// inverse (Gentleman-Sande): values in [0, r), r = 2q (exact quotient) or
+// 4q (APPROX, q < 2^61)
+template <bool APPROX>
+__device__ __forceinline__ void bfly_inv(u64 &a, u64 &b, u64 w, u64 w_s, u64 q, u64 r) {
+  const u64 x = a, y = b;
+  u64 sum = x + y;
+  if (sum >= r) sum -= r;
+  a = sum;
+  b = APPROX ? shoup_approx(x + r - y, w, w_s, q) : shoup_lazy(x + r - y, w, w_s, q);
+}
 // Counter-based uniform sampling (reading C4): draw(key, c) is output c + 1 of
 // SplitMix64 (Steele, Lea and Flood 2014) started at state `key`, and a
 // uniform residue is (draw(2 idx) 2^64 + draw(2 idx + 1)) mod q.

@@ -420,6 +420,7 @@ static int launch_inner(ckks_ctx *c, int level, int nv, const u64 *const *d, con
     a.base0[i] = pbase0 ? pbase0[i] : nullptr;
   }
   const int group = c->ip_group > 0 ? c->ip_group : 8;
+  c->prof.count_ks(level, (unsigned long long)nv);
   dim3 g((nv + group - 1) / group, (n + TPB - 1) / TPB, ext);
   switch (ndig) {
 #define ILAUNCH(D, M)                                                                                        \

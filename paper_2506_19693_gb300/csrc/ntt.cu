@@ -47,21 +47,6 @@ struct NttParams {
 // strided accesses of the row stages conflict-free.
 __device__ __forceinline__ int padb(int off) { return off + (off >> 4); }
 
-// High word of a 64 x 64-bit product less e, e in {0, 1, 2}: the low x low
-// partial product and the carries out of the cross products' low halves are
-// dropped (each of the three dropped terms is below 2^32 after the shift, so
-// together they carry at most 2 into the high word).  Three 32-bit multiplies
-// instead of the exact high word's four and its carry chain.
-__device__ __forceinline__ u64 umulhi_approx(u64 a, u64 b) {
-  const u32 al = (u32)a, ah = (u32)(a >> 32), bl = (u32)b, bh = (u32)(b >> 32);
-  return (u64)ah * bh + __umulhi(ah, bl) + __umulhi(al, bh);
-}
-// Shoup product with that quotient: w x - (floor(w_s x / 2^64) - e) q lies in
-// [0, 4q) (the exact quotient gives [0, 2q)); q < 2^62.
-__device__ __forceinline__ u64 shoup_approx(u64 x, u64 w, u64 w_s, u64 q) {
-  return w * x - umulhi_approx(w_s, x) * q;
-}
-
 // Cooley-Tukey stages of a 2^K-point block.  Strict (Harvey): inputs < 4q,
 // x brought below 2q before each butterfly, outputs < 4q.  LOOSE, for
 // 65 q < 2^64 only: no correction and the approximate Shoup product (t < 4q),
@@ -77,17 +62,10 @@ __device__ __forceinline__ void fwd_step_t(u64 (&v)[1 << K], TW tw_of, u64 q, u6
     for (int e = 0; e < (1 << K); ++e) {
       if (e & half) continue;
       const ulonglong2 w = tw_of(s, e >> (K - s));
-      u64 x = v[e];
-      if (LOOSE) {
-        const u64 t = shoup_approx(v[e + half], w.x, w.y, q);
-        v[e] = x + t;
-        v[e + half] = x + 2 * twoq - t;
-      } else {
-        if (x >= twoq) x -= twoq;
-        const u64 t = shoup_lazy(v[e + half], w.x, w.y, q);
-        v[e] = x + t;
-        v[e + half] = x + twoq - t;
-      }
+      if (LOOSE)
+        bfly_fwd_loose(v[e], v[e + half], w.x, w.y, q, twoq);
+      else
+        bfly_fwd_strict(v[e], v[e + half], w.x, w.y, q, twoq);
     }
   }
 }
@@ -121,11 +99,7 @@ __device__ __forceinline__ void inv_step_t(u64 (&v)[1 << K], TW tw_of, u64 q, u6
     for (int e = 0; e < (1 << K); ++e) {
       if (e & half) continue;
       const ulonglong2 w = tw_of(s, e >> (K - s));
-      const u64 x = v[e], y = v[e + half];
-      u64 sum = x + y;
-      if (sum >= r) sum -= r;
-      v[e] = sum;
-      v[e + half] = APPROX ? shoup_approx(x + r - y, w.x, w.y, q) : shoup_lazy(x + r - y, w.x, w.y, q);
+      bfly_inv<APPROX>(v[e], v[e + half], w.x, w.y, q, r);
     }
   }
 }
@@ -494,10 +468,14 @@ int launch_ntt(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, i
   prm.n = c->n;
   prm.n_limbs = nl;
   bool approx = true;  // inverse: every modulus below 2^61
+  int strict = 0;      // forward: limbs whose prime takes the strict butterfly
   for (int l = 0; l < nl; ++l) {
     prm.mod_of_limb[l] = (unsigned char)mods[l];
     approx = approx && c->mod[mods[l]] < APPROX_INV_BOUND;
+    strict += c->mod[mods[l]] >= LOOSE_BOUND ? 1 : 0;
   }
+  if (inverse && !approx) c->prof.count(PK_NTT_INV_EXACT, (unsigned long long)nl * npoly);
+  if (!inverse) c->prof.count(PK_NTT_FWD_STRICT, (unsigned long long)strict * npoly);
   for (int i = 0; i < npoly; ++i)  // the row passes move 16-byte words
     if (((uintptr_t)src[i] | (uintptr_t)dst[i]) & 15) return CKKS_E_PARAM;
   for (int p0 = 0; p0 < npoly; p0 += MAX_POLYS) {

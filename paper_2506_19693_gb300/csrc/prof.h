@@ -23,8 +23,14 @@ enum ProfKind {
   PK_BCONV_TC,
   PK_BOOT_MAC,        // units: limbs of N words moved (algorithmic)
   PK_BOOT_LINCOMB,    // units: limbs of N words moved (algorithmic)
+  // counting-only classes (no launches, no time): limbs of the forward NTT
+  // passes whose prime takes the strict butterfly (65 q >= 2^64), and limbs of
+  // inverse passes launched with the exact quotient (a prime >= 2^61)
+  PK_NTT_FWD_STRICT,
+  PK_NTT_INV_EXACT,
   PK_COUNT
 };
+constexpr int PROF_MAX_LEVEL = 64;
 
 struct Profiler {
   bool on = false;
@@ -40,6 +46,14 @@ struct Profiler {
   };
   std::vector<Rec> recs;
   double kind_ms[PK_COUNT] = {0};
+  // key switches by level: outputs of key inner products (each reads one
+  // switching key), indexed by the level they run at
+  unsigned long long ks_level[PROF_MAX_LEVEL] = {0};
+
+  void count(int kind, unsigned long long units) { kind_units[kind] += units; }
+  void count_ks(int level, unsigned long long n) {
+    if (level >= 0 && level < PROF_MAX_LEVEL) ks_level[level] += n;
+  }
 
   int begin(int kind, unsigned long long units, cudaStream_t st) {
     ++launches;
@@ -76,6 +90,7 @@ struct Profiler {
       kind_launches[k] = 0;
       kind_units[k] = 0;
     }
+    for (int l = 0; l < PROF_MAX_LEVEL; ++l) ks_level[l] = 0;
   }
   ~Profiler() {
     for (cudaEvent_t e : pool) cudaEventDestroy(e);
