@@ -194,7 +194,8 @@ def run_reference(args):
 
 
 FORM_NAMES = {"uint64": "uint64 CUDA-core basis conversion",
-              "tensor": "byte-split basis conversion on tcgen05 tensor cores"}
+              "tensor": "byte-split basis conversion on tcgen05 tensor cores",
+              "fused": "uint64 basis conversion fused with the NTTs' column passes (one kernel per column tile)"}
 
 
 def config_of(w, batch, form):
@@ -254,6 +255,14 @@ def kernel_work(name, units, w, ndig, prof):  # noqa: C901
             alu = [(units * (1 - f) * per_limb, "bfly_inv_approx_per_s"), (units * f * per_limb, "bfly_inv_exact_per_s")]
     elif name == "bconv":
         alu = [(units * n, "mac_per_s")]
+    elif name == "conv_fused":
+        # the conversion's MACs plus the column stages of the transforms around it
+        g = lambda k: prof.get(k, (0, 0, 0))[2]  # noqa: E731
+        src, dst, strict = g("fused_src_limbs"), g("fused_dst_limbs"), g("fused_dst_strict_limbs")
+        half = (n // 2) * lh
+        alu = [(units * n, "mac_per_s"), (src * half, "bfly_inv_approx_per_s"),
+               ((dst - strict) * half, "bfly_fwd_loose_per_s"), (strict * half, "bfly_fwd_strict_per_s")]
+        return 8 * n * (src + dst), alu, None
     elif name == "ks_inner_product":
         alu = [(units * 2 * ndig * n, "mac_per_s")]
     if name == "bconv_tc":
@@ -496,8 +505,8 @@ def run_gpu(args):
 
     def timed(form, warmup, clocks=None):
         """Warm-up, spot checks, then `args.steps` timed steps in one form."""
-        ctx.set_form(form == "tensor")
-        bctx.set_form(form == "tensor")
+        ctx.set_form(form)
+        bctx.set_form(form)
         for _ in range(warmup):
             step()
         torch.cuda.synchronize()
@@ -577,14 +586,15 @@ def run_gpu(args):
 
     def op_rooflines(r):
         ph = phase_profiles()
-        hm = op_roofline([ph["hmult"][0]], world * B * args.steps, r["mul_ms"] / 1e3, hbm, alu, tflops,
+        # the profiled pass is one step: its ops over one step's device time
+        hm = op_roofline([ph["hmult"][0]], B, r["mul_ms"] / args.steps / 1e3, hbm, alu, tflops,
                          hmult_bytes(w, B))
         hm["bytes_model"] = ("2 inputs + the relinearisation key / batch + the product one level down "
                              "(the fused minimum)")
-        ro = op_roofline([ph["rotations"][0]], world * B * len(w.rot_steps) * args.steps, r["rot_ms"] / 1e3, hbm,
+        ro = op_roofline([ph["rotations"][0]], B * len(w.rot_steps), r["rot_ms"] / args.steps / 1e3, hbm,
                          alu, tflops, rotation_bytes(w, B, len(w.rot_steps)))
         ro["bytes_model"] = "the input once per 15 hoisted rotations + one Galois key / batch + the output"
-        bo = op_roofline([ph["bootstrap"][0]], world * nb * args.steps, r["boot_ms"] / 1e3, hbm, alu, tflops,
+        bo = op_roofline([ph["bootstrap"][0]], nb, r["boot_ms"] / args.steps / 1e3, hbm, alu, tflops,
                          bootstrap_bytes(ph["bootstrap"][1], wb, nb))
         bo["bytes_model"] = ("sum over the circuit's key switches at level l of input (2(l+1) limbs) + key "
                              "(digits x 2(l+1+K) limbs) / batch + output (2l limbs)")
@@ -597,13 +607,15 @@ def run_gpu(args):
     # the same three phases in the other basis-conversion form, for comparison
     forms = {}
     if not args.no_form_compare:
-        other = "tensor" if args.form == "uint64" else "uint64"
-        cmp = timed(other, 2)
-        cmp_roofs = op_rooflines(cmp)
-        ctx.set_form(args.form == "tensor")
-        bctx.set_form(args.form == "tensor")
-        for f, r, orf in ((args.form, main, op_roofs), (other, cmp, cmp_roofs)):
-            conv = "bconv_tc" if f == "tensor" else "bconv"
+        runs = [(args.form, main, op_roofs)]
+        for other in FORM_NAMES:
+            if other != args.form:
+                r = timed(other, 2)
+                runs.append((other, r, op_rooflines(r)))
+        ctx.set_form(args.form)
+        bctx.set_form(args.form)
+        for f, r, orf in runs:
+            conv = {"tensor": "bconv_tc", "uint64": "bconv", "fused": "conv_fused"}[f]
             total = sum(timed_classes(r["parts"]).values())
             forms[f] = {"hmult_per_s": r["hmult_per_s"], "rotations_per_s": r["rotations_per_s"],
                         "bootstraps_per_s": r["bootstraps_per_s"], "slot_error": r["errors"],
@@ -624,10 +636,10 @@ def run_gpu(args):
         n_scaling = run_n_scaling(torch, stream, reps=max(2, min(args.steps, 3)))
     key_compression = None
     if not (args.no_key_compression or args.small):
-        key_compression = run_key_compression(torch, stream, max(3, min(args.steps, 5)), args.form == "tensor")
+        key_compression = run_key_compression(torch, stream, max(3, min(args.steps, 5)), args.form)
     sparse_boot = None
     if not (args.no_sparse_boot or args.small):
-        sparse_boot = run_sparse_boot(torch, stream, max(2, min(args.steps, 3)), args.form == "tensor")
+        sparse_boot = run_sparse_boot(torch, stream, max(2, min(args.steps, 3)), args.form)
     iterative = None
     if not (args.no_iterative or args.small):
         iterative = run_iterative(bctx, wb, BIN, BOUT, zb, torch, stream, reps=max(2, min(args.steps, 3)))
@@ -635,7 +647,7 @@ def run_gpu(args):
     if not (args.no_uneven or args.small):
         uneven = run_uneven(ctx, w, torch, stream, rank, reps=max(3, args.steps), warmup=args.warmup,
                             hbm_peak=hbm)
-        ctx.set_form(args.form == "tensor")
+        ctx.set_form(args.form)
 
     # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -761,10 +773,10 @@ def run_uneven(ctx16, w, torch, stream, rank, reps, warmup, dnums=(3, 2), hbm_pe
     eager = None
     try:
         for d in dnums:
-            for form in ("uint64", "tensor"):
+            for form in ("uint64", "tensor", "fused"):
                 for (dd, _), c in ctxs.items():
                     if dd == d:
-                        c.set_form(form == "tensor")
+                        c.set_form(form)
                 ops = ops_for(d)
                 if eager is None:
                     torch.cuda.synchronize()
@@ -791,7 +803,6 @@ def run_uneven(ctx16, w, torch, stream, rank, reps, warmup, dnums=(3, 2), hbm_pe
     finally:
         for c in ctxs.values():
             c.set_form(False)
-        ctx16.set_form(True)
         for c in ctxs.values():
             if getattr(c, "_owned_by_uneven", False):
                 c.close()
@@ -889,7 +900,7 @@ def run_n_scaling(torch, stream, reps):
     return out
 
 
-def run_sparse_boot(torch, stream, reps, tensor_form, log_slots=13):
+def run_sparse_boot(torch, stream, reps, form, log_slots=13):
     """Sparse-slot bootstrapping at N = 2^16 (reading B13): 2^13-slot messages
     repeated 4 times across the 2^15 slots, 16 ciphertexts per batch on the
     bootstrapping chain (25 + 9 primes), fresh encryptions at level 0."""
@@ -897,7 +908,7 @@ def run_sparse_boot(torch, stream, reps, tensor_form, log_slots=13):
     wb = si.BOOT
     ctx = ck.Context.from_workload(wb, stream=stream)
     try:
-        ctx.set_form(tensor_form)
+        ctx.set_form(form)
         ctx.boot_set_slots(1 << log_slots)
         ctx.keygen_boot(4)
         ctx.boot_setup()
@@ -928,7 +939,7 @@ def run_sparse_boot(torch, stream, reps, tensor_form, log_slots=13):
         ctx.close()
 
 
-def run_key_compression(torch, stream, reps, tensor_form):
+def run_key_compression(torch, stream, reps, form):
     """Compressed switching keys (b rows plus the generator state of a) against
     full keys, on the HMult workload: merged HMult+relin+rescale over 64 pairs and
     over 1 pair, and one input rotated by the 15 powers of two in one hoisted
@@ -943,7 +954,7 @@ def run_key_compression(torch, stream, reps, tensor_form):
         ctx = ck.Context.from_workload(w, stream=stream)
         try:
             ctx.set_key_compression(compressed)
-            ctx.set_form(tensor_form)
+            ctx.set_form(form)
             ctx.keygen(9, rot_steps=list(w.rot_steps))
             z = si.messages(720, 2, w.slots)
             base = [ctx.encrypt(ctx.encode(z[i], level, scale), level, scale, 920 + i) for i in range(2)]
@@ -1188,8 +1199,9 @@ def main():
     ap.add_argument("--no-sparse-boot", action="store_true")
     ap.add_argument("--no-n-scaling", action="store_true")
     ap.add_argument("--no-form-compare", action="store_true")
-    ap.add_argument("--form", default="tensor", choices=["uint64", "tensor"],
-                    help="basis conversion on the CUDA cores (uint64) or the tensor cores (tensor)")
+    ap.add_argument("--form", default="tensor", choices=["uint64", "tensor", "fused"],
+                    help="basis conversion on the CUDA cores (uint64), on the tensor cores (tensor), or on the "
+                         "CUDA cores fused with the transforms' column passes (fused)")
     ap.add_argument("--small", action="store_true",
                     help="8 pairs and 2 bootstraps: a few GB on the device, for ncu captures")
     args = ap.parse_args()

@@ -132,11 +132,18 @@ int ckks_alu_peaks(ckks_ctx *ctx, double *out, int cap);
 
 #define CKKS_FORM_UINT64 0 /* basis conversion as 64x64->128 MACs on the CUDA cores (default) */
 #define CKKS_FORM_TENSOR 1 /* basis conversion as an exact byte-split fp16 GEMM on tcgen05   */
+#define CKKS_FORM_FUSED 2  /* uint64 conversion fused with the NTTs' column passes          */
 
-/* Select how ModUp / ModDown basis conversion (reading C8/C9) runs.  Both forms
+/* Select how ModUp / ModDown basis conversion (reading C8/C9) runs.  All forms
  * give identical limbs.  The tensor form splits each residue into bytes and the
  * constants into byte planes, multiplies on tcgen05 tensor cores with exact fp32
- * accumulation in tensor memory, and recombines modularly. */
+ * accumulation in tensor memory, and recombines modularly.  The fused form runs
+ * the key-switch pipeline iNTT -> conversion -> NTT with the middle in one
+ * kernel per column tile: the inverse transform's column stages, the
+ * conversion (64x64->128 multiply-accumulates on the CUDA cores) and the
+ * forward transform's column stages on shared-memory tiles, so the
+ * coefficient-domain digits and conversion targets never reach HBM (rings up
+ * to 2^16; the 2^17 ring runs the uint64 form's kernels). */
 int ckks_ctx_set_form(ckks_ctx *ctx, int form);
 /* CKKS_E_TIMEOUT if a bounded device-side wait of a tensor-core kernel expired
  * since the last call (the affected outputs are invalid; no matrix multiply was

@@ -278,9 +278,11 @@ class Context:
         return dict(zip(("mac_per_s", "bfly_fwd_loose_per_s", "bfly_fwd_strict_per_s", "bfly_inv_approx_per_s",
                          "bfly_inv_exact_per_s"), (float(v) for v in out)))
 
-    def set_form(self, tensor: bool) -> None:
-        """Basis conversion on the tensor cores (True) or the CUDA cores (False)."""
-        _check(self.lib.ckks_ctx_set_form(self._h, 1 if tensor else 0), "ckks_ctx_set_form")
+    def set_form(self, form) -> None:
+        """Basis-conversion form: "uint64" (or False), "tensor" (or True) or
+        "fused" (the conversion fused with the transforms' column passes)."""
+        code = {False: 0, True: 1, "uint64": 0, "tensor": 1, "fused": 2}[form]
+        _check(self.lib.ckks_ctx_set_form(self._h, code), "ckks_ctx_set_form")
 
     def device_error(self) -> int:
         return self.lib.ckks_ctx_device_error(self._h)

@@ -577,8 +577,9 @@ int ckks_ctx_profile_read(ckks_ctx *c, double *ms, uint64_t *launches, uint64_t 
 int ckks_profile_kinds(void) { return (int)PK_COUNT; }
 
 int ckks_ctx_set_form(ckks_ctx *c, int form) {
-  if (!c || (form != CKKS_FORM_UINT64 && form != CKKS_FORM_TENSOR)) return CKKS_E_PARAM;
+  if (!c || (form != CKKS_FORM_UINT64 && form != CKKS_FORM_TENSOR && form != CKKS_FORM_FUSED)) return CKKS_E_PARAM;
   c->use_tc = form == CKKS_FORM_TENSOR;
+  c->use_fused = form == CKKS_FORM_FUSED;
   return CKKS_OK;
 }
 
@@ -599,8 +600,9 @@ const char *ckks_profile_kind_name(int k) {
   static const char *names[PK_COUNT] = {"ntt_fwd_pass_a", "ntt_fwd_pass_b", "ntt_inv_pass_a", "ntt_inv_pass_b",
                                         "bconv", "ks_inner_product", "ks_moddown_combine", "tensor",
                                         "automorph", "rescale", "elementwise", "encode_decode", "bconv_tc",
-                                        "boot_mac_ext", "boot_lincomb", "ntt_fwd_strict_limbs",
-                                        "ntt_inv_exact_limbs"};
+                                        "boot_mac_ext", "boot_lincomb", "conv_fused", "ntt_fwd_strict_limbs",
+                                        "ntt_inv_exact_limbs", "fused_src_limbs", "fused_dst_limbs",
+                                        "fused_dst_strict_limbs"};
   return (k >= 0 && k < PK_COUNT) ? names[k] : "unknown";
 }
 

@@ -98,6 +98,7 @@ struct ckks_ctx {
   int ip_group = 8;                  // key inner product: outputs per thread (ckks_tune)
   int ntt_rows = 16;                 // NTT row pass: rows per CTA, 16 or 8 (ckks_tune_ntt)
   bool use_tc = false;               // basis conversion on the tensor cores (ckks_ctx_set_form)
+  bool use_fused = false;            // conversion fused with the transforms' column passes (N <= 2^16)
   std::map<size_t, void *> tc_bmats; // byte-plane constants per conversion
   int *tc_err = nullptr;             // device flag: a bounded wait expired
   // host-streamed batches (ckks_mul_relin_host): copy streams, staging slots, events
@@ -144,6 +145,31 @@ int ensure_fscratch(ckks_ctx *c, size_t words);
 // mods[l].  src may equal dst.
 int launch_ntt(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, int nl,
                const int *mods, bool inverse);
+// One pass only: NTT_ROWS runs the row pass alone (the inverse's first pass,
+// src -> dst; the forward's last pass, src -> dst) around a fused column pass.
+enum { NTT_COLS = 1, NTT_ROWS = 2, NTT_BOTH = 3 };
+int launch_ntt_part(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, int nl,
+                    const int *mods, bool inverse, int part);
+
+// ---- fused conversion column pass (ntt.cu) ----
+// A basis conversion between NTT domains with its transforms' column passes
+// fused in one kernel: the sources have had the inverse row pass
+// (launch_ntt_part NTT_ROWS), the targets get the forward row pass after.
+struct FusedConv {
+  struct Digit {
+    int ns = 0, nt = 0, gap_lo = 0, gap_hi = 0;  // targets tt -> limb tt (< gap_lo) or tt + gap_hi - gap_lo
+    size_t src_off = 0, dst_off = 0;            // words from a polynomial's src / dst pointer
+    int src_mod[16] = {0};
+    const u64 *inv = nullptr;                   // device [ns] Shoup pairs
+    const u64 *tab = nullptr;                   // device [nt][ns]
+  };
+  int ndig = 0;
+  Digit dig[8];
+  int pos_mod[MAX_MODS] = {0};                  // modulus of each target limb position
+  const u64 *src_add = nullptr, *dst_sub = nullptr, *rdiv = nullptr, *negs = nullptr;  // reading C21
+};
+bool conv_fused_supported(const ckks_ctx *c);
+int launch_conv_fused(ckks_ctx *c, const FusedConv &f, const u64 *const *src, u64 *const *dst, int np);
 
 // ---- packed wire format (ops.cu) ----
 // A ciphertext at level l on the wire: polynomial 0 then polynomial 1, each

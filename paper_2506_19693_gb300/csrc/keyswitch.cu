@@ -324,6 +324,46 @@ int ks_modup(ckks_ctx *c, int level, int np, const u64 *const *d, u64 *ws, u64 *
   }
   int mods[MAX_MODS];
   for (int t = 0; t < ext; ++t) mods[t] = c->ext_mod(level, t);
+  if (c->use_fused && conv_fused_supported(c)) {
+    // the fused pipeline: inverse row pass of every limb, one launch of the
+    // fused column pass for all digits, the forward row pass of their targets
+    rc = launch_ntt_part(c, d, dc.data(), np, nl, mods, true, NTT_ROWS);
+    if (rc) return rc;
+    FusedConv f;
+    f.ndig = ndig;
+    for (int j = 0; j < ndig; ++j) {
+      const int lo = j * c->alpha, hi = std::min((j + 1) * c->alpha, nl), ns = hi - lo;
+      const u64 *tbl = c->d_conv + c->conv.modup_off[(size_t)level * c->n_digits + j];
+      FusedConv::Digit &g = f.dig[j];
+      g.ns = ns;
+      g.nt = ext - ns;
+      g.gap_lo = lo;
+      g.gap_hi = hi;
+      g.src_off = (size_t)lo * n;
+      g.dst_off = (size_t)j * ext * n;
+      for (int i = 0; i < ns; ++i) g.src_mod[i] = lo + i;
+      g.inv = tbl;
+      g.tab = tbl + 2 * ns;
+    }
+    for (int t = 0; t < ext; ++t) f.pos_mod[t] = mods[t];
+    std::vector<const u64 *> dcc(dc.begin(), dc.end());
+    rc = launch_conv_fused(c, f, dcc.data(), eb.data(), np);
+    if (rc) return rc;
+    std::vector<const u64 *> s2(np);
+    std::vector<u64 *> d2(np);
+    for (int j = 0; j < ndig; ++j) {
+      const int lo = j * c->alpha, hi = std::min((j + 1) * c->alpha, nl);
+      if (lo > 0) {
+        for (int i = 0; i < np; ++i) d2[i] = eb[i] + (size_t)j * ext * n, s2[i] = d2[i];
+        rc = launch_ntt_part(c, s2.data(), d2.data(), np, lo, mods, false, NTT_ROWS);
+        if (rc) return rc;
+      }
+      for (int i = 0; i < np; ++i) d2[i] = eb[i] + ((size_t)j * ext + hi) * n, s2[i] = d2[i];
+      rc = launch_ntt_part(c, s2.data(), d2.data(), np, ext - hi, mods + hi, false, NTT_ROWS);
+      if (rc) return rc;
+    }
+    return CKKS_OK;
+  }
   rc = launch_ntt(c, d, dc.data(), np, nl, mods, true);
   if (rc) return rc;
   std::vector<const u64 *> srcs(np);
@@ -447,6 +487,10 @@ static int launch_inner(ckks_ctx *c, int level, int nv, const u64 *const *d, con
   return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_CUDA;
 }
 
+static int combine_rescale(ckks_ctx *c, int level, int nv, u64 *const *acc, u64 *const *z,
+                           const u64 *const *base0, const u64 *const *base1, u64 *const *o0, u64 *const *o1,
+                           const MdrLayout &L);
+
 // ModDown and rescale merged (reading C21) on the accumulators of nv outputs:
 // o_c = round((acc_c + P base_c) / (P q_l)) - u over q_0..q_{l-1}.
 static int ks_merged_tail(ckks_ctx *c, int level, int nv, u64 *const *acc, u64 *const *z, const int *mods,
@@ -482,6 +526,37 @@ static int ks_merged_tail(ckks_ctx *c, int level, int nv, u64 *const *acc, u64 *
       pd[2 * i + cc] = acc[i] + ((size_t)cc * ext + l) * n;
       ps[2 * i + cc] = pd[2 * i + cc];
     }
+  if (c->use_fused && conv_fused_supported(c)) {
+    rc = launch_ntt_part(c, ps.data(), pd.data(), 2 * nv, ns, mods + l, true, NTT_ROWS);
+    if (rc) return rc;
+    FusedConv f;
+    f.ndig = 1;
+    FusedConv::Digit &g = f.dig[0];
+    g.ns = ns;
+    g.nt = l;
+    g.gap_lo = g.gap_hi = l;
+    g.src_mod[0] = l;
+    for (int k = 0; k < K; ++k) g.src_mod[1 + k] = c->n_q + k;
+    g.inv = c->d_conv + L.inv;
+    g.tab = c->d_conv + L.tab;
+    for (int t = 0; t < l; ++t) f.pos_mod[t] = t;
+    f.src_add = c->d_conv + L.src_add;
+    f.dst_sub = c->d_conv + L.dst_sub;
+    f.rdiv = c->d_conv + L.rdiv;
+    f.negs = c->d_conv + L.negs;
+    std::vector<u64 *> pz(2 * nv);
+    for (int i = 0; i < nv; ++i)
+      for (int cc = 0; cc < 2; ++cc) pz[2 * i + cc] = z[i] + (size_t)cc * l * n;
+    for (int p0 = 0; p0 < 2 * nv; p0 += MAX_CTS) {
+      const int cnt = std::min(MAX_CTS, 2 * nv - p0);
+      rc = launch_conv_fused(c, f, ps.data() + p0, pz.data() + p0, cnt);
+      if (rc) return rc;
+    }
+    std::vector<const u64 *> pzc(pz.begin(), pz.end());
+    rc = launch_ntt_part(c, pzc.data(), pz.data(), 2 * nv, l, mods, false, NTT_ROWS);
+    if (rc) return rc;
+    return combine_rescale(c, level, nv, acc, z, base0, base1, o0, o1, L);
+  }
   rc = launch_ntt(c, ps.data(), pd.data(), 2 * nv, ns, mods + l, true);
   if (rc) return rc;
   for (int p0 = 0; p0 < 2 * nv; p0 += MAX_CTS) {
@@ -522,6 +597,15 @@ static int ks_merged_tail(ckks_ctx *c, int level, int nv, u64 *const *acc, u64 *
     for (int cc = 0; cc < 2; ++cc) pz[2 * i + cc] = z[i] + (size_t)cc * l * n, pzc[2 * i + cc] = pz[2 * i + cc];
   rc = launch_ntt(c, pzc.data(), pz.data(), 2 * nv, l, mods, false);
   if (rc) return rc;
+  return combine_rescale(c, level, nv, acc, z, base0, base1, o0, o1, L);
+}
+
+// out_c = (acc_c - z_c) S^-1 + d_c q_l^-1 over q_0..q_{l-1} (the merged finish)
+static int combine_rescale(ckks_ctx *c, int level, int nv, u64 *const *acc, u64 *const *z,
+                           const u64 *const *base0, const u64 *const *base1, u64 *const *o0, u64 *const *o1,
+                           const MdrLayout &L) {
+  const u32 n = c->n;
+  const int l = level, ext = level + 1 + c->n_p;
   CombineRArgs r;
   r.mods = c->d_mods;
   r.n = n;
@@ -558,9 +642,30 @@ static int moddown_tail(ckks_ctx *c, int level, int nv, u64 *const *acc, u64 *co
       pd[2 * i + cc] = acc[i] + ((size_t)cc * ext + nl) * n;
       ps[2 * i + cc] = pd[2 * i + cc];
     }
-  rc = launch_ntt(c, ps.data(), pd.data(), 2 * nv, K, mods + nl, true);
+  const bool fused = c->use_fused && conv_fused_supported(c);
+  rc = launch_ntt_part(c, ps.data(), pd.data(), 2 * nv, K, mods + nl, true, fused ? NTT_ROWS : NTT_BOTH);
   if (rc) return rc;
-  for (int p0 = 0; p0 < 2 * nv; p0 += MAX_CTS) {
+  if (fused) {
+    FusedConv f;
+    f.ndig = 1;
+    FusedConv::Digit &g = f.dig[0];
+    g.ns = K;
+    g.nt = nl;
+    g.gap_lo = g.gap_hi = nl;
+    for (int k = 0; k < K; ++k) g.src_mod[k] = c->n_q + k;
+    g.inv = c->d_conv + c->conv.moddown_phat_inv;
+    g.tab = c->d_conv + c->conv.moddown_phat_mod;
+    for (int t = 0; t < nl; ++t) f.pos_mod[t] = t;
+    std::vector<u64 *> pz(2 * nv);
+    for (int i = 0; i < nv; ++i)
+      for (int cc = 0; cc < 2; ++cc) pz[2 * i + cc] = z[i] + (size_t)cc * nl * n;
+    for (int p0 = 0; p0 < 2 * nv; p0 += MAX_CTS) {
+      const int cnt = std::min(MAX_CTS, 2 * nv - p0);
+      rc = launch_conv_fused(c, f, ps.data() + p0, pz.data() + p0, cnt);
+      if (rc) return rc;
+    }
+  }
+  for (int p0 = 0; !fused && p0 < 2 * nv; p0 += MAX_CTS) {
     const int cnt = std::min(MAX_CTS, 2 * nv - p0);
     BConvArgs a;
     a.inv = c->d_conv + c->conv.moddown_phat_inv;
@@ -593,7 +698,7 @@ static int moddown_tail(ckks_ctx *c, int level, int nv, u64 *const *acc, u64 *co
       pd[2 * i + cc] = z[i] + (size_t)cc * nl * n;
       ps[2 * i + cc] = pd[2 * i + cc];
     }
-  rc = launch_ntt(c, ps.data(), pd.data(), 2 * nv, nl, mods, false);
+  rc = launch_ntt_part(c, ps.data(), pd.data(), 2 * nv, nl, mods, false, fused ? NTT_ROWS : NTT_BOTH);
   if (rc) return rc;
   CombineArgs a;
   a.mods = c->d_mods;

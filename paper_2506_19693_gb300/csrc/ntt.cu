@@ -18,7 +18,9 @@
 // Each thread owns 2^s words and runs s butterfly stages in registers
 // (Harvey's lazy butterflies: values stay in [0, 4q) forward, [0, 2q)
 // inverse; q < 2^62).
-#include "ctx.h"
+#include <algorithm>
+
+#include "ops.cuh"
 
 namespace {
 
@@ -422,22 +424,26 @@ __global__ void __launch_bounds__(THREADS, 4) inv_pass_a(const NttParams prm) {
     inv_a_body<LH, S1, APPROX>(prm, sm, mi, dst);
 }
 
+// part: NTT_BOTH, or one pass alone -- the inverse's row pass (NTT_ROWS) or the
+// forward's row pass (NTT_ROWS, reading src) around a fused column pass.
 template <int LH, int RB, bool APPROX>
-void launch_inv(ckks_ctx *c, const NttParams &prm, int npoly) {
+void launch_inv(ckks_ctx *c, const NttParams &prm, int npoly, int part) {
   constexpr int S1 = (LH + 1) / 2;
   const unsigned long long units = (unsigned long long)prm.n_limbs * npoly;
   dim3 ga(BROW / ca_of(LH), prm.n_limbs, npoly), gb((1 << LH) / RB, prm.n_limbs, npoly);
-  PROF_LAUNCH(c, PK_NTT_INV_B, units, (inv_pass_b<LH, RB, APPROX><<<gb, threads_b<RB>(), 0, c->stream>>>(prm)));
-  PROF_LAUNCH(c, PK_NTT_INV_A, units, (inv_pass_a<LH, S1, APPROX><<<ga, THREADS, 0, c->stream>>>(prm)));
+  if (part & NTT_ROWS)
+    PROF_LAUNCH(c, PK_NTT_INV_B, units, (inv_pass_b<LH, RB, APPROX><<<gb, threads_b<RB>(), 0, c->stream>>>(prm)));
+  if (part & NTT_COLS)
+    PROF_LAUNCH(c, PK_NTT_INV_A, units, (inv_pass_a<LH, S1, APPROX><<<ga, THREADS, 0, c->stream>>>(prm)));
 }
 
 template <int LH>
-void launch_lh(ckks_ctx *c, const NttParams &prm, int npoly, bool inverse, bool approx) {
+void launch_lh(ckks_ctx *c, const NttParams &prm, int npoly, bool inverse, bool approx, int part) {
   if (inverse) {
     if (c->ntt_rows == 8)
-      approx ? launch_inv<LH, 8, true>(c, prm, npoly) : launch_inv<LH, 8, false>(c, prm, npoly);
+      approx ? launch_inv<LH, 8, true>(c, prm, npoly, part) : launch_inv<LH, 8, false>(c, prm, npoly, part);
     else
-      approx ? launch_inv<LH, 16, true>(c, prm, npoly) : launch_inv<LH, 16, false>(c, prm, npoly);
+      approx ? launch_inv<LH, 16, true>(c, prm, npoly, part) : launch_inv<LH, 16, false>(c, prm, npoly, part);
     return;
   }
   constexpr int S1 = (LH + 1) / 2;
@@ -445,21 +451,238 @@ void launch_lh(ckks_ctx *c, const NttParams &prm, int npoly, bool inverse, bool 
   cudaStream_t st = c->stream;
   const unsigned long long units = (unsigned long long)prm.n_limbs * npoly;
   dim3 ga(BROW / ca_of(LH), prm.n_limbs, npoly);
-  PROF_LAUNCH(c, PK_NTT_FWD_A, units, (fwd_pass_a<LH, S1><<<ga, THREADS, 0, st>>>(prm)));
+  if (part & NTT_COLS) PROF_LAUNCH(c, PK_NTT_FWD_A, units, (fwd_pass_a<LH, S1><<<ga, THREADS, 0, st>>>(prm)));
+  if (!(part & NTT_ROWS)) return;
+  const int from_src = (part & NTT_COLS) ? 0 : 1;
   if (c->ntt_rows == 8) {
     dim3 gb(H / 8, prm.n_limbs, npoly);
-    PROF_LAUNCH(c, PK_NTT_FWD_B, units, (fwd_pass_b<LH, 8><<<gb, threads_b<8>(), 0, st>>>(prm, 0)));
+    PROF_LAUNCH(c, PK_NTT_FWD_B, units, (fwd_pass_b<LH, 8><<<gb, threads_b<8>(), 0, st>>>(prm, from_src)));
   } else {
     dim3 gb(H / 16, prm.n_limbs, npoly);
-    PROF_LAUNCH(c, PK_NTT_FWD_B, units, (fwd_pass_b<LH, 16><<<gb, threads_b<16>(), 0, st>>>(prm, 0)));
+    PROF_LAUNCH(c, PK_NTT_FWD_B, units, (fwd_pass_b<LH, 16><<<gb, threads_b<16>(), 0, st>>>(prm, from_src)));
   }
+}
+
+// ---------------------------------------------------------------- fused conversion column pass
+// The middle of the key-switch pipeline in one kernel (readings C8, C9, C21):
+// a CTA takes one tile of FCA columns x H rows of one polynomial and one digit,
+//   A. runs the inverse transform's column stages on each of the digit's
+//      source limbs (their row stages ran before, NTT_ROWS), with N^-1, and
+//      multiplies by [Bhat_i^-1]_{b_i}: y_i in shared memory;
+//   B. for each target t: y_t = sum_i y_i (Bhat_i mod t) mod t at every
+//      position of the tile (128-bit sums, one reduction), then the forward
+//      transform's column stages, and stores the tile (its row stages run
+//      after, NTT_ROWS).
+// So the digit's coefficient-domain limbs and the conversion's targets never
+// reach HBM: the sources are read once after their row pass, the targets
+// written once before theirs.  The arithmetic per value is the unfused
+// path's (same lazy butterflies per modulus, same conversion), so the limbs
+// are identical.  MERGED adds reading C21's terms: [H]_{s_i} on the sources,
+// the overflow estimate v (32.32 fixed point) times -S mod t, and -[H]_t.
+constexpr int FCA = 4;          // columns per tile: 32-byte row segments
+constexpr int F_THREADS = 256;
+constexpr int F_MAXS = 16;      // sources of one conversion
+constexpr int F_MAXD = 8;       // digits per launch
+// shared-memory word index of (row, column) in a padded tile: four spare words
+// per 16 rows keep the 16-row strided accesses free of bank conflicts
+__host__ __device__ constexpr int fpad(int r, int c) { return FCA * (r + (r >> 4)) + c; }
+__host__ __device__ constexpr int ftile(int lh) { return FCA * ((1 << lh) + ((1 << lh) >> 4)); }
+
+struct FusedArgs {
+  const ModInfo *mods;
+  const ulonglong2 *tw_inv, *tw_fwd;   // [modulus][N]
+  u32 n;
+  // per digit (blockIdx.y): sources = limbs src_off .. +ns of the polynomial's
+  // source buffer (moduli src_mod); targets tt < nt go to limb pos(tt) of the
+  // digit's target buffer (dst_off), pos(tt) = tt below gap_lo and
+  // tt + gap_hi - gap_lo from there (the digit's own limbs are skipped)
+  int ns[F_MAXD], nt[F_MAXD], gap_lo[F_MAXD], gap_hi[F_MAXD];
+  size_t src_off[F_MAXD], dst_off[F_MAXD];
+  unsigned char src_mod[F_MAXD][F_MAXS];
+  unsigned char pos_mod[MAX_MODS];     // modulus of target limb position
+  const u64 *inv[F_MAXD];              // [ns] Shoup pairs: [Bhat_i^-1]_{b_i}
+  const u64 *tab[F_MAXD];              // [nt][ns]: Bhat_i mod t
+  const u64 *src_add, *dst_sub, *rdiv, *negs;  // MERGED: [ns], [nt], [ns], [nt]
+  const u64 *src[MAX_CTS];
+  u64 *dst[MAX_CTS];
+};
+
+template <int LH, bool MERGED>
+__global__ void __launch_bounds__(F_THREADS, 2) k_conv_fused(const FusedArgs a) {
+  constexpr int H = 1 << LH, S1 = (LH + 1) / 2, S2 = LH - S1, T = ftile(LH);
+  constexpr int PER_T = (H >> S1) * FCA;    // threads per target in phase B
+  constexpr int TCON = F_THREADS / PER_T;   // targets in flight
+  static_assert(F_THREADS % PER_T == 0, "phase B groups");
+  extern __shared__ u64 fsm[];
+  const int j = blockIdx.y, p = blockIdx.z;
+  const int ns = a.ns[j], nt = a.nt[j];
+  u64 *sy = fsm;                          // [ns][T]: the sources, then y
+  u64 *sx = sy + (size_t)ns * T;          // [TCON][T]: phase B exchange tiles
+  u64 *stab = sx + (size_t)TCON * T;      // [nt][ns] conversion constants
+  const int c0 = blockIdx.x * FCA;
+  const u64 *src = a.src[p] + a.src_off[j];
+  u64 *dst = a.dst[p] + a.dst_off[j];
+  for (int x = threadIdx.x; x < nt * ns; x += F_THREADS) stab[x] = __ldg(a.tab[j] + x);
+
+  // A.1 inverse column stages S1 .. LH-1 (rows (g << S2) + e), from global
+  for (int x = threadIdx.x; x < ns * (1 << S1) * FCA; x += F_THREADS) {
+    const int i = x / ((1 << S1) * FCA), r = x % ((1 << S1) * FCA);
+    const int c = r % FCA, g = r / FCA;
+    const int mi = a.src_mod[j][i];
+    const u64 q = a.mods[mi].q, twoq = 2 * q;
+    const ulonglong2 *tw = a.tw_inv + (size_t)mi * a.n;
+    const u64 *sl = src + (size_t)i * a.n;
+    u64 v[1 << S2];
+#pragma unroll
+    for (int e = 0; e < (1 << S2); ++e) v[e] = sl[(size_t)((g << S2) + e) * BROW + c0 + c];
+    if (q < APPROX_INV_BOUND)
+      inv_step<S2, true>(v, (1u << S1) + g, tw, q, twoq);
+    else
+      inv_step<S2, false>(v, (1u << S1) + g, tw, q, twoq);
+#pragma unroll
+    for (int e = 0; e < (1 << S2); ++e) sy[i * T + fpad((g << S2) + e, c)] = v[e];
+  }
+  __syncthreads();
+  // A.2 the remaining stages with N^-1, then y = x [Bhat_i^-1]_{b_i} (+ [H]_{b_i})
+  for (int x = threadIdx.x; x < ns * (H >> S1) * FCA; x += F_THREADS) {
+    const int i = x / ((H >> S1) * FCA), r = x % ((H >> S1) * FCA);
+    const int c = r % FCA, r0 = r / FCA;
+    const int mi = a.src_mod[j][i];
+    const ModInfo m = a.mods[mi];
+    const u64 q = m.q, twoq = 2 * q;
+    const bool approx = q < APPROX_INV_BOUND;
+    const ulonglong2 *tw = a.tw_inv + (size_t)mi * a.n;
+    u64 v[1 << S1];
+#pragma unroll
+    for (int e = 0; e < (1 << S1); ++e) v[e] = sy[i * T + fpad(r0 + (e << S2), c)];
+    if (approx)
+      inv_step<S1, true, 1>(v, 1u, tw, q, twoq);
+    else
+      inv_step<S1, false, 1>(v, 1u, tw, q, twoq);
+    const u64 rr = approx ? 2 * twoq : twoq;
+    const ulonglong2 w0 = __ldg(&tw[0]);
+    const u64 iw = __ldg(a.inv[j] + 2 * i), iws = __ldg(a.inv[j] + 2 * i + 1);
+    const u64 add = MERGED ? __ldg(a.src_add + i) : 0;
+    constexpr int HALF = 1 << (S1 - 1);
+#pragma unroll
+    for (int e = 0; e < HALF; ++e) {
+      const u64 xa = v[e], xb = v[e + HALF];
+      u64 ya = shoup(shoup(xa + xb, m.ninv, m.ninv_s, q), iw, iws, q);
+      u64 yb = shoup(shoup(xa + rr - xb, w0.x, w0.y, q), iw, iws, q);
+      if (MERGED) {
+        ya = addmod(ya, add, q);
+        yb = addmod(yb, add, q);
+      }
+      sy[i * T + fpad(r0 + (e << S2), c)] = ya;
+      sy[i * T + fpad(r0 + ((e + HALF) << S2), c)] = yb;
+    }
+  }
+  __syncthreads();
+
+  // B. per target: conversion at the tile's positions, forward column stages
+  const int grp = threadIdx.x / PER_T, lt = threadIdx.x % PER_T;
+  const int gl = a.gap_lo[j], gh = a.gap_hi[j];
+  u64 *xt = sx + grp * T;
+  for (int t0 = 0; t0 < nt; t0 += TCON) {
+    const int tt = t0 + grp;
+    const bool act = tt < nt;
+    const int pos = tt < gl ? tt : tt + (gh - gl);
+    const int mi = act ? a.pos_mod[pos] : 0;
+    const ModInfo m = a.mods[mi];
+    const u64 q = m.q, twoq = 2 * q;
+    const bool loose = q < LOOSE_BOUND;
+    const ulonglong2 *tw = a.tw_fwd + (size_t)mi * a.n;
+    if (act) {
+      const int c = lt % FCA, r0 = lt / FCA;
+      const u64 *crow = stab + tt * ns;
+      const u64 ng = MERGED ? __ldg(a.negs + tt) : 0, ds = MERGED ? __ldg(a.dst_sub + tt) : 0;
+      u64 v[1 << S1];
+      // sources outer, positions inner, in halves: FH independent 128-bit sums
+      // per thread at a time (the other half's results wait in v)
+      constexpr int FH = (1 << S1) > 8 ? 8 : (1 << S1);
+#pragma unroll
+      for (int h = 0; h < (1 << S1); h += FH) {
+        u64 hi[FH], lo[FH], fix[FH];
+#pragma unroll
+        for (int e = 0; e < FH; ++e) hi[e] = lo[e] = fix[e] = 0;
+        for (int i = 0; i < ns; ++i) {
+          const u64 cf = crow[i];
+          const u64 rd = MERGED ? __ldg(a.rdiv + i) : 0;
+          const u64 *yi = sy + i * T;
+#pragma unroll
+          for (int e = 0; e < FH; ++e) {
+            const u64 y = yi[fpad(r0 + ((h + e) << S2), c)];
+            mac128(hi[e], lo[e], y, cf);
+            if (MERGED) fix[e] += __umul64hi(y, rd);
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < FH; ++e) {
+          if (MERGED) mac128(hi[e], lo[e], fix[e] >> 32, ng);
+          u64 r = reduce128(hi[e], lo[e], m);
+          if (MERGED) r = submod(r, ds, q);
+          v[h + e] = r;
+        }
+      }
+      if (loose)
+        fwd_step<S1, true>(v, 1u, tw, q, twoq);
+      else
+        fwd_step<S1, false>(v, 1u, tw, q, twoq);
+#pragma unroll
+      for (int e = 0; e < (1 << S1); ++e) xt[fpad(r0 + (e << S2), c)] = v[e];
+    }
+    __syncthreads();
+    if (act) {
+      u64 *dl = dst + (size_t)pos * a.n;
+      for (int x = lt; x < (1 << S1) * FCA; x += PER_T) {
+        const int c = x % FCA, g = x / FCA;
+        u64 v[1 << S2];
+#pragma unroll
+        for (int e = 0; e < (1 << S2); ++e) v[e] = xt[fpad((g << S2) + e, c)];
+        if (loose)
+          fwd_step<S2, true>(v, (1u << S1) + g, tw, q, twoq);
+        else
+          fwd_step<S2, false>(v, (1u << S1) + g, tw, q, twoq);
+#pragma unroll
+        for (int e = 0; e < (1 << S2); ++e) dl[(size_t)((g << S2) + e) * BROW + c0 + c] = v[e];
+      }
+    }
+    __syncthreads();  // xt is rewritten by the next target
+  }
+}
+
+template <int LH>
+int launch_fused_lh(ckks_ctx *c, const FusedArgs &a, int ndig, int np, size_t smem, bool merged) {
+  dim3 g(BROW / FCA, ndig, np);
+  u64 pairs = 0, srcs = 0, dsts = 0, strict = 0;
+  for (int j = 0; j < ndig; ++j) {
+    pairs += (u64)a.ns[j] * a.nt[j];
+    srcs += (u64)a.ns[j];
+    dsts += (u64)a.nt[j];
+    for (int tt = 0; tt < a.nt[j]; ++tt) {
+      const int pos = tt < a.gap_lo[j] ? tt : tt + (a.gap_hi[j] - a.gap_lo[j]);
+      strict += c->mod[a.pos_mod[pos]] >= LOOSE_BOUND ? 1 : 0;
+    }
+  }
+  c->prof.count(PK_FUSED_SRC_LIMBS, srcs * np);
+  c->prof.count(PK_FUSED_DST_LIMBS, dsts * np);
+  c->prof.count(PK_FUSED_DST_STRICT, strict * np);
+  if (merged) {
+    CK_CUDA(cudaFuncSetAttribute(k_conv_fused<LH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PROF_LAUNCH(c, PK_CONV_FUSED, pairs * np, (k_conv_fused<LH, true><<<g, F_THREADS, smem, c->stream>>>(a)));
+  } else {
+    CK_CUDA(cudaFuncSetAttribute(k_conv_fused<LH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PROF_LAUNCH(c, PK_CONV_FUSED, pairs * np, (k_conv_fused<LH, false><<<g, F_THREADS, smem, c->stream>>>(a)));
+  }
+  return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_CUDA;
 }
 
 }  // namespace
 
-int launch_ntt(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, int nl, const int *mods,
-               bool inverse) {
+int launch_ntt_part(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, int nl, const int *mods,
+                    bool inverse, int part) {
   if (npoly <= 0 || nl <= 0) return CKKS_OK;
+  if (part != NTT_BOTH && part != NTT_ROWS) return CKKS_E_PARAM;
   if (nl > MAX_MODS) return CKKS_E_PARAM;
   NttParams prm;
   prm.mods = c->d_mods;
@@ -475,7 +698,7 @@ int launch_ntt(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, i
     strict += c->mod[mods[l]] >= LOOSE_BOUND ? 1 : 0;
   }
   if (inverse && !approx) c->prof.count(PK_NTT_INV_EXACT, (unsigned long long)nl * npoly);
-  if (!inverse) c->prof.count(PK_NTT_FWD_STRICT, (unsigned long long)strict * npoly);
+  if (!inverse && (part & NTT_COLS)) c->prof.count(PK_NTT_FWD_STRICT, (unsigned long long)strict * npoly);
   for (int i = 0; i < npoly; ++i)  // the row passes move 16-byte words
     if (((uintptr_t)src[i] | (uintptr_t)dst[i]) & 15) return CKKS_E_PARAM;
   for (int p0 = 0; p0 < npoly; p0 += MAX_POLYS) {
@@ -485,16 +708,73 @@ int launch_ntt(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, i
       prm.dst.p[i] = dst[p0 + i];
     }
     switch (c->log_n - LB) {
-      case 2: launch_lh<2>(c, prm, cnt, inverse, approx); break;
-      case 3: launch_lh<3>(c, prm, cnt, inverse, approx); break;
-      case 4: launch_lh<4>(c, prm, cnt, inverse, approx); break;
-      case 5: launch_lh<5>(c, prm, cnt, inverse, approx); break;
-      case 6: launch_lh<6>(c, prm, cnt, inverse, approx); break;
-      case 7: launch_lh<7>(c, prm, cnt, inverse, approx); break;
-      case 8: launch_lh<8>(c, prm, cnt, inverse, approx); break;
-      case 9: launch_lh<9>(c, prm, cnt, inverse, approx); break;
+      case 2: launch_lh<2>(c, prm, cnt, inverse, approx, part); break;
+      case 3: launch_lh<3>(c, prm, cnt, inverse, approx, part); break;
+      case 4: launch_lh<4>(c, prm, cnt, inverse, approx, part); break;
+      case 5: launch_lh<5>(c, prm, cnt, inverse, approx, part); break;
+      case 6: launch_lh<6>(c, prm, cnt, inverse, approx, part); break;
+      case 7: launch_lh<7>(c, prm, cnt, inverse, approx, part); break;
+      case 8: launch_lh<8>(c, prm, cnt, inverse, approx, part); break;
+      case 9: launch_lh<9>(c, prm, cnt, inverse, approx, part); break;
       default: return CKKS_E_PARAM;
     }
   }
   return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_CUDA;
+}
+
+int launch_ntt(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, int nl, const int *mods,
+               bool inverse) {
+  return launch_ntt_part(c, src, dst, npoly, nl, mods, inverse, NTT_BOTH);
+}
+
+// Host side of the fused column pass (see k_conv_fused).  Rings of 2^12..2^16
+// (the 2^17 ring's pass A runs three register phases and is not fused).
+bool conv_fused_supported(const ckks_ctx *c) { return c->log_n >= 12 && c->log_n <= 16; }
+
+int launch_conv_fused(ckks_ctx *c, const FusedConv &f, const u64 *const *src, u64 *const *dst, int np) {
+  if (!conv_fused_supported(c) || f.ndig < 1 || f.ndig > F_MAXD || np < 1 || np > MAX_CTS) return CKKS_E_PARAM;
+  FusedArgs a;
+  a.mods = c->d_mods;
+  a.tw_inv = c->d_tw_inv;
+  a.tw_fwd = c->d_tw_fwd;
+  a.n = c->n;
+  int max_ns = 0, max_tab = 0;
+  for (int j = 0; j < f.ndig; ++j) {
+    const FusedConv::Digit &d = f.dig[j];
+    if (d.ns < 1 || d.ns > F_MAXS || d.nt < 1 || d.nt > MAX_MODS) return CKKS_E_PARAM;
+    a.ns[j] = d.ns;
+    a.nt[j] = d.nt;
+    a.gap_lo[j] = d.gap_lo;
+    a.gap_hi[j] = d.gap_hi;
+    a.src_off[j] = d.src_off;
+    a.dst_off[j] = d.dst_off;
+    for (int i = 0; i < d.ns; ++i) a.src_mod[j][i] = (unsigned char)d.src_mod[i];
+    a.inv[j] = d.inv;
+    a.tab[j] = d.tab;
+    max_ns = std::max(max_ns, d.ns);
+    max_tab = std::max(max_tab, d.ns * d.nt);
+  }
+  for (int t = 0; t < MAX_MODS; ++t) a.pos_mod[t] = (unsigned char)f.pos_mod[t];
+  a.src_add = f.src_add;
+  a.dst_sub = f.dst_sub;
+  a.rdiv = f.rdiv;
+  a.negs = f.negs;
+  const bool merged = f.src_add != nullptr;
+  if (merged && f.ndig != 1) return CKKS_E_PARAM;
+  for (int i = 0; i < np; ++i) {
+    a.src[i] = src[i];
+    a.dst[i] = dst[i];
+  }
+  const int lh = c->log_n - LB;
+  const int per_t = ((1 << lh) >> ((lh + 1) / 2)) * FCA;
+  const size_t smem = sizeof(u64) * ((size_t)(max_ns + F_THREADS / per_t) * ftile(lh) + max_tab);
+  if (smem > 227 * 1024) return CKKS_E_PARAM;
+  switch (lh) {
+    case 4: return launch_fused_lh<4>(c, a, f.ndig, np, smem, merged);
+    case 5: return launch_fused_lh<5>(c, a, f.ndig, np, smem, merged);
+    case 6: return launch_fused_lh<6>(c, a, f.ndig, np, smem, merged);
+    case 7: return launch_fused_lh<7>(c, a, f.ndig, np, smem, merged);
+    case 8: return launch_fused_lh<8>(c, a, f.ndig, np, smem, merged);
+    default: return CKKS_E_PARAM;
+  }
 }

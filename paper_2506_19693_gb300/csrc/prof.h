@@ -23,11 +23,18 @@ enum ProfKind {
   PK_BCONV_TC,
   PK_BOOT_MAC,        // units: limbs of N words moved (algorithmic)
   PK_BOOT_LINCOMB,    // units: limbs of N words moved (algorithmic)
+  PK_CONV_FUSED,      // units: source-target limb pairs of one polynomial (as the conversions)
   // counting-only classes (no launches, no time): limbs of the forward NTT
   // passes whose prime takes the strict butterfly (65 q >= 2^64), and limbs of
   // inverse passes launched with the exact quotient (a prime >= 2^61)
   PK_NTT_FWD_STRICT,
   PK_NTT_INV_EXACT,
+  // counting-only: limbs through the fused conversion's inverse column stages
+  // (sources), its forward column stages (targets), and the strict-butterfly
+  // targets among them
+  PK_FUSED_SRC_LIMBS,
+  PK_FUSED_DST_LIMBS,
+  PK_FUSED_DST_STRICT,
   PK_COUNT
 };
 constexpr int PROF_MAX_LEVEL = 64;

@@ -52,7 +52,7 @@ def test_gpu_constants_match_oracle_constants(small):
     assert np.max(np.abs(cheb - plan.cheb)) < 1e-13
 
 
-@pytest.mark.parametrize("tensor_form", [False, True], ids=["uint64", "tensor"])
+@pytest.mark.parametrize("tensor_form", ["uint64", "tensor", "fused"])
 def test_bootstrap_bit_exact_with_oracle_constants(small, tensor_form):
     import oracle.bootstrap as ob
     w, ctx, orc, plan, consts = small
@@ -111,7 +111,7 @@ def test_bootstrap_error_bound_full_ring():
         ctx.close()
 
 
-@pytest.mark.parametrize("tensor_form", [False, True], ids=["uint64", "tensor"])
+@pytest.mark.parametrize("tensor_form", ["uint64", "tensor", "fused"])
 def test_iterative_bootstrap_bit_exact_with_oracle_constants(small, tensor_form):
     """Reading B12 on the GPU: every limb of the two-pass result equals the
     oracle's, with the oracle's constants imported."""

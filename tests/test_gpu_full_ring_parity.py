@@ -114,7 +114,7 @@ def boot_pair():
     ctx.close()
 
 
-@pytest.mark.parametrize("tensor_form", [False, True], ids=["uint64", "tensor"])
+@pytest.mark.parametrize("tensor_form", ["uint64", "tensor", "fused"])
 def test_evalmod_level_products_bit_exact_at_full_ring(boot_pair, tensor_form):
     """B9: the relinearised product with ModDown and rescale merged, at two of
     EvalMod's levels of the bootstrapping chain (nine special primes)."""
@@ -149,8 +149,8 @@ def level_consts(boot_pair):
 @pytest.mark.parametrize("index", [0, 3], ids=["coeff_to_slot_0", "slot_to_coeff_0"])
 def test_linear_level_bit_exact_at_full_ring(boot_pair, level_consts, index):
     """One merged level of the special DFT (B3, B10, B11) at N = 2^16 with the
-    oracle's constants: every output limb equals the oracle's level, in both
-    basis-conversion forms."""
+    oracle's constants: every output limb equals the oracle's level, in all
+    three basis-conversion forms."""
     import oracle.bootstrap as ob
     w, ctx, orc, plan = boot_pair
     levels = plan.cts + plan.stc
@@ -163,7 +163,7 @@ def test_linear_level_bit_exact_at_full_ring(boot_pair, level_consts, index):
     co = orc.encrypt(orc.pt_from_int(m, lv.level), lv.level, scale, 7700 + index)
     cg = ctx.encrypt(ctx.pt_from_int(m, lv.level), lv.level, scale, 7700 + index)
     want = ev.linear(co, lv, ev.pts[index])
-    for tensor_form in (False, True):
+    for tensor_form in ("uint64", "tensor", "fused"):
         ctx.set_form(tensor_form)
         try:
             got = ctx.boot_linear(index, [cg])[0]

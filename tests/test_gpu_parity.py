@@ -125,7 +125,7 @@ def test_mul_relin_and_rescale_bit_exact(pair):
     _same(ctx, pg2, po2)
 
 
-@pytest.mark.parametrize("tensor_form", [False, True], ids=["uint64", "tensor"])
+@pytest.mark.parametrize("tensor_form", ["uint64", "tensor", "fused"])
 def test_merged_moddown_rescale_bit_exact(pair, tensor_form):
     """Reading C21 (ModDown and rescale in one conversion) against the oracle,
     at the top level and again one level down (partial top digit)."""

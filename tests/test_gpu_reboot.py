@@ -19,7 +19,7 @@ def _data(seed, b, k0, k1, o, x_hi=1.0):
     return x, y, w, ws
 
 
-@pytest.mark.parametrize("tensor_form", [False, True], ids=["uint64", "tensor"])
+@pytest.mark.parametrize("tensor_form", ["uint64", "tensor", "fused"])
 def test_reboot_step_bit_exact_small_ring(tensor_form):
     import torch
     import oracle
@@ -110,7 +110,7 @@ def test_reboot_step_config3_size_with_bootstrap():
         ctx.close()
 
 
-@pytest.mark.parametrize("tensor_form", [False, True], ids=["uint64", "tensor"])
+@pytest.mark.parametrize("tensor_form", ["uint64", "tensor", "fused"])
 def test_ce_block_step_bit_exact_small_ring(tensor_form):
     """Reading R6: the CE-Block step (inputs at level 9 as a RE-Block leaves
     them, weights at level 11) equals the oracle's limb for limb."""
