@@ -649,6 +649,10 @@ def run_gpu(args):
                             hbm_peak=hbm)
         ctx.set_form(args.form)
 
+    tc_ntt = None
+    if not (args.no_tc_ntt or args.small):
+        tc_ntt = run_tc_ntt_prototype(ctx, w, torch, stream, reps=max(2, min(args.steps, 3)))
+
     # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
     if not (args.no_e2e or args.small):
@@ -688,6 +692,7 @@ def run_gpu(args):
                 "n_scaling": n_scaling,
                 "key_compression": key_compression,
                 "sparse_slot_bootstrap": sparse_boot,
+                "tensor_ntt_stage_prototype": tc_ntt,
                 "tuning": tuning,
                 "e2e": e2e, "roofline": roof, "op_rooflines": op_roofs, "alu_peaks": alu, "cpu_baseline": cpu,
                 "clocks": clk,
@@ -814,6 +819,57 @@ def run_uneven(ctx16, w, torch, stream, rank, reps, warmup, dnums=(3, 2), hbm_pe
                            "switching key once (dnum 3)",
             "ops": "256: 1/3 HMult+relin+rescale, 1/3 Rot(2^k), 1/3 rescale; N in {2^15, 2^16} p=1/2; "
                    "limbs U{4..24} (level index 3..23)", "replays": reps, "tuned": tuned}
+
+
+def run_tc_ntt_prototype(ctx, w, torch, stream, reps, n_polys=64):
+    """The tensor-core NTT stage group (ckks_ntt_tc: the first four column
+    stages as a byte-split tcgen05 GEMM) against the uint64 transform on the
+    same 64 polynomials x 24 limbs; the profiler splits the prototype's time
+    into the tensor-core stage group and the CUDA-core stages after it."""
+    import paper_2506_19693_gb300 as ck
+    L = len(w.q_bits)
+    n = ctx.n
+    g = torch.Generator(device=ctx.device)
+    g.manual_seed(5)
+    data = torch.empty((n_polys, L, n), dtype=torch.int64, device=ctx.device)
+    for t in range(L):
+        data[:, t] = torch.randint(0, int(ctx.q[t]), (n_polys, n), device=ctx.device, generator=g)
+    a = data.clone()
+    b = data.clone()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    ctx.ntt_tc(a, n_polys, L)  # warm-up (builds the byte-plane matrices)
+    for p in range(n_polys):
+        ctx.ntt(b[p], 0)
+    torch.cuda.synchronize()
+    same = bool(torch.equal(a, b))
+    e0, e1, e2 = ev(), ev(), ev()
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.ntt_tc(a, n_polys, L)
+    e1.record(stream)
+    for _ in range(reps):
+        for p in range(n_polys):
+            ctx.ntt(b[p], 0)
+    e2.record(stream)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ctx.ntt_tc(a, n_polys, L)
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    stage_ms = prof.get("bconv_tc", (0.0, 0, 0))[0]
+    rest_ms = prof.get("ntt_fwd_pass_a", (0.0, 0, 0))[0] + prof.get("ntt_fwd_pass_b", (0.0, 0, 0))[0]
+    limbs = n_polys * L
+    # the stage group: a 16 x 16 product per 16-point block = 16 MACs per value,
+    # as byte-split fp16 MMAs: 8 x 8 byte products each, 2 flops each
+    tc_flops = limbs * n * 16 * 64 * 2
+    return {"limbs": limbs, "bit_exact_vs_uint64": same,
+            "ms_tensor_stage_ntt": e0.elapsed_time(e1) / reps, "ms_uint64_ntt": e1.elapsed_time(e2) / reps,
+            "stage_group_ms": stage_ms, "remaining_stages_ms": rest_ms,
+            "stage_group_us_per_limb": 1e3 * stage_ms / limbs,
+            "stage_group_tensor_tflops": tc_flops / (stage_ms / 1e3) / 1e12 if stage_ms else None,
+            "note": "uint64 NTT launched per polynomial (24 limbs per launch); the four stages the prototype moves "
+                    "to the tensor cores are half of the uint64 column pass"}
 
 
 def run_n_scaling(torch, stream, reps):
@@ -1199,6 +1255,7 @@ def main():
     ap.add_argument("--no-sparse-boot", action="store_true")
     ap.add_argument("--no-n-scaling", action="store_true")
     ap.add_argument("--no-form-compare", action="store_true")
+    ap.add_argument("--no-tc-ntt", action="store_true")
     ap.add_argument("--form", default="tensor", choices=["uint64", "tensor", "fused"],
                     help="basis conversion on the CUDA cores (uint64), on the tensor cores (tensor), or on the "
                          "CUDA cores fused with the transforms' column passes (fused)")

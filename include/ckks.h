@@ -210,6 +210,16 @@ int ckks_pt_from_int(ckks_ctx *ctx, const int64_t *m_host, uint32_t level, uint6
  * at data_dev; limb l uses modulus index first_mod + l (0..n_q-1 are q_i,
  * n_q.. are p_j).  Residues in [0, modulus) in and out. */
 int ckks_ntt(ckks_ctx *ctx, uint64_t *data_dev, uint32_t n_limbs, uint32_t first_mod, int inverse);
+/* Forward NTT of n_polys (1..128) polynomials stored back to back
+ * (uint64[n_polys][n_limbs][N], limb t under modulus t), in place, with the
+ * first four column stages on the tensor cores (no paper counterpart: the
+ * byte-split tensor-core form of an NTT stage group, measured against the
+ * butterflies).  Those stages map every 16-point block by one 16 x 16 matrix
+ * over Z_q, applied to the limb's 16-row slabs as an exact byte-split fp16
+ * GEMM on tcgen05 with fp32 accumulation and modular recombination; the other
+ * twelve stages run as in ckks_ntt.  Same residues as ckks_ntt.  N = 2^15 or
+ * 2^16 (else CKKS_E_PARAM); uses the context scratch (n_polys N words). */
+int ckks_ntt_tc(ckks_ctx *ctx, uint64_t *data_dev, uint32_t n_polys, uint32_t n_limbs);
 
 /* ---- encryption (Sec. 3, reading C5) ------------------------------------ */
 

@@ -123,6 +123,7 @@ SIGNATURES = {
     "ckks_ctx_set_ntt_rows": (_I, [_V, _I]),
     "ckks_tune_dnum": (_I, [_V, _V, ctypes.POINTER(ctypes.c_uint32), _I, _I, ctypes.c_uint64,
                             ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_double)]),
+    "ckks_ntt_tc": (_I, [_V, _V, ctypes.c_uint32, ctypes.c_uint32]),
     "ckks_ct_alloc": (_I, [_V, ctypes.c_uint32, _CTP]),
     "ckks_ct_free": (_I, [_V, _CTP]),
     "ckks_ct_export": (_I, [_V, _CTP, _V]),
@@ -363,6 +364,11 @@ class Context:
                "ckks_ntt")
 
     # ---- encryption ----
+    def ntt_tc(self, data, n_polys: int, n_limbs: int) -> None:
+        """Forward NTT with the first four stages on the tensor cores (ckks_ntt_tc):
+        data is a device tensor of n_polys x n_limbs limbs, limb t under modulus t."""
+        _check(self.lib.ckks_ntt_tc(self._h, data.data_ptr(), n_polys, n_limbs), "ckks_ntt_tc")
+
     def encrypt(self, pt, level: int, scale: float, enc_seed: int, n_limbs: int | None = None) -> Ciphertext:
         ct = self.new_ct(n_limbs or level + 1, level, scale)
         h = ct.handle(self.log_n)

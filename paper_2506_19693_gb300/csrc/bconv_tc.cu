@@ -403,9 +403,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_bconv_tc(const TcArgs a) {
 static int launch_bconv_tc_ex(ckks_ctx *c, size_t key, const u64 *inv_host, const u64 *tab_host, int ns, int nt,
                               const int *src_mod, const int *dst_mod, const int *dst_pos, const u64 *const *src,
                               u64 *const *dst, int np, const u64 *src_add_host, const u64 *dst_sub_host,
-                              const u64 *rdiv_host, const u64 *negs_host, u64 wait_ns, int test_expire) {
+                              const u64 *rdiv_host, const u64 *negs_host, u64 wait_ns, int test_expire,
+                              u32 n_virt) {
   if (ns < 1 || ns > TC_MAX_S || nt < 1 || nt > TC_MAX_T || np < 1 || np > MAX_CTS) return CKKS_E_PARAM;
-  if (c->n % TC_M) return CKKS_E_PARAM;
+  if (n_virt % TC_M || n_virt == 0) return CKKS_E_PARAM;
   const bool has_v = rdiv_host && negs_host;
   if (has_v && ns == TC_MAX_S) return CKKS_E_PARAM;  // the overflow column needs K <= 8 ns + 1 <= 128
   const int kpad = ((8 * ns + (has_v ? 1 : 0) + 15) / 16) * 16, npad = ((8 * nt + 15) / 16) * 16;
@@ -439,7 +440,7 @@ static int launch_bconv_tc_ex(ckks_ctx *c, size_t key, const u64 *inv_host, cons
     it = c->tc_bmats.emplace(key, d).first;
   }
   TcArgs a;
-  a.n = c->n;
+  a.n = n_virt;
   a.ns = ns;
   a.nt = nt;
   a.kpad = kpad;
@@ -483,7 +484,7 @@ static int launch_bconv_tc_ex(ckks_ctx *c, size_t key, const u64 *inv_host, cons
   CK_CUDA(cudaFuncSetAttribute(k_bconv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  const int total = (int)(c->n / TC_M) * np;
+  const int total = (int)(n_virt / TC_M) * np;
   const int grid = std::min(total, sms);
   PROF_LAUNCH(c, PK_BCONV_TC, (u64)np * nt * ns, (k_bconv_tc<<<grid, TC_THREADS, smem, c->stream>>>(a)));
   return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_CUDA;
@@ -494,7 +495,7 @@ int launch_bconv_tc(ckks_ctx *c, size_t key, const u64 *inv_host, const u64 *tab
                     u64 *const *dst, int np, const u64 *src_add_host, const u64 *dst_sub_host,
                     const u64 *rdiv_host, const u64 *negs_host) {
   return launch_bconv_tc_ex(c, key, inv_host, tab_host, ns, nt, src_mod, dst_mod, dst_pos, src, dst, np,
-                            src_add_host, dst_sub_host, rdiv_host, negs_host, TC_WAIT_NS, 0);
+                            src_add_host, dst_sub_host, rdiv_host, negs_host, TC_WAIT_NS, 0, c->n);
 }
 
 // TEST ONLY (ckks_debug_tc_expire): one launch of the conversion kernel on a
@@ -514,5 +515,15 @@ extern "C" int ckks_debug_tc_expire(ckks_ctx *c, uint64_t wait_ns) {
   const u64 *src[1] = {c->scratch};
   u64 *dst[1] = {c->scratch + c->n};
   return launch_bconv_tc_ex(c, ~(size_t)0, inv, tab, 1, 1, sm, dm, dp, src, dst, 1, nullptr, nullptr, nullptr,
-                            nullptr, wait_ns, 1);
+                            nullptr, wait_ns, 1, c->n);
+}
+
+// The same exact byte-split product on a strided view: `n_virt` coefficients
+// per source and per target, source i at src + i n_virt (the tensor-core NTT
+// stage prototype views a limb's 16-row blocks as 16 sources).
+int launch_bconv_tc_view(ckks_ctx *c, size_t key, const u64 *inv_host, const u64 *tab_host, int ns, int nt,
+                         const int *src_mod, const int *dst_mod, const int *dst_pos, const u64 *const *src,
+                         u64 *const *dst, int np, u32 n_virt) {
+  return launch_bconv_tc_ex(c, key, inv_host, tab_host, ns, nt, src_mod, dst_mod, dst_pos, src, dst, np, nullptr,
+                            nullptr, nullptr, nullptr, TC_WAIT_NS, 0, n_virt);
 }

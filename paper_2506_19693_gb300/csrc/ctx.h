@@ -198,6 +198,11 @@ int launch_bconv_tc(ckks_ctx *c, size_t key, const u64 *inv_host, const u64 *tab
                     u64 *const *dst, int np, const u64 *src_add_host, const u64 *dst_sub_host,
                     const u64 *rdiv_host, const u64 *negs_host);
 
+// the same on a strided view of n_virt coefficients per source / target limb
+int launch_bconv_tc_view(ckks_ctx *c, size_t key, const u64 *inv_host, const u64 *tab_host, int ns, int nt,
+                         const int *src_mod, const int *dst_mod, const int *dst_pos, const u64 *const *src,
+                         u64 *const *dst, int np, u32 n_virt);
+
 // ---- batched ciphertext operations (capi.cu); n <= 128, all at one level ----
 int rescale_chunk(ckks_ctx *c, ckks_ct *cts, int n);
 // merged: ModDown and rescale in one step (reading C21), output at level - 1

@@ -40,6 +40,7 @@ struct NttParams {
   const ulonglong2 *tw_row;      // [modulus][15 N / 16]: the row pass's second phase, regrouped
   u32 n;
   int n_limbs;
+  int skip_first;                // pass A: the first S1 column stages ran elsewhere
   unsigned char mod_of_limb[MAX_MODS];
   CPolyPtrs src;
   PolyPtrs dst;
@@ -138,7 +139,7 @@ __device__ __forceinline__ void fwd_a_body(const NttParams &prm, u64 *sm, int mi
     u64 v[1 << S1];
 #pragma unroll
     for (int e = 0; e < (1 << S1); ++e) v[e] = src[(size_t)(r0 + (e << S2)) * BROW + c0 + c];
-    fwd_step<S1, LOOSE>(v, 1u, tw, q, twoq);
+    if (!prm.skip_first) fwd_step<S1, LOOSE>(v, 1u, tw, q, twoq);
 #pragma unroll
     for (int e = 0; e < (1 << S1); ++e) sm[(r0 + (e << S2)) * CA + c] = v[e];
   }
@@ -685,6 +686,7 @@ int launch_ntt_part(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npo
   if (part != NTT_BOTH && part != NTT_ROWS) return CKKS_E_PARAM;
   if (nl > MAX_MODS) return CKKS_E_PARAM;
   NttParams prm;
+  prm.skip_first = 0;
   prm.mods = c->d_mods;
   prm.tw = inverse ? c->d_tw_inv : c->d_tw_fwd;
   prm.tw_row = inverse ? c->d_tw_row_inv : c->d_tw_row_fwd;
@@ -777,4 +779,80 @@ int launch_conv_fused(ckks_ctx *c, const FusedConv &f, const u64 *const *src, u6
     case 8: return launch_fused_lh<8>(c, a, f.ndig, np, smem, merged);
     default: return CKKS_E_PARAM;
   }
+}
+
+// ---------------------------------------------------------------- tensor-core NTT stage prototype
+// The forward transform's first S1 = 4 column stages act on 16-point blocks
+// (rows r0 + 16 e of one column) with the same twiddles for every block: the
+// block transform is one 16 x 16 matrix M over Z_q, and applying it to a limb
+// is the product M V with V the limb's 16-row slabs as 16 "sources" of N/16
+// coefficients.  That product runs as the exact byte-split GEMM of the
+// tensor-core conversion (fp16 bytes, fp32 accumulation in tensor memory,
+// modular recombination, fully reduced residues); the remaining 12 stages run
+// on the CUDA cores.  The result equals launch_ntt's bit for bit.
+static void stage_matrix(const ckks_ctx *c, int mi, u64 *M) {  // M[16][16], row = output
+  const u64 q = c->mod[mi];
+  for (int j = 0; j < 16; ++j) {
+    u64 v[16] = {0};
+    v[j] = 1;
+    for (int st = 0; st < 4; ++st) {  // Cooley-Tukey stages of the block, group mg = 1
+      const int half = 8 >> st;
+      for (int e = 0; e < 16; ++e) {
+        if (e & half) continue;
+        const u64 idx = (1u << st) + (u64)(e >> (4 - st));
+        const u64 w = host_powmod(c->psi[mi], host_bitrev(idx, c->log_n), q);
+        const u64 t = host_mulmod(w, v[e + half], q);
+        const u64 a = v[e];
+        v[e] = (a + t) % q;
+        v[e + half] = (a + q - t) % q;
+      }
+    }
+    for (int k = 0; k < 16; ++k) M[k * 16 + j] = v[k];
+  }
+}
+
+extern "C" int ckks_ntt_tc(ckks_ctx *c, uint64_t *data, uint32_t n_polys, uint32_t n_limbs) {
+  if (!c || !data || n_polys < 1 || n_polys > MAX_CTS || n_limbs < 1 || (int)n_limbs > c->n_q + c->n_p)
+    return CKKS_E_PARAM;
+  const int lh = c->log_n - LB;
+  if (lh != 7 && lh != 8) return CKKS_E_PARAM;  // 16-point first phase: N = 2^15, 2^16
+  if (c->capturing) return CKKS_E_STATE;
+  const u32 n = c->n, nv = n / 16;
+  int rc = ensure_scratch(c, (size_t)n_polys * n);
+  if (rc) return rc;
+  for (u32 t = 0; t < n_limbs; ++t) {
+    const int mi = (int)t;
+    u64 M[256], inv[32];
+    stage_matrix(c, mi, M);
+    for (int i = 0; i < 16; ++i) inv[2 * i] = 1, inv[2 * i + 1] = host_shoup(1, c->mod[mi]);
+    int sm[16], dm[16], dp[16];
+    for (int i = 0; i < 16; ++i) sm[i] = mi, dm[i] = mi, dp[i] = i;
+    std::vector<const u64 *> src(n_polys);
+    std::vector<u64 *> dst(n_polys);
+    for (u32 p = 0; p < n_polys; ++p) {
+      src[p] = data + ((size_t)p * n_limbs + t) * n;
+      dst[p] = c->scratch + (size_t)p * n;
+    }
+    rc = launch_bconv_tc_view(c, ((size_t)1 << 62) | (size_t)mi, inv, M, 16, 16, sm, dm, dp, src.data(), dst.data(),
+                              (int)n_polys, nv);
+    if (rc) return rc;
+    NttParams prm;
+    prm.skip_first = 1;
+    prm.mods = c->d_mods;
+    prm.tw = c->d_tw_fwd;
+    prm.tw_row = c->d_tw_row_fwd;
+    prm.n = n;
+    prm.n_limbs = 1;
+    prm.mod_of_limb[0] = (unsigned char)mi;
+    for (u32 p = 0; p < n_polys; ++p) {
+      prm.src.p[p] = dst[p];
+      prm.dst.p[p] = const_cast<u64 *>(src[p]);
+    }
+    if (lh == 8)
+      launch_lh<8>(c, prm, (int)n_polys, false, true, NTT_BOTH);
+    else
+      launch_lh<7>(c, prm, (int)n_polys, false, true, NTT_BOTH);
+    if (cudaGetLastError() != cudaSuccess) return CKKS_E_CUDA;
+  }
+  return CKKS_OK;
 }
