@@ -1173,7 +1173,7 @@ def run_e2e(ctx, torch, A, Bc, OUT, level, args, dist):
     region.  Two wire formats: plain uint64 limbs (ckks_mul_relin_host, the
     headline `e2e`) and limbs packed at their primes' bit widths
     (ckks_mul_relin_host_packed).  The chunk size of each is the fastest of two
-    untimed passes at each of 8, 16, 32; the JSON keeps those passes and the
+    untimed passes at each of 4, 8, 16, 32; the JSON keeps those passes and the
     timed steps one by one."""
     import paper_2506_19693_gb300 as ck
     n = ctx.n
@@ -1185,7 +1185,7 @@ def run_e2e(ctx, torch, A, Bc, OUT, level, args, dist):
 
     def measure(once):
         best, best_t, sel = 16, None, {}
-        for chunk in (8, 16, 32):
+        for chunk in (4, 8, 16, 32):
             once(chunk)  # staging allocated outside the timing
             for _ in range(2):  # the faster of two passes per candidate
                 torch.cuda.synchronize()
