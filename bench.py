@@ -674,6 +674,21 @@ def run_gpu(args):
                "rotations_per_s": 1.0 / dr,
                "rotation_sample": "1 rotation by 1 slot of 1 ciphertext at N=2^16, L=24 (key generated untimed)"}
 
+    # the metric's op-level fractions and the other half of the metric (bootstraps/s),
+    # per form, as flat scalars of the roofline object
+    if roof is not None:
+        for k, v in op_roofs.items():
+            roof[f"op_{k}_per_s"] = v["ops_per_s"]
+            roof[f"op_{k}_frac"] = v["frac"]
+            roof[f"op_{k}_bound"] = v["bound"]
+            roof[f"op_{k}_hbm_frac"] = v["hbm"]["frac"]
+            roof[f"op_{k}_compute_frac"] = v["compute"]["frac"]
+        roof["bootstraps_per_s"] = boot_rate
+        for f, r in forms.items():
+            roof[f"form_{f}_hmult_per_s"] = r["hmult_per_s"]
+            roof[f"form_{f}_bootstraps_per_s"] = r["bootstraps_per_s"]
+            roof[f"form_{f}_rotations_per_s"] = r["rotations_per_s"]
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",

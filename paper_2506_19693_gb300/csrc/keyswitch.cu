@@ -56,10 +56,18 @@ struct BConvArgs {
   const u64 *negs = nullptr;       // [nt] -B mod t
 };
 
+// The conversion constants ([nt][NS] words, at most 40 x 16) are staged in
+// shared memory once per CTA, and the targets are taken in pairs, so that two
+// independent 128-bit sums (and their constant loads) are in flight per thread.
+constexpr int BCONV_MAX_TAB = MAX_MODS * 16;
+
 template <int NS>
 __global__ void __launch_bounds__(TPB) k_bconv(const BConvArgs a) {
+  __shared__ u64 stab[BCONV_MAX_TAB];
   const u32 k = blockIdx.x * TPB + threadIdx.x;
   const int p = blockIdx.y;
+  for (int x = threadIdx.x; x < a.nt * NS; x += TPB) stab[x] = __ldg(a.tab + x);
+  __syncthreads();
   if (k >= a.n) return;
   const u64 *src = a.src[p];
   u64 y[NS];
@@ -73,16 +81,29 @@ __global__ void __launch_bounds__(TPB) k_bconv(const BConvArgs a) {
   }
   const u64 v = fix >> 32;
   u64 *dst = a.dst[p];
-  for (int t = 0; t < a.nt; ++t) {
-    const u64 *row = a.tab + (size_t)t * NS;
-    u64 hi = 0, lo = 0;
+  for (int t = 0; t < a.nt; t += 2) {
+    const bool two = t + 1 < a.nt;
+    const u64 *r0 = stab + t * NS, *r1 = stab + (two ? t + 1 : t) * NS;
+    u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0;
 #pragma unroll
-    for (int i = 0; i < NS; ++i) mac128(hi, lo, y[i], __ldg(&row[i]));
-    if (a.negs) mac128(hi, lo, v, __ldg(a.negs + t));
-    const ModInfo m = a.mods[a.dst_mod[t]];
-    u64 r = reduce128(hi, lo, m);
-    if (a.dst_sub) r = submod(r, __ldg(a.dst_sub + t), m.q);
-    dst[(size_t)a.dst_pos[t] * a.n + k] = r;
+    for (int i = 0; i < NS; ++i) {
+      mac128(h0, l0, y[i], r0[i]);
+      mac128(h1, l1, y[i], r1[i]);
+    }
+    if (a.negs) {
+      mac128(h0, l0, v, __ldg(a.negs + t));
+      if (two) mac128(h1, l1, v, __ldg(a.negs + t + 1));
+    }
+    const ModInfo m0 = a.mods[a.dst_mod[t]];
+    u64 o0 = reduce128(h0, l0, m0);
+    if (a.dst_sub) o0 = submod(o0, __ldg(a.dst_sub + t), m0.q);
+    dst[(size_t)a.dst_pos[t] * a.n + k] = o0;
+    if (two) {
+      const ModInfo m1 = a.mods[a.dst_mod[t + 1]];
+      u64 o1 = reduce128(h1, l1, m1);
+      if (a.dst_sub) o1 = submod(o1, __ldg(a.dst_sub + t + 1), m1.q);
+      dst[(size_t)a.dst_pos[t + 1] * a.n + k] = o1;
+    }
   }
 }
 
@@ -267,6 +288,7 @@ __global__ void __launch_bounds__(TPB) k_combine_rescale(const CombineRArgs a) {
 }
 
 int launch_bconv(ckks_ctx *c, BConvArgs &a, int ns, int np) {
+  if (a.nt * ns > BCONV_MAX_TAB) return CKKS_E_PARAM;
   a.mods = c->d_mods;
   a.n = c->n;
   dim3 g((c->n + TPB - 1) / TPB, np);
