@@ -193,6 +193,57 @@ __global__ void __launch_bounds__(TPB, NDIG <= 3 ? 4 : 2) k_inner(const IPArgs a
   }
 }
 
+// The same product for groups whose outputs share one key and one
+// automorphism (a relinearisation batch; the outputs of one rotation step of a
+// hoisted set), which the host checks per group: the key words, the gathered
+// source index and the digit layout are fixed before the loop, so each output
+// costs its loads, the multiply-accumulates, two reductions and two stores.
+template <int NDIG, int MODE>
+__global__ void __launch_bounds__(TPB, 4) k_inner_uni(const IPArgs a, int group) {
+  const u32 k = blockIdx.y * TPB + threadIdx.x;
+  const int t = blockIdx.z;
+  if (k >= a.n) return;
+  const ModInfo m = a.mods[a.mod_of[t]];
+  const int kl = a.keylimb_of[t];
+  const int p0 = blockIdx.x * group, p_end = min(a.np, p0 + group);
+  const u64 *key = a.key[p0];
+  u64 kb[NDIG], ka[NDIG];
+  size_t off[NDIG];
+  bool own[NDIG];
+  const u32 src = gal_src(k, a.gal[p0], a.n, a.log_n);
+#pragma unroll
+  for (int j = 0; j < NDIG; ++j) {
+    kb[j] = __ldg(key + ((size_t)(2 * j) * a.key_ext + kl) * a.n + k);
+    ka[j] = __ldg(key + ((size_t)(2 * j + 1) * a.key_ext + kl) * a.n + k);
+    own[j] = t >= a.lo[j] && t < a.hi[j];
+    off[j] = (own[j] ? (size_t)t : (size_t)j * a.ext + t) * a.n + src;
+  }
+  const bool with_base = MODE == IP_BASE && t < a.nq_base;
+  const u64 pm = with_base ? a.pm_mont[t] : 0;
+  const size_t o_off = (size_t)t * a.n + k, o_pol = (size_t)a.ext * a.n;
+  const size_t b_off = (size_t)t * a.n + src;
+#pragma unroll 4
+  for (int p = p0; p < p_end; ++p) {
+    const u64 *dp = a.d[p], *ep = a.ext_buf[p];
+    u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0;
+#pragma unroll
+    for (int j = 0; j < NDIG; ++j) {
+      const u64 v = __ldg((own[j] ? dp : ep) + off[j]);
+      mac128(h0, l0, v, kb[j]);
+      mac128(h1, l1, v, ka[j]);
+    }
+    if (MODE == IP_BASE && with_base) mac128(h0, l0, __ldg(a.base0[p] + b_off), pm);
+    u64 r0 = redc128(h0, l0, m), r1 = redc128(h1, l1, m);
+    u64 *o = a.acc[p] + o_off;
+    if (MODE == IP_ACC) {
+      r0 = addmod(r0, o[0], m.q);
+      r1 = addmod(r1, o[o_pol], m.q);
+    }
+    o[0] = r0;
+    o[o_pol] = r1;
+  }
+}
+
 struct CombineArgs {
   const ModInfo *mods;
   u32 n;
@@ -481,9 +532,41 @@ static int launch_inner(ckks_ctx *c, int level, int nv, const u64 *const *d, con
     a.acc[i] = acc[i];
     a.base0[i] = pbase0 ? pbase0[i] : nullptr;
   }
-  const int group = c->ip_group > 0 ? c->ip_group : 8;
+  int group = c->ip_group > 0 ? c->ip_group : 8;
   c->prof.count_ks(level, (unsigned long long)nv);
+  // every group of outputs on one key and one automorphism: the uniform kernel,
+  // at the largest group (the tuned one, halved as needed) for which that holds
+  auto uniform = [&](int gs) {
+    for (int p = 0; p < nv; ++p) {
+      const int q0 = p - p % gs;
+      if (a.key[p] != a.key[q0] || a.gal[p] != a.gal[q0]) return false;
+    }
+    return true;
+  };
+  bool uni = false;
+  if (!a.kc && ndig <= 4)
+    for (int gs = group; gs >= 4 && !uni; gs /= 2)
+      if (uniform(gs)) {
+        uni = true;
+        group = gs;
+      }
   dim3 g((nv + group - 1) / group, (n + TPB - 1) / TPB, ext);
+  if (uni) {
+    switch (ndig) {
+#define UCASE(D)                                                                                          \
+  case D:                                                                                                 \
+    if (pbase0)                                                                                           \
+      PROF_LAUNCH(c, PK_INNER, (u64)nv * ext, (k_inner_uni<D, IP_BASE><<<g, TPB, 0, c->stream>>>(a, group))); \
+    else if (accumulate)                                                                                  \
+      PROF_LAUNCH(c, PK_INNER, (u64)nv * ext, (k_inner_uni<D, IP_ACC><<<g, TPB, 0, c->stream>>>(a, group)));  \
+    else                                                                                                  \
+      PROF_LAUNCH(c, PK_INNER, (u64)nv * ext, (k_inner_uni<D, IP_SET><<<g, TPB, 0, c->stream>>>(a, group)));  \
+    break;
+      UCASE(1) UCASE(2) UCASE(3) UCASE(4)
+#undef UCASE
+    }
+    return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_CUDA;
+  }
   switch (ndig) {
 #define ILAUNCH(D, M)                                                                                        \
   do {                                                                                                       \
