@@ -1,7 +1,8 @@
 // Integer-pipe roofs for the ALU-bound kernels, measured on this GPU with the
 // production instruction sequences themselves (common.cuh): the 128-bit
 // multiply-accumulate of the basis conversion and the key inner product
-// (mac128), and the NTT's butterflies (bfly_fwd_loose for primes with
+// (mac128, with a multiplicand that changes every iteration), and the NTT's
+// butterflies (bfly_fwd_loose for primes with
 // 65 q < 2^64, bfly_fwd_strict for the others, bfly_inv<true> for the inverse
 // below 2^61).  Register-only kernels: eight independent chains per thread,
 // 256-thread CTAs at the occupancy the sequence allows, several waves; no
@@ -23,8 +24,12 @@ __global__ void __launch_bounds__(TPB) k_peak_mac(u64 *sink, u64 seed, int iters
     hi[c] = lo[c] = 0;
   }
   for (int it = 0; it < iters; ++it) {
+    // a multiplicand that changes every iteration (both halves), so that no
+    // partial product of the 64 x 64 multiply is loop-invariant; the XOR
+    // stands in for the operand load each production MAC pays
+    const u64 salt = (u64)it * 0x9E3779B97F4A7C15ULL;
 #pragma unroll
-    for (int c = 0; c < CHAINS; ++c) mac128(hi[c], lo[c], a[c], b[c]);
+    for (int c = 0; c < CHAINS; ++c) mac128(hi[c], lo[c], a[c] ^ salt, b[c]);
   }
   u64 r = 0;
 #pragma unroll
