@@ -195,10 +195,11 @@ struct TcArgs {
 
 // Sources of one 128-coefficient block for this thread: row tid mod 128,
 // sources i = tid / 128 + 4 k.
-__device__ __forceinline__ void load_sources(const TcArgs &a, int tile, int tiles_per_poly, int tid,
+// tiles_per_poly is a power of two (n / 128): tpp_log2 its log
+__device__ __forceinline__ void load_sources(const TcArgs &a, int tile, int tpp_log2, int tid,
                                              u64 (&x)[TC_SRC_PER]) {
-  const u64 *src = a.src[tile / tiles_per_poly];
-  const u32 kc = (u32)(tile % tiles_per_poly) * TC_M + (u32)(tid & (TC_M - 1));
+  const u64 *src = a.src[tile >> tpp_log2];
+  const u32 kc = (u32)(tile & ((1 << tpp_log2) - 1)) * TC_M + (u32)(tid & (TC_M - 1));
 #pragma unroll
   for (int k = 0; k < TC_SRC_PER; ++k) {
     const int i = tid / TC_M + k * TC_SRC_GROUPS;
@@ -268,16 +269,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_bconv_tc(const TcArgs a) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
 
-  const int tiles_per_poly = (int)(a.n / TC_M);
-  const int total = tiles_per_poly * a.np;
+  const int tpp_log2 = 31 - __clz((int)(a.n / TC_M));  // n / 128 is a power of two
+  const int total = (1 << tpp_log2) * a.np;
   const int grid = (int)gridDim.x;
   int tile = blockIdx.x;
   u64 x[TC_SRC_PER];  // sources of the next block to be written into an A tile
   if (tile < total) {
-    load_sources(a, tile, tiles_per_poly, tid, x);
+    load_sources(a, tile, tpp_log2, tid, x);
     store_sources(a, smem, tid, x, part);
   }
-  if (tile + grid < total) load_sources(a, tile + grid, tiles_per_poly, tid, x);
+  if (tile + grid < total) load_sources(a, tile + grid, tpp_log2, tid, x);
   if (a.has_v && tile < total) {
     __syncthreads();
     if (tid < TC_M) store_overflow(a, smem, tid, part);
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_bconv_tc(const TcArgs a) {
     // A tile of the next block from the prefetched sources (its buffer's MMAs
     // completed before epilogue j - 1), then prefetch the block after it
     if (next < total) store_sources(a, smem + nxt * a_bytes, tid, x, part);
-    if (next + grid < total) load_sources(a, next + grid, tiles_per_poly, tid, x);
+    if (next + grid < total) load_sources(a, next + grid, tpp_log2, tid, x);
     if (a.has_v && next < total) {  // the parts are complete after this barrier
       __syncthreads();
       if (tid < TC_M) store_overflow(a, smem + nxt * a_bytes, tid, part);
@@ -348,8 +349,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_bconv_tc(const TcArgs a) {
     pending &= ~(1u << cur);
     asm volatile("tcgen05.fence::after_thread_sync;");
     // epilogue: lanes 32 lq .. +31 = coefficients k0 + 32 lq + lane, targets t_lo .. t_hi - 1
-    u64 *dst = a.dst[tile / tiles_per_poly];
-    const u32 kc = (u32)(tile % tiles_per_poly) * TC_M + (u32)(lq * 32 + lane);
+    u64 *dst = a.dst[tile >> tpp_log2];
+    const u32 kc = (u32)(tile & ((1 << tpp_log2) - 1)) * TC_M + (u32)(lq * 32 + lane);
     const u32 tbase = tmem + ((u32)(lq * 32) << 16) + (u32)(cur * TC_ACC_COLS);
     // four targets per wait where possible, then a pair, then a single one
     int t = t_lo;
@@ -406,7 +407,7 @@ static int launch_bconv_tc_ex(ckks_ctx *c, size_t key, const u64 *inv_host, cons
                               const u64 *rdiv_host, const u64 *negs_host, u64 wait_ns, int test_expire,
                               u32 n_virt) {
   if (ns < 1 || ns > TC_MAX_S || nt < 1 || nt > TC_MAX_T || np < 1 || np > MAX_CTS) return CKKS_E_PARAM;
-  if (n_virt % TC_M || n_virt == 0) return CKKS_E_PARAM;
+  if (n_virt % TC_M || n_virt == 0 || ((n_virt / TC_M) & (n_virt / TC_M - 1))) return CKKS_E_PARAM;
   const bool has_v = rdiv_host && negs_host;
   if (has_v && ns == TC_MAX_S) return CKKS_E_PARAM;  // the overflow column needs K <= 8 ns + 1 <= 128
   const int kpad = ((8 * ns + (has_v ? 1 : 0) + 15) / 16) * 16, npad = ((8 * nt + 15) / 16) * 16;
