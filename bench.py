@@ -265,6 +265,10 @@ def kernel_work(name, units, w, ndig, prof):  # noqa: C901
         return 8 * n * (src + dst), alu, None
     elif name == "ks_inner_product":
         alu = [(units * 2 * ndig * n, "mac_per_s")]
+    elif name == "boot_mac_ext":
+        # the launches' multiply-accumulates, counted by the library (all launches of the class)
+        alu = [(prof.get("boot_mac_ext_macs", (0, 0, 0))[2] * (units / max(1, prof.get(name, (0, 0, 1))[2])),
+                "mac_per_s")]
     if name == "bconv_tc":
         tensor = units * n * 64 * 2  # 8 x 8 byte products per coefficient and pair, 2 flops each
     if name in ("bconv", "bconv_tc"):

@@ -951,6 +951,12 @@ struct Eval {
         break;
       }
       const dim3 g(c->n / MB_K, ext);
+      // 128-bit multiply-accumulates: two polynomials per (ciphertext, limb,
+      // coefficient, diagonal); baby 0 only on the q-limbs
+      u64 macs = 0;
+      for (int j = 0; j < ng; ++j)
+        for (auto &it : lv.plan[j].items) macs += it.first ? (u64)ext : (u64)nl;
+      c->prof.count(PK_BOOT_MAC_MACS, macs * 2 * cn * c->n);
       PROF_LAUNCH(c, PK_BOOT_MAC, moved, (k_mac_ext<<<g, MB_THREADS, smem, c->stream>>>(a)));
       if (cudaGetLastError() != cudaSuccess) err = CKKS_E_CUDA;
     }

@@ -602,7 +602,7 @@ const char *ckks_profile_kind_name(int k) {
                                         "automorph", "rescale", "elementwise", "encode_decode", "bconv_tc",
                                         "boot_mac_ext", "boot_lincomb", "conv_fused", "ntt_fwd_strict_limbs",
                                         "ntt_inv_exact_limbs", "fused_src_limbs", "fused_dst_limbs",
-                                        "fused_dst_strict_limbs"};
+                                        "fused_dst_strict_limbs", "boot_mac_ext_macs"};
   return (k >= 0 && k < PK_COUNT) ? names[k] : "unknown";
 }
 

@@ -35,6 +35,7 @@ enum ProfKind {
   PK_FUSED_SRC_LIMBS,
   PK_FUSED_DST_LIMBS,
   PK_FUSED_DST_STRICT,
+  PK_BOOT_MAC_MACS,   // counting-only: k_mac_ext's 128-bit multiply-accumulates
   PK_COUNT
 };
 constexpr int PROF_MAX_LEVEL = 64;
