@@ -475,6 +475,8 @@ def run_gpu(args):
     # autotuning, untimed: key inner-product group and NTT row tile per context
     tuning = {"ip_group": ctx.tune(level, B), "ntt_rows": ctx.tune_ntt(16),
               "boot_ip_group": bctx.tune(len(wb.q_bits) - 1, nb), "boot_ntt_rows": bctx.tune_ntt(16)}
+    tuning["ntt_cluster"] = ctx.ntt_config()["cluster"]
+    tuning["boot_ntt_cluster"] = bctx.ntt_config()["cluster"]
 
     nvtx = torch.cuda.nvtx
 
@@ -656,6 +658,9 @@ def run_gpu(args):
     tc_ntt = None
     if not (args.no_tc_ntt or args.small):
         tc_ntt = run_tc_ntt_prototype(ctx, w, torch, stream, reps=max(2, min(args.steps, 3)))
+    cluster_ntt = None
+    if not (args.no_tc_ntt or args.small):
+        cluster_ntt = run_cluster_ntt(ctx, w, torch, stream, max(2, min(args.steps, 3)), A, Bc, OUT)
 
     # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -712,6 +717,7 @@ def run_gpu(args):
                 "key_compression": key_compression,
                 "sparse_slot_bootstrap": sparse_boot,
                 "tensor_ntt_stage_prototype": tc_ntt,
+                "cluster_ntt": cluster_ntt,
                 "tuning": tuning,
                 "e2e": e2e, "roofline": roof, "op_rooflines": op_roofs, "alu_peaks": alu, "cpu_baseline": cpu,
                 "clocks": clk,
@@ -889,6 +895,47 @@ def run_tc_ntt_prototype(ctx, w, torch, stream, reps, n_polys=64):
             "stage_group_tensor_tflops": tc_flops / (stage_ms / 1e3) / 1e12 if stage_ms else None,
             "note": "uint64 NTT launched per polynomial (24 limbs per launch); the four stages the prototype moves "
                     "to the tensor cores are half of the uint64 column pass"}
+
+
+def run_cluster_ntt(ctx, w, torch, stream, reps, A, Bc, OUT):
+    """The forward NTT in one pass on 8-CTA clusters (each limb read and written
+    once) against the two passes (each limb crosses HBM twice), on the bench's
+    merged HMult batch: batch time and the profiler's forward-transform time per
+    limb in each form.  Both forms give identical limbs (checked here too)."""
+    import paper_2506_19693_gb300 as ck
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    was = ctx.ntt_config()["cluster"]
+    res = {}
+    outs = {}
+    for on in (False, True):
+        res_key = "cluster" if on else "two_pass"
+        info = ctx.set_ntt_cluster(on)
+        ctx.mul_relin_batch(A, Bc, OUT, rescale=ck.RESCALE_MERGED)
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        for _ in range(reps):
+            ctx.mul_relin_batch(A, Bc, OUT, rescale=ck.RESCALE_MERGED)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        ctx.profile_read()
+        ctx.mul_relin_batch(A, Bc, OUT, rescale=ck.RESCALE_MERGED)
+        torch.cuda.synchronize()
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        outs[on] = ctx.export_ct(OUT[0])
+        kinds = ("ntt_fwd_cluster",) if on else ("ntt_fwd_pass_a", "ntt_fwd_pass_b")
+        fwd_ms = sum(prof.get(k, (0.0, 0, 0))[0] for k in kinds)
+        limbs = prof.get(kinds[0], (0.0, 0, 0))[2]
+        res[res_key] = {"ms_per_batch": e0.elapsed_time(e1) / reps, "forward_ntt_ms": fwd_ms,
+                        "forward_limbs": limbs, "us_per_limb": 1e3 * fwd_ms / limbs if limbs else None,
+                        "hbm_bytes_per_limb": (1 if on else 2) * 2 * 8 * ctx.n}
+        if on:
+            res[res_key]["resident_clusters"] = info
+    ctx.set_ntt_cluster(was)
+    res["bit_exact"] = bool(np.array_equal(outs[False], outs[True]))
+    return res
 
 
 def run_n_scaling(torch, stream, reps):

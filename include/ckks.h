@@ -452,11 +452,25 @@ int ckks_tune(ckks_ctx *ctx, int level, int batch, int *chosen);
 /* Autotune the NTT's row pass for this context: time forward + inverse
  * transforms of n_polys (1..64) polynomials over all ciphertext primes with
  * 16 and 8 rows per CTA and keep the faster; *rows (may be NULL) receives it.
+ * At N = 2^16 it then times the forward transform in one pass on clusters
+ * (ckks_ctx_set_ntt_cluster) against the two passes and keeps the faster.
  * Needs the relinearisation key (its limbs are the timing input);
  * CKKS_E_STATE during graph capture. */
 int ckks_tune_ntt(ckks_ctx *ctx, int n_polys, int *rows);
 /* Set the NTT row-pass tile directly: 16 or 8 rows per CTA (else CKKS_E_PARAM). */
 int ckks_ctx_set_ntt_rows(ckks_ctx *ctx, int rows);
+/* Forward NTT in one pass (Sec. 2.2's negacyclic transform, the same
+ * butterflies and the same residues as the two-pass form): on = 1 runs each
+ * limb of a full forward transform on a cluster of 8 CTAs that hold the whole
+ * limb in distributed shared memory, so it is read from and written to HBM
+ * once; on = 0 restores the two passes.  N = 2^16 only (else CKKS_E_PARAM when
+ * on = 1).  *max_clusters (may be NULL) receives how many such clusters the
+ * device runs at once; CKKS_E_CUDA when it runs none.  The inverse and the
+ * fused conversion's column passes are unchanged. */
+int ckks_ctx_set_ntt_cluster(ckks_ctx *ctx, int on, int *max_clusters);
+/* The NTT launch choices in force: *rows (16 or 8 rows per row-pass CTA) and
+ * *cluster (1 when the forward transform runs in one pass); either may be NULL. */
+int ckks_ctx_ntt_config(const ckks_ctx *ctx, int *rows, int *cluster);
 /* Autotune the gadget (reading C7) of a parameter set: for each candidate
  * dnum a context with alpha = ceil(n_q / dnum) special primes of p_bits[0]
  * bits (P spans one digit) is created on cuda_stream, its relinearisation key

@@ -121,6 +121,8 @@ SIGNATURES = {
     "ckks_tune": (_I, [_V, _I, _I, ctypes.POINTER(_I)]),
     "ckks_tune_ntt": (_I, [_V, _I, ctypes.POINTER(ctypes.c_int)]),
     "ckks_ctx_set_ntt_rows": (_I, [_V, _I]),
+    "ckks_ctx_set_ntt_cluster": (_I, [_V, _I, ctypes.POINTER(ctypes.c_int)]),
+    "ckks_ctx_ntt_config": (_I, [_V, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "ckks_tune_dnum": (_I, [_V, _V, ctypes.POINTER(ctypes.c_uint32), _I, _I, ctypes.c_uint64,
                             ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_double)]),
     "ckks_ntt_tc": (_I, [_V, _V, ctypes.c_uint32, ctypes.c_uint32]),
@@ -294,6 +296,20 @@ class Context:
 
     def set_ntt_rows(self, rows: int) -> None:
         _check(self.lib.ckks_ctx_set_ntt_rows(self._h, rows), "ckks_ctx_set_ntt_rows")
+
+    def set_ntt_cluster(self, on: bool) -> int:
+        """One-pass forward NTT on 8-CTA clusters (N = 2^16); returns the number
+        of clusters the device holds at once (0 when switched off)."""
+        m = ctypes.c_int(0)
+        _check(self.lib.ckks_ctx_set_ntt_cluster(self._h, 1 if on else 0, ctypes.byref(m)),
+               "ckks_ctx_set_ntt_cluster")
+        return m.value
+
+    def ntt_config(self) -> dict:
+        """The NTT launch choices in force: {"rows": 16 or 8, "cluster": bool}."""
+        r, cl = ctypes.c_int(0), ctypes.c_int(0)
+        _check(self.lib.ckks_ctx_ntt_config(self._h, ctypes.byref(r), ctypes.byref(cl)), "ckks_ctx_ntt_config")
+        return {"rows": r.value, "cluster": bool(cl.value)}
 
     def tune_ntt(self, n_polys: int = 16) -> int:
         """Autotune the NTT row pass (rows per CTA); returns the choice."""

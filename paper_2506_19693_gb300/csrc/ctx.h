@@ -97,6 +97,7 @@ struct ckks_ctx {
   Profiler prof;
   int ip_group = 8;                  // key inner product: outputs per thread (ckks_tune)
   int ntt_rows = 16;                 // NTT row pass: rows per CTA, 16 or 8 (ckks_tune_ntt)
+  bool ntt_cluster = false;          // forward NTT at N = 2^16 in one pass on an 8-CTA cluster
   bool use_tc = false;               // basis conversion on the tensor cores (ckks_ctx_set_form)
   bool use_fused = false;            // conversion fused with the transforms' column passes (N <= 2^16)
   std::map<size_t, void *> tc_bmats; // byte-plane constants per conversion
@@ -150,6 +151,9 @@ int launch_ntt(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, i
 enum { NTT_COLS = 1, NTT_ROWS = 2, NTT_BOTH = 3 };
 int launch_ntt_part(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, int nl,
                     const int *mods, bool inverse, int part);
+// The one-pass forward transform on an 8-CTA cluster (N = 2^16 only): opt in
+// its shared memory and count the clusters the device holds at once.
+int ntt_cluster_prepare(const ckks_ctx *c, int *max_clusters);
 
 // ---- fused conversion column pass (ntt.cu) ----
 // A basis conversion between NTT domains with its transforms' column passes

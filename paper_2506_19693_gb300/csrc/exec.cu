@@ -293,6 +293,25 @@ int ckks_ctx_set_ntt_rows(ckks_ctx *c, int rows) {
   return CKKS_OK;
 }
 
+int ckks_ctx_ntt_config(const ckks_ctx *c, int *rows, int *cluster) {
+  if (!c) return CKKS_E_PARAM;
+  if (rows) *rows = c->ntt_rows;
+  if (cluster) *cluster = c->ntt_cluster ? 1 : 0;
+  return CKKS_OK;
+}
+
+int ckks_ctx_set_ntt_cluster(ckks_ctx *c, int on, int *max_clusters) {
+  if (!c) return CKKS_E_PARAM;
+  if (!on) {
+    c->ntt_cluster = false;
+    return CKKS_OK;
+  }
+  const int rc = ntt_cluster_prepare(c, max_clusters);
+  if (rc) return rc;
+  c->ntt_cluster = true;
+  return CKKS_OK;
+}
+
 int ckks_tune_ntt(ckks_ctx *c, int n_polys, int *rows) {
   if (!c || n_polys < 1 || n_polys > 64) return CKKS_E_PARAM;
   if (c->capturing) return CKKS_E_STATE;
@@ -339,10 +358,31 @@ int ckks_tune_ntt(ckks_ctx *c, int n_polys, int *rows) {
       best_r = cand;
     }
   }
+  c->ntt_rows = best_r;
+  // at N = 2^16, the one-pass forward transform on clusters against the two passes
+  const bool was_cluster = c->ntt_cluster;
+  bool best_cluster = false;
+  if (!rc && c->log_n == 16 && ntt_cluster_prepare(c, nullptr) == CKKS_OK) {
+    for (int on = 0; on < 2 && !rc; ++on) {
+      c->ntt_cluster = on != 0;
+      float tot = 0.f;
+      for (int rep = 0; rep < 3 && !rc; ++rep) {
+        cudaEventRecord(e0, c->stream);
+        rc = launch_ntt(c, src.data(), dst.data(), n_polys, nl, mods, false);
+        cudaEventRecord(e1, c->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep) tot += ms;
+      }
+      if (!on) best = tot;
+      else if (tot < best) best_cluster = true;
+    }
+  }
+  c->ntt_cluster = rc ? was_cluster : best_cluster;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(outs);
-  c->ntt_rows = best_r;
   if (rows) *rows = best_r;
   return rc;
 }

@@ -18,9 +18,13 @@
 // Each thread owns 2^s words and runs s butterfly stages in registers
 // (Harvey's lazy butterflies: values stay in [0, 4q) forward, [0, 2q)
 // inverse; q < 2^62).
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "ops.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -425,6 +429,8 @@ __global__ void __launch_bounds__(THREADS, 4) inv_pass_a(const NttParams prm) {
     inv_a_body<LH, S1, APPROX>(prm, sm, mi, dst);
 }
 
+void launch_fwd_cluster(ckks_ctx *c, const NttParams &prm, int npoly);
+
 // part: NTT_BOTH, or one pass alone -- the inverse's row pass (NTT_ROWS) or the
 // forward's row pass (NTT_ROWS, reading src) around a fused column pass.
 template <int LH, int RB, bool APPROX>
@@ -451,6 +457,10 @@ void launch_lh(ckks_ctx *c, const NttParams &prm, int npoly, bool inverse, bool 
   const int H = 1 << LH;
   cudaStream_t st = c->stream;
   const unsigned long long units = (unsigned long long)prm.n_limbs * npoly;
+  if (LH == 8 && part == NTT_BOTH && c->ntt_cluster && !prm.skip_first) {
+    launch_fwd_cluster(c, prm, npoly);
+    return;
+  }
   dim3 ga(BROW / ca_of(LH), prm.n_limbs, npoly);
   if (part & NTT_COLS) PROF_LAUNCH(c, PK_NTT_FWD_A, units, (fwd_pass_a<LH, S1><<<ga, THREADS, 0, st>>>(prm)));
   if (!(part & NTT_ROWS)) return;
@@ -462,6 +472,166 @@ void launch_lh(ckks_ctx *c, const NttParams &prm, int npoly, bool inverse, bool 
     dim3 gb(H / 16, prm.n_limbs, npoly);
     PROF_LAUNCH(c, PK_NTT_FWD_B, units, (fwd_pass_b<LH, 16><<<gb, threads_b<16>(), 0, st>>>(prm, from_src)));
   }
+}
+
+// ---------------------------------------------------------------- one-pass forward transform on a cluster
+// N = 2^16: the limb (256 rows x 256 words, 512 KiB) is spread over a cluster of
+// eight CTAs, 64 KiB of shared memory each, so it crosses HBM once (read once,
+// written once) instead of twice.
+//   phase 1: CTA r loads columns 32r .. 32r+31 (all rows) and runs the eight
+//            column stages (pass A's two register phases, exchange in its tile);
+//   cluster barrier;
+//   phase 2: CTA r gathers rows 32r .. 32r+31 from the eight tiles through
+//            distributed shared memory and runs the first four row stages in
+//            registers; a second cluster barrier (every remote read done) frees
+//            the tile for the row exchange; the last four row stages, the final
+//            reduction and a contiguous store follow (pass B's steps).
+// Every value goes through the same butterflies in the same order as
+// fwd_pass_a then fwd_pass_b, so the output is bit-identical.  Both cluster
+// barriers are reached by every thread: the only branch (loose or strict
+// prime) is uniform over the cluster, which holds one limb.
+constexpr int NC = 8;                    // CTAs per cluster
+constexpr int NC_THREADS = 256;
+constexpr int NC_IT = 512 / NC_THREADS;  // 16-value groups per thread in each phase
+constexpr int NC_CA = BROW / NC;         // 32 columns per CTA in phase 1
+constexpr int NC_RB = 256 / NC;          // 32 rows per CTA in phase 2
+constexpr int NC_SMEM_WORDS = NC_RB * BROW + (NC_RB * BROW >> 4);  // the padded row buffer (>= 256 x 32)
+
+template <bool LOOSE>
+__device__ __forceinline__ void fwd_cluster_body(const NttParams &prm, u64 *sm, int mi, const u64 *src, u64 *dst,
+                                                 cg::cluster_group &cl) {
+  constexpr int H = 256, S1 = 4, S2 = 4, U1 = 4, U2 = 4;
+  const u64 q = prm.mods[mi].q, twoq = 2 * q;
+  const ulonglong2 *tw = prm.tw + (size_t)mi * prm.n;
+  const int rank = (int)cl.block_rank();
+  const int c0 = rank * NC_CA;
+  {  // column stages 0..3: rows r0 + 16 e of column c0 + c, every load issued first
+    u64 v[NC_IT][1 << S1];
+#pragma unroll
+    for (int it = 0; it < NC_IT; ++it) {
+      const int x = threadIdx.x + it * NC_THREADS, c = x % NC_CA, r0 = x / NC_CA;
+#pragma unroll
+      for (int e = 0; e < (1 << S1); ++e) v[it][e] = src[(size_t)(r0 + (e << S2)) * BROW + c0 + c];
+    }
+#pragma unroll
+    for (int it = 0; it < NC_IT; ++it) {
+      const int x = threadIdx.x + it * NC_THREADS, c = x % NC_CA, r0 = x / NC_CA;
+      fwd_step<S1, LOOSE>(v[it], 1u, tw, q, twoq);
+#pragma unroll
+      for (int e = 0; e < (1 << S1); ++e) sm[(r0 + (e << S2)) * NC_CA + c] = v[it][e];
+    }
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int it = 0; it < NC_IT; ++it) {  // column stages 4..7: rows 16 g + e
+    const int x = threadIdx.x + it * NC_THREADS, c = x % NC_CA, g = x / NC_CA;
+    u64 v[1 << S2];
+#pragma unroll
+    for (int e = 0; e < (1 << S2); ++e) v[e] = sm[((g << S2) + e) * NC_CA + c];
+    fwd_step<S2, LOOSE>(v, (1u << S1) + g, tw, q, twoq);
+#pragma unroll
+    for (int e = 0; e < (1 << S2); ++e) sm[((g << S2) + e) * NC_CA + c] = v[e];
+  }
+  cl.sync();  // every CTA's columns are transformed
+  u64 v[NC_IT][1 << U1];
+#pragma unroll
+  for (int it = 0; it < NC_IT; ++it) {
+    const int x = threadIdx.x + it * NC_THREADS, l0 = x % (BROW >> U1), rr = x / (BROW >> U1);
+    const int b = rank * NC_RB + rr;
+#pragma unroll
+    for (int e = 0; e < (1 << U1); ++e) {  // word l0 + 16 e of row b lives in CTA (l0 + 16 e) / 32
+      const int col = l0 + (e << U2);
+      const u64 *rem = cl.map_shared_rank(sm, col / NC_CA);
+      v[it][e] = rem[b * NC_CA + col % NC_CA];
+    }
+  }
+#pragma unroll
+  for (int it = 0; it < NC_IT; ++it) {
+    const int x = threadIdx.x + it * NC_THREADS, rr = x / (BROW >> U1);
+    fwd_step<U1, LOOSE>(v[it], (u32)(H + rank * NC_RB + rr), tw, q, twoq);
+  }
+  cl.sync();  // every remote read is done: the tile becomes the row buffer
+#pragma unroll
+  for (int it = 0; it < NC_IT; ++it) {
+    const int x = threadIdx.x + it * NC_THREADS, l0 = x % (BROW >> U1), rr = x / (BROW >> U1);
+#pragma unroll
+    for (int e = 0; e < (1 << U1); ++e) sm[padb(rr * BROW + l0 + (e << U2))] = v[it][e];
+  }
+  __syncthreads();
+  const u64 one_s = LOOSE ? prm.mods[mi].one_s : 0;
+#pragma unroll 1
+  for (int it = 0; it < NC_IT; ++it) {
+    const int x = threadIdx.x + it * NC_THREADS, g = x % (1 << U1), r2 = x / (1 << U1);
+    const int b2 = rank * NC_RB + r2;
+    u64 w[1 << U2];
+#pragma unroll
+    for (int e = 0; e < (1 << U2); ++e) w[e] = sm[padb(r2 * BROW + (g << U2) + e)];
+    fwd_step_row<U2, LOOSE>(w, ((u32)b2 << U1) + g, prm.tw_row + (size_t)mi * 15 * (prm.n / 16), prm.n / 16, q,
+                            twoq);
+#pragma unroll
+    for (int e = 0; e < (1 << U2); ++e) {
+      u64 r = w[e];
+      if (LOOSE) {
+        r -= __umul64hi(r, one_s) * q;
+      } else if (r >= twoq) {
+        r -= twoq;
+      }
+      if (r >= q) r -= q;
+      sm[padb(r2 * BROW + (g << U2) + e)] = r;
+    }
+  }
+  __syncthreads();
+  ulonglong2 *d2 = reinterpret_cast<ulonglong2 *>(dst + (size_t)rank * NC_RB * BROW);
+#pragma unroll 4
+  for (int y = threadIdx.x; y < NC_RB * BROW / 2; y += NC_THREADS) {
+    const int o = padb(2 * y);
+    d2[y] = make_ulonglong2(sm[o], sm[o + 1]);
+  }
+}
+
+__global__ void __cluster_dims__(NC, 1, 1) __launch_bounds__(NC_THREADS, 2) fwd_cluster(const NttParams prm) {
+  extern __shared__ u64 csm[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int limb = blockIdx.y, poly = blockIdx.z;
+  const int mi = prm.mod_of_limb[limb];
+  const u64 *src = prm.src.p[poly] + (size_t)limb * prm.n;
+  u64 *dst = prm.dst.p[poly] + (size_t)limb * prm.n;
+  if (prm.mods[mi].q < LOOSE_BOUND)
+    fwd_cluster_body<true>(prm, csm, mi, src, dst, cl);
+  else
+    fwd_cluster_body<false>(prm, csm, mi, src, dst, cl);
+}
+
+constexpr size_t NC_SMEM_BYTES = NC_SMEM_WORDS * sizeof(u64);
+
+// Launch errors stay pending for the caller's cudaGetLastError.
+void launch_fwd_cluster(ckks_ctx *c, const NttParams &prm, int npoly) {
+  const unsigned long long units = (unsigned long long)prm.n_limbs * npoly;
+  dim3 g(NC, prm.n_limbs, npoly);
+  PROF_LAUNCH(c, PK_NTT_FWD_CLUSTER, units, (fwd_cluster<<<g, NC_THREADS, NC_SMEM_BYTES, c->stream>>>(prm)));
+}
+
+// Opt the kernel into its dynamic shared memory and check that the device can
+// hold at least one cluster of it: CKKS_E_PARAM off N = 2^16, CKKS_E_CUDA when
+// the attribute or the occupancy query fails or no cluster fits.
+int prepare_fwd_cluster(const ckks_ctx *c, int *max_clusters) {
+  if (c->log_n != 16) return CKKS_E_PARAM;
+  if (cudaFuncSetAttribute(fwd_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NC_SMEM_BYTES) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return CKKS_E_CUDA;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(NC, 1, 1);
+  cfg.blockDim = dim3(NC_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = NC_SMEM_BYTES;
+  int nclu = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclu, fwd_cluster, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return CKKS_E_CUDA;
+  }
+  if (max_clusters) *max_clusters = nclu;
+  return nclu > 0 ? CKKS_OK : CKKS_E_CUDA;
 }
 
 // ---------------------------------------------------------------- fused conversion column pass
@@ -679,6 +849,8 @@ int launch_fused_lh(ckks_ctx *c, const FusedArgs &a, int ndig, int np, size_t sm
 }
 
 }  // namespace
+
+int ntt_cluster_prepare(const ckks_ctx *c, int *max_clusters) { return prepare_fwd_cluster(c, max_clusters); }
 
 int launch_ntt_part(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, int nl, const int *mods,
                     bool inverse, int part) {

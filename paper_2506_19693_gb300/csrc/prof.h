@@ -24,6 +24,7 @@ enum ProfKind {
   PK_BOOT_MAC,        // units: limbs of N words moved (algorithmic)
   PK_BOOT_LINCOMB,    // units: limbs of N words moved (algorithmic)
   PK_CONV_FUSED,      // units: source-target limb pairs of one polynomial (as the conversions)
+  PK_NTT_FWD_CLUSTER, // units: limbs (the one-pass forward transform on a cluster)
   // counting-only classes (no launches, no time): limbs of the forward NTT
   // passes whose prime takes the strict butterfly (65 q >= 2^64), and limbs of
   // inverse passes launched with the exact quotient (a prime >= 2^61)
