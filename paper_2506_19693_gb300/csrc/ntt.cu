@@ -50,6 +50,22 @@ struct NttParams {
   PolyPtrs dst;
 };
 
+// Final reduction of a loose forward output r < 65 q to [0, q), s = floor(2^64 / q).
+// For q > 2^32 (s < 2^32) the quotient k = floor(r_hi s / 2^32), r_hi =
+// floor(r / 2^32), satisfies floor(r/q) - 2 <= k <= r/q: the terms it drops
+// are below r / 2^64 < 1 and 2^32 / q < 1.  So r - k q lies in [0, 3q), from
+// one 32-bit high multiply and a 32 x 64 product instead of the 64 x 64 Barrett
+// quotient (kept for q < 2^32, whose result lies in [0, 2q)).
+__device__ __forceinline__ u64 reduce_loose_out(u64 r, u64 q, u64 one_s) {
+  if (one_s >> 32) {
+    r -= __umul64hi(r, one_s) * q;
+  } else {
+    r -= (u64)__umulhi((u32)(r >> 32), (u32)one_s) * q;
+    if (r >= 2 * q) r -= 2 * q;
+  }
+  return r >= q ? r - q : r;
+}
+
 // Pass-B shared-memory padding: one spare word per 16 keeps the 16-word
 // strided accesses of the row stages conflict-free.
 __device__ __forceinline__ int padb(int off) { return off + (off >> 4); }
@@ -247,12 +263,12 @@ __device__ __forceinline__ void fwd_b_body(const NttParams &prm, u64 *sm, int mi
 #pragma unroll
     for (int e = 0; e < (1 << U2); ++e) {
       u64 r = v[e];
-      if (LOOSE) {  // r < 65 q: Barrett with floor(2^64 / q) to [0, 2q), then [0, q)
-        r -= __umul64hi(r, one_s) * q;
-      } else if (r >= twoq) {
-        r -= twoq;
+      if (LOOSE) {  // r < 65 q
+        r = reduce_loose_out(r, q, one_s);
+      } else {      // r < 4 q
+        if (r >= twoq) r -= twoq;
+        if (r >= q) r -= q;
       }
-      if (r >= q) r -= q;
       sm[padb(rr * BROW + (g << U2) + e)] = r;
     }
   }
@@ -572,11 +588,11 @@ __device__ __forceinline__ void fwd_cluster_body(const NttParams &prm, u64 *sm, 
     for (int e = 0; e < (1 << U2); ++e) {
       u64 r = w[e];
       if (LOOSE) {
-        r -= __umul64hi(r, one_s) * q;
-      } else if (r >= twoq) {
-        r -= twoq;
+        r = reduce_loose_out(r, q, one_s);
+      } else {
+        if (r >= twoq) r -= twoq;
+        if (r >= q) r -= q;
       }
-      if (r >= q) r -= q;
       sm[padb(r2 * BROW + (g << U2) + e)] = r;
     }
   }
