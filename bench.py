@@ -242,13 +242,17 @@ def kernel_work(name, units, w, ndig, prof):  # noqa: C901
     n = 1 << w.log_n
     lh = w.log_n - 8
     hbm_words = {"ntt_fwd_pass_a": 2, "ntt_fwd_pass_b": 2, "ntt_inv_pass_a": 2, "ntt_inv_pass_b": 2,
+                 "ntt_fwd_cluster": 2,
                  "automorph": 2, "tensor": 7, "ks_moddown_combine": 8, "ks_inner_product": ndig + 2,
                  "boot_mac_ext": 1, "boot_lincomb": 1, "bconv": None, "bconv_tc": None}.get(name)
     alu, tensor = [], None
     if name.startswith("ntt_"):
-        per_limb = (n // 2) * (lh if name.endswith("pass_a") else 8)
+        # the one-pass cluster form runs all log2 N stages per limb
+        per_limb = (n // 2) * (lh if name.endswith("pass_a") else w.log_n if name.endswith("cluster") else 8)
         if name.startswith("ntt_fwd"):
-            f = prof.get("ntt_fwd_strict_limbs", (0, 0, 0))[2] / max(1, prof.get("ntt_fwd_pass_a", (0, 0, 1))[2])
+            # strict limbs are counted for every forward transform that runs the column stages
+            fwd_limbs = prof.get("ntt_fwd_pass_a", (0, 0, 0))[2] + prof.get("ntt_fwd_cluster", (0, 0, 0))[2]
+            f = prof.get("ntt_fwd_strict_limbs", (0, 0, 0))[2] / max(1, fwd_limbs)
             alu = [(units * (1 - f) * per_limb, "bfly_fwd_loose_per_s"), (units * f * per_limb, "bfly_fwd_strict_per_s")]
         else:
             f = prof.get("ntt_inv_exact_limbs", (0, 0, 0))[2] / max(1, prof.get("ntt_inv_pass_a", (0, 0, 1))[2])

@@ -84,3 +84,14 @@ def test_op_roofline_sums_each_class_at_its_roof(bench):
     assert abs(op["compute"]["frac"] - t / 2e-3) < 1e-12
     assert abs(op["hbm"]["frac"] - 1.0e6 * 2000 / 6000e9) < 1e-12
     assert op["ops_per_s"] == 2000
+
+
+def test_cluster_ntt_work_is_one_pass_of_all_stages(bench):
+    w = si.PLAIN
+    n = w.n
+    # 10 limbs in the one-pass cluster form, 5 of them strict
+    prof = {"ntt_fwd_cluster": (1.0, 1, 10), "ntt_fwd_strict_limbs": (0.0, 0, 5)}
+    hbm, alu, tensor = bench.kernel_work("ntt_fwd_cluster", 10, w, 3, prof)
+    per_limb = n // 2 * w.log_n
+    assert hbm == 2 * 8 * n * 10 and tensor is None
+    assert dict((k, o) for o, k in alu) == {"bfly_fwd_loose_per_s": 5 * per_limb, "bfly_fwd_strict_per_s": 5 * per_limb}
