@@ -177,7 +177,7 @@ struct TcArgs {
   const __half *bmat;                         // [npad][kpad] row-major constants (bytes)
   u64 sq[TC_MAX_S], inv[TC_MAX_S], inv_s[TC_MAX_S];  // b_i, [Bhat_i^-1]_(b_i), Shoup companion
   u64 src_add[TC_MAX_S];                      // added to y_i mod b_i when has_add
-  u64 rdiv[TC_MAX_S];                         // floor(2^96 / b_i) when has_v
+  u64 rdiv[TC_MAX_S], rdiv_hi[TC_MAX_S];      // floor(2^96 / b_i), low and high words, when has_v
   int has_add, has_sub;
   int has_v;                                  // overflow removal: A column 8 ns holds v, B row holds -B mod t
   TcTarget tg[TC_MAX_T];
@@ -208,7 +208,7 @@ __device__ __forceinline__ void load_sources(const TcArgs &a, int tile, int tpp_
 }
 
 // y_i = [x_i Bhat_i^-1]_(b_i) as 8 fp16 bytes into row tid mod 128 of an A tile;
-// with overflow removal, this thread's part of sum_i floor(y_i rdiv_i / 2^64)
+// with overflow removal, this thread's part of sum_i floor(y_i R_i / 2^64)
 // goes to part[group][row].
 __device__ __forceinline__ void store_sources(const TcArgs &a, unsigned char *sA, int tid,
                                               const u64 (&x)[TC_SRC_PER], u64 *part) {
@@ -220,7 +220,7 @@ __device__ __forceinline__ void store_sources(const TcArgs &a, unsigned char *sA
     if (i < a.ns) {
       u64 y = shoup(x[k], a.inv[i], a.inv_s[i], a.sq[i]);
       if (a.has_add) y = addmod(y, a.src_add[i], a.sq[i]);
-      if (a.has_v) fix += __umul64hi(y, a.rdiv[i]);
+      if (a.has_v) fix += __umul64hi(y, a.rdiv[i]) + y * a.rdiv_hi[i];  // high word: b_i < 2^32 only
       const u32 lo = (u32)y, hi = (u32)(y >> 32);
       uint4 v;
       v.x = bytes_to_half2(lo, 0x4140);
@@ -456,6 +456,7 @@ static int launch_bconv_tc_ex(ckks_ctx *c, size_t key, const u64 *inv_host, cons
     a.inv_s[i] = inv_host[2 * i + 1];
     a.src_add[i] = src_add_host ? src_add_host[i] : 0;
     a.rdiv[i] = has_v ? rdiv_host[i] : 0;
+    a.rdiv_hi[i] = has_v ? rdiv_host[ns + i] : 0;
   }
   const unsigned __int128 two64 = (unsigned __int128)1 << 64;
   for (int t = 0; t < nt; ++t) {

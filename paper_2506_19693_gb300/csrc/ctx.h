@@ -40,7 +40,9 @@ struct ConvTables {
   //   sinv[l] pairs    S^-1 mod q_t
   //   qlinv[l] pairs   q_l^-1 mod q_t
   //   pmod pair        [P]_{q_l}
-  //   rdiv[K+1]        floor(2^96 / s_i): y_i / s_i in 32.32 fixed point
+  //   rdiv[2][K+1]     R_i = floor(2^96 / s_i) as low words, then high words
+  //                    (R_i >= 2^64 only for s_i < 2^32): y_i / s_i in 32.32
+  //                    fixed point is y_i R_hi + floor(y_i R_lo / 2^64), exact
   //   negs[l]          -S mod q_t (removes the overflow estimate v S)
   std::vector<size_t> mdr_off;     // index l (0 unused)
   // decode: Garner constants inv(q_j) mod q_i  [n_q][n_q] and half-Q digits per level
@@ -195,8 +197,9 @@ int ew_wire(ckks_ctx *c, const WireLayout &L, unsigned char *const *wire, u64 *c
 // ---- tensor-core basis conversion (bconv_tc.cu) ----
 // src_add_host [ns] / dst_sub_host [nt] (or null): constants added to y_i
 // mod b_i before the products / subtracted from the result mod t.
-// rdiv_host [ns] / negs_host [nt] (or null): overflow removal, y_t += v negs_t
-// with v = floor(sum_i floor(y_i rdiv_i / 2^64) / 2^32).
+// rdiv_host [2][ns] / negs_host [nt] (or null): overflow removal, y_t += v negs_t
+// with v = floor(sum_i floor(y_i R_i / 2^64) / 2^32), R_i = rdiv_host[ns + i] 2^64
+// + rdiv_host[i] = floor(2^96 / b_i).
 int launch_bconv_tc(ckks_ctx *c, size_t key, const u64 *inv_host, const u64 *tab_host, int ns, int nt,
                     const int *src_mod, const int *dst_mod, const int *dst_pos, const u64 *const *src,
                     u64 *const *dst, int np, const u64 *src_add_host, const u64 *dst_sub_host,

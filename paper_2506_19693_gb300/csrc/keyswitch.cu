@@ -50,9 +50,9 @@ struct BConvArgs {
   u64 *dst[MAX_CTS];               // output polynomial base (limb positions dst_pos)
   const u64 *src_add = nullptr;    // [ns] or null: added to y_i mod b_i
   const u64 *dst_sub = nullptr;    // [nt] or null: subtracted from y_t mod t
-  // overflow removal (or null): v = floor(sum_i floor(y_i rdiv_i / 2^64) / 2^32),
+  // overflow removal (or null): v = floor(sum_i floor(y_i R_i / 2^64) / 2^32),
   // the overflow sum_i y_i / s_i in 32.32 fixed point; y_t += v negs_t
-  const u64 *rdiv = nullptr;       // [ns] floor(2^96 / b_i)
+  const u64 *rdiv = nullptr;       // [2][ns]: R_i = floor(2^96 / b_i), low then high words
   const u64 *negs = nullptr;       // [nt] -B mod t
 };
 
@@ -77,7 +77,8 @@ __global__ void __launch_bounds__(TPB) k_bconv(const BConvArgs a) {
     const u64 q = a.mods[a.src_mod[i]].q;
     y[i] = shoup(src[(size_t)i * a.n + k], a.inv[2 * i], a.inv[2 * i + 1], q);
     if (a.src_add) y[i] = addmod(y[i], __ldg(a.src_add + i), q);
-    if (a.rdiv) fix += __umul64hi(y[i], __ldg(a.rdiv + i));
+    // y_i R_hi is nonzero only for b_i < 2^32, where y_i < 2^32 keeps it below 2^44
+    if (a.rdiv) fix += __umul64hi(y[i], __ldg(a.rdiv + i)) + y[i] * __ldg(a.rdiv + NS + i);
   }
   const u64 v = fix >> 32;
   u64 *dst = a.dst[p];
@@ -286,7 +287,7 @@ struct MdrLayout {
     qlinv = sinv + 2 * (size_t)l;
     pmod = qlinv + 2 * (size_t)l;
     rdiv = pmod + 2;
-    negs = rdiv + (K + 1);
+    negs = rdiv + 2 * (size_t)(K + 1);
   }
 };
 

@@ -689,7 +689,7 @@ struct FusedArgs {
   unsigned char pos_mod[MAX_MODS];     // modulus of target limb position
   const u64 *inv[F_MAXD];              // [ns] Shoup pairs: [Bhat_i^-1]_{b_i}
   const u64 *tab[F_MAXD];              // [nt][ns]: Bhat_i mod t
-  const u64 *src_add, *dst_sub, *rdiv, *negs;  // MERGED: [ns], [nt], [ns], [nt]
+  const u64 *src_add, *dst_sub, *rdiv, *negs;  // MERGED: [ns], [nt], [2][ns] (low, high words), [nt]
   const u64 *src[MAX_CTS];
   u64 *dst[MAX_CTS];
 };
@@ -794,13 +794,13 @@ __global__ void __launch_bounds__(F_THREADS, 2) k_conv_fused(const FusedArgs a) 
         for (int e = 0; e < FH; ++e) hi[e] = lo[e] = fix[e] = 0;
         for (int i = 0; i < ns; ++i) {
           const u64 cf = crow[i];
-          const u64 rd = MERGED ? __ldg(a.rdiv + i) : 0;
+          const u64 rd = MERGED ? __ldg(a.rdiv + i) : 0, rd_hi = MERGED ? __ldg(a.rdiv + ns + i) : 0;
           const u64 *yi = sy + i * T;
 #pragma unroll
           for (int e = 0; e < FH; ++e) {
             const u64 y = yi[fpad(r0 + ((h + e) << S2), c)];
             mac128(hi[e], lo[e], y, cf);
-            if (MERGED) fix[e] += __umul64hi(y, rd);
+            if (MERGED) fix[e] += __umul64hi(y, rd) + y * rd_hi;
           }
         }
 #pragma unroll

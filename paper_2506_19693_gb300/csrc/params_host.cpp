@@ -227,7 +227,9 @@ int build_tables(ckks_ctx *c) {
     u64 pm = 1;
     for (int k = 0; k < K; ++k) pm = host_mulmod(pm, c->mod[c->n_q + k] % c->mod[l], c->mod[l]);
     push_pair(v, pm, c->mod[l]);
-    for (int i = 0; i <= K; ++i) v.push_back((u64)(((unsigned __int128)1 << 96) / smod[i]));  // R_i
+    for (int i = 0; i <= K; ++i) v.push_back((u64)(((unsigned __int128)1 << 96) / smod[i]));  // R_i low words
+    for (int i = 0; i <= K; ++i)  // R_i high words: nonzero only for s_i < 2^32
+      v.push_back((u64)((((unsigned __int128)1 << 96) / smod[i]) >> 64));
     for (int tt = 0; tt < l; ++tt) {                                                          // -S mod q_t
       const u64 qt = c->mod[tt], sm = shat_mod(-1, qt);
       v.push_back(sm ? qt - sm : 0);

@@ -27,9 +27,10 @@ def _pair(w, rot=ROT_STEPS, conj=True):
     return ctx, orc
 
 
-@pytest.fixture(scope="module", params=["toy", "small", "mid", "n15", "n17"])
+@pytest.fixture(scope="module", params=["toy", "small", "mid", "n15", "n17", "smallq"])
 def pair(request):
-    w = {"toy": si.TOY, "small": si.SMALL, "mid": si.MID, "n15": si.N15, "n17": si.N17}[request.param]
+    w = {"toy": si.TOY, "small": si.SMALL, "mid": si.MID, "n15": si.N15, "n17": si.N17,
+         "smallq": si.SMALLQ}[request.param]
     ctx, orc = _pair(w)
     yield w, ctx, orc
     ctx.close()
@@ -46,6 +47,13 @@ def _enc_both(w, ctx, orc, seed, level=None, count=1):
         cg = ctx.encrypt(ctx.pt_from_int(m, level), level, scale, 1000 * seed + i)
         out.append((z[i], cg, co))
     return out
+
+
+def _noise_bound(w):
+    """Slot-error bound for a fresh or once key-switched ciphertext: 2^-20 at
+    scales of 2^40 and above; at a smaller scale the same noise, about 2^20
+    below the scale at these ring sizes, is a larger fraction of the message."""
+    return 2.0 ** -min(20.0, w.log2_scale - 20.0)
 
 
 def _same(ctx, cg, co):
@@ -186,7 +194,7 @@ def test_hoisted_rotations_bit_exact(pair):
         for j in range(len(steps)):
             _same(ctx, outs[j * 2 + i], want[j])
     got = ctx.decrypt_decode(outs[0])
-    assert np.max(np.abs(got - np.roll(za, -1))) < 2.0 ** -20
+    assert np.max(np.abs(got - np.roll(za, -1))) < _noise_bound(w)
 
 
 def test_encode_matches_oracle_within_fp64_rounding(pair):
@@ -218,7 +226,7 @@ def test_decode_matches_oracle(pair):
     got = ctx.decrypt_decode(a)
     want = orc.decrypt_decode(ao)
     assert np.max(np.abs(got - want)) <= 2.0 ** -40 * 8
-    assert np.max(np.abs(got - z)) < 2.0 ** -20
+    assert np.max(np.abs(got - z)) < _noise_bound(w)
 
 
 def test_toy_mult_error_bound():

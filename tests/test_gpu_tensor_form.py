@@ -35,9 +35,9 @@ def _enc(w, ctx, orc, seed, count):
     return out
 
 
-@pytest.mark.parametrize("name", ["toy", "small", "mid", "n17"])
+@pytest.mark.parametrize("name", ["toy", "small", "mid", "n17", "smallq"])
 def test_tensor_form_bit_exact_vs_oracle(name):
-    w = {"toy": si.TOY, "small": si.SMALL, "mid": si.MID, "n17": si.N17}[name]
+    w = {"toy": si.TOY, "small": si.SMALL, "mid": si.MID, "n17": si.N17, "smallq": si.SMALLQ}[name]
     ctx, orc = _pair(w)
     try:
         (a, ao), (b, bo) = _enc(w, ctx, orc, 31, 2)
