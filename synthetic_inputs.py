@@ -64,6 +64,10 @@ MID = Workload("n8192_L8_dnum3", 13, (61,) + (55,) * 7, (61,) * 3, 3, 55.0,
 # merged rescale's overflow estimate.  Not secure; scale 2^26.
 SMALLQ = Workload("n4096_q31_28x3_p31x2_dnum2", 12, (31, 28, 28, 28), (31, 31), 2, 26.0,
                   batch=2, rot_steps=(1, -1))
+# The largest primes the parameter check admits (62 bits: strict forward
+# butterflies, the inverse with exact quotients) mixed with 60 and 55 bits.
+BIGQ = Workload("n4096_q62_60_62_55_p62x2_dnum2", 12, (62, 60, 62, 55), (62, 62), 2, 50.0,
+                batch=2, rot_steps=(1, -1))
 # N = 2^15, the other ring degree of the uneven batch, on a short chain of the
 # same prime sizes (the primes are shared with N = 2^16: all = 1 mod 2^17)
 N15 = Workload("n32768_L6_dnum3", 15, (61,) + (55,) * 5, (61,) * 2, 3, 55.0,

@@ -38,11 +38,11 @@ def _enc(w, ctx, orc, seed, count, level=None):
     return out
 
 
-@pytest.mark.parametrize("name", ["toy", "small", "mid", "n15", "n17", "smallq"])
+@pytest.mark.parametrize("name", ["toy", "small", "mid", "n15", "n17", "smallq", "bigq"])
 def test_fused_form_bit_exact_vs_oracle(name):
     import paper_2506_19693_gb300 as ck
     w = {"toy": si.TOY, "small": si.SMALL, "mid": si.MID, "n15": si.N15, "n17": si.N17,
-         "smallq": si.SMALLQ}[name]
+         "smallq": si.SMALLQ, "bigq": si.BIGQ}[name]
     ctx, orc = _pair(w)
     try:
         (a, ao), (b, bo) = _enc(w, ctx, orc, 31, 2)

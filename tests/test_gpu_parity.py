@@ -27,10 +27,10 @@ def _pair(w, rot=ROT_STEPS, conj=True):
     return ctx, orc
 
 
-@pytest.fixture(scope="module", params=["toy", "small", "mid", "n15", "n17", "smallq"])
+@pytest.fixture(scope="module", params=["toy", "small", "mid", "n15", "n17", "smallq", "bigq"])
 def pair(request):
     w = {"toy": si.TOY, "small": si.SMALL, "mid": si.MID, "n15": si.N15, "n17": si.N17,
-         "smallq": si.SMALLQ}[request.param]
+         "smallq": si.SMALLQ, "bigq": si.BIGQ}[request.param]
     ctx, orc = _pair(w)
     yield w, ctx, orc
     ctx.close()

@@ -35,9 +35,10 @@ def _enc(w, ctx, orc, seed, count):
     return out
 
 
-@pytest.mark.parametrize("name", ["toy", "small", "mid", "n17", "smallq"])
+@pytest.mark.parametrize("name", ["toy", "small", "mid", "n17", "smallq", "bigq"])
 def test_tensor_form_bit_exact_vs_oracle(name):
-    w = {"toy": si.TOY, "small": si.SMALL, "mid": si.MID, "n17": si.N17, "smallq": si.SMALLQ}[name]
+    w = {"toy": si.TOY, "small": si.SMALL, "mid": si.MID, "n17": si.N17, "smallq": si.SMALLQ,
+         "bigq": si.BIGQ}[name]
     ctx, orc = _pair(w)
     try:
         (a, ao), (b, bo) = _enc(w, ctx, orc, 31, 2)
