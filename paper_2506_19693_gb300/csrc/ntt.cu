@@ -251,14 +251,24 @@ __device__ __forceinline__ void fwd_b_body(const NttParams &prm, u64 *sm, int mi
 #pragma unroll
     for (int e = 0; e < (1 << U1); ++e) sm[padb(rr * BROW + l0 + (e << U2))] = v[e];
   }
+  // one 16-value group per thread in the second phase: its 15 twiddles (one
+  // per block of each of the last four stages, all distinct per thread, from
+  // L2) are loaded before the barrier, so their latency overlaps it
+  static_assert(THREADS == (RB << U1), "one group per thread");
+  const int g = threadIdx.x % (1 << U1), rr = threadIdx.x / (1 << U1), b = row0 + rr;
+  ulonglong2 twv[(1 << U2) - 1];
+  {
+    const u32 n16 = prm.n / 16, m = ((u32)b << U1) + g;
+    const ulonglong2 *twr = prm.tw_row + (size_t)mi * 15 * n16;
+#pragma unroll
+    for (int k = 0; k < (1 << U2) - 1; ++k) twv[k] = __ldg(&twr[(size_t)k * n16 + m]);
+  }
   __syncthreads();
-  for (int x = threadIdx.x; x < (RB << U1); x += THREADS) {
-    const int g = x % (1 << U1), rr = x / (1 << U1), b = row0 + rr;
+  {
     u64 v[1 << U2];
 #pragma unroll
     for (int e = 0; e < (1 << U2); ++e) v[e] = sm[padb(rr * BROW + (g << U2) + e)];
-    fwd_step_row<U2, LOOSE>(v, ((u32)b << U1) + g, prm.tw_row + (size_t)mi * 15 * (prm.n / 16), prm.n / 16, q,
-                            twoq);
+    fwd_step_t<U2, LOOSE>(v, [&](int s, int i) { return twv[(1 << s) - 1 + i]; }, q, twoq);
     const u64 one_s = LOOSE ? prm.mods[mi].one_s : 0;
 #pragma unroll
     for (int e = 0; e < (1 << U2); ++e) {
@@ -316,14 +326,21 @@ __device__ __forceinline__ void inv_b_body(const NttParams &prm, u64 *sm, int mi
       sm[o + 1] = t[k].y;
     }
   }
-  __syncthreads();
-  for (int x = threadIdx.x; x < (RB << U1); x += THREADS) {
-    const int g = x % (1 << U1), rr = x / (1 << U1), b = row0 + rr;
+  // one 16-value group per thread in the row stages: its 15 distinct twiddles
+  // (from L2) are loaded before the barrier, so their latency overlaps it
+  static_assert(THREADS == (RB << U1), "one group per thread");
+  {
+    const int g = threadIdx.x % (1 << U1), rr = threadIdx.x / (1 << U1), b = row0 + rr;
+    ulonglong2 twv[(1 << U2) - 1];
+    const u32 n16 = prm.n / 16, m = ((u32)b << U1) + g;
+    const ulonglong2 *twr = prm.tw_row + (size_t)mi * 15 * n16;
+#pragma unroll
+    for (int k = 0; k < (1 << U2) - 1; ++k) twv[k] = __ldg(&twr[(size_t)k * n16 + m]);
+    __syncthreads();
     u64 v[1 << U2];
 #pragma unroll
     for (int e = 0; e < (1 << U2); ++e) v[e] = sm[padb(rr * BROW + (g << U2) + e)];
-    inv_step_row<U2, APPROX>(v, ((u32)b << U1) + g, prm.tw_row + (size_t)mi * 15 * (prm.n / 16), prm.n / 16, q,
-                             twoq);
+    inv_step_t<U2, APPROX, 0>(v, [&](int s, int i) { return twv[(1 << s) - 1 + i]; }, q, twoq);
 #pragma unroll
     for (int e = 0; e < (1 << U2); ++e) sm[padb(rr * BROW + (g << U2) + e)] = v[e];
   }
