@@ -88,6 +88,10 @@ def _load():
         "oc_galois_elt": (ctypes.c_uint64, [V, ctypes.c_int64]),
         "oc_pt_from_signed": (None, [V, _i64p, P, _u64p]),
         "oc_encrypt": (P, [V, _u64p, P, ctypes.c_uint64, _u64p]),
+        "oc_gen_public_key": (P, [V]),
+        "oc_public_key": (P, [V, _u64p]),
+        "oc_pk_mask": (None, [ctypes.c_uint64, ctypes.c_uint64, _i64p]),
+        "oc_encrypt_pk": (P, [V, _u64p, P, ctypes.c_uint64, _u64p]),
         "oc_enc_error": (None, [V, ctypes.c_uint64, _i64p]),
         "oc_decrypt": (P, [V, _u64p, P, _u64p]),
         "oc_add": (None, [V, _u64p, _u64p, P, _u64p]),
@@ -341,6 +345,30 @@ class Oracle:
         ct = np.zeros((2, level + 1, self.n), dtype=np.uint64)
         if self._lib.oc_encrypt(self._c, _p64(pt), level, enc_seed, _p64(ct)) != 0:
             raise RuntimeError("encrypt failed (keygen first?)")
+        return OCt(ct, level, scale)
+
+    def gen_public_key(self) -> None:
+        """pk = ([-a s + e]_Q, a) at the top level (C5, pk form); keygen first."""
+        if self._lib.oc_gen_public_key(self._c) != 0:
+            raise RuntimeError("public key generation failed (keygen first?)")
+
+    def public_key(self) -> np.ndarray:
+        out = np.zeros((2, self.n_q, self.n), dtype=np.uint64)
+        if self._lib.oc_public_key(self._c, _p64(out)) != 0:
+            raise RuntimeError("no public key")
+        return out
+
+    def pk_mask(self, enc_seed: int) -> np.ndarray:
+        v = np.zeros(self.n, dtype=np.int64)
+        self._lib.oc_pk_mask(enc_seed, self.n, _pi64(v))
+        return v
+
+    def encrypt_pk(self, pt: np.ndarray, level: int, scale: float, enc_seed: int) -> OCt:
+        """ct = ([v b + m + e0]_Q, [v a + e1]_Q) with the public key (b, a)."""
+        pt = np.ascontiguousarray(pt[: level + 1], dtype=np.uint64)
+        ct = np.zeros((2, level + 1, self.n), dtype=np.uint64)
+        if self._lib.oc_encrypt_pk(self._c, _p64(pt), level, enc_seed, _p64(ct)) != 0:
+            raise RuntimeError("public-key encryption failed (gen_public_key first?)")
         return OCt(ct, level, scale)
 
     def enc_error(self, enc_seed: int) -> np.ndarray:

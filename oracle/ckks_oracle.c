@@ -15,7 +15,7 @@
  * inside the scheme is a reading of the textbook RNS-CKKS definitions; each
  * reading is named in a comment where it is used:
  *   C1 primes, C2 roots and transform order, C4 seeded randomness,
- *   C5 encryption, C6 tensor/relinearisation, C7 hybrid key-switch gadget,
+ *   C5 encryption (secret- and public-key forms), C6 tensor/relinearisation, C7 hybrid key-switch gadget,
  *   C8 ModUp, C9 ModDown, C10 rescale, C11 automorphisms.
  */
 #include <math.h>
@@ -96,7 +96,8 @@ static u64 sm_mix(u64 z) {
 static u64 sm_draw(u64 key, u64 c) { return sm_mix(key + (c + 1) * SM_GAMMA); }
 static u64 sm_stream(u64 seed, u64 tag, u64 idx) { return sm_draw(sm_draw(seed, tag), idx); }
 
-enum { TAG_SECRET = 1, TAG_KEY_A = 2, TAG_KEY_E = 3, TAG_ENC_A = 4, TAG_ENC_E = 5 };
+enum { TAG_SECRET = 1, TAG_KEY_A = 2, TAG_KEY_E = 3, TAG_ENC_A = 4, TAG_ENC_E = 5,
+       TAG_PK_A = 6, TAG_PK_E = 7, TAG_PKENC_V = 8, TAG_PKENC_E0 = 9, TAG_PKENC_E1 = 10 };
 
 u64 oc_splitmix_draw(u64 key, u64 c) { return sm_draw(key, c); }
 
@@ -143,6 +144,7 @@ typedef struct {
   u64 *s_ntt;         /* [n_q + n_p][N] */
   u64 key_seed;
   okey *keys;
+  u64 *pk;            /* [2][n_q][N] public key (b, a), NTT domain, or NULL */
 } oc_ctx;
 
 /* C1: for each bit size b scan t = 2^b + 1 - m * 2^e, m = 1, 2, ..., with
@@ -204,6 +206,7 @@ void oc_destroy(oc_ctx *c) {
   while (k) { okey *nx = k->next; free(k->data); free(k); k = nx; }
   free(c->s_coeff);
   free(c->s_ntt);
+  free(c->pk);
   free(c);
 }
 
@@ -398,6 +401,8 @@ int oc_keygen(oc_ctx *c, u64 seed) {
   c->keys = NULL;
   free(c->s_coeff);
   free(c->s_ntt);
+  free(c->pk);
+  c->pk = NULL;
   c->key_seed = seed;
   c->s_coeff = (i64 *)malloc(sizeof(i64) * n);
   c->s_ntt = (u64 *)malloc(sizeof(u64) * (u64)ext * n);
@@ -498,6 +503,97 @@ int oc_encrypt(const oc_ctx *c, const u64 *pt, int level, u64 enc_seed, u64 *ct)
 void oc_enc_error(const oc_ctx *c, u64 enc_seed, i64 *e) {
   u64 ke = sm_stream(enc_seed, TAG_ENC_E, 0);
   for (u64 x = 0; x < c->n; x++) e[x] = gauss_sample(ke, x, c->sigma, c->e_bound);
+}
+
+/* Public key (C5, pk form; Sec. 3 writes encryption as E(pk, .)): the
+ * secret-key encryption of 0 at the top level, drawn from the key seed's own
+ * streams: pk = ([-a s + e]_Q, a) over q_0..q_{n_q-1}. */
+int oc_gen_public_key(oc_ctx *c) {
+  if (!c->have_secret) return -1;
+  u64 n = c->n;
+  int nl = c->n_q;
+  u64 *pk = (u64 *)malloc(sizeof(u64) * 2 * (u64)nl * n);
+  u64 ka = sm_stream(c->key_seed, TAG_PK_A, 0), ke = sm_stream(c->key_seed, TAG_PK_E, 0);
+  i64 *e = (i64 *)malloc(sizeof(i64) * n);
+  for (u64 x = 0; x < n; x++) e[x] = gauss_sample(ke, x, c->sigma, c->e_bound);
+  u64 *er = (u64 *)malloc(sizeof(u64) * (u64)nl * n);
+  int mods[OC_MAXMOD];
+  q_basis(nl, mods);
+  from_signed(c, e, nl, mods, er);
+  oc_ntt(c, er, nl, mods);
+  u64 *b = pk, *a = pk + (u64)nl * n;
+  for (int t = 0; t < nl; t++) {
+    u64 q = c->mod[t];
+    for (u64 x = 0; x < n; x++) {
+      u64 idx = (u64)t * n + x;
+      u64 av = uniform_mod(ka, idx, q);
+      a[idx] = av;
+      b[idx] = submod(er[idx], mulmod(av, c->s_ntt[idx], q), q);
+    }
+  }
+  free(e);
+  free(er);
+  free(c->pk);
+  c->pk = pk;
+  return 0;
+}
+
+int oc_public_key(const oc_ctx *c, u64 *out) {
+  if (!c->pk) return -1;
+  memcpy(out, c->pk, sizeof(u64) * 2 * (u64)c->n_q * c->n);
+  return 0;
+}
+
+/* The masking polynomial of public-key encryption: each coefficient 0 with
+ * probability 1/2 and +1, -1 with probability 1/4 each, from the low two bits
+ * of one draw (0, 1 -> 0; 2 -> +1; 3 -> -1). */
+void oc_pk_mask(u64 enc_seed, u64 n, i64 *v) {
+  u64 kv = sm_stream(enc_seed, TAG_PKENC_V, 0);
+  for (u64 x = 0; x < n; x++) {
+    u64 r = sm_draw(kv, x) & 3;
+    v[x] = r < 2 ? 0 : (r == 2 ? 1 : -1);
+  }
+}
+
+/* Public-key encryption (C5, pk form): v the mask above, e0 and e1 Gaussian,
+ * ct = ([v b + m + e0]_Q, [v a + e1]_Q) over q_0..q_level, with (b, a) = pk
+ * restricted to those primes; the products are negacyclic, taken as
+ * point-wise products of NTT-domain residues. */
+int oc_encrypt_pk(const oc_ctx *c, const u64 *pt, int level, u64 enc_seed, u64 *ct) {
+  if (!c->pk || level < 0 || level >= c->n_q) return -1;
+  u64 n = c->n;
+  int nl = level + 1;
+  int mods[OC_MAXMOD];
+  q_basis(nl, mods);
+  i64 *w = (i64 *)malloc(sizeof(i64) * n);
+  u64 *vr = (u64 *)malloc(sizeof(u64) * (u64)nl * n);
+  u64 *e0r = (u64 *)malloc(sizeof(u64) * (u64)nl * n);
+  u64 *e1r = (u64 *)malloc(sizeof(u64) * (u64)nl * n);
+  oc_pk_mask(enc_seed, n, w);
+  from_signed(c, w, nl, mods, vr);
+  oc_ntt(c, vr, nl, mods);
+  u64 k0 = sm_stream(enc_seed, TAG_PKENC_E0, 0), k1 = sm_stream(enc_seed, TAG_PKENC_E1, 0);
+  for (u64 x = 0; x < n; x++) w[x] = gauss_sample(k0, x, c->sigma, c->e_bound);
+  from_signed(c, w, nl, mods, e0r);
+  oc_ntt(c, e0r, nl, mods);
+  for (u64 x = 0; x < n; x++) w[x] = gauss_sample(k1, x, c->sigma, c->e_bound);
+  from_signed(c, w, nl, mods, e1r);
+  oc_ntt(c, e1r, nl, mods);
+  const u64 *b = c->pk, *a = c->pk + (u64)c->n_q * n;
+  u64 *c0 = ct, *c1 = ct + (u64)nl * n;
+  for (int t = 0; t < nl; t++) {
+    u64 q = c->mod[t];
+    for (u64 x = 0; x < n; x++) {
+      u64 idx = (u64)t * n + x;
+      c0[idx] = addmod(addmod(mulmod(vr[idx], b[idx], q), pt[idx], q), e0r[idx], q);
+      c1[idx] = addmod(mulmod(vr[idx], a[idx], q), e1r[idx], q);
+    }
+  }
+  free(w);
+  free(vr);
+  free(e0r);
+  free(e1r);
+  return 0;
 }
 
 /* m' = c0 + c1 s (NTT domain) over q_0..q_level */

@@ -222,6 +222,74 @@ def test_decrypt_of_encrypt_is_message_plus_small_error(tiny_oracle):
     assert err == [int(v) for v in o.enc_error(99)]
 
 
+def _centred_poly(o, res, level):
+    return o.crt_centred(o.intt(res, list(range(level + 1))), level)
+
+
+def test_public_key_relation_by_big_integers(tiny_oracle):
+    """pk = (b, a) with b + a s = e small over Q (C5, pk form)."""
+    o = tiny_oracle
+    n, level = o.n, o.n_q - 1
+    o.gen_public_key()
+    pk = o.public_key()
+    s = [int(v) for v in o.secret()]
+    Q = math.prod(o.q)
+    b = _centred_poly(o, pk[0], level)
+    a = _centred_poly(o, pk[1], level)
+    e = [centred(x + y, Q) for x, y in zip(b, negacyclic_mul_int(a, s, n))]
+    assert max(abs(v) for v in e) <= 19 and any(e)
+    assert max(abs(v) for v in a) > Q // 8  # a is spread over Z_Q, not small
+
+
+@pytest.mark.parametrize("level", [3, 1])
+def test_public_key_encryption_by_big_integers(tiny_oracle, level):
+    """ct = (v b + m + e0, v a + e1) over q_0..q_level with the mask v the
+    library draws, e0 and e1 small; so c0 + c1 s = m + v e + e0 + e1 s."""
+    o = tiny_oracle
+    n = o.n
+    o.gen_public_key()
+    pk = o.public_key()
+    rng = np.random.default_rng(11)
+    m = rng.integers(-2 ** 30, 2 ** 30, size=n).astype(np.int64)
+    ct = o.encrypt_pk(o.pt_from_int(m, level), level, 1.0, 123)
+    v = [int(x) for x in o.pk_mask(123)]
+    assert set(v) <= {-1, 0, 1}
+    Ql = math.prod(o.q[: level + 1])
+    c0 = _centred_poly(o, ct.data[0], level)
+    c1 = _centred_poly(o, ct.data[1], level)
+    b = _centred_poly(o, np.ascontiguousarray(pk[0][: level + 1]), level)
+    a = _centred_poly(o, np.ascontiguousarray(pk[1][: level + 1]), level)
+    e0 = [centred(x - y - int(mm), Ql) for x, y, mm in zip(c0, negacyclic_mul_int(v, b, n), m)]
+    e1 = [centred(x - y, Ql) for x, y in zip(c1, negacyclic_mul_int(v, a, n))]
+    assert max(abs(x) for x in e0) <= 19 and max(abs(x) for x in e1) <= 19
+    assert any(e0) and any(e1) and e0 != e1  # both errors present, from separate streams
+    s = [int(x) for x in o.secret()]
+    dec = [centred(x + y, Ql) for x, y in zip(c0, negacyclic_mul_int(c1, s, n))]
+    noise = [d - int(mm) for d, mm in zip(dec, m)]
+    assert max(abs(x) for x in noise) <= 19 * (n + 1 + 8)
+
+
+def test_public_key_mask_distribution():
+    """P(0) = 1/2, P(+1) = P(-1) = 1/4, within five standard deviations."""
+    o = oracle.Oracle(12, (50,), (51,), 1, h=64, sigma=3.2)
+    v = np.concatenate([o.pk_mask(seed) for seed in range(4)])
+    n = len(v)
+    for val, p in ((0, 0.5), (1, 0.25), (-1, 0.25)):
+        cnt = int(np.sum(v == val))
+        assert abs(cnt - p * n) <= 5 * math.sqrt(n * p * (1 - p)), (val, cnt)
+
+
+def test_public_key_encryption_decodes(toy_oracle):
+    o = toy_oracle
+    o.gen_public_key()
+    scale = 2.0 ** 40
+    z = si.messages(21, 1, o.n // 2)[0]
+    level = o.n_q - 1
+    ct = o.encrypt_pk(o.pt_from_int(o.encode(z, scale), level), level, scale, 77)
+    # noise v e + e0 + e1 s: at most a few thousand per coefficient, over 2^40
+    assert np.max(np.abs(o.decrypt_decode(ct) - z)) < 2.0 ** -20
+
+
 # ---------------------------------------------------------------- keys (C7)
 def test_switching_key_relation_by_big_integers(tiny_oracle):
     o = tiny_oracle
