@@ -168,7 +168,8 @@ int ckks_debug_tc_expire(ckks_ctx *ctx, uint64_t wait_ns);
  * (left rotation by k, g = 5^(k mod N/2) mod 2N), the conjugation key when
  * want_conj, and, when want_boot, the conjugation key and every rotation key
  * the bootstrapping circuit uses (ckks_boot_rotation_steps).  Randomness:
- * counter-based SplitMix64 keyed by seed (reading C4).  Replaces earlier keys. */
+ * counter-based SplitMix64 keyed by seed (reading C4).  Replaces earlier keys,
+ * the public key included. */
 int ckks_keygen_from_seed(ckks_ctx *ctx, uint64_t seed, const int32_t *rot_steps, int n_rot,
                           int want_conj, int want_boot);
 /* Key compression (reading C22; no paper counterpart).  With on = 1, keys
@@ -230,6 +231,24 @@ int ckks_encrypt(ckks_ctx *ctx, const uint64_t *pt_dev, uint32_t level, double s
                  uint64_t enc_seed, ckks_ct *out);
 /* pt_dev (uint64[level+1][N]) = c0 + c1 s, NTT domain. */
 int ckks_decrypt(ckks_ctx *ctx, const ckks_ct *ct, uint64_t *pt_dev);
+
+/* Public key (Sec. 3 writes encryption as E(pk, .); reading C5, pk form):
+ * pk = ([-a s + e]_Q, a) over q_0..q_{n_q-1}, NTT domain, the secret-key
+ * encryption of 0 with a and e drawn from the key seed's own streams.  Needs
+ * the secret (CKKS_E_NOKEY before ckks_keygen_from_seed); CKKS_E_STATE during
+ * graph capture.  Kept on the device until the next key generation. */
+int ckks_keygen_public(ckks_ctx *ctx);
+/* Copy the public key to host memory: out_host uint64[2][n_q][N] (b, then a),
+ * NTT domain.  CKKS_E_NOKEY before ckks_keygen_public. */
+int ckks_public_key_export(ckks_ctx *ctx, uint64_t *out_host);
+/* Public-key encryption (reading C5, pk form): with the mask v (each
+ * coefficient 0 with probability 1/2, +1 and -1 with 1/4 each) and rounded
+ * Gaussian e0, e1, all from enc_seed's streams,
+ *   ct = ([v b + m + e0], [v a + e1]) over q_0..q_level,
+ * products negacyclic (point-wise in the NTT domain).  Arguments as
+ * ckks_encrypt; CKKS_E_NOKEY without a public key. */
+int ckks_encrypt_pk(ckks_ctx *ctx, const uint64_t *pt_dev, uint32_t level, double scale,
+                    uint64_t enc_seed, ckks_ct *out);
 
 /* ---- evaluation (Eq. add, sub, mult; Sec. 3) ----------------------------- */
 

@@ -82,6 +82,9 @@ SIGNATURES = {
     "ckks_ntt": (_I, [_V, _V, ctypes.c_uint32, ctypes.c_uint32, _I]),
     "ckks_encrypt": (_I, [_V, _V, ctypes.c_uint32, _D, _U64, _CTP]),
     "ckks_decrypt": (_I, [_V, _CTP, _V]),
+    "ckks_keygen_public": (_I, [_V]),
+    "ckks_public_key_export": (_I, [_V, _V]),
+    "ckks_encrypt_pk": (_I, [_V, _V, ctypes.c_uint32, _D, _U64, _CTP]),
     "ckks_add": (_I, [_V, _CTP, _CTP, _CTP]),
     "ckks_sub": (_I, [_V, _CTP, _CTP, _CTP]),
     "ckks_mul_plain": (_I, [_V, _CTP, _V, _D, _CTP]),
@@ -390,6 +393,24 @@ class Context:
         h = ct.handle(self.log_n)
         _check(self.lib.ckks_encrypt(self._h, pt.data_ptr(), level, scale, enc_seed, ctypes.byref(h)),
                "ckks_encrypt")
+        return ct
+
+    def keygen_public(self) -> None:
+        """The public key pk = ([-a s + e]_Q, a) at the top level (after keygen)."""
+        _check(self.lib.ckks_keygen_public(self._h), "ckks_keygen_public")
+
+    def public_key(self) -> np.ndarray:
+        """The public key as host uint64[2][n_q][N] (b, then a), NTT domain."""
+        out = np.zeros((2, self.n_q, self.n), dtype=np.uint64)
+        _check(self.lib.ckks_public_key_export(self._h, out.ctypes.data), "ckks_public_key_export")
+        return out
+
+    def encrypt_pk(self, pt, level: int, scale: float, enc_seed: int, n_limbs: int | None = None) -> Ciphertext:
+        """Public-key encryption: ct = (v b + m + e0, v a + e1) over q_0..q_level."""
+        ct = self.new_ct(n_limbs or level + 1, level, scale)
+        h = ct.handle(self.log_n)
+        _check(self.lib.ckks_encrypt_pk(self._h, pt.data_ptr(), level, scale, enc_seed, ctypes.byref(h)),
+               "ckks_encrypt_pk")
         return ct
 
     def decrypt(self, ct: Ciphertext):

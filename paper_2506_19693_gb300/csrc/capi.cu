@@ -53,6 +53,8 @@ void free_keys(ckks_ctx *c) {
   c->relin.data = nullptr;
   for (auto &kv : c->galois) cudaFree(kv.second.data);
   c->galois.clear();
+  if (c->d_pk) cudaFree(c->d_pk);
+  c->d_pk = nullptr;
 }
 
 size_t full_key_words(const ckks_ctx *c) { return (size_t)c->n_digits * 2 * (c->n_q + c->n_p) * c->n; }
@@ -819,6 +821,96 @@ int ckks_encrypt(ckks_ctx *c, const uint64_t *pt, uint32_t level, double scale, 
   ea.c0[0] = out->data;
   ea.c1[0] = poly1(out, n);
   rc = ew_encrypt(c, ea, nl, 1);
+  if (rc) return rc;
+  out->level = level;
+  out->scale = scale;
+  out->is_ntt = 1;
+  out->log_n = c->log_n;
+  CK_CUDA(cudaStreamSynchronize(c->stream));
+  return CKKS_OK;
+}
+
+// Signed host coefficients (n each, `count` polynomials) -> NTT-domain
+// residues over q_0..q_{nl-1} at out + i * nl * N; uses the scratch after `out`.
+static int upload_small_polys(ckks_ctx *c, const std::vector<i64> &host, int count, int nl, u64 *out) {
+  const u32 n = c->n;
+  i64 *dev = reinterpret_cast<i64 *>(out + (size_t)count * nl * n);
+  CK_CUDA(cudaMemcpyAsync(dev, host.data(), sizeof(i64) * (size_t)count * n, cudaMemcpyHostToDevice, c->stream));
+  std::vector<const u64 *> src(count);
+  std::vector<u64 *> dst(count);
+  for (int i = 0; i < count; ++i) {
+    int rc = ew_signed_to_res(c, dev + (size_t)i * n, out + (size_t)i * nl * n, 0, nl);
+    if (rc) return rc;
+    src[i] = dst[i] = out + (size_t)i * nl * n;
+  }
+  int mods[MAX_MODS];
+  for (int l = 0; l < nl; ++l) mods[l] = l;
+  return launch_ntt(c, src.data(), dst.data(), count, nl, mods, false);
+}
+
+int ckks_keygen_public(ckks_ctx *c) {
+  if (!c) return CKKS_E_PARAM;
+  if (!c->have_secret) return CKKS_E_NOKEY;
+  if (c->capturing) return CKKS_E_STATE;
+  const u32 n = c->n;
+  const int nl = c->n_q;
+  if (!c->d_pk && cudaMalloc(&c->d_pk, sizeof(u64) * 2 * (size_t)nl * n) != cudaSuccess) {
+    cudaGetLastError();
+    return CKKS_E_OOM;
+  }
+  int rc = ensure_scratch(c, (size_t)nl * n + n);
+  if (rc) return rc;
+  std::vector<i64> e(n);
+  sample_gaussian(sm_stream(c->key_seed, TAG_PK_E, 0), n, c->sigma, c->e_bound, e.data());
+  rc = upload_small_polys(c, e, 1, nl, c->scratch);
+  if (rc) return rc;
+  // the secret-key encryption of 0: b = e - a s, a uniform from the key seed
+  CK_CUDA(cudaMemsetAsync(c->d_pk, 0, sizeof(u64) * (size_t)nl * n, c->stream));
+  EncArgs ea;
+  ea.key_a[0] = sm_stream(c->key_seed, TAG_PK_A, 0);
+  ea.pt[0] = c->d_pk;
+  ea.err[0] = c->scratch;
+  ea.c0[0] = c->d_pk;
+  ea.c1[0] = c->d_pk + (size_t)nl * n;
+  rc = ew_encrypt(c, ea, nl, 1);
+  if (rc) return rc;
+  CK_CUDA(cudaStreamSynchronize(c->stream));
+  return CKKS_OK;
+}
+
+int ckks_public_key_export(ckks_ctx *c, uint64_t *out) {
+  if (!c || !out) return CKKS_E_PARAM;
+  if (!c->d_pk) return CKKS_E_NOKEY;
+  CK_CUDA(cudaStreamSynchronize(c->stream));
+  CK_CUDA(cudaMemcpy(out, c->d_pk, sizeof(u64) * 2 * (size_t)c->n_q * c->n, cudaMemcpyDeviceToHost));
+  return CKKS_OK;
+}
+
+int ckks_encrypt_pk(ckks_ctx *c, const uint64_t *pt, uint32_t level, double scale, uint64_t enc_seed,
+                    ckks_ct *out) {
+  if (!c || !pt || !out || !out->data) return CKKS_E_PARAM;
+  if (!c->d_pk) return CKKS_E_NOKEY;
+  if ((int)level >= c->n_q || out->n_limbs < level + 1) return CKKS_E_LEVEL;
+  const u32 n = c->n;
+  const int nl = level + 1;
+  int rc = ensure_scratch(c, 3 * (size_t)nl * n + 3 * (size_t)n);
+  if (rc) return rc;
+  std::vector<i64> h(3 * (size_t)n);
+  sample_pk_mask(sm_stream(enc_seed, TAG_PKENC_V, 0), n, h.data());
+  sample_gaussian(sm_stream(enc_seed, TAG_PKENC_E0, 0), n, c->sigma, c->e_bound, h.data() + n);
+  sample_gaussian(sm_stream(enc_seed, TAG_PKENC_E1, 0), n, c->sigma, c->e_bound, h.data() + 2 * (size_t)n);
+  rc = upload_small_polys(c, h, 3, nl, c->scratch);
+  if (rc) return rc;
+  EncPkArgs ea;
+  ea.b = c->d_pk;
+  ea.a = c->d_pk + (size_t)c->n_q * n;
+  ea.v = c->scratch;
+  ea.e0 = c->scratch + (size_t)nl * n;
+  ea.e1 = c->scratch + 2 * (size_t)nl * n;
+  ea.pt = pt;
+  ea.c0 = out->data;
+  ea.c1 = poly1(out, n);
+  rc = ew_encrypt_pk(c, ea, nl);
   if (rc) return rc;
   out->level = level;
   out->scale = scale;

@@ -83,6 +83,7 @@ struct ckks_ctx {
   bool have_secret = false;
   std::vector<int8_t> s_host;        // [N]
   u64 *d_s_ntt = nullptr;            // [n_q + n_p][N]
+  u64 *d_pk = nullptr;               // [2][n_q][N] public key (b, a), NTT domain, or null
   u64 key_seed = 0;
   DevKey relin;
   std::map<u64, DevKey> galois;
@@ -133,9 +134,12 @@ int build_tables(ckks_ctx *c);
 // ---- host sampling (sampling_host.cpp) ----
 u64 sm_draw(u64 key, u64 ctr);
 u64 sm_stream(u64 seed, u64 tag, u64 idx);
-enum { TAG_SECRET = 1, TAG_KEY_A = 2, TAG_KEY_E = 3, TAG_ENC_A = 4, TAG_ENC_E = 5 };
+enum { TAG_SECRET = 1, TAG_KEY_A = 2, TAG_KEY_E = 3, TAG_ENC_A = 4, TAG_ENC_E = 5,
+       TAG_PK_A = 6, TAG_PK_E = 7, TAG_PKENC_V = 8, TAG_PKENC_E0 = 9, TAG_PKENC_E1 = 10 };
 void sample_secret(u64 seed, u32 n, int h, int8_t *s);
 void sample_gaussian(u64 key, u32 n, double sigma, i64 bound, i64 *e);
+// public-key encryption's mask: 0 with probability 1/2, +1 and -1 with 1/4 each
+void sample_pk_mask(u64 key, u32 n, i64 *v);
 u64 sample_uniform(u64 key, u64 idx, u64 q);
 
 // ---- scratch ----

@@ -144,6 +144,18 @@ __global__ void k_encrypt(EncArgs e) {
   e.c1[c][off] = a;
 }
 
+// public-key encryption (C5, pk form): c0 = v b + pt + e0, c1 = v a + e1
+__global__ void k_encrypt_pk(EncPkArgs e) {
+  const u32 k = blockIdx.x * TPB + threadIdx.x;
+  const int t = blockIdx.y;
+  if (k >= e.n) return;
+  const ModInfo m = e.mods[t];
+  const size_t off = (size_t)t * e.n + k;
+  const u64 v = e.v[off];
+  e.c0[off] = addmod(addmod(mulmod(v, e.b[off], m), e.pt[off], m.q), e.e0[off], m.q);
+  e.c1[off] = addmod(mulmod(v, e.a[off], m), e.e1[off], m.q);
+}
+
 __global__ void k_decrypt(EwArgs a, const u64 *s_ntt) {
   const u32 k = blockIdx.x * TPB + threadIdx.x;
   const int l = blockIdx.y, c = blockIdx.z;
@@ -358,6 +370,12 @@ int ew_encrypt(ckks_ctx *c, EncArgs &e, int nl, int ncts) {
   e.n = c->n;
   e.s_ntt = c->d_s_ntt;
   PROF_LAUNCH(c, PK_ELEMENTWISE, (u64)nl * ncts, (k_encrypt<<<grid_for(c->n, nl, ncts), TPB, 0, c->stream>>>(e)));
+  return last_status();
+}
+int ew_encrypt_pk(ckks_ctx *c, EncPkArgs &e, int nl) {
+  e.mods = c->d_mods;
+  e.n = c->n;
+  PROF_LAUNCH(c, PK_ELEMENTWISE, (u64)nl, (k_encrypt_pk<<<grid_for(c->n, nl, 1), TPB, 0, c->stream>>>(e)));
   return last_status();
 }
 int ew_signed_to_res(ckks_ctx *c, const i64 *v, u64 *out, int first_mod, int nl) {

@@ -34,6 +34,16 @@ struct EncArgs {
   u64 *c0[MAX_CTS], *c1[MAX_CTS];
 };
 
+// public-key encryption (C5, pk form): c0 = v b + pt + e0, c1 = v a + e1
+struct EncPkArgs {
+  const ModInfo *mods;
+  u32 n;
+  const u64 *b, *a;                  // the public key's limbs q_0..
+  const u64 *v, *e0, *e1;            // NTT-domain mask and errors [nl][N]
+  const u64 *pt;
+  u64 *c0, *c1;
+};
+
 struct KeyArgs {
   const ModInfo *mods;
   u32 n;
@@ -56,6 +66,7 @@ int ew_decrypt(ckks_ctx *c, EwArgs &a, int nl, int ncts);
 int ew_rescale_lift(ckks_ctx *c, RescaleArgs &r, int ncts);
 int ew_rescale_finish(ckks_ctx *c, RescaleArgs &r, int ncts);
 int ew_encrypt(ckks_ctx *c, EncArgs &e, int nl, int ncts);
+int ew_encrypt_pk(ckks_ctx *c, EncPkArgs &e, int nl);
 int ew_signed_to_res(ckks_ctx *c, const i64 *v, u64 *out, int first_mod, int nl);
 int ew_keyrow(ckks_ctx *c, KeyArgs &k, int nl);
 int ew_square(ckks_ctx *c, u64 *out, const u64 *in, int nl);

@@ -6,6 +6,7 @@
 //   error  : rounded Gaussian by the Box-Muller cosine branch, tail cut at
 //            |e| <= bound, up to 16 tries per sample, else 0
 //   uniform: (hi * 2^64 + lo) mod q from two consecutive draws
+//   mask   : public-key encryption's v in {0, +1, -1}, two bits of one draw
 #include <cmath>
 
 #include "ctx.h"
@@ -43,6 +44,14 @@ void sample_gaussian(u64 key, u32 n, double sigma, i64 bound, i64 *e) {
       if (r >= -bound && r <= bound) { val = r; break; }
     }
     e[j] = val;
+  }
+}
+
+// the low two bits of one draw per coefficient: 0, 1 -> 0; 2 -> +1; 3 -> -1
+void sample_pk_mask(u64 key, u32 n, i64 *v) {
+  for (u32 j = 0; j < n; ++j) {
+    const u64 r = sm_draw(key, j) & 3;
+    v[j] = r < 2 ? 0 : (r == 2 ? 1 : -1);
   }
 }
 

@@ -197,6 +197,45 @@ def test_hoisted_rotations_bit_exact(pair):
     assert np.max(np.abs(got - np.roll(za, -1))) < _noise_bound(w)
 
 
+def test_public_key_and_public_key_encryption_bit_exact(pair):
+    """Reading C5, pk form: the public key and Enc_pk at the top level and at
+    level 0 equal the oracle's limb for limb, and decrypt to the message."""
+    w, ctx, orc = pair
+    ctx.keygen_public()
+    orc.gen_public_key()
+    assert np.array_equal(ctx.public_key(), orc.public_key())
+    scale = 2.0 ** w.log2_scale
+    z = si.messages(15, 1, w.slots)[0]
+    m = orc.encode(z, scale)
+    for lvl in (len(w.q_bits) - 1, 0):
+        cg = ctx.encrypt_pk(ctx.pt_from_int(m, lvl), lvl, scale, 555 + lvl)
+        co = orc.encrypt_pk(orc.pt_from_int(m, lvl), lvl, scale, 555 + lvl)
+        _same(ctx, cg, co)
+    # the mask multiplies the key's error: about sqrt(N/2) sigma per coefficient
+    got = ctx.decrypt_decode(ctx.encrypt_pk(ctx.pt_from_int(m, len(w.q_bits) - 1), len(w.q_bits) - 1, scale, 9))
+    assert np.max(np.abs(got - z)) < 2.0 ** 6 * _noise_bound(w)
+    assert ctx.device_error() == 0
+
+
+def test_public_key_statuses():
+    import paper_2506_19693_gb300 as ck
+    ctx, orc = _pair(si.TOY, rot=(1,), conj=False)
+    try:
+        level = len(si.TOY.q_bits) - 1
+        pt = ctx.pt_from_int(np.zeros(ctx.n, dtype=np.int64), level)
+        with pytest.raises(ck.CkksError):
+            ctx.encrypt_pk(pt, level, 1.0, 1)
+        with pytest.raises(ck.CkksError):
+            ctx.public_key()
+        ctx.keygen_public()
+        ctx.encrypt_pk(pt, level, 1.0, 1)
+        ctx.keygen(KEY_SEED, rot_steps=[1])  # a new secret discards the public key
+        with pytest.raises(ck.CkksError):
+            ctx.encrypt_pk(pt, level, 1.0, 1)
+    finally:
+        ctx.close()
+
+
 def test_encode_matches_oracle_within_fp64_rounding(pair):
     import paper_2506_19693_gb300 as ck
     w, ctx, orc = pair
