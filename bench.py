@@ -665,6 +665,9 @@ def run_gpu(args):
     cluster_ntt = None
     if not (args.no_tc_ntt or args.small):
         cluster_ntt = run_cluster_ntt(ctx, w, torch, stream, max(2, min(args.steps, 3)), A, Bc, OUT)
+    tc_inner = None
+    if not (args.no_tc_ntt or args.small):
+        tc_inner = run_tc_inner_prototype(torch, stream, max(2, min(args.steps, 3)))
 
     # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -722,6 +725,7 @@ def run_gpu(args):
                 "sparse_slot_bootstrap": sparse_boot,
                 "tensor_ntt_stage_prototype": tc_ntt,
                 "cluster_ntt": cluster_ntt,
+                "tensor_inner_product_prototype": tc_inner,
                 "tuning": tuning,
                 "e2e": e2e, "roofline": roof, "op_rooflines": op_roofs, "alu_peaks": alu, "cpu_baseline": cpu,
                 "clocks": clk,
@@ -899,6 +903,51 @@ def run_tc_ntt_prototype(ctx, w, torch, stream, reps, n_polys=64):
             "stage_group_tensor_tflops": tc_flops / (stage_ms / 1e3) / 1e12 if stage_ms else None,
             "note": "uint64 NTT launched per polynomial (24 limbs per launch); the four stages the prototype moves "
                     "to the tensor cores are half of the uint64 column pass"}
+
+
+def run_tc_inner_prototype(torch, stream, reps):
+    """The key-switch inner product of 128 ciphertexts sharing one key (3
+    digits, all 32 limbs of the N = 2^16 chain) as a byte-split tcgen05 GEMM
+    (ckks_ks_inner_tc) against the same product on the CUDA cores
+    (ckks_ks_inner_u64), on identical random residues."""
+    import paper_2506_19693_gb300 as ck
+    w = si.PLAIN
+    ctx = ck.Context.from_workload(w, stream=stream)
+    P, ndig = 128, 3
+    L, n = len(ctx.moduli), ctx.n
+    g = torch.Generator(device=ctx.device)
+    g.manual_seed(9)
+    d = torch.empty((P, ndig, L, n), dtype=torch.int64, device=ctx.device)
+    key = torch.empty((ndig, 2, L, n), dtype=torch.int64, device=ctx.device)
+    for t in range(L):
+        q = int(ctx.moduli[t])
+        d[:, :, t] = torch.randint(0, q, (P, ndig, n), device=ctx.device, generator=g)
+        key[:, :, t] = torch.randint(0, q, (ndig, 2, n), device=ctx.device, generator=g)
+    outs = {f: torch.empty((P, 2, L, n), dtype=torch.int64, device=ctx.device) for f in ("tensor", "uint64")}
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    ms = {}
+    for f in ("tensor", "uint64"):
+        ctx.ks_inner(d, key, outs[f], f)
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        for _ in range(reps):
+            ctx.ks_inner(d, key, outs[f], f)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms[f] = e0.elapsed_time(e1) / reps
+    same = bool(torch.equal(outs["tensor"], outs["uint64"]))
+    err = ctx.device_error()
+    ctx.close()
+    pairs = P * L * n  # output pairs (o = 0, 1)
+    flops = pairs * 16 * (8 * ndig) * 2  # one 16-column row of the byte GEMM per output pair
+    hbm_bytes = 8 * L * n * (P * ndig + 2 * ndig + 2 * P)
+    return {"ciphertexts": P, "digits": ndig, "limbs": L, "bit_exact_vs_uint64": same, "device_error": err,
+            "ms_tensor": ms["tensor"], "ms_uint64": ms["uint64"],
+            "tensor_tflops": flops / (ms["tensor"] / 1e3) / 1e12,
+            "hbm_gbs_tensor": hbm_bytes / (ms["tensor"] / 1e3) / 1e9,
+            "hbm_gbs_uint64": hbm_bytes / (ms["uint64"] / 1e3) / 1e9,
+            "note": "bytes: the digits, the key and the outputs once each"}
 
 
 def run_cluster_ntt(ctx, w, torch, stream, reps, A, Bc, OUT):

@@ -221,6 +221,24 @@ int ckks_ntt(ckks_ctx *ctx, uint64_t *data_dev, uint32_t n_limbs, uint32_t first
  * twelve stages run as in ckks_ntt.  Same residues as ckks_ntt.  N = 2^15 or
  * 2^16 (else CKKS_E_PARAM); uses the context scratch (n_polys N words). */
 int ckks_ntt_tc(ckks_ctx *ctx, uint64_t *data_dev, uint32_t n_polys, uint32_t n_limbs);
+/* Key-switch inner product (reading C7: the products of the lifted digits with
+ * the key, summed over digits) for a batch sharing one key, in two forms with
+ * identical outputs, for comparison:
+ *   out[p][o][t][k] = sum_j d[p][j][t][k] key[j][o][t][k]  mod q_t,  o = 0, 1,
+ * all device arrays of plain residues: d uint64[n_cts][n_digits][n_limbs][N],
+ * key uint64[n_digits][2][n_limbs][N], out uint64[n_cts][2][n_limbs][N]
+ * (16-byte aligned); limb t is reduced mod the context's modulus t.
+ * n_digits 1..4, n_limbs <= min(40, n_q + n_p) (else CKKS_E_PARAM); CKKS_E_STATE
+ * during graph capture.
+ * _tc: a byte-split fp16 GEMM on tcgen05 per coefficient, M = 128 ciphertexts
+ * (n_cts must be 128), N = 16 (2 outputs x 8 byte planes of 2^(8a) key mod q),
+ * K = 8 n_digits, fp32 accumulation in tensor memory, modular recombination;
+ * bounded waits as the tensor-core conversion (ckks_ctx_device_error).
+ * _u64: 128-bit multiply-accumulates on the CUDA cores, any n_cts >= 1. */
+int ckks_ks_inner_tc(ckks_ctx *ctx, const uint64_t *d_dev, const uint64_t *key_dev, uint32_t n_cts,
+                     uint32_t n_digits, uint32_t n_limbs, uint64_t *out_dev);
+int ckks_ks_inner_u64(ckks_ctx *ctx, const uint64_t *d_dev, const uint64_t *key_dev, uint32_t n_cts,
+                      uint32_t n_digits, uint32_t n_limbs, uint64_t *out_dev);
 
 /* ---- encryption (Sec. 3, reading C5) ------------------------------------ */
 

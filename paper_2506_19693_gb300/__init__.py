@@ -83,6 +83,8 @@ SIGNATURES = {
     "ckks_encrypt": (_I, [_V, _V, ctypes.c_uint32, _D, _U64, _CTP]),
     "ckks_decrypt": (_I, [_V, _CTP, _V]),
     "ckks_keygen_public": (_I, [_V]),
+    "ckks_ks_inner_tc": (_I, [_V, _V, _V, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _V]),
+    "ckks_ks_inner_u64": (_I, [_V, _V, _V, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _V]),
     "ckks_public_key_export": (_I, [_V, _V]),
     "ckks_encrypt_pk": (_I, [_V, _V, ctypes.c_uint32, _D, _U64, _CTP]),
     "ckks_add": (_I, [_V, _CTP, _CTP, _CTP]),
@@ -394,6 +396,14 @@ class Context:
         _check(self.lib.ckks_encrypt(self._h, pt.data_ptr(), level, scale, enc_seed, ctypes.byref(h)),
                "ckks_encrypt")
         return ct
+
+    def ks_inner(self, d, key, out, form: str = "tensor") -> None:
+        """out[p][o][t] = sum_j d[p][j][t] key[j][o][t] mod q_t on device tensors
+        d [P][D][L][N], key [D][2][L][N], out [P][2][L][N]; form "tensor"
+        (tcgen05, P = 128) or "uint64"."""
+        fn = {"tensor": self.lib.ckks_ks_inner_tc, "uint64": self.lib.ckks_ks_inner_u64}[form]
+        P, D, L = int(d.shape[0]), int(d.shape[1]), int(d.shape[2])
+        _check(fn(self._h, d.data_ptr(), key.data_ptr(), P, D, L, out.data_ptr()), "ckks_ks_inner")
 
     def keygen_public(self) -> None:
         """The public key pk = ([-a s + e]_Q, a) at the top level (after keygen)."""

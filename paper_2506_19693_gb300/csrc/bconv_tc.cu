@@ -396,6 +396,224 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_bconv_tc(const TcArgs a) {
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
 }
 
+
+// ---------------------------------------------------------------- key inner product as a GEMM
+// The key-switch inner product out_o = sum_j d_j key_(j,o) mod q (o = 0, 1;
+// reading C7) for P = 128 ciphertexts sharing one key: at one coefficient k
+// of limb t it is a [P x ndig] x [ndig x 2] product whose right operand (the
+// key words) is shared by the 128 rows.  Byte-split as the conversion above:
+//   A[p][(j, a)]     = byte a of d_j[p]                       (K = 8 ndig <= 32)
+//   B[(o, b)][(j, a)] = byte b of 2^(8a) key_(j,o) mod q       (N = 16)
+//   out_o[p] = sum_b 2^(8b) D[p][(o, b)] mod q, every D entry below 32 255^2 < 2^23.
+// One M = 128, N = 16 MMA (K in steps of 16) per coefficient; a unit is 8
+// consecutive coefficients of one limb, built into one of two shared-memory
+// buffers while the other's MMAs run; 8 x 16 TMEM columns per buffer.
+// Layouts: digits [P][ndig][L][N], keys [ndig][2][L][N] (plain residues),
+// out [P][2][L][N]; limb t is taken mod the context's modulus t.
+constexpr int IP_P = 128;         // ciphertexts (MMA rows)
+constexpr int IP_G = 8;           // coefficients per unit
+constexpr int IP_MAX_L = 40;
+constexpr int IP_TMEM_COLS = 2 * IP_G * 16;
+
+struct IpTcArgs {
+  u32 n;
+  int L, ndig, kpad, upl_log2;    // units per limb = n / IP_G = 2^upl_log2
+  const u64 *d, *key;
+  u64 *out;
+  const ModInfo *mods;
+  u64 pw[IP_MAX_L][8];            // 2^(8a) mod q_t
+  TcTarget tg[IP_MAX_L];
+  int *err;
+  u64 wait_ns;
+};
+
+__device__ __forceinline__ int ip_a_item(int kpad) { return IP_P * kpad * 2; }
+__device__ __forceinline__ int ip_b_item(int kpad) { return 16 * kpad * 2; }
+__device__ __forceinline__ int ip_buf(int kpad) { return IP_G * (ip_a_item(kpad) + ip_b_item(kpad)); }
+
+// A and B tiles of one unit (limb t, coefficients k0 .. k0 + 7) into buffer sbuf.
+__device__ __forceinline__ void ip_build(const IpTcArgs &a, unsigned char *sbuf, int unit, int tid) {
+  const int t = unit >> a.upl_log2;
+  const u32 k0 = (u32)(unit & ((1 << a.upl_log2) - 1)) * IP_G;
+  const int a_item = ip_a_item(a.kpad), b_item = ip_b_item(a.kpad);
+  unsigned char *sB = sbuf + IP_G * a_item;
+  const size_t limb = (size_t)a.L * a.n;
+  for (int idx = tid; idx < IP_P * IP_G; idx += TC_THREADS) {  // (ciphertext, coefficient)
+    const int p = idx / IP_G, kk = idx % IP_G;
+    const u64 *dp = a.d + (size_t)p * a.ndig * limb + (size_t)t * a.n + k0 + kk;
+    for (int j = 0; j < a.ndig; ++j) {
+      const u64 y = __ldg(dp + (size_t)j * limb);
+      const u32 lo = (u32)y, hi = (u32)(y >> 32);
+      uint4 v;
+      v.x = bytes_to_half2(lo, 0x4140);
+      v.y = bytes_to_half2(lo, 0x4342);
+      v.z = bytes_to_half2(hi, 0x4140);
+      v.w = bytes_to_half2(hi, 0x4342);
+      *reinterpret_cast<uint4 *>(sbuf + kk * a_item + canon_offset(p, j * 8, a.kpad)) = v;
+    }
+  }
+  const ModInfo m = a.mods[t];
+  for (int idx = tid; idx < IP_G * 2 * a.ndig * 8; idx += TC_THREADS) {  // (coefficient, output, digit, a)
+    const int a8 = idx & 7;
+    int r = idx >> 3;
+    const int j = r % a.ndig;
+    r /= a.ndig;
+    const int o = r & 1, kk = r >> 1;
+    const u64 w = __ldg(a.key + ((size_t)(j * 2 + o) * a.L + t) * a.n + k0 + kk);
+    const u64 c = mulmod(w, a.pw[t][a8], m);
+    unsigned char *b0 = sB + kk * b_item;
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+      *reinterpret_cast<__half *>(b0 + canon_offset(o * 8 + b, j * 8 + a8, a.kpad)) =
+          __uint2half_rn((unsigned)((c >> (8 * b)) & 255u));
+  }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_inner_tc(const IpTcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int a_item = ip_a_item(a.kpad), b_item = ip_b_item(a.kpad), buf_bytes = ip_buf(a.kpad);
+  u64 *mbar = reinterpret_cast<u64 *>(smem + 2 * buf_bytes);
+  u32 *tmem_slot = reinterpret_cast<u32 *>(mbar + 2);
+  // zero the padding columns 8 ndig .. kpad - 1 of every tile of both buffers
+  const int padc = a.kpad / 8 - a.ndig;
+  for (int idx = tid; idx < 2 * IP_G * (IP_P + 16) * padc; idx += TC_THREADS) {
+    int r = idx;
+    const int cblk = a.ndig + r % padc;
+    r /= padc;
+    const int row = r % (IP_P + 16);
+    r /= IP_P + 16;
+    const int kk = r % IP_G, b = r / IP_G;
+    unsigned char *base = smem + b * buf_bytes;
+    unsigned char *tile = row < IP_P ? base + kk * a_item : base + IP_G * a_item + kk * b_item;
+    const int rr = row < IP_P ? row : row - IP_P;
+    *reinterpret_cast<uint4 *>(tile + canon_offset(rr, cblk * 8, a.kpad)) = make_uint4(0, 0, 0, 0);
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + 1)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(IP_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  const int total = a.L << a.upl_log2;
+  const int grid = (int)gridDim.x;
+  int unit = blockIdx.x;
+  if (unit < total) ip_build(a, smem, unit, tid);
+  asm volatile("fence.proxy.async.shared::cta;");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const u32 tmem = *tmem_slot;
+  // D fp32, A and B fp16, K-major, M = 128, N = 16
+  const u32 idesc = (1u << 4) | ((u32)(16 >> 3) << 17) | ((u32)(IP_P >> 4) << 24);
+  const u32 sbo = (u32)(a.kpad / 8) * 128;
+  u32 phase = 0, pending = 0;
+  auto issue = [&](int b) {
+    if (tid == 0) {
+      const u32 base = smem_u32(smem + b * buf_bytes);
+      for (int kk = 0; kk < IP_G; ++kk) {
+        const u32 sa = base + kk * a_item, sb = base + IP_G * a_item + kk * b_item;
+        for (int ks = 0; ks < a.kpad / 16; ++ks) {
+          const u64 ad = make_desc(sa + ks * 256, 128, sbo);
+          const u64 bd = make_desc(sb + ks * 256, 128, sbo);
+          const u32 acc = ks > 0 ? 1u : 0u;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+                  tmem + (u32)((b * IP_G + kk) * 16)),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(mbar + b)));
+    }
+    pending |= 1u << b;
+  };
+  bool failed = false;
+  if (unit < total) issue(0);
+  const int lq = warp & 3, cg = warp >> 2;
+  const size_t limb = (size_t)a.L * a.n;
+  for (int j = 0; unit < total; ++j, unit += grid) {
+    const int cur = j & 1, nxt = cur ^ 1;
+    const int next = unit + grid;
+    if (next < total) ip_build(a, smem + nxt * buf_bytes, next, tid);
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (next < total) issue(nxt);
+    const u32 done = wait_parity(smem_u32(mbar + cur), (phase >> cur) & 1u, a.wait_ns);
+    if (__syncthreads_or(done == 0)) {
+      failed = true;
+      break;
+    }
+    phase ^= 1u << cur;
+    pending &= ~(1u << cur);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // epilogue: lanes 32 lq .. +31 = ciphertexts, coefficients cg and cg + 4 of the unit
+    const int t = unit >> a.upl_log2;
+    const u32 k0 = (u32)(unit & ((1 << a.upl_log2) - 1)) * IP_G;
+    const int p = lq * 32 + lane;
+    u64 *o0 = a.out + (size_t)(2 * p) * limb + (size_t)t * a.n + k0;
+    const u32 tbase = tmem + ((u32)(lq * 32) << 16) + (u32)(cur * IP_G * 16);
+    u32 v[16], u[16];
+    tmem_ld16(v, tbase + (u32)(cg * 16));
+    tmem_ld16(u, tbase + (u32)((cg + 4) * 16));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+    o0[cg] = recombine_target(v, a.tg[t], 0);
+    o0[limb + cg] = recombine_target(v + 8, a.tg[t], 0);
+    o0[cg + 4] = recombine_target(u, a.tg[t], 0);
+    o0[limb + cg + 4] = recombine_target(u + 8, a.tg[t], 0);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+  }
+  if (failed) {
+    u32 drained = 1;
+    for (int b = 0; b < 2; ++b)
+      if ((pending >> b) & 1u) drained &= wait_parity(smem_u32(mbar + b), (phase >> b) & 1u, TC_DRAIN_NS);
+    const int stuck = __syncthreads_or(drained == 0);
+    if (tid == 0) atomicMax(a.err, stuck ? 2 : 1);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+  }
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(IP_TMEM_COLS));
+}
+
+// The same product on the CUDA cores, for comparison: one thread per
+// coefficient of one limb, the key words in registers, the ciphertexts in a
+// loop; 128-bit sums, one reduction per output.
+template <int NDIG>
+__global__ void __launch_bounds__(256) k_inner_flat(const u64 *__restrict__ d, const u64 *__restrict__ key,
+                                                   u64 *__restrict__ out, const ModInfo *mods, u32 n, int L,
+                                                   int np) {
+  const u32 k = blockIdx.x * 256 + threadIdx.x;
+  const int t = blockIdx.y;
+  if (k >= n) return;
+  const ModInfo m = mods[t];
+  const size_t limb = (size_t)L * n, off = (size_t)t * n + k;
+  u64 kb[NDIG], ka[NDIG];
+#pragma unroll
+  for (int j = 0; j < NDIG; ++j) {
+    kb[j] = __ldg(key + (size_t)(2 * j) * limb + off);
+    ka[j] = __ldg(key + (size_t)(2 * j + 1) * limb + off);
+  }
+#pragma unroll 4
+  for (int p = 0; p < np; ++p) {
+    u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0;
+#pragma unroll
+    for (int j = 0; j < NDIG; ++j) {
+      const u64 v = __ldg(d + ((size_t)p * NDIG + j) * limb + off);
+      mac128(h0, l0, v, kb[j]);
+      mac128(h1, l1, v, ka[j]);
+    }
+    out[(size_t)(2 * p) * limb + off] = reduce128(h0, l0, m);
+    out[(size_t)(2 * p + 1) * limb + off] = reduce128(h1, l1, m);
+  }
+}
+
 }  // namespace
 
 // Host: the byte-plane constant matrix of one conversion, cached on the device
@@ -528,4 +746,78 @@ int launch_bconv_tc_view(ckks_ctx *c, size_t key, const u64 *inv_host, const u64
                          u64 *const *dst, int np, u32 n_virt) {
   return launch_bconv_tc_ex(c, key, inv_host, tab_host, ns, nt, src_mod, dst_mod, dst_pos, src, dst, np, nullptr,
                             nullptr, nullptr, nullptr, TC_WAIT_NS, 0, n_virt);
+}
+
+// ---- key inner product prototype entry points ----
+static int check_inner_args(const ckks_ctx *c, const uint64_t *d, const uint64_t *key, uint32_t n_cts,
+                            uint32_t n_digits, uint32_t n_limbs, const uint64_t *out) {
+  if (!c || !d || !key || !out) return CKKS_E_PARAM;
+  if (n_digits < 1 || n_digits > 4 || n_limbs < 1 || n_limbs > (uint32_t)std::min(IP_MAX_L, c->n_q + c->n_p))
+    return CKKS_E_PARAM;
+  if (n_cts < 1) return CKKS_E_PARAM;
+  if (c->capturing) return CKKS_E_STATE;
+  return CKKS_OK;
+}
+
+extern "C" int ckks_ks_inner_tc(ckks_ctx *c, const uint64_t *d, const uint64_t *key, uint32_t n_cts,
+                                uint32_t n_digits, uint32_t n_limbs, uint64_t *out) {
+  int rc = check_inner_args(c, d, key, n_cts, n_digits, n_limbs, out);
+  if (rc) return rc;
+  if (n_cts != IP_P) return CKKS_E_PARAM;
+  if ((((uintptr_t)d) | ((uintptr_t)key) | ((uintptr_t)out)) & 15) return CKKS_E_PARAM;
+  IpTcArgs a;
+  a.n = c->n;
+  a.L = (int)n_limbs;
+  a.ndig = (int)n_digits;
+  a.kpad = (8 * (int)n_digits + 15) / 16 * 16;
+  a.upl_log2 = c->log_n - 3;  // n / IP_G units per limb
+  a.d = d;
+  a.key = key;
+  a.out = out;
+  a.mods = c->d_mods;
+  const unsigned __int128 two64 = (unsigned __int128)1 << 64;
+  for (int t = 0; t < a.L; ++t) {
+    const u64 m = c->mod[t];
+    u64 w = 1 % m;
+    for (int k = 0; k < 8; ++k) {
+      a.pw[t][k] = w;
+      w = (u64)(((unsigned __int128)w << 8) % m);
+    }
+    TcTarget &g = a.tg[t];
+    g.q = m;
+    g.one_s = (u64)(two64 / m);
+    g.r64 = (u64)(two64 % m);
+    g.r64_s = (u64)(((unsigned __int128)g.r64 << 64) / m);
+    g.w96_s = (u64)(((unsigned __int128)1 << 96) / m);  // used only when t > 2^48 (wide)
+    g.wide = m > (1ULL << 48) ? 1 : 0;
+    g.sub = 0;
+  }
+  a.err = c->tc_err;
+  a.wait_ns = TC_WAIT_NS;
+  const size_t smem = 2 * (size_t)IP_G * (IP_P * a.kpad * 2 + 16 * a.kpad * 2) + 32;
+  CK_CUDA(cudaFuncSetAttribute(k_inner_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  const int total = a.L << a.upl_log2;
+  const int grid = std::min(total, sms);
+  PROF_LAUNCH(c, PK_INNER_TC, (u64)n_cts * n_limbs, (k_inner_tc<<<grid, TC_THREADS, smem, c->stream>>>(a)));
+  return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_CUDA;
+}
+
+extern "C" int ckks_ks_inner_u64(ckks_ctx *c, const uint64_t *d, const uint64_t *key, uint32_t n_cts,
+                                 uint32_t n_digits, uint32_t n_limbs, uint64_t *out) {
+  int rc = check_inner_args(c, d, key, n_cts, n_digits, n_limbs, out);
+  if (rc) return rc;
+  dim3 g((c->n + 255) / 256, n_limbs);
+  const int np = (int)n_cts, L = (int)n_limbs;
+  switch (n_digits) {
+#define FCASE(D)                                                                                             \
+  case D:                                                                                                    \
+    PROF_LAUNCH(c, PK_INNER_FLAT, (u64)n_cts * n_limbs,                                                      \
+                (k_inner_flat<D><<<g, 256, 0, c->stream>>>(d, key, out, c->d_mods, c->n, L, np)));          \
+    break;
+    FCASE(1) FCASE(2) FCASE(3) FCASE(4)
+#undef FCASE
+  }
+  return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_CUDA;
 }

@@ -602,7 +602,8 @@ const char *ckks_profile_kind_name(int k) {
   static const char *names[PK_COUNT] = {"ntt_fwd_pass_a", "ntt_fwd_pass_b", "ntt_inv_pass_a", "ntt_inv_pass_b",
                                         "bconv", "ks_inner_product", "ks_moddown_combine", "tensor",
                                         "automorph", "rescale", "elementwise", "encode_decode", "bconv_tc",
-                                        "boot_mac_ext", "boot_lincomb", "conv_fused", "ntt_fwd_cluster",
+                                        "boot_mac_ext", "boot_lincomb", "conv_fused", "ntt_fwd_cluster", "ks_inner_tc",
+                                        "ks_inner_flat",
                                         "ntt_fwd_strict_limbs",
                                         "ntt_inv_exact_limbs", "fused_src_limbs", "fused_dst_limbs",
                                         "fused_dst_strict_limbs", "boot_mac_ext_macs"};

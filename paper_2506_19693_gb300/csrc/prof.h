@@ -25,6 +25,8 @@ enum ProfKind {
   PK_BOOT_LINCOMB,    // units: limbs of N words moved (algorithmic)
   PK_CONV_FUSED,      // units: source-target limb pairs of one polynomial (as the conversions)
   PK_NTT_FWD_CLUSTER, // units: limbs (the one-pass forward transform on a cluster)
+  PK_INNER_TC,        // units: ciphertext limbs of the tensor-core inner product prototype
+  PK_INNER_FLAT,      // units: ciphertext limbs of its CUDA-core comparison kernel
   // counting-only classes (no launches, no time): limbs of the forward NTT
   // passes whose prime takes the strict butterfly (65 q >= 2^64), and limbs of
   // inverse passes launched with the exact quotient (a prime >= 2^61)
