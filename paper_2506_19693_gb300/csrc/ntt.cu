@@ -163,15 +163,32 @@ __device__ __forceinline__ void fwd_a_body(const NttParams &prm, u64 *sm, int mi
 #pragma unroll
     for (int e = 0; e < (1 << S1); ++e) sm[(r0 + (e << S2)) * CA + c] = v[e];
   }
-  __syncthreads();
-  for (int x = threadIdx.x; x < (1 << S1) * CA; x += THREADS) {
-    const int c = x % CA, g = x / CA;
+  if constexpr ((1 << S1) * CA == THREADS) {
+    // one group per thread: its twiddles are loaded before the barrier
+    const int c = threadIdx.x % CA, g = threadIdx.x / CA;
+    ulonglong2 twv[(1 << S2) - 1];
+#pragma unroll
+    for (int s = 0; s < S2; ++s)
+#pragma unroll
+      for (int i = 0; i < (1 << s); ++i) twv[(1 << s) - 1 + i] = __ldg(&tw[(((1u << S1) + g) << s) + i]);
+    __syncthreads();
     u64 v[1 << S2];
 #pragma unroll
     for (int e = 0; e < (1 << S2); ++e) v[e] = sm[((g << S2) + e) * CA + c];
-    fwd_step<S2, LOOSE>(v, (1u << S1) + g, tw, q, twoq);
+    fwd_step_t<S2, LOOSE>(v, [&](int s, int i) { return twv[(1 << s) - 1 + i]; }, q, twoq);
 #pragma unroll
     for (int e = 0; e < (1 << S2); ++e) dst[(size_t)((g << S2) + e) * BROW + c0 + c] = v[e];
+  } else {
+    __syncthreads();
+    for (int x = threadIdx.x; x < (1 << S1) * CA; x += THREADS) {
+      const int c = x % CA, g = x / CA;
+      u64 v[1 << S2];
+#pragma unroll
+      for (int e = 0; e < (1 << S2); ++e) v[e] = sm[((g << S2) + e) * CA + c];
+      fwd_step<S2, LOOSE>(v, (1u << S1) + g, tw, q, twoq);
+#pragma unroll
+      for (int e = 0; e < (1 << S2); ++e) dst[(size_t)((g << S2) + e) * BROW + c0 + c] = v[e];
+    }
   }
 }
 
