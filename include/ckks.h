@@ -6,7 +6,7 @@
  * Delta the scale); batching of up to N/2 complex values into one plaintext
  * through the complex canonical embedding; secret-key encryption; slot-wise
  * homomorphic +, -, x (Eq. add, sub, mult) and their plaintext variants;
- * switching to the next prime after a multiplication; Rot(a, k), a cyclic left
+ * dropping the chain's top prime after a multiplication; Rot(a, k), a cyclic left
  * shift by k slots with one key per k; and bootstrapping.  The scheme's
  * internals (prime chain, NTT order, hybrid key switching, rescale rounding)
  * are the textbook RNS-CKKS readings listed in the design notes as C1..C12.

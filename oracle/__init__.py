@@ -9,8 +9,8 @@ module adds the FP64 canonical-embedding encode/decode and an exact big-integer
 CRT written with Python integers.
 
 Paper passages followed (ReBoot, arXiv 2506.19693):
-  * Sec. 3 -- parameter set {N, q, Delta}; a multiplication consumes one level
-    by switching to the next prime of the chain ("rescale");
+  * Sec. 3 -- parameter set {N, q, Delta}; a multiplication costs one level,
+    the top prime of the modulus chain being dropped (rescale);
   * Sec. 3 -- batching: N/2 complex slots through the complex canonical
     embedding phi : C^{N/2} -> Z[X]/(X^N + 1); secret-key encryption;
   * Sec. 3, Eq. add/sub/mult -- slot-wise +, -, x of ciphertexts and the

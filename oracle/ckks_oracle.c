@@ -8,7 +8,7 @@
  * as possible (every modular product is a 128-bit product followed by `%`).
  *
  * What the paper fixes (ReBoot, Sec. 3): the parameter set {N, q, Delta}, that
- * a multiplication consumes a level by switching to the next prime of the
+ * a multiplication costs one level, dropping the top prime of the modulus
  * chain, batching of N/2 complex slots through the canonical embedding,
  * element-wise +, -, x on slots (Eq. add/sub/mult), left rotation Rot(a, k)
  * with one key per k, and bootstrapping (Sec. 3, last paragraph).  Everything
