@@ -147,8 +147,18 @@ __device__ __forceinline__ u64 recombine_wide(const u32 *v, const TcTarget &tg) 
   return csub(csub(r + L, tg.q << 1), tg.q);
 }
 
-__device__ __forceinline__ u64 recombine_target(const u32 *v, const TcTarget &tg, int has_sub) {
-  u64 r = tg.wide ? recombine_wide(v, tg) : recombine(v, tg);
+// ALL_WIDE: every target of the launch is above 2^48 (checked on the host), so
+// only the one-product path is compiled in.
+// The launch's options (TcArgs::has_add, has_sub, has_v) at compile time: FL = 0
+// none, 7 all three (the merged ModDown-rescale), -1 read at run time.
+template <int FL>
+__device__ __forceinline__ bool tc_flag(int runtime, int bit) {
+  return FL < 0 ? runtime != 0 : ((FL >> bit) & 1) != 0;
+}
+
+template <bool ALL_WIDE = false>
+__device__ __forceinline__ u64 recombine_target(const u32 *v, const TcTarget &tg, bool has_sub) {
+  u64 r = (ALL_WIDE || tg.wide) ? recombine_wide(v, tg) : recombine(v, tg);
   if (has_sub) r = submod(r, tg.sub, tg.q);
   return r;
 }
@@ -210,6 +220,7 @@ __device__ __forceinline__ void load_sources(const TcArgs &a, int tile, int tpp_
 // y_i = [x_i Bhat_i^-1]_(b_i) as 8 fp16 bytes into row tid mod 128 of an A tile;
 // with overflow removal, this thread's part of sum_i floor(y_i R_i / 2^64)
 // goes to part[group][row].
+template <int FL>
 __device__ __forceinline__ void store_sources(const TcArgs &a, unsigned char *sA, int tid,
                                               const u64 (&x)[TC_SRC_PER], u64 *part) {
   const int row = tid & (TC_M - 1);
@@ -219,8 +230,8 @@ __device__ __forceinline__ void store_sources(const TcArgs &a, unsigned char *sA
     const int i = tid / TC_M + k * TC_SRC_GROUPS;
     if (i < a.ns) {
       u64 y = shoup(x[k], a.inv[i], a.inv_s[i], a.sq[i]);
-      if (a.has_add) y = addmod(y, a.src_add[i], a.sq[i]);
-      if (a.has_v) fix += __umul64hi(y, a.rdiv[i]) + y * a.rdiv_hi[i];  // high word: b_i < 2^32 only
+      if (tc_flag<FL>(a.has_add, 0)) y = addmod(y, a.src_add[i], a.sq[i]);
+      if (tc_flag<FL>(a.has_v, 2)) fix += __umul64hi(y, a.rdiv[i]) + y * a.rdiv_hi[i];  // high word: b_i < 2^32 only
       const u32 lo = (u32)y, hi = (u32)(y >> 32);
       uint4 v;
       v.x = bytes_to_half2(lo, 0x4140);
@@ -230,7 +241,7 @@ __device__ __forceinline__ void store_sources(const TcArgs &a, unsigned char *sA
       *reinterpret_cast<uint4 *>(sA + canon_offset(row, i * 8, a.kpad)) = v;
     }
   }
-  if (a.has_v) part[(tid / TC_M) * TC_M + row] = fix;
+  if (tc_flag<FL>(a.has_v, 2)) part[(tid / TC_M) * TC_M + row] = fix;
 }
 
 // v = floor(sum of the four parts / 2^32) into column 8 ns of row tid (tid < 128).
@@ -239,7 +250,9 @@ __device__ __forceinline__ void store_overflow(const TcArgs &a, unsigned char *s
   *reinterpret_cast<__half *>(sA + canon_offset(tid, 8 * a.ns, a.kpad)) = __uint2half_rn((unsigned)(f >> 32));
 }
 
+template <bool ALL_WIDE, int FL>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_bconv_tc(const TcArgs a) {
+  const bool has_v = tc_flag<FL>(a.has_v, 2), has_sub = tc_flag<FL>(a.has_sub, 1);
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int a_bytes = TC_M * a.kpad * 2;
@@ -276,10 +289,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_bconv_tc(const TcArgs a) {
   u64 x[TC_SRC_PER];  // sources of the next block to be written into an A tile
   if (tile < total) {
     load_sources(a, tile, tpp_log2, tid, x);
-    store_sources(a, smem, tid, x, part);
+    store_sources<FL>(a, smem, tid, x, part);
   }
   if (tile + grid < total) load_sources(a, tile + grid, tpp_log2, tid, x);
-  if (a.has_v && tile < total) {
+  if (has_v && tile < total) {
     __syncthreads();
     if (tid < TC_M) store_overflow(a, smem, tid, part);
   }
@@ -328,9 +341,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_bconv_tc(const TcArgs a) {
     const int next = tile + grid;
     // A tile of the next block from the prefetched sources (its buffer's MMAs
     // completed before epilogue j - 1), then prefetch the block after it
-    if (next < total) store_sources(a, smem + nxt * a_bytes, tid, x, part);
+    if (next < total) store_sources<FL>(a, smem + nxt * a_bytes, tid, x, part);
     if (next + grid < total) load_sources(a, next + grid, tpp_log2, tid, x);
-    if (a.has_v && next < total) {  // the parts are complete after this barrier
+    if (has_v && next < total) {  // the parts are complete after this barrier
       __syncthreads();
       if (tid < TC_M) store_overflow(a, smem + nxt * a_bytes, tid, part);
     }
@@ -359,24 +372,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_bconv_tc(const TcArgs a) {
       tmem_ld16(v, tbase + (u32)(t * 8));
       tmem_ld16(u, tbase + (u32)((t + 2) * 8));
       asm volatile("tcgen05.wait::ld.sync.aligned;");
-      dst[(size_t)a.dst_pos[t] * a.n + kc] = recombine_target(v, a.tg[t], a.has_sub);
-      dst[(size_t)a.dst_pos[t + 1] * a.n + kc] = recombine_target(v + 8, a.tg[t + 1], a.has_sub);
-      dst[(size_t)a.dst_pos[t + 2] * a.n + kc] = recombine_target(u, a.tg[t + 2], a.has_sub);
-      dst[(size_t)a.dst_pos[t + 3] * a.n + kc] = recombine_target(u + 8, a.tg[t + 3], a.has_sub);
+      dst[(size_t)a.dst_pos[t] * a.n + kc] = recombine_target<ALL_WIDE>(v, a.tg[t], has_sub);
+      dst[(size_t)a.dst_pos[t + 1] * a.n + kc] = recombine_target<ALL_WIDE>(v + 8, a.tg[t + 1], has_sub);
+      dst[(size_t)a.dst_pos[t + 2] * a.n + kc] = recombine_target<ALL_WIDE>(u, a.tg[t + 2], has_sub);
+      dst[(size_t)a.dst_pos[t + 3] * a.n + kc] = recombine_target<ALL_WIDE>(u + 8, a.tg[t + 3], has_sub);
     }
     if (t + 2 <= t_hi) {
       u32 v[16];
       tmem_ld16(v, tbase + (u32)(t * 8));
       asm volatile("tcgen05.wait::ld.sync.aligned;");
-      dst[(size_t)a.dst_pos[t] * a.n + kc] = recombine_target(v, a.tg[t], a.has_sub);
-      dst[(size_t)a.dst_pos[t + 1] * a.n + kc] = recombine_target(v + 8, a.tg[t + 1], a.has_sub);
+      dst[(size_t)a.dst_pos[t] * a.n + kc] = recombine_target<ALL_WIDE>(v, a.tg[t], has_sub);
+      dst[(size_t)a.dst_pos[t + 1] * a.n + kc] = recombine_target<ALL_WIDE>(v + 8, a.tg[t + 1], has_sub);
       t += 2;
     }
     if (t < t_hi) {
       u32 v[8];
       tmem_ld8(v, tbase + (u32)(t * 8));
       asm volatile("tcgen05.wait::ld.sync.aligned;");
-      dst[(size_t)a.dst_pos[t] * a.n + kc] = recombine_target(v, a.tg[t], a.has_sub);
+      dst[(size_t)a.dst_pos[t] * a.n + kc] = recombine_target<ALL_WIDE>(v, a.tg[t], has_sub);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
   }
@@ -701,12 +714,18 @@ static int launch_bconv_tc_ex(ckks_ctx *c, size_t key, const u64 *inv_host, cons
   // 512-column TMEM allocation never waits for another CTA's
   const size_t need = 2 * (size_t)TC_M * kpad * 2 + (size_t)npad * kpad * 2 + 32 + 4 * TC_M * 8;
   const size_t smem = std::max<size_t>(need, 120 * 1024);
-  CK_CUDA(cudaFuncSetAttribute(k_bconv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  bool all_wide = true;
+  for (int t = 0; t < nt; ++t) all_wide = all_wide && a.tg[t].wide;
+  const int flags = a.has_add | a.has_sub << 1 | a.has_v << 2;
+  auto kern = flags == 0   ? (all_wide ? k_bconv_tc<true, 0> : k_bconv_tc<false, 0>)
+              : flags == 7 ? (all_wide ? k_bconv_tc<true, 7> : k_bconv_tc<false, 7>)
+                           : (all_wide ? k_bconv_tc<true, -1> : k_bconv_tc<false, -1>);
+  CK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
   const int total = (int)(n_virt / TC_M) * np;
   const int grid = std::min(total, sms);
-  PROF_LAUNCH(c, PK_BCONV_TC, (u64)np * nt * ns, (k_bconv_tc<<<grid, TC_THREADS, smem, c->stream>>>(a)));
+  PROF_LAUNCH(c, PK_BCONV_TC, (u64)np * nt * ns, (kern<<<grid, TC_THREADS, smem, c->stream>>>(a)));
   return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_CUDA;
 }
 
