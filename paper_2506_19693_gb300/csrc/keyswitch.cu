@@ -61,7 +61,9 @@ struct BConvArgs {
 // independent 128-bit sums (and their constant loads) are in flight per thread.
 constexpr int BCONV_MAX_TAB = MAX_MODS * 16;
 
-template <int NS>
+// MERGED: the merged ModDown-rescale's options (src_add, dst_sub, rdiv and negs
+// all given), else none of them: fixed per instantiation, no branch per value.
+template <int NS, bool MERGED>
 __global__ void __launch_bounds__(TPB) k_bconv(const BConvArgs a) {
   __shared__ u64 stab[BCONV_MAX_TAB];
   const u32 k = blockIdx.x * TPB + threadIdx.x;
@@ -76,9 +78,9 @@ __global__ void __launch_bounds__(TPB) k_bconv(const BConvArgs a) {
   for (int i = 0; i < NS; ++i) {
     const u64 q = a.mods[a.src_mod[i]].q;
     y[i] = shoup(src[(size_t)i * a.n + k], a.inv[2 * i], a.inv[2 * i + 1], q);
-    if (a.src_add) y[i] = addmod(y[i], __ldg(a.src_add + i), q);
+    if (MERGED) y[i] = addmod(y[i], __ldg(a.src_add + i), q);
     // y_i R_hi is nonzero only for b_i < 2^32, where y_i < 2^32 keeps it below 2^44
-    if (a.rdiv) fix += __umul64hi(y[i], __ldg(a.rdiv + i)) + y[i] * __ldg(a.rdiv + NS + i);
+    if (MERGED) fix += __umul64hi(y[i], __ldg(a.rdiv + i)) + y[i] * __ldg(a.rdiv + NS + i);
   }
   const u64 v = fix >> 32;
   u64 *dst = a.dst[p];
@@ -91,18 +93,18 @@ __global__ void __launch_bounds__(TPB) k_bconv(const BConvArgs a) {
       mac128(h0, l0, y[i], r0[i]);
       mac128(h1, l1, y[i], r1[i]);
     }
-    if (a.negs) {
+    if (MERGED) {
       mac128(h0, l0, v, __ldg(a.negs + t));
       if (two) mac128(h1, l1, v, __ldg(a.negs + t + 1));
     }
     const ModInfo m0 = a.mods[a.dst_mod[t]];
     u64 o0 = reduce128(h0, l0, m0);
-    if (a.dst_sub) o0 = submod(o0, __ldg(a.dst_sub + t), m0.q);
+    if (MERGED) o0 = submod(o0, __ldg(a.dst_sub + t), m0.q);
     dst[(size_t)a.dst_pos[t] * a.n + k] = o0;
     if (two) {
       const ModInfo m1 = a.mods[a.dst_mod[t + 1]];
       u64 o1 = reduce128(h1, l1, m1);
-      if (a.dst_sub) o1 = submod(o1, __ldg(a.dst_sub + t + 1), m1.q);
+      if (MERGED) o1 = submod(o1, __ldg(a.dst_sub + t + 1), m1.q);
       dst[(size_t)a.dst_pos[t + 1] * a.n + k] = o1;
     }
   }
@@ -343,10 +345,17 @@ int launch_bconv(ckks_ctx *c, BConvArgs &a, int ns, int np) {
   if (a.nt * ns > BCONV_MAX_TAB) return CKKS_E_PARAM;
   a.mods = c->d_mods;
   a.n = c->n;
+  const bool merged = a.src_add && a.dst_sub && a.rdiv && a.negs;
+  if (!merged && (a.src_add || a.dst_sub || a.rdiv || a.negs)) return CKKS_E_PARAM;  // all or none
   dim3 g((c->n + TPB - 1) / TPB, np);
   switch (ns) {
-#define CASE(S) \
-  case S: PROF_LAUNCH(c, PK_BCONV, (u64)np * a.nt * S, (k_bconv<S><<<g, TPB, 0, c->stream>>>(a))); break;
+#define CASE(S)                                                                                         \
+  case S:                                                                                               \
+    if (merged)                                                                                         \
+      PROF_LAUNCH(c, PK_BCONV, (u64)np * a.nt * S, (k_bconv<S, true><<<g, TPB, 0, c->stream>>>(a)));    \
+    else                                                                                                \
+      PROF_LAUNCH(c, PK_BCONV, (u64)np * a.nt * S, (k_bconv<S, false><<<g, TPB, 0, c->stream>>>(a)));   \
+    break;
     CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
     CASE(9) CASE(10) CASE(11) CASE(12) CASE(13) CASE(14) CASE(15) CASE(16)
 #undef CASE
