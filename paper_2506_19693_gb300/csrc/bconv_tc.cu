@@ -113,7 +113,7 @@ __device__ __forceinline__ u64 mul_lo_32x64(u32 s, u64 w) {
 struct TcTarget {
   u64 q, one_s;    // t, floor(2^64 / t)
   u64 r64, r64_s;  // 2^64 mod t and its Shoup companion
-  u64 w96_s;       // floor(2^96 / t): Shoup companion of 2^32 (t > 2^32)
+  u32 m80;         // floor(2^80 / t) when t > 2^48 (the quotient estimate of recombine_wide)
   u64 sub;         // subtracted from the result mod t when TcArgs::has_sub
   int wide;        // t > 2^48: the low half L < 2^47.01 is already reduced
 };
@@ -136,15 +136,20 @@ __device__ __forceinline__ u64 recombine(const u32 *v, const TcTarget &tg) {
   return csub(csub(r_lo + r_hi, tg.q << 1), tg.q);
 }
 
-// The same for t > 2^48, where L < 2^47.01 < t is already a residue:
-// y = L + (H 2^32 mod t), the latter one Shoup product with w = 2^32.
+// The same for t > 2^48: y = L + H 2^32 < 2^80 has a quotient below 2^32.  With
+// H' = floor(H / 2^16), y lies in [H' 2^48, H' 2^48 + 2^49); with m = floor(2^80 / t)
+// < 2^32, k = floor(H' m / 2^32) satisfies floor(y / t) - 3 <= k <= y / t (the
+// dropped parts are below 2^49 / t < 2 and H' / 2^32 < 1).  So y - k t lies in
+// [0, 4t) and is formed exactly from the low words: one 32-bit high multiply and
+// a 32 x 64 product.
 __device__ __forceinline__ u64 recombine_wide(const u32 *v, const TcTarget &tg) {
   const u32 c0 = acc_int(v[0]), c1 = acc_int(v[1]), c2 = acc_int(v[2]), c3 = acc_int(v[3]);
   const u32 c4 = acc_int(v[4]), c5 = acc_int(v[5]), c6 = acc_int(v[6]), c7 = acc_int(v[7]);
   const u64 L = mad_wide(c3, 1u << 24, mad_wide(c2, 1u << 16, (u64)(c0 + (c1 << 8))));
   const u64 H = mad_wide(c7, 1u << 24, mad_wide(c6, 1u << 16, (u64)(c4 + (c5 << 8))));
-  const u64 r = (H << 32) - __umul64hi(H, tg.w96_s) * tg.q;  // [0, 2t)
-  return csub(csub(r + L, tg.q << 1), tg.q);
+  const u32 k = __umulhi((u32)(H >> 16), tg.m80);
+  const u64 r = L + (H << 32) - (u64)k * tg.q;  // [0, 4t)
+  return csub(csub(r, tg.q << 1), tg.q);
 }
 
 // ALL_WIDE: every target of the launch is above 2^48 (checked on the host), so
@@ -697,8 +702,8 @@ static int launch_bconv_tc_ex(ckks_ctx *c, size_t key, const u64 *inv_host, cons
     g.one_s = (u64)(two64 / m);
     g.r64 = (u64)(two64 % m);
     g.r64_s = (u64)(((unsigned __int128)g.r64 << 64) / m);
-    g.w96_s = (u64)(((unsigned __int128)1 << 96) / m);  // < 2^64 since t > 2^32
     g.wide = m > (1ULL << 48) ? 1 : 0;
+    g.m80 = g.wide ? (u32)(((unsigned __int128)1 << 80) / m) : 0;  // < 2^32 since t > 2^48
     g.sub = dst_sub_host ? dst_sub_host[t] : 0;
     a.dst_pos[t] = (unsigned char)dst_pos[t];
   }
@@ -807,8 +812,8 @@ extern "C" int ckks_ks_inner_tc(ckks_ctx *c, const uint64_t *d, const uint64_t *
     g.one_s = (u64)(two64 / m);
     g.r64 = (u64)(two64 % m);
     g.r64_s = (u64)(((unsigned __int128)g.r64 << 64) / m);
-    g.w96_s = (u64)(((unsigned __int128)1 << 96) / m);  // used only when t > 2^48 (wide)
     g.wide = m > (1ULL << 48) ? 1 : 0;
+    g.m80 = g.wide ? (u32)(((unsigned __int128)1 << 80) / m) : 0;
     g.sub = 0;
   }
   a.err = c->tc_err;
