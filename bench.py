@@ -242,7 +242,7 @@ def kernel_work(name, units, w, ndig, prof):  # noqa: C901
     n = 1 << w.log_n
     lh = w.log_n - 8
     hbm_words = {"ntt_fwd_pass_a": 2, "ntt_fwd_pass_b": 2, "ntt_inv_pass_a": 2, "ntt_inv_pass_b": 2,
-                 "ntt_fwd_cluster": 2,
+                 "ntt_fwd_cluster": 2, "ntt_fwd_pass_b_finish": 3,
                  "automorph": 2, "tensor": 7, "ks_moddown_combine": 8, "ks_inner_product": ndig + 2,
                  "boot_mac_ext": 1, "boot_lincomb": 1, "bconv": None, "bconv_tc": None}.get(name)
     alu, tensor = [], None
@@ -281,6 +281,11 @@ def kernel_work(name, units, w, ndig, prof):  # noqa: C901
         hbm = units * 8 * n * (1 / 24 + 1 / 8)
     else:
         hbm = hbm_words * 8 * n * units if hbm_words is not None else None
+    if name == "ntt_fwd_pass_b_finish":
+        # the transformed limb, the accumulator limb and the output limb, plus a
+        # base limb where the finish adds one (counted by the library)
+        base = prof.get("finish_base_limbs", (0, 0, 0))[2] * (units / max(1, prof.get(name, (0, 0, 1))[2]))
+        hbm += 8 * n * base
     return hbm, alu, tensor
 
 
@@ -480,6 +485,8 @@ def run_gpu(args):
     tuning = {"ip_group": ctx.tune(level, B), "ntt_rows": ctx.tune_ntt(16),
               "boot_ip_group": bctx.tune(len(wb.q_bits) - 1, nb), "boot_ntt_rows": bctx.tune_ntt(16)}
     tuning["ntt_cluster"] = ctx.ntt_config()["cluster"]
+    tuning["finish_rows"] = ctx.finish_rows()
+    tuning["boot_finish_rows"] = bctx.finish_rows()
     tuning["boot_ntt_cluster"] = bctx.ntt_config()["cluster"]
 
     nvtx = torch.cuda.nvtx
@@ -665,6 +672,10 @@ def run_gpu(args):
     cluster_ntt = None
     if not (args.no_tc_ntt or args.small):
         cluster_ntt = run_cluster_ntt(ctx, w, torch, stream, max(2, min(args.steps, 3)), A, Bc, OUT)
+    finish = None
+    if not (args.no_finish_compare or args.small):
+        finish = run_fused_finish(ctx, bctx, w, torch, stream, max(2, min(args.steps, 3)), A, Bc, OUT, ROT, BIN,
+                                  BOUT)
     tc_inner = None
     if not (args.no_tc_ntt or args.small):
         tc_inner = run_tc_inner_prototype(torch, stream, max(2, min(args.steps, 3)))
@@ -725,6 +736,7 @@ def run_gpu(args):
                 "sparse_slot_bootstrap": sparse_boot,
                 "tensor_ntt_stage_prototype": tc_ntt,
                 "cluster_ntt": cluster_ntt,
+                "fused_finish": finish,
                 "tensor_inner_product_prototype": tc_inner,
                 "tuning": tuning,
                 "e2e": e2e, "roofline": roof, "op_rooflines": op_roofs, "alu_peaks": alu, "cpu_baseline": cpu,
@@ -950,6 +962,43 @@ def run_tc_inner_prototype(torch, stream, reps):
             "note": "bytes: the digits, the key and the outputs once each"}
 
 
+def run_fused_finish(ctx, bctx, w, torch, stream, reps, A, Bc, OUT, ROT, BIN, BOUT):
+    """The key-switch finish in the forward NTT's row pass (both row tiles)
+    against a separate kernel after the transform: the three phases of the step
+    timed with each (CUDA events), and the outputs compared bit for bit."""
+    import paper_2506_19693_gb300 as ck
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    phases = [("hmult_ms", lambda: ctx.mul_relin_batch(A, Bc, OUT, rescale=ck.RESCALE_MERGED), reps),
+              ("rotations_ms", lambda: ctx.rotate_hoisted(A, list(w.rot_steps), ROT), reps),
+              ("bootstrap_ms", lambda: bctx.bootstrap_batch(BIN, BOUT), max(1, reps - 1))]
+    res, outs = {}, {}
+    tuned = (ctx.finish_rows(), bctx.finish_rows())
+    for on, rows in ((False, 0), (True, 16), (True, 8)):
+        ctx.set_fused_finish(on)
+        bctx.set_fused_finish(on)
+        if on:
+            ctx.set_finish_rows(rows)
+            bctx.set_finish_rows(rows)
+        r = {}
+        for key, fn, k in phases:
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            for _ in range(k):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            r[key] = e0.elapsed_time(e1) / k
+        res[f"fused_rows{rows}" if on else "separate"] = r
+        outs[rows] = [ctx.export_ct(OUT[0]), ctx.export_ct(ROT[-1]), bctx.export_ct(BOUT[0])]
+    ctx.set_finish_rows(tuned[0])
+    bctx.set_finish_rows(tuned[1])
+    res["tuned_rows"] = {"main": tuned[0], "bootstrap": tuned[1]}
+    res["bit_exact"] = all(bool(np.array_equal(x, y)) for r in (16, 8) for x, y in zip(outs[0], outs[r]))
+    return res
+
+
 def run_cluster_ntt(ctx, w, torch, stream, reps, A, Bc, OUT):
     """The forward NTT in one pass on 8-CTA clusters (each limb read and written
     once) against the two passes (each limb crosses HBM twice), on the bench's
@@ -958,6 +1007,8 @@ def run_cluster_ntt(ctx, w, torch, stream, reps, A, Bc, OUT):
     import paper_2506_19693_gb300 as ck
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     was = ctx.ntt_config()["cluster"]
+    # like for like: the fused key-switch finish always takes the two passes
+    ctx.set_fused_finish(False)
     res = {}
     outs = {}
     for on in (False, True):
@@ -987,7 +1038,9 @@ def run_cluster_ntt(ctx, w, torch, stream, reps, A, Bc, OUT):
         if on:
             res[res_key]["resident_clusters"] = info
     ctx.set_ntt_cluster(was)
+    ctx.set_fused_finish(True)
     res["bit_exact"] = bool(np.array_equal(outs[False], outs[True]))
+    res["note"] = "key-switch finish in a separate kernel for both forms"
     return res
 
 
@@ -1375,6 +1428,7 @@ def main():
     ap.add_argument("--no-n-scaling", action="store_true")
     ap.add_argument("--no-form-compare", action="store_true")
     ap.add_argument("--no-tc-ntt", action="store_true")
+    ap.add_argument("--no-finish-compare", action="store_true")
     ap.add_argument("--form", default="tensor", choices=["uint64", "tensor", "fused"],
                     help="basis conversion on the CUDA cores (uint64), on the tensor cores (tensor), or on the "
                          "CUDA cores fused with the transforms' column passes (fused)")

@@ -491,6 +491,8 @@ int ckks_tune(ckks_ctx *ctx, int level, int batch, int *chosen);
  * 16 and 8 rows per CTA and keep the faster; *rows (may be NULL) receives it.
  * At N = 2^16 it then times the forward transform in one pass on clusters
  * (ckks_ctx_set_ntt_cluster) against the two passes and keeps the faster.
+ * Last it times the row pass that carries the key-switch finish with 16 and 8
+ * rows per CTA (ckks_ctx_set_finish_rows) and keeps the faster.
  * Needs the relinearisation key (its limbs are the timing input);
  * CKKS_E_STATE during graph capture. */
 int ckks_tune_ntt(ckks_ctx *ctx, int n_polys, int *rows);
@@ -508,6 +510,21 @@ int ckks_ctx_set_ntt_cluster(ckks_ctx *ctx, int on, int *max_clusters);
 /* The NTT launch choices in force: *rows (16 or 8 rows per row-pass CTA) and
  * *cluster (1 when the forward transform runs in one pass); either may be NULL. */
 int ckks_ctx_ntt_config(const ckks_ctx *ctx, int *rows, int *cluster);
+/* Key-switch finish in the forward NTT's row pass (ModDown, reading C9; the
+ * merged ModDown-rescale, reading C21): on = 1 (the default) computes the last
+ * step of every ModDown, (acc - [converted limbs]) P^-1 + base, and of every
+ * merged ModDown-rescale in the output stage of the transform that brings the
+ * converted limbs to the NTT domain, so those limbs are never stored; on = 0
+ * runs the transform and then a separate element-wise kernel.  Both give the
+ * same residues.  The fused form always takes the two-pass transform.  Pointers
+ * not 16-byte aligned take the separate kernel.  CKKS_E_PARAM unless on is 0 or 1. */
+int ckks_ctx_set_fused_finish(ckks_ctx *ctx, int on);
+/* The row tile of the forward row pass that carries the key-switch finish: 16
+ * or 8 rows per CTA, or 0 to follow ckks_ctx_set_ntt_rows (the default); else
+ * CKKS_E_PARAM.  ckks_tune_ntt times both and sets it. */
+int ckks_ctx_set_finish_rows(ckks_ctx *ctx, int rows);
+/* The row tile in force for that pass (16 or 8) in *rows. */
+int ckks_ctx_finish_rows(const ckks_ctx *ctx, int *rows);
 /* Autotune the gadget (reading C7) of a parameter set: for each candidate
  * dnum a context with alpha = ceil(n_q / dnum) special primes of p_bits[0]
  * bits (P spans one digit) is created on cuda_stream, its relinearisation key

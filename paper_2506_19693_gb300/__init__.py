@@ -128,6 +128,9 @@ SIGNATURES = {
     "ckks_ctx_set_ntt_rows": (_I, [_V, _I]),
     "ckks_ctx_set_ntt_cluster": (_I, [_V, _I, ctypes.POINTER(ctypes.c_int)]),
     "ckks_ctx_ntt_config": (_I, [_V, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "ckks_ctx_set_fused_finish": (_I, [_V, _I]),
+    "ckks_ctx_set_finish_rows": (_I, [_V, _I]),
+    "ckks_ctx_finish_rows": (_I, [_V, ctypes.POINTER(ctypes.c_int)]),
     "ckks_tune_dnum": (_I, [_V, _V, ctypes.POINTER(ctypes.c_uint32), _I, _I, ctypes.c_uint64,
                             ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_double)]),
     "ckks_ntt_tc": (_I, [_V, _V, ctypes.c_uint32, ctypes.c_uint32]),
@@ -309,6 +312,22 @@ class Context:
         _check(self.lib.ckks_ctx_set_ntt_cluster(self._h, 1 if on else 0, ctypes.byref(m)),
                "ckks_ctx_set_ntt_cluster")
         return m.value
+
+    def set_fused_finish(self, on: bool) -> None:
+        """Key-switch finish in the forward NTT's row pass (on, the default) or
+        in a separate element-wise kernel after it (off); same residues."""
+        _check(self.lib.ckks_ctx_set_fused_finish(self._h, 1 if on else 0), "ckks_ctx_set_fused_finish")
+
+    def set_finish_rows(self, rows: int) -> None:
+        """Row tile of the row pass carrying the key-switch finish: 16, 8, or 0
+        (follow the NTT row tile)."""
+        _check(self.lib.ckks_ctx_set_finish_rows(self._h, rows), "ckks_ctx_set_finish_rows")
+
+    def finish_rows(self) -> int:
+        """The row tile in force for the row pass carrying the finish."""
+        r = ctypes.c_int(0)
+        _check(self.lib.ckks_ctx_finish_rows(self._h, ctypes.byref(r)), "ckks_ctx_finish_rows")
+        return r.value
 
     def ntt_config(self) -> dict:
         """The NTT launch choices in force: {"rows": 16 or 8, "cluster": bool}."""

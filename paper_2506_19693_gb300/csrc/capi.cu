@@ -603,10 +603,10 @@ const char *ckks_profile_kind_name(int k) {
                                         "bconv", "ks_inner_product", "ks_moddown_combine", "tensor",
                                         "automorph", "rescale", "elementwise", "encode_decode", "bconv_tc",
                                         "boot_mac_ext", "boot_lincomb", "conv_fused", "ntt_fwd_cluster", "ks_inner_tc",
-                                        "ks_inner_flat",
+                                        "ks_inner_flat", "ntt_fwd_pass_b_finish",
                                         "ntt_fwd_strict_limbs",
                                         "ntt_inv_exact_limbs", "fused_src_limbs", "fused_dst_limbs",
-                                        "fused_dst_strict_limbs", "boot_mac_ext_macs"};
+                                        "fused_dst_strict_limbs", "boot_mac_ext_macs", "finish_base_limbs"};
   return (k >= 0 && k < PK_COUNT) ? names[k] : "unknown";
 }
 

@@ -123,6 +123,14 @@ __device__ __forceinline__ u64 uniform_dev(u64 key, u64 idx, const ModInfo &m) {
   return reduce128(draw_dev(key, 2 * idx), draw_dev(key, 2 * idx + 1), m);
 }
 __device__ __forceinline__ u64 submod(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
+// Index read by the automorphism sigma_g (X -> X^g, g odd) at output position
+// j of the canonical NTT order A[j] = a(psi^(2 brv(j) + 1)) (reading C11): the
+// output at exponent 2 brv(j) + 1 takes the input at g (2 brv(j) + 1) mod 2N.
+__device__ __forceinline__ u32 gal_src(u32 j, u32 g, u32 n, int log_n) {
+  if (g == 1) return j;
+  const u32 e = (u32)(((u64)g * (2 * (__brev(j) >> (32 - log_n)) + 1)) & (2 * n - 1));
+  return __brev((e - 1) >> 1) >> (32 - log_n);
+}
 #endif  // __CUDACC__
 
 // Host-side error helper

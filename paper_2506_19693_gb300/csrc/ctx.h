@@ -103,6 +103,8 @@ struct ckks_ctx {
   bool ntt_cluster = false;          // forward NTT at N = 2^16 in one pass on an 8-CTA cluster
   bool use_tc = false;               // basis conversion on the tensor cores (ckks_ctx_set_form)
   bool use_fused = false;            // conversion fused with the transforms' column passes (N <= 2^16)
+  bool fuse_finish = true;           // key-switch finish in the forward row pass (ckks_ctx_set_fused_finish)
+  int fin_rows = 0;                  // row tile of that row pass: 16 or 8 (0: as ntt_rows)
   std::map<size_t, void *> tc_bmats; // byte-plane constants per conversion
   int *tc_err = nullptr;             // device flag: a bounded wait expired
   // host-streamed batches (ckks_mul_relin_host): copy streams, staging slots, events
@@ -157,6 +159,26 @@ int launch_ntt(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, i
 enum { NTT_COLS = 1, NTT_ROWS = 2, NTT_BOTH = 3 };
 int launch_ntt_part(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, int nl,
                     const int *mods, bool inverse, int part);
+// The key-switch finish in the forward row pass's output stage (reading C9 and
+// C21): for limb t of polynomial p, with v the transform's fully reduced
+// output, out[p][t] = (acc[p][t] - v) w_t + b, where b = base[p][t] read
+// through sigma_gal[p] (wb null) or b = base[p][t] wb_t (wb set, gal 1), and
+// b = 0 without a base.  v itself is not stored.  acc, base (with gal 1) and
+// out are 16-byte aligned; out may alias base only with gal 1.
+struct RowFinish {
+  const u64 *w = nullptr;          // device [nl] pairs: w_t and its Shoup companion
+  const u64 *wb = nullptr;         // device [nl] pairs, or null
+  const u64 *acc[MAX_POLYS];       // limb 0 of each polynomial's accumulator
+  const u64 *base[MAX_POLYS];      // limb 0, or null
+  u32 gal[MAX_POLYS];
+  u64 *out[MAX_POLYS];
+};
+// The forward transform (NTT_BOTH, or its row pass alone after a fused column
+// pass: NTT_ROWS) of npoly <= MAX_POLYS polynomials, finished by `f` instead of
+// storing the result in dst (which then holds the column pass's output only).
+// Always the two-pass form.
+int launch_ntt_fwd_finish(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, int nl,
+                          const int *mods, int part, const RowFinish &f);
 // The one-pass forward transform on an 8-CTA cluster (N = 2^16 only): opt in
 // its shared memory and count the clusters the device holds at once.
 int ntt_cluster_prepare(const ckks_ctx *c, int *max_clusters);

@@ -312,6 +312,24 @@ int ckks_ctx_set_ntt_cluster(ckks_ctx *c, int on, int *max_clusters) {
   return CKKS_OK;
 }
 
+int ckks_ctx_set_fused_finish(ckks_ctx *c, int on) {
+  if (!c || (on != 0 && on != 1)) return CKKS_E_PARAM;
+  c->fuse_finish = on != 0;
+  return CKKS_OK;
+}
+
+int ckks_ctx_set_finish_rows(ckks_ctx *c, int rows) {
+  if (!c || (rows != 0 && rows != 8 && rows != 16)) return CKKS_E_PARAM;
+  c->fin_rows = rows;
+  return CKKS_OK;
+}
+
+int ckks_ctx_finish_rows(const ckks_ctx *c, int *rows) {
+  if (!c || !rows) return CKKS_E_PARAM;
+  *rows = c->fin_rows ? c->fin_rows : c->ntt_rows;
+  return CKKS_OK;
+}
+
 int ckks_tune_ntt(ckks_ctx *c, int n_polys, int *rows) {
   if (!c || n_polys < 1 || n_polys > 64) return CKKS_E_PARAM;
   if (c->capturing) return CKKS_E_STATE;
@@ -380,6 +398,38 @@ int ckks_tune_ntt(ckks_ctx *c, int n_polys, int *rows) {
     }
   }
   c->ntt_cluster = rc ? was_cluster : best_cluster;
+  // the row tile of the forward row pass with the key-switch finish, timed on
+  // the key's limbs as accumulators and bases (with the ModDown constants)
+  if (!rc) {
+    RowFinish f;
+    f.w = c->d_conv + c->conv.moddown_pinv;
+    for (int i = 0; i < n_polys; ++i) {
+      f.acc[i] = c->relin.data;
+      f.base[i] = c->relin.data;
+      f.gal[i] = 1u;
+      f.out[i] = dst[i];
+    }
+    float fbest = 1e30f;
+    int fbest_r = 0;
+    for (int cand : cands) {
+      c->fin_rows = cand;
+      float tot = 0.f;
+      for (int rep = 0; rep < 3 && !rc; ++rep) {
+        cudaEventRecord(e0, c->stream);
+        rc = launch_ntt_fwd_finish(c, src.data(), dst.data(), n_polys, nl, mods, NTT_BOTH, f);
+        cudaEventRecord(e1, c->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep) tot += ms;
+      }
+      if (!rc && tot < fbest) {
+        fbest = tot;
+        fbest_r = cand;
+      }
+    }
+    c->fin_rows = rc ? 0 : fbest_r;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(outs);

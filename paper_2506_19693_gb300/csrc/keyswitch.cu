@@ -29,13 +29,6 @@ constexpr int TPB = 256;
 constexpr int MAXS = 16;   // source limbs of one basis conversion
 constexpr int MAXD = 8;    // digits
 
-__device__ __forceinline__ u32 brv_ks(u32 x, int bits) { return __brev(x) >> (32 - bits); }
-// index read by sigma_g at output position j (canonical NTT order)
-__device__ __forceinline__ u32 gal_src(u32 j, u32 g, u32 n, int log_n) {
-  if (g == 1) return j;
-  const u32 e = (u32)(((u64)g * (2 * brv_ks(j, log_n) + 1)) & (2 * n - 1));
-  return brv_ks((e - 1) >> 1, log_n);
-}
 
 struct BConvArgs {
   const ModInfo *mods;
@@ -605,6 +598,20 @@ static int launch_inner(ckks_ctx *c, int level, int nv, const u64 *const *d, con
 static int combine_rescale(ckks_ctx *c, int level, int nv, u64 *const *acc, u64 *const *z,
                            const u64 *const *base0, const u64 *const *base1, u64 *const *o0, u64 *const *o1,
                            const MdrLayout &L);
+static int finish_rescale(ckks_ctx *c, int level, int nv, u64 *const *acc, u64 *const *z,
+                          const u64 *const *base0, const u64 *const *base1, u64 *const *o0, u64 *const *o1,
+                          const MdrLayout &L, int part);
+
+// The fused finish moves 16-byte words: accumulators, outputs and bases read
+// as they are must be 16-byte aligned (else the separate combine kernels run).
+static bool finish_aligned(const RowFinish &f, int np) {
+  for (int i = 0; i < np; ++i) {
+    uintptr_t a = (uintptr_t)f.acc[i] | (uintptr_t)f.out[i];
+    if (f.base[i] && f.gal[i] == 1) a |= (uintptr_t)f.base[i];
+    if (a & 15) return false;
+  }
+  return true;
+}
 
 // ModDown and rescale merged (reading C21) on the accumulators of nv outputs:
 // o_c = round((acc_c + P base_c) / (P q_l)) - u over q_0..q_{l-1}.
@@ -667,10 +674,7 @@ static int ks_merged_tail(ckks_ctx *c, int level, int nv, u64 *const *acc, u64 *
       rc = launch_conv_fused(c, f, ps.data() + p0, pz.data() + p0, cnt);
       if (rc) return rc;
     }
-    std::vector<const u64 *> pzc(pz.begin(), pz.end());
-    rc = launch_ntt_part(c, pzc.data(), pz.data(), 2 * nv, l, mods, false, NTT_ROWS);
-    if (rc) return rc;
-    return combine_rescale(c, level, nv, acc, z, base0, base1, o0, o1, L);
+    return finish_rescale(c, level, nv, acc, z, base0, base1, o0, o1, L, NTT_ROWS);
   }
   rc = launch_ntt(c, ps.data(), pd.data(), 2 * nv, ns, mods + l, true);
   if (rc) return rc;
@@ -706,11 +710,38 @@ static int ks_merged_tail(ckks_ctx *c, int level, int nv, u64 *const *acc, u64 *
     }
     if (rc) return rc;
   }
+  return finish_rescale(c, level, nv, acc, z, base0, base1, o0, o1, L, NTT_BOTH);
+}
+
+// The forward transform of the converted limbs z (the row pass alone after a
+// fused column pass: part NTT_ROWS), then the merged finish: in the row pass's
+// output stage (fuse_finish) or by k_combine_rescale after it.
+static int finish_rescale(ckks_ctx *c, int level, int nv, u64 *const *acc, u64 *const *z,
+                          const u64 *const *base0, const u64 *const *base1, u64 *const *o0, u64 *const *o1,
+                          const MdrLayout &L, int part) {
+  const u32 n = c->n;
+  const int l = level, ext = level + 1 + c->n_p;
+  int mods[MAX_MODS];
+  for (int t = 0; t < l; ++t) mods[t] = c->ext_mod(level, t);
   std::vector<u64 *> pz(2 * nv);
   std::vector<const u64 *> pzc(2 * nv);
   for (int i = 0; i < nv; ++i)
     for (int cc = 0; cc < 2; ++cc) pz[2 * i + cc] = z[i] + (size_t)cc * l * n, pzc[2 * i + cc] = pz[2 * i + cc];
-  rc = launch_ntt(c, pzc.data(), pz.data(), 2 * nv, l, mods, false);
+  if (c->fuse_finish) {
+    RowFinish f;
+    f.w = c->d_conv + L.sinv;
+    f.wb = c->d_conv + L.qlinv;
+    for (int i = 0; i < nv; ++i)
+      for (int cc = 0; cc < 2; ++cc) {
+        const int pp = 2 * i + cc;
+        f.acc[pp] = acc[i] + (size_t)cc * ext * n;
+        f.base[pp] = cc ? base1[i] : base0[i];
+        f.gal[pp] = 1u;
+        f.out[pp] = cc ? o1[i] : o0[i];
+      }
+    if (finish_aligned(f, 2 * nv)) return launch_ntt_fwd_finish(c, pzc.data(), pz.data(), 2 * nv, l, mods, part, f);
+  }
+  const int rc = launch_ntt_part(c, pzc.data(), pz.data(), 2 * nv, l, mods, false, part);
   if (rc) return rc;
   return combine_rescale(c, level, nv, acc, z, base0, base1, o0, o1, L);
 }
@@ -813,6 +844,20 @@ static int moddown_tail(ckks_ctx *c, int level, int nv, u64 *const *acc, u64 *co
       pd[2 * i + cc] = z[i] + (size_t)cc * nl * n;
       ps[2 * i + cc] = pd[2 * i + cc];
     }
+  if (c->fuse_finish) {
+    RowFinish f;
+    f.w = c->d_conv + c->conv.moddown_pinv;
+    for (int i = 0; i < nv; ++i)
+      for (int cc = 0; cc < 2; ++cc) {
+        const int pp = 2 * i + cc;
+        f.acc[pp] = acc[i] + (size_t)cc * ext * n;
+        f.base[pp] = cc ? (base1 ? base1[i] : nullptr) : (base0 ? base0[i] : nullptr);
+        f.gal[pp] = (!cc && base0_gal) ? base0_gal[i] : 1u;
+        f.out[pp] = cc ? o1[i] : o0[i];
+      }
+    if (finish_aligned(f, 2 * nv))
+      return launch_ntt_fwd_finish(c, ps.data(), pd.data(), 2 * nv, nl, mods, fused ? NTT_ROWS : NTT_BOTH, f);
+  }
   rc = launch_ntt_part(c, ps.data(), pd.data(), 2 * nv, nl, mods, false, fused ? NTT_ROWS : NTT_BOTH);
   if (rc) return rc;
   CombineArgs a;

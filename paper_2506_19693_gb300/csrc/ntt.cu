@@ -253,12 +253,84 @@ __global__ void __launch_bounds__(THREADS, 3) fwd_pass_a(const NttParams prm) {
   }
 }
 
-template <int LH, bool LOOSE, int RB>
-__device__ __forceinline__ void fwd_b_body(const NttParams &prm, u64 *sm, int mi, const u64 *src, u64 *dst) {
+// One bulk prefetch of [p, p + bytes) into L2 (p and bytes multiples of 16).
+__device__ __forceinline__ void l2_prefetch_bulk(const void *p, u32 bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// The fused key-switch finish (RowFinish) of one row-pass tile: rows row0 ..
+// row0 + RB - 1 of limb blockIdx.y, polynomial blockIdx.z, the transform's
+// outputs in the padded tile `sm`.  Each thread finishes PER pairs (k, k + 1);
+// UNR pairs' accumulator and base words are loaded before any is used.
+template <int RB, int THREADS>
+__device__ __forceinline__ void finish_tile(const RowFinish &f, const u64 *sm, int row0, u32 n, int log_n, u64 q) {
+  constexpr int PER = RB * BROW / 2 / THREADS, UNR = 4;
+  static_assert(PER % UNR == 0, "whole groups of pairs");
+  const int poly = blockIdx.z, limb = blockIdx.y;
+  const size_t lo = (size_t)limb * n + (size_t)row0 * BROW;
+  const ulonglong2 *a2 = reinterpret_cast<const ulonglong2 *>(f.acc[poly] + lo);
+  ulonglong2 *o2 = reinterpret_cast<ulonglong2 *>(f.out[poly] + lo);
+  const u64 *base = f.base[poly];
+  const u32 g = f.gal[poly];
+  const u64 w = f.w[2 * limb], ws = f.w[2 * limb + 1];
+  const bool scaled = f.wb != nullptr;
+  const u64 wb = scaled ? f.wb[2 * limb] : 0, wbs = scaled ? f.wb[2 * limb + 1] : 0;
+#pragma unroll 1
+  for (int i0 = 0; i0 < PER; i0 += UNR) {
+    ulonglong2 av[UNR], bv[UNR];
+#pragma unroll
+    for (int j = 0; j < UNR; ++j) av[j] = a2[threadIdx.x + (i0 + j) * THREADS];
+    if (base) {
+      if (g == 1) {
+        const ulonglong2 *b2 = reinterpret_cast<const ulonglong2 *>(base + lo);
+#pragma unroll
+        for (int j = 0; j < UNR; ++j) bv[j] = b2[threadIdx.x + (i0 + j) * THREADS];
+      } else {
+        const u64 *bl = base + (size_t)limb * n;
+#pragma unroll
+        for (int j = 0; j < UNR; ++j) {
+          const u32 k = (u32)(row0 * BROW + 2 * (threadIdx.x + (i0 + j) * THREADS));
+          bv[j] = make_ulonglong2(bl[gal_src(k, g, n, log_n)], bl[gal_src(k + 1, g, n, log_n)]);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < UNR; ++j) {
+      const int x = threadIdx.x + (i0 + j) * THREADS, o = padb(2 * x);
+      u64 r0 = shoup(submod(av[j].x, sm[o], q), w, ws, q), r1 = shoup(submod(av[j].y, sm[o + 1], q), w, ws, q);
+      if (base) {
+        u64 b0 = bv[j].x, b1 = bv[j].y;
+        if (scaled) {
+          b0 = shoup(b0, wb, wbs, q);
+          b1 = shoup(b1, wb, wbs, q);
+        }
+        r0 = addmod(r0, b0, q);
+        r1 = addmod(r1, b1, q);
+      }
+      o2[x] = make_ulonglong2(r0, r1);
+    }
+  }
+}
+
+// FIN: the output stage applies the key-switch finish `fin` (fwd_pass_b_fin)
+// and stores to fin.out instead of dst.
+template <int LH, bool LOOSE, int RB, bool FIN = false>
+__device__ __forceinline__ void fwd_b_body(const NttParams &prm, u64 *sm, int mi, const u64 *src, u64 *dst,
+                                           const RowFinish *fin = nullptr) {
   constexpr int H = 1 << LH, U1 = 4, U2 = LB - U1, THREADS = threads_b<RB>();
   const u64 q = prm.mods[mi].q, twoq = 2 * q;
   const ulonglong2 *tw = prm.tw + (size_t)mi * prm.n;
   const int row0 = blockIdx.x * RB;
+  if constexpr (FIN) {
+    // the finish's accumulator rows (and base rows read as they are) are
+    // needed only after the butterflies: start bringing them to L2 now
+    if (threadIdx.x == 0) {
+      const int poly = blockIdx.z;
+      const size_t lo = (size_t)blockIdx.y * prm.n + (size_t)row0 * BROW;
+      l2_prefetch_bulk(fin->acc[poly] + lo, RB * BROW * 8);
+      if (fin->base[poly] && fin->gal[poly] == 1) l2_prefetch_bulk(fin->base[poly] + lo, RB * BROW * 8);
+    }
+  }
   for (int x = threadIdx.x; x < RB * (BROW >> U1); x += THREADS) {
     const int l0 = x % (BROW >> U1), rr = x / (BROW >> U1), b = row0 + rr;
     u64 v[1 << U1];
@@ -300,6 +372,10 @@ __device__ __forceinline__ void fwd_b_body(const NttParams &prm, u64 *sm, int mi
     }
   }
   __syncthreads();
+  if constexpr (FIN) {
+    finish_tile<RB, THREADS>(*fin, sm, row0, prm.n, LH + LB, q);
+    return;
+  }
   ulonglong2 *d2 = reinterpret_cast<ulonglong2 *>(dst + (size_t)row0 * BROW);
 #pragma unroll 4
   for (int x = threadIdx.x; x < RB * BROW / 2; x += THREADS) {
@@ -319,6 +395,20 @@ __global__ void __launch_bounds__(threads_b<RB>(), RB == 16 ? 3 : 6) fwd_pass_b(
     fwd_b_body<LH, true, RB>(prm, sm, mi, src, dst);
   else
     fwd_b_body<LH, false, RB>(prm, sm, mi, src, dst);
+}
+
+// The row pass with the key-switch finish in its output stage (RowFinish).
+template <int LH, int RB>
+__global__ void __launch_bounds__(threads_b<RB>(), RB == 16 ? 3 : 6)
+    fwd_pass_b_fin(const NttParams prm, int from_src, const RowFinish fin) {
+  __shared__ u64 sm[RB * BROW + (RB * BROW >> 4)];
+  const int limb = blockIdx.y, poly = blockIdx.z;
+  const int mi = prm.mod_of_limb[limb];
+  const u64 *src = (from_src ? prm.src.p[poly] : prm.dst.p[poly]) + (size_t)limb * prm.n;
+  if (prm.mods[mi].q < LOOSE_BOUND)
+    fwd_b_body<LH, true, RB, true>(prm, sm, mi, src, nullptr, &fin);
+  else
+    fwd_b_body<LH, false, RB, true>(prm, sm, mi, src, nullptr, &fin);
 }
 
 // ---------------------------------------------------------------- inverse
@@ -495,7 +585,8 @@ void launch_inv(ckks_ctx *c, const NttParams &prm, int npoly, int part) {
 }
 
 template <int LH>
-void launch_lh(ckks_ctx *c, const NttParams &prm, int npoly, bool inverse, bool approx, int part) {
+void launch_lh(ckks_ctx *c, const NttParams &prm, int npoly, bool inverse, bool approx, int part,
+               const RowFinish *fin = nullptr) {
   if (inverse) {
     if (c->ntt_rows == 8)
       approx ? launch_inv<LH, 8, true>(c, prm, npoly, part) : launch_inv<LH, 8, false>(c, prm, npoly, part);
@@ -507,7 +598,7 @@ void launch_lh(ckks_ctx *c, const NttParams &prm, int npoly, bool inverse, bool 
   const int H = 1 << LH;
   cudaStream_t st = c->stream;
   const unsigned long long units = (unsigned long long)prm.n_limbs * npoly;
-  if (LH == 8 && part == NTT_BOTH && c->ntt_cluster && !prm.skip_first) {
+  if (LH == 8 && part == NTT_BOTH && c->ntt_cluster && !prm.skip_first && !fin) {
     launch_fwd_cluster(c, prm, npoly);
     return;
   }
@@ -515,6 +606,18 @@ void launch_lh(ckks_ctx *c, const NttParams &prm, int npoly, bool inverse, bool 
   if (part & NTT_COLS) PROF_LAUNCH(c, PK_NTT_FWD_A, units, (fwd_pass_a<LH, S1><<<ga, THREADS, 0, st>>>(prm)));
   if (!(part & NTT_ROWS)) return;
   const int from_src = (part & NTT_COLS) ? 0 : 1;
+  if (fin) {
+    if ((c->fin_rows ? c->fin_rows : c->ntt_rows) == 8) {
+      dim3 gb(H / 8, prm.n_limbs, npoly);
+      PROF_LAUNCH(c, PK_NTT_FWD_FINISH, units,
+                  (fwd_pass_b_fin<LH, 8><<<gb, threads_b<8>(), 0, st>>>(prm, from_src, *fin)));
+    } else {
+      dim3 gb(H / 16, prm.n_limbs, npoly);
+      PROF_LAUNCH(c, PK_NTT_FWD_FINISH, units,
+                  (fwd_pass_b_fin<LH, 16><<<gb, threads_b<16>(), 0, st>>>(prm, from_src, *fin)));
+    }
+    return;
+  }
   if (c->ntt_rows == 8) {
     dim3 gb(H / 8, prm.n_limbs, npoly);
     PROF_LAUNCH(c, PK_NTT_FWD_B, units, (fwd_pass_b<LH, 8><<<gb, threads_b<8>(), 0, st>>>(prm, from_src)));
@@ -902,11 +1005,23 @@ int launch_fused_lh(ckks_ctx *c, const FusedArgs &a, int ndig, int np, size_t sm
 
 int ntt_cluster_prepare(const ckks_ctx *c, int *max_clusters) { return prepare_fwd_cluster(c, max_clusters); }
 
-int launch_ntt_part(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, int nl, const int *mods,
-                    bool inverse, int part) {
+static int launch_ntt_impl(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, int nl, const int *mods,
+                           bool inverse, int part, const RowFinish *fin) {
   if (npoly <= 0 || nl <= 0) return CKKS_OK;
   if (part != NTT_BOTH && part != NTT_ROWS) return CKKS_E_PARAM;
   if (nl > MAX_MODS) return CKKS_E_PARAM;
+  if (fin) {  // one launch set, the 16-byte words of the output stage
+    if (inverse || npoly > MAX_POLYS || !fin->w) return CKKS_E_PARAM;
+    unsigned long long with_base = 0;
+    for (int i = 0; i < npoly; ++i) {
+      uintptr_t a = (uintptr_t)fin->acc[i] | (uintptr_t)fin->out[i];
+      if (fin->base[i] && fin->gal[i] == 1) a |= (uintptr_t)fin->base[i];
+      if (!fin->acc[i] || !fin->out[i] || (a & 15)) return CKKS_E_PARAM;
+      if (fin->base[i] && fin->gal[i] != 1 && (fin->wb || !(fin->gal[i] & 1))) return CKKS_E_PARAM;
+      with_base += fin->base[i] ? 1 : 0;
+    }
+    c->prof.count(PK_FINISH_BASE_LIMBS, with_base * nl);
+  }
   NttParams prm;
   prm.skip_first = 0;
   prm.mods = c->d_mods;
@@ -932,18 +1047,28 @@ int launch_ntt_part(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npo
       prm.dst.p[i] = dst[p0 + i];
     }
     switch (c->log_n - LB) {
-      case 2: launch_lh<2>(c, prm, cnt, inverse, approx, part); break;
-      case 3: launch_lh<3>(c, prm, cnt, inverse, approx, part); break;
-      case 4: launch_lh<4>(c, prm, cnt, inverse, approx, part); break;
-      case 5: launch_lh<5>(c, prm, cnt, inverse, approx, part); break;
-      case 6: launch_lh<6>(c, prm, cnt, inverse, approx, part); break;
-      case 7: launch_lh<7>(c, prm, cnt, inverse, approx, part); break;
-      case 8: launch_lh<8>(c, prm, cnt, inverse, approx, part); break;
-      case 9: launch_lh<9>(c, prm, cnt, inverse, approx, part); break;
+      case 2: launch_lh<2>(c, prm, cnt, inverse, approx, part, fin); break;
+      case 3: launch_lh<3>(c, prm, cnt, inverse, approx, part, fin); break;
+      case 4: launch_lh<4>(c, prm, cnt, inverse, approx, part, fin); break;
+      case 5: launch_lh<5>(c, prm, cnt, inverse, approx, part, fin); break;
+      case 6: launch_lh<6>(c, prm, cnt, inverse, approx, part, fin); break;
+      case 7: launch_lh<7>(c, prm, cnt, inverse, approx, part, fin); break;
+      case 8: launch_lh<8>(c, prm, cnt, inverse, approx, part, fin); break;
+      case 9: launch_lh<9>(c, prm, cnt, inverse, approx, part, fin); break;
       default: return CKKS_E_PARAM;
     }
   }
   return cudaGetLastError() == cudaSuccess ? CKKS_OK : CKKS_E_CUDA;
+}
+
+int launch_ntt_part(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, int nl, const int *mods,
+                    bool inverse, int part) {
+  return launch_ntt_impl(c, src, dst, npoly, nl, mods, inverse, part, nullptr);
+}
+
+int launch_ntt_fwd_finish(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, int nl, const int *mods,
+                          int part, const RowFinish &f) {
+  return launch_ntt_impl(c, src, dst, npoly, nl, mods, false, part, &f);
 }
 
 int launch_ntt(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, int nl, const int *mods,

@@ -27,6 +27,7 @@ enum ProfKind {
   PK_NTT_FWD_CLUSTER, // units: limbs (the one-pass forward transform on a cluster)
   PK_INNER_TC,        // units: ciphertext limbs of the tensor-core inner product prototype
   PK_INNER_FLAT,      // units: ciphertext limbs of its CUDA-core comparison kernel
+  PK_NTT_FWD_FINISH,  // units: limbs (the forward row pass with the key-switch finish)
   // counting-only classes (no launches, no time): limbs of the forward NTT
   // passes whose prime takes the strict butterfly (65 q >= 2^64), and limbs of
   // inverse passes launched with the exact quotient (a prime >= 2^61)
@@ -39,6 +40,7 @@ enum ProfKind {
   PK_FUSED_DST_LIMBS,
   PK_FUSED_DST_STRICT,
   PK_BOOT_MAC_MACS,   // counting-only: k_mac_ext's 128-bit multiply-accumulates
+  PK_FINISH_BASE_LIMBS,  // counting-only: limbs of the fused finish that read a base
   PK_COUNT
 };
 constexpr int PROF_MAX_LEVEL = 64;
