@@ -515,9 +515,11 @@ int ckks_ctx_ntt_config(const ckks_ctx *ctx, int *rows, int *cluster);
  * step of every ModDown, (acc - [converted limbs]) P^-1 + base, and of every
  * merged ModDown-rescale in the output stage of the transform that brings the
  * converted limbs to the NTT domain, so those limbs are never stored; on = 0
- * runs the transform and then a separate element-wise kernel.  Both give the
- * same residues.  The fused form always takes the two-pass transform.  Pointers
- * not 16-byte aligned take the separate kernel.  CKKS_E_PARAM unless on is 0 or 1. */
+ * runs the transform and then a separate element-wise kernel.  The rescale's
+ * last step, (c - [lifted top limb]) q_l^-1 (reading C10), takes the same
+ * route.  Both give the same residues.  The fused form always takes the
+ * two-pass transform.  Pointers not 16-byte aligned take the separate kernel.
+ * CKKS_E_PARAM unless on is 0 or 1. */
 int ckks_ctx_set_fused_finish(ckks_ctx *ctx, int on);
 /* The row tile of the forward row pass that carries the key-switch finish: 16
  * or 8 rows per CTA, or 0 to follow ckks_ctx_set_ntt_rows (the default); else

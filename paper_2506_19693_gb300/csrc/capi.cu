@@ -197,10 +197,32 @@ int rescale_chunk(ckks_ctx *c, ckks_ct *cts, int n) {
     }
   int mods[MAX_MODS];
   for (int l = 0; l < level; ++l) mods[l] = l;
-  rc = launch_ntt(c, ls.data(), ld.data(), 2 * n, level, mods, false);
-  if (rc) return rc;
-  rc = ew_rescale_finish(c, r, n);
-  if (rc) return rc;
+  // c_i = (c_i - lift_i) q_l^-1 in the output stage of the lift's forward
+  // transform (in place: each output word is read before it is written), or by
+  // k_rescale_finish after it
+  bool fused = c->fuse_finish;
+  RowFinish f;
+  if (fused) {
+    f.w = r.qlinv;
+    for (int i = 0; i < n && fused; ++i)
+      for (int p = 0; p < 2; ++p) {
+        u64 *cp = p ? r.c1[i] : r.c0[i];
+        f.acc[2 * i + p] = cp;
+        f.base[2 * i + p] = nullptr;
+        f.gal[2 * i + p] = 1u;
+        f.out[2 * i + p] = cp;
+        if ((uintptr_t)cp & 15) fused = false;
+      }
+  }
+  if (fused) {
+    rc = launch_ntt_fwd_finish(c, ls.data(), ld.data(), 2 * n, level, mods, NTT_BOTH, f);
+    if (rc) return rc;
+  } else {
+    rc = launch_ntt(c, ls.data(), ld.data(), 2 * n, level, mods, false);
+    if (rc) return rc;
+    rc = ew_rescale_finish(c, r, n);
+    if (rc) return rc;
+  }
   for (int i = 0; i < n; ++i) {
     cts[i].scale /= (double)c->mod[level];
     cts[i].level = level - 1;

@@ -160,11 +160,12 @@ enum { NTT_COLS = 1, NTT_ROWS = 2, NTT_BOTH = 3 };
 int launch_ntt_part(ckks_ctx *c, const u64 *const *src, u64 *const *dst, int npoly, int nl,
                     const int *mods, bool inverse, int part);
 // The key-switch finish in the forward row pass's output stage (reading C9 and
-// C21): for limb t of polynomial p, with v the transform's fully reduced
-// output, out[p][t] = (acc[p][t] - v) w_t + b, where b = base[p][t] read
-// through sigma_gal[p] (wb null) or b = base[p][t] wb_t (wb set, gal 1), and
-// b = 0 without a base.  v itself is not stored.  acc, base (with gal 1) and
-// out are 16-byte aligned; out may alias base only with gal 1.
+// C21; the rescale's last step, C10, has the same form): for limb t of
+// polynomial p, with v the transform's fully reduced output, out[p][t] =
+// (acc[p][t] - v) w_t + b, where b = base[p][t] read through sigma_gal[p] (wb
+// null) or b = base[p][t] wb_t (wb set, gal 1), and b = 0 without a base.  v
+// itself is not stored.  acc, base (with gal 1) and out are 16-byte aligned;
+// out may equal acc, and may alias base only with gal 1.
 struct RowFinish {
   const u64 *w = nullptr;          // device [nl] pairs: w_t and its Shoup companion
   const u64 *wb = nullptr;         // device [nl] pairs, or null

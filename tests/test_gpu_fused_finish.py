@@ -5,7 +5,9 @@ through sigma_g for hoisted rotations), and of every merged ModDown-rescale,
 transform that brings the converted limbs to the NTT domain.  The residues must
 equal those of the separate element-wise finish, for every conversion form,
 both row-pass tiles and both kinds of prime, and the result must still match
-the oracle (the oracle parity tests run with the fused finish, the default)."""
+the oracle (the oracle parity tests run with the fused finish, the default).
+The rescale's last step, (c - lift) q_l^-1, takes the same pass and is checked
+the same way."""
 import numpy as np
 import pytest
 
@@ -78,6 +80,36 @@ def test_fused_finish_equals_separate_n65536(form):
                 assert np.array_equal(x, y), (rows, i)
             err = np.max(np.abs(ctx.decrypt_decode(mer[0]) - z[0] * z[pairs]))
             assert err < 2.0 ** -30, err
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("wl", ["SMALL", "SMALLQ", "BIGQ", "PLAIN"])
+def test_fused_rescale_equals_separate(wl):
+    """The rescale's last step, (c - lift) q_l^-1, in the lift transform's row
+    pass against k_rescale_finish, on a batch and on one ciphertext (the fused
+    rescale against the oracle: test_gpu_parity.py)."""
+    import torch
+    import paper_2506_19693_gb300 as ck
+    torch.cuda.set_device(0)
+    w = getattr(si, wl)
+    ctx = ck.Context.from_workload(w)
+    try:
+        ctx.keygen(1)
+        level = len(w.q_bits) - 1
+        scale = 2.0 ** w.log2_scale
+        z = si.messages(77, 4, w.slots)
+        outs = {}
+        for on in (False, True):
+            ctx.set_fused_finish(on)
+            cts = [ctx.encrypt(ctx.encode(z[i], level, scale), level, scale, 80 + i) for i in range(4)]
+            ctx.rescale_batch(cts[:3])
+            ctx.rescale(cts[3])
+            ctx.rescale(cts[3])  # and again one level down
+            outs[on] = [ctx.export_ct(c) for c in cts]
+        assert ctx.device_error() == 0
+        for i, (x, y) in enumerate(zip(outs[False], outs[True])):
+            assert np.array_equal(x, y), i
     finally:
         ctx.close()
 
