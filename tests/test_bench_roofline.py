@@ -95,3 +95,19 @@ def test_cluster_ntt_work_is_one_pass_of_all_stages(bench):
     per_limb = n // 2 * w.log_n
     assert hbm == 2 * 8 * n * 10 and tensor is None
     assert dict((k, o) for o, k in alu) == {"bfly_fwd_loose_per_s": 5 * per_limb, "bfly_fwd_strict_per_s": 5 * per_limb}
+
+
+def test_finish_row_pass_bytes_count_base_limbs(bench):
+    """The row pass with the key-switch finish moves its input, the accumulator
+    and the output (3 limbs), plus a base limb where the finish adds one; its
+    butterflies are the 8 row stages."""
+    w = si.PLAIN
+    n = w.n
+    prof = {"ntt_fwd_pass_b_finish": (1.0, 2, 12), "finish_base_limbs": (0.0, 0, 8),
+            "ntt_fwd_pass_a": (1.0, 2, 12), "ntt_fwd_strict_limbs": (0.0, 0, 0)}
+    hbm, alu, tensor = bench.kernel_work("ntt_fwd_pass_b_finish", 12, w, 3, prof)
+    assert hbm == 8 * n * (3 * 12 + 8) and tensor is None
+    assert dict((k, o) for o, k in alu) == {"bfly_fwd_loose_per_s": 12 * (n // 2) * 8, "bfly_fwd_strict_per_s": 0}
+    # half of the class's launches: half of its base limbs
+    hbm_half, _, _ = bench.kernel_work("ntt_fwd_pass_b_finish", 6, w, 3, prof)
+    assert hbm_half == 8 * n * (3 * 6 + 4)
